@@ -1,0 +1,231 @@
+"""Python access to the plain FP64 CPU oracle (``dba_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg may import this package; the product path never
+does.  The oracle shares no code with the CUDA path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dba_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libdba_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+LOSS_L2, LOSS_HUBER, LOSS_STUDENT_T = 0, 1, 2
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("focal", ctypes.c_double), ("cx", ctypes.c_double), ("cy", ctypes.c_double),
+        ("loss", ctypes.c_int), ("loss_param", ctypes.c_double),
+        ("rho_x", ctypes.c_double), ("rho_y", ctypes.c_double),
+        ("inner_steps", ctypes.c_int), ("lm_lambda0", ctypes.c_double),
+        ("lm_lambda_min", ctypes.c_double), ("eps_depth", ctypes.c_double),
+    ]
+
+
+class Metrics(ctypes.Structure):
+    _fields_ = [
+        ("rmse_obs", ctypes.c_double), ("rmse_gt", ctypes.c_double),
+        ("objective", ctypes.c_double), ("primal_res", ctypes.c_double),
+        ("dual_res", ctypes.c_double), ("n_invalid", ctypes.c_long),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP if available, no fast-math, no FP contraction)."""
+    with _lock:
+        if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= max(
+            os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "dba_oracle.h"))
+        ):
+            return _LIB_PATH
+        os.makedirs(_BUILD, exist_ok=True)
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        base = ["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+                "-o", tmp, _SRC, "-lm"]
+        try:
+            subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
+        except subprocess.CalledProcessError:
+            subprocess.run(base, check=True, capture_output=True)
+        os.replace(tmp, _LIB_PATH)
+        return _LIB_PATH
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = build()
+        L = ctypes.CDLL(path)
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int)
+        cfgp = ctypes.POINTER(Config)
+        L.ora_rotation.argtypes = [dp, dp]
+        L.ora_project.argtypes = [cfgp, dp, dp, dp]
+        L.ora_project.restype = ctypes.c_double
+        L.ora_jacobian.argtypes = [cfgp, dp, dp, dp]
+        L.ora_loss.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double]
+        L.ora_loss.restype = ctypes.c_double
+        L.ora_weight.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double]
+        L.ora_weight.restype = ctypes.c_double
+        L.ora_local_objective.argtypes = [cfgp, dp, dp, dp, dp, dp]
+        L.ora_local_objective.restype = ctypes.c_double
+        L.ora_local_solve.argtypes = [cfgp, dp, dp, dp, dp, dp]
+        L.ora_chol_solve.argtypes = [ctypes.c_int, dp, dp, dp]
+        L.ora_chol_solve.restype = ctypes.c_int
+        L.ora_admm_init.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_long, ip, ip, dp, dp, dp, dp]
+        L.ora_admm_iterate.argtypes = [cfgp, ctypes.c_int, ctypes.c_int, ctypes.c_long, ip, ip, dp, dp,
+                                       dp, dp, dp, dp, ctypes.c_int, ctypes.c_int,
+                                       ctypes.POINTER(Metrics)]
+        L.ora_admm_iterate.restype = ctypes.c_int
+        L.ora_eval.argtypes = [cfgp, ctypes.c_int, ctypes.c_int, ctypes.c_long, ip, ip, dp, dp, dp, dp,
+                               dp, dp, dp, ctypes.POINTER(Metrics)]
+        L.ora_dense_lm.argtypes = [cfgp, ctypes.c_int, ctypes.c_int, ctypes.c_long, ip, ip, dp, dp, dp,
+                                   ctypes.c_int, dp]
+        L.ora_dense_lm.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _d(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _i(a):
+    assert a.dtype == np.int32 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def config(focal=500.0, cx=320.0, cy=240.0, loss=LOSS_HUBER, loss_param=2.0, rho_x=1.0, rho_y=1.0,
+           inner_steps=5, lm_lambda0=1e-3, lm_lambda_min=1e-12, eps_depth=1e-6) -> Config:
+    return Config(focal, cx, cy, loss, loss_param, rho_x, rho_y, inner_steps, lm_lambda0,
+                  lm_lambda_min, eps_depth)
+
+
+def config_for(scene, **overrides) -> Config:
+    kw = dict(focal=scene.focal, cx=scene.cx, cy=scene.cy, loss=scene.loss, loss_param=scene.loss_param,
+              rho_x=scene.rho_x, rho_y=scene.rho_y)
+    kw.update(overrides)
+    return config(**kw)
+
+
+def rotation(y):
+    R = np.zeros(9)
+    lib().ora_rotation(_d(_f64(y)), _d(R))
+    return R.reshape(3, 3)
+
+
+def project(cfg, x, y):
+    zp = np.zeros(2)
+    depth = lib().ora_project(ctypes.byref(cfg), _d(_f64(x)), _d(_f64(y)), _d(zp))
+    return zp, depth
+
+
+def jacobian(cfg, x, y):
+    J = np.zeros(18)
+    lib().ora_jacobian(ctypes.byref(cfg), _d(_f64(x)), _d(_f64(y)), _d(J))
+    return J.reshape(2, 9)
+
+
+def loss(kind, param, s):
+    return lib().ora_loss(kind, param, float(s))
+
+
+def weight(kind, param, s):
+    return lib().ora_weight(kind, param, float(s))
+
+
+def local_objective(cfg, z, xbar, ybar, dual, v):
+    return lib().ora_local_objective(ctypes.byref(cfg), _d(_f64(z)), _d(_f64(xbar)), _d(_f64(ybar)),
+                                     _d(_f64(dual)), _d(_f64(v)))
+
+
+def local_solve(cfg, z, xbar, ybar, dual, v0):
+    v = _f64(v0).copy()
+    lib().ora_local_solve(ctypes.byref(cfg), _d(_f64(z)), _d(_f64(xbar)), _d(_f64(ybar)),
+                          _d(_f64(dual)), _d(v))
+    return v
+
+
+def chol_solve(A, b):
+    A = _f64(A)
+    n = A.shape[0]
+    x = np.zeros(n)
+    rc = lib().ora_chol_solve(n, _d(A), _d(_f64(b)), _d(x))
+    if rc != 0:
+        raise np.linalg.LinAlgError("not positive definite")
+    return x
+
+
+class State:
+    """ADMM state in caller order: copies/duals [l, 9], cams [m, 6], pts [n, 3]."""
+
+    def __init__(self, scene, cams=None, pts=None):
+        self.scene = scene
+        self.cams = _f64(scene.cams0 if cams is None else cams).copy()
+        self.pts = _f64(scene.pts0 if pts is None else pts).copy()
+        l = scene.n_obs
+        self.copies = np.zeros((l, 9))
+        self.duals = np.zeros((l, 9))
+        lib().ora_admm_init(scene.n_cams, scene.n_pts, l, _i(scene.pt_idx), _i(scene.cam_idx),
+                            _d(self.cams), _d(self.pts), _d(self.copies), _d(self.duals))
+        self.k = 0
+
+    def clone(self):
+        o = object.__new__(State)
+        o.scene = self.scene
+        o.cams, o.pts = self.cams.copy(), self.pts.copy()
+        o.copies, o.duals, o.k = self.copies.copy(), self.duals.copy(), self.k
+        return o
+
+    def iterate(self, cfg, iters, nthreads=0, with_gt=True):
+        s = self.scene
+        m = Metrics()
+        zt = _f64(s.z_true) if with_gt else None
+        rc = lib().ora_admm_iterate(ctypes.byref(cfg), s.n_cams, s.n_pts, s.n_obs, _i(s.pt_idx),
+                                    _i(s.cam_idx), _d(_f64(s.z)), _d(zt), _d(self.copies),
+                                    _d(self.duals), _d(self.cams), _d(self.pts), iters, nthreads,
+                                    ctypes.byref(m))
+        if rc != 0:
+            raise ValueError("oracle rejected the scene")
+        self.k += iters
+        return m.as_dict()
+
+    def metrics(self, cfg, cams_prev=None, pts_prev=None, with_gt=True):
+        s = self.scene
+        m = Metrics()
+        zt = _f64(s.z_true) if with_gt else None
+        lib().ora_eval(ctypes.byref(cfg), s.n_cams, s.n_pts, s.n_obs, _i(s.pt_idx), _i(s.cam_idx),
+                       _d(_f64(s.z)), _d(zt), _d(self.copies), _d(self.cams), _d(self.pts),
+                       _d(cams_prev), _d(pts_prev), ctypes.byref(m))
+        return m.as_dict()
+
+
+def dense_lm(cfg, scene, cams=None, pts=None, max_iters=200):
+    cams = _f64(scene.cams0 if cams is None else cams).copy()
+    pts = _f64(scene.pts0 if pts is None else pts).copy()
+    obj = ctypes.c_double(0.0)
+    it = lib().ora_dense_lm(ctypes.byref(cfg), scene.n_cams, scene.n_pts, scene.n_obs, _i(scene.pt_idx),
+                            _i(scene.cam_idx), _d(_f64(scene.z)), _d(cams), _d(pts), max_iters,
+                            ctypes.byref(obj))
+    if it < 0:
+        raise ValueError("dense LM failed")
+    return cams, pts, obj.value, it
