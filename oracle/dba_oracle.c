@@ -130,7 +130,7 @@ double ora_loss(int kind, double param, double s) {
   }
   if (kind == ORA_LOSS_STUDENT_T) {
     double nu = param;
-    return nu * log(1.0 + s / nu);
+    return nu * log1p(s / nu);
   }
   return s;
 }
