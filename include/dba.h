@@ -1,0 +1,165 @@
+/*
+ * dba.h -- C ABI of a GB300 (sm_103a) implementation of distributed bundle
+ * adjustment by consensus ADMM (Ramamurthy, Lin, Aravkin, Pankanti, Viguier,
+ * "Distributed Bundle Adjustment", arXiv 1708.07954).
+ *
+ * Problem (Sec. 2.1-2.2 of the paper): m cameras y_j = (alpha, beta, gamma,
+ * tx, ty, tz) with R = Rz(gamma) Ry(beta) Rx(alpha), n points x_i in R^3,
+ * observations z_ij (pixels) for the pairs (i, j) listed by the caller.  The
+ * pixel model is z = f (R x + t)_{1,2} / (R x + t)_3 + (cx, cy) (Eq. 1 with the
+ * focal matrix K applied and a known principal point).
+ *
+ * Method (Sec. 3.1): every observation o = (i, j) owns a private copy of its
+ * point and camera (9 unknowns) and the duals r_o (3), s_o (6).  One ADMM
+ * iteration is
+ *   (9)       local solve of every observation's robust subproblem,
+ *   (10),(11) consensus means of the copies plus scaled duals per point/camera,
+ *   (12),(13) dual ascent with the new consensus.
+ * Equation numbers follow the order of the paper's LaTeX source.
+ *
+ * Conventions for every entry point:
+ *   - host pointers are caller-owned and only read (inputs) or written
+ *     (outputs) during the call; the library owns all device memory;
+ *   - observations are accepted and returned in caller order;
+ *   - arrays are row-major, float64, C-contiguous: cams [m][6], pts [n][3],
+ *     z [l][2], copies/duals [l][9] = (point part 3, camera part 6);
+ *   - every call returns a dba_status and never aborts; dba_last_error() gives
+ *     the message of the last failure on that context;
+ *   - a context is not thread-safe; separate contexts are independent.
+ */
+#ifndef DBA_H
+#define DBA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dba_ctx dba_ctx;
+
+typedef enum {
+  DBA_OK = 0,
+  DBA_EINVAL = -1,   /* bad argument: index out of range, n <= 0, non-finite input, bad config */
+  DBA_ENOMEM = -2,   /* device or host allocation failed */
+  DBA_ECUDA = -3,    /* a CUDA call failed (message in dba_last_error) */
+  DBA_ESTATE = -4,   /* call out of order, e.g. dba_iterate before dba_set_observations */
+  DBA_ENUMERIC = -5, /* a local solve produced a non-finite value */
+  DBA_ETIMEOUT = -6  /* a bounded device-side wait gave up */
+} dba_status;
+
+typedef enum {
+  DBA_LOSS_L2 = 0,        /* phi_m(e) = |e|^2, Eq. (2) */
+  DBA_LOSS_HUBER = 1,     /* |e|^2 if |e| <= delta else 2 delta |e| - delta^2 (Sec. 3.1) */
+  DBA_LOSS_STUDENT_T = 2  /* nu log(1 + |e|^2 / nu) (robust loss cited in Sec. 1) */
+} dba_loss;
+
+typedef enum {
+  DBA_PREC_F64 = 0,       /* local solves, consensus and duals in FP64 */
+  DBA_PREC_F32_LOCAL = 1  /* local solves in FP32; consensus, duals, objective in FP64 */
+} dba_precision;
+
+typedef struct {
+  double focal, cx, cy;   /* pinhole intrinsics (pixels), shared by all cameras */
+  int loss;               /* dba_loss */
+  double loss_param;      /* Huber delta (pixels) or Student's t nu */
+  double rho_x, rho_y;    /* consensus penalties of Eq. (8), > 0 */
+  int inner_steps;        /* damped Gauss-Newton steps per local solve, >= 0 */
+  double lm_lambda0;      /* first damping = lm_lambda0 * mean(diag H) */
+  double lm_lambda_min;   /* lower clamp of the damping after an accepted step */
+  double eps_depth;       /* a copy with depth (R x + t)_3 <= eps_depth is rejected */
+  int precision;          /* dba_precision */
+  int tile_obs;           /* observations per tile (32..256, multiple of 32); 0 = automatic */
+  int use_graph;          /* 1: replay each iteration as a CUDA graph; 0: plain launches */
+  void* cuda_stream;      /* cudaStream_t to launch on; NULL = a stream owned by the context */
+} dba_config;
+
+typedef struct {
+  long long iters_done;   /* ADMM iterations run on this context since the state was set */
+  double rmse_obs;        /* sqrt(mean |z - f(x_i, y_j)|^2) at consensus, valid observations */
+  double rmse_gt;         /* sqrt(mean over inliers |f(x_i, y_j) - f(x*_i, y*_j)|^2); 0 without ground truth */
+  double objective;       /* sum of phi_m(z - f(x_i, y_j)) at consensus: Eq. (2) with phi_m */
+  double primal_res;      /* sqrt(sum over copies |copy - consensus|^2) */
+  double dual_res;        /* sqrt(sum over copies rho^2 |consensus - previous consensus|^2) */
+  long long n_invalid;    /* observations with consensus depth <= eps_depth (excluded above) */
+  double seconds;         /* device time of the dba_iterate call (CUDA events) */
+} dba_stats;
+
+/* Fills *cfg with defaults: focal 500, principal point (320, 240), Huber 2 px,
+ * rho 1, 5 inner steps, lambda0 1e-3, lambda_min 1e-12, eps_depth 1e-6,
+ * FP32 local solves, automatic tile size, graphs on, own stream. */
+void dba_config_default(dba_config* cfg);
+
+/* Creates a context on the current CUDA device.  Validates *cfg (EINVAL).
+ * No device memory is allocated until dba_set_observations. */
+dba_status dba_create(const dba_config* cfg, dba_ctx** out);
+
+/* Loads one problem (Sec. 2.2: unknowns 6m + 3n, one observation per listed
+ * pair).  pt_idx/cam_idx [n_obs] index pts0/cams0; z [n_obs][2] pixels;
+ * cams0 [n_cams][6], pts0 [n_pts][3] the initial estimate.  Copies start at
+ * the initial estimate and duals at zero (the paper does not state an
+ * initialisation).  A camera or point with no observation keeps its value.
+ * EINVAL on an index out of range, n_obs <= 0, n_cams/n_pts <= 0 or a
+ * non-finite value.  Replaces any previous problem of this context. */
+dba_status dba_set_observations(dba_ctx* ctx, int32_t n_cams, int32_t n_pts, int64_t n_obs,
+                                const int32_t* pt_idx, const int32_t* cam_idx, const double* z,
+                                const double* cams0, const double* pts0);
+
+/* Optional: ground-truth cameras [n_cams][6] and points [n_pts][3]; enables
+ * dba_stats.rmse_gt, the RMS distance between the consensus projections and
+ * the noise-free projections of the ground truth.  inlier [n_obs] (caller
+ * order, nullable = all) selects the observations it averages over: pass 0 for
+ * observations whose pixel is an outlier rather than a noisy measurement. */
+dba_status dba_set_ground_truth(dba_ctx* ctx, const double* cams_gt, const double* pts_gt,
+                                const uint8_t* inlier);
+
+/* Runs n_iters >= 0 ADMM iterations, Eqs. (9)-(13), on the context's stream
+ * and waits for them.  stats (nullable) receives the metrics at the final
+ * consensus.  ESTATE before dba_set_observations, ENUMERIC if a local solve
+ * produced a non-finite value (the state is then unspecified). */
+dba_status dba_iterate(dba_ctx* ctx, int n_iters, dba_stats* stats);
+
+/* Runs up to max_iters iterations and stops after the first iteration whose
+ * consensus has rmse_gt <= target_rmse_gt (needs ground truth; ESTATE
+ * otherwise).  Metrics are evaluated after every iteration; stats receives
+ * those of the last one. */
+dba_status dba_iterate_until(dba_ctx* ctx, int max_iters, double target_rmse_gt, dba_stats* stats);
+
+/* Metrics of the current state without iterating. */
+dba_status dba_evaluate(dba_ctx* ctx, dba_stats* stats);
+
+/* Copies the consensus estimate to cams [n_cams][6] and pts [n_pts][3]. */
+dba_status dba_get_params(dba_ctx* ctx, double* cams, double* pts);
+
+/* Copies the per-observation copies [n_obs][9] and duals (r, s) [n_obs][9],
+ * caller order.  Either pointer may be NULL. */
+dba_status dba_get_state(dba_ctx* ctx, double* copies, double* duals);
+
+/* Replaces the whole ADMM state (checkpoint resume): copies, duals [n_obs][9]
+ * in caller order, consensus cams [n_cams][6] and pts [n_pts][3].
+ * iters_done restarts at 0. */
+dba_status dba_set_state(dba_ctx* ctx, const double* copies, const double* duals,
+                         const double* cams, const double* pts);
+
+/* Device time per kernel, averaged over the launches of the last dba_profile
+ * call: names[i] (static strings) and ms[i] for i < *count (in: capacity). */
+dba_status dba_profile(dba_ctx* ctx, int n_iters, const char** names, double* ms, int* count);
+
+/* Sizes of the internal observation layout after dba_set_observations, for
+ * traffic models: out[0] tiles, out[1] observations per tile (block size),
+ * out[2] point runs, out[3] camera runs (= camera partial slots), out[4]
+ * points whose track spans several tiles, out[5] their partial slots.
+ * *count: in capacity, out entries written. */
+dba_status dba_layout(dba_ctx* ctx, int64_t* out, int* count);
+
+/* Message of the last failed call on ctx (or of the last failed dba_create
+ * when ctx is NULL).  Never NULL. */
+const char* dba_last_error(const dba_ctx* ctx);
+
+/* Frees the context and its device memory.  NULL is ignored. */
+void dba_destroy(dba_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DBA_H */

@@ -1,0 +1,757 @@
+// Host side of the C ABI declared in include/dba.h: validation, the
+// observation layout (sort by point, tiles of whole tracks, segmented-run
+// tables), device memory, CUDA-graph replay of one ADMM iteration, metrics
+// and state transfer.  Every step of the iteration itself runs in the kernels
+// of dba_kernels.cu; the host only prepares static index tables.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/dba.h"
+#include "dba_internal.h"
+
+using dba::DevCtl;
+using dba::DevProblem;
+using dba::Params;
+
+namespace {
+thread_local std::string g_create_error = "no error";
+
+struct HostLayout {
+  std::vector<long long> perm;  // internal position -> caller index
+  std::vector<int> obs_pt, obs_cam;
+  std::vector<unsigned char> cam_rank;
+  std::vector<int> tile_off{0}, tile_pseg_off{0}, pseg_pt, pseg_slot, tile_cseg_off{0}, cseg_slot;
+  std::vector<int2> pseg, cseg;
+  std::vector<int> cam_slot_off, cam_count, split_pt, split_slot_off{0}, pt_count;
+  int n_cam_slots = 0, n_pt_slots = 0;
+};
+
+bool finite_all(const double* p, long long n) {
+  for (long long k = 0; k < n; ++k)
+    if (!std::isfinite(p[k])) return false;
+  return true;
+}
+}  // namespace
+
+struct dba_ctx {
+  dba_config cfg;
+  Params prm;
+  std::string err = "no error";
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  bool fp32 = true;
+  // problem
+  bool has_problem = false, has_gt = false;
+  int n_cams = 0, n_pts = 0;
+  long long n_obs = 0;
+  std::vector<long long> perm;   // internal position -> caller index
+  std::vector<int> h_obs_pt, h_obs_cam;
+  int64_t n_pseg = 0;
+  std::vector<void*> allocs;
+  DevProblem P{};
+  int cur = 0, pending = 0;
+  long long iters = 0;
+  // graph of one iteration
+  cudaGraphExec_t graph = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+  dba_status fail(dba_status s, const std::string& msg) {
+    err = msg;
+    return s;
+  }
+  dba_status cuda_fail(cudaError_t e, const char* where) {
+    err = std::string(where) + ": " + cudaGetErrorString(e);
+    return DBA_ECUDA;
+  }
+  void free_problem() {
+    if (graph) cudaGraphExecDestroy(graph);
+    graph = nullptr;
+    for (void* p : allocs) cudaFree(p);
+    allocs.clear();
+    P = DevProblem{};
+    has_problem = has_gt = false;
+    perm.clear();
+    h_obs_pt.clear();
+    h_obs_cam.clear();
+  }
+  template <typename V>
+  cudaError_t alloc(V** out, size_t count) {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(V));
+    if (e != cudaSuccess) return e;
+    allocs.push_back(p);
+    *out = static_cast<V*>(p);
+    return cudaSuccess;
+  }
+  template <typename V>
+  cudaError_t upload(const V** out, const std::vector<V>& h) {
+    V* d = nullptr;
+    cudaError_t e = alloc(&d, h.size());
+    if (e != cudaSuccess) return e;
+    if (!h.empty()) e = cudaMemcpyAsync(d, h.data(), h.size() * sizeof(V), cudaMemcpyHostToDevice, stream);
+    *out = d;
+    return e;
+  }
+};
+
+#define DBA_CUDA(call, where)                           \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return ctx->cuda_fail(e_, where); \
+  } while (0)
+
+namespace {
+
+// Observation layout.  Points are ordered by their smallest camera index so
+// that a tile's tracks share cameras; each point's observations are sorted by
+// camera.  Tiles hold whole tracks of at most tile_obs observations; a track
+// longer than a tile is cut into tile-sized pieces reduced in the finalize
+// kernel.  Within a tile, observations of one camera form runs in camera order.
+void build_layout(int n_cams, int n_pts, long long n_obs, const int32_t* pt_idx,
+                  const int32_t* cam_idx, int NT, HostLayout& L) {
+  L.pt_count.assign(n_pts, 0);
+  L.cam_count.assign(n_cams, 0);
+  std::vector<int> min_cam(n_pts, n_cams);
+  for (long long o = 0; o < n_obs; ++o) {
+    L.pt_count[pt_idx[o]] += 1;
+    L.cam_count[cam_idx[o]] += 1;
+    min_cam[pt_idx[o]] = std::min(min_cam[pt_idx[o]], (int)cam_idx[o]);
+  }
+  // counting sort of observations by point
+  std::vector<long long> pstart(n_pts + 1, 0);
+  for (int i = 0; i < n_pts; ++i) pstart[i + 1] = pstart[i] + L.pt_count[i];
+  std::vector<long long> by_pt(n_obs);
+  {
+    std::vector<long long> fill(pstart.begin(), pstart.end() - 1);
+    for (long long o = 0; o < n_obs; ++o) by_pt[fill[pt_idx[o]]++] = o;
+  }
+  std::vector<int> order;
+  order.reserve(n_pts);
+  for (int i = 0; i < n_pts; ++i)
+    if (L.pt_count[i] > 0) order.push_back(i);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return min_cam[a] < min_cam[b]; });
+
+  L.perm.resize(n_obs);
+  L.obs_pt.resize(n_obs);
+  L.obs_cam.resize(n_obs);
+  L.cam_rank.assign(n_obs, 0);
+  long long pos = 0;
+  int fill_tile = 0;  // observations in the open tile
+  auto close_tile = [&]() {
+    L.tile_off.push_back((int)pos);
+    L.tile_pseg_off.push_back((int)L.pseg.size());
+    fill_tile = 0;
+  };
+  for (int i : order) {
+    const long long s = pstart[i];
+    const int c = L.pt_count[i];
+    std::sort(by_pt.begin() + s, by_pt.begin() + s + c, [&](long long a, long long b) {
+      return cam_idx[a] != cam_idx[b] ? cam_idx[a] < cam_idx[b] : a < b;
+    });
+    for (int k = 0; k < c; ++k) {
+      const long long o = by_pt[s + k];
+      L.perm[pos + k] = o;
+      L.obs_pt[pos + k] = i;
+      L.obs_cam[pos + k] = cam_idx[o];
+    }
+    if (c <= NT) {
+      if (fill_tile + c > NT) close_tile();
+      L.pseg.push_back(make_int2(fill_tile, c));
+      L.pseg_pt.push_back(i);
+      L.pseg_slot.push_back(-1);
+      fill_tile += c;
+      pos += c;
+    } else {
+      if (fill_tile > 0) close_tile();
+      L.split_pt.push_back(i);
+      int rem = c;
+      while (rem > 0) {
+        const int take = std::min(rem, NT);
+        L.pseg.push_back(make_int2(0, take));
+        L.pseg_pt.push_back(i);
+        L.pseg_slot.push_back(L.n_pt_slots++);
+        fill_tile = take;
+        pos += take;
+        rem -= take;
+        if (rem > 0) close_tile();
+      }
+      L.split_slot_off.push_back(L.n_pt_slots);
+    }
+  }
+  if (fill_tile > 0) close_tile();
+  const int n_tiles = (int)L.tile_off.size() - 1;
+
+  // camera runs per tile, in camera order
+  std::vector<int> run_cam;
+  std::vector<int> idx;
+  for (int t = 0; t < n_tiles; ++t) {
+    const int o0 = L.tile_off[t], o1 = L.tile_off[t + 1];
+    idx.resize(o1 - o0);
+    for (int k = 0; k < o1 - o0; ++k) idx[k] = o0 + k;
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return L.obs_cam[a] < L.obs_cam[b]; });
+    for (int r = 0; r < (int)idx.size(); ++r) L.cam_rank[idx[r]] = (unsigned char)r;
+    int r = 0;
+    while (r < (int)idx.size()) {
+      int e = r;
+      while (e < (int)idx.size() && L.obs_cam[idx[e]] == L.obs_cam[idx[r]]) ++e;
+      L.cseg.push_back(make_int2(r, e - r));
+      run_cam.push_back(L.obs_cam[idx[r]]);
+      r = e;
+    }
+    L.tile_cseg_off.push_back((int)L.cseg.size());
+  }
+  // camera partial slots grouped by camera
+  L.cam_slot_off.assign(n_cams + 1, 0);
+  for (int cam : run_cam) L.cam_slot_off[cam + 1] += 1;
+  for (int j = 0; j < n_cams; ++j) L.cam_slot_off[j + 1] += L.cam_slot_off[j];
+  std::vector<int> cfill(L.cam_slot_off.begin(), L.cam_slot_off.end() - 1);
+  L.cseg_slot.resize(run_cam.size());
+  for (size_t r = 0; r < run_cam.size(); ++r) L.cseg_slot[r] = cfill[run_cam[r]]++;
+  L.n_cam_slots = L.cam_slot_off[n_cams];
+}
+
+}  // namespace
+
+extern "C" {
+
+void dba_config_default(dba_config* cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof *cfg);
+  cfg->focal = 500.0;
+  cfg->cx = 320.0;
+  cfg->cy = 240.0;
+  cfg->loss = DBA_LOSS_HUBER;
+  cfg->loss_param = 2.0;
+  cfg->rho_x = 1.0;
+  cfg->rho_y = 1.0;
+  cfg->inner_steps = 5;
+  cfg->lm_lambda0 = 1e-3;
+  cfg->lm_lambda_min = 1e-12;
+  cfg->eps_depth = 1e-6;
+  cfg->precision = DBA_PREC_F32_LOCAL;
+  cfg->tile_obs = 0;
+  cfg->use_graph = 1;
+  cfg->cuda_stream = nullptr;
+}
+
+dba_status dba_create(const dba_config* cfg, dba_ctx** out) {
+  if (!cfg || !out) {
+    g_create_error = "dba_create: null argument";
+    return DBA_EINVAL;
+  }
+  *out = nullptr;
+  const bool ok = std::isfinite(cfg->focal) && cfg->focal > 0 && std::isfinite(cfg->cx) &&
+                  std::isfinite(cfg->cy) && cfg->loss >= 0 && cfg->loss <= 2 &&
+                  (cfg->loss == DBA_LOSS_L2 || (std::isfinite(cfg->loss_param) && cfg->loss_param > 0)) &&
+                  std::isfinite(cfg->rho_x) && cfg->rho_x > 0 && std::isfinite(cfg->rho_y) &&
+                  cfg->rho_y > 0 && cfg->inner_steps >= 0 && cfg->inner_steps <= 1000 &&
+                  std::isfinite(cfg->lm_lambda0) && cfg->lm_lambda0 > 0 &&
+                  std::isfinite(cfg->lm_lambda_min) && cfg->lm_lambda_min >= 0 &&
+                  std::isfinite(cfg->eps_depth) && (cfg->precision == 0 || cfg->precision == 1) &&
+                  (cfg->tile_obs == 0 || cfg->tile_obs == 64 || cfg->tile_obs == 128 ||
+                   cfg->tile_obs == 256);
+  if (!ok) {
+    g_create_error = "dba_create: invalid configuration (check focal, loss, rho, steps, precision, tile_obs)";
+    return DBA_EINVAL;
+  }
+  cudaError_t e = cudaFree(nullptr);  // initialise the runtime on the current device
+  if (e != cudaSuccess) {
+    g_create_error = std::string("dba_create: CUDA unavailable: ") + cudaGetErrorString(e);
+    return DBA_ECUDA;
+  }
+  dba_ctx* ctx = new (std::nothrow) dba_ctx();
+  if (!ctx) {
+    g_create_error = "dba_create: out of host memory";
+    return DBA_ENOMEM;
+  }
+  ctx->cfg = *cfg;
+  ctx->fp32 = cfg->precision == DBA_PREC_F32_LOCAL;
+  ctx->prm = Params{cfg->focal, cfg->cx, cfg->cy, cfg->loss, cfg->loss_param, cfg->rho_x, cfg->rho_y,
+                    cfg->inner_steps, cfg->lm_lambda0, cfg->lm_lambda_min, cfg->eps_depth};
+  if (cfg->cuda_stream) {
+    ctx->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
+  } else {
+    e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      g_create_error = std::string("dba_create: ") + cudaGetErrorString(e);
+      delete ctx;
+      return DBA_ECUDA;
+    }
+    ctx->own_stream = true;
+  }
+  if (cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess) {
+    g_create_error = "dba_create: cudaEventCreate failed";
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return DBA_ECUDA;
+  }
+  *out = ctx;
+  return DBA_OK;
+}
+
+void dba_destroy(dba_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  ctx->free_problem();
+  if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+  if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+const char* dba_last_error(const dba_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+}  // extern "C"
+
+namespace {
+
+template <typename T>
+void to_T(const std::vector<double>& src, std::vector<T>& dst) {
+  dst.resize(src.size());
+  for (size_t k = 0; k < src.size(); ++k) dst[k] = (T)src[k];
+}
+
+template <typename T>
+dba_status upload_state_T(dba_ctx* ctx, const double* cams, const double* pts,
+                          const std::vector<double>& hdel, const std::vector<double>& hdual) {
+  DevProblem& P = ctx->P;
+  const int m = ctx->n_cams, n = ctx->n_pts;
+  std::vector<T> tdel, tX, tY;
+  to_T(hdel, tdel);
+  to_T(std::vector<double>(pts, pts + 3 * (size_t)n), tX);
+  to_T(std::vector<double>(cams, cams + 6 * (size_t)m), tY);
+  cudaStream_t st = ctx->stream;
+  DBA_CUDA(cudaMemcpyAsync(P.delta, tdel.data(), tdel.size() * sizeof(T), cudaMemcpyHostToDevice, st), "upload copies");
+  DBA_CUDA(cudaMemcpyAsync(P.adual, hdual.data(), hdual.size() * sizeof(double), cudaMemcpyHostToDevice, st), "upload duals");
+  for (int b = 0; b < 2; ++b) {
+    DBA_CUDA(cudaMemcpyAsync(P.X[b], pts, 3 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice, st), "upload points");
+    DBA_CUDA(cudaMemcpyAsync(P.Y[b], cams, 6 * (size_t)m * sizeof(double), cudaMemcpyHostToDevice, st), "upload cameras");
+  }
+  DBA_CUDA(cudaMemcpyAsync(P.Xm, tX.data(), tX.size() * sizeof(T), cudaMemcpyHostToDevice, st), "upload points");
+  DBA_CUDA(cudaMemcpyAsync(P.Ym, tY.data(), tY.size() * sizeof(T), cudaMemcpyHostToDevice, st), "upload cameras");
+  DBA_CUDA(cudaMemsetAsync(P.DX, 0, 3 * (size_t)n * sizeof(T), st), "clear");
+  DBA_CUDA(cudaMemsetAsync(P.DY, 0, 6 * (size_t)m * sizeof(T), st), "clear");
+  DBA_CUDA(cudaMemsetAsync(P.ctl, 0, sizeof(DevCtl), st), "clear");
+  DBA_CUDA(cudaStreamSynchronize(st), "upload state");
+  ctx->cur = 0;
+  ctx->pending = 0;
+  ctx->iters = 0;
+  return DBA_OK;
+}
+
+// Copies given as absolute values are stored as offsets from the consensus;
+// duals (r, s) are stored scaled by 1/rho.  NULL copies = consensus, NULL duals = 0.
+dba_status upload_state(dba_ctx* ctx, const double* cams, const double* pts, const double* copies,
+                        const double* duals) {
+  const long long l = ctx->n_obs;
+  std::vector<double> hdel(9 * (size_t)l, 0.0), hdual(9 * (size_t)l, 0.0);
+  if (copies || duals) {
+    for (long long o = 0; o < l; ++o) {
+      const long long src = ctx->perm[o];
+      const size_t i = ctx->h_obs_pt[o], j = ctx->h_obs_cam[o];
+      for (int c = 0; c < 9; ++c) {
+        if (copies) {
+          const double cons = c < 3 ? pts[3 * i + c] : cams[6 * j + c - 3];
+          hdel[c * (size_t)l + o] = copies[9 * src + c] - cons;
+        }
+        if (duals) hdual[c * (size_t)l + o] = duals[9 * src + c] / (c < 3 ? ctx->prm.rho_x : ctx->prm.rho_y);
+      }
+    }
+  }
+  return ctx->fp32 ? upload_state_T<float>(ctx, cams, pts, hdel, hdual)
+                   : upload_state_T<double>(ctx, cams, pts, hdel, hdual);
+}
+
+dba_status read_metrics(dba_ctx* ctx, dba_stats* st, double seconds) {
+  DBA_CUDA(dba::launch_metrics(ctx->P, ctx->prm, ctx->fp32, ctx->cur, ctx->pending, ctx->stream), "metrics launch");
+  double h[8];
+  DBA_CUDA(cudaMemcpyAsync(h, ctx->P.metric_out, sizeof h, cudaMemcpyDeviceToHost, ctx->stream), "metrics copy");
+  DBA_CUDA(cudaStreamSynchronize(ctx->stream), "metrics");
+  const double valid = h[3];
+  st->iters_done = ctx->iters;
+  st->rmse_obs = valid > 0 ? std::sqrt(h[0] / valid) : 0.0;
+  st->objective = h[1];
+  st->rmse_gt = (h[7] > 0 && ctx->has_gt) ? std::sqrt(h[2] / h[7]) : 0.0;
+  st->n_invalid = (long long)h[4];
+  st->primal_res = std::sqrt(h[5]);
+  st->dual_res = std::sqrt(h[6]);
+  st->seconds = seconds;
+  return DBA_OK;
+}
+
+dba_status launch_iteration(dba_ctx* ctx) {
+  DBA_CUDA(dba::launch_tile_iterate(ctx->P, ctx->prm, ctx->fp32, ctx->stream), "tile_iterate launch");
+  DBA_CUDA(dba::launch_finalize(ctx->P, ctx->fp32, ctx->stream), "finalize launch");
+  return DBA_OK;
+}
+
+dba_status ensure_graph(dba_ctx* ctx) {
+  if (ctx->graph) return DBA_OK;
+  cudaGraph_t g = nullptr;
+  DBA_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal), "graph capture");
+  cudaError_t e1 = dba::launch_tile_iterate(ctx->P, ctx->prm, ctx->fp32, ctx->stream);
+  cudaError_t e2 = dba::launch_finalize(ctx->P, ctx->fp32, ctx->stream);
+  cudaError_t e3 = cudaStreamEndCapture(ctx->stream, &g);
+  if (e1 != cudaSuccess) return ctx->cuda_fail(e1, "graph capture (tile_iterate)");
+  if (e2 != cudaSuccess) return ctx->cuda_fail(e2, "graph capture (finalize)");
+  if (e3 != cudaSuccess) return ctx->cuda_fail(e3, "graph capture");
+  cudaError_t e = cudaGraphInstantiate(&ctx->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    ctx->graph = nullptr;
+    return ctx->cuda_fail(e, "graph instantiate");
+  }
+  return DBA_OK;
+}
+
+dba_status run_iterations(dba_ctx* ctx, int n) {
+  if (ctx->cfg.use_graph) {
+    dba_status s = ensure_graph(ctx);
+    if (s != DBA_OK) return s;
+    for (int it = 0; it < n; ++it) DBA_CUDA(cudaGraphLaunch(ctx->graph, ctx->stream), "graph launch");
+  } else {
+    for (int it = 0; it < n; ++it) {
+      dba_status s = launch_iteration(ctx);
+      if (s != DBA_OK) return s;
+    }
+  }
+  if (n > 0) {
+    ctx->cur ^= (n & 1);
+    ctx->pending = 1;
+    ctx->iters += n;
+  }
+  return DBA_OK;
+}
+
+dba_status check_device_flags(dba_ctx* ctx) {
+  DevCtl h{};
+  DBA_CUDA(cudaMemcpyAsync(&h, ctx->P.ctl, sizeof h, cudaMemcpyDeviceToHost, ctx->stream), "read control");
+  DBA_CUDA(cudaStreamSynchronize(ctx->stream), "iterate");
+  if (h.err & 1) return ctx->fail(DBA_ENUMERIC, "a local solve produced a non-finite value");
+  if (h.cur != ctx->cur) return ctx->fail(DBA_ECUDA, "device control word out of step with the host");
+  return DBA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dba_status dba_set_observations(dba_ctx* ctx, int32_t n_cams, int32_t n_pts, int64_t n_obs,
+                                const int32_t* pt_idx, const int32_t* cam_idx, const double* z,
+                                const double* cams0, const double* pts0) {
+  if (!ctx) return DBA_EINVAL;
+  if (n_cams <= 0 || n_pts <= 0 || n_obs <= 0)
+    return ctx->fail(DBA_EINVAL, "dba_set_observations: n_cams, n_pts and n_obs must be positive");
+  if (n_obs > (int64_t)0x7fffffff)
+    return ctx->fail(DBA_EINVAL, "dba_set_observations: at most 2^31-1 observations");
+  if (!pt_idx || !cam_idx || !z || !cams0 || !pts0)
+    return ctx->fail(DBA_EINVAL, "dba_set_observations: null array");
+  for (int64_t o = 0; o < n_obs; ++o)
+    if (pt_idx[o] < 0 || pt_idx[o] >= n_pts || cam_idx[o] < 0 || cam_idx[o] >= n_cams)
+      return ctx->fail(DBA_EINVAL, "dba_set_observations: observation " + std::to_string(o) +
+                                       " has an index out of range");
+  if (!finite_all(z, 2 * n_obs) || !finite_all(cams0, 6 * (long long)n_cams) ||
+      !finite_all(pts0, 3 * (long long)n_pts))
+    return ctx->fail(DBA_EINVAL, "dba_set_observations: non-finite input value");
+  cudaStreamSynchronize(ctx->stream);
+  ctx->free_problem();
+
+  const int NT = ctx->cfg.tile_obs ? ctx->cfg.tile_obs : (ctx->fp32 ? 256 : 128);
+  HostLayout L;
+  build_layout(n_cams, n_pts, n_obs, pt_idx, cam_idx, NT, L);
+  ctx->n_cams = n_cams;
+  ctx->n_pts = n_pts;
+  ctx->n_obs = n_obs;
+  ctx->perm = std::move(L.perm);
+  ctx->h_obs_pt = L.obs_pt;
+  ctx->h_obs_cam = L.obs_cam;
+  ctx->n_pseg = (int64_t)L.pseg.size();
+
+  DevProblem& P = ctx->P;
+  P.n_cams = n_cams;
+  P.n_pts = n_pts;
+  P.n_obs = n_obs;
+  P.n_tiles = (int)L.tile_off.size() - 1;
+  P.tile_obs = NT;
+  P.n_cam_slots = L.n_cam_slots;
+  P.n_pt_slots = L.n_pt_slots;
+  P.n_split_pts = (int)L.split_pt.size();
+  DBA_CUDA(ctx->upload(&P.obs_pt, L.obs_pt), "upload");
+  DBA_CUDA(ctx->upload(&P.obs_cam, L.obs_cam), "upload");
+  DBA_CUDA(ctx->upload(&P.cam_rank, L.cam_rank), "upload");
+  DBA_CUDA(ctx->upload(&P.tile_off, L.tile_off), "upload");
+  DBA_CUDA(ctx->upload(&P.tile_pseg_off, L.tile_pseg_off), "upload");
+  DBA_CUDA(ctx->upload(&P.pseg, L.pseg), "upload");
+  DBA_CUDA(ctx->upload(&P.pseg_pt, L.pseg_pt), "upload");
+  DBA_CUDA(ctx->upload(&P.pseg_slot, L.pseg_slot), "upload");
+  DBA_CUDA(ctx->upload(&P.tile_cseg_off, L.tile_cseg_off), "upload");
+  DBA_CUDA(ctx->upload(&P.cseg, L.cseg), "upload");
+  DBA_CUDA(ctx->upload(&P.cseg_slot, L.cseg_slot), "upload");
+  DBA_CUDA(ctx->upload(&P.cam_slot_off, L.cam_slot_off), "upload");
+  DBA_CUDA(ctx->upload(&P.cam_count, L.cam_count), "upload");
+  DBA_CUDA(ctx->upload(&P.split_pt, L.split_pt), "upload");
+  DBA_CUDA(ctx->upload(&P.split_slot_off, L.split_slot_off), "upload");
+  DBA_CUDA(ctx->upload(&P.pt_count, L.pt_count), "upload");
+  // observations in internal order
+  if (ctx->fp32) {
+    std::vector<float2> hz(n_obs);
+    for (int64_t o = 0; o < n_obs; ++o)
+      hz[o] = make_float2((float)z[2 * ctx->perm[o]], (float)z[2 * ctx->perm[o] + 1]);
+    const float2* dz = nullptr;
+    DBA_CUDA(ctx->upload(&dz, hz), "upload observations");
+    P.z = dz;
+  } else {
+    std::vector<double2> hz(n_obs);
+    for (int64_t o = 0; o < n_obs; ++o) hz[o] = make_double2(z[2 * ctx->perm[o]], z[2 * ctx->perm[o] + 1]);
+    const double2* dz = nullptr;
+    DBA_CUDA(ctx->upload(&dz, hz), "upload observations");
+    P.z = dz;
+  }
+  const size_t esz = ctx->fp32 ? sizeof(float) : sizeof(double);
+  char* p = nullptr;
+  DBA_CUDA(ctx->alloc(&p, 9 * (size_t)n_obs * esz), "alloc copies");
+  P.delta = p;
+  DBA_CUDA(ctx->alloc(&P.adual, 9 * (size_t)n_obs), "alloc duals");
+  for (int b = 0; b < 2; ++b) {
+    DBA_CUDA(ctx->alloc(&P.X[b], 3 * (size_t)n_pts), "alloc points");
+    DBA_CUDA(ctx->alloc(&P.Y[b], 6 * (size_t)n_cams), "alloc cameras");
+  }
+  DBA_CUDA(ctx->alloc(&p, 3 * (size_t)n_pts * esz), "alloc");
+  P.Xm = p;
+  DBA_CUDA(ctx->alloc(&p, 3 * (size_t)n_pts * esz), "alloc");
+  P.DX = p;
+  DBA_CUDA(ctx->alloc(&p, 6 * (size_t)n_cams * esz), "alloc");
+  P.Ym = p;
+  DBA_CUDA(ctx->alloc(&p, 6 * (size_t)n_cams * esz), "alloc");
+  P.DY = p;
+  DBA_CUDA(ctx->alloc(&P.pt_part, 3 * (size_t)std::max(1, P.n_pt_slots)), "alloc partials");
+  DBA_CUDA(ctx->alloc(&P.cam_part, 6 * (size_t)std::max(1, P.n_cam_slots)), "alloc partials");
+  DBA_CUDA(ctx->alloc(&P.metric_part, 8 * (size_t)dba::kMetricBlocks), "alloc metrics");
+  DBA_CUDA(ctx->alloc(&P.metric_out, 8), "alloc metrics");
+  DBA_CUDA(ctx->alloc(&P.ctl, 1), "alloc control");
+  ctx->has_problem = true;
+  dba_status s = upload_state(ctx, cams0, pts0, nullptr, nullptr);
+  if (s != DBA_OK) {
+    ctx->free_problem();
+    return s;
+  }
+  return DBA_OK;
+}
+
+dba_status dba_set_ground_truth(dba_ctx* ctx, const double* cams_gt, const double* pts_gt,
+                                const uint8_t* inlier) {
+  if (!ctx) return DBA_EINVAL;
+  if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_set_ground_truth before dba_set_observations");
+  if (!cams_gt || !pts_gt) return ctx->fail(DBA_EINVAL, "dba_set_ground_truth: null array");
+  if (!finite_all(cams_gt, 6 * (long long)ctx->n_cams) || !finite_all(pts_gt, 3 * (long long)ctx->n_pts))
+    return ctx->fail(DBA_EINVAL, "dba_set_ground_truth: non-finite value");
+  double *dc = nullptr, *dp = nullptr;
+  cudaStream_t st = ctx->stream;
+  DBA_CUDA(cudaMallocAsync(&dc, 6 * (size_t)ctx->n_cams * sizeof(double), st), "alloc");
+  DBA_CUDA(cudaMallocAsync(&dp, 3 * (size_t)ctx->n_pts * sizeof(double), st), "alloc");
+  DBA_CUDA(cudaMemcpyAsync(dc, cams_gt, 6 * (size_t)ctx->n_cams * sizeof(double), cudaMemcpyHostToDevice, st), "upload");
+  DBA_CUDA(cudaMemcpyAsync(dp, pts_gt, 3 * (size_t)ctx->n_pts * sizeof(double), cudaMemcpyHostToDevice, st), "upload");
+  void* zt = const_cast<void*>(ctx->P.zt);
+  if (!zt) {
+    char* p = nullptr;
+    DBA_CUDA(ctx->alloc(&p, (size_t)ctx->n_obs * (ctx->fp32 ? sizeof(float2) : sizeof(double2))), "alloc");
+    zt = p;
+  }
+  DBA_CUDA(dba::launch_project_truth(ctx->P, ctx->prm, ctx->fp32, dc, dp, zt, st), "project truth");
+  if (inlier) {
+    std::vector<unsigned char> h(ctx->n_obs);
+    for (long long o = 0; o < ctx->n_obs; ++o) h[o] = inlier[ctx->perm[o]] ? 1 : 0;
+    if (!ctx->P.inlier) {
+      DBA_CUDA(ctx->upload(&ctx->P.inlier, h), "upload inlier mask");
+    } else {
+      DBA_CUDA(cudaMemcpyAsync(const_cast<unsigned char*>(ctx->P.inlier), h.data(), h.size(),
+                               cudaMemcpyHostToDevice, st), "upload inlier mask");
+    }
+    DBA_CUDA(cudaStreamSynchronize(st), "upload inlier mask");
+  } else {
+    ctx->P.inlier = nullptr;
+  }
+  DBA_CUDA(cudaFreeAsync(dc, st), "free");
+  DBA_CUDA(cudaFreeAsync(dp, st), "free");
+  DBA_CUDA(cudaStreamSynchronize(st), "ground truth");
+  ctx->P.zt = zt;
+  ctx->has_gt = true;
+  if (ctx->graph) {  // kernel arguments changed
+    cudaGraphExecDestroy(ctx->graph);
+    ctx->graph = nullptr;
+  }
+  return DBA_OK;
+}
+
+dba_status dba_iterate(dba_ctx* ctx, int n_iters, dba_stats* stats) {
+  if (!ctx) return DBA_EINVAL;
+  if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_iterate before dba_set_observations");
+  if (n_iters < 0) return ctx->fail(DBA_EINVAL, "dba_iterate: n_iters < 0");
+  DBA_CUDA(cudaEventRecord(ctx->ev0, ctx->stream), "event");
+  dba_status s = run_iterations(ctx, n_iters);
+  if (s != DBA_OK) return s;
+  DBA_CUDA(cudaEventRecord(ctx->ev1, ctx->stream), "event");
+  s = check_device_flags(ctx);
+  if (s != DBA_OK) return s;
+  float ms = 0.f;
+  DBA_CUDA(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1), "event");
+  if (stats) return read_metrics(ctx, stats, ms * 1e-3);
+  return DBA_OK;
+}
+
+dba_status dba_iterate_until(dba_ctx* ctx, int max_iters, double target_rmse_gt, dba_stats* stats) {
+  if (!ctx) return DBA_EINVAL;
+  if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_iterate_until before dba_set_observations");
+  if (!ctx->has_gt) return ctx->fail(DBA_ESTATE, "dba_iterate_until needs dba_set_ground_truth");
+  if (max_iters < 0) return ctx->fail(DBA_EINVAL, "dba_iterate_until: max_iters < 0");
+  dba_stats st{};
+  double seconds = 0.0;
+  for (int it = 0; it < max_iters; ++it) {
+    DBA_CUDA(cudaEventRecord(ctx->ev0, ctx->stream), "event");
+    dba_status s = run_iterations(ctx, 1);
+    if (s != DBA_OK) return s;
+    DBA_CUDA(dba::launch_metrics(ctx->P, ctx->prm, ctx->fp32, ctx->cur, ctx->pending, ctx->stream), "metrics");
+    DBA_CUDA(cudaEventRecord(ctx->ev1, ctx->stream), "event");
+    s = check_device_flags(ctx);
+    if (s != DBA_OK) return s;
+    float ms = 0.f;
+    DBA_CUDA(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1), "event");
+    seconds += ms * 1e-3;
+    s = read_metrics(ctx, &st, seconds);
+    if (s != DBA_OK) return s;
+    if (st.rmse_gt <= target_rmse_gt) break;
+  }
+  if (max_iters == 0) {
+    dba_status s = read_metrics(ctx, &st, 0.0);
+    if (s != DBA_OK) return s;
+  }
+  if (stats) *stats = st;
+  return DBA_OK;
+}
+
+dba_status dba_evaluate(dba_ctx* ctx, dba_stats* stats) {
+  if (!ctx || !stats) return DBA_EINVAL;
+  if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_evaluate before dba_set_observations");
+  return read_metrics(ctx, stats, 0.0);
+}
+
+dba_status dba_get_params(dba_ctx* ctx, double* cams, double* pts) {
+  if (!ctx) return DBA_EINVAL;
+  if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_get_params before dba_set_observations");
+  cudaStream_t st = ctx->stream;
+  if (cams)
+    DBA_CUDA(cudaMemcpyAsync(cams, ctx->P.Y[ctx->cur], 6 * (size_t)ctx->n_cams * sizeof(double),
+                             cudaMemcpyDeviceToHost, st), "read cameras");
+  if (pts)
+    DBA_CUDA(cudaMemcpyAsync(pts, ctx->P.X[ctx->cur], 3 * (size_t)ctx->n_pts * sizeof(double),
+                             cudaMemcpyDeviceToHost, st), "read points");
+  DBA_CUDA(cudaStreamSynchronize(st), "get_params");
+  return DBA_OK;
+}
+
+dba_status dba_get_state(dba_ctx* ctx, double* copies, double* duals) {
+  if (!ctx) return DBA_EINVAL;
+  if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_get_state before dba_set_observations");
+  cudaStream_t st = ctx->stream;
+  if (ctx->pending) {
+    DBA_CUDA(dba::launch_settle(ctx->P, ctx->fp32, ctx->cur, st), "settle");
+    const int zero = 0;
+    DBA_CUDA(cudaMemcpyAsync(&ctx->P.ctl->pending, &zero, sizeof zero, cudaMemcpyHostToDevice, st), "settle");
+    DBA_CUDA(cudaStreamSynchronize(st), "settle");
+    ctx->pending = 0;
+  }
+  const long long l = ctx->n_obs;
+  const int m = ctx->n_cams, n = ctx->n_pts;
+  std::vector<double> X(3 * (size_t)n), Y(6 * (size_t)m), del(9 * (size_t)l), a(9 * (size_t)l);
+  DBA_CUDA(cudaMemcpyAsync(X.data(), ctx->P.X[ctx->cur], X.size() * sizeof(double), cudaMemcpyDeviceToHost, st), "read");
+  DBA_CUDA(cudaMemcpyAsync(Y.data(), ctx->P.Y[ctx->cur], Y.size() * sizeof(double), cudaMemcpyDeviceToHost, st), "read");
+  DBA_CUDA(cudaMemcpyAsync(a.data(), ctx->P.adual, a.size() * sizeof(double), cudaMemcpyDeviceToHost, st), "read");
+  if (ctx->fp32) {
+    std::vector<float> f(9 * (size_t)l);
+    DBA_CUDA(cudaMemcpyAsync(f.data(), ctx->P.delta, f.size() * sizeof(float), cudaMemcpyDeviceToHost, st), "read");
+    DBA_CUDA(cudaStreamSynchronize(st), "get_state");
+    for (size_t k = 0; k < f.size(); ++k) del[k] = f[k];
+  } else {
+    DBA_CUDA(cudaMemcpyAsync(del.data(), ctx->P.delta, del.size() * sizeof(double), cudaMemcpyDeviceToHost, st), "read");
+    DBA_CUDA(cudaStreamSynchronize(st), "get_state");
+  }
+  for (long long o = 0; o < l; ++o) {
+    const long long dst = ctx->perm[o];
+    const size_t i = ctx->h_obs_pt[o], j = ctx->h_obs_cam[o];
+    for (int c = 0; c < 9; ++c) {
+      if (copies) copies[9 * dst + c] = (c < 3 ? X[3 * i + c] : Y[6 * j + c - 3]) + del[c * (size_t)l + o];
+      if (duals) duals[9 * dst + c] = (c < 3 ? ctx->prm.rho_x : ctx->prm.rho_y) * a[c * (size_t)l + o];
+    }
+  }
+  return DBA_OK;
+}
+
+dba_status dba_set_state(dba_ctx* ctx, const double* copies, const double* duals, const double* cams,
+                         const double* pts) {
+  if (!ctx) return DBA_EINVAL;
+  if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_set_state before dba_set_observations");
+  if (!copies || !duals || !cams || !pts) return ctx->fail(DBA_EINVAL, "dba_set_state: null array");
+  if (!finite_all(copies, 9 * ctx->n_obs) || !finite_all(duals, 9 * ctx->n_obs) ||
+      !finite_all(cams, 6 * (long long)ctx->n_cams) || !finite_all(pts, 3 * (long long)ctx->n_pts))
+    return ctx->fail(DBA_EINVAL, "dba_set_state: non-finite value");
+  return upload_state(ctx, cams, pts, copies, duals);
+}
+
+dba_status dba_profile(dba_ctx* ctx, int n_iters, const char** names, double* ms, int* count) {
+  if (!ctx || !count) return DBA_EINVAL;
+  if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_profile before dba_set_observations");
+  if (n_iters <= 0 || *count < 2 || !names || !ms) return ctx->fail(DBA_EINVAL, "dba_profile: bad arguments");
+  std::vector<cudaEvent_t> ev(3 * (size_t)n_iters);
+  for (auto& e : ev) DBA_CUDA(cudaEventCreate(&e), "event");
+  cudaStream_t st = ctx->stream;
+  for (int it = 0; it < n_iters; ++it) {
+    DBA_CUDA(cudaEventRecord(ev[3 * it], st), "event");
+    DBA_CUDA(dba::launch_tile_iterate(ctx->P, ctx->prm, ctx->fp32, st), "tile_iterate");
+    DBA_CUDA(cudaEventRecord(ev[3 * it + 1], st), "event");
+    DBA_CUDA(dba::launch_finalize(ctx->P, ctx->fp32, st), "finalize");
+    DBA_CUDA(cudaEventRecord(ev[3 * it + 2], st), "event");
+  }
+  ctx->cur ^= (n_iters & 1);
+  ctx->pending = 1;
+  ctx->iters += n_iters;
+  dba_status s = check_device_flags(ctx);
+  double t0 = 0, t1 = 0;
+  for (int it = 0; it < n_iters && s == DBA_OK; ++it) {
+    float a = 0, b = 0;
+    cudaEventElapsedTime(&a, ev[3 * it], ev[3 * it + 1]);
+    cudaEventElapsedTime(&b, ev[3 * it + 1], ev[3 * it + 2]);
+    t0 += a;
+    t1 += b;
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  if (s != DBA_OK) return s;
+  names[0] = "tile_iterate";
+  ms[0] = t0 / n_iters;
+  names[1] = "finalize";
+  ms[1] = t1 / n_iters;
+  *count = 2;
+  return DBA_OK;
+}
+
+dba_status dba_layout(dba_ctx* ctx, int64_t* out, int* count) {
+  if (!ctx || !out || !count) return DBA_EINVAL;
+  if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_layout before dba_set_observations");
+  const int64_t v[6] = {ctx->P.n_tiles, ctx->P.tile_obs, ctx->n_pseg, (int64_t)ctx->P.n_cam_slots,
+                        (int64_t)ctx->P.n_split_pts, (int64_t)ctx->P.n_pt_slots};
+  const int n = std::min(*count, 6);
+  for (int k = 0; k < n; ++k) out[k] = v[k];
+  *count = n;
+  return DBA_OK;
+}
+
+}  // extern "C"

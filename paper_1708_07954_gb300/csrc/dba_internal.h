@@ -1,0 +1,90 @@
+// Internal interface between the host C ABI (dba_api.cu) and the kernels
+// (dba_kernels.cu).  Not installed; not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dba {
+
+// Device control word read by every kernel of an iteration, so that one
+// captured CUDA graph serves every iteration: which consensus buffer is
+// current, whether the previous iteration's dual ascent (Eqs. 12-13) is still
+// to be applied, and a sticky error flag.
+struct DevCtl {
+  int cur;          // index (0/1) of the current consensus buffer
+  int pending;      // 1: copies are offsets from the previous consensus, duals lag by one step
+  int err;          // bit 0: non-finite local solve
+  int pad;
+  unsigned long long k;   // iterations run
+  unsigned int done;      // finalize-kernel block counter
+  unsigned int pad2;
+};
+
+struct Params {
+  double focal, cx, cy;
+  int loss;
+  double loss_param;
+  double rho_x, rho_y;
+  int inner_steps;
+  double lambda0, lambda_min, eps_depth;
+};
+
+// All device pointers of one problem.  Observation arrays are in internal
+// (tile) order; per-observation vectors are structure-of-arrays with stride n_obs.
+struct DevProblem {
+  int n_cams, n_pts;
+  long long n_obs;
+  int n_tiles;
+  int tile_obs;                 // block size of the tile kernel
+  int n_cam_slots, n_pt_slots, n_split_pts;
+  // static structure
+  const int* obs_pt;            // [l]
+  const int* obs_cam;           // [l]
+  const void* z;                // [l] float2 (FP32 path) or double2 (FP64 path)
+  const void* zt;               // [l] same type: ground-truth projections, or nullptr
+  const unsigned char* inlier;  // [l] 1: counted in rmse_gt (nullptr: all)
+  const unsigned char* cam_rank;// [l] position of the observation in its tile's camera order
+  const int* tile_off;          // [n_tiles+1]
+  const int* tile_pseg_off;     // [n_tiles+1]
+  const int2* pseg;             // (start, length) of each point run inside its tile
+  const int* pseg_pt;           // point of each run
+  const int* pseg_slot;         // -1: the whole track is in this tile; else partial slot
+  const int* tile_cseg_off;     // [n_tiles+1]
+  const int2* cseg;             // (start, length) of each camera run in the tile's camera order
+  const int* cseg_slot;         // partial slot of each camera run
+  const int* cam_slot_off;      // [m+1] camera -> its partial slots
+  const int* cam_count;         // [m] observations per camera
+  const int* split_pt;          // [n_split_pts] points whose track spans several tiles
+  const int* split_slot_off;    // [n_split_pts+1]
+  const int* pt_count;          // [n] observations per point
+  // state
+  void* delta;                  // [9][l] T: copy minus the consensus it was solved against
+  double* adual;                // [9][l] scaled duals (r/rho_x, s/rho_y)
+  double* X[2];                 // [n][3] point consensus, ping-pong
+  double* Y[2];                 // [m][6] camera consensus, ping-pong
+  void* Xm;                     // [n][3] T copy of the current point consensus
+  void* DX;                     // [n][3] T: previous minus current point consensus
+  void* Ym;                     // [m][6]
+  void* DY;                     // [m][6]
+  double* pt_part;              // [n_pt_slots][3]
+  double* cam_part;             // [n_cam_slots][6]
+  double* metric_part;          // [metric blocks][8]
+  double* metric_out;           // [8]
+  DevCtl* ctl;
+};
+
+constexpr int kMetricBlocks = 1024;
+constexpr int kMetricThreads = 256;
+
+// Kernel launchers (return the launch error).  fp32 selects the FP32 local-solve path.
+cudaError_t launch_tile_iterate(const DevProblem& P, const Params& prm, bool fp32, cudaStream_t s);
+cudaError_t launch_finalize(const DevProblem& P, bool fp32, cudaStream_t s);
+cudaError_t launch_metrics(const DevProblem& P, const Params& prm, bool fp32, int cur, int pending,
+                           cudaStream_t s);
+cudaError_t launch_settle(const DevProblem& P, bool fp32, int cur, cudaStream_t s);
+cudaError_t launch_project_truth(const DevProblem& P, const Params& prm, bool fp32,
+                                 const double* cams_gt, const double* pts_gt, void* zt_out,
+                                 cudaStream_t s);
+
+}  // namespace dba

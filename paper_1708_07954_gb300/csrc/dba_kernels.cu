@@ -1,0 +1,597 @@
+// CUDA kernels for one consensus-ADMM iteration of distributed bundle
+// adjustment (arXiv 1708.07954, Sec. 3.1, Eqs. 9-13), written for sm_103a.
+//
+// Layout: observations are sorted by point (points ordered by their first
+// camera) and cut into tiles of whole point tracks, one tile per thread block,
+// one observation per thread.  Per observation the state is
+//   delta[9]  (T)      copy minus the consensus it was last solved against,
+//   adual[9]  (double) scaled duals a = (r / rho_x, s / rho_y),
+// and per point / camera the FP64 consensus (ping-pong buffers) plus a T
+// mirror of it and of its last change.  T = float on the reduced-precision
+// path, double on the FP64 path; consensus sums and dual ascent are FP64.
+//
+//  tile_iterate  Eq. (12)-(13) of the previous iteration (dual ascent, deferred
+//                until the new consensus exists), Eq. (9) for every
+//                observation, Eq. (10) for every point whose whole track is in
+//                the tile, and per-tile partial sums for Eq. (11).
+//  finalize      Eq. (11) from the partial sums; Eq. (10) for tracks that
+//                span several tiles.
+//  metrics       reprojection RMSE, objective and residuals at consensus.
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include "dba_internal.h"
+
+namespace dba {
+namespace {
+
+// ------------------------------------------------------------ scalar helpers
+template <typename T> struct Num;
+template <> struct Num<float> {
+  using V2 = float2;
+  static __device__ __forceinline__ void sc(float x, float* s, float* c) { sincosf(x, s, c); }
+  static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+  static __device__ __forceinline__ float log1p_(float x) { return log1pf(x); }
+  static __device__ __forceinline__ float inf() { return CUDART_INF_F; }
+};
+template <> struct Num<double> {
+  using V2 = double2;
+  static __device__ __forceinline__ void sc(double x, double* s, double* c) { sincos(x, s, c); }
+  static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+  static __device__ __forceinline__ double log1p_(double x) { return log1p(x); }
+  static __device__ __forceinline__ double inf() { return CUDART_INF; }
+};
+
+template <typename T>
+struct Prm {
+  T focal, cx, cy, lp, rho_x, rho_y, lambda0, lambda_min, eps;
+  int loss, steps;
+};
+
+template <typename T>
+__host__ __device__ Prm<T> make_prm(const Params& p) {
+  Prm<T> q;
+  q.focal = (T)p.focal; q.cx = (T)p.cx; q.cy = (T)p.cy; q.lp = (T)p.loss_param;
+  q.rho_x = (T)p.rho_x; q.rho_y = (T)p.rho_y; q.lambda0 = (T)p.lambda0;
+  q.lambda_min = (T)p.lambda_min; q.eps = (T)p.eps_depth;
+  q.loss = p.loss; q.steps = p.inner_steps;
+  return q;
+}
+
+// Misfit phi_m as a function of s = |e|^2 and its derivative (IRLS weight).
+template <typename T>
+__device__ __forceinline__ T misfit(int loss, T p, T s) {
+  if (loss == 1) return s <= p * p ? s : T(2) * p * Num<T>::sqrt_(s) - p * p;
+  if (loss == 2) return p * Num<T>::log1p_(s / p);
+  return s;
+}
+template <typename T>
+__device__ __forceinline__ T misfit_weight(int loss, T p, T s) {
+  if (loss == 1) return s <= p * p ? T(1) : p / Num<T>::sqrt_(s);
+  if (loss == 2) return p / (p + s);
+  return T(1);
+}
+
+// Camera pose evaluated at v = (x, alpha, beta, gamma, t): R = Rz Ry Rx
+// (Sec. 2.1), u = R x and p = u + t (camera frame).
+template <typename T>
+struct Pose {
+  T R[9];
+  T u[3];
+  T p[3];
+  T sg, cg;
+  bool valid;
+};
+
+template <typename T>
+__device__ __forceinline__ void pose_at(const T v[9], T eps, Pose<T>& P) {
+  T sa, ca, sb, cb;
+  Num<T>::sc(v[3], &sa, &ca);
+  Num<T>::sc(v[4], &sb, &cb);
+  Num<T>::sc(v[5], &P.sg, &P.cg);
+  const T sg = P.sg, cg = P.cg;
+  P.R[0] = cg * cb;
+  P.R[1] = cg * sb * sa - sg * ca;
+  P.R[2] = cg * sb * ca + sg * sa;
+  P.R[3] = sg * cb;
+  P.R[4] = sg * sb * sa + cg * ca;
+  P.R[5] = sg * sb * ca - cg * sa;
+  P.R[6] = -sb;
+  P.R[7] = cb * sa;
+  P.R[8] = cb * ca;
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    P.u[r] = P.R[3 * r] * v[0] + P.R[3 * r + 1] * v[1] + P.R[3 * r + 2] * v[2];
+    P.p[r] = P.u[r] + v[6 + r];
+  }
+  P.valid = P.p[2] > eps;
+}
+
+// Eq. (9) in offset form: with d = v - vbar and a = dual / rho,
+// r^T d + rho/2 |d|^2 = rho (a.d + d.d/2).  +inf behind the camera.
+template <typename T>
+__device__ __forceinline__ T local_objective(const T d[9], const T a[9], const Pose<T>& P,
+                                             T z0, T z1, const Prm<T>& q) {
+  if (!P.valid) return Num<T>::inf();
+  const T iz = T(1) / P.p[2];
+  const T e0 = z0 - (q.focal * P.p[0] * iz + q.cx);
+  const T e1 = z1 - (q.focal * P.p[1] * iz + q.cy);
+  T px = 0, py = 0;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) px += d[c] * (a[c] + T(0.5) * d[c]);
+#pragma unroll
+  for (int c = 3; c < 9; ++c) py += d[c] * (a[c] + T(0.5) * d[c]);
+  return misfit<T>(q.loss, q.lp, e0 * e0 + e1 * e1) + q.rho_x * px + q.rho_y * py;
+}
+
+// Eq. (9): inner_steps damped Gauss-Newton steps with IRLS weights.  The
+// damped normal matrix 2w J^T J + diag(rho) + lambda I is diagonal plus rank
+// 2 (one observation has two residuals), so each step solves it exactly
+// through its 2x2 capacitance matrix (Sherman-Morrison-Woodbury) instead of a
+// 9x9 factorisation.  Accept/reject and the damping schedule follow the
+// Levenberg rule: accept iff the trial is in front of the camera and lowers
+// Eq. (9).  d (offset from vbar) is updated in place.
+template <typename T>
+__device__ __forceinline__ void local_solve(T z0, T z1, const T vbar[9], const T a[9], T d[9],
+                                            const Prm<T>& q) {
+  T v[9];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) v[c] = vbar[c] + d[c];
+  Pose<T> P;
+  pose_at(v, q.eps, P);
+  T L = local_objective(d, a, P, z0, z1, q);
+  T lambda = T(-1);
+  for (int step = 0; step < q.steps; ++step) {
+    T J0[9], J1[9];
+    T w = 0, e0 = 0, e1 = 0;
+    if (P.valid) {
+      const T iz = T(1) / P.p[2];
+      const T zx = P.p[0] * iz, zy = P.p[1] * iz;
+      e0 = z0 - (q.focal * zx + q.cx);
+      e1 = z1 - (q.focal * zy + q.cy);
+      w = misfit_weight<T>(q.loss, q.lp, e0 * e0 + e1 * e1);
+      const T fi = q.focal * iz;
+      // d p / d v columns: x_k -> R[:,k]; alpha -> R[:,0] x u; beta -> (-sg, cg, 0) x u;
+      // gamma -> e_z x u; t_k -> e_k.   Row r of J: fi * (dp_r - z_r dp_2).
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        J0[k] = fi * (P.R[k] - zx * P.R[6 + k]);
+        J1[k] = fi * (P.R[3 + k] - zy * P.R[6 + k]);
+      }
+      {
+        const T c0 = P.R[0], c1 = P.R[3], c2 = P.R[6];
+        const T d0 = c1 * P.u[2] - c2 * P.u[1];
+        const T d1 = c2 * P.u[0] - c0 * P.u[2];
+        const T d2 = c0 * P.u[1] - c1 * P.u[0];
+        J0[3] = fi * (d0 - zx * d2);
+        J1[3] = fi * (d1 - zy * d2);
+      }
+      {
+        const T b0 = -P.sg, b1 = P.cg;
+        const T d0 = b1 * P.u[2];
+        const T d1 = -b0 * P.u[2];
+        const T d2 = b0 * P.u[1] - b1 * P.u[0];
+        J0[4] = fi * (d0 - zx * d2);
+        J1[4] = fi * (d1 - zy * d2);
+      }
+      J0[5] = fi * (-P.u[1]);
+      J1[5] = fi * (P.u[0]);
+      J0[6] = fi;
+      J1[6] = 0;
+      J0[7] = 0;
+      J1[7] = fi;
+      J0[8] = -fi * zx;
+      J1[8] = -fi * zy;
+    } else {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) J0[k] = J1[k] = 0;
+    }
+    const T tw = T(2) * w;
+    T g[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      const T rho = c < 3 ? q.rho_x : q.rho_y;
+      g[c] = -tw * (J0[c] * e0 + J1[c] * e1) + rho * (a[c] + d[c]);
+    }
+    if (lambda < T(0)) {
+      T tr = T(3) * q.rho_x + T(6) * q.rho_y;
+#pragma unroll
+      for (int c = 0; c < 9; ++c) tr += tw * (J0[c] * J0[c] + J1[c] * J1[c]);
+      lambda = q.lambda0 * tr / T(9);
+    }
+    const T iDx = T(1) / (q.rho_x + lambda), iDy = T(1) / (q.rho_y + lambda);
+    T G00 = 0, G01 = 0, G11 = 0, t0 = 0, t1 = 0;
+    T qv[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      const T iD = c < 3 ? iDx : iDy;
+      qv[c] = g[c] * iD;
+      G00 += J0[c] * J0[c] * iD;
+      G01 += J0[c] * J1[c] * iD;
+      G11 += J1[c] * J1[c] * iD;
+      t0 += J0[c] * qv[c];
+      t1 += J1[c] * qv[c];
+    }
+    const T S00 = T(1) + tw * G00, S01 = tw * G01, S11 = T(1) + tw * G11;
+    const T idet = T(1) / (S00 * S11 - S01 * S01);
+    const T y0 = (S11 * t0 - S01 * t1) * idet;
+    const T y1 = (S00 * t1 - S01 * t0) * idet;
+    T dt[9], vt[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      const T iD = c < 3 ? iDx : iDy;
+      dt[c] = d[c] + (-qv[c] + tw * iD * (J0[c] * y0 + J1[c] * y1));
+      vt[c] = vbar[c] + dt[c];
+    }
+    Pose<T> Pt;
+    pose_at(vt, q.eps, Pt);
+    const T Lt = local_objective(dt, a, Pt, z0, z1, q);
+    if (Lt < L) {
+#pragma unroll
+      for (int c = 0; c < 9; ++c) d[c] = dt[c];
+      P = Pt;
+      L = Lt;
+      lambda = fmax(lambda / T(10), q.lambda_min);
+    } else {
+      lambda *= T(10);
+    }
+  }
+}
+
+// ------------------------------------------------------------ tile kernel
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT) tile_iterate_kernel(DevProblem P, Prm<T> q) {
+  using V2 = typename Num<T>::V2;
+  __shared__ double s_pt[3][NT];
+  __shared__ double s_cm[6][NT];
+  const int tile = blockIdx.x;
+  const int t = threadIdx.x;
+  const long long l = P.n_obs;
+  const int o0 = P.tile_off[tile], o1 = P.tile_off[tile + 1];
+  const int o = o0 + t;
+  const volatile DevCtl* ctl = P.ctl;
+  const int cur = ctl->cur;
+  const int pending = ctl->pending;
+  T* delta = static_cast<T*>(P.delta);
+  const T* Xm = static_cast<const T*>(P.Xm);
+  const T* Ym = static_cast<const T*>(P.Ym);
+  const T* DX = static_cast<const T*>(P.DX);
+  const T* DY = static_cast<const T*>(P.DY);
+
+  if (o < o1) {
+    const int i = P.obs_pt[o], j = P.obs_cam[o];
+    const V2 zz = static_cast<const V2*>(P.z)[o];
+    T d[9], vbar[9], aT[9];
+    double a[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      d[c] = delta[c * l + o];
+      a[c] = P.adual[c * l + o];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) vbar[c] = Xm[3 * i + c];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) vbar[3 + c] = Ym[6 * j + c];
+    if (pending) {
+      // Eqs. (12)-(13) of the previous iteration: the copy relative to the new
+      // consensus is d0 = delta + (old - new consensus); a += d0.
+#pragma unroll
+      for (int c = 0; c < 3; ++c) d[c] += DX[3 * i + c];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) d[3 + c] += DY[6 * j + c];
+#pragma unroll
+      for (int c = 0; c < 9; ++c) {
+        a[c] += (double)d[c];
+        P.adual[c * l + o] = a[c];
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 9; ++c) aT[c] = (T)a[c];
+    local_solve<T>(zz.x, zz.y, vbar, aT, d, q);
+    bool finite = true;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      delta[c * l + o] = d[c];
+      finite = finite && isfinite(d[c]);
+    }
+    if (!finite) atomicOr(&P.ctl->err, 1);
+    // Eqs. (10)-(11) summands relative to the current consensus: copy + dual / rho - consensus.
+#pragma unroll
+    for (int c = 0; c < 3; ++c) s_pt[c][t] = (double)d[c] + a[c];
+    const int rk = P.cam_rank[o];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) s_cm[c][rk] = (double)d[3 + c] + a[3 + c];
+  }
+  __syncthreads();
+
+  // Eq. (10): per point run, one thread per (run, coordinate), FP64 sums.
+  const int nxt = cur ^ 1;
+  {
+    const int r0 = P.tile_pseg_off[tile], nr = P.tile_pseg_off[tile + 1] - r0;
+    for (int task = t; task < 3 * nr; task += NT) {
+      const int r = r0 + task / 3, c = task % 3;
+      const int2 se = P.pseg[r];
+      double acc = 0.0;
+      for (int e = se.x; e < se.x + se.y; ++e) acc += s_pt[c][e];
+      const int slot = P.pseg_slot[r];
+      if (slot < 0) {
+        const int pt = P.pseg_pt[r];
+        const double xo = P.X[cur][3 * pt + c];
+        const double xn = xo + acc / (double)se.y;
+        P.X[nxt][3 * pt + c] = xn;
+        static_cast<T*>(P.Xm)[3 * pt + c] = (T)xn;
+        static_cast<T*>(P.DX)[3 * pt + c] = (T)(xo - xn);
+      } else {
+        P.pt_part[3 * slot + c] = acc;
+      }
+    }
+  }
+  // Eq. (11): per camera run, partial sums for the finalize kernel.
+  {
+    const int r0 = P.tile_cseg_off[tile], nr = P.tile_cseg_off[tile + 1] - r0;
+    for (int task = t; task < 6 * nr; task += NT) {
+      const int r = r0 + task / 6, c = task % 6;
+      const int2 se = P.cseg[r];
+      double acc = 0.0;
+      for (int e = se.x; e < se.x + se.y; ++e) acc += s_cm[c][e];
+      P.cam_part[6 * P.cseg_slot[r] + c] = acc;
+    }
+  }
+}
+
+// ------------------------------------------------------------ finalize
+constexpr int kFinThreads = 128;
+
+template <typename T>
+__global__ void __launch_bounds__(kFinThreads) finalize_kernel(DevProblem P) {
+  __shared__ double red[6][kFinThreads];
+  const volatile DevCtl* ctl = P.ctl;
+  const int cur = ctl->cur, nxt = cur ^ 1;
+  const int b = blockIdx.x, t = threadIdx.x;
+  const bool is_cam = b < P.n_cams;
+  const int nc = is_cam ? 6 : 3;
+  int s0, s1, cnt, id;
+  if (is_cam) {
+    id = b;
+    s0 = P.cam_slot_off[b];
+    s1 = P.cam_slot_off[b + 1];
+    cnt = P.cam_count[b];
+  } else {
+    const int sp = b - P.n_cams;
+    id = P.split_pt[sp];
+    s0 = P.split_slot_off[sp];
+    s1 = P.split_slot_off[sp + 1];
+    cnt = P.pt_count[id];
+  }
+  const double* part = is_cam ? P.cam_part : P.pt_part;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (int s = s0 + t; s < s1; s += kFinThreads)
+    for (int c = 0; c < nc; ++c) acc[c] += part[nc * s + c];
+  for (int c = 0; c < 6; ++c) red[c][t] = acc[c];
+  __syncthreads();
+  for (int w = kFinThreads / 2; w > 0; w >>= 1) {
+    if (t < w)
+      for (int c = 0; c < 6; ++c) red[c][t] += red[c][t + w];
+    __syncthreads();
+  }
+  if (t < nc && cnt > 0) {
+    double* C = is_cam ? P.Y[cur] : P.X[cur];
+    double* Cn = is_cam ? P.Y[nxt] : P.X[nxt];
+    T* Cm = static_cast<T*>(is_cam ? P.Ym : P.Xm);
+    T* DC = static_cast<T*>(is_cam ? P.DY : P.DX);
+    const double co = C[nc * id + t];
+    const double cn = co + red[t][0] / (double)cnt;
+    Cn[nc * id + t] = cn;
+    Cm[nc * id + t] = (T)cn;
+    DC[nc * id + t] = (T)(co - cn);
+  }
+  // The last block to finish advances the control word for the next iteration.
+  if (t == 0) {
+    __threadfence();
+    const unsigned int prev = atomicAdd(&P.ctl->done, 1u);
+    if (prev == gridDim.x - 1) {
+      P.ctl->cur = nxt;
+      P.ctl->pending = 1;
+      P.ctl->k += 1;
+      P.ctl->done = 0;
+      __threadfence();
+    }
+  }
+}
+
+// ------------------------------------------------------------ metrics
+template <typename T>
+__global__ void __launch_bounds__(kMetricThreads) metrics_kernel(DevProblem P, Prm<T> q, int pending) {
+  using V2 = typename Num<T>::V2;
+  __shared__ double red[8][kMetricThreads];
+  const long long l = P.n_obs;
+  const T* Xm = static_cast<const T*>(P.Xm);
+  const T* Ym = static_cast<const T*>(P.Ym);
+  const T* DX = static_cast<const T*>(P.DX);
+  const T* DY = static_cast<const T*>(P.DY);
+  const T* delta = static_cast<const T*>(P.delta);
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (long long o = blockIdx.x * (long long)kMetricThreads + threadIdx.x; o < l;
+       o += (long long)gridDim.x * kMetricThreads) {
+    const int i = P.obs_pt[o], j = P.obs_cam[o];
+    T v[9];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) v[c] = Xm[3 * i + c];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) v[3 + c] = Ym[6 * j + c];
+    Pose<T> Q;
+    pose_at(v, q.eps, Q);
+    if (Q.valid) {
+      const V2 zz = static_cast<const V2*>(P.z)[o];
+      const T iz = T(1) / Q.p[2];
+      const T zp0 = q.focal * Q.p[0] * iz + q.cx, zp1 = q.focal * Q.p[1] * iz + q.cy;
+      const T e0 = zz.x - zp0, e1 = zz.y - zp1;
+      const T s = e0 * e0 + e1 * e1;
+      acc[0] += (double)s;
+      acc[1] += (double)misfit<T>(q.loss, q.lp, s);
+      if (P.zt && (!P.inlier || P.inlier[o])) {
+        const V2 gt = static_cast<const V2*>(P.zt)[o];
+        const T g0 = zp0 - gt.x, g1 = zp1 - gt.y;
+        acc[2] += (double)(g0 * g0 + g1 * g1);
+        acc[7] += 1.0;
+      }
+      acc[3] += 1.0;
+    } else {
+      acc[4] += 1.0;
+    }
+    T pr = 0, dr = 0;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      const T dc = c < 3 ? DX[3 * i + c] : DY[6 * j + c - 3];
+      const T cp = delta[c * l + o] + (pending ? dc : T(0));
+      const T rho = c < 3 ? q.rho_x : q.rho_y;
+      pr += cp * cp;
+      dr += (rho * dc) * (rho * dc);
+    }
+    acc[5] += (double)pr;
+    acc[6] += (double)dr;
+  }
+  for (int k = 0; k < 8; ++k) red[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int w = kMetricThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int k = 0; k < 8; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < 8) P.metric_part[8 * blockIdx.x + threadIdx.x] = red[threadIdx.x][0];
+}
+
+__global__ void __launch_bounds__(kMetricThreads) metrics_final_kernel(DevProblem P, int nblocks) {
+  __shared__ double red[8][kMetricThreads];
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int b = threadIdx.x; b < nblocks; b += kMetricThreads)
+    for (int k = 0; k < 8; ++k) acc[k] += P.metric_part[8 * b + k];
+  for (int k = 0; k < 8; ++k) red[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int w = kMetricThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int k = 0; k < 8; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < 8) P.metric_out[threadIdx.x] = red[threadIdx.x][0];
+}
+
+// ------------------------------------------------------------ settle
+// Applies a deferred dual ascent and rebases the copies onto the current
+// consensus, so the stored state is the paper's (copy, dual) after Eq. (13).
+template <typename T>
+__global__ void settle_kernel(DevProblem P) {
+  const long long l = P.n_obs;
+  T* delta = static_cast<T*>(P.delta);
+  const T* DX = static_cast<const T*>(P.DX);
+  const T* DY = static_cast<const T*>(P.DY);
+  for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < l;
+       o += (long long)gridDim.x * blockDim.x) {
+    const int i = P.obs_pt[o], j = P.obs_cam[o];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      const T d = delta[c * l + o] + (c < 3 ? DX[3 * i + c] : DY[6 * j + c - 3]);
+      delta[c * l + o] = d;
+      P.adual[c * l + o] += (double)d;
+    }
+  }
+}
+
+// ------------------------------------------------------------ ground truth
+template <typename T>
+__global__ void project_truth_kernel(DevProblem P, Prm<double> q, const double* cams,
+                                     const double* pts, typename Num<T>::V2* out) {
+  const long long l = P.n_obs;
+  for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < l;
+       o += (long long)gridDim.x * blockDim.x) {
+    const int i = P.obs_pt[o], j = P.obs_cam[o];
+    double v[9];
+    for (int c = 0; c < 3; ++c) v[c] = pts[3 * i + c];
+    for (int c = 0; c < 6; ++c) v[3 + c] = cams[6 * j + c];
+    Pose<double> Q;
+    pose_at(v, -CUDART_INF, Q);
+    const double iz = 1.0 / Q.p[2];
+    typename Num<T>::V2 r;
+    r.x = (T)(q.focal * Q.p[0] * iz + q.cx);
+    r.y = (T)(q.focal * Q.p[1] * iz + q.cy);
+    out[o] = r;
+  }
+}
+
+int grid_for(long long n, int threads, int cap) {
+  long long g = (n + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (int)g;
+}
+
+}  // namespace
+
+cudaError_t launch_tile_iterate(const DevProblem& P, const Params& prm, bool fp32, cudaStream_t s) {
+  if (P.n_tiles == 0) return cudaSuccess;
+  if (fp32) {
+    const Prm<float> q = make_prm<float>(prm);
+    switch (P.tile_obs) {
+      case 256: tile_iterate_kernel<float, 256><<<P.n_tiles, 256, 0, s>>>(P, q); break;
+      case 128: tile_iterate_kernel<float, 128><<<P.n_tiles, 128, 0, s>>>(P, q); break;
+      case 64: tile_iterate_kernel<float, 64><<<P.n_tiles, 64, 0, s>>>(P, q); break;
+      default: return cudaErrorInvalidValue;
+    }
+  } else {
+    const Prm<double> q = make_prm<double>(prm);
+    switch (P.tile_obs) {
+      case 256: tile_iterate_kernel<double, 256><<<P.n_tiles, 256, 0, s>>>(P, q); break;
+      case 128: tile_iterate_kernel<double, 128><<<P.n_tiles, 128, 0, s>>>(P, q); break;
+      case 64: tile_iterate_kernel<double, 64><<<P.n_tiles, 64, 0, s>>>(P, q); break;
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finalize(const DevProblem& P, bool fp32, cudaStream_t s) {
+  const int blocks = P.n_cams + P.n_split_pts;
+  if (fp32)
+    finalize_kernel<float><<<blocks, kFinThreads, 0, s>>>(P);
+  else
+    finalize_kernel<double><<<blocks, kFinThreads, 0, s>>>(P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_metrics(const DevProblem& P, const Params& prm, bool fp32, int cur, int pending,
+                           cudaStream_t s) {
+  (void)cur;
+  const int g = grid_for(P.n_obs, kMetricThreads, kMetricBlocks);
+  if (fp32)
+    metrics_kernel<float><<<g, kMetricThreads, 0, s>>>(P, make_prm<float>(prm), pending);
+  else
+    metrics_kernel<double><<<g, kMetricThreads, 0, s>>>(P, make_prm<double>(prm), pending);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  metrics_final_kernel<<<1, kMetricThreads, 0, s>>>(P, g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_settle(const DevProblem& P, bool fp32, int cur, cudaStream_t s) {
+  (void)cur;
+  const int g = grid_for(P.n_obs, 256, 152 * 16);
+  if (fp32)
+    settle_kernel<float><<<g, 256, 0, s>>>(P);
+  else
+    settle_kernel<double><<<g, 256, 0, s>>>(P);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_project_truth(const DevProblem& P, const Params& prm, bool fp32,
+                                 const double* cams_gt, const double* pts_gt, void* zt_out,
+                                 cudaStream_t s) {
+  const int g = grid_for(P.n_obs, 256, 152 * 16);
+  const Prm<double> q = make_prm<double>(prm);
+  if (fp32)
+    project_truth_kernel<float><<<g, 256, 0, s>>>(P, q, cams_gt, pts_gt, static_cast<float2*>(zt_out));
+  else
+    project_truth_kernel<double><<<g, 256, 0, s>>>(P, q, cams_gt, pts_gt, static_cast<double2*>(zt_out));
+  return cudaGetLastError();
+}
+
+}  // namespace dba

@@ -1,0 +1,281 @@
+"""Thin Python binding of the C ABI in include/dba.h (argument marshalling only).
+
+Every function has the name and meaning of its C counterpart; failures raise
+DbaError carrying the status and dba_last_error().  The library is the
+in-tree ``_build/libdba.so`` compiled by ``build.build()``; nothing here falls
+back to any other implementation: if the library or a GPU is missing the
+calls fail loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+DBA_OK, DBA_EINVAL, DBA_ENOMEM, DBA_ECUDA, DBA_ESTATE, DBA_ENUMERIC, DBA_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+DBA_LOSS_L2, DBA_LOSS_HUBER, DBA_LOSS_STUDENT_T = 0, 1, 2
+DBA_PREC_F64, DBA_PREC_F32_LOCAL = 0, 1
+
+EXPORTED = [
+    "dba_config_default", "dba_create", "dba_set_observations", "dba_set_ground_truth", "dba_iterate",
+    "dba_iterate_until", "dba_evaluate", "dba_get_params", "dba_get_state", "dba_set_state",
+    "dba_profile", "dba_layout", "dba_last_error", "dba_destroy",
+]
+
+
+class DbaError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"dba status {status}: {message}")
+        self.status = status
+
+
+class dba_config(ctypes.Structure):
+    _fields_ = [
+        ("focal", ctypes.c_double), ("cx", ctypes.c_double), ("cy", ctypes.c_double),
+        ("loss", ctypes.c_int), ("loss_param", ctypes.c_double),
+        ("rho_x", ctypes.c_double), ("rho_y", ctypes.c_double),
+        ("inner_steps", ctypes.c_int), ("lm_lambda0", ctypes.c_double),
+        ("lm_lambda_min", ctypes.c_double), ("eps_depth", ctypes.c_double),
+        ("precision", ctypes.c_int), ("tile_obs", ctypes.c_int), ("use_graph", ctypes.c_int),
+        ("cuda_stream", ctypes.c_void_p),
+    ]
+
+
+class dba_stats(ctypes.Structure):
+    _fields_ = [
+        ("iters_done", ctypes.c_longlong), ("rmse_obs", ctypes.c_double), ("rmse_gt", ctypes.c_double),
+        ("objective", ctypes.c_double), ("primal_res", ctypes.c_double), ("dual_res", ctypes.c_double),
+        ("n_invalid", ctypes.c_longlong), ("seconds", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Loads the in-tree library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        raise ImportError(f"{_build.LIB} is missing: run paper_1708_07954_gb300.build.build() first")
+    L = ctypes.CDLL(_build.LIB)
+    P = ctypes.POINTER
+    vp = ctypes.c_void_p
+    dp = P(ctypes.c_double)
+    ip = P(ctypes.c_int32)
+    L.dba_config_default.argtypes = [P(dba_config)]
+    L.dba_config_default.restype = None
+    L.dba_create.argtypes = [P(dba_config), P(vp)]
+    L.dba_set_observations.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ip, ip, dp, dp, dp]
+    L.dba_set_ground_truth.argtypes = [vp, dp, dp, P(ctypes.c_uint8)]
+    L.dba_iterate.argtypes = [vp, ctypes.c_int, P(dba_stats)]
+    L.dba_iterate_until.argtypes = [vp, ctypes.c_int, ctypes.c_double, P(dba_stats)]
+    L.dba_evaluate.argtypes = [vp, P(dba_stats)]
+    L.dba_get_params.argtypes = [vp, dp, dp]
+    L.dba_get_state.argtypes = [vp, dp, dp]
+    L.dba_set_state.argtypes = [vp, dp, dp, dp, dp]
+    L.dba_profile.argtypes = [vp, ctypes.c_int, P(ctypes.c_char_p), dp, P(ctypes.c_int)]
+    L.dba_layout.argtypes = [vp, P(ctypes.c_int64), P(ctypes.c_int)]
+    L.dba_last_error.argtypes = [vp]
+    L.dba_last_error.restype = ctypes.c_char_p
+    L.dba_destroy.argtypes = [vp]
+    L.dba_destroy.restype = None
+    for name in EXPORTED:
+        if name not in ("dba_config_default", "dba_last_error", "dba_destroy"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(status, ctx=None):
+    if status != DBA_OK:
+        msg = load().dba_last_error(ctx).decode()
+        raise DbaError(status, msg)
+
+
+def _d(a, shape):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.shape != shape:
+        a = a.reshape(shape)
+    return a
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double if a.dtype == np.float64 else ctypes.c_int32))
+
+
+def dba_config_default(**overrides) -> dba_config:
+    cfg = dba_config()
+    load().dba_config_default(ctypes.byref(cfg))
+    for k, v in overrides.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+def dba_create(cfg: dba_config) -> ctypes.c_void_p:
+    ctx = ctypes.c_void_p()
+    _check(load().dba_create(ctypes.byref(cfg), ctypes.byref(ctx)))
+    return ctx
+
+
+def dba_set_observations(ctx, n_cams, n_pts, pt_idx, cam_idx, z, cams0, pts0):
+    pt_idx = np.ascontiguousarray(pt_idx, dtype=np.int32)
+    cam_idx = np.ascontiguousarray(cam_idx, dtype=np.int32)
+    l = pt_idx.shape[0]
+    if cam_idx.shape[0] != l:
+        raise ValueError("pt_idx and cam_idx differ in length")
+    z = _d(z, (l, 2))
+    cams0 = _d(cams0, (n_cams, 6))
+    pts0 = _d(pts0, (n_pts, 3))
+    _check(load().dba_set_observations(ctx, n_cams, n_pts, l, _ptr(pt_idx), _ptr(cam_idx), _ptr(z),
+                                       _ptr(cams0), _ptr(pts0)), ctx)
+
+
+def dba_set_ground_truth(ctx, cams_gt, pts_gt, inlier=None):
+    cams_gt = np.ascontiguousarray(cams_gt, dtype=np.float64)
+    pts_gt = np.ascontiguousarray(pts_gt, dtype=np.float64)
+    mask = None
+    if inlier is not None:
+        inlier = np.ascontiguousarray(inlier, dtype=np.uint8)
+        mask = inlier.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+    _check(load().dba_set_ground_truth(ctx, _ptr(cams_gt), _ptr(pts_gt), mask), ctx)
+
+
+def dba_iterate(ctx, n_iters, stats=True):
+    st = dba_stats()
+    _check(load().dba_iterate(ctx, int(n_iters), ctypes.byref(st) if stats else None), ctx)
+    return st.as_dict() if stats else None
+
+
+def dba_iterate_until(ctx, max_iters, target_rmse_gt):
+    st = dba_stats()
+    _check(load().dba_iterate_until(ctx, int(max_iters), float(target_rmse_gt), ctypes.byref(st)), ctx)
+    return st.as_dict()
+
+
+def dba_evaluate(ctx):
+    st = dba_stats()
+    _check(load().dba_evaluate(ctx, ctypes.byref(st)), ctx)
+    return st.as_dict()
+
+
+def dba_get_params(ctx, n_cams, n_pts):
+    cams = np.zeros((n_cams, 6))
+    pts = np.zeros((n_pts, 3))
+    _check(load().dba_get_params(ctx, _ptr(cams), _ptr(pts)), ctx)
+    return cams, pts
+
+
+def dba_get_state(ctx, n_obs):
+    copies = np.zeros((n_obs, 9))
+    duals = np.zeros((n_obs, 9))
+    _check(load().dba_get_state(ctx, _ptr(copies), _ptr(duals)), ctx)
+    return copies, duals
+
+
+def dba_set_state(ctx, copies, duals, cams, pts):
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (copies, duals, cams, pts)]
+    _check(load().dba_set_state(ctx, *[_ptr(a) for a in arrs]), ctx)
+
+
+def dba_profile(ctx, n_iters):
+    cap = 16
+    names = (ctypes.c_char_p * cap)()
+    ms = (ctypes.c_double * cap)()
+    count = ctypes.c_int(cap)
+    _check(load().dba_profile(ctx, int(n_iters), names, ms, ctypes.byref(count)), ctx)
+    return {names[k].decode(): ms[k] for k in range(count.value)}
+
+
+def dba_layout(ctx):
+    out = (ctypes.c_int64 * 6)()
+    count = ctypes.c_int(6)
+    _check(load().dba_layout(ctx, out, ctypes.byref(count)), ctx)
+    keys = ["tiles", "tile_obs", "point_runs", "camera_runs", "split_points", "point_slots"]
+    return {keys[k]: int(out[k]) for k in range(count.value)}
+
+
+def dba_last_error(ctx=None) -> str:
+    return load().dba_last_error(ctx).decode()
+
+
+def dba_destroy(ctx):
+    if ctx:
+        load().dba_destroy(ctx)
+
+
+class Solver:
+    """Owns one context for one scene (a scenes.Scene or anything with its fields)."""
+
+    def __init__(self, scene, precision=None, inner_steps=5, rho_x=None, rho_y=None, tile_obs=0,
+                 use_graph=1, stream=None, ground_truth=True, **cfg_overrides):
+        self.scene = scene
+        prec = scene.precision if precision is None else precision
+        self.cfg = dba_config_default(
+            focal=scene.focal, cx=scene.cx, cy=scene.cy, loss=scene.loss, loss_param=scene.loss_param,
+            rho_x=scene.rho_x if rho_x is None else rho_x, rho_y=scene.rho_y if rho_y is None else rho_y,
+            inner_steps=inner_steps, precision=prec, tile_obs=tile_obs, use_graph=use_graph,
+            cuda_stream=stream, **cfg_overrides)
+        self.ctx = dba_create(self.cfg)
+        try:
+            dba_set_observations(self.ctx, scene.n_cams, scene.n_pts, scene.pt_idx, scene.cam_idx, scene.z,
+                                 scene.cams0, scene.pts0)
+            if ground_truth:
+                dba_set_ground_truth(self.ctx, scene.cams_gt, scene.pts_gt, ~scene.outlier)
+        except Exception:
+            self.close()
+            raise
+
+    def iterate(self, n, stats=True):
+        return dba_iterate(self.ctx, n, stats)
+
+    def iterate_until(self, max_iters, target):
+        return dba_iterate_until(self.ctx, max_iters, target)
+
+    def evaluate(self):
+        return dba_evaluate(self.ctx)
+
+    def params(self):
+        return dba_get_params(self.ctx, self.scene.n_cams, self.scene.n_pts)
+
+    def state(self):
+        return dba_get_state(self.ctx, self.scene.n_obs)
+
+    def set_state(self, copies, duals, cams, pts):
+        dba_set_state(self.ctx, copies, duals, cams, pts)
+
+    def profile(self, n):
+        return dba_profile(self.ctx, n)
+
+    def layout(self):
+        return dba_layout(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            dba_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

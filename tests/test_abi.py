@@ -1,0 +1,64 @@
+"""C ABI checks that need no GPU: the library builds, loads and exports every
+entry point include/dba.h declares; configuration validation runs on the host."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1708_07954_gb300 import build, dba
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return dba.load()
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "dba.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(dba_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("dba_create", "dba_set_observations", "dba_iterate", "dba_get_params"):
+        assert required in names
+    assert set(names) == set(dba.EXPORTED)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+    out = os.popen(f"nm -D --defined-only {build.LIB}").read()
+    for name in _declared():
+        assert re.search(rf"\bT {name}\b", out), name
+
+
+def test_config_defaults(lib):
+    cfg = dba.dba_config_default()
+    assert cfg.focal == 500.0 and cfg.cx == 320.0 and cfg.cy == 240.0
+    assert cfg.loss == dba.DBA_LOSS_HUBER and cfg.loss_param == 2.0
+    assert cfg.inner_steps == 5 and cfg.precision == dba.DBA_PREC_F32_LOCAL and cfg.use_graph == 1
+
+
+@pytest.mark.parametrize("field,value", [("focal", -1.0), ("rho_x", 0.0), ("rho_y", float("nan")),
+                                         ("loss", 7), ("inner_steps", -1), ("precision", 3),
+                                         ("tile_obs", 100), ("loss_param", 0.0)])
+def test_invalid_config_is_rejected_before_any_device_work(lib, field, value):
+    cfg = dba.dba_config_default(**{field: value})
+    with pytest.raises(dba.DbaError) as ei:
+        dba.dba_create(cfg)
+    assert ei.value.status == dba.DBA_EINVAL
+    assert "invalid configuration" in dba.dba_last_error(None)
+
+
+def test_null_arguments(lib):
+    assert lib.dba_create(None, None) == dba.DBA_EINVAL
+    assert lib.dba_iterate(None, 1, None) == dba.DBA_EINVAL
+    assert lib.dba_get_params(None, None, None) == dba.DBA_EINVAL
+    lib.dba_destroy(None)
+    assert isinstance(lib.dba_last_error(None), bytes)
