@@ -63,7 +63,10 @@ typedef struct {
   double focal, cx, cy;   /* pinhole intrinsics (pixels), shared by all cameras */
   int loss;               /* dba_loss */
   double loss_param;      /* Huber delta (pixels) or Student's t nu */
-  double rho_x, rho_y;    /* consensus penalties of Eq. (8), > 0 */
+  double rho_x, rho_y;    /* consensus penalties of Eq. (8), > 0: points; camera translations */
+  double rho_angle;       /* penalty of the camera Euler angles; <= 0: rho_y (the paper's single
+                             camera penalty).  Angles are radians and translations lengths, so
+                             their data curvatures differ by ~depth^2 */
   int inner_steps;        /* damped Gauss-Newton steps per local solve, >= 0 */
   double lm_lambda0;      /* first damping = lm_lambda0 * mean(diag H) */
   double lm_lambda_min;   /* lower clamp of the damping after an accepted step */
@@ -86,7 +89,7 @@ typedef struct {
 } dba_stats;
 
 /* Fills *cfg with defaults: focal 500, principal point (320, 240), Huber 2 px,
- * rho 1, 5 inner steps, lambda0 1e-3, lambda_min 1e-12, eps_depth 1e-6,
+ * rho 1 (angles: rho_y), 5 inner steps, lambda0 1e-3, lambda_min 1e-12, eps_depth 1e-6,
  * FP32 local solves, automatic tile size, graphs on, own stream. */
 void dba_config_default(dba_config* cfg);
 

@@ -150,7 +150,15 @@ double ora_weight(int kind, double param, double s) {
 
 /* ------------------------------------------------ local subproblem, Eq. (9) */
 
-static double rho_of(const ora_config* c, int k) { return k < 3 ? c->rho_x : c->rho_y; }
+/* Penalty of coordinate k of (x, alpha, beta, gamma, t).  phi_a is the squared
+ * Euclidean distance (Sec. 3.1); the camera block may weight its angles
+ * (radians) apart from its translation (lengths), rho_angle <= 0 keeping the
+ * paper's single rho_y. */
+static double rho_of(const ora_config* c, int k) {
+  if (k < 3) return c->rho_x;
+  if (k < 6 && c->rho_angle > 0.0) return c->rho_angle;
+  return c->rho_y;
+}
 
 /* phi_m(z - f(v)) + r^T (x - xbar) + s^T (y - ybar) + rho_x/2 |x - xbar|^2 + rho_y/2 |y - ybar|^2 */
 double ora_local_objective(const ora_config* c, const double z[2], const double xbar[3],
@@ -326,7 +334,7 @@ int ora_admm_iterate(const ora_config* c, int n_cams, int n_pts, long n_obs, con
     for (long o = 0; o < n_obs; ++o) {
       long j = cam_idx[o];
       for (int k = 0; k < 6; ++k)
-        sum_y[6 * j + k] += copies[9 * o + 3 + k] + duals[9 * o + 3 + k] / c->rho_y;
+        sum_y[6 * j + k] += copies[9 * o + 3 + k] + duals[9 * o + 3 + k] / rho_of(c, 3 + k);
       cnt_y[j] += 1;
     }
     for (long j = 0; j < n_cams; ++j)
@@ -339,7 +347,7 @@ int ora_admm_iterate(const ora_config* c, int n_cams, int n_pts, long n_obs, con
       long i = pt_idx[o], j = cam_idx[o];
       for (int k = 0; k < 3; ++k) duals[9 * o + k] += c->rho_x * (copies[9 * o + k] - pts[3 * i + k]);
       for (int k = 0; k < 6; ++k)
-        duals[9 * o + 3 + k] += c->rho_y * (copies[9 * o + 3 + k] - cams[6 * j + k]);
+        duals[9 * o + 3 + k] += rho_of(c, 3 + k) * (copies[9 * o + 3 + k] - cams[6 * j + k]);
     }
   }
   if (metrics)
@@ -384,7 +392,7 @@ void ora_eval(const ora_config* c, int n_cams, int n_pts, long n_obs, const int*
         dr += d * d;
       }
       for (int k = 0; k < 6; ++k) {
-        double d = c->rho_y * (y[k] - cams_prev[6 * (long)cam_idx[o] + k]);
+        double d = rho_of(c, 3 + k) * (y[k] - cams_prev[6 * (long)cam_idx[o] + k]);
         dr += d * d;
       }
     }

@@ -33,7 +33,8 @@ typedef struct {
   double focal, cx, cy;
   int loss;             /* ORA_LOSS_* */
   double loss_param;    /* Huber delta (px) or Student's t nu */
-  double rho_x, rho_y;  /* consensus penalties, Eq. (8) */
+  double rho_x, rho_y;  /* consensus penalties, Eq. (8): points; camera translations */
+  double rho_angle;     /* camera Euler angles; <= 0: rho_y (the paper's single camera penalty) */
   int inner_steps;      /* damped Gauss-Newton steps per local solve */
   double lm_lambda0;    /* initial damping = lm_lambda0 * mean diag of H */
   double lm_lambda_min; /* lower clamp of the damping */

@@ -62,6 +62,7 @@ struct dba_ctx {
   cudaGraphExec_t graph = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 
+  double rho_of(int c) const { return c < 3 ? prm.rho_x : (c < 6 ? prm.rho_a : prm.rho_y); }
   dba_status fail(dba_status s, const std::string& msg) {
     err = msg;
     return s;
@@ -252,7 +253,7 @@ dba_status dba_create(const dba_config* cfg, dba_ctx** out) {
                   std::isfinite(cfg->cy) && cfg->loss >= 0 && cfg->loss <= 2 &&
                   (cfg->loss == DBA_LOSS_L2 || (std::isfinite(cfg->loss_param) && cfg->loss_param > 0)) &&
                   std::isfinite(cfg->rho_x) && cfg->rho_x > 0 && std::isfinite(cfg->rho_y) &&
-                  cfg->rho_y > 0 && cfg->inner_steps >= 0 && cfg->inner_steps <= 1000 &&
+                  cfg->rho_y > 0 && std::isfinite(cfg->rho_angle) && cfg->inner_steps >= 0 && cfg->inner_steps <= 1000 &&
                   std::isfinite(cfg->lm_lambda0) && cfg->lm_lambda0 > 0 &&
                   std::isfinite(cfg->lm_lambda_min) && cfg->lm_lambda_min >= 0 &&
                   std::isfinite(cfg->eps_depth) && (cfg->precision == 0 || cfg->precision == 1) &&
@@ -275,6 +276,7 @@ dba_status dba_create(const dba_config* cfg, dba_ctx** out) {
   ctx->cfg = *cfg;
   ctx->fp32 = cfg->precision == DBA_PREC_F32_LOCAL;
   ctx->prm = Params{cfg->focal, cfg->cx, cfg->cy, cfg->loss, cfg->loss_param, cfg->rho_x, cfg->rho_y,
+                    cfg->rho_angle > 0 ? cfg->rho_angle : cfg->rho_y,
                     cfg->inner_steps, cfg->lm_lambda0, cfg->lm_lambda_min, cfg->eps_depth};
   if (cfg->cuda_stream) {
     ctx->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
@@ -323,7 +325,7 @@ void to_T(const std::vector<double>& src, std::vector<T>& dst) {
 
 template <typename T>
 dba_status upload_state_T(dba_ctx* ctx, const double* cams, const double* pts,
-                          const std::vector<double>& hdel, const std::vector<double>& hdual) {
+                          const std::vector<double>& hdel, const std::vector<double>& hdual, bool exact) {
   DevProblem& P = ctx->P;
   const int m = ctx->n_cams, n = ctx->n_pts;
   std::vector<T> tdel, tX, tY;
@@ -341,7 +343,9 @@ dba_status upload_state_T(dba_ctx* ctx, const double* cams, const double* pts,
   DBA_CUDA(cudaMemcpyAsync(P.Ym, tY.data(), tY.size() * sizeof(T), cudaMemcpyHostToDevice, st), "upload cameras");
   DBA_CUDA(cudaMemsetAsync(P.DX, 0, 3 * (size_t)n * sizeof(T), st), "clear");
   DBA_CUDA(cudaMemsetAsync(P.DY, 0, 6 * (size_t)m * sizeof(T), st), "clear");
-  DBA_CUDA(cudaMemsetAsync(P.ctl, 0, sizeof(DevCtl), st), "clear");
+  DevCtl c0{};
+  c0.exact = exact ? 1 : 0;
+  DBA_CUDA(cudaMemcpyAsync(P.ctl, &c0, sizeof c0, cudaMemcpyHostToDevice, st), "clear");
   DBA_CUDA(cudaStreamSynchronize(st), "upload state");
   ctx->cur = 0;
   ctx->pending = 0;
@@ -364,12 +368,14 @@ dba_status upload_state(dba_ctx* ctx, const double* cams, const double* pts, con
           const double cons = c < 3 ? pts[3 * i + c] : cams[6 * j + c - 3];
           hdel[c * (size_t)l + o] = copies[9 * src + c] - cons;
         }
-        if (duals) hdual[c * (size_t)l + o] = duals[9 * src + c] / (c < 3 ? ctx->prm.rho_x : ctx->prm.rho_y);
+        if (duals) hdual[c * (size_t)l + o] = duals[9 * src + c] / ctx->rho_of(c);
       }
     }
   }
-  return ctx->fp32 ? upload_state_T<float>(ctx, cams, pts, hdel, hdual)
-                   : upload_state_T<double>(ctx, cams, pts, hdel, hdual);
+  // with caller-supplied duals the per-point/camera dual sums need not vanish
+  const bool exact = duals != nullptr;
+  return ctx->fp32 ? upload_state_T<float>(ctx, cams, pts, hdel, hdual, exact)
+                   : upload_state_T<double>(ctx, cams, pts, hdel, hdual, exact);
 }
 
 dba_status read_metrics(dba_ctx* ctx, dba_stats* st, double seconds) {
@@ -690,7 +696,7 @@ dba_status dba_get_state(dba_ctx* ctx, double* copies, double* duals) {
     const size_t i = ctx->h_obs_pt[o], j = ctx->h_obs_cam[o];
     for (int c = 0; c < 9; ++c) {
       if (copies) copies[9 * dst + c] = (c < 3 ? X[3 * i + c] : Y[6 * j + c - 3]) + del[c * (size_t)l + o];
-      if (duals) duals[9 * dst + c] = (c < 3 ? ctx->prm.rho_x : ctx->prm.rho_y) * a[c * (size_t)l + o];
+      if (duals) duals[9 * dst + c] = ctx->rho_of(c) * a[c * (size_t)l + o];
     }
   }
   return DBA_OK;

@@ -15,7 +15,7 @@ struct DevCtl {
   int cur;          // index (0/1) of the current consensus buffer
   int pending;      // 1: copies are offsets from the previous consensus, duals lag by one step
   int err;          // bit 0: non-finite local solve
-  int pad;
+  int exact;        // 1: duals may not sum to zero per point/camera (first iteration after set_state)
   unsigned long long k;   // iterations run
   unsigned int done;      // finalize-kernel block counter
   unsigned int pad2;
@@ -25,7 +25,7 @@ struct Params {
   double focal, cx, cy;
   int loss;
   double loss_param;
-  double rho_x, rho_y;
+  double rho_x, rho_y, rho_a;  // points, camera translations, camera angles
   int inner_steps;
   double lambda0, lambda_min, eps_depth;
 };

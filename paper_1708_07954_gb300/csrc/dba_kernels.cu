@@ -27,32 +27,76 @@ namespace {
 
 // ------------------------------------------------------------ scalar helpers
 template <typename T> struct Num;
+// FP32 path: hardware approximations where their error (<= 2 ulp, or 2^-21 absolute for
+// sin/cos after reduction to [-pi, pi]) stays far below the pixel tolerance.
 template <> struct Num<float> {
   using V2 = float2;
-  static __device__ __forceinline__ void sc(float x, float* s, float* c) { sincosf(x, s, c); }
-  static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+  static __device__ __forceinline__ void sc(float x, float* s, float* c) {
+    // Cody-Waite reduction by 2 pi (two-term split of 2 pi), then the SFU sin/cos
+    const float k = rintf(x * 0.15915494309189535f);
+    float r = fmaf(-k, 6.28318548202514648f, x);
+    r = fmaf(-k, -1.7484555314695172e-7f, r);
+    __sincosf(r, s, c);
+  }
+  static __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
+  static __device__ __forceinline__ float div(float a, float b) { return a * __frcp_rn(b); }
+  static __device__ __forceinline__ float sqrt_(float x) { return __fsqrt_rn(x); }
   static __device__ __forceinline__ float log1p_(float x) { return log1pf(x); }
   static __device__ __forceinline__ float inf() { return CUDART_INF_F; }
 };
+// FP64 path: correctly rounded operations, as the oracle uses.
 template <> struct Num<double> {
   using V2 = double2;
   static __device__ __forceinline__ void sc(double x, double* s, double* c) { sincos(x, s, c); }
+  static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+  static __device__ __forceinline__ double div(double a, double b) { return a / b; }
   static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
   static __device__ __forceinline__ double log1p_(double x) { return log1p(x); }
   static __device__ __forceinline__ double inf() { return CUDART_INF; }
 };
 
+// float <-> double by integer bit manipulation (IEEE-754 binary32/binary64 layouts), so the
+// FP32 path spends none of GB300's scarce FP64 issue slots on conversions.  Exact for normal
+// numbers; magnitudes below 2^-126 become signed zero; non-finite values and float overflow
+// take the hardware conversion.
+__device__ __forceinline__ double widen(float f) {
+  const unsigned int b = __float_as_uint(f);
+  const unsigned int mag = b & 0x7fffffffu;
+  if (mag >= 0x7f800000u) return (double)f;
+  if (mag < 0x00800000u) return __hiloint2double((int)(b & 0x80000000u), 0);
+  const unsigned int hi = (b & 0x80000000u) | ((mag >> 3) + (896u << 20));
+  return __hiloint2double((int)hi, (int)(mag << 29));
+}
+__device__ __forceinline__ float narrow(double d) {
+  const unsigned int hi = (unsigned int)__double2hiint(d);
+  const unsigned int lo = (unsigned int)__double2loint(d);
+  const unsigned int e = (hi >> 20) & 0x7ffu;
+  if (e >= 1151u) return (float)d;
+  if (e <= 896u) return __uint_as_float(hi & 0x80000000u);
+  unsigned int f = ((e - 896u) << 23) + (((hi & 0xfffffu) << 3) | (lo >> 29));
+  f += (lo >> 28) & 1u;  // round to nearest (halfway cases away from zero)
+  return __uint_as_float(f | (hi & 0x80000000u));
+}
+template <typename T> __device__ __forceinline__ double to_f64(T v);
+template <> __device__ __forceinline__ double to_f64<float>(float v) { return widen(v); }
+template <> __device__ __forceinline__ double to_f64<double>(double v) { return v; }
+template <typename T> __device__ __forceinline__ T from_f64(double v);
+template <> __device__ __forceinline__ float from_f64<float>(double v) { return narrow(v); }
+template <> __device__ __forceinline__ double from_f64<double>(double v) { return v; }
+
 template <typename T>
 struct Prm {
-  T focal, cx, cy, lp, rho_x, rho_y, lambda0, lambda_min, eps;
+  T focal, cx, cy, lp, rho_x, rho_y, rho_a, lambda0, lambda_min, eps;
   int loss, steps;
+  // penalty of coordinate c of (x, alpha, beta, gamma, t)
+  __device__ __forceinline__ T rho(int c) const { return c < 3 ? rho_x : (c < 6 ? rho_a : rho_y); }
 };
 
 template <typename T>
 __host__ __device__ Prm<T> make_prm(const Params& p) {
   Prm<T> q;
   q.focal = (T)p.focal; q.cx = (T)p.cx; q.cy = (T)p.cy; q.lp = (T)p.loss_param;
-  q.rho_x = (T)p.rho_x; q.rho_y = (T)p.rho_y; q.lambda0 = (T)p.lambda0;
+  q.rho_x = (T)p.rho_x; q.rho_y = (T)p.rho_y; q.rho_a = (T)p.rho_a; q.lambda0 = (T)p.lambda0;
   q.lambda_min = (T)p.lambda_min; q.eps = (T)p.eps_depth;
   q.loss = p.loss; q.steps = p.inner_steps;
   return q;
@@ -62,13 +106,13 @@ __host__ __device__ Prm<T> make_prm(const Params& p) {
 template <typename T>
 __device__ __forceinline__ T misfit(int loss, T p, T s) {
   if (loss == 1) return s <= p * p ? s : T(2) * p * Num<T>::sqrt_(s) - p * p;
-  if (loss == 2) return p * Num<T>::log1p_(s / p);
+  if (loss == 2) return p * Num<T>::log1p_(Num<T>::div(s, p));
   return s;
 }
 template <typename T>
 __device__ __forceinline__ T misfit_weight(int loss, T p, T s) {
-  if (loss == 1) return s <= p * p ? T(1) : p / Num<T>::sqrt_(s);
-  if (loss == 2) return p / (p + s);
+  if (loss == 1) return s <= p * p ? T(1) : Num<T>::div(p, Num<T>::sqrt_(s));
+  if (loss == 2) return Num<T>::div(p, p + s);
   return T(1);
 }
 
@@ -113,15 +157,17 @@ template <typename T>
 __device__ __forceinline__ T local_objective(const T d[9], const T a[9], const Pose<T>& P,
                                              T z0, T z1, const Prm<T>& q) {
   if (!P.valid) return Num<T>::inf();
-  const T iz = T(1) / P.p[2];
+  const T iz = Num<T>::rcp(P.p[2]);
   const T e0 = z0 - (q.focal * P.p[0] * iz + q.cx);
   const T e1 = z1 - (q.focal * P.p[1] * iz + q.cy);
-  T px = 0, py = 0;
+  T px = 0, pa = 0, pt = 0;
 #pragma unroll
   for (int c = 0; c < 3; ++c) px += d[c] * (a[c] + T(0.5) * d[c]);
 #pragma unroll
-  for (int c = 3; c < 9; ++c) py += d[c] * (a[c] + T(0.5) * d[c]);
-  return misfit<T>(q.loss, q.lp, e0 * e0 + e1 * e1) + q.rho_x * px + q.rho_y * py;
+  for (int c = 3; c < 6; ++c) pa += d[c] * (a[c] + T(0.5) * d[c]);
+#pragma unroll
+  for (int c = 6; c < 9; ++c) pt += d[c] * (a[c] + T(0.5) * d[c]);
+  return misfit<T>(q.loss, q.lp, e0 * e0 + e1 * e1) + q.rho_x * px + q.rho_a * pa + q.rho_y * pt;
 }
 
 // Eq. (9): inner_steps damped Gauss-Newton steps with IRLS weights.  The
@@ -145,7 +191,7 @@ __device__ __forceinline__ void local_solve(T z0, T z1, const T vbar[9], const T
     T J0[9], J1[9];
     T w = 0, e0 = 0, e1 = 0;
     if (P.valid) {
-      const T iz = T(1) / P.p[2];
+      const T iz = Num<T>::rcp(P.p[2]);
       const T zx = P.p[0] * iz, zy = P.p[1] * iz;
       e0 = z0 - (q.focal * zx + q.cx);
       e1 = z1 - (q.focal * zy + q.cy);
@@ -189,22 +235,20 @@ __device__ __forceinline__ void local_solve(T z0, T z1, const T vbar[9], const T
     const T tw = T(2) * w;
     T g[9];
 #pragma unroll
-    for (int c = 0; c < 9; ++c) {
-      const T rho = c < 3 ? q.rho_x : q.rho_y;
-      g[c] = -tw * (J0[c] * e0 + J1[c] * e1) + rho * (a[c] + d[c]);
-    }
+    for (int c = 0; c < 9; ++c) g[c] = -tw * (J0[c] * e0 + J1[c] * e1) + q.rho(c) * (a[c] + d[c]);
     if (lambda < T(0)) {
-      T tr = T(3) * q.rho_x + T(6) * q.rho_y;
+      T tr = T(3) * (q.rho_x + q.rho_a + q.rho_y);
 #pragma unroll
       for (int c = 0; c < 9; ++c) tr += tw * (J0[c] * J0[c] + J1[c] * J1[c]);
       lambda = q.lambda0 * tr / T(9);
     }
-    const T iDx = T(1) / (q.rho_x + lambda), iDy = T(1) / (q.rho_y + lambda);
+    const T iDx = Num<T>::rcp(q.rho_x + lambda), iDa = Num<T>::rcp(q.rho_a + lambda),
+            iDy = Num<T>::rcp(q.rho_y + lambda);
     T G00 = 0, G01 = 0, G11 = 0, t0 = 0, t1 = 0;
     T qv[9];
 #pragma unroll
     for (int c = 0; c < 9; ++c) {
-      const T iD = c < 3 ? iDx : iDy;
+      const T iD = c < 3 ? iDx : (c < 6 ? iDa : iDy);
       qv[c] = g[c] * iD;
       G00 += J0[c] * J0[c] * iD;
       G01 += J0[c] * J1[c] * iD;
@@ -213,13 +257,13 @@ __device__ __forceinline__ void local_solve(T z0, T z1, const T vbar[9], const T
       t1 += J1[c] * qv[c];
     }
     const T S00 = T(1) + tw * G00, S01 = tw * G01, S11 = T(1) + tw * G11;
-    const T idet = T(1) / (S00 * S11 - S01 * S01);
+    const T idet = Num<T>::rcp(S00 * S11 - S01 * S01);
     const T y0 = (S11 * t0 - S01 * t1) * idet;
     const T y1 = (S00 * t1 - S01 * t0) * idet;
     T dt[9], vt[9];
 #pragma unroll
     for (int c = 0; c < 9; ++c) {
-      const T iD = c < 3 ? iDx : iDy;
+      const T iD = c < 3 ? iDx : (c < 6 ? iDa : iDy);
       dt[c] = d[c] + (-qv[c] + tw * iD * (J0[c] * y0 + J1[c] * y1));
       vt[c] = vbar[c] + dt[c];
     }
@@ -231,7 +275,7 @@ __device__ __forceinline__ void local_solve(T z0, T z1, const T vbar[9], const T
       for (int c = 0; c < 9; ++c) d[c] = dt[c];
       P = Pt;
       L = Lt;
-      lambda = fmax(lambda / T(10), q.lambda_min);
+      lambda = lambda * T(0.1) > q.lambda_min ? lambda * T(0.1) : q.lambda_min;
     } else {
       lambda *= T(10);
     }
@@ -239,11 +283,19 @@ __device__ __forceinline__ void local_solve(T z0, T z1, const T vbar[9], const T
 }
 
 // ------------------------------------------------------------ tile kernel
+// One block per tile, one thread per observation.
+//
+// Steady state: after any full iteration the scaled duals of every point and
+// camera sum to zero (sum of Eq. 12 over a track after Eq. 10; the oracle's
+// tests pin this), so Eq. (10)/(11) reduce to consensus + mean of the new
+// offsets.  Those offsets are summed per run in T inside the tile and in FP64
+// across tiles and into the consensus; the dual ascent itself is FP64.  In the
+// first iteration after dba_set_state (ctl->exact) the duals are arbitrary and
+// the summands offset + dual are formed and summed in FP64.
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT) tile_iterate_kernel(DevProblem P, Prm<T> q) {
   using V2 = typename Num<T>::V2;
-  __shared__ double s_pt[3][NT];
-  __shared__ double s_cm[6][NT];
+  __shared__ double s_buf[9][NT];
   const int tile = blockIdx.x;
   const int t = threadIdx.x;
   const long long l = P.n_obs;
@@ -252,41 +304,41 @@ __global__ void __launch_bounds__(NT) tile_iterate_kernel(DevProblem P, Prm<T> q
   const volatile DevCtl* ctl = P.ctl;
   const int cur = ctl->cur;
   const int pending = ctl->pending;
+  const int exact = ctl->exact;
   T* delta = static_cast<T*>(P.delta);
   const T* Xm = static_cast<const T*>(P.Xm);
   const T* Ym = static_cast<const T*>(P.Ym);
   const T* DX = static_cast<const T*>(P.DX);
   const T* DY = static_cast<const T*>(P.DY);
+  T(*s_t)[NT] = reinterpret_cast<T(*)[NT]>(&s_buf[0][0]);  // T view: row c at s_t[c]
 
   if (o < o1) {
     const int i = P.obs_pt[o], j = P.obs_cam[o];
     const V2 zz = static_cast<const V2*>(P.z)[o];
     T d[9], vbar[9], aT[9];
-    double a[9];
 #pragma unroll
-    for (int c = 0; c < 9; ++c) {
-      d[c] = delta[c * l + o];
-      a[c] = P.adual[c * l + o];
-    }
+    for (int c = 0; c < 9; ++c) d[c] = delta[c * l + o];
 #pragma unroll
     for (int c = 0; c < 3; ++c) vbar[c] = Xm[3 * i + c];
 #pragma unroll
     for (int c = 0; c < 6; ++c) vbar[3 + c] = Ym[6 * j + c];
     if (pending) {
       // Eqs. (12)-(13) of the previous iteration: the copy relative to the new
-      // consensus is d0 = delta + (old - new consensus); a += d0.
+      // consensus is d0 = delta + (old - new consensus); a += d0 in FP64.
 #pragma unroll
       for (int c = 0; c < 3; ++c) d[c] += DX[3 * i + c];
 #pragma unroll
       for (int c = 0; c < 6; ++c) d[3 + c] += DY[6 * j + c];
 #pragma unroll
       for (int c = 0; c < 9; ++c) {
-        a[c] += (double)d[c];
-        P.adual[c * l + o] = a[c];
+        const double a = P.adual[c * l + o] + to_f64<T>(d[c]);
+        P.adual[c * l + o] = a;
+        aT[c] = from_f64<T>(a);
       }
-    }
+    } else {
 #pragma unroll
-    for (int c = 0; c < 9; ++c) aT[c] = (T)a[c];
+      for (int c = 0; c < 9; ++c) aT[c] = from_f64<T>(P.adual[c * l + o]);
+    }
     local_solve<T>(zz.x, zz.y, vbar, aT, d, q);
     bool finite = true;
 #pragma unroll
@@ -295,34 +347,48 @@ __global__ void __launch_bounds__(NT) tile_iterate_kernel(DevProblem P, Prm<T> q
       finite = finite && isfinite(d[c]);
     }
     if (!finite) atomicOr(&P.ctl->err, 1);
-    // Eqs. (10)-(11) summands relative to the current consensus: copy + dual / rho - consensus.
-#pragma unroll
-    for (int c = 0; c < 3; ++c) s_pt[c][t] = (double)d[c] + a[c];
     const int rk = P.cam_rank[o];
+    if (exact) {
 #pragma unroll
-    for (int c = 0; c < 6; ++c) s_cm[c][rk] = (double)d[3 + c] + a[3 + c];
+      for (int c = 0; c < 9; ++c) {
+        const double v = to_f64<T>(d[c]) + P.adual[c * l + o];
+        if (c < 3) s_buf[c][t] = v; else s_buf[c][rk] = v;
+      }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 3; ++c) s_t[c][t] = d[c];
+#pragma unroll
+      for (int c = 3; c < 9; ++c) s_t[c][rk] = d[c];
+    }
   }
   __syncthreads();
 
-  // Eq. (10): per point run, one thread per (run, coordinate), FP64 sums.
+  // Eq. (10): per point run, one thread per (run, coordinate).
   const int nxt = cur ^ 1;
   {
     const int r0 = P.tile_pseg_off[tile], nr = P.tile_pseg_off[tile + 1] - r0;
     for (int task = t; task < 3 * nr; task += NT) {
       const int r = r0 + task / 3, c = task % 3;
       const int2 se = P.pseg[r];
-      double acc = 0.0;
-      for (int e = se.x; e < se.x + se.y; ++e) acc += s_pt[c][e];
+      double sum;
+      if (exact) {
+        sum = 0.0;
+        for (int e = se.x; e < se.x + se.y; ++e) sum += s_buf[c][e];
+      } else {
+        T acc = 0;
+        for (int e = se.x; e < se.x + se.y; ++e) acc += s_t[c][e];
+        sum = to_f64<T>(acc);
+      }
       const int slot = P.pseg_slot[r];
       if (slot < 0) {
         const int pt = P.pseg_pt[r];
         const double xo = P.X[cur][3 * pt + c];
-        const double xn = xo + acc / (double)se.y;
+        const double xn = xo + sum / (double)se.y;
         P.X[nxt][3 * pt + c] = xn;
         static_cast<T*>(P.Xm)[3 * pt + c] = (T)xn;
         static_cast<T*>(P.DX)[3 * pt + c] = (T)(xo - xn);
       } else {
-        P.pt_part[3 * slot + c] = acc;
+        P.pt_part[3 * slot + c] = sum;
       }
     }
   }
@@ -332,9 +398,16 @@ __global__ void __launch_bounds__(NT) tile_iterate_kernel(DevProblem P, Prm<T> q
     for (int task = t; task < 6 * nr; task += NT) {
       const int r = r0 + task / 6, c = task % 6;
       const int2 se = P.cseg[r];
-      double acc = 0.0;
-      for (int e = se.x; e < se.x + se.y; ++e) acc += s_cm[c][e];
-      P.cam_part[6 * P.cseg_slot[r] + c] = acc;
+      double sum;
+      if (exact) {
+        sum = 0.0;
+        for (int e = se.x; e < se.x + se.y; ++e) sum += s_buf[3 + c][e];
+      } else {
+        T acc = 0;
+        for (int e = se.x; e < se.x + se.y; ++e) acc += s_t[3 + c][e];
+        sum = to_f64<T>(acc);
+      }
+      P.cam_part[6 * P.cseg_slot[r] + c] = sum;
     }
   }
 }
@@ -392,6 +465,7 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(DevProblem P) {
     if (prev == gridDim.x - 1) {
       P.ctl->cur = nxt;
       P.ctl->pending = 1;
+      P.ctl->exact = 0;
       P.ctl->k += 1;
       P.ctl->done = 0;
       __threadfence();
@@ -444,7 +518,7 @@ __global__ void __launch_bounds__(kMetricThreads) metrics_kernel(DevProblem P, P
     for (int c = 0; c < 9; ++c) {
       const T dc = c < 3 ? DX[3 * i + c] : DY[6 * j + c - 3];
       const T cp = delta[c * l + o] + (pending ? dc : T(0));
-      const T rho = c < 3 ? q.rho_x : q.rho_y;
+      const T rho = q.rho(c);
       pr += cp * cp;
       dr += (rho * dc) * (rho * dc);
     }

@@ -36,7 +36,7 @@ class dba_config(ctypes.Structure):
     _fields_ = [
         ("focal", ctypes.c_double), ("cx", ctypes.c_double), ("cy", ctypes.c_double),
         ("loss", ctypes.c_int), ("loss_param", ctypes.c_double),
-        ("rho_x", ctypes.c_double), ("rho_y", ctypes.c_double),
+        ("rho_x", ctypes.c_double), ("rho_y", ctypes.c_double), ("rho_angle", ctypes.c_double),
         ("inner_steps", ctypes.c_int), ("lm_lambda0", ctypes.c_double),
         ("lm_lambda_min", ctypes.c_double), ("eps_depth", ctypes.c_double),
         ("precision", ctypes.c_int), ("tile_obs", ctypes.c_int), ("use_graph", ctypes.c_int),
@@ -220,13 +220,14 @@ def dba_destroy(ctx):
 class Solver:
     """Owns one context for one scene (a scenes.Scene or anything with its fields)."""
 
-    def __init__(self, scene, precision=None, inner_steps=5, rho_x=None, rho_y=None, tile_obs=0,
-                 use_graph=1, stream=None, ground_truth=True, **cfg_overrides):
+    def __init__(self, scene, precision=None, inner_steps=5, rho_x=None, rho_y=None, rho_angle=None,
+                 tile_obs=0, use_graph=1, stream=None, ground_truth=True, **cfg_overrides):
         self.scene = scene
         prec = scene.precision if precision is None else precision
         self.cfg = dba_config_default(
             focal=scene.focal, cx=scene.cx, cy=scene.cy, loss=scene.loss, loss_param=scene.loss_param,
             rho_x=scene.rho_x if rho_x is None else rho_x, rho_y=scene.rho_y if rho_y is None else rho_y,
+            rho_angle=getattr(scene, "rho_angle", 0.0) if rho_angle is None else rho_angle,
             inner_steps=inner_steps, precision=prec, tile_obs=tile_obs, use_graph=use_graph,
             cuda_stream=stream, **cfg_overrides)
         self.ctx = dba_create(self.cfg)
@@ -234,7 +235,9 @@ class Solver:
             dba_set_observations(self.ctx, scene.n_cams, scene.n_pts, scene.pt_idx, scene.cam_idx, scene.z,
                                  scene.cams0, scene.pts0)
             if ground_truth:
-                dba_set_ground_truth(self.ctx, scene.cams_gt, scene.pts_gt, ~scene.outlier)
+                # rmse_gt over observations of outlier-free tracks
+                mask = scene.clean_mask() if hasattr(scene, "clean_mask") else None
+                dba_set_ground_truth(self.ctx, scene.cams_gt, scene.pts_gt, mask)
         except Exception:
             self.close()
             raise

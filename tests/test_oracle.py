@@ -124,8 +124,8 @@ def test_cholesky_matches_numpy():
 
 
 # ------------------------------------------------- local subproblem, Eq. (9)
-def _indep_local_objective(kind, p, f, cx, cy, z, xbar, ybar, dual, rho_x, rho_y, v):
-    """Eq. (9) written with a library rotation and numpy only."""
+def _indep_local_objective(kind, p, f, cx, cy, z, xbar, ybar, dual, rho_x, rho_y, v, rho_a=None):
+    """Eq. (9) written with a library rotation and numpy only (rho_a: camera-angle penalty)."""
     R = Rotation.from_euler("xyz", v[3:6]).as_matrix()
     q = R @ v[:3] + v[6:9]
     if q[2] <= 1e-6:
@@ -139,7 +139,9 @@ def _indep_local_objective(kind, p, f, cx, cy, z, xbar, ybar, dual, rho_x, rho_y
     else:
         phi = sq
     dx, dy = v[:3] - xbar, v[3:] - ybar
-    return phi + dual[:3] @ dx + dual[3:] @ dy + 0.5 * rho_x * dx @ dx + 0.5 * rho_y * dy @ dy
+    ra = rho_y if rho_a is None else rho_a
+    return (phi + dual[:3] @ dx + dual[3:] @ dy + 0.5 * rho_x * dx @ dx + 0.5 * ra * dy[:3] @ dy[:3]
+            + 0.5 * rho_y * dy[3:] @ dy[3:])
 
 
 def _local_case(seed, kind):
@@ -150,7 +152,7 @@ def _local_case(seed, kind):
     dual = rng.normal(0, 5.0, 9)
     z = s.z[o] + rng.normal(0, 3.0, 2)
     p = {O.LOSS_L2: 0.0, O.LOSS_HUBER: 2.0, O.LOSS_STUDENT_T: 4.0}[kind]
-    cfg = O.config_for(s, loss=kind, loss_param=p, rho_x=2000.0, rho_y=2000.0)
+    cfg = O.config_for(s, loss=kind, loss_param=p, rho_x=2000.0, rho_y=2000.0, rho_angle=0.0)
     return s, cfg, z, xbar, ybar, dual, p
 
 
@@ -163,18 +165,27 @@ def test_local_objective_matches_independent_restatement(kind):
         a = O.local_objective(cfg, z, xbar, ybar, dual, v)
         b = _indep_local_objective(kind, p, s.focal, s.cx, s.cy, z, xbar, ybar, dual, 2000.0, 2000.0, v)
         assert abs(a - b) <= 1e-10 * max(1.0, abs(b))
+        # a separate camera-angle penalty weights only the three Euler angles
+        cfg.rho_angle = 9.0e4
+        a = O.local_objective(cfg, z, xbar, ybar, dual, v)
+        b = _indep_local_objective(kind, p, s.focal, s.cx, s.cy, z, xbar, ybar, dual, 2000.0, 2000.0, v,
+                                   rho_a=9.0e4)
+        cfg.rho_angle = 0.0
+        assert abs(a - b) <= 1e-10 * max(1.0, abs(b))
 
 
+@pytest.mark.parametrize("rho_a", [None, 5.0e4])
 @pytest.mark.parametrize("kind", [O.LOSS_L2, O.LOSS_HUBER, O.LOSS_STUDENT_T])
-def test_local_solve_reaches_brute_force_minimum(kind):
+def test_local_solve_reaches_brute_force_minimum(kind, rho_a):
     """Long damped-GN run equals a BFGS minimisation of the independently written Eq. (9)."""
     for seed in (5, 6, 7):
         s, cfg, z, xbar, ybar, dual, p = _local_case(seed, kind)
         cfg.inner_steps = 200
+        cfg.rho_angle = 0.0 if rho_a is None else rho_a
         v0 = np.r_[xbar, ybar]
         v = O.local_solve(cfg, z, xbar, ybar, dual, v0)
         fun = lambda u: _indep_local_objective(kind, p, s.focal, s.cx, s.cy, z, xbar, ybar, dual,
-                                               2000.0, 2000.0, v0 + u)
+                                               2000.0, 2000.0, v0 + u, rho_a=rho_a)
         res = minimize(fun, np.zeros(9), method="BFGS", options={"gtol": 1e-10, "maxiter": 5000})
         vb = v0 + res.x
         assert O.local_objective(cfg, z, xbar, ybar, dual, v) <= fun(res.x) + 1e-9
@@ -270,7 +281,7 @@ def test_converged_admm_matches_centralized_lm(kind):
     """Thm. 1: the ADMM limit is a stationary point of Eq. (2) with phi_m; compare with dense LM
     (Sec. 4 stop rule) on a tiny scene of the Sec. 4.2 size (5 cameras, 10 points, 50 observations)."""
     s = S.scene0(n_pts=10, n_cams=5, seed=11)
-    cfg = O.config_for(s, loss=kind, rho_x=2000.0, rho_y=2000.0)
+    cfg = O.config_for(s, loss=kind, rho_x=2000.0, rho_y=2000.0, rho_angle=0.0)
     st = O.State(s)
     st.iterate(cfg, 4000)
     cams_lm, pts_lm, obj_lm, it = O.dense_lm(cfg, s, max_iters=500)
