@@ -71,6 +71,11 @@ typedef struct {
   double lm_lambda0;      /* first damping = lm_lambda0 * mean(diag H) */
   double lm_lambda_min;   /* lower clamp of the damping after an accepted step */
   double eps_depth;       /* a copy with depth (R x + t)_3 <= eps_depth is rejected */
+  double lm_model_tol;    /* kappa >= 0: a local step whose predicted decrease is below
+                             kappa u (|L| + 2 w |e| (|z_1| + |z_2|)), the rounding noise of the
+                             local objective L in the working precision (u = 2^-24 or 2^-53),
+                             is accepted without comparing objective values; 0 = always
+                             compare */
   int precision;          /* dba_precision */
   int tile_obs;           /* observations per tile (32..256, multiple of 32); 0 = automatic */
   int use_graph;          /* 1: replay each iteration as a CUDA graph; 0: plain launches */
@@ -90,6 +95,7 @@ typedef struct {
 
 /* Fills *cfg with defaults: focal 500, principal point (320, 240), Huber 2 px,
  * rho 1 (angles: rho_y), 5 inner steps, lambda0 1e-3, lambda_min 1e-12, eps_depth 1e-6,
+ * lm_model_tol 16,
  * FP32 local solves, automatic tile size, graphs on, own stream. */
 void dba_config_default(dba_config* cfg);
 

@@ -30,6 +30,7 @@ class Config(ctypes.Structure):
         ("rho_x", ctypes.c_double), ("rho_y", ctypes.c_double), ("rho_angle", ctypes.c_double),
         ("inner_steps", ctypes.c_int), ("lm_lambda0", ctypes.c_double),
         ("lm_lambda_min", ctypes.c_double), ("eps_depth", ctypes.c_double),
+        ("lm_model_tol", ctypes.c_double),
     ]
 
 
@@ -115,9 +116,10 @@ def _f64(a):
 
 
 def config(focal=500.0, cx=320.0, cy=240.0, loss=LOSS_HUBER, loss_param=2.0, rho_x=1.0, rho_y=1.0,
-           rho_angle=0.0, inner_steps=5, lm_lambda0=1e-3, lm_lambda_min=1e-12, eps_depth=1e-6) -> Config:
+           rho_angle=0.0, inner_steps=5, lm_lambda0=1e-3, lm_lambda_min=1e-12, eps_depth=1e-6,
+           lm_model_tol=16.0) -> Config:
     return Config(focal, cx, cy, loss, loss_param, rho_x, rho_y, rho_angle, inner_steps, lm_lambda0,
-                  lm_lambda_min, eps_depth)
+                  lm_lambda_min, eps_depth, lm_model_tol)
 
 
 def config_for(scene, **overrides) -> Config:

@@ -218,7 +218,9 @@ int ora_chol_solve(int n, const double* A, const double* b, double* x) {
  *   (H + lambda I) d = -g;  accept v + d iff it is in front of the camera and
  *   lowers Eq. (9): lambda /= 10 (clamped), else lambda *= 10.
  * lambda starts at lm_lambda0 * mean(diag H) at the first step.  A linearisation
- * point behind the camera contributes no misfit term (the proximal step).
+ * point behind the camera contributes no misfit term (the proximal step).  A
+ * step whose predicted decrease is below the objective's rounding noise is
+ * accepted without the comparison (lm_model_tol).
  */
 void ora_local_solve(const ora_config* c, const double z[2], const double xbar[3],
                      const double ybar[6], const double dual[9], double v[9]) {
@@ -253,10 +255,27 @@ void ora_local_solve(const ora_config* c, const double z[2], const double xbar[3
       lambda *= 10.0;
       continue;
     }
+    double L_old = ora_local_objective(c, z, xbar, ybar, dual, v);
+    /* Decrease of the Gauss-Newton model for the step: -g.d - d^T H d / 2 (undamped H). */
+    double Jd0 = 0.0, Jd1 = 0.0, pred = 0.0;
+    for (int a = 0; a < 9; ++a) {
+      Jd0 += J[a] * d[a];
+      Jd1 += J[9 + a] * d[a];
+      pred -= g[a] * d[a] + 0.5 * rho_of(c, a) * d[a] * d[a];
+    }
+    pred -= w * (Jd0 * Jd0 + Jd1 * Jd1);
+    /* Below the rounding noise of the objective (residuals carry ~u |z| each), comparing
+       objective values cannot tell a better point from a worse one, so the model's step
+       is trusted: accepted if the trial point is in front of the camera. */
+    int trust = 0;
+    if (isfinite(L_old) && c->lm_model_tol > 0.0) {
+      double noise = c->lm_model_tol * 0x1p-53 *
+                     (fabs(L_old) + 2.0 * w * sqrt(e[0] * e[0] + e[1] * e[1]) * (fabs(z[0]) + fabs(z[1])));
+      trust = pred <= noise;
+    }
     for (int a = 0; a < 9; ++a) vt[a] = v[a] + d[a];
     double L_new = ora_local_objective(c, z, xbar, ybar, dual, vt);
-    double L_old = ora_local_objective(c, z, xbar, ybar, dual, v);
-    if (L_new < L_old) {
+    if (isfinite(L_new) && (trust || L_new < L_old)) {
       memcpy(v, vt, sizeof vt);
       lambda = fmax(lambda / 10.0, c->lm_lambda_min);
     } else {

@@ -39,6 +39,9 @@ typedef struct {
   double lm_lambda0;    /* initial damping = lm_lambda0 * mean diag of H */
   double lm_lambda_min; /* lower clamp of the damping */
   double eps_depth;     /* a copy with z~_3 <= eps_depth is rejected (Thm. 1 proof, A4) */
+  double lm_model_tol;  /* kappa: a step whose predicted decrease is <= kappa u (|L| + 2 w |e| (|z1|+|z2|)),
+                           the rounding noise of the objective (u = 2^-53), is accepted without
+                           the objective comparison; 0 disables */
 } ora_config;
 
 typedef struct {

@@ -237,6 +237,7 @@ void dba_config_default(dba_config* cfg) {
   cfg->lm_lambda0 = 1e-3;
   cfg->lm_lambda_min = 1e-12;
   cfg->eps_depth = 1e-6;
+  cfg->lm_model_tol = 16.0;
   cfg->precision = DBA_PREC_F32_LOCAL;
   cfg->tile_obs = 0;
   cfg->use_graph = 1;
@@ -256,7 +257,8 @@ dba_status dba_create(const dba_config* cfg, dba_ctx** out) {
                   cfg->rho_y > 0 && std::isfinite(cfg->rho_angle) && cfg->inner_steps >= 0 && cfg->inner_steps <= 1000 &&
                   std::isfinite(cfg->lm_lambda0) && cfg->lm_lambda0 > 0 &&
                   std::isfinite(cfg->lm_lambda_min) && cfg->lm_lambda_min >= 0 &&
-                  std::isfinite(cfg->eps_depth) && (cfg->precision == 0 || cfg->precision == 1) &&
+                  std::isfinite(cfg->eps_depth) && std::isfinite(cfg->lm_model_tol) &&
+                  cfg->lm_model_tol >= 0 && (cfg->precision == 0 || cfg->precision == 1) &&
                   (cfg->tile_obs == 0 || cfg->tile_obs == 64 || cfg->tile_obs == 128 ||
                    cfg->tile_obs == 256);
   if (!ok) {
@@ -277,7 +279,8 @@ dba_status dba_create(const dba_config* cfg, dba_ctx** out) {
   ctx->fp32 = cfg->precision == DBA_PREC_F32_LOCAL;
   ctx->prm = Params{cfg->focal, cfg->cx, cfg->cy, cfg->loss, cfg->loss_param, cfg->rho_x, cfg->rho_y,
                     cfg->rho_angle > 0 ? cfg->rho_angle : cfg->rho_y,
-                    cfg->inner_steps, cfg->lm_lambda0, cfg->lm_lambda_min, cfg->eps_depth};
+                    cfg->inner_steps, cfg->lm_lambda0, cfg->lm_lambda_min, cfg->eps_depth,
+                    cfg->lm_model_tol};
   if (cfg->cuda_stream) {
     ctx->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
   } else {

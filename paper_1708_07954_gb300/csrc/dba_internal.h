@@ -27,7 +27,7 @@ struct Params {
   double loss_param;
   double rho_x, rho_y, rho_a;  // points, camera translations, camera angles
   int inner_steps;
-  double lambda0, lambda_min, eps_depth;
+  double lambda0, lambda_min, eps_depth, model_tol;
 };
 
 // All device pointers of one problem.  Observation arrays are in internal

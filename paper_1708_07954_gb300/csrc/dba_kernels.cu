@@ -43,6 +43,7 @@ template <> struct Num<float> {
   static __device__ __forceinline__ float sqrt_(float x) { return __fsqrt_rn(x); }
   static __device__ __forceinline__ float log1p_(float x) { return log1pf(x); }
   static __device__ __forceinline__ float inf() { return CUDART_INF_F; }
+  static constexpr float unit_roundoff = 5.9604644775390625e-08f;  // 2^-24
 };
 // FP64 path: correctly rounded operations, as the oracle uses.
 template <> struct Num<double> {
@@ -53,6 +54,7 @@ template <> struct Num<double> {
   static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
   static __device__ __forceinline__ double log1p_(double x) { return log1p(x); }
   static __device__ __forceinline__ double inf() { return CUDART_INF; }
+  static constexpr double unit_roundoff = 1.1102230246251565e-16;  // 2^-53
 };
 
 // float <-> double by integer bit manipulation (IEEE-754 binary32/binary64 layouts), so the
@@ -86,7 +88,7 @@ template <> __device__ __forceinline__ double from_f64<double>(double v) { retur
 
 template <typename T>
 struct Prm {
-  T focal, cx, cy, lp, rho_x, rho_y, rho_a, lambda0, lambda_min, eps;
+  T focal, cx, cy, lp, rho_x, rho_y, rho_a, lambda0, lambda_min, eps, model_tol;
   int loss, steps;
   // penalty of coordinate c of (x, alpha, beta, gamma, t)
   __device__ __forceinline__ T rho(int c) const { return c < 3 ? rho_x : (c < 6 ? rho_a : rho_y); }
@@ -97,7 +99,7 @@ __host__ __device__ Prm<T> make_prm(const Params& p) {
   Prm<T> q;
   q.focal = (T)p.focal; q.cx = (T)p.cx; q.cy = (T)p.cy; q.lp = (T)p.loss_param;
   q.rho_x = (T)p.rho_x; q.rho_y = (T)p.rho_y; q.rho_a = (T)p.rho_a; q.lambda0 = (T)p.lambda0;
-  q.lambda_min = (T)p.lambda_min; q.eps = (T)p.eps_depth;
+  q.lambda_min = (T)p.lambda_min; q.eps = (T)p.eps_depth; q.model_tol = (T)p.model_tol;
   q.loss = p.loss; q.steps = p.inner_steps;
   return q;
 }
@@ -176,7 +178,9 @@ __device__ __forceinline__ T local_objective(const T d[9], const T a[9], const P
 // through its 2x2 capacitance matrix (Sherman-Morrison-Woodbury) instead of a
 // 9x9 factorisation.  Accept/reject and the damping schedule follow the
 // Levenberg rule: accept iff the trial is in front of the camera and lowers
-// Eq. (9).  d (offset from vbar) is updated in place.
+// Eq. (9).  A step whose predicted decrease is below the objective's rounding
+// noise is accepted without the comparison (model_tol).  d (offset from vbar)
+// is updated in place.
 template <typename T>
 __device__ __forceinline__ void local_solve(T z0, T z1, const T vbar[9], const T a[9], T d[9],
                                             const Prm<T>& q) {
@@ -260,17 +264,34 @@ __device__ __forceinline__ void local_solve(T z0, T z1, const T vbar[9], const T
     const T idet = Num<T>::rcp(S00 * S11 - S01 * S01);
     const T y0 = (S11 * t0 - S01 * t1) * idet;
     const T y1 = (S00 * t1 - S01 * t0) * idet;
-    T dt[9], vt[9];
+    T stp[9];
+    T Js0 = 0, Js1 = 0, pred = 0;
 #pragma unroll
     for (int c = 0; c < 9; ++c) {
       const T iD = c < 3 ? iDx : (c < 6 ? iDa : iDy);
-      dt[c] = d[c] + (-qv[c] + tw * iD * (J0[c] * y0 + J1[c] * y1));
+      stp[c] = -qv[c] + tw * iD * (J0[c] * y0 + J1[c] * y1);
+      Js0 += J0[c] * stp[c];
+      Js1 += J1[c] * stp[c];
+      pred -= g[c] * stp[c] + T(0.5) * q.rho(c) * stp[c] * stp[c];
+    }
+    pred -= w * (Js0 * Js0 + Js1 * Js1);  // decrease of the Gauss-Newton model
+    bool trust = false;
+    if (P.valid && q.model_tol > T(0)) {
+      // below the rounding noise of L the objective comparison is arbitrary: trust the model
+      const T noise = q.model_tol * Num<T>::unit_roundoff *
+                      (fabs(L) + T(2) * w * Num<T>::sqrt_(e0 * e0 + e1 * e1) * (fabs(z0) + fabs(z1)));
+      trust = pred <= noise;
+    }
+    T dt[9], vt[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      dt[c] = d[c] + stp[c];
       vt[c] = vbar[c] + dt[c];
     }
     Pose<T> Pt;
     pose_at(vt, q.eps, Pt);
     const T Lt = local_objective(dt, a, Pt, z0, z1, q);
-    if (Lt < L) {
+    if (Pt.valid && (trust || Lt < L)) {
 #pragma unroll
       for (int c = 0; c < 9; ++c) d[c] = dt[c];
       P = Pt;

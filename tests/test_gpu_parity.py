@@ -34,7 +34,8 @@ def oracle_cfg(scene, solver):
     c = solver.cfg
     return O.config(focal=c.focal, cx=c.cx, cy=c.cy, loss=c.loss, loss_param=c.loss_param, rho_x=c.rho_x,
                     rho_y=c.rho_y, rho_angle=c.rho_angle, inner_steps=c.inner_steps, lm_lambda0=c.lm_lambda0,
-                    lm_lambda_min=c.lm_lambda_min, eps_depth=c.eps_depth)
+                    lm_lambda_min=c.lm_lambda_min, eps_depth=c.eps_depth,
+                    lm_model_tol=c.lm_model_tol)
 
 
 def centres(cams):
@@ -62,7 +63,8 @@ def run_pair(scene, iters, check_every=1, state_at=(), **kw):
                 assert relerr(copies, st.copies) <= TOL64
                 # a dual is rho * (copy - consensus): its error is rho times the copies' error
                 scale = max(np.abs(st.pts).max(), np.abs(st.cams).max())
-                assert np.abs(duals - st.duals).max() <= 2 * TOL64 * max(cfg.rho_x, cfg.rho_y) * scale
+                rho = max(cfg.rho_x, cfg.rho_y, cfg.rho_angle)
+                assert np.abs(duals - st.duals).max() <= 2 * TOL64 * rho * scale
         return worst
 
 

@@ -181,6 +181,7 @@ def test_local_solve_reaches_brute_force_minimum(kind, rho_a):
     for seed in (5, 6, 7):
         s, cfg, z, xbar, ybar, dual, p = _local_case(seed, kind)
         cfg.inner_steps = 200
+        cfg.lm_model_tol = 0.0  # plain comparisons on every step: converge to the rounding floor
         cfg.rho_angle = 0.0 if rho_a is None else rho_a
         v0 = np.r_[xbar, ybar]
         v = O.local_solve(cfg, z, xbar, ybar, dual, v0)
@@ -195,15 +196,45 @@ def test_local_solve_reaches_brute_force_minimum(kind, rho_a):
         assert np.abs(g).max() < 1e-3
 
 
+@pytest.mark.parametrize("kind", [O.LOSS_L2, O.LOSS_HUBER, O.LOSS_STUDENT_T])
+def test_local_solve_noise_rule_keeps_the_minimum(kind):
+    """Trusting model steps below the objective's rounding noise converges to the same
+    minimiser as plain comparisons, to well below sqrt(eps)."""
+    for seed in (9, 10):
+        s, cfg, z, xbar, ybar, dual, p = _local_case(seed, kind)
+        v0 = np.r_[xbar, ybar]
+        cfg.inner_steps, cfg.lm_model_tol = 300, 0.0
+        vinf = O.local_solve(cfg, z, xbar, ybar, dual, v0)
+        cfg.lm_model_tol = 16.0
+        v1 = O.local_solve(cfg, z, xbar, ybar, dual, v0)
+        assert np.all(np.abs(v1 - vinf) <= 1e-9 * (1 + np.abs(vinf)))
+
+
+def test_admm_is_insensitive_to_last_bit_perturbations():
+    """With the noise rule, one ulp of difference in the state stays at the rounding level over
+    iterations (plain objective comparisons amplify it ~1e6 in one iteration)."""
+    s = S.scene0()
+    c = O.config_for(s)
+    a, b = O.State(s), O.State(s)
+    b.pts = b.pts * (1 + 2.2e-16)
+    b.copies[:, :3] *= 1 + 2.2e-16
+    for _ in range(6):
+        a.iterate(c, 1)
+        b.iterate(c, 1)
+    err = max(np.abs(a.pts - b.pts).max() / np.abs(a.pts).max(), np.abs(a.cams - b.cams).max() / np.abs(a.cams).max())
+    assert err < 1e-13
+
+
 def test_local_solve_monotone_and_fixed_count():
-    """Each accepted step lowers Eq. (9); zero steps leave the copy unchanged."""
+    """Each accepted step lowers Eq. (9) (up to its rounding noise, where model steps are
+    trusted); zero steps leave the copy unchanged."""
     s, cfg, z, xbar, ybar, dual, p = _local_case(8, O.LOSS_HUBER)
     v0 = np.r_[xbar, ybar] + 1e-3
     prev = O.local_objective(cfg, z, xbar, ybar, dual, v0)
     for k in range(1, 8):
         cfg.inner_steps = k
         cur = O.local_objective(cfg, z, xbar, ybar, dual, O.local_solve(cfg, z, xbar, ybar, dual, v0))
-        assert cur <= prev
+        assert cur <= prev + 1e-12 * abs(prev)
         prev = cur
     cfg.inner_steps = 0
     np.testing.assert_array_equal(O.local_solve(cfg, z, xbar, ybar, dual, v0), v0)
