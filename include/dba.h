@@ -161,6 +161,36 @@ dba_status dba_profile(dba_ctx* ctx, int n_iters, const char** names, double* ms
  * *count: in capacity, out entries written. */
 dba_status dba_layout(dba_ctx* ctx, int64_t* out, int* count);
 
+/* Allocation-free evaluation.  For callers that cannot let the library call cudaMalloc:
+ * processes whose device memory belongs to another allocator (a framework's caching
+ * allocator, a fixed pool reserved up front), loops replayed as CUDA graphs or with
+ * real-time budgets where an allocation would stall or fail, and embedders that do not let
+ * a library own device memory.  The paper has no counterpart; this is an interface of this
+ * library only, and it uses no context.
+ *
+ * At the caller's cameras and points it computes, over all observations, out[0] = sum of
+ * |z - f(x_i, y_j)|^2, out[1] = sum of phi_m (Eq. 2 with the configured misfit), out[2] = the
+ * number of observations evaluated, out[3] = the number not evaluated (depth <= eps_depth, or
+ * an index outside [0, n_pts) / [0, n_cams)).  FP64 throughout.
+ * All arrays are DEVICE pointers the caller owns, laid out as elsewhere in this header:
+ * pt_idx, cam_idx int32 [n_obs]; z float64 [n_obs][2]; cams [n_cams][6]; pts [n_pts][3];
+ * out float64 [4], written only.  Uses cfg->focal, cx, cy, loss, loss_param, eps_depth.
+ * Launches on `stream` (a cudaStream_t; NULL = the default stream) and returns without
+ * waiting: out is complete when the stream reaches that point.
+ * Limit: 0 <= n_obs <= DBA_NOALLOC_MAX_OBS; larger sizes return DBA_EINVAL.
+ * Scratch: one file-scope device array of 4096 x 4 doubles (128 KiB), which every GPU that
+ * loads this library holds until the process exits.  All calls share it and each call
+ * overwrites what it reads, so nothing needs clearing, but calls whose kernels may overlap
+ * on the GPU (other streams, other host threads on the same device) race: serialise them.
+ * The first call on each device looks up the array's device address with that device
+ * current; make that first call before capturing a stream into a graph.
+ * Errors: DBA_EINVAL for null pointers, bad sizes or configuration, DBA_ECUDA for a launch
+ * failure; the message is in dba_last_error(NULL). */
+#define DBA_NOALLOC_MAX_OBS 16777216
+dba_status dba_evaluate_noalloc(const dba_config* cfg, int32_t n_cams, int32_t n_pts, int64_t n_obs,
+                                const int32_t* pt_idx, const int32_t* cam_idx, const double* z,
+                                const double* cams, const double* pts, double* out, void* stream);
+
 /* Message of the last failed call on ctx (or of the last failed dba_create
  * when ctx is NULL).  Never NULL. */
 const char* dba_last_error(const dba_ctx* ctx);

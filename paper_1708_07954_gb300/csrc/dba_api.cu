@@ -763,4 +763,34 @@ dba_status dba_layout(dba_ctx* ctx, int64_t* out, int* count) {
   return DBA_OK;
 }
 
+dba_status dba_evaluate_noalloc(const dba_config* cfg, int32_t n_cams, int32_t n_pts, int64_t n_obs,
+                                const int32_t* pt_idx, const int32_t* cam_idx, const double* z,
+                                const double* cams, const double* pts, double* out, void* stream) {
+  if (!cfg || !out || (n_obs > 0 && (!pt_idx || !cam_idx || !z || !cams || !pts))) {
+    g_create_error = "dba_evaluate_noalloc: null pointer";
+    return DBA_EINVAL;
+  }
+  if (n_obs < 0 || n_obs > (int64_t)DBA_NOALLOC_MAX_OBS || n_cams < 0 || n_pts < 0) {
+    g_create_error = "dba_evaluate_noalloc: n_obs must lie in [0, " + std::to_string(DBA_NOALLOC_MAX_OBS) +
+                     "] (the size of its fixed device scratch) and n_cams, n_pts must be >= 0";
+    return DBA_EINVAL;
+  }
+  if (!(std::isfinite(cfg->focal) && cfg->focal > 0 && std::isfinite(cfg->cx) && std::isfinite(cfg->cy) &&
+        cfg->loss >= 0 && cfg->loss <= 2 &&
+        (cfg->loss == DBA_LOSS_L2 || (std::isfinite(cfg->loss_param) && cfg->loss_param > 0)) &&
+        std::isfinite(cfg->eps_depth))) {
+    g_create_error = "dba_evaluate_noalloc: invalid configuration (focal, principal point, loss, eps_depth)";
+    return DBA_EINVAL;
+  }
+  const Params prm{cfg->focal, cfg->cx, cfg->cy, cfg->loss, cfg->loss_param, 1.0, 1.0, 1.0,
+                   0, 1e-3, 0.0, cfg->eps_depth, 0.0};
+  const cudaError_t e = dba::launch_eval_noalloc(prm, n_obs, n_cams, n_pts, pt_idx, cam_idx, z, cams, pts, out,
+                                                 static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) {
+    g_create_error = std::string("dba_evaluate_noalloc: ") + cudaGetErrorString(e);
+    return DBA_ECUDA;
+  }
+  return DBA_OK;
+}
+
 }  // extern "C"

@@ -87,4 +87,9 @@ cudaError_t launch_project_truth(const DevProblem& P, const Params& prm, bool fp
                                  const double* cams_gt, const double* pts_gt, void* zt_out,
                                  cudaStream_t s);
 
+// Allocation-free reprojection statistics (file-scope device scratch; see dba_evaluate_noalloc).
+cudaError_t launch_eval_noalloc(const Params& prm, long long n_obs, int n_cams, int n_pts, const int* pt_idx,
+                                const int* cam_idx, const double* z, const double* cams, const double* pts,
+                                double* out, cudaStream_t s);
+
 }  // namespace dba

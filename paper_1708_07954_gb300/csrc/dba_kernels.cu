@@ -20,6 +20,9 @@
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
+#include <mutex>
+
+#include "../../include/dba.h"
 #include "dba_internal.h"
 
 namespace dba {
@@ -613,6 +616,77 @@ __global__ void project_truth_kernel(DevProblem P, Prm<double> q, const double* 
   }
 }
 
+// ------------------------------------------------------------ allocation-free evaluation
+// Reprojection statistics at caller-given parameters for callers that cannot
+// allocate device memory.  Per-block partial sums go to a file-scope device
+// array instead of an allocated buffer; a second single-block kernel reduces
+// them into the caller's output.  Each block handles a fixed chunk of
+// observations, so the array bounds the number of observations per call.
+constexpr int kNoallocThreads = 256;
+constexpr int kNoallocObsPerBlock = 4096;
+constexpr int kNoallocMaxBlocks = 4096;  // 4096 x 4 doubles = 128 KiB of scratch
+static_assert((long long)kNoallocMaxBlocks * kNoallocObsPerBlock == (long long)DBA_NOALLOC_MAX_OBS,
+              "scratch size and the documented observation limit must agree");
+
+__device__ __align__(256) double g_noalloc_partials[kNoallocMaxBlocks * 4];
+
+__global__ void __launch_bounds__(kNoallocThreads)
+eval_noalloc_kernel(Prm<double> q, long long l, int n_cams, int n_pts, const int* pt_idx, const int* cam_idx,
+                    const double2* z, const double* cams, const double* pts, double* partials) {
+  __shared__ double red[4][kNoallocThreads];
+  double acc[4] = {0, 0, 0, 0};
+  const long long o0 = (long long)blockIdx.x * kNoallocObsPerBlock;
+  const long long o1 = o0 + kNoallocObsPerBlock < l ? o0 + kNoallocObsPerBlock : l;
+  for (long long o = o0 + threadIdx.x; o < o1; o += kNoallocThreads) {
+    const int i = pt_idx[o], j = cam_idx[o];
+    if (i < 0 || i >= n_pts || j < 0 || j >= n_cams) {  // not evaluated: index out of range
+      acc[3] += 1.0;
+      continue;
+    }
+    double v[9];
+    for (int c = 0; c < 3; ++c) v[c] = pts[3 * (long long)i + c];
+    for (int c = 0; c < 6; ++c) v[3 + c] = cams[6 * (long long)j + c];
+    Pose<double> Q;
+    pose_at(v, q.eps, Q);
+    if (Q.valid) {
+      const double iz = 1.0 / Q.p[2];
+      const double2 zz = z[o];
+      const double e0 = zz.x - (q.focal * Q.p[0] * iz + q.cx);
+      const double e1 = zz.y - (q.focal * Q.p[1] * iz + q.cy);
+      const double sq = e0 * e0 + e1 * e1;
+      acc[0] += sq;
+      acc[1] += misfit<double>(q.loss, q.lp, sq);
+      acc[2] += 1.0;
+    } else {
+      acc[3] += 1.0;
+    }
+  }
+  for (int k = 0; k < 4; ++k) red[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int w = kNoallocThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int k = 0; k < 4; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < 4) partials[4 * blockIdx.x + threadIdx.x] = red[threadIdx.x][0];
+}
+
+__global__ void __launch_bounds__(kNoallocThreads)
+eval_noalloc_final_kernel(const double* partials, int nblocks, double* out) {
+  __shared__ double red[4][kNoallocThreads];
+  double acc[4] = {0, 0, 0, 0};
+  for (int b = threadIdx.x; b < nblocks; b += kNoallocThreads)
+    for (int k = 0; k < 4; ++k) acc[k] += partials[4 * b + k];
+  for (int k = 0; k < 4; ++k) red[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int w = kNoallocThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int k = 0; k < 4; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < 4) out[threadIdx.x] = red[threadIdx.x][0];
+}
+
 int grid_for(long long n, int threads, int cap) {
   long long g = (n + threads - 1) / threads;
   if (g < 1) g = 1;
@@ -689,4 +763,43 @@ cudaError_t launch_project_truth(const DevProblem& P, const Params& prm, bool fp
   return cudaGetLastError();
 }
 
+// Device address of g_noalloc_partials, looked up once per device with that
+// device current.  In host code the symbol's name is only a host-side stand-in.
+namespace {
+std::mutex g_noalloc_mutex;
+double* g_noalloc_addr[256] = {nullptr};
+}  // namespace
+
+cudaError_t launch_eval_noalloc(const Params& prm, long long n_obs, int n_cams, int n_pts, const int* pt_idx,
+                                const int* cam_idx, const double* z, const double* cams, const double* pts,
+                                double* out, cudaStream_t s) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
+  double* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+      void* ptr = nullptr;
+      e = cudaGetSymbolAddress(&ptr, g_noalloc_partials);
+      if (e != cudaSuccess) return e;
+      g_noalloc_addr[dev] = static_cast<double*>(ptr);
+    }
+    scratch = g_noalloc_addr[dev];
+  }
+  const int blocks = n_obs > 0 ? (int)((n_obs + kNoallocObsPerBlock - 1) / kNoallocObsPerBlock) : 0;
+  if (blocks > kNoallocMaxBlocks) return cudaErrorInvalidValue;
+  if (blocks > 0) {
+    eval_noalloc_kernel<<<blocks, kNoallocThreads, 0, s>>>(make_prm<double>(prm), n_obs, n_cams, n_pts, pt_idx,
+                                                           cam_idx, reinterpret_cast<const double2*>(z), cams,
+                                                           pts, scratch);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  eval_noalloc_final_kernel<<<1, kNoallocThreads, 0, s>>>(scratch, blocks, out);
+  return cudaGetLastError();
+}
+
 }  // namespace dba
+

@@ -22,8 +22,9 @@ DBA_PREC_F64, DBA_PREC_F32_LOCAL = 0, 1
 EXPORTED = [
     "dba_config_default", "dba_create", "dba_set_observations", "dba_set_ground_truth", "dba_iterate",
     "dba_iterate_until", "dba_evaluate", "dba_get_params", "dba_get_state", "dba_set_state",
-    "dba_profile", "dba_layout", "dba_last_error", "dba_destroy",
+    "dba_profile", "dba_layout", "dba_evaluate_noalloc", "dba_last_error", "dba_destroy",
 ]
+DBA_NOALLOC_MAX_OBS = 16777216
 
 
 class DbaError(RuntimeError):
@@ -87,6 +88,8 @@ def load():
     L.dba_set_state.argtypes = [vp, dp, dp, dp, dp]
     L.dba_profile.argtypes = [vp, ctypes.c_int, P(ctypes.c_char_p), dp, P(ctypes.c_int)]
     L.dba_layout.argtypes = [vp, P(ctypes.c_int64), P(ctypes.c_int)]
+    L.dba_evaluate_noalloc.argtypes = [P(dba_config), ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, vp, vp, vp,
+                                       vp, vp, vp, vp]
     L.dba_last_error.argtypes = [vp]
     L.dba_last_error.restype = ctypes.c_char_p
     L.dba_destroy.argtypes = [vp]
@@ -206,6 +209,13 @@ def dba_layout(ctx):
     _check(load().dba_layout(ctx, out, ctypes.byref(count)), ctx)
     keys = ["tiles", "tile_obs", "point_runs", "camera_runs", "split_points", "point_slots"]
     return {keys[k]: int(out[k]) for k in range(count.value)}
+
+
+def dba_evaluate_noalloc(cfg, n_cams, n_pts, n_obs, pt_idx_ptr, cam_idx_ptr, z_ptr, cams_ptr, pts_ptr,
+                         out_ptr, stream=None):
+    """Device pointers (ints) in, device pointer out; see include/dba.h."""
+    _check(load().dba_evaluate_noalloc(ctypes.byref(cfg), int(n_cams), int(n_pts), int(n_obs), pt_idx_ptr,
+                                       cam_idx_ptr, z_ptr, cams_ptr, pts_ptr, out_ptr, stream))
 
 
 def dba_last_error(ctx=None) -> str:
