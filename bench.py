@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["f32", "f64"], default="f32")
     ap.add_argument("--n-pts", type=int, default=500000, help="points of the scene (default: full size)")
+    ap.add_argument("--inner-steps", type=int, default=5, help="damped Gauss-Newton steps per local solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=2)
@@ -200,7 +201,7 @@ def run_ours(args, rank, world, local_rank):
     prec = dba.DBA_PREC_F32_LOCAL if fp32 else dba.DBA_PREC_F64
     sc = S.scene2(n_pts=args.n_pts)
     stream = torch.cuda.Stream()  # a real stream: the library launches on it, events are recorded on it
-    solver = dba.Solver(sc, precision=prec, stream=stream.cuda_stream)
+    solver = dba.Solver(sc, precision=prec, inner_steps=args.inner_steps, stream=stream.cuda_stream)
     layout = solver.layout()
     solver.iterate(args.warmup, stats=False)
 
@@ -248,7 +249,8 @@ def run_ours(args, rank, world, local_rank):
         iters = sc.iters
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        with dba.Solver(sc, precision=prec, stream=stream.cuda_stream, ground_truth=False) as s2:
+        with dba.Solver(sc, precision=prec, inner_steps=args.inner_steps, stream=stream.cuda_stream,
+                        ground_truth=False) as s2:
             s2.iterate(iters, stats=False)
             s2.params()
         dt = time.perf_counter() - t0
@@ -278,7 +280,7 @@ def run_ours(args, rank, world, local_rank):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64" if fp32 else "f64", "data": "synthetic",
             "config": {"workload": sc.name, "n_obs": sc.n_obs, "n_cams": sc.n_cams, "n_pts": sc.n_pts,
-                       "loss": "huber", "inner_steps": 5,
+                       "loss": "huber", "inner_steps": args.inner_steps,
                        "precision": "f32 local solves, f64 consensus/duals" if fp32 else "f64",
                        "l2": "inputs larger than L2 (~1 GB per iteration), no flush",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},

@@ -220,11 +220,13 @@ int ora_chol_solve(int n, const double* A, const double* b, double* x) {
  * lambda starts at lm_lambda0 * mean(diag H) at the first step.  A linearisation
  * point behind the camera contributes no misfit term (the proximal step).  A
  * step whose predicted decrease is below the objective's rounding noise is
- * accepted without the comparison (lm_model_tol).
+ * accepted without the comparison (lm_model_tol) and the objective is then
+ * carried as its model value.
  */
 void ora_local_solve(const ora_config* c, const double z[2], const double xbar[3],
                      const double ybar[6], const double dual[9], double v[9]) {
   double lambda = -1.0;
+  double L_old = ora_local_objective(c, z, xbar, ybar, dual, v);
   for (int step = 0; step < c->inner_steps; ++step) {
     double H[81], g[9], d[9], vt[9], J[18] = {0};
     double zp[2], e[2] = {0.0, 0.0}, w = 0.0;
@@ -255,18 +257,18 @@ void ora_local_solve(const ora_config* c, const double z[2], const double xbar[3
       lambda *= 10.0;
       continue;
     }
-    double L_old = ora_local_objective(c, z, xbar, ybar, dual, v);
-    /* Decrease of the Gauss-Newton model for the step: -g.d - d^T H d / 2 (undamped H). */
-    double Jd0 = 0.0, Jd1 = 0.0, pred = 0.0;
+    /* Decrease of the Gauss-Newton model -g.d - d^T H d / 2 (undamped H); since
+       (H + lambda I) d = -g it equals (lambda |d|^2 - g.d) / 2. */
+    double gd = 0.0, dd = 0.0;
     for (int a = 0; a < 9; ++a) {
-      Jd0 += J[a] * d[a];
-      Jd1 += J[9 + a] * d[a];
-      pred -= g[a] * d[a] + 0.5 * rho_of(c, a) * d[a] * d[a];
+      gd += g[a] * d[a];
+      dd += d[a] * d[a];
     }
-    pred -= w * (Jd0 * Jd0 + Jd1 * Jd1);
+    double pred = 0.5 * (lambda * dd - gd);
     /* Below the rounding noise of the objective (residuals carry ~u |z| each), comparing
        objective values cannot tell a better point from a worse one, so the model's step
-       is trusted: accepted if the trial point is in front of the camera. */
+       is trusted: accepted if the trial point is in front of the camera, and the objective
+       is carried as L - pred. */
     int trust = 0;
     if (isfinite(L_old) && c->lm_model_tol > 0.0) {
       double noise = c->lm_model_tol * 0x1p-53 *
@@ -274,9 +276,21 @@ void ora_local_solve(const ora_config* c, const double z[2], const double xbar[3
       trust = pred <= noise;
     }
     for (int a = 0; a < 9; ++a) vt[a] = v[a] + d[a];
+    if (trust) {
+      double zp_t[2];
+      if (ora_project(c, vt, vt + 3, zp_t) > c->eps_depth) {
+        memcpy(v, vt, sizeof vt);
+        L_old -= pred;
+        lambda = fmax(lambda / 10.0, c->lm_lambda_min);
+      } else {
+        lambda *= 10.0;
+      }
+      continue;
+    }
     double L_new = ora_local_objective(c, z, xbar, ybar, dual, vt);
-    if (isfinite(L_new) && (trust || L_new < L_old)) {
+    if (L_new < L_old) {
       memcpy(v, vt, sizeof vt);
+      L_old = L_new;
       lambda = fmax(lambda / 10.0, c->lm_lambda_min);
     } else {
       lambda *= 10.0;

@@ -25,9 +25,12 @@ thread_local std::string g_create_error = "no error";
 
 struct HostLayout {
   std::vector<long long> perm;  // internal position -> caller index
-  std::vector<int> obs_pt, obs_cam;
-  std::vector<unsigned char> cam_rank;
-  std::vector<int> tile_off{0}, tile_pseg_off{0}, pseg_pt, pseg_slot, tile_cseg_off{0}, cseg_slot;
+  std::vector<int> pt_perm;     // internal point -> caller point
+  std::vector<int> obs_pt;      // internal point of each observation
+  std::vector<int> obs_cam;     // camera of each observation
+  std::vector<int> obs_cam_rank;  // camera | rank in the tile's camera order << 24
+  std::vector<dba::TileInfo> tiles;
+  std::vector<int> pseg_slot, cseg_slot;
   std::vector<int2> pseg, cseg;
   std::vector<int> cam_slot_off, cam_count, split_pt, split_slot_off{0}, pt_count;
   int n_cam_slots = 0, n_pt_slots = 0;
@@ -52,6 +55,7 @@ struct dba_ctx {
   int n_cams = 0, n_pts = 0;
   long long n_obs = 0;
   std::vector<long long> perm;   // internal position -> caller index
+  std::vector<int> pt_perm;      // internal point -> caller point
   std::vector<int> h_obs_pt, h_obs_cam;
   int64_t n_pseg = 0;
   std::vector<void*> allocs;
@@ -79,6 +83,7 @@ struct dba_ctx {
     P = DevProblem{};
     has_problem = has_gt = false;
     perm.clear();
+    pt_perm.clear();
     h_obs_pt.clear();
     h_obs_cam.clear();
   }
@@ -110,74 +115,92 @@ struct dba_ctx {
 
 namespace {
 
-// Observation layout.  Points are ordered by their smallest camera index so
-// that a tile's tracks share cameras; each point's observations are sorted by
-// camera.  Tiles hold whole tracks of at most tile_obs observations; a track
-// longer than a tile is cut into tile-sized pieces reduced in the finalize
-// kernel.  Within a tile, observations of one camera form runs in camera order.
+// Observation layout.  Points are ordered by their smallest camera index (so a
+// tile's tracks share cameras) and renumbered internally in that order, so
+// every tile covers a contiguous range of internal point ids; each point's
+// observations are sorted by camera.  Tiles hold whole tracks of at most
+// tile_obs observations; a longer track is cut into tile-sized pieces reduced
+// in the finalize kernel.  Within a tile, observations of one camera form runs
+// in camera order; an observation's position in that order is packed above its
+// camera index.
 void build_layout(int n_cams, int n_pts, long long n_obs, const int32_t* pt_idx,
                   const int32_t* cam_idx, int NT, HostLayout& L) {
-  L.pt_count.assign(n_pts, 0);
+  std::vector<int> count(n_pts, 0), min_cam(n_pts, n_cams);
   L.cam_count.assign(n_cams, 0);
-  std::vector<int> min_cam(n_pts, n_cams);
   for (long long o = 0; o < n_obs; ++o) {
-    L.pt_count[pt_idx[o]] += 1;
+    count[pt_idx[o]] += 1;
     L.cam_count[cam_idx[o]] += 1;
     min_cam[pt_idx[o]] = std::min(min_cam[pt_idx[o]], (int)cam_idx[o]);
   }
-  // counting sort of observations by point
+  // counting sort of observations by caller point
   std::vector<long long> pstart(n_pts + 1, 0);
-  for (int i = 0; i < n_pts; ++i) pstart[i + 1] = pstart[i] + L.pt_count[i];
+  for (int i = 0; i < n_pts; ++i) pstart[i + 1] = pstart[i] + count[i];
   std::vector<long long> by_pt(n_obs);
   {
     std::vector<long long> fill(pstart.begin(), pstart.end() - 1);
     for (long long o = 0; o < n_obs; ++o) by_pt[fill[pt_idx[o]]++] = o;
   }
+  // internal point numbering: observed points by first camera, then unobserved ones
   std::vector<int> order;
   order.reserve(n_pts);
   for (int i = 0; i < n_pts; ++i)
-    if (L.pt_count[i] > 0) order.push_back(i);
-  std::stable_sort(order.begin(), order.end(),
-                   [&](int a, int b) { return min_cam[a] < min_cam[b]; });
+    if (count[i] > 0) order.push_back(i);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return min_cam[a] < min_cam[b]; });
+  for (int i = 0; i < n_pts; ++i)
+    if (count[i] == 0) order.push_back(i);
+  L.pt_perm = order;
+  L.pt_count.resize(n_pts);
+  for (int k = 0; k < n_pts; ++k) L.pt_count[k] = count[order[k]];
 
   L.perm.resize(n_obs);
   L.obs_pt.resize(n_obs);
   L.obs_cam.resize(n_obs);
-  L.cam_rank.assign(n_obs, 0);
+  L.obs_cam_rank.resize(n_obs);
   long long pos = 0;
-  int fill_tile = 0;  // observations in the open tile
+  int fill_tile = 0;           // observations in the open tile
+  long long tile_start = 0;    // first observation of the open tile
+  int tile_first_run = 0;      // first point run of the open tile
+  int tile_first_pt = 0;       // first internal point of the open tile
   auto close_tile = [&]() {
-    L.tile_off.push_back((int)pos);
-    L.tile_pseg_off.push_back((int)L.pseg.size());
+    dba::TileInfo ti{};
+    ti.o0 = (int)tile_start;
+    ti.n = (int)(pos - tile_start);
+    ti.r0 = tile_first_run;
+    ti.nr = (int)L.pseg.size() - tile_first_run;
+    ti.pt_lo = tile_first_pt;
+    L.tiles.push_back(ti);
+    tile_start = pos;
+    tile_first_run = (int)L.pseg.size();
     fill_tile = 0;
   };
-  for (int i : order) {
+  for (int k = 0; k < n_pts && L.pt_count[k] > 0; ++k) {
+    const int i = order[k];
     const long long s = pstart[i];
-    const int c = L.pt_count[i];
+    const int c = count[i];
     std::sort(by_pt.begin() + s, by_pt.begin() + s + c, [&](long long a, long long b) {
       return cam_idx[a] != cam_idx[b] ? cam_idx[a] < cam_idx[b] : a < b;
     });
-    for (int k = 0; k < c; ++k) {
-      const long long o = by_pt[s + k];
-      L.perm[pos + k] = o;
-      L.obs_pt[pos + k] = i;
-      L.obs_cam[pos + k] = cam_idx[o];
+    for (int q = 0; q < c; ++q) {
+      const long long o = by_pt[s + q];
+      L.perm[pos + q] = o;
+      L.obs_pt[pos + q] = k;
+      L.obs_cam[pos + q] = cam_idx[o];
     }
     if (c <= NT) {
       if (fill_tile + c > NT) close_tile();
+      if (fill_tile == 0) tile_first_pt = k;
       L.pseg.push_back(make_int2(fill_tile, c));
-      L.pseg_pt.push_back(i);
       L.pseg_slot.push_back(-1);
       fill_tile += c;
       pos += c;
     } else {
       if (fill_tile > 0) close_tile();
-      L.split_pt.push_back(i);
+      L.split_pt.push_back(k);
       int rem = c;
       while (rem > 0) {
         const int take = std::min(rem, NT);
+        tile_first_pt = k;
         L.pseg.push_back(make_int2(0, take));
-        L.pseg_pt.push_back(i);
         L.pseg_slot.push_back(L.n_pt_slots++);
         fill_tile = take;
         pos += take;
@@ -188,17 +211,16 @@ void build_layout(int n_cams, int n_pts, long long n_obs, const int32_t* pt_idx,
     }
   }
   if (fill_tile > 0) close_tile();
-  const int n_tiles = (int)L.tile_off.size() - 1;
 
   // camera runs per tile, in camera order
   std::vector<int> run_cam;
   std::vector<int> idx;
-  for (int t = 0; t < n_tiles; ++t) {
-    const int o0 = L.tile_off[t], o1 = L.tile_off[t + 1];
-    idx.resize(o1 - o0);
-    for (int k = 0; k < o1 - o0; ++k) idx[k] = o0 + k;
+  for (dba::TileInfo& ti : L.tiles) {
+    idx.resize(ti.n);
+    for (int q = 0; q < ti.n; ++q) idx[q] = ti.o0 + q;
     std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return L.obs_cam[a] < L.obs_cam[b]; });
-    for (int r = 0; r < (int)idx.size(); ++r) L.cam_rank[idx[r]] = (unsigned char)r;
+    for (int r = 0; r < (int)idx.size(); ++r) L.obs_cam_rank[idx[r]] = L.obs_cam[idx[r]] | (r << 24);
+    ti.c0 = (int)L.cseg.size();
     int r = 0;
     while (r < (int)idx.size()) {
       int e = r;
@@ -207,7 +229,7 @@ void build_layout(int n_cams, int n_pts, long long n_obs, const int32_t* pt_idx,
       run_cam.push_back(L.obs_cam[idx[r]]);
       r = e;
     }
-    L.tile_cseg_off.push_back((int)L.cseg.size());
+    ti.nc = (int)L.cseg.size() - ti.c0;
   }
   // camera partial slots grouped by camera
   L.cam_slot_off.assign(n_cams + 1, 0);
@@ -266,6 +288,7 @@ dba_status dba_create(const dba_config* cfg, dba_ctx** out) {
     return DBA_EINVAL;
   }
   cudaError_t e = cudaFree(nullptr);  // initialise the runtime on the current device
+  if (e == cudaSuccess) e = dba::prepare_tile_kernels();
   if (e != cudaSuccess) {
     g_create_error = std::string("dba_create: CUDA unavailable: ") + cudaGetErrorString(e);
     return DBA_ECUDA;
@@ -358,9 +381,13 @@ dba_status upload_state_T(dba_ctx* ctx, const double* cams, const double* pts,
 
 // Copies given as absolute values are stored as offsets from the consensus;
 // duals (r, s) are stored scaled by 1/rho.  NULL copies = consensus, NULL duals = 0.
-dba_status upload_state(dba_ctx* ctx, const double* cams, const double* pts, const double* copies,
+dba_status upload_state(dba_ctx* ctx, const double* cams, const double* pts_caller, const double* copies,
                         const double* duals) {
   const long long l = ctx->n_obs;
+  std::vector<double> pts_int(3 * (size_t)ctx->n_pts);
+  for (int k = 0; k < ctx->n_pts; ++k)
+    for (int c = 0; c < 3; ++c) pts_int[3 * (size_t)k + c] = pts_caller[3 * (size_t)ctx->pt_perm[k] + c];
+  const double* pts = pts_int.data();
   std::vector<double> hdel(9 * (size_t)l, 0.0), hdual(9 * (size_t)l, 0.0);
   if (copies || duals) {
     for (long long o = 0; o < l; ++o) {
@@ -463,6 +490,8 @@ dba_status dba_set_observations(dba_ctx* ctx, int32_t n_cams, int32_t n_pts, int
     return ctx->fail(DBA_EINVAL, "dba_set_observations: n_cams, n_pts and n_obs must be positive");
   if (n_obs > (int64_t)0x7fffffff)
     return ctx->fail(DBA_EINVAL, "dba_set_observations: at most 2^31-1 observations");
+  if (n_cams > dba::kCamMask)
+    return ctx->fail(DBA_EINVAL, "dba_set_observations: at most 16,777,215 cameras");
   if (!pt_idx || !cam_idx || !z || !cams0 || !pts0)
     return ctx->fail(DBA_EINVAL, "dba_set_observations: null array");
   for (int64_t o = 0; o < n_obs; ++o)
@@ -482,6 +511,7 @@ dba_status dba_set_observations(dba_ctx* ctx, int32_t n_cams, int32_t n_pts, int
   ctx->n_pts = n_pts;
   ctx->n_obs = n_obs;
   ctx->perm = std::move(L.perm);
+  ctx->pt_perm = L.pt_perm;
   ctx->h_obs_pt = L.obs_pt;
   ctx->h_obs_cam = L.obs_cam;
   ctx->n_pseg = (int64_t)L.pseg.size();
@@ -490,20 +520,16 @@ dba_status dba_set_observations(dba_ctx* ctx, int32_t n_cams, int32_t n_pts, int
   P.n_cams = n_cams;
   P.n_pts = n_pts;
   P.n_obs = n_obs;
-  P.n_tiles = (int)L.tile_off.size() - 1;
+  P.n_tiles = (int)L.tiles.size();
   P.tile_obs = NT;
   P.n_cam_slots = L.n_cam_slots;
   P.n_pt_slots = L.n_pt_slots;
   P.n_split_pts = (int)L.split_pt.size();
   DBA_CUDA(ctx->upload(&P.obs_pt, L.obs_pt), "upload");
-  DBA_CUDA(ctx->upload(&P.obs_cam, L.obs_cam), "upload");
-  DBA_CUDA(ctx->upload(&P.cam_rank, L.cam_rank), "upload");
-  DBA_CUDA(ctx->upload(&P.tile_off, L.tile_off), "upload");
-  DBA_CUDA(ctx->upload(&P.tile_pseg_off, L.tile_pseg_off), "upload");
+  DBA_CUDA(ctx->upload(&P.obs_cam_rank, L.obs_cam_rank), "upload");
+  DBA_CUDA(ctx->upload(&P.tiles, L.tiles), "upload");
   DBA_CUDA(ctx->upload(&P.pseg, L.pseg), "upload");
-  DBA_CUDA(ctx->upload(&P.pseg_pt, L.pseg_pt), "upload");
   DBA_CUDA(ctx->upload(&P.pseg_slot, L.pseg_slot), "upload");
-  DBA_CUDA(ctx->upload(&P.tile_cseg_off, L.tile_cseg_off), "upload");
   DBA_CUDA(ctx->upload(&P.cseg, L.cseg), "upload");
   DBA_CUDA(ctx->upload(&P.cseg_slot, L.cseg_slot), "upload");
   DBA_CUDA(ctx->upload(&P.cam_slot_off, L.cam_slot_off), "upload");
@@ -569,7 +595,11 @@ dba_status dba_set_ground_truth(dba_ctx* ctx, const double* cams_gt, const doubl
   DBA_CUDA(cudaMallocAsync(&dc, 6 * (size_t)ctx->n_cams * sizeof(double), st), "alloc");
   DBA_CUDA(cudaMallocAsync(&dp, 3 * (size_t)ctx->n_pts * sizeof(double), st), "alloc");
   DBA_CUDA(cudaMemcpyAsync(dc, cams_gt, 6 * (size_t)ctx->n_cams * sizeof(double), cudaMemcpyHostToDevice, st), "upload");
-  DBA_CUDA(cudaMemcpyAsync(dp, pts_gt, 3 * (size_t)ctx->n_pts * sizeof(double), cudaMemcpyHostToDevice, st), "upload");
+  std::vector<double> pts_int(3 * (size_t)ctx->n_pts);
+  for (int k = 0; k < ctx->n_pts; ++k)
+    for (int c = 0; c < 3; ++c) pts_int[3 * (size_t)k + c] = pts_gt[3 * (size_t)ctx->pt_perm[k] + c];
+  DBA_CUDA(cudaMemcpyAsync(dp, pts_int.data(), pts_int.size() * sizeof(double), cudaMemcpyHostToDevice, st),
+           "upload");
   void* zt = const_cast<void*>(ctx->P.zt);
   if (!zt) {
     char* p = nullptr;
@@ -658,13 +688,17 @@ dba_status dba_get_params(dba_ctx* ctx, double* cams, double* pts) {
   if (!ctx) return DBA_EINVAL;
   if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_get_params before dba_set_observations");
   cudaStream_t st = ctx->stream;
+  std::vector<double> X(3 * (size_t)ctx->n_pts);
   if (cams)
     DBA_CUDA(cudaMemcpyAsync(cams, ctx->P.Y[ctx->cur], 6 * (size_t)ctx->n_cams * sizeof(double),
                              cudaMemcpyDeviceToHost, st), "read cameras");
   if (pts)
-    DBA_CUDA(cudaMemcpyAsync(pts, ctx->P.X[ctx->cur], 3 * (size_t)ctx->n_pts * sizeof(double),
-                             cudaMemcpyDeviceToHost, st), "read points");
+    DBA_CUDA(cudaMemcpyAsync(X.data(), ctx->P.X[ctx->cur], X.size() * sizeof(double), cudaMemcpyDeviceToHost, st),
+             "read points");
   DBA_CUDA(cudaStreamSynchronize(st), "get_params");
+  if (pts)
+    for (int k = 0; k < ctx->n_pts; ++k)
+      for (int c = 0; c < 3; ++c) pts[3 * (size_t)ctx->pt_perm[k] + c] = X[3 * (size_t)k + c];
   return DBA_OK;
 }
 

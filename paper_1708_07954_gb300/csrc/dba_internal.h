@@ -11,7 +11,7 @@ namespace dba {
 // captured CUDA graph serves every iteration: which consensus buffer is
 // current, whether the previous iteration's dual ascent (Eqs. 12-13) is still
 // to be applied, and a sticky error flag.
-struct DevCtl {
+struct alignas(16) DevCtl {
   int cur;          // index (0/1) of the current consensus buffer
   int pending;      // 1: copies are offsets from the previous consensus, duals lag by one step
   int err;          // bit 0: non-finite local solve
@@ -19,6 +19,12 @@ struct DevCtl {
   unsigned long long k;   // iterations run
   unsigned int done;      // finalize-kernel block counter
   unsigned int pad2;
+};
+
+// One tile of the observation layout: observations [o0, o0 + n), point runs
+// [r0, r0 + nr) covering internal points [pt_lo, pt_lo + nr), camera runs [c0, c0 + nc).
+struct alignas(16) TileInfo {
+  int o0, n, r0, nr, c0, nc, pt_lo, pad;
 };
 
 struct Params {
@@ -39,18 +45,14 @@ struct DevProblem {
   int tile_obs;                 // block size of the tile kernel
   int n_cam_slots, n_pt_slots, n_split_pts;
   // static structure
-  const int* obs_pt;            // [l]
-  const int* obs_cam;           // [l]
+  const int* obs_pt;            // [l] internal point id
+  const int* obs_cam_rank;      // [l] camera | (position in the tile's camera order) << 24
   const void* z;                // [l] float2 (FP32 path) or double2 (FP64 path)
   const void* zt;               // [l] same type: ground-truth projections, or nullptr
   const unsigned char* inlier;  // [l] 1: counted in rmse_gt (nullptr: all)
-  const unsigned char* cam_rank;// [l] position of the observation in its tile's camera order
-  const int* tile_off;          // [n_tiles+1]
-  const int* tile_pseg_off;     // [n_tiles+1]
+  const TileInfo* tiles;        // [n_tiles]
   const int2* pseg;             // (start, length) of each point run inside its tile
-  const int* pseg_pt;           // point of each run
   const int* pseg_slot;         // -1: the whole track is in this tile; else partial slot
-  const int* tile_cseg_off;     // [n_tiles+1]
   const int2* cseg;             // (start, length) of each camera run in the tile's camera order
   const int* cseg_slot;         // partial slot of each camera run
   const int* cam_slot_off;      // [m+1] camera -> its partial slots
@@ -74,8 +76,13 @@ struct DevProblem {
   DevCtl* ctl;
 };
 
+constexpr int kCamMask = 0xffffff;  // camera index bits of obs_cam_rank
 constexpr int kMetricBlocks = 1024;
 constexpr int kMetricThreads = 256;
+
+// One-time kernel set-up on the current device (shared-memory opt-in, occupancy); call
+// before any stream capture.
+cudaError_t prepare_tile_kernels();
 
 // Kernel launchers (return the launch error).  fp32 selects the FP32 local-solve path.
 cudaError_t launch_tile_iterate(const DevProblem& P, const Params& prm, bool fp32, cudaStream_t s);

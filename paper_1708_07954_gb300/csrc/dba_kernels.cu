@@ -182,8 +182,8 @@ __device__ __forceinline__ T local_objective(const T d[9], const T a[9], const P
 // 9x9 factorisation.  Accept/reject and the damping schedule follow the
 // Levenberg rule: accept iff the trial is in front of the camera and lowers
 // Eq. (9).  A step whose predicted decrease is below the objective's rounding
-// noise is accepted without the comparison (model_tol).  d (offset from vbar)
-// is updated in place.
+// noise is accepted without the comparison (model_tol) and the objective is
+// carried as its model value.  d (offset from vbar) is updated in place.
 template <typename T>
 __device__ __forceinline__ void local_solve(T z0, T z1, const T vbar[9], const T a[9], T d[9],
                                             const Prm<T>& q) {
@@ -268,16 +268,16 @@ __device__ __forceinline__ void local_solve(T z0, T z1, const T vbar[9], const T
     const T y0 = (S11 * t0 - S01 * t1) * idet;
     const T y1 = (S00 * t1 - S01 * t0) * idet;
     T stp[9];
-    T Js0 = 0, Js1 = 0, pred = 0;
+    T gs = 0, ss = 0;
 #pragma unroll
     for (int c = 0; c < 9; ++c) {
       const T iD = c < 3 ? iDx : (c < 6 ? iDa : iDy);
       stp[c] = -qv[c] + tw * iD * (J0[c] * y0 + J1[c] * y1);
-      Js0 += J0[c] * stp[c];
-      Js1 += J1[c] * stp[c];
-      pred -= g[c] * stp[c] + T(0.5) * q.rho(c) * stp[c] * stp[c];
+      gs += g[c] * stp[c];
+      ss += stp[c] * stp[c];
     }
-    pred -= w * (Js0 * Js0 + Js1 * Js1);  // decrease of the Gauss-Newton model
+    // decrease of the Gauss-Newton model; with (H + lambda I) s = -g it is (lambda s.s - g.s) / 2
+    const T pred = T(0.5) * (lambda * ss - gs);
     bool trust = false;
     if (P.valid && q.model_tol > T(0)) {
       // below the rounding noise of L the objective comparison is arbitrary: trust the model
@@ -293,13 +293,15 @@ __device__ __forceinline__ void local_solve(T z0, T z1, const T vbar[9], const T
     }
     Pose<T> Pt;
     pose_at(vt, q.eps, Pt);
-    const T Lt = local_objective(dt, a, Pt, z0, z1, q);
+    // a trusted step carries the objective as its model value L - pred
+    const T Lt = trust ? L - pred : local_objective(dt, a, Pt, z0, z1, q);
     if (Pt.valid && (trust || Lt < L)) {
 #pragma unroll
       for (int c = 0; c < 9; ++c) d[c] = dt[c];
       P = Pt;
       L = Lt;
-      lambda = lambda * T(0.1) > q.lambda_min ? lambda * T(0.1) : q.lambda_min;
+      const T lr = Num<T>::div(lambda, T(10));
+      lambda = lr > q.lambda_min ? lr : q.lambda_min;
     } else {
       lambda *= T(10);
     }
@@ -307,45 +309,117 @@ __device__ __forceinline__ void local_solve(T z0, T z1, const T vbar[9], const T
 }
 
 // ------------------------------------------------------------ tile kernel
-// One block per tile, one thread per observation.
+// Persistent, software-pipelined: each block walks tiles blockIdx.x,
+// blockIdx.x + gridDim.x, ... and while it computes one tile the copies, duals,
+// pixels and indices of its next tile stream into shared memory with cp.async
+// (no registers hold loads in flight), so DRAM latency hides behind the local
+// solves.  One thread per observation of a tile.
 //
 // Steady state: after any full iteration the scaled duals of every point and
 // camera sum to zero (sum of Eq. 12 over a track after Eq. 10; the oracle's
 // tests pin this), so Eq. (10)/(11) reduce to consensus + mean of the new
 // offsets.  Those offsets are summed per run in T inside the tile and in FP64
 // across tiles and into the consensus; the dual ascent itself is FP64.  In the
-// first iteration after dba_set_state (ctl->exact) the duals are arbitrary and
-// the summands offset + dual are formed and summed in FP64.
+// first iteration after dba_set_state (exact) the duals are arbitrary and the
+// summands offset + dual are formed and summed in FP64.
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+  const unsigned int s = static_cast<unsigned int>(__cvta_generic_to_shared(smem));
+  if constexpr (BYTES == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 template <typename T, int NT>
-__global__ void __launch_bounds__(NT) tile_iterate_kernel(DevProblem P, Prm<T> q) {
+struct TileStage {
+  T delta[9][NT];
+  double adual[9][NT];
+  typename Num<T>::V2 z[NT];
+  int pt[NT];
+  int cam[NT];       // camera | rank << 24
+  double X[3 * NT];  // FP64 consensus of the tile's points (contiguous internal ids)
+  int2 pseg[NT];
+  int pslot[NT];
+  int2 cseg[NT];
+  int cslot[NT];
+};
+
+template <typename T, int NT>
+constexpr size_t tile_smem_bytes() {
+  return 2 * sizeof(TileStage<T, NT>) + sizeof(double) * 9 * NT;
+}
+
+__device__ __forceinline__ TileInfo load_tile_info(const TileInfo* tiles, int tile) {
+  const int4* p = reinterpret_cast<const int4*>(tiles + tile);
+  const int4 a = __ldg(p), b = __ldg(p + 1);
+  TileInfo ti;
+  ti.o0 = a.x; ti.n = a.y; ti.r0 = a.z; ti.nr = a.w;
+  ti.c0 = b.x; ti.nc = b.y; ti.pt_lo = b.z; ti.pad = b.w;
+  return ti;
+}
+
+// Issues (and commits) the asynchronous copies of one tile into stage S.
+template <typename T, int NT>
+__device__ __forceinline__ void stage_tile(const DevProblem& P, TileStage<T, NT>& S, const TileInfo& ti,
+                                           int cur) {
   using V2 = typename Num<T>::V2;
-  __shared__ double s_buf[9][NT];
-  const int tile = blockIdx.x;
+  const int t = threadIdx.x;
+  if (t < ti.n) {
+    const long long l = P.n_obs, o = (long long)ti.o0 + t;
+    const T* delta = static_cast<const T*>(P.delta);
+#pragma unroll
+    for (int c = 0; c < 9; ++c) cp_async<sizeof(T)>(&S.delta[c][t], delta + c * l + o);
+#pragma unroll
+    for (int c = 0; c < 9; ++c) cp_async<8>(&S.adual[c][t], P.adual + c * l + o);
+    cp_async<sizeof(V2)>(&S.z[t], static_cast<const V2*>(P.z) + o);
+    cp_async<4>(&S.pt[t], P.obs_pt + o);
+    cp_async<4>(&S.cam[t], P.obs_cam_rank + o);
+  }
+  if (t < ti.nr) {
+    cp_async<8>(&S.pseg[t], P.pseg + ti.r0 + t);
+    cp_async<4>(&S.pslot[t], P.pseg_slot + ti.r0 + t);
+  }
+  if (t < ti.nc) {
+    cp_async<8>(&S.cseg[t], P.cseg + ti.c0 + t);
+    cp_async<4>(&S.cslot[t], P.cseg_slot + ti.c0 + t);
+  }
+  const double* X = P.X[cur] + 3 * (long long)ti.pt_lo;
+  for (int e = t; e < 3 * ti.nr; e += NT) cp_async<8>(&S.X[e], X + e);
+  cp_async_commit();
+}
+
+// One tile from its staged inputs: deferred dual ascent, local solves, run sums.
+template <typename T, int NT>
+__device__ __forceinline__ void process_tile(const DevProblem& P, const Prm<T>& q, const TileStage<T, NT>& S,
+                                             double (*s_buf)[NT], const TileInfo& ti, int cur, int pending,
+                                             int exact) {
   const int t = threadIdx.x;
   const long long l = P.n_obs;
-  const int o0 = P.tile_off[tile], o1 = P.tile_off[tile + 1];
-  const int o = o0 + t;
-  const volatile DevCtl* ctl = P.ctl;
-  const int cur = ctl->cur;
-  const int pending = ctl->pending;
-  const int exact = ctl->exact;
-  T* delta = static_cast<T*>(P.delta);
-  const T* Xm = static_cast<const T*>(P.Xm);
-  const T* Ym = static_cast<const T*>(P.Ym);
-  const T* DX = static_cast<const T*>(P.DX);
-  const T* DY = static_cast<const T*>(P.DY);
+  const long long o = (long long)ti.o0 + t;
+  T* __restrict__ delta = static_cast<T*>(P.delta);
+  double* __restrict__ adual = P.adual;
+  const T* __restrict__ Xm = static_cast<const T*>(P.Xm);
+  const T* __restrict__ Ym = static_cast<const T*>(P.Ym);
+  const T* __restrict__ DX = static_cast<const T*>(P.DX);
+  const T* __restrict__ DY = static_cast<const T*>(P.DY);
   T(*s_t)[NT] = reinterpret_cast<T(*)[NT]>(&s_buf[0][0]);  // T view: row c at s_t[c]
 
-  if (o < o1) {
-    const int i = P.obs_pt[o], j = P.obs_cam[o];
-    const V2 zz = static_cast<const V2*>(P.z)[o];
+  if (t < ti.n) {
+    const int i = S.pt[t];
+    const int cr = S.cam[t];
+    const int j = cr & kCamMask, rk = (int)((unsigned int)cr >> 24);
     T d[9], vbar[9], aT[9];
-#pragma unroll
-    for (int c = 0; c < 9; ++c) d[c] = delta[c * l + o];
 #pragma unroll
     for (int c = 0; c < 3; ++c) vbar[c] = Xm[3 * i + c];
 #pragma unroll
     for (int c = 0; c < 6; ++c) vbar[3 + c] = Ym[6 * j + c];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) d[c] = S.delta[c][t];
     if (pending) {
       // Eqs. (12)-(13) of the previous iteration: the copy relative to the new
       // consensus is d0 = delta + (old - new consensus); a += d0 in FP64.
@@ -355,14 +429,15 @@ __global__ void __launch_bounds__(NT) tile_iterate_kernel(DevProblem P, Prm<T> q
       for (int c = 0; c < 6; ++c) d[3 + c] += DY[6 * j + c];
 #pragma unroll
       for (int c = 0; c < 9; ++c) {
-        const double a = P.adual[c * l + o] + to_f64<T>(d[c]);
-        P.adual[c * l + o] = a;
+        const double a = S.adual[c][t] + to_f64<T>(d[c]);
+        adual[c * l + o] = a;
         aT[c] = from_f64<T>(a);
       }
     } else {
 #pragma unroll
-      for (int c = 0; c < 9; ++c) aT[c] = from_f64<T>(P.adual[c * l + o]);
+      for (int c = 0; c < 9; ++c) aT[c] = from_f64<T>(S.adual[c][t]);
     }
+    const typename Num<T>::V2 zz = S.z[t];
     local_solve<T>(zz.x, zz.y, vbar, aT, d, q);
     bool finite = true;
 #pragma unroll
@@ -371,11 +446,11 @@ __global__ void __launch_bounds__(NT) tile_iterate_kernel(DevProblem P, Prm<T> q
       finite = finite && isfinite(d[c]);
     }
     if (!finite) atomicOr(&P.ctl->err, 1);
-    const int rk = P.cam_rank[o];
     if (exact) {
+      // first iteration after dba_set_state: full summands offset + dual (pending is 0 then)
 #pragma unroll
       for (int c = 0; c < 9; ++c) {
-        const double v = to_f64<T>(d[c]) + P.adual[c * l + o];
+        const double v = to_f64<T>(d[c]) + S.adual[c][t];
         if (c < 3) s_buf[c][t] = v; else s_buf[c][rk] = v;
       }
     } else {
@@ -387,52 +462,81 @@ __global__ void __launch_bounds__(NT) tile_iterate_kernel(DevProblem P, Prm<T> q
   }
   __syncthreads();
 
-  // Eq. (10): per point run, one thread per (run, coordinate).
+  // Eq. (10): per point run, one thread per (run, coordinate); run r is point pt_lo + r.
   const int nxt = cur ^ 1;
-  {
-    const int r0 = P.tile_pseg_off[tile], nr = P.tile_pseg_off[tile + 1] - r0;
-    for (int task = t; task < 3 * nr; task += NT) {
-      const int r = r0 + task / 3, c = task % 3;
-      const int2 se = P.pseg[r];
-      double sum;
-      if (exact) {
-        sum = 0.0;
-        for (int e = se.x; e < se.x + se.y; ++e) sum += s_buf[c][e];
-      } else {
-        T acc = 0;
-        for (int e = se.x; e < se.x + se.y; ++e) acc += s_t[c][e];
-        sum = to_f64<T>(acc);
-      }
-      const int slot = P.pseg_slot[r];
-      if (slot < 0) {
-        const int pt = P.pseg_pt[r];
-        const double xo = P.X[cur][3 * pt + c];
-        const double xn = xo + sum / (double)se.y;
-        P.X[nxt][3 * pt + c] = xn;
-        static_cast<T*>(P.Xm)[3 * pt + c] = (T)xn;
-        static_cast<T*>(P.DX)[3 * pt + c] = (T)(xo - xn);
-      } else {
-        P.pt_part[3 * slot + c] = sum;
-      }
+  for (int task = t; task < 3 * ti.nr; task += NT) {
+    const int r = task / 3, c = task % 3;
+    const int2 se = S.pseg[r];
+    double sum;
+    if (exact) {
+      sum = 0.0;
+      for (int e = se.x; e < se.x + se.y; ++e) sum += s_buf[c][e];
+    } else {
+      T acc = 0;
+      for (int e = se.x; e < se.x + se.y; ++e) acc += s_t[c][e];
+      sum = to_f64<T>(acc);
+    }
+    const int slot = S.pslot[r];
+    if (slot < 0) {
+      const long long k = 3 * ((long long)ti.pt_lo + r) + c;
+      const double xo = S.X[task];
+      const double xn = xo + sum / (double)se.y;
+      P.X[nxt][k] = xn;
+      static_cast<T*>(P.Xm)[k] = (T)xn;
+      static_cast<T*>(P.DX)[k] = (T)(xo - xn);
+    } else {
+      P.pt_part[3 * slot + c] = sum;
     }
   }
   // Eq. (11): per camera run, partial sums for the finalize kernel.
-  {
-    const int r0 = P.tile_cseg_off[tile], nr = P.tile_cseg_off[tile + 1] - r0;
-    for (int task = t; task < 6 * nr; task += NT) {
-      const int r = r0 + task / 6, c = task % 6;
-      const int2 se = P.cseg[r];
-      double sum;
-      if (exact) {
-        sum = 0.0;
-        for (int e = se.x; e < se.x + se.y; ++e) sum += s_buf[3 + c][e];
-      } else {
-        T acc = 0;
-        for (int e = se.x; e < se.x + se.y; ++e) acc += s_t[3 + c][e];
-        sum = to_f64<T>(acc);
-      }
-      P.cam_part[6 * P.cseg_slot[r] + c] = sum;
+  for (int task = t; task < 6 * ti.nc; task += NT) {
+    const int r = task / 6, c = task % 6;
+    const int2 se = S.cseg[r];
+    double sum;
+    if (exact) {
+      sum = 0.0;
+      for (int e = se.x; e < se.x + se.y; ++e) sum += s_buf[3 + c][e];
+    } else {
+      T acc = 0;
+      for (int e = se.x; e < se.x + se.y; ++e) acc += s_t[3 + c][e];
+      sum = to_f64<T>(acc);
     }
+    P.cam_part[6 * S.cslot[r] + c] = sum;
+  }
+}
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT, 2) tile_iterate_kernel(DevProblem P, Prm<T> q) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TileStage<T, NT>* stage = reinterpret_cast<TileStage<T, NT>*>(smem_raw);
+  double(*s_buf)[NT] = reinterpret_cast<double(*)[NT]>(smem_raw + 2 * sizeof(TileStage<T, NT>));
+  // The control word is written by the previous kernel and constant during this one: one
+  // read-only-cache load per thread (cached per SM) instead of same-address L2 traffic.
+  const int4 ctl = __ldg(reinterpret_cast<const int4*>(P.ctl));
+  const int cur = ctl.x, pending = ctl.y, exact = ctl.w;
+  int tile = blockIdx.x;
+  if (tile >= P.n_tiles) return;
+  TileInfo info = load_tile_info(P.tiles, tile);
+  stage_tile<T, NT>(P, stage[0], info, cur);
+  int next = tile + gridDim.x;
+  TileInfo info_next{};
+  if (next < P.n_tiles) info_next = load_tile_info(P.tiles, next);
+  for (int k = 0; tile < P.n_tiles; ++k) {
+    if (next < P.n_tiles)
+      stage_tile<T, NT>(P, stage[(k + 1) & 1], info_next, cur);
+    else
+      cp_async_commit();  // empty group keeps the wait count uniform
+    const int after = next + gridDim.x;
+    TileInfo info_after{};
+    if (after < P.n_tiles) info_after = load_tile_info(P.tiles, after);  // used two tiles later
+    cp_async_wait<1>();    // this thread's copies of the current tile have landed
+    __syncthreads();       // ... and everyone else's
+    process_tile<T, NT>(P, q, stage[k & 1], s_buf, info, cur, pending, exact);
+    __syncthreads();       // stage and run buffers are free for reuse
+    tile = next;
+    next = after;
+    info = info_next;
+    info_next = info_after;
   }
 }
 
@@ -442,8 +546,7 @@ constexpr int kFinThreads = 128;
 template <typename T>
 __global__ void __launch_bounds__(kFinThreads) finalize_kernel(DevProblem P) {
   __shared__ double red[6][kFinThreads];
-  const volatile DevCtl* ctl = P.ctl;
-  const int cur = ctl->cur, nxt = cur ^ 1;
+  const int cur = __ldg(&P.ctl->cur), nxt = cur ^ 1;
   const int b = blockIdx.x, t = threadIdx.x;
   const bool is_cam = b < P.n_cams;
   const int nc = is_cam ? 6 : 3;
@@ -511,7 +614,7 @@ __global__ void __launch_bounds__(kMetricThreads) metrics_kernel(DevProblem P, P
   double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (long long o = blockIdx.x * (long long)kMetricThreads + threadIdx.x; o < l;
        o += (long long)gridDim.x * kMetricThreads) {
-    const int i = P.obs_pt[o], j = P.obs_cam[o];
+    const int i = P.obs_pt[o], j = P.obs_cam_rank[o] & kCamMask;
     T v[9];
 #pragma unroll
     for (int c = 0; c < 3; ++c) v[c] = Xm[3 * i + c];
@@ -585,7 +688,7 @@ __global__ void settle_kernel(DevProblem P) {
   const T* DY = static_cast<const T*>(P.DY);
   for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < l;
        o += (long long)gridDim.x * blockDim.x) {
-    const int i = P.obs_pt[o], j = P.obs_cam[o];
+    const int i = P.obs_pt[o], j = P.obs_cam_rank[o] & kCamMask;
 #pragma unroll
     for (int c = 0; c < 9; ++c) {
       const T d = delta[c * l + o] + (c < 3 ? DX[3 * i + c] : DY[6 * j + c - 3]);
@@ -602,7 +705,7 @@ __global__ void project_truth_kernel(DevProblem P, Prm<double> q, const double* 
   const long long l = P.n_obs;
   for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < l;
        o += (long long)gridDim.x * blockDim.x) {
-    const int i = P.obs_pt[o], j = P.obs_cam[o];
+    const int i = P.obs_pt[o], j = P.obs_cam_rank[o] & kCamMask;
     double v[9];
     for (int c = 0; c < 3; ++c) v[c] = pts[3 * i + c];
     for (int c = 0; c < 6; ++c) v[3 + c] = cams[6 * j + c];
@@ -696,26 +799,67 @@ int grid_for(long long n, int threads, int cap) {
 
 }  // namespace
 
+namespace {
+// Persistent grid of the pipelined tile kernel: resident blocks per SM times SMs, set up
+// once per instantiation (dynamic shared memory opt-in, occupancy query).
+template <typename T, int NT>
+cudaError_t tile_grid(int* grid) {
+  static int cached = 0;
+  if (!cached) {
+    const int smem = (int)tile_smem_bytes<T, NT>();
+    cudaError_t e = cudaFuncSetAttribute(tile_iterate_kernel<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, dev = 0, sms = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tile_iterate_kernel<T, NT>, NT, smem);
+    if (e != cudaSuccess) return e;
+    e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    cached = (per_sm > 0 ? per_sm : 1) * sms;
+  }
+  *grid = cached;
+  return cudaSuccess;
+}
+
+template <typename T, int NT>
+cudaError_t launch_tile(const DevProblem& P, const Params& prm, cudaStream_t s) {
+  int grid = 0;
+  const cudaError_t e = tile_grid<T, NT>(&grid);
+  if (e != cudaSuccess) return e;
+  if (grid > P.n_tiles) grid = P.n_tiles;
+  tile_iterate_kernel<T, NT><<<grid, NT, tile_smem_bytes<T, NT>(), s>>>(P, make_prm<T>(prm));
+  return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t prepare_tile_kernels() {
+  int g = 0;
+  cudaError_t e;
+  if ((e = tile_grid<float, 256>(&g)) != cudaSuccess) return e;
+  if ((e = tile_grid<float, 128>(&g)) != cudaSuccess) return e;
+  if ((e = tile_grid<float, 64>(&g)) != cudaSuccess) return e;
+  if ((e = tile_grid<double, 256>(&g)) != cudaSuccess) return e;
+  if ((e = tile_grid<double, 128>(&g)) != cudaSuccess) return e;
+  return tile_grid<double, 64>(&g);
+}
+
 cudaError_t launch_tile_iterate(const DevProblem& P, const Params& prm, bool fp32, cudaStream_t s) {
   if (P.n_tiles == 0) return cudaSuccess;
   if (fp32) {
-    const Prm<float> q = make_prm<float>(prm);
     switch (P.tile_obs) {
-      case 256: tile_iterate_kernel<float, 256><<<P.n_tiles, 256, 0, s>>>(P, q); break;
-      case 128: tile_iterate_kernel<float, 128><<<P.n_tiles, 128, 0, s>>>(P, q); break;
-      case 64: tile_iterate_kernel<float, 64><<<P.n_tiles, 64, 0, s>>>(P, q); break;
-      default: return cudaErrorInvalidValue;
-    }
-  } else {
-    const Prm<double> q = make_prm<double>(prm);
-    switch (P.tile_obs) {
-      case 256: tile_iterate_kernel<double, 256><<<P.n_tiles, 256, 0, s>>>(P, q); break;
-      case 128: tile_iterate_kernel<double, 128><<<P.n_tiles, 128, 0, s>>>(P, q); break;
-      case 64: tile_iterate_kernel<double, 64><<<P.n_tiles, 64, 0, s>>>(P, q); break;
+      case 256: return launch_tile<float, 256>(P, prm, s);
+      case 128: return launch_tile<float, 128>(P, prm, s);
+      case 64: return launch_tile<float, 64>(P, prm, s);
       default: return cudaErrorInvalidValue;
     }
   }
-  return cudaGetLastError();
+  switch (P.tile_obs) {
+    case 256: return launch_tile<double, 256>(P, prm, s);
+    case 128: return launch_tile<double, 128>(P, prm, s);
+    case 64: return launch_tile<double, 64>(P, prm, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_finalize(const DevProblem& P, bool fp32, cudaStream_t s) {
