@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--inner-steps", type=int, default=5, help="damped Gauss-Newton steps per local solve")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-0.5-px measurement")
+    ap.add_argument("--ttt-max-iters", type=int, default=400)
     ap.add_argument("--cpu-iters", type=int, default=2)
     ap.add_argument("--profile-iters", type=int, default=200)
     ap.add_argument("--reference-seconds", type=float, default=90.0,
@@ -118,6 +120,40 @@ def algorithmic_bytes(scene, layout, fp32):
     total = (per_obs * l + per_point * n + per_cam_run * layout["camera_runs"] + per_cam * m +
              per_tile * layout["tiles"] + 24 * layout["point_slots"])
     return total, per_obs
+
+
+# FP32 operations of the method per observation and ADMM iteration, counted from the
+# tile kernel's arithmetic (add/sub/mul 1, fma 2, rcp/sqrt/sin/cos 1), every Gauss-Newton
+# step counted as a full step with its trial objective:
+#   start: copy + pose + objective 111, first damping 50, deferred dual re-base 9, run sums 9;
+#   per step: linearisation and Jacobian 64, gradient 64, damping reciprocals 6,
+#   capacitance terms 126, 2x2 solve 17, step + model decrease 96, noise bound 7,
+#   trial point 18, trial pose 44, trial objective 58, damping update 1  -> 501.
+FLOPS_START, FLOPS_PER_STEP = 179, 501
+
+# 152 SMs x 128 FP32 lanes x 2 flops per FMA x 2.07 GHz (maximum SM clock)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def algorithmic_flops(n_obs, inner_steps):
+    return n_obs * (FLOPS_START + FLOPS_PER_STEP * inner_steps)
+
+
+def ncu_traffic(n_obs):
+    """DRAM bytes per tile_iterate launch from the committed ncu summary, scaled to n_obs,
+    or None when the kernel source changed since the counters were taken."""
+    import hashlib
+
+    try:
+        with open(os.path.join(ROOT, "profiles", "tile_iterate_workload2.json")) as fh:
+            prof = json.load(fh)
+        with open(os.path.join(ROOT, "paper_1708_07954_gb300", "csrc", "dba_kernels.cu"), "rb") as fh:
+            sha = hashlib.sha256(fh.read()).hexdigest()
+    except (OSError, ValueError):
+        return None
+    if prof.get("kernel_source_sha256") != sha:
+        return None
+    return prof["dram_bytes_per_obs"] * n_obs
 
 
 def measured_peaks():
@@ -234,12 +270,19 @@ def run_ours(args, rank, world, local_rank):
     tile_ms = prof["tile_iterate"]
     bytes_launch, per_obs = algorithmic_bytes(sc, layout, fp32)
     peaks, src = measured_peaks()
-    achieved = bytes_launch / (tile_ms * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": "tile_iterate",
-                "kernel_ms": tile_ms, "kernel_share": tile_ms / sum(prof.values()),
-                "algorithmic_bytes_per_launch": bytes_launch, "algorithmic_bytes_per_obs": per_obs,
-                "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback",
+    flops = algorithmic_flops(sc.n_obs, args.inner_steps)
+    achieved_tf = flops / (tile_ms * 1e-3) / 1e12
+    achieved_gbs = bytes_launch / (tile_ms * 1e-3) / 1e9
+    roofline = {"bound": "alu", "achieved": achieved_tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved_tf / FP32_PEAK_TFLOPS, "traffic": ncu_traffic(sc.n_obs),
+                "kernel": "tile_iterate", "kernel_ms": tile_ms, "kernel_share": tile_ms / sum(prof.values()),
+                "algorithmic_flops_per_launch": flops,
+                "algorithmic_flops_per_obs": FLOPS_START + FLOPS_PER_STEP * args.inner_steps,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (unit counts and maximum clock)",
+                "hbm": {"achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": achieved_gbs / peaks["hbm_gbs"], "algorithmic_bytes_per_launch": bytes_launch,
+                        "algorithmic_bytes_per_obs": per_obs,
+                        "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback"},
                 "kernels_ms": prof}
     solver.close()
 
@@ -260,6 +303,24 @@ def run_ours(args, rank, world, local_rank):
                "d2h_bytes_per_step": d2h / iters, "iters_per_solve": iters, "seconds_per_solve": dt,
                "what": "dba_create + dba_set_observations (host arrays, layout, upload) + dba_iterate("
                        f"{iters}) + dba_get_params, wall clock"}
+
+    ttt = None
+    if not args.no_ttt:
+        # time to rmse_gt <= 0.5 px (noise-free projections, observations of outlier-free tracks),
+        # device time of iterations + per-iteration metrics, each precision from the initial state
+        ttt = {"target_px": 0.5, "rmse": "vs noise-free projections over observations of outlier-free tracks",
+               "max_iters": args.ttt_max_iters}
+        for name, pr in (("fp32_plain", dba.DBA_PREC_F32_LOCAL), ("fp64_plain", dba.DBA_PREC_F64)):
+            with dba.Solver(sc, precision=pr, inner_steps=args.inner_steps, stream=stream.cuda_stream) as s3:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                m = s3.iterate_until(args.ttt_max_iters, 0.5)
+                wall = time.perf_counter() - t0
+            ttt[name] = {"seconds": m["seconds"], "wall_seconds": wall, "iters": m["iters_done"],
+                         "rmse_gt": m["rmse_gt"], "reached": m["rmse_gt"] <= 0.5}
+        ttt["fp32_learned"] = None
+        if ttt["fp32_plain"]["reached"] and ttt["fp64_plain"]["reached"]:
+            ttt["speedup_fp32_plain_vs_fp64_plain"] = ttt["fp64_plain"]["seconds"] / ttt["fp32_plain"]["seconds"]
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -284,7 +345,7 @@ def run_ours(args, rank, world, local_rank):
                        "precision": "f32 local solves, f64 consensus/duals" if fp32 else "f64",
                        "l2": "inputs larger than L2 (~1 GB per iteration), no flush",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "time_to_target": ttt,
             "clocks": clk, "gpu_launches": 2 * args.steps,
             "final": {k: final[k] for k in ("rmse_obs", "rmse_gt", "objective", "iters_done")},
         }
