@@ -77,7 +77,10 @@ typedef struct {
                              is accepted without comparing objective values; 0 = always
                              compare */
   int precision;          /* dba_precision */
-  int tile_obs;           /* observations per tile (32..256, multiple of 32); 0 = automatic */
+  int tile_obs;           /* observations per tile and thread block: 64, 128 or 256; 0 = by
+                             precision (256 FP32-local, 128 FP64); -1 = autotune: time each
+                             size on the problem at dba_set_observations and keep the fastest
+                             (cached per process by precision, size and mean track length) */
   int use_graph;          /* 1: replay each iteration as a CUDA graph; 0: plain launches */
   void* cuda_stream;      /* cudaStream_t to launch on; NULL = a stream owned by the context */
 } dba_config;
@@ -121,6 +124,21 @@ dba_status dba_set_observations(dba_ctx* ctx, int32_t n_cams, int32_t n_pts, int
  * observations whose pixel is an outlier rather than a noisy measurement. */
 dba_status dba_set_ground_truth(dba_ctx* ctx, const double* cams_gt, const double* pts_gt,
                                 const uint8_t* inlier);
+
+/* Declares that the loaded problem is a batch of n_scenes independent scenes:
+ * observations [obs_off[s], obs_off[s+1]) (caller order) use only cameras
+ * [cam_off[s], cam_off[s+1]) and points [pt_off[s], pt_off[s+1]).  The offsets
+ * are nondecreasing, start at 0 and end at n_obs, n_cams, n_pts.  The scenes are
+ * solved together, one tile kernel launch per iteration, with no coupling
+ * (each consensus segment lies inside one scene); this call only enables
+ * dba_scene_stats.  EINVAL if an observation leaves its scene. */
+dba_status dba_set_scenes(dba_ctx* ctx, int32_t n_scenes, const int64_t* obs_off, const int32_t* cam_off,
+                          const int32_t* pt_off);
+
+/* Per-scene metrics at the current consensus after dba_set_scenes: rmse_obs,
+ * rmse_gt (0 without ground truth) and the objective, each [n_scenes]; any
+ * pointer may be NULL. */
+dba_status dba_scene_stats(dba_ctx* ctx, double* rmse_obs, double* rmse_gt, double* objective);
 
 /* Runs n_iters >= 0 ADMM iterations, Eqs. (9)-(13), on the context's stream
  * and waits for them.  stats (nullable) receives the metrics at the final

@@ -7,6 +7,9 @@
 
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -58,6 +61,9 @@ struct dba_ctx {
   std::vector<int> pt_perm;      // internal point -> caller point
   std::vector<int> h_obs_pt, h_obs_cam;
   int64_t n_pseg = 0;
+  int n_scenes = 0;
+  int* d_scene_of_obs = nullptr;   // [l] internal order
+  double* d_scene_sums = nullptr;  // [n_scenes][5]
   std::vector<void*> allocs;
   DevProblem P{};
   int cur = 0, pending = 0;
@@ -82,6 +88,9 @@ struct dba_ctx {
     allocs.clear();
     P = DevProblem{};
     has_problem = has_gt = false;
+    n_scenes = 0;
+    d_scene_of_obs = nullptr;
+    d_scene_sums = nullptr;
     perm.clear();
     pt_perm.clear();
     h_obs_pt.clear();
@@ -281,8 +290,8 @@ dba_status dba_create(const dba_config* cfg, dba_ctx** out) {
                   std::isfinite(cfg->lm_lambda_min) && cfg->lm_lambda_min >= 0 &&
                   std::isfinite(cfg->eps_depth) && std::isfinite(cfg->lm_model_tol) &&
                   cfg->lm_model_tol >= 0 && (cfg->precision == 0 || cfg->precision == 1) &&
-                  (cfg->tile_obs == 0 || cfg->tile_obs == 64 || cfg->tile_obs == 128 ||
-                   cfg->tile_obs == 256);
+                  (cfg->tile_obs == 0 || cfg->tile_obs == -1 || cfg->tile_obs == 64 ||
+                   cfg->tile_obs == 128 || cfg->tile_obs == 256);
   if (!ok) {
     g_create_error = "dba_create: invalid configuration (check focal, loss, rho, steps, precision, tile_obs)";
     return DBA_EINVAL;
@@ -480,31 +489,13 @@ dba_status check_device_flags(dba_ctx* ctx) {
 
 }  // namespace
 
-extern "C" {
+namespace {
 
-dba_status dba_set_observations(dba_ctx* ctx, int32_t n_cams, int32_t n_pts, int64_t n_obs,
-                                const int32_t* pt_idx, const int32_t* cam_idx, const double* z,
-                                const double* cams0, const double* pts0) {
-  if (!ctx) return DBA_EINVAL;
-  if (n_cams <= 0 || n_pts <= 0 || n_obs <= 0)
-    return ctx->fail(DBA_EINVAL, "dba_set_observations: n_cams, n_pts and n_obs must be positive");
-  if (n_obs > (int64_t)0x7fffffff)
-    return ctx->fail(DBA_EINVAL, "dba_set_observations: at most 2^31-1 observations");
-  if (n_cams > dba::kCamMask)
-    return ctx->fail(DBA_EINVAL, "dba_set_observations: at most 16,777,215 cameras");
-  if (!pt_idx || !cam_idx || !z || !cams0 || !pts0)
-    return ctx->fail(DBA_EINVAL, "dba_set_observations: null array");
-  for (int64_t o = 0; o < n_obs; ++o)
-    if (pt_idx[o] < 0 || pt_idx[o] >= n_pts || cam_idx[o] < 0 || cam_idx[o] >= n_cams)
-      return ctx->fail(DBA_EINVAL, "dba_set_observations: observation " + std::to_string(o) +
-                                       " has an index out of range");
-  if (!finite_all(z, 2 * n_obs) || !finite_all(cams0, 6 * (long long)n_cams) ||
-      !finite_all(pts0, 3 * (long long)n_pts))
-    return ctx->fail(DBA_EINVAL, "dba_set_observations: non-finite input value");
-  cudaStreamSynchronize(ctx->stream);
-  ctx->free_problem();
-
-  const int NT = ctx->cfg.tile_obs ? ctx->cfg.tile_obs : (ctx->fp32 ? 256 : 128);
+// Builds the layout for tile size NT, uploads it and the initial state (copies at the
+// initial estimate, zero duals).  Inputs are already validated.
+dba_status load_problem(dba_ctx* ctx, int NT, int32_t n_cams, int32_t n_pts, int64_t n_obs,
+                        const int32_t* pt_idx, const int32_t* cam_idx, const double* z,
+                        const double* cams0, const double* pts0) {
   HostLayout L;
   build_layout(n_cams, n_pts, n_obs, pt_idx, cam_idx, NT, L);
   ctx->n_cams = n_cams;
@@ -581,6 +572,95 @@ dba_status dba_set_observations(dba_ctx* ctx, int32_t n_cams, int32_t n_pts, int
     return s;
   }
   return DBA_OK;
+}
+
+// Tile-size autotuner: times a few iterations per candidate size and keeps the fastest,
+// then reloads the problem with it (so the state is the initial one).  Results are cached
+// per process by precision, problem size (power of two) and mean track length.
+std::mutex g_tune_mutex;
+std::map<std::tuple<int, int, int>, int> g_tune_cache;
+
+dba_status autotune_tile(dba_ctx* ctx, int32_t n_cams, int32_t n_pts, int64_t n_obs, const int32_t* pt_idx,
+                         const int32_t* cam_idx, const double* z, const double* cams0, const double* pts0,
+                         int* best) {
+  int used = 0;
+  {
+    std::vector<char> seen(n_pts, 0);
+    for (int64_t o = 0; o < n_obs; ++o) seen[pt_idx[o]] = 1;
+    for (char c : seen) used += c;
+  }
+  int lg = 0;
+  while ((1ll << (lg + 1)) <= n_obs) ++lg;
+  const int mean_track = (int)std::lround((double)n_obs / std::max(1, used));
+  const auto key = std::make_tuple(ctx->fp32 ? 1 : 0, lg, std::min(mean_track, 64));
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      *best = it->second;
+      return DBA_OK;
+    }
+  }
+  const int candidates[3] = {64, 128, 256};
+  float best_ms = 0.f;
+  *best = ctx->fp32 ? 256 : 128;
+  const int reps = 3;
+  for (int nt : candidates) {
+    dba_status s = load_problem(ctx, nt, n_cams, n_pts, n_obs, pt_idx, cam_idx, z, cams0, pts0);
+    if (s != DBA_OK) return s;
+    s = launch_iteration(ctx);  // warm-up
+    if (s != DBA_OK) return s;
+    DBA_CUDA(cudaEventRecord(ctx->ev0, ctx->stream), "autotune");
+    for (int r = 0; r < reps; ++r) {
+      s = launch_iteration(ctx);
+      if (s != DBA_OK) return s;
+    }
+    DBA_CUDA(cudaEventRecord(ctx->ev1, ctx->stream), "autotune");
+    DBA_CUDA(cudaEventSynchronize(ctx->ev1), "autotune");
+    float ms = 0.f;
+    DBA_CUDA(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1), "autotune");
+    if (best_ms == 0.f || ms < best_ms) {
+      best_ms = ms;
+      *best = nt;
+    }
+    ctx->free_problem();
+  }
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  g_tune_cache[key] = *best;
+  return DBA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dba_status dba_set_observations(dba_ctx* ctx, int32_t n_cams, int32_t n_pts, int64_t n_obs,
+                                const int32_t* pt_idx, const int32_t* cam_idx, const double* z,
+                                const double* cams0, const double* pts0) {
+  if (!ctx) return DBA_EINVAL;
+  if (n_cams <= 0 || n_pts <= 0 || n_obs <= 0)
+    return ctx->fail(DBA_EINVAL, "dba_set_observations: n_cams, n_pts and n_obs must be positive");
+  if (n_obs > (int64_t)0x7fffffff)
+    return ctx->fail(DBA_EINVAL, "dba_set_observations: at most 2^31-1 observations");
+  if (n_cams > dba::kCamMask)
+    return ctx->fail(DBA_EINVAL, "dba_set_observations: at most 16,777,215 cameras");
+  if (!pt_idx || !cam_idx || !z || !cams0 || !pts0)
+    return ctx->fail(DBA_EINVAL, "dba_set_observations: null array");
+  for (int64_t o = 0; o < n_obs; ++o)
+    if (pt_idx[o] < 0 || pt_idx[o] >= n_pts || cam_idx[o] < 0 || cam_idx[o] >= n_cams)
+      return ctx->fail(DBA_EINVAL, "dba_set_observations: observation " + std::to_string(o) +
+                                       " has an index out of range");
+  if (!finite_all(z, 2 * n_obs) || !finite_all(cams0, 6 * (long long)n_cams) ||
+      !finite_all(pts0, 3 * (long long)n_pts))
+    return ctx->fail(DBA_EINVAL, "dba_set_observations: non-finite input value");
+  cudaStreamSynchronize(ctx->stream);
+  ctx->free_problem();
+  int NT = ctx->cfg.tile_obs > 0 ? ctx->cfg.tile_obs : (ctx->fp32 ? 256 : 128);
+  if (ctx->cfg.tile_obs < 0) {
+    dba_status s = autotune_tile(ctx, n_cams, n_pts, n_obs, pt_idx, cam_idx, z, cams0, pts0, &NT);
+    if (s != DBA_OK) return s;
+  }
+  return load_problem(ctx, NT, n_cams, n_pts, n_obs, pt_idx, cam_idx, z, cams0, pts0);
 }
 
 dba_status dba_set_ground_truth(dba_ctx* ctx, const double* cams_gt, const double* pts_gt,
@@ -823,6 +903,63 @@ dba_status dba_evaluate_noalloc(const dba_config* cfg, int32_t n_cams, int32_t n
   if (e != cudaSuccess) {
     g_create_error = std::string("dba_evaluate_noalloc: ") + cudaGetErrorString(e);
     return DBA_ECUDA;
+  }
+  return DBA_OK;
+}
+
+dba_status dba_set_scenes(dba_ctx* ctx, int32_t n_scenes, const int64_t* obs_off, const int32_t* cam_off,
+                          const int32_t* pt_off) {
+  if (!ctx) return DBA_EINVAL;
+  if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_set_scenes before dba_set_observations");
+  if (n_scenes <= 0 || !obs_off || !cam_off || !pt_off) return ctx->fail(DBA_EINVAL, "dba_set_scenes: bad arguments");
+  if (obs_off[0] != 0 || cam_off[0] != 0 || pt_off[0] != 0 || obs_off[n_scenes] != ctx->n_obs ||
+      cam_off[n_scenes] != ctx->n_cams || pt_off[n_scenes] != ctx->n_pts)
+    return ctx->fail(DBA_EINVAL, "dba_set_scenes: offsets must start at 0 and end at n_obs, n_cams, n_pts");
+  for (int sc = 0; sc < n_scenes; ++sc)
+    if (obs_off[sc + 1] < obs_off[sc] || cam_off[sc + 1] < cam_off[sc] || pt_off[sc + 1] < pt_off[sc])
+      return ctx->fail(DBA_EINVAL, "dba_set_scenes: offsets must be nondecreasing");
+  // scene of every caller observation, checked against its camera and point
+  std::vector<int> scene_caller(ctx->n_obs);
+  std::vector<int> cam_scene(ctx->n_cams), pt_scene(ctx->n_pts);
+  for (int sc = 0; sc < n_scenes; ++sc) {
+    for (int64_t o = obs_off[sc]; o < obs_off[sc + 1]; ++o) scene_caller[o] = sc;
+    for (int32_t j = cam_off[sc]; j < cam_off[sc + 1]; ++j) cam_scene[j] = sc;
+    for (int32_t i = pt_off[sc]; i < pt_off[sc + 1]; ++i) pt_scene[i] = sc;
+  }
+  std::vector<int> scene_int(ctx->n_obs);
+  for (long long o = 0; o < ctx->n_obs; ++o) {
+    const long long src = ctx->perm[o];
+    const int sc = scene_caller[src];
+    if (cam_scene[ctx->h_obs_cam[o]] != sc || pt_scene[ctx->pt_perm[ctx->h_obs_pt[o]]] != sc)
+      return ctx->fail(DBA_EINVAL, "dba_set_scenes: observation " + std::to_string(src) + " leaves its scene");
+    scene_int[o] = sc;
+  }
+  const int* d = nullptr;
+  DBA_CUDA(ctx->upload(&d, scene_int), "upload scenes");
+  ctx->d_scene_of_obs = const_cast<int*>(d);
+  DBA_CUDA(ctx->alloc(&ctx->d_scene_sums, 5 * (size_t)n_scenes), "alloc scene sums");
+  DBA_CUDA(cudaStreamSynchronize(ctx->stream), "set_scenes");
+  ctx->n_scenes = n_scenes;
+  return DBA_OK;
+}
+
+dba_status dba_scene_stats(dba_ctx* ctx, double* rmse_obs, double* rmse_gt, double* objective) {
+  if (!ctx) return DBA_EINVAL;
+  if (!ctx->has_problem || ctx->n_scenes == 0)
+    return ctx->fail(DBA_ESTATE, "dba_scene_stats needs dba_set_observations and dba_set_scenes");
+  cudaStream_t st = ctx->stream;
+  std::vector<double> h(5 * (size_t)ctx->n_scenes);
+  DBA_CUDA(cudaMemsetAsync(ctx->d_scene_sums, 0, h.size() * sizeof(double), st), "scene stats");
+  DBA_CUDA(dba::launch_scene_metrics(ctx->P, ctx->prm, ctx->fp32, ctx->d_scene_of_obs, ctx->d_scene_sums, st),
+           "scene stats");
+  DBA_CUDA(cudaMemcpyAsync(h.data(), ctx->d_scene_sums, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st),
+           "scene stats");
+  DBA_CUDA(cudaStreamSynchronize(st), "scene stats");
+  for (int sc = 0; sc < ctx->n_scenes; ++sc) {
+    const double* v = &h[5 * (size_t)sc];
+    if (rmse_obs) rmse_obs[sc] = v[3] > 0 ? std::sqrt(v[0] / v[3]) : 0.0;
+    if (objective) objective[sc] = v[1];
+    if (rmse_gt) rmse_gt[sc] = (ctx->has_gt && v[4] > 0) ? std::sqrt(v[2] / v[4]) : 0.0;
   }
   return DBA_OK;
 }

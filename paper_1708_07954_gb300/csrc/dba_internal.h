@@ -94,6 +94,11 @@ cudaError_t launch_project_truth(const DevProblem& P, const Params& prm, bool fp
                                  const double* cams_gt, const double* pts_gt, void* zt_out,
                                  cudaStream_t s);
 
+// Per-scene metrics: out[5 * scene + k] += (sum e^2, objective, sum gt^2, valid count,
+// gt count) over observations whose internal scene id is `scene` (out zeroed by the caller).
+cudaError_t launch_scene_metrics(const DevProblem& P, const Params& prm, bool fp32, const int* scene_of_obs,
+                                 double* out, cudaStream_t s);
+
 // Allocation-free reprojection statistics (file-scope device scratch; see dba_evaluate_noalloc).
 cudaError_t launch_eval_noalloc(const Params& prm, long long n_obs, int n_cams, int n_pts, const int* pt_idx,
                                 const int* cam_idx, const double* z, const double* cams, const double* pts,

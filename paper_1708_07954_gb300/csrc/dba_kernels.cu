@@ -662,6 +662,59 @@ __global__ void __launch_bounds__(kMetricThreads) metrics_kernel(DevProblem P, P
   if (threadIdx.x < 8) P.metric_part[8 * blockIdx.x + threadIdx.x] = red[threadIdx.x][0];
 }
 
+// Per-scene metrics of a batch: each block walks a contiguous chunk of
+// observations (scene ids are nondecreasing in internal order, so a chunk spans
+// few scenes); a thread accumulates while its scene stays the same and flushes
+// with FP64 atomics when it changes.
+constexpr int kSceneChunk = 4096;
+
+template <typename T>
+__global__ void __launch_bounds__(kMetricThreads)
+scene_metrics_kernel(DevProblem P, Prm<T> q, const int* scene_of_obs, double* out) {
+  using V2 = typename Num<T>::V2;
+  const long long l = P.n_obs;
+  const T* Xm = static_cast<const T*>(P.Xm);
+  const T* Ym = static_cast<const T*>(P.Ym);
+  const long long o0 = (long long)blockIdx.x * kSceneChunk;
+  const long long o1 = o0 + kSceneChunk < l ? o0 + kSceneChunk : l;
+  int scene = -1;
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (long long o = o0 + threadIdx.x; o < o1; o += kMetricThreads) {
+    const int sc = scene_of_obs[o];
+    if (sc != scene) {
+      if (scene >= 0)
+        for (int k = 0; k < 5; ++k) atomicAdd(&out[5 * scene + k], acc[k]);
+      scene = sc;
+      for (int k = 0; k < 5; ++k) acc[k] = 0.0;
+    }
+    const int i = P.obs_pt[o], j = P.obs_cam_rank[o] & kCamMask;
+    T v[9];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) v[c] = Xm[3 * i + c];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) v[3 + c] = Ym[6 * j + c];
+    Pose<T> Q;
+    pose_at(v, q.eps, Q);
+    if (!Q.valid) continue;
+    const V2 zz = static_cast<const V2*>(P.z)[o];
+    const T iz = T(1) / Q.p[2];
+    const T zp0 = q.focal * Q.p[0] * iz + q.cx, zp1 = q.focal * Q.p[1] * iz + q.cy;
+    const T e0 = zz.x - zp0, e1 = zz.y - zp1;
+    const T sq = e0 * e0 + e1 * e1;
+    acc[0] += (double)sq;
+    acc[1] += (double)misfit<T>(q.loss, q.lp, sq);
+    acc[3] += 1.0;
+    if (P.zt && (!P.inlier || P.inlier[o])) {
+      const V2 gt = static_cast<const V2*>(P.zt)[o];
+      const T g0 = zp0 - gt.x, g1 = zp1 - gt.y;
+      acc[2] += (double)(g0 * g0 + g1 * g1);
+      acc[4] += 1.0;
+    }
+  }
+  if (scene >= 0)
+    for (int k = 0; k < 5; ++k) atomicAdd(&out[5 * scene + k], acc[k]);
+}
+
 __global__ void __launch_bounds__(kMetricThreads) metrics_final_kernel(DevProblem P, int nblocks) {
   __shared__ double red[8][kMetricThreads];
   double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -882,6 +935,17 @@ cudaError_t launch_metrics(const DevProblem& P, const Params& prm, bool fp32, in
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   metrics_final_kernel<<<1, kMetricThreads, 0, s>>>(P, g);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scene_metrics(const DevProblem& P, const Params& prm, bool fp32, const int* scene_of_obs,
+                                 double* out, cudaStream_t s) {
+  const int g = (int)((P.n_obs + kSceneChunk - 1) / kSceneChunk);
+  if (g == 0) return cudaSuccess;
+  if (fp32)
+    scene_metrics_kernel<float><<<g, kMetricThreads, 0, s>>>(P, make_prm<float>(prm), scene_of_obs, out);
+  else
+    scene_metrics_kernel<double><<<g, kMetricThreads, 0, s>>>(P, make_prm<double>(prm), scene_of_obs, out);
   return cudaGetLastError();
 }
 

@@ -22,7 +22,8 @@ DBA_PREC_F64, DBA_PREC_F32_LOCAL = 0, 1
 EXPORTED = [
     "dba_config_default", "dba_create", "dba_set_observations", "dba_set_ground_truth", "dba_iterate",
     "dba_iterate_until", "dba_evaluate", "dba_get_params", "dba_get_state", "dba_set_state",
-    "dba_profile", "dba_layout", "dba_evaluate_noalloc", "dba_last_error", "dba_destroy",
+    "dba_profile", "dba_layout", "dba_evaluate_noalloc", "dba_set_scenes", "dba_scene_stats",
+    "dba_last_error", "dba_destroy",
 ]
 DBA_NOALLOC_MAX_OBS = 16777216
 
@@ -88,6 +89,8 @@ def load():
     L.dba_set_state.argtypes = [vp, dp, dp, dp, dp]
     L.dba_profile.argtypes = [vp, ctypes.c_int, P(ctypes.c_char_p), dp, P(ctypes.c_int)]
     L.dba_layout.argtypes = [vp, P(ctypes.c_int64), P(ctypes.c_int)]
+    L.dba_set_scenes.argtypes = [vp, ctypes.c_int32, P(ctypes.c_int64), ip, ip]
+    L.dba_scene_stats.argtypes = [vp, dp, dp, dp]
     L.dba_evaluate_noalloc.argtypes = [P(dba_config), ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, vp, vp, vp,
                                        vp, vp, vp, vp]
     L.dba_last_error.argtypes = [vp]
@@ -218,6 +221,20 @@ def dba_evaluate_noalloc(cfg, n_cams, n_pts, n_obs, pt_idx_ptr, cam_idx_ptr, z_p
                                        cam_idx_ptr, z_ptr, cams_ptr, pts_ptr, out_ptr, stream))
 
 
+def dba_set_scenes(ctx, obs_off, cam_off, pt_off):
+    obs_off = np.ascontiguousarray(obs_off, dtype=np.int64)
+    cam_off = np.ascontiguousarray(cam_off, dtype=np.int32)
+    pt_off = np.ascontiguousarray(pt_off, dtype=np.int32)
+    _check(load().dba_set_scenes(ctx, len(obs_off) - 1, obs_off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                 _ptr(cam_off), _ptr(pt_off)), ctx)
+
+
+def dba_scene_stats(ctx, n_scenes):
+    out = [np.zeros(n_scenes) for _ in range(3)]
+    _check(load().dba_scene_stats(ctx, *[_ptr(a) for a in out]), ctx)
+    return {"rmse_obs": out[0], "rmse_gt": out[1], "objective": out[2]}
+
+
 def dba_last_error(ctx=None) -> str:
     return load().dba_last_error(ctx).decode()
 
@@ -244,6 +261,8 @@ class Solver:
         try:
             dba_set_observations(self.ctx, scene.n_cams, scene.n_pts, scene.pt_idx, scene.cam_idx, scene.z,
                                  scene.cams0, scene.pts0)
+            if getattr(scene, "scene_off", None) is not None:
+                dba_set_scenes(self.ctx, scene.scene_off, scene.cam_off, scene.pt_off)
             if ground_truth:
                 # rmse_gt over observations of outlier-free tracks
                 mask = scene.clean_mask() if hasattr(scene, "clean_mask") else None
@@ -275,6 +294,9 @@ class Solver:
 
     def layout(self):
         return dba_layout(self.ctx)
+
+    def scene_stats(self):
+        return dba_scene_stats(self.ctx, len(self.scene.scene_off) - 1)
 
     def close(self):
         if self.ctx:
