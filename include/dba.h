@@ -209,6 +209,48 @@ dba_status dba_evaluate_noalloc(const dba_config* cfg, int32_t n_cams, int32_t n
                                 const int32_t* pt_idx, const int32_t* cam_idx, const double* z,
                                 const double* cams, const double* pts, double* out, void* stream);
 
+/* ---- Learned warm start (no counterpart in the paper) ------------------------------------
+ * A small network (32-64-64-64-16, GELU in its tanh form) predicts, for every observation, a start for its
+ * local solve (Eq. 9) from the residual, Jacobian, offset and dual at the plain start, all in
+ * coordinates scaled by sqrt(rho).  Inference runs on BF16 tensor cores (tcgen05, FP32
+ * accumulation) before each iteration's local solves; each local solve starts from the
+ * learned candidate only if that lowers Eq. (9) (the Levenberg-Marquardt solve is both the
+ * judge and the fallback).  The network is trained on the GPU by this library's own FP32
+ * forward/backward/Adam kernels on targets harvested from long local solves.  The dba_mlp_*
+ * calls run on a stream of the network that is ordered after work queued on the legacy
+ * default stream and return when done; buffers filled on other streams must be complete. */
+typedef struct dba_mlp dba_mlp;
+#define DBA_MLP_N_PARAMS 11552  /* W1 64x32, b1, W2 64x64, b2, W3 64x64, b3, W4 16x64, b4, input
+                                   mean[32], input std[32], target scale[16] (FP32, row-major) */
+#define DBA_MLP_N_FEATURES 32
+#define DBA_MLP_N_TARGETS 16
+
+/* New network with He-normal weights from `seed`; identity normaliser. */
+dba_status dba_mlp_create(uint64_t seed, dba_mlp** out);
+void dba_mlp_destroy(dba_mlp* mlp);
+const char* dba_mlp_last_error(const dba_mlp* mlp);
+/* Host copies of the parameters [DBA_MLP_N_PARAMS]. */
+dba_status dba_mlp_get_params(const dba_mlp* mlp, float* params);
+dba_status dba_mlp_set_params(dba_mlp* mlp, const float* params);
+/* Features [cap][32] and targets [cap][16] (DEVICE buffers owned by the caller) of the local
+ * problems of observations 0, stride, 2 stride, ... of ctx's current state (internal order),
+ * the targets from target_steps damped Gauss-Newton steps.  The state is only read. */
+dba_status dba_mlp_harvest(dba_ctx* ctx, int64_t stride, int target_steps, float* feats, float* targets,
+                           int64_t cap, int64_t* n_out);
+/* Input mean/std and target scale from n harvested rows (device buffers). */
+dba_status dba_mlp_fit_normalizer(dba_mlp* mlp, const float* feats, const float* targets, int64_t n);
+/* Mean squared error over the 9 used outputs of n rows and its gradient (host
+ * [DBA_MLP_N_PARAMS], normaliser entries 0). */
+dba_status dba_mlp_loss_grad(dba_mlp* mlp, const float* feats, const float* targets, int64_t n, double* loss,
+                             float* grad);
+/* Adam (beta 0.9/0.999) over `epochs` shuffled passes of minibatches; last epoch's mean loss. */
+dba_status dba_mlp_train(dba_mlp* mlp, const float* feats, const float* targets, int64_t n, int epochs,
+                         int batch, float lr, uint64_t seed, double* last_loss);
+/* Tensor-core inference on n feature rows (device) -> out [n][16] (device), in target-scale units. */
+dba_status dba_mlp_predict(dba_mlp* mlp, const float* feats, int64_t n, float* out);
+/* Uses (a copy of) the network to warm-start ctx's local solves; NULL disables. */
+dba_status dba_set_warm_start(dba_ctx* ctx, const dba_mlp* mlp);
+
 /* Message of the last failed call on ctx (or of the last failed dba_create
  * when ctx is NULL).  Never NULL. */
 const char* dba_last_error(const dba_ctx* ctx);

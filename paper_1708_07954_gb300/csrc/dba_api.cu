@@ -62,6 +62,9 @@ struct dba_ctx {
   std::vector<int> h_obs_pt, h_obs_cam;
   int64_t n_pseg = 0;
   int n_scenes = 0;
+  bool warm = false;
+  unsigned char* d_mlp_blob = nullptr;  // BF16 operands of the warm-start network
+  float* d_mlp_params = nullptr;        // FP32 parameters (biases, normaliser)
   int* d_scene_of_obs = nullptr;   // [l] internal order
   double* d_scene_sums = nullptr;  // [n_scenes][5]
   std::vector<void*> allocs;
@@ -89,6 +92,9 @@ struct dba_ctx {
     P = DevProblem{};
     has_problem = has_gt = false;
     n_scenes = 0;
+    warm = false;
+    d_mlp_blob = nullptr;
+    d_mlp_params = nullptr;
     d_scene_of_obs = nullptr;
     d_scene_sums = nullptr;
     perm.clear();
@@ -435,6 +441,9 @@ dba_status read_metrics(dba_ctx* ctx, dba_stats* st, double seconds) {
 }
 
 dba_status launch_iteration(dba_ctx* ctx) {
+  if (ctx->warm)
+    DBA_CUDA(dba::launch_mlp_warmstart(ctx->P, ctx->prm, ctx->fp32, ctx->d_mlp_blob, ctx->d_mlp_params, ctx->stream),
+             "warm start launch");
   DBA_CUDA(dba::launch_tile_iterate(ctx->P, ctx->prm, ctx->fp32, ctx->stream), "tile_iterate launch");
   DBA_CUDA(dba::launch_finalize(ctx->P, ctx->fp32, ctx->stream), "finalize launch");
   return DBA_OK;
@@ -444,9 +453,13 @@ dba_status ensure_graph(dba_ctx* ctx) {
   if (ctx->graph) return DBA_OK;
   cudaGraph_t g = nullptr;
   DBA_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal), "graph capture");
+  cudaError_t e0 = ctx->warm ? dba::launch_mlp_warmstart(ctx->P, ctx->prm, ctx->fp32, ctx->d_mlp_blob,
+                                                          ctx->d_mlp_params, ctx->stream)
+                             : cudaSuccess;
   cudaError_t e1 = dba::launch_tile_iterate(ctx->P, ctx->prm, ctx->fp32, ctx->stream);
   cudaError_t e2 = dba::launch_finalize(ctx->P, ctx->fp32, ctx->stream);
   cudaError_t e3 = cudaStreamEndCapture(ctx->stream, &g);
+  if (e0 != cudaSuccess) return ctx->cuda_fail(e0, "graph capture (warm start)");
   if (e1 != cudaSuccess) return ctx->cuda_fail(e1, "graph capture (tile_iterate)");
   if (e2 != cudaSuccess) return ctx->cuda_fail(e2, "graph capture (finalize)");
   if (e3 != cudaSuccess) return ctx->cuda_fail(e3, "graph capture");
@@ -483,6 +496,7 @@ dba_status check_device_flags(dba_ctx* ctx) {
   DBA_CUDA(cudaMemcpyAsync(&h, ctx->P.ctl, sizeof h, cudaMemcpyDeviceToHost, ctx->stream), "read control");
   DBA_CUDA(cudaStreamSynchronize(ctx->stream), "iterate");
   if (h.err & 1) return ctx->fail(DBA_ENUMERIC, "a local solve produced a non-finite value");
+  if (h.err & 2) return ctx->fail(DBA_ETIMEOUT, "a tensor-core wait of the warm-start network timed out");
   if (h.cur != ctx->cur) return ctx->fail(DBA_ECUDA, "device control word out of step with the host");
   return DBA_OK;
 }
@@ -834,10 +848,18 @@ dba_status dba_profile(dba_ctx* ctx, int n_iters, const char** names, double* ms
   if (!ctx || !count) return DBA_EINVAL;
   if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_profile before dba_set_observations");
   if (n_iters <= 0 || *count < 2 || !names || !ms) return ctx->fail(DBA_EINVAL, "dba_profile: bad arguments");
+  const int capacity = *count;
   std::vector<cudaEvent_t> ev(3 * (size_t)n_iters);
   for (auto& e : ev) DBA_CUDA(cudaEventCreate(&e), "event");
   cudaStream_t st = ctx->stream;
+  std::vector<cudaEvent_t> evw(ctx->warm ? (size_t)n_iters : 0);
+  for (auto& e : evw) DBA_CUDA(cudaEventCreate(&e), "event");
   for (int it = 0; it < n_iters; ++it) {
+    if (ctx->warm) {
+      DBA_CUDA(cudaEventRecord(evw[it], st), "event");
+      DBA_CUDA(dba::launch_mlp_warmstart(ctx->P, ctx->prm, ctx->fp32, ctx->d_mlp_blob, ctx->d_mlp_params, st),
+               "warm start");
+    }
     DBA_CUDA(cudaEventRecord(ev[3 * it], st), "event");
     DBA_CUDA(dba::launch_tile_iterate(ctx->P, ctx->prm, ctx->fp32, st), "tile_iterate");
     DBA_CUDA(cudaEventRecord(ev[3 * it + 1], st), "event");
@@ -848,21 +870,29 @@ dba_status dba_profile(dba_ctx* ctx, int n_iters, const char** names, double* ms
   ctx->pending = 1;
   ctx->iters += n_iters;
   dba_status s = check_device_flags(ctx);
-  double t0 = 0, t1 = 0;
+  double t0 = 0, t1 = 0, tw = 0;
   for (int it = 0; it < n_iters && s == DBA_OK; ++it) {
-    float a = 0, b = 0;
+    float a = 0, b = 0, c = 0;
     cudaEventElapsedTime(&a, ev[3 * it], ev[3 * it + 1]);
     cudaEventElapsedTime(&b, ev[3 * it + 1], ev[3 * it + 2]);
+    if (ctx->warm) cudaEventElapsedTime(&c, evw[it], ev[3 * it]);
     t0 += a;
     t1 += b;
+    tw += c;
   }
   for (auto& e : ev) cudaEventDestroy(e);
+  for (auto& e : evw) cudaEventDestroy(e);
   if (s != DBA_OK) return s;
   names[0] = "tile_iterate";
   ms[0] = t0 / n_iters;
   names[1] = "finalize";
   ms[1] = t1 / n_iters;
   *count = 2;
+  if (ctx->warm && capacity >= 3) {
+    names[2] = "mlp_warm_start";
+    ms[2] = tw / n_iters;
+    *count = 3;
+  }
   return DBA_OK;
 }
 
@@ -961,6 +991,55 @@ dba_status dba_scene_stats(dba_ctx* ctx, double* rmse_obs, double* rmse_gt, doub
     if (objective) objective[sc] = v[1];
     if (rmse_gt) rmse_gt[sc] = (ctx->has_gt && v[4] > 0) ? std::sqrt(v[2] / v[4]) : 0.0;
   }
+  return DBA_OK;
+}
+
+dba_status dba_mlp_harvest(dba_ctx* ctx, int64_t stride, int target_steps, float* feats, float* targets,
+                           int64_t cap, int64_t* n_out) {
+  if (!ctx) return DBA_EINVAL;
+  if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_mlp_harvest before dba_set_observations");
+  if (stride <= 0 || cap < 0 || target_steps < 0 || target_steps > 1000 || !feats || !targets || !n_out)
+    return ctx->fail(DBA_EINVAL, "dba_mlp_harvest: bad arguments");
+  const int64_t n = std::min<int64_t>(cap, (ctx->n_obs + stride - 1) / stride);
+  DBA_CUDA(dba::launch_mlp_harvest(ctx->P, ctx->prm, ctx->fp32, ctx->pending, stride, n, target_steps, feats,
+                                   targets, ctx->stream),
+           "harvest");
+  DBA_CUDA(cudaStreamSynchronize(ctx->stream), "harvest");
+  *n_out = n;
+  return DBA_OK;
+}
+
+dba_status dba_set_warm_start(dba_ctx* ctx, const dba_mlp* mlp) {
+  if (!ctx) return DBA_EINVAL;
+  if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_set_warm_start before dba_set_observations");
+  if (ctx->graph) {
+    cudaGraphExecDestroy(ctx->graph);
+    ctx->graph = nullptr;
+  }
+  if (!mlp) {
+    ctx->warm = false;
+    ctx->P.mlp_start = nullptr;
+    return DBA_OK;
+  }
+  std::vector<float> params(DBA_MLP_N_PARAMS);
+  const dba_status ps = dba_mlp_get_params(mlp, params.data());
+  if (ps != DBA_OK) return ctx->fail(ps, "dba_set_warm_start: cannot read the network");
+  std::vector<unsigned char> blob;
+  dba::mlp_make_blob(params.data(), blob);
+  if (!ctx->d_mlp_blob) {
+    DBA_CUDA(ctx->alloc(&ctx->d_mlp_blob, blob.size()), "warm start");
+    DBA_CUDA(ctx->alloc(&ctx->d_mlp_params, params.size()), "warm start");
+    char* p = nullptr;
+    DBA_CUDA(ctx->alloc(&p, 9 * (size_t)ctx->n_obs * (ctx->fp32 ? sizeof(float) : sizeof(double))), "warm start");
+    ctx->P.mlp_start = p;
+  }
+  DBA_CUDA(cudaMemcpyAsync(ctx->d_mlp_blob, blob.data(), blob.size(), cudaMemcpyHostToDevice, ctx->stream),
+           "warm start");
+  DBA_CUDA(cudaMemcpyAsync(ctx->d_mlp_params, params.data(), params.size() * sizeof(float), cudaMemcpyHostToDevice,
+                           ctx->stream),
+           "warm start");
+  DBA_CUDA(cudaStreamSynchronize(ctx->stream), "warm start");
+  ctx->warm = true;
   return DBA_OK;
 }
 

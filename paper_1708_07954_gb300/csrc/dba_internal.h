@@ -71,6 +71,7 @@ struct DevProblem {
   void* DY;                     // [m][6]
   double* pt_part;              // [n_pt_slots][3]
   double* cam_part;             // [n_cam_slots][6]
+  const void* mlp_start;        // [9][l] T: learned candidate start (nullptr: none)
   double* metric_part;          // [metric blocks][8]
   double* metric_out;           // [8]
   DevCtl* ctl;
@@ -99,9 +100,21 @@ cudaError_t launch_project_truth(const DevProblem& P, const Params& prm, bool fp
 cudaError_t launch_scene_metrics(const DevProblem& P, const Params& prm, bool fp32, const int* scene_of_obs,
                                  double* out, cudaStream_t s);
 
+// Learned warm start (dba_mlp.cu): tensor-core inference writing P.mlp_start from the
+// state, feature/target harvest, and the BF16 operand blob built from FP32 parameters.
+cudaError_t launch_mlp_warmstart(const DevProblem& P, const Params& prm, bool fp32, const unsigned char* blob,
+                                 const float* params, cudaStream_t s);
+cudaError_t launch_mlp_harvest(const DevProblem& P, const Params& prm, bool fp32, int pending, long long stride,
+                               long long cap, int target_steps, float* feats, float* targs, cudaStream_t s);
+
 // Allocation-free reprojection statistics (file-scope device scratch; see dba_evaluate_noalloc).
 cudaError_t launch_eval_noalloc(const Params& prm, long long n_obs, int n_cams, int n_pts, const int* pt_idx,
                                 const int* cam_idx, const double* z, const double* cams, const double* pts,
                                 double* out, cudaStream_t s);
 
+}  // namespace dba
+
+#include <vector>
+namespace dba {
+void mlp_make_blob(const float* params, std::vector<unsigned char>& blob);
 }  // namespace dba

@@ -23,290 +23,11 @@
 #include <mutex>
 
 #include "../../include/dba.h"
+#include "dba_device.cuh"
 #include "dba_internal.h"
 
 namespace dba {
 namespace {
-
-// ------------------------------------------------------------ scalar helpers
-template <typename T> struct Num;
-// FP32 path: hardware approximations where their error (<= 2 ulp, or 2^-21 absolute for
-// sin/cos after reduction to [-pi, pi]) stays far below the pixel tolerance.
-template <> struct Num<float> {
-  using V2 = float2;
-  static __device__ __forceinline__ void sc(float x, float* s, float* c) {
-    // Cody-Waite reduction by 2 pi (two-term split of 2 pi), then the SFU sin/cos
-    const float k = rintf(x * 0.15915494309189535f);
-    float r = fmaf(-k, 6.28318548202514648f, x);
-    r = fmaf(-k, -1.7484555314695172e-7f, r);
-    __sincosf(r, s, c);
-  }
-  static __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
-  static __device__ __forceinline__ float div(float a, float b) { return a * __frcp_rn(b); }
-  static __device__ __forceinline__ float sqrt_(float x) { return __fsqrt_rn(x); }
-  static __device__ __forceinline__ float log1p_(float x) { return log1pf(x); }
-  static __device__ __forceinline__ float inf() { return CUDART_INF_F; }
-  static constexpr float unit_roundoff = 5.9604644775390625e-08f;  // 2^-24
-};
-// FP64 path: correctly rounded operations, as the oracle uses.
-template <> struct Num<double> {
-  using V2 = double2;
-  static __device__ __forceinline__ void sc(double x, double* s, double* c) { sincos(x, s, c); }
-  static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
-  static __device__ __forceinline__ double div(double a, double b) { return a / b; }
-  static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
-  static __device__ __forceinline__ double log1p_(double x) { return log1p(x); }
-  static __device__ __forceinline__ double inf() { return CUDART_INF; }
-  static constexpr double unit_roundoff = 1.1102230246251565e-16;  // 2^-53
-};
-
-// float <-> double by integer bit manipulation (IEEE-754 binary32/binary64 layouts), so the
-// FP32 path spends none of GB300's scarce FP64 issue slots on conversions.  Exact for normal
-// numbers; magnitudes below 2^-126 become signed zero; non-finite values and float overflow
-// take the hardware conversion.
-__device__ __forceinline__ double widen(float f) {
-  const unsigned int b = __float_as_uint(f);
-  const unsigned int mag = b & 0x7fffffffu;
-  if (mag >= 0x7f800000u) return (double)f;
-  if (mag < 0x00800000u) return __hiloint2double((int)(b & 0x80000000u), 0);
-  const unsigned int hi = (b & 0x80000000u) | ((mag >> 3) + (896u << 20));
-  return __hiloint2double((int)hi, (int)(mag << 29));
-}
-__device__ __forceinline__ float narrow(double d) {
-  const unsigned int hi = (unsigned int)__double2hiint(d);
-  const unsigned int lo = (unsigned int)__double2loint(d);
-  const unsigned int e = (hi >> 20) & 0x7ffu;
-  if (e >= 1151u) return (float)d;
-  if (e <= 896u) return __uint_as_float(hi & 0x80000000u);
-  unsigned int f = ((e - 896u) << 23) + (((hi & 0xfffffu) << 3) | (lo >> 29));
-  f += (lo >> 28) & 1u;  // round to nearest (halfway cases away from zero)
-  return __uint_as_float(f | (hi & 0x80000000u));
-}
-template <typename T> __device__ __forceinline__ double to_f64(T v);
-template <> __device__ __forceinline__ double to_f64<float>(float v) { return widen(v); }
-template <> __device__ __forceinline__ double to_f64<double>(double v) { return v; }
-template <typename T> __device__ __forceinline__ T from_f64(double v);
-template <> __device__ __forceinline__ float from_f64<float>(double v) { return narrow(v); }
-template <> __device__ __forceinline__ double from_f64<double>(double v) { return v; }
-
-template <typename T>
-struct Prm {
-  T focal, cx, cy, lp, rho_x, rho_y, rho_a, lambda0, lambda_min, eps, model_tol;
-  int loss, steps;
-  // penalty of coordinate c of (x, alpha, beta, gamma, t)
-  __device__ __forceinline__ T rho(int c) const { return c < 3 ? rho_x : (c < 6 ? rho_a : rho_y); }
-};
-
-template <typename T>
-__host__ __device__ Prm<T> make_prm(const Params& p) {
-  Prm<T> q;
-  q.focal = (T)p.focal; q.cx = (T)p.cx; q.cy = (T)p.cy; q.lp = (T)p.loss_param;
-  q.rho_x = (T)p.rho_x; q.rho_y = (T)p.rho_y; q.rho_a = (T)p.rho_a; q.lambda0 = (T)p.lambda0;
-  q.lambda_min = (T)p.lambda_min; q.eps = (T)p.eps_depth; q.model_tol = (T)p.model_tol;
-  q.loss = p.loss; q.steps = p.inner_steps;
-  return q;
-}
-
-// Misfit phi_m as a function of s = |e|^2 and its derivative (IRLS weight).
-template <typename T>
-__device__ __forceinline__ T misfit(int loss, T p, T s) {
-  if (loss == 1) return s <= p * p ? s : T(2) * p * Num<T>::sqrt_(s) - p * p;
-  if (loss == 2) return p * Num<T>::log1p_(Num<T>::div(s, p));
-  return s;
-}
-template <typename T>
-__device__ __forceinline__ T misfit_weight(int loss, T p, T s) {
-  if (loss == 1) return s <= p * p ? T(1) : Num<T>::div(p, Num<T>::sqrt_(s));
-  if (loss == 2) return Num<T>::div(p, p + s);
-  return T(1);
-}
-
-// Camera pose evaluated at v = (x, alpha, beta, gamma, t): R = Rz Ry Rx
-// (Sec. 2.1), u = R x and p = u + t (camera frame).
-template <typename T>
-struct Pose {
-  T R[9];
-  T u[3];
-  T p[3];
-  T sg, cg;
-  bool valid;
-};
-
-template <typename T>
-__device__ __forceinline__ void pose_at(const T v[9], T eps, Pose<T>& P) {
-  T sa, ca, sb, cb;
-  Num<T>::sc(v[3], &sa, &ca);
-  Num<T>::sc(v[4], &sb, &cb);
-  Num<T>::sc(v[5], &P.sg, &P.cg);
-  const T sg = P.sg, cg = P.cg;
-  P.R[0] = cg * cb;
-  P.R[1] = cg * sb * sa - sg * ca;
-  P.R[2] = cg * sb * ca + sg * sa;
-  P.R[3] = sg * cb;
-  P.R[4] = sg * sb * sa + cg * ca;
-  P.R[5] = sg * sb * ca - cg * sa;
-  P.R[6] = -sb;
-  P.R[7] = cb * sa;
-  P.R[8] = cb * ca;
-#pragma unroll
-  for (int r = 0; r < 3; ++r) {
-    P.u[r] = P.R[3 * r] * v[0] + P.R[3 * r + 1] * v[1] + P.R[3 * r + 2] * v[2];
-    P.p[r] = P.u[r] + v[6 + r];
-  }
-  P.valid = P.p[2] > eps;
-}
-
-// Eq. (9) in offset form: with d = v - vbar and a = dual / rho,
-// r^T d + rho/2 |d|^2 = rho (a.d + d.d/2).  +inf behind the camera.
-template <typename T>
-__device__ __forceinline__ T local_objective(const T d[9], const T a[9], const Pose<T>& P,
-                                             T z0, T z1, const Prm<T>& q) {
-  if (!P.valid) return Num<T>::inf();
-  const T iz = Num<T>::rcp(P.p[2]);
-  const T e0 = z0 - (q.focal * P.p[0] * iz + q.cx);
-  const T e1 = z1 - (q.focal * P.p[1] * iz + q.cy);
-  T px = 0, pa = 0, pt = 0;
-#pragma unroll
-  for (int c = 0; c < 3; ++c) px += d[c] * (a[c] + T(0.5) * d[c]);
-#pragma unroll
-  for (int c = 3; c < 6; ++c) pa += d[c] * (a[c] + T(0.5) * d[c]);
-#pragma unroll
-  for (int c = 6; c < 9; ++c) pt += d[c] * (a[c] + T(0.5) * d[c]);
-  return misfit<T>(q.loss, q.lp, e0 * e0 + e1 * e1) + q.rho_x * px + q.rho_a * pa + q.rho_y * pt;
-}
-
-// Eq. (9): inner_steps damped Gauss-Newton steps with IRLS weights.  The
-// damped normal matrix 2w J^T J + diag(rho) + lambda I is diagonal plus rank
-// 2 (one observation has two residuals), so each step solves it exactly
-// through its 2x2 capacitance matrix (Sherman-Morrison-Woodbury) instead of a
-// 9x9 factorisation.  Accept/reject and the damping schedule follow the
-// Levenberg rule: accept iff the trial is in front of the camera and lowers
-// Eq. (9).  A step whose predicted decrease is below the objective's rounding
-// noise is accepted without the comparison (model_tol) and the objective is
-// carried as its model value.  d (offset from vbar) is updated in place.
-template <typename T>
-__device__ __forceinline__ void local_solve(T z0, T z1, const T vbar[9], const T a[9], T d[9],
-                                            const Prm<T>& q) {
-  T v[9];
-#pragma unroll
-  for (int c = 0; c < 9; ++c) v[c] = vbar[c] + d[c];
-  Pose<T> P;
-  pose_at(v, q.eps, P);
-  T L = local_objective(d, a, P, z0, z1, q);
-  T lambda = T(-1);
-  for (int step = 0; step < q.steps; ++step) {
-    T J0[9], J1[9];
-    T w = 0, e0 = 0, e1 = 0;
-    if (P.valid) {
-      const T iz = Num<T>::rcp(P.p[2]);
-      const T zx = P.p[0] * iz, zy = P.p[1] * iz;
-      e0 = z0 - (q.focal * zx + q.cx);
-      e1 = z1 - (q.focal * zy + q.cy);
-      w = misfit_weight<T>(q.loss, q.lp, e0 * e0 + e1 * e1);
-      const T fi = q.focal * iz;
-      // d p / d v columns: x_k -> R[:,k]; alpha -> R[:,0] x u; beta -> (-sg, cg, 0) x u;
-      // gamma -> e_z x u; t_k -> e_k.   Row r of J: fi * (dp_r - z_r dp_2).
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        J0[k] = fi * (P.R[k] - zx * P.R[6 + k]);
-        J1[k] = fi * (P.R[3 + k] - zy * P.R[6 + k]);
-      }
-      {
-        const T c0 = P.R[0], c1 = P.R[3], c2 = P.R[6];
-        const T d0 = c1 * P.u[2] - c2 * P.u[1];
-        const T d1 = c2 * P.u[0] - c0 * P.u[2];
-        const T d2 = c0 * P.u[1] - c1 * P.u[0];
-        J0[3] = fi * (d0 - zx * d2);
-        J1[3] = fi * (d1 - zy * d2);
-      }
-      {
-        const T b0 = -P.sg, b1 = P.cg;
-        const T d0 = b1 * P.u[2];
-        const T d1 = -b0 * P.u[2];
-        const T d2 = b0 * P.u[1] - b1 * P.u[0];
-        J0[4] = fi * (d0 - zx * d2);
-        J1[4] = fi * (d1 - zy * d2);
-      }
-      J0[5] = fi * (-P.u[1]);
-      J1[5] = fi * (P.u[0]);
-      J0[6] = fi;
-      J1[6] = 0;
-      J0[7] = 0;
-      J1[7] = fi;
-      J0[8] = -fi * zx;
-      J1[8] = -fi * zy;
-    } else {
-#pragma unroll
-      for (int k = 0; k < 9; ++k) J0[k] = J1[k] = 0;
-    }
-    const T tw = T(2) * w;
-    T g[9];
-#pragma unroll
-    for (int c = 0; c < 9; ++c) g[c] = -tw * (J0[c] * e0 + J1[c] * e1) + q.rho(c) * (a[c] + d[c]);
-    if (lambda < T(0)) {
-      T tr = T(3) * (q.rho_x + q.rho_a + q.rho_y);
-#pragma unroll
-      for (int c = 0; c < 9; ++c) tr += tw * (J0[c] * J0[c] + J1[c] * J1[c]);
-      lambda = q.lambda0 * tr / T(9);
-    }
-    const T iDx = Num<T>::rcp(q.rho_x + lambda), iDa = Num<T>::rcp(q.rho_a + lambda),
-            iDy = Num<T>::rcp(q.rho_y + lambda);
-    T G00 = 0, G01 = 0, G11 = 0, t0 = 0, t1 = 0;
-    T qv[9];
-#pragma unroll
-    for (int c = 0; c < 9; ++c) {
-      const T iD = c < 3 ? iDx : (c < 6 ? iDa : iDy);
-      qv[c] = g[c] * iD;
-      G00 += J0[c] * J0[c] * iD;
-      G01 += J0[c] * J1[c] * iD;
-      G11 += J1[c] * J1[c] * iD;
-      t0 += J0[c] * qv[c];
-      t1 += J1[c] * qv[c];
-    }
-    const T S00 = T(1) + tw * G00, S01 = tw * G01, S11 = T(1) + tw * G11;
-    const T idet = Num<T>::rcp(S00 * S11 - S01 * S01);
-    const T y0 = (S11 * t0 - S01 * t1) * idet;
-    const T y1 = (S00 * t1 - S01 * t0) * idet;
-    T stp[9];
-    T gs = 0, ss = 0;
-#pragma unroll
-    for (int c = 0; c < 9; ++c) {
-      const T iD = c < 3 ? iDx : (c < 6 ? iDa : iDy);
-      stp[c] = -qv[c] + tw * iD * (J0[c] * y0 + J1[c] * y1);
-      gs += g[c] * stp[c];
-      ss += stp[c] * stp[c];
-    }
-    // decrease of the Gauss-Newton model; with (H + lambda I) s = -g it is (lambda s.s - g.s) / 2
-    const T pred = T(0.5) * (lambda * ss - gs);
-    bool trust = false;
-    if (P.valid && q.model_tol > T(0)) {
-      // below the rounding noise of L the objective comparison is arbitrary: trust the model
-      const T noise = q.model_tol * Num<T>::unit_roundoff *
-                      (fabs(L) + T(2) * w * Num<T>::sqrt_(e0 * e0 + e1 * e1) * (fabs(z0) + fabs(z1)));
-      trust = pred <= noise;
-    }
-    T dt[9], vt[9];
-#pragma unroll
-    for (int c = 0; c < 9; ++c) {
-      dt[c] = d[c] + stp[c];
-      vt[c] = vbar[c] + dt[c];
-    }
-    Pose<T> Pt;
-    pose_at(vt, q.eps, Pt);
-    // a trusted step carries the objective as its model value L - pred
-    const T Lt = trust ? L - pred : local_objective(dt, a, Pt, z0, z1, q);
-    if (Pt.valid && (trust || Lt < L)) {
-#pragma unroll
-      for (int c = 0; c < 9; ++c) d[c] = dt[c];
-      P = Pt;
-      L = Lt;
-      const T lr = Num<T>::div(lambda, T(10));
-      lambda = lr > q.lambda_min ? lr : q.lambda_min;
-    } else {
-      lambda *= T(10);
-    }
-  }
-}
 
 // ------------------------------------------------------------ tile kernel
 // Persistent, software-pipelined: each block walks tiles blockIdx.x,
@@ -438,7 +159,15 @@ __device__ __forceinline__ void process_tile(const DevProblem& P, const Prm<T>& 
       for (int c = 0; c < 9; ++c) aT[c] = from_f64<T>(S.adual[c][t]);
     }
     const typename Num<T>::V2 zz = S.z[t];
-    local_solve<T>(zz.x, zz.y, vbar, aT, d, q);
+    if (P.mlp_start) {
+      const T* ms = static_cast<const T*>(P.mlp_start);
+      T alt[9];
+#pragma unroll
+      for (int c = 0; c < 9; ++c) alt[c] = ms[c * l + o];
+      local_solve<T, true>(zz.x, zz.y, vbar, aT, d, q, alt);
+    } else {
+      local_solve<T>(zz.x, zz.y, vbar, aT, d, q);
+    }
     bool finite = true;
 #pragma unroll
     for (int c = 0; c < 9; ++c) {

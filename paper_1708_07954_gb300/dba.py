@@ -23,8 +23,11 @@ EXPORTED = [
     "dba_config_default", "dba_create", "dba_set_observations", "dba_set_ground_truth", "dba_iterate",
     "dba_iterate_until", "dba_evaluate", "dba_get_params", "dba_get_state", "dba_set_state",
     "dba_profile", "dba_layout", "dba_evaluate_noalloc", "dba_set_scenes", "dba_scene_stats",
-    "dba_last_error", "dba_destroy",
+    "dba_last_error", "dba_destroy", "dba_mlp_create", "dba_mlp_destroy", "dba_mlp_last_error",
+    "dba_mlp_get_params", "dba_mlp_set_params", "dba_mlp_harvest", "dba_mlp_fit_normalizer",
+    "dba_mlp_loss_grad", "dba_mlp_train", "dba_mlp_predict", "dba_set_warm_start",
 ]
+DBA_MLP_N_PARAMS, DBA_MLP_N_FEATURES, DBA_MLP_N_TARGETS = 11552, 32, 16
 DBA_NOALLOC_MAX_OBS = 16777216
 
 
@@ -93,12 +96,28 @@ def load():
     L.dba_scene_stats.argtypes = [vp, dp, dp, dp]
     L.dba_evaluate_noalloc.argtypes = [P(dba_config), ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, vp, vp, vp,
                                        vp, vp, vp, vp]
+    fp = P(ctypes.c_float)
+    L.dba_mlp_create.argtypes = [ctypes.c_uint64, P(vp)]
+    L.dba_mlp_destroy.argtypes = [vp]
+    L.dba_mlp_destroy.restype = None
+    L.dba_mlp_last_error.argtypes = [vp]
+    L.dba_mlp_last_error.restype = ctypes.c_char_p
+    L.dba_mlp_get_params.argtypes = [vp, fp]
+    L.dba_mlp_set_params.argtypes = [vp, fp]
+    L.dba_mlp_harvest.argtypes = [vp, ctypes.c_int64, ctypes.c_int, vp, vp, ctypes.c_int64, P(ctypes.c_int64)]
+    L.dba_mlp_fit_normalizer.argtypes = [vp, vp, vp, ctypes.c_int64]
+    L.dba_mlp_loss_grad.argtypes = [vp, vp, vp, ctypes.c_int64, P(ctypes.c_double), fp]
+    L.dba_mlp_train.argtypes = [vp, vp, vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_float,
+                                ctypes.c_uint64, P(ctypes.c_double)]
+    L.dba_mlp_predict.argtypes = [vp, vp, ctypes.c_int64, vp]
+    L.dba_set_warm_start.argtypes = [vp, vp]
     L.dba_last_error.argtypes = [vp]
     L.dba_last_error.restype = ctypes.c_char_p
     L.dba_destroy.argtypes = [vp]
     L.dba_destroy.restype = None
     for name in EXPORTED:
-        if name not in ("dba_config_default", "dba_last_error", "dba_destroy"):
+        if name not in ("dba_config_default", "dba_last_error", "dba_destroy", "dba_mlp_destroy",
+                        "dba_mlp_last_error"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -244,6 +263,73 @@ def dba_destroy(ctx):
         load().dba_destroy(ctx)
 
 
+class Mlp:
+    """The warm-start network (C object dba_mlp).  Feature/target buffers are device pointers
+    (e.g. torch CUDA tensors' data_ptr())."""
+
+    def __init__(self, seed=0):
+        L = load()
+        self.h = ctypes.c_void_p()
+        st = L.dba_mlp_create(ctypes.c_uint64(seed), ctypes.byref(self.h))
+        if st != DBA_OK:
+            raise DbaError(st, L.dba_mlp_last_error(None).decode())
+
+    def _check(self, st):
+        if st != DBA_OK:
+            raise DbaError(st, load().dba_mlp_last_error(self.h).decode())
+
+    def get_params(self):
+        out = np.zeros(DBA_MLP_N_PARAMS, dtype=np.float32)
+        self._check(load().dba_mlp_get_params(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.shape == (DBA_MLP_N_PARAMS,)
+        self._check(load().dba_mlp_set_params(self.h, p.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+
+    def fit_normalizer(self, feats_ptr, targs_ptr, n):
+        self._check(load().dba_mlp_fit_normalizer(self.h, feats_ptr, targs_ptr, int(n)))
+
+    def loss_grad(self, feats_ptr, targs_ptr, n):
+        loss = ctypes.c_double()
+        g = np.zeros(DBA_MLP_N_PARAMS, dtype=np.float32)
+        self._check(load().dba_mlp_loss_grad(self.h, feats_ptr, targs_ptr, int(n), ctypes.byref(loss),
+                                             g.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return loss.value, g
+
+    def train(self, feats_ptr, targs_ptr, n, epochs, batch, lr, seed=0):
+        loss = ctypes.c_double()
+        self._check(load().dba_mlp_train(self.h, feats_ptr, targs_ptr, int(n), int(epochs), int(batch),
+                                         ctypes.c_float(lr), ctypes.c_uint64(seed), ctypes.byref(loss)))
+        return loss.value
+
+    def predict(self, feats_ptr, n, out_ptr):
+        self._check(load().dba_mlp_predict(self.h, feats_ptr, int(n), out_ptr))
+
+    def close(self):
+        if self.h:
+            load().dba_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def dba_mlp_harvest(ctx, stride, target_steps, feats_ptr, targs_ptr, cap):
+    n = ctypes.c_int64()
+    _check(load().dba_mlp_harvest(ctx, int(stride), int(target_steps), feats_ptr, targs_ptr, int(cap),
+                                  ctypes.byref(n)), ctx)
+    return n.value
+
+
+def dba_set_warm_start(ctx, mlp):
+    _check(load().dba_set_warm_start(ctx, mlp.h if mlp is not None else None), ctx)
+
+
 class Solver:
     """Owns one context for one scene (a scenes.Scene or anything with its fields)."""
 
@@ -294,6 +380,12 @@ class Solver:
 
     def layout(self):
         return dba_layout(self.ctx)
+
+    def set_warm_start(self, mlp):
+        dba_set_warm_start(self.ctx, mlp)
+
+    def harvest(self, stride, target_steps, feats_ptr, targs_ptr, cap):
+        return dba_mlp_harvest(self.ctx, stride, target_steps, feats_ptr, targs_ptr, cap)
 
     def scene_stats(self):
         return dba_scene_stats(self.ctx, len(self.scene.scene_off) - 1)

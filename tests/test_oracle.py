@@ -331,3 +331,38 @@ def test_dense_lm_stop_rule_on_noise_free_data():
     cfg = O.config_for(s, loss=O.LOSS_L2)
     _, _, obj, it = O.dense_lm(cfg, s, max_iters=1000)
     assert obj < 1e-14 and it < 1000
+
+
+# --------------------------------------------- warm-start network reference
+def test_mlp_reference_gradient_matches_finite_differences():
+    import oracle.mlp as OM
+
+    rng = np.random.default_rng(21)
+    p = rng.normal(0, 0.3, OM.N_PARAMS)
+    p[OM.N_TRAINABLE + OM.N_IN:OM.N_TRAINABLE + 2 * OM.N_IN] = rng.uniform(0.5, 2, OM.N_IN)
+    p[OM.N_TRAINABLE + 2 * OM.N_IN:] = rng.uniform(0.5, 2, OM.N_OUT)
+    f = rng.normal(0, 1, (7, OM.N_IN))
+    t = rng.normal(0, 1, (7, OM.N_OUT))
+    loss, g = OM.loss_and_grad(p, f, t)
+    for k in rng.choice(OM.N_TRAINABLE, 40, replace=False):
+        h = 1e-6
+        pp, pm = p.copy(), p.copy()
+        pp[k] += h
+        pm[k] -= h
+        fd = (OM.loss_and_grad(pp, f, t)[0] - OM.loss_and_grad(pm, f, t)[0]) / (2 * h)
+        assert abs(g[k] - fd) <= 1e-6 * max(1.0, abs(fd))
+    # the unused outputs 9..15 and the normaliser get no gradient
+    assert np.all(g[OM.N_TRAINABLE:] == 0)
+
+
+def test_mlp_reference_gelu_tanh_form():
+    """The tanh form tracks x Phi(x) to ~1e-3 and its derivative matches finite differences."""
+    import math
+
+    import oracle.mlp as OM
+
+    for z in (-3.0, -0.5, 0.0, 0.7, 2.5):
+        phi = 0.5 * (1 + math.erf(z / math.sqrt(2)))
+        assert abs(OM.gelu(np.array(z)) - z * phi) < 2e-3
+        fd = (OM.gelu(np.array(z + 1e-6)) - OM.gelu(np.array(z - 1e-6))) / 2e-6
+        assert abs(OM.gelu_grad(np.array(z)) - fd) < 1e-8
