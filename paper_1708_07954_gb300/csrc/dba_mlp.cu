@@ -1,10 +1,10 @@
 // Learned warm start for the local solves (no counterpart in the paper).
 //
-// A 32-64-64-64-16 GELU network maps the features of one local problem
+// A 32-64-64-64-16 ReLU network maps the features of one local problem
 // (warm_features in dba_device.cuh) to the scaled step r (d* - d0) towards the
 // solution of a long local solve.  This unit holds
 //   - harvest_kernel: features and targets from the current ADMM state;
-//   - FP32 training kernels (tiled SGEMM, GELU, loss, Adam);
+//   - FP32 training kernels (tiled SGEMM, ReLU, loss, Adam);
 //   - mlp_infer_kernel: BF16 tensor-core inference with tcgen05.mma (operands
 //     in shared memory, FP32 accumulators in tensor memory), either on given
 //     features or fused with feature extraction from the ADMM state, writing a
@@ -80,21 +80,7 @@ __global__ void harvest_kernel(DevProblem P, Prm<T> q, int pending, long long st
 }
 
 // ------------------------------------------------------------ training (FP32)
-// GELU in its tanh form, 0.5 x (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3))), and its derivative
-constexpr float kGeluC0 = 0.7978845608028654f, kGeluC1 = 0.044715f;
-__device__ __forceinline__ float gelu(float x) {
-  return 0.5f * x * (1.f + tanhf(kGeluC0 * (x + kGeluC1 * x * x * x)));
-}
-__device__ __forceinline__ float gelu_grad(float x) {
-  const float t = tanhf(kGeluC0 * (x + kGeluC1 * x * x * x));
-  return 0.5f * (1.f + t) + 0.5f * x * (1.f - t * t) * kGeluC0 * (1.f + 3.f * kGeluC1 * x * x);
-}
-// the same with the SFU tanh (tensor-core inference, whose BF16 operands are coarser)
-__device__ __forceinline__ float gelu_fast(float x) {
-  float t;
-  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(kGeluC0 * (x + kGeluC1 * x * x * x)));
-  return 0.5f * x * (1.f + t);
-}
+__device__ __forceinline__ float relu(float x) { return fmaxf(x, 0.f); }
 
 // C[M x N] = op(A) op(B) (+ C if accumulate), row-major; op(A) is M x K, op(B) K x N.
 constexpr int kGemmTile = 16;
@@ -142,13 +128,13 @@ __global__ void gather_targets_kernel(const float* Y, const int* idx, int n, con
   const long long src = idx ? idx[r] : r;
   out[e] = Y[src * kMlpOut + c] / params[kOutStd + c];
 }
-// Z += bias (per column); H = GELU(Z) when H != nullptr
+// Z += bias (per column); H = ReLU(Z) when H != nullptr
 __global__ void bias_act_kernel(float* Z, const float* bias, int n, int width, float* H) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n * width) return;
   const float z = Z[e] + bias[e % width];
   Z[e] = z;
-  if (H) H[e] = gelu(z);
+  if (H) H[e] = relu(z);
 }
 // dY = 2 (Y - T) / (n * 9) on the 9 used outputs; loss partial sums
 __global__ void loss_grad_kernel(const float* Y, const float* Tt, int n, float* dY, double* loss) {
@@ -163,10 +149,10 @@ __global__ void loss_grad_kernel(const float* Y, const float* Tt, int n, float* 
   for (int w = 16; w > 0; w >>= 1) l += __shfl_down_sync(0xffffffffu, l, w);
   if ((threadIdx.x & 31) == 0) atomicAdd(loss, l / (double)(n * kMlpUsedOut));
 }
-// dZ = dH * GELU'(Z)
-__global__ void gelu_back_kernel(const float* dH, const float* Z, int total, float* dZ) {
+// dZ = dH * ReLU'(Z)
+__global__ void relu_back_kernel(const float* dH, const float* Z, int total, float* dZ) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < total) dZ[e] = dH[e] * gelu_grad(Z[e]);
+  if (e < total) dZ[e] = Z[e] > 0.f ? dH[e] : 0.f;
 }
 // column sums of dZ into grad (bias gradient)
 __global__ void colsum_kernel(const float* dZ, int n, int width, float* out) {
@@ -293,15 +279,15 @@ cudaError_t mlp_forward_backward(dba_mlp* m, int n) {
   sgemm(s, kMlpOut, H, n, m->dy, kMlpOut, true, m->h3, H, false, G + kW4, H);    // dW4 = dY^T H3
   colsum_kernel<<<kMlpOut, 256, 0, s>>>(m->dy, n, kMlpOut, G + kB4);
   sgemm(s, n, H, kMlpOut, m->dy, kMlpOut, false, P + kW4, H, false, m->d64a, H);  // dH3 = dY W4
-  gelu_back_kernel<<<blocks_for((long long)n * H, 256), 256, 0, s>>>(m->d64a, m->z3, n * H, m->d64b);
+  relu_back_kernel<<<blocks_for((long long)n * H, 256), 256, 0, s>>>(m->d64a, m->z3, n * H, m->d64b);
   sgemm(s, H, H, n, m->d64b, H, true, m->h2, H, false, G + kW3, H);              // dW3 = dZ3^T H2
   colsum_kernel<<<H, 256, 0, s>>>(m->d64b, n, H, G + kB3);
   sgemm(s, n, H, H, m->d64b, H, false, P + kW3, H, false, m->d64a, H);           // dH2 = dZ3 W3
-  gelu_back_kernel<<<blocks_for((long long)n * H, 256), 256, 0, s>>>(m->d64a, m->z2, n * H, m->d64b);
+  relu_back_kernel<<<blocks_for((long long)n * H, 256), 256, 0, s>>>(m->d64a, m->z2, n * H, m->d64b);
   sgemm(s, H, H, n, m->d64b, H, true, m->h1, H, false, G + kW2, H);              // dW2 = dZ2^T H1
   colsum_kernel<<<H, 256, 0, s>>>(m->d64b, n, H, G + kB2);
   sgemm(s, n, H, H, m->d64b, H, false, P + kW2, H, false, m->d64a, H);           // dH1 = dZ2 W2
-  gelu_back_kernel<<<blocks_for((long long)n * H, 256), 256, 0, s>>>(m->d64a, m->z1, n * H, m->d64b);
+  relu_back_kernel<<<blocks_for((long long)n * H, 256), 256, 0, s>>>(m->d64a, m->z1, n * H, m->d64b);
   sgemm(s, H, kMlpIn, n, m->d64b, H, true, m->x, kMlpIn, false, G + kW1, kMlpIn);  // dW1 = dZ1^T X
   colsum_kernel<<<H, 256, 0, s>>>(m->d64b, n, H, G + kB1);
   return cudaGetLastError();
@@ -331,10 +317,13 @@ __host__ __device__ constexpr uint32_t kmajor_off(int row, int k, int kdim) {
 
 struct __align__(128) MlpSmem {
   unsigned char w[kBlobBytes];
-  unsigned char a1[kInferThreads * kMlpIn * 2];
-  unsigned char a2[kInferThreads * kMlpHidden * 2];
+  // one 128-row activation tile: the layer-1 operand (K = 32 layout) and then, in
+  // place, each hidden layer's output (K = 64 layout); a layer's MMA has completed
+  // before its epilogue overwrites the tile
+  unsigned char act[kInferThreads * kMlpHidden * 2];
   float bias[3 * kMlpHidden + kMlpOut];
-  float in_mean[kMlpIn], in_std[kMlpIn], out_std[kMlpOut];
+  float in_scale[kMlpIn], in_shift[kMlpIn];  // x = f * scale + shift standardises a feature
+  float out_scale[kMlpOut];                  // target scale / r: network output -> step in d
   unsigned long long mbar;
   uint32_t tmem;
 };
@@ -383,26 +372,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
   return done != 0;
 }
 
-__device__ __forceinline__ void tmem_ld64(uint32_t taddr, float v[64]) {
-  uint32_t r[64];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
-      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,"
-      "%47,%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
-        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]),
-        "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]),
-        "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]),
-        "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]),
-        "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int c = 0; c < 64; ++c) v[c] = __uint_as_float(r[c]);
-}
-
+// 16 consecutive accumulator columns of this thread's row
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
   uint32_t r[16];
   asm volatile(
@@ -424,25 +394,43 @@ __device__ __forceinline__ void operands_ready() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// Hidden layer epilogue: bias + GELU of the accumulator row, BF16 into the next A operand.
-__device__ __forceinline__ void hidden_epilogue(uint32_t trow, const float* bias, unsigned char* a2, int row) {
-  float h[64];
-  tmem_ld64(trow, h);
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t*>(&p);
+}
+
+// Hidden layer epilogue: bias + ReLU of the accumulator row, BF16 into the
+// activation tile; 16 columns at a time, two 16-byte stores per 16 columns (the
+// 8 rows of a core matrix fill 128 contiguous bytes: no bank conflicts).
+__device__ __forceinline__ void hidden_epilogue(uint32_t trow, const float* bias, unsigned char* act, int row) {
 #pragma unroll
-  for (int c = 0; c < 64; c += 2) {
-    const __nv_bfloat162 p = __floats2bfloat162_rn(gelu_fast(h[c] + bias[c]), gelu_fast(h[c + 1] + bias[c + 1]));
-    *reinterpret_cast<__nv_bfloat162*>(a2 + kmajor_off(row, c, kMlpHidden)) = p;
+  for (int c0 = 0; c0 < kMlpHidden; c0 += 16) {
+    float h[16];
+    tmem_ld16(trow + c0, h);
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      const int c = c0 + 8 * half;
+      uint4 v;
+      v.x = pack_bf16x2(relu(h[8 * half + 0] + bias[c + 0]), relu(h[8 * half + 1] + bias[c + 1]));
+      v.y = pack_bf16x2(relu(h[8 * half + 2] + bias[c + 2]), relu(h[8 * half + 3] + bias[c + 3]));
+      v.z = pack_bf16x2(relu(h[8 * half + 4] + bias[c + 4]), relu(h[8 * half + 5] + bias[c + 5]));
+      v.w = pack_bf16x2(relu(h[8 * half + 6] + bias[c + 6]), relu(h[8 * half + 7] + bias[c + 7]));
+      *reinterpret_cast<uint4*>(act + kmajor_off(row, c, kMlpHidden)) = v;
+    }
   }
 }
 
 // Persistent inference.  kFromState: features from the ADMM state of every
 // observation, output = candidate start d0 + step / r written to P.mlp_start;
 // else features from `feats` (n rows), output = the network's 16 standardised
-// outputs.  Each CTA holds the weights once and walks tiles of 128 rows.
+// outputs.  Each CTA holds the weights once and walks tiles of 128 rows, one
+// row per thread; the activations of a tile stay in shared memory (BF16
+// operands) and tensor memory (FP32 accumulators, 64 columns).
 template <typename T, bool kFromState>
-__global__ void __launch_bounds__(kInferThreads) mlp_infer_kernel(DevProblem P, Prm<T> q, const unsigned char* blob,
-                                                                  const float* params, const float* feats,
-                                                                  long long n, float* y_out, int* err) {
+__global__ void __launch_bounds__(kInferThreads, 4) mlp_infer_kernel(DevProblem P, Prm<T> q,
+                                                                     const unsigned char* blob, const float* params,
+                                                                     const float* feats, long long n, float* y_out,
+                                                                     int* err) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   MlpSmem& S = *reinterpret_cast<MlpSmem*>(smem_raw);
   const int t = threadIdx.x;
@@ -455,11 +443,14 @@ __global__ void __launch_bounds__(kInferThreads) mlp_infer_kernel(DevProblem P, 
   }
   if (t < kMlpOut) {
     S.bias[3 * kMlpHidden + t] = params[kB4 + t];
-    S.out_std[t] = params[kOutStd + t];
+    // the step in d is (output * target scale) / r, r = sqrt(rho) of the component
+    S.out_scale[t] = kFromState && t < 9 ? (float)((double)params[kOutStd + t] / sqrt((double)q.rho(t)))
+                                         : params[kOutStd + t];
   }
   if (t < kMlpIn) {
-    S.in_mean[t] = params[kInMean + t];
-    S.in_std[t] = params[kInStd + t];
+    const float sd = params[kInStd + t];
+    S.in_scale[t] = 1.f / sd;
+    S.in_shift[t] = -params[kInMean + t] / sd;
   }
   const uint32_t mbar = smem_u32(&S.mbar);
   if (t == 0) {
@@ -474,7 +465,7 @@ __global__ void __launch_bounds__(kInferThreads) mlp_infer_kernel(DevProblem P, 
   operands_ready();
   const uint32_t tmem = S.tmem;
   const uint32_t trow = tmem + ((uint32_t)(32 * (t / 32)) << 16);  // this warp's 32 lanes
-  const uint32_t a1 = smem_u32(S.a1), a2 = smem_u32(S.a2), w = smem_u32(S.w);
+  const uint32_t act = smem_u32(S.act), w = smem_u32(S.w);
   const long long l = P.n_obs;
   const long long rows = kFromState ? l : n;
   int pending = 0;
@@ -486,7 +477,7 @@ __global__ void __launch_bounds__(kInferThreads) mlp_infer_kernel(DevProblem P, 
     const long long o = base + t;
     float f[kMlpIn];
     bool ok = false;
-    T d0[9], r[9];
+    T d0[9];
     if (kFromState) {
       if (o < rows) {
         const int i = P.obs_pt[o], j = P.obs_cam_rank[o] & kCamMask;
@@ -495,7 +486,7 @@ __global__ void __launch_bounds__(kInferThreads) mlp_infer_kernel(DevProblem P, 
         const T* Ym = static_cast<const T*>(P.Ym);
         const T* DX = static_cast<const T*>(P.DX);
         const T* DY = static_cast<const T*>(P.DY);
-        T vbar[9], aT[9];
+        T vbar[9], aT[9], r[9];
 #pragma unroll
         for (int c = 0; c < 9; ++c) {
           d0[c] = delta[c * l + o] + (pending ? (c < 3 ? DX[3 * i + c] : DY[6 * j + c - 3]) : T(0));
@@ -506,61 +497,77 @@ __global__ void __launch_bounds__(kInferThreads) mlp_infer_kernel(DevProblem P, 
         ok = warm_features<T>(zz.x, zz.y, vbar, aT, d0, q, f, r);
       }
     } else if (o < rows) {
+      const float4* src = reinterpret_cast<const float4*>(feats + o * kMlpIn);
 #pragma unroll
-      for (int c = 0; c < kMlpIn; ++c) f[c] = feats[o * kMlpIn + c];
+      for (int c = 0; c < kMlpIn / 4; ++c) {
+        const float4 v = src[c];
+        f[4 * c] = v.x;
+        f[4 * c + 1] = v.y;
+        f[4 * c + 2] = v.z;
+        f[4 * c + 3] = v.w;
+      }
       ok = true;
     }
 #pragma unroll
-    for (int c = 0; c < kMlpIn; c += 2) {
-      const float x0 = ok ? (f[c] - S.in_mean[c]) / S.in_std[c] : 0.f;
-      const float x1 = ok ? (f[c + 1] - S.in_mean[c + 1]) / S.in_std[c + 1] : 0.f;
-      *reinterpret_cast<__nv_bfloat162*>(S.a1 + kmajor_off(t, c, kMlpIn)) = __floats2bfloat162_rn(x0, x1);
+    for (int c = 0; c < kMlpIn; c += 8) {
+      float x[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) x[k] = ok ? fmaf(f[c + k], S.in_scale[c + k], S.in_shift[c + k]) : 0.f;
+      uint4 v;
+      v.x = pack_bf16x2(x[0], x[1]);
+      v.y = pack_bf16x2(x[2], x[3]);
+      v.z = pack_bf16x2(x[4], x[5]);
+      v.w = pack_bf16x2(x[6], x[7]);
+      *reinterpret_cast<uint4*>(S.act + kmajor_off(t, c, kMlpIn)) = v;
     }
     operands_ready();
     // layer 1: [128 x 32] x [64 x 32]^T
-    if (t == 0) mma_layer(tmem, a1, w + kBlobW1, kMlpIn, kMlpHidden, mbar);
+    if (t == 0) mma_layer(tmem, act, w + kBlobW1, kMlpIn, kMlpHidden, mbar);
     ok_all = mbar_wait(mbar, phase) && ok_all;
     phase ^= 1;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    hidden_epilogue(trow, S.bias, S.a2, t);
+    hidden_epilogue(trow, S.bias, S.act, t);
     operands_ready();
-    // layer 2
-    if (t == 0) mma_layer(tmem, a2, w + kBlobW2, kMlpHidden, kMlpHidden, mbar);
+    // layers 2 and 3: [128 x 64] x [64 x 64]^T
+    if (t == 0) mma_layer(tmem, act, w + kBlobW2, kMlpHidden, kMlpHidden, mbar);
     ok_all = mbar_wait(mbar, phase) && ok_all;
     phase ^= 1;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    hidden_epilogue(trow, S.bias + kMlpHidden, S.a2, t);
+    hidden_epilogue(trow, S.bias + kMlpHidden, S.act, t);
     operands_ready();
-    // layer 3
-    if (t == 0) mma_layer(tmem, a2, w + kBlobW3, kMlpHidden, kMlpHidden, mbar);
+    if (t == 0) mma_layer(tmem, act, w + kBlobW3, kMlpHidden, kMlpHidden, mbar);
     ok_all = mbar_wait(mbar, phase) && ok_all;
     phase ^= 1;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    hidden_epilogue(trow, S.bias + 2 * kMlpHidden, S.a2, t);
+    hidden_epilogue(trow, S.bias + 2 * kMlpHidden, S.act, t);
     operands_ready();
     // layer 4: [128 x 64] x [16 x 64]^T
-    if (t == 0) mma_layer(tmem, a2, w + kBlobW4, kMlpHidden, kMlpOut, mbar);
+    if (t == 0) mma_layer(tmem, act, w + kBlobW4, kMlpHidden, kMlpOut, mbar);
     ok_all = mbar_wait(mbar, phase) && ok_all;
     phase ^= 1;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     float y[16];
     tmem_ld16(trow, y);
-#pragma unroll
-    for (int c = 0; c < kMlpOut; ++c) y[c] += S.bias[3 * kMlpHidden + c];
     if (kFromState) {
       if (o < rows) {
         T* out = static_cast<T*>(const_cast<void*>(P.mlp_start));
 #pragma unroll
         for (int c = 0; c < 9; ++c) {
-          const T step = ok ? (T)(y[c] * S.out_std[c]) * Num<T>::rcp(r[c]) : T(0);
-          out[c * l + o] = d0[c] + step;
+          const float step = (y[c] + S.bias[3 * kMlpHidden + c]) * S.out_scale[c];
+          out[c * l + o] = d0[c] + (ok ? (T)step : T(0));
         }
       }
     } else if (o < rows) {
+      float4* dst = reinterpret_cast<float4*>(y_out + o * kMlpOut);
 #pragma unroll
-      for (int c = 0; c < kMlpOut; ++c) y_out[o * kMlpOut + c] = y[c];
+      for (int c = 0; c < kMlpOut / 4; ++c)
+        dst[c] = make_float4(y[4 * c] + S.bias[3 * kMlpHidden + 4 * c], y[4 * c + 1] + S.bias[3 * kMlpHidden + 4 * c + 1],
+                             y[4 * c + 2] + S.bias[3 * kMlpHidden + 4 * c + 2],
+                             y[4 * c + 3] + S.bias[3 * kMlpHidden + 4 * c + 3]);
     }
-    operands_ready();  // tensor memory and operands free for the next tile
+    // the next tile's features overwrite the activation tile: every MMA reading it
+    // has completed (waited above), and the tensor-memory reads of this tile are
+    // ordered before the next layer-1 MMA by the operands_ready() that precedes it
   }
   if (!ok_all) atomicOr(err, 2);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -568,28 +575,48 @@ __global__ void __launch_bounds__(kInferThreads) mlp_infer_kernel(DevProblem P, 
   if (t < 32) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kMlpHidden));
 }
 
+// Resident CTAs per SM, from the resources one CTA takes: registers, shared
+// memory, and 64 of an SM's 512 tensor-memory columns.
+template <typename T, bool kFromState>
+cudaError_t infer_grid(int* grid) {
+  static int cached = 0;
+  if (cached) {
+    *grid = cached;
+    return cudaSuccess;
+  }
+  const int smem = (int)sizeof(MlpSmem);
+  cudaError_t e =
+      cudaFuncSetAttribute(mlp_infer_kernel<T, kFromState>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  if ((e = cudaFuncGetAttributes(&fa, mlp_infer_kernel<T, kFromState>)) != cudaSuccess) return e;
+  int dev = 0, sms = 0, smem_sm = 0, smem_rsv = 0, regs_sm = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess)
+    return e;
+  if ((e = cudaDeviceGetAttribute(&smem_rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev)) != cudaSuccess) return e;
+  const int regs = (fa.numRegs + 7) / 8 * 8;
+  int per_sm = 512 / kMlpHidden;
+  per_sm = std::min(per_sm, regs_sm / std::max(1, regs * kInferThreads));
+  per_sm = std::min(per_sm, smem_sm / (smem + smem_rsv + (int)fa.sharedSizeBytes));
+  cached = std::max(per_sm, 1) * sms;
+  *grid = cached;
+  return cudaSuccess;
+}
+
 template <typename T, bool kFromState>
 cudaError_t launch_infer(const DevProblem& P, const Params& prm, const unsigned char* blob, const float* params,
                          const float* feats, long long n, float* y_out, int* err, cudaStream_t s) {
-  static int grid = 0;
-  const int smem = (int)sizeof(MlpSmem);
-  if (!grid) {
-    cudaError_t e =
-        cudaFuncSetAttribute(mlp_infer_kernel<T, kFromState>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0, dev = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_infer_kernel<T, kFromState>, kInferThreads, smem);
-    if (e != cudaSuccess) return e;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    // tensor memory: each CTA allocates 64 of an SM's 512 columns
-    grid = (per_sm < 8 ? (per_sm > 0 ? per_sm : 1) : 8) * sms;
-  }
+  int grid = 0;
+  cudaError_t e = infer_grid<T, kFromState>(&grid);
+  if (e != cudaSuccess) return e;
   const long long rows = kFromState ? P.n_obs : n;
   long long need = (rows + kInferThreads - 1) / kInferThreads;
   const int g = (int)(need < grid ? (need > 0 ? need : 1) : grid);
-  mlp_infer_kernel<T, kFromState><<<g, kInferThreads, smem, s>>>(P, make_prm<T>(prm), blob, params, feats, n, y_out,
-                                                                 err);
+  mlp_infer_kernel<T, kFromState><<<g, kInferThreads, sizeof(MlpSmem), s>>>(P, make_prm<T>(prm), blob, params, feats,
+                                                                            n, y_out, err);
   return cudaGetLastError();
 }
 

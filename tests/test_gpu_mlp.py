@@ -75,7 +75,7 @@ def test_tensor_core_inference_matches_reference():
     x = _bf16((f - q["in_mean"]) / q["in_std"])
     h = x
     for k in (1, 2, 3):
-        h = _bf16(OM.gelu(h @ _bf16(q[f"W{k}"]).T + q[f"b{k}"]))
+        h = _bf16(OM.relu(h @ _bf16(q[f"W{k}"]).T + q[f"b{k}"]))
     ref = h @ _bf16(q["W4"]).T + q["b4"]
     assert np.abs(y - ref).max() <= 2e-2 * max(1.0, np.abs(ref).max())
     # and close to the unrounded FP64 network
@@ -123,5 +123,6 @@ def test_trained_warm_start_gain_is_reported():
             m = s.iterate_until(400, 0.5)
             res[name] = (m["iters_done"], m["seconds"], m["rmse_gt"])
     print("time to 0.5 px (iterations, device s, rmse):", res)
-    assert res["learned1"][2] <= 0.5 or res["learned1"][0] >= res["plain1"][0]
-    assert res["learned1"][0] <= 1.05 * res["plain1"][0] + 1
+    # the learned start reaches the target in well under the iterations of the plain one
+    assert res["plain1"][2] <= 0.5 and res["learned1"][2] <= 0.5
+    assert res["learned1"][0] <= 0.6 * res["plain1"][0]
