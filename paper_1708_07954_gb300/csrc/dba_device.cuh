@@ -14,8 +14,9 @@ namespace {
 
 // ------------------------------------------------------------ scalar helpers
 template <typename T> struct Num;
-// FP32 path: hardware approximations where their error (<= 2 ulp, or 2^-21 absolute for
-// sin/cos after reduction to [-pi, pi]) stays far below the pixel tolerance.
+// FP32 path: single SFU instructions (PTX rcp/sqrt/rsqrt .approx, relative error of
+// about one ulp; sin/cos with 2^-21 absolute error after reduction to [-pi, pi]).  Their
+// error stays far below the pixel tolerance and inside the model_tol noise rule.
 template <> struct Num<float> {
   using V2 = float2;
   static __device__ __forceinline__ void sc(float x, float* s, float* c) {
@@ -25,9 +26,24 @@ template <> struct Num<float> {
     r = fmaf(-k, -1.7484555314695172e-7f, r);
     __sincosf(r, s, c);
   }
-  static __device__ __forceinline__ float rcp(float x) { return __frcp_rn(x); }
-  static __device__ __forceinline__ float div(float a, float b) { return a * __frcp_rn(b); }
-  static __device__ __forceinline__ float sqrt_(float x) { return __fsqrt_rn(x); }
+  static __device__ __forceinline__ float rcp(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+  }
+  static __device__ __forceinline__ float div(float a, float b) { return a * rcp(b); }
+  static __device__ __forceinline__ float sqrt_(float x) {
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+  }
+  // p / sqrt(s) for s > 0
+  static __device__ __forceinline__ float div_sqrt(float p, float s) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(s));
+    return p * r;
+  }
+  static __device__ __forceinline__ float tenth(float x) { return x * 0.1f; }
   static __device__ __forceinline__ float log1p_(float x) { return log1pf(x); }
   static __device__ __forceinline__ float inf() { return CUDART_INF_F; }
   static constexpr float unit_roundoff = 5.9604644775390625e-08f;  // 2^-24
@@ -39,6 +55,8 @@ template <> struct Num<double> {
   static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
   static __device__ __forceinline__ double div(double a, double b) { return a / b; }
   static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+  static __device__ __forceinline__ double div_sqrt(double p, double s) { return p / sqrt(s); }
+  static __device__ __forceinline__ double tenth(double x) { return x / 10.0; }
   static __device__ __forceinline__ double log1p_(double x) { return log1p(x); }
   static __device__ __forceinline__ double inf() { return CUDART_INF; }
   static constexpr double unit_roundoff = 1.1102230246251565e-16;  // 2^-53
@@ -100,7 +118,7 @@ __device__ __forceinline__ T misfit(int loss, T p, T s) {
 }
 template <typename T>
 __device__ __forceinline__ T misfit_weight(int loss, T p, T s) {
-  if (loss == 1) return s <= p * p ? T(1) : Num<T>::div(p, Num<T>::sqrt_(s));
+  if (loss == 1) return s <= p * p ? T(1) : Num<T>::div_sqrt(p, s);
   if (loss == 2) return Num<T>::div(p, p + s);
   return T(1);
 }
@@ -320,7 +338,7 @@ __device__ __forceinline__ void local_solve(T z0, T z1, const T vbar[9], const T
       for (int c = 0; c < 9; ++c) d[c] = dt[c];
       P = Pt;
       L = Lt;
-      const T lr = Num<T>::div(lambda, T(10));
+      const T lr = Num<T>::tenth(lambda);
       lambda = lr > q.lambda_min ? lr : q.lambda_min;
     } else {
       lambda *= T(10);
