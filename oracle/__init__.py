@@ -95,6 +95,16 @@ def lib():
         L.ora_dense_lm.argtypes = [cfgp, ctypes.c_int, ctypes.c_int, ctypes.c_long, ip, ip, dp, dp, dp,
                                    ctypes.c_int, dp]
         L.ora_dense_lm.restype = ctypes.c_int
+        lp = ctypes.POINTER(ctypes.c_long)
+        L.ora_block_objective.argtypes = [cfgp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ip, ip, dp, dp, dp,
+                                          dp, dp, dp, dp]
+        L.ora_block_objective.restype = ctypes.c_double
+        L.ora_block_solve.argtypes = [cfgp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ip, ip, dp, dp, dp, dp,
+                                      dp, dp, dp]
+        L.ora_block_iterate.argtypes = [cfgp, ctypes.c_int, ctypes.c_int, ctypes.c_long, ip, ip, dp, dp,
+                                        ctypes.c_long, lp, lp, ip, ip, lp, ip, lp, ip, dp, dp, dp, dp, dp, dp,
+                                        ctypes.c_int, ctypes.c_int, ctypes.POINTER(Metrics)]
+        L.ora_block_iterate.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -109,6 +119,11 @@ def _d(a):
 def _i(a):
     assert a.dtype == np.int32 and a.flags.c_contiguous
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def _l(a):
+    assert a.dtype == np.int64 and a.flags.c_contiguous
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_long))
 
 
 def _f64(a):
@@ -231,3 +246,97 @@ def dense_lm(cfg, scene, cams=None, pts=None, max_iters=200):
     if it < 0:
         raise ValueError("dense LM failed")
     return cams, pts, obj.value, it
+
+
+# ------------------------------------------------ generalized block step, Eq. (14)
+class BlockLayout:
+    """Blocks of the generalized step (Sec. 3.1.4, Eq. 14) under this reading: points
+    ranked by (smallest observing camera index, point index) and cut into groups of
+    `pi` consecutive ranks; cameras cut into groups of `kappa` consecutive indices; one
+    block per (point group, camera group) pair holding at least one observation.
+    Blocks run in (point group, camera group) order; inside a block the point copies
+    follow rank, the camera copies index, the observations (local point, local camera).
+    """
+
+    def __init__(self, scene, pi, kappa):
+        if pi < 1 or kappa < 1:
+            raise ValueError("pi and kappa must be >= 1")
+        pt = np.asarray(scene.pt_idx, np.int64)
+        cam = np.asarray(scene.cam_idx, np.int64)
+        n, m = scene.n_pts, scene.n_cams
+        first = np.full(n, np.iinfo(np.int64).max)
+        np.minimum.at(first, pt, cam)
+        order = np.lexsort((np.arange(n), first))
+        rank = np.empty(n, np.int64)
+        rank[order] = np.arange(n)
+        pg, cg = rank[pt] // pi, cam // kappa
+        n_cg = (m + kappa - 1) // kappa
+        bkey = pg * n_cg + cg
+        uniq_b, blk = np.unique(bkey, return_inverse=True)
+        self.n_blocks = len(uniq_b)
+        # observations in block order, then (point rank, camera)
+        self.blk_obs = np.lexsort((cam, rank[pt], blk)).astype(np.int64)
+        b_sorted = blk[self.blk_obs]
+        self.obs_off = np.searchsorted(b_sorted, np.arange(self.n_blocks + 1)).astype(np.int64)
+        # point copies: distinct (block, point rank) pairs
+        pkey = blk * n + rank[pt]
+        upk, pinv = np.unique(pkey, return_inverse=True)
+        self.pc_pt = order[upk % n].astype(np.int32)
+        self.pc_off = np.searchsorted(upk // n, np.arange(self.n_blocks + 1)).astype(np.int64)
+        # camera copies: distinct (block, camera) pairs
+        ckey = blk * m + cam
+        uck, cinv = np.unique(ckey, return_inverse=True)
+        self.cc_cam = (uck % m).astype(np.int32)
+        self.cc_off = np.searchsorted(uck // m, np.arange(self.n_blocks + 1)).astype(np.int64)
+        o = self.blk_obs
+        self.obs_lp = (pinv[o] - self.pc_off[blk[o]]).astype(np.int32)
+        self.obs_lc = (cinv[o] - self.cc_off[blk[o]]).astype(np.int32)
+        self.n_pc, self.n_cc = len(self.pc_pt), len(self.cc_cam)
+
+
+def block_objective(cfg, opl, ocl, z, xbar, ybar, rx, sy, X, Y):
+    np_, nc, no = len(xbar) // 3, len(ybar) // 6, len(opl)
+    return lib().ora_block_objective(ctypes.byref(cfg), np_, nc, no, _i(np.asarray(opl, np.int32)),
+                                     _i(np.asarray(ocl, np.int32)), _d(_f64(z)), _d(_f64(xbar)),
+                                     _d(_f64(ybar)), _d(_f64(rx)), _d(_f64(sy)), _d(_f64(X)), _d(_f64(Y)))
+
+
+def block_solve(cfg, opl, ocl, z, xbar, ybar, rx, sy, X0, Y0):
+    X, Y = _f64(X0).copy(), _f64(Y0).copy()
+    np_, nc, no = len(xbar) // 3, len(ybar) // 6, len(opl)
+    lib().ora_block_solve(ctypes.byref(cfg), np_, nc, no, _i(np.asarray(opl, np.int32)),
+                          _i(np.asarray(ocl, np.int32)), _d(_f64(z)), _d(_f64(xbar)), _d(_f64(ybar)),
+                          _d(_f64(rx)), _d(_f64(sy)), _d(X), _d(Y))
+    return X, Y
+
+
+class BlockState:
+    """ADMM state with block subproblems: point copies/duals [n_pc, 3] and camera
+    copies/duals [n_cc, 6] in layout order, cams [m, 6], pts [n, 3]."""
+
+    def __init__(self, scene, pi, kappa, cams=None, pts=None):
+        self.scene = scene
+        self.layout = BlockLayout(scene, pi, kappa)
+        B = self.layout
+        self.cams = _f64(scene.cams0 if cams is None else cams).copy()
+        self.pts = _f64(scene.pts0 if pts is None else pts).copy()
+        self.pcopies = self.pts[B.pc_pt].copy()
+        self.ccopies = self.cams[B.cc_cam].copy()
+        self.pduals = np.zeros((B.n_pc, 3))
+        self.cduals = np.zeros((B.n_cc, 6))
+        self.k = 0
+
+    def iterate(self, cfg, iters, nthreads=0, with_gt=True):
+        s, B = self.scene, self.layout
+        m = Metrics()
+        zt = _f64(s.z_true) if with_gt else None
+        rc = lib().ora_block_iterate(ctypes.byref(cfg), s.n_cams, s.n_pts, s.n_obs, _i(s.pt_idx),
+                                     _i(s.cam_idx), _d(_f64(s.z)), _d(zt), B.n_blocks, _l(B.obs_off),
+                                     _l(B.blk_obs), _i(B.obs_lp), _i(B.obs_lc), _l(B.pc_off), _i(B.pc_pt),
+                                     _l(B.cc_off), _i(B.cc_cam), _d(self.pcopies), _d(self.pduals),
+                                     _d(self.ccopies), _d(self.cduals), _d(self.cams), _d(self.pts), iters,
+                                     nthreads, ctypes.byref(m))
+        if rc != 0:
+            raise ValueError("oracle rejected the block problem")
+        self.k += iters
+        return m.as_dict()

@@ -415,10 +415,11 @@ void ora_eval(const ora_config* c, int n_cams, int n_pts, long n_obs, const int*
     } else {
       invalid += 1;
     }
-    for (int k = 0; k < 9; ++k) {
-      double d = copies[9 * o + k] - (k < 3 ? x[k] : y[k - 3]);
-      pr += d * d;
-    }
+    if (copies)
+      for (int k = 0; k < 9; ++k) {
+        double d = copies[9 * o + k] - (k < 3 ? x[k] : y[k - 3]);
+        pr += d * d;
+      }
     if (cams_prev && pts_prev) {
       for (int k = 0; k < 3; ++k) {
         double d = c->rho_x * (x[k] - pts_prev[3 * (long)pt_idx[o] + k]);
@@ -518,4 +519,265 @@ int ora_dense_lm(const ora_config* c, int n_cams, int n_pts, long n_obs, const i
   if (final_objective) *final_objective = obj;
   free(H); free(g); free(neg_g); free(d); free(cams_t); free(pts_t);
   return it;
+}
+
+/* ------------------------------------------ generalized block step, Eq. (14) */
+
+/* Eq. (14) for one block: misfits of its observations + dual terms + rho/2 penalties
+ * of its copies.  Unknown order: point copies (3 each), then camera copies (6 each). */
+double ora_block_objective(const ora_config* c, int np, int nc, int no, const int* opl, const int* ocl,
+                           const double* z, const double* xbar, const double* ybar, const double* rx,
+                           const double* sy, const double* X, const double* Y) {
+  double L = 0.0;
+  for (int k = 0; k < no; ++k) {
+    double zp[2];
+    double depth = ora_project(c, X + 3 * opl[k], Y + 6 * ocl[k], zp);
+    if (!(depth > c->eps_depth)) return INFINITY;
+    double e0 = z[2 * k] - zp[0], e1 = z[2 * k + 1] - zp[1];
+    L += ora_loss(c->loss, c->loss_param, e0 * e0 + e1 * e1);
+  }
+  for (int p = 0; p < np; ++p)
+    for (int a = 0; a < 3; ++a) {
+      double d = X[3 * p + a] - xbar[3 * p + a];
+      L += rx[3 * p + a] * d + 0.5 * rho_of(c, a) * d * d;
+    }
+  for (int q = 0; q < nc; ++q)
+    for (int a = 0; a < 6; ++a) {
+      double d = Y[6 * q + a] - ybar[6 * q + a];
+      L += sy[6 * q + a] * d + 0.5 * rho_of(c, 3 + a) * d * d;
+    }
+  return L;
+}
+
+/* The local solve of Eq. (9) carried over to the block: each step linearises every
+ * observation of the block, assembles the dense Gauss-Newton system of Eq. (14)
+ *   g = sum_k -2 w_k J_k^T e_k + duals + diag(rho) (v - vbar),
+ *   H = sum_k 2 w_k J_k^T J_k + diag(rho),
+ * solves (H + lambda I) d = -g by Cholesky and accepts or rejects as the local
+ * solve does (lambda starts at lm_lambda0 * mean diag H; noise bound summed over
+ * the block's observations). */
+void ora_block_solve(const ora_config* c, int np, int nc, int no, const int* opl, const int* ocl,
+                     const double* z, const double* xbar, const double* ybar, const double* rx,
+                     const double* sy, double* X, double* Y) {
+  const int n = 3 * np + 6 * nc;
+  double* H = (double*)malloc((size_t)n * n * sizeof(double));
+  double* g = (double*)malloc((size_t)n * sizeof(double));
+  double* neg_g = (double*)malloc((size_t)n * sizeof(double));
+  double* d = (double*)malloc((size_t)n * sizeof(double));
+  double* Xt = (double*)malloc((size_t)(3 * np + 1) * sizeof(double));
+  double* Yt = (double*)malloc((size_t)(6 * nc + 1) * sizeof(double));
+  if (!H || !g || !neg_g || !d || !Xt || !Yt) {
+    free(H); free(g); free(neg_g); free(d); free(Xt); free(Yt);
+    return;
+  }
+  double lambda = -1.0;
+  double L_old = ora_block_objective(c, np, nc, no, opl, ocl, z, xbar, ybar, rx, sy, X, Y);
+  for (int step = 0; step < c->inner_steps; ++step) {
+    memset(H, 0, (size_t)n * n * sizeof(double));
+    memset(g, 0, (size_t)n * sizeof(double));
+    double noise_terms = 0.0;
+    for (int k = 0; k < no; ++k) {
+      const double* x = X + 3 * opl[k];
+      const double* y = Y + 6 * ocl[k];
+      double zp[2], J[18];
+      double depth = ora_project(c, x, y, zp);
+      if (!(depth > c->eps_depth)) continue; /* no misfit term at this linearisation point */
+      double e0 = z[2 * k] - zp[0], e1 = z[2 * k + 1] - zp[1];
+      double w = ora_weight(c->loss, c->loss_param, e0 * e0 + e1 * e1);
+      ora_jacobian(c, x, y, J);
+      int col[9];
+      for (int a = 0; a < 3; ++a) col[a] = 3 * opl[k] + a;
+      for (int a = 0; a < 6; ++a) col[3 + a] = 3 * np + 6 * ocl[k] + a;
+      for (int a = 0; a < 9; ++a) {
+        g[col[a]] += -2.0 * w * (J[a] * e0 + J[9 + a] * e1);
+        for (int b = 0; b < 9; ++b)
+          H[(size_t)col[a] * n + col[b]] += 2.0 * w * (J[a] * J[b] + J[9 + a] * J[9 + b]);
+      }
+      noise_terms += 2.0 * w * sqrt(e0 * e0 + e1 * e1) * (fabs(z[2 * k]) + fabs(z[2 * k + 1]));
+    }
+    for (int p = 0; p < np; ++p)
+      for (int a = 0; a < 3; ++a) {
+        int u = 3 * p + a;
+        g[u] += rx[u] + rho_of(c, a) * (X[u] - xbar[u]);
+        H[(size_t)u * n + u] += rho_of(c, a);
+      }
+    for (int q = 0; q < nc; ++q)
+      for (int a = 0; a < 6; ++a) {
+        int u = 3 * np + 6 * q + a;
+        g[u] += sy[6 * q + a] + rho_of(c, 3 + a) * (Y[6 * q + a] - ybar[6 * q + a]);
+        H[(size_t)u * n + u] += rho_of(c, 3 + a);
+      }
+    if (lambda < 0.0) {
+      double tr = 0.0;
+      for (int u = 0; u < n; ++u) tr += H[(size_t)u * n + u];
+      lambda = c->lm_lambda0 * tr / (double)n;
+    }
+    for (int u = 0; u < n; ++u) {
+      H[(size_t)u * n + u] += lambda;
+      neg_g[u] = -g[u];
+    }
+    if (ora_chol_solve(n, H, neg_g, d) != 0) {
+      lambda *= 10.0;
+      continue;
+    }
+    double gd = 0.0, dd = 0.0;
+    for (int u = 0; u < n; ++u) {
+      gd += g[u] * d[u];
+      dd += d[u] * d[u];
+    }
+    double pred = 0.5 * (lambda * dd - gd);
+    int trust = 0;
+    if (isfinite(L_old) && c->lm_model_tol > 0.0)
+      trust = pred <= c->lm_model_tol * 0x1p-53 * (fabs(L_old) + noise_terms);
+    for (int u = 0; u < 3 * np; ++u) Xt[u] = X[u] + d[u];
+    for (int u = 0; u < 6 * nc; ++u) Yt[u] = Y[u] + d[3 * np + u];
+    if (trust) {
+      int valid = 1;
+      for (int k = 0; k < no && valid; ++k) {
+        double zp[2];
+        valid = ora_project(c, Xt + 3 * opl[k], Yt + 6 * ocl[k], zp) > c->eps_depth;
+      }
+      if (valid) {
+        memcpy(X, Xt, (size_t)3 * np * sizeof(double));
+        memcpy(Y, Yt, (size_t)6 * nc * sizeof(double));
+        L_old -= pred;
+        lambda = fmax(lambda / 10.0, c->lm_lambda_min);
+      } else {
+        lambda *= 10.0;
+      }
+      continue;
+    }
+    double L_new = ora_block_objective(c, np, nc, no, opl, ocl, z, xbar, ybar, rx, sy, Xt, Yt);
+    if (L_new < L_old) {
+      memcpy(X, Xt, (size_t)3 * np * sizeof(double));
+      memcpy(Y, Yt, (size_t)6 * nc * sizeof(double));
+      L_old = L_new;
+      lambda = fmax(lambda / 10.0, c->lm_lambda_min);
+    } else {
+      lambda *= 10.0;
+    }
+  }
+  free(H); free(g); free(neg_g); free(d); free(Xt); free(Yt);
+}
+
+int ora_block_iterate(const ora_config* c, int n_cams, int n_pts, long n_obs, const int* pt_idx,
+                      const int* cam_idx, const double* z, const double* z_true, long n_blocks,
+                      const long* obs_off, const long* blk_obs, const int* obs_lp, const int* obs_lc,
+                      const long* pc_off, const int* pc_pt, const long* cc_off, const int* cc_cam,
+                      double* pcopies, double* pduals, double* ccopies, double* cduals, double* cams,
+                      double* pts, int iters, int nthreads, ora_metrics* metrics) {
+  if (n_cams < 0 || n_pts < 0 || n_obs < 0 || n_blocks < 0 || iters < 0) return -1;
+  if (check_indices(n_cams, n_pts, n_obs, pt_idx, cam_idx) != 0) return -1;
+  const long n_pc = pc_off[n_blocks], n_cc = cc_off[n_blocks];
+  for (long k = 0; k < n_pc; ++k)
+    if (pc_pt[k] < 0 || pc_pt[k] >= n_pts) return -1;
+  for (long k = 0; k < n_cc; ++k)
+    if (cc_cam[k] < 0 || cc_cam[k] >= n_cams) return -1;
+  if (obs_off[n_blocks] != n_obs) return -1;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+  (void)nthreads;
+#endif
+  double* sum_x = (double*)calloc((size_t)n_pts * 3 + 1, sizeof(double));
+  double* sum_y = (double*)calloc((size_t)n_cams * 6 + 1, sizeof(double));
+  long* cnt_x = (long*)calloc((size_t)n_pts + 1, sizeof(long));
+  long* cnt_y = (long*)calloc((size_t)n_cams + 1, sizeof(long));
+  double* pts_prev = (double*)malloc(((size_t)n_pts * 3 + 1) * sizeof(double));
+  double* cams_prev = (double*)malloc(((size_t)n_cams * 6 + 1) * sizeof(double));
+  if (!sum_x || !sum_y || !cnt_x || !cnt_y || !pts_prev || !cams_prev) {
+    free(sum_x); free(sum_y); free(cnt_x); free(cnt_y); free(pts_prev); free(cams_prev);
+    return -1;
+  }
+  int status = 0;
+  for (int it = 0; it < iters && status == 0; ++it) {
+    memcpy(pts_prev, pts, (size_t)n_pts * 3 * sizeof(double));
+    memcpy(cams_prev, cams, (size_t)n_cams * 6 * sizeof(double));
+
+    /* Eq. (14): every block's subproblem, warm-started at its copies. */
+#pragma omp parallel for schedule(dynamic, 16)
+    for (long b = 0; b < n_blocks; ++b) {
+      const int np = (int)(pc_off[b + 1] - pc_off[b]), nc = (int)(cc_off[b + 1] - cc_off[b]);
+      const int no = (int)(obs_off[b + 1] - obs_off[b]);
+      double* xbar = (double*)malloc((size_t)(3 * np + 1) * sizeof(double));
+      double* ybar = (double*)malloc((size_t)(6 * nc + 1) * sizeof(double));
+      double* zb = (double*)malloc((size_t)(2 * no + 1) * sizeof(double));
+      if (!xbar || !ybar || !zb) {
+        free(xbar); free(ybar); free(zb);
+        continue;
+      }
+      for (int p = 0; p < np; ++p)
+        for (int a = 0; a < 3; ++a) xbar[3 * p + a] = pts[3 * (long)pc_pt[pc_off[b] + p] + a];
+      for (int q = 0; q < nc; ++q)
+        for (int a = 0; a < 6; ++a) ybar[6 * q + a] = cams[6 * (long)cc_cam[cc_off[b] + q] + a];
+      for (int k = 0; k < no; ++k) {
+        zb[2 * k] = z[2 * blk_obs[obs_off[b] + k]];
+        zb[2 * k + 1] = z[2 * blk_obs[obs_off[b] + k] + 1];
+      }
+      ora_block_solve(c, np, nc, no, obs_lp + obs_off[b], obs_lc + obs_off[b], zb, xbar, ybar,
+                      pduals + 3 * pc_off[b], cduals + 6 * cc_off[b], pcopies + 3 * pc_off[b],
+                      ccopies + 6 * cc_off[b]);
+      free(xbar); free(ybar); free(zb);
+    }
+
+    /* Eqs. (10)-(11) over copies: x_i = mean over the copies of point i of (copy + r / rho_x),
+       y_j likewise, with the old duals. */
+    memset(sum_x, 0, (size_t)n_pts * 3 * sizeof(double));
+    memset(cnt_x, 0, (size_t)n_pts * sizeof(long));
+    for (long k = 0; k < n_pc; ++k) {
+      long i = pc_pt[k];
+      for (int a = 0; a < 3; ++a) sum_x[3 * i + a] += pcopies[3 * k + a] + pduals[3 * k + a] / rho_of(c, a);
+      cnt_x[i] += 1;
+    }
+    for (long i = 0; i < n_pts; ++i)
+      if (cnt_x[i] > 0)
+        for (int a = 0; a < 3; ++a) pts[3 * i + a] = sum_x[3 * i + a] / (double)cnt_x[i];
+    memset(sum_y, 0, (size_t)n_cams * 6 * sizeof(double));
+    memset(cnt_y, 0, (size_t)n_cams * sizeof(long));
+    for (long k = 0; k < n_cc; ++k) {
+      long j = cc_cam[k];
+      for (int a = 0; a < 6; ++a) sum_y[6 * j + a] += ccopies[6 * k + a] + cduals[6 * k + a] / rho_of(c, 3 + a);
+      cnt_y[j] += 1;
+    }
+    for (long j = 0; j < n_cams; ++j)
+      if (cnt_y[j] > 0)
+        for (int a = 0; a < 6; ++a) cams[6 * j + a] = sum_y[6 * j + a] / (double)cnt_y[j];
+
+    /* Eqs. (12)-(13) per copy, with the new consensus. */
+    for (long k = 0; k < n_pc; ++k)
+      for (int a = 0; a < 3; ++a)
+        pduals[3 * k + a] += rho_of(c, a) * (pcopies[3 * k + a] - pts[3 * (long)pc_pt[k] + a]);
+    for (long k = 0; k < n_cc; ++k)
+      for (int a = 0; a < 6; ++a)
+        cduals[6 * k + a] += rho_of(c, 3 + a) * (ccopies[6 * k + a] - cams[6 * (long)cc_cam[k] + a]);
+  }
+  if (metrics && status == 0) {
+    /* reprojection terms at consensus as ora_eval; residuals over the copies */
+    ora_eval(c, n_cams, n_pts, n_obs, pt_idx, cam_idx, z, z_true, NULL, cams, pts, NULL, NULL, metrics);
+    double pr = 0.0, dr = 0.0;
+    for (long k = 0; k < n_pc; ++k)
+      for (int a = 0; a < 3; ++a) {
+        long u = 3 * (long)pc_pt[k] + a;
+        double d = pcopies[3 * k + a] - pts[u];
+        pr += d * d;
+        if (iters > 0) {
+          double q = rho_of(c, a) * (pts[u] - pts_prev[u]);
+          dr += q * q;
+        }
+      }
+    for (long k = 0; k < n_cc; ++k)
+      for (int a = 0; a < 6; ++a) {
+        long u = 6 * (long)cc_cam[k] + a;
+        double d = ccopies[6 * k + a] - cams[u];
+        pr += d * d;
+        if (iters > 0) {
+          double q = rho_of(c, 3 + a) * (cams[u] - cams_prev[u]);
+          dr += q * q;
+        }
+      }
+    metrics->primal_res = sqrt(pr);
+    metrics->dual_res = sqrt(dr);
+  }
+  free(sum_x); free(sum_y); free(cnt_x); free(cnt_y); free(pts_prev); free(cams_prev);
+  return status;
 }

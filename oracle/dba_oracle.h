@@ -83,7 +83,8 @@ int ora_admm_iterate(const ora_config* c, int n_cams, int n_pts, long n_obs, con
                      const int* cam_idx, const double* z, const double* z_true, double* copies,
                      double* duals, double* cams, double* pts, int iters, int nthreads,
                      ora_metrics* metrics);
-/* Metrics at consensus; cams_prev/pts_prev may be NULL (dual_res = 0). */
+/* Metrics at consensus; cams_prev/pts_prev may be NULL (dual_res = 0), copies may be
+ * NULL (primal_res = 0). */
 void ora_eval(const ora_config* c, int n_cams, int n_pts, long n_obs, const int* pt_idx,
               const int* cam_idx, const double* z, const double* z_true, const double* copies,
               const double* cams, const double* pts, const double* cams_prev,
@@ -95,6 +96,37 @@ void ora_eval(const ora_config* c, int n_cams, int n_pts, long n_obs, const int*
 int ora_dense_lm(const ora_config* c, int n_cams, int n_pts, long n_obs, const int* pt_idx,
                  const int* cam_idx, const double* z, double* cams, double* pts, int max_iters,
                  double* final_objective);
+
+/* ------------------------------------------ generalized block step, Eq. (14) */
+/* A block holds np point copies, nc camera copies and no observations; observation k
+ * links local point opl[k] and local camera ocl[k] with pixel z[2k..2k+1].  Arrays per
+ * copy: xbar/rx/X 3 values per point copy, ybar/sy/Y 6 per camera copy (consensus,
+ * unscaled dual, copy).  The block objective is Eq. (14): the sum of the misfits of
+ * the block's observations plus, per copy, the dual term and the rho/2 penalty;
+ * +INFINITY when an observation is behind its camera. */
+double ora_block_objective(const ora_config* c, int np, int nc, int no, const int* opl, const int* ocl,
+                           const double* z, const double* xbar, const double* ybar, const double* rx,
+                           const double* sy, const double* X, const double* Y);
+/* inner_steps damped Gauss-Newton steps on Eq. (14) over all 3 np + 6 nc unknowns of
+ * the block (dense normal matrix, Cholesky), with the local solve's damping, acceptance
+ * and noise rules; X, Y in/out. */
+void ora_block_solve(const ora_config* c, int np, int nc, int no, const int* opl, const int* ocl,
+                     const double* z, const double* xbar, const double* ybar, const double* rx,
+                     const double* sy, double* X, double* Y);
+/* ADMM with block subproblems.  Block b owns observations blk_obs[obs_off[b] .. obs_off[b+1])
+ * (ids into the caller's arrays; obs_lp/obs_lc give their local point/camera index, aligned
+ * with blk_obs), point copies pc_off[b] .. pc_off[b+1] of points pc_pt[.], camera copies
+ * cc_off[b] .. cc_off[b+1] of cameras cc_cam[.].  pcopies/pduals: 3 per point copy,
+ * ccopies/cduals: 6 per camera copy.  Each iteration: block solves (Eq. 14), consensus as
+ * the mean over copies of copy + dual / rho (Eqs. 10-11 over copies, old duals), dual
+ * ascent (Eqs. 12-13).  metrics (nullable): as ora_eval, with the primal residual over the
+ * copies and the dual residual summed over the copies.  Returns 0, or -1 on bad input. */
+int ora_block_iterate(const ora_config* c, int n_cams, int n_pts, long n_obs, const int* pt_idx,
+                      const int* cam_idx, const double* z, const double* z_true, long n_blocks,
+                      const long* obs_off, const long* blk_obs, const int* obs_lp, const int* obs_lc,
+                      const long* pc_off, const int* pc_pt, const long* cc_off, const int* cc_cam,
+                      double* pcopies, double* pduals, double* ccopies, double* cduals, double* cams,
+                      double* pts, int iters, int nthreads, ora_metrics* metrics);
 
 #ifdef __cplusplus
 }
