@@ -258,6 +258,54 @@ const char* dba_last_error(const dba_ctx* ctx);
 /* Frees the context and its device memory.  NULL is ignored. */
 void dba_destroy(dba_ctx* ctx);
 
+/* ---------------------------------------------------------------------------
+ * Block subproblems: the generalized update step (Sec. 3.1.4, Eq. 14).
+ *
+ * Instead of one observation, each update solves a block of up to
+ * block_points points and block_cams cameras together with all observations
+ * between them, over one copy of each of its points and cameras; consensus
+ * (Eqs. 10-11) averages copy + dual / rho over a point's (camera's) copies and
+ * the dual ascent (Eqs. 12-13) runs per copy.  Blocks: points ranked by
+ * (smallest observing camera index, point index) and cut into groups of
+ * block_points consecutive ranks; cameras cut into groups of block_cams
+ * consecutive indices; one block per (point group, camera group) pair that
+ * holds observations.  block_points = block_cams = 1 is the per-observation
+ * method of dba_iterate.  Each block's subproblem takes inner_steps damped
+ * Gauss-Newton steps with the damping, acceptance and noise rules of the
+ * per-observation solve (points eliminated, the reduced camera system
+ * factorised).  The context owns its device memory; inputs are host arrays in
+ * caller order, copied in.  Not thread-safe per context.
+ * ------------------------------------------------------------------------- */
+typedef struct dba_block_ctx dba_block_ctx;
+#define DBA_BLOCK_MAX_POINTS 32
+#define DBA_BLOCK_MAX_CAMERAS 4
+
+/* Validates cfg as dba_create does (tile_obs, use_graph are ignored) and
+ * 1 <= block_points <= 32, 1 <= block_cams <= 4 (EINVAL). */
+dba_status dba_block_create(const dba_config* cfg, int block_points, int block_cams, dba_block_ctx** out);
+/* Same arrays and checks as dba_set_observations, and a (point, camera) pair
+ * may appear once (EINVAL); builds the blocks and starts with copies at the
+ * initial estimate and zero duals. */
+dba_status dba_block_set_observations(dba_block_ctx* ctx, int32_t n_cams, int32_t n_pts, int64_t n_obs,
+                                      const int32_t* pt_idx, const int32_t* cam_idx, const double* z,
+                                      const double* cams0, const double* pts0);
+/* Reference pixels z_ref [n_obs][2] (e.g. noise-free projections) for rmse_gt,
+ * over observations with inlier[o] != 0 (inlier NULL: all). */
+dba_status dba_block_set_reference_pixels(dba_block_ctx* ctx, const double* z_ref, const uint8_t* inlier);
+/* n_iters iterations; stats (nullable) as dba_iterate, residuals over copies. */
+dba_status dba_block_iterate(dba_block_ctx* ctx, int n_iters, dba_stats* stats);
+/* Iterates until rmse_gt <= target (metrics after every iteration, included in
+ * stats->seconds) or max_iters; needs reference pixels (ESTATE). */
+dba_status dba_block_iterate_until(dba_block_ctx* ctx, int max_iters, double target_rmse_gt, dba_stats* stats);
+/* Consensus cameras [m][6] and points [n][3]. */
+dba_status dba_block_get_params(dba_block_ctx* ctx, double* cams_out, double* pts_out);
+/* Number of blocks, point copies and camera copies (any pointer may be NULL). */
+dba_status dba_block_layout(const dba_block_ctx* ctx, int64_t* n_blocks, int64_t* n_point_copies,
+                            int64_t* n_camera_copies);
+/* Message of the last failed call on ctx (ctx NULL: of the last failed create). */
+const char* dba_block_last_error(const dba_block_ctx* ctx);
+void dba_block_destroy(dba_block_ctx* ctx);
+
 #ifdef __cplusplus
 }
 #endif

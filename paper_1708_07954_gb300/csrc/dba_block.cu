@@ -1,0 +1,1083 @@
+// Block subproblems: the generalized update step of Sec. 3.1.4, Eq. (14).
+//
+// Each update solves, instead of one observation, a block of up to pi points and
+// kappa cameras with all observations between them, over one copy of each of its
+// points and cameras.  Blocks are formed by this reading of the paper: points
+// ranked by (smallest observing camera index, point index) and cut into groups of
+// pi consecutive ranks, cameras cut into groups of kappa consecutive indices, one
+// block per (point group, camera group) pair holding observations.
+//
+// GPU mapping: one warp per block, one lane per point copy (pi <= 32), camera
+// copies (kappa <= 4) shared by the warp in shared memory.  Each damped
+// Gauss-Newton step eliminates the points (3x3 per lane) and solves the reduced
+// camera system (at most 24 x 24, a Schur complement accumulated with warp
+// reductions) by a lane-per-row Cholesky factorisation.  Consensus (Eqs. 10-11
+// over copies) and dual ascent (Eqs. 12-13) run in FP64 over copy lists.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/dba.h"
+#include "dba_device.cuh"
+#include "dba_internal.h"
+
+namespace dba {
+namespace {
+
+constexpr int kBlkMaxCams = 4;
+constexpr int kBlkMaxU = 6 * kBlkMaxCams;
+constexpr int kBlkWarps = 4;  // blocks solved concurrently per CTA, one per warp
+constexpr int kLin = 21;      // per observation: A = dz/dx (2x3), B = dz/dy (2x6), 2w, e (2)
+
+struct BlockInfo {
+  int o0, no;  // observations (block order)
+  int p0, np;  // point copies
+  int c0, nc;  // camera copies
+};
+
+struct BlockProblem {
+  int n_cams, n_pts, n_blocks;
+  long long n_obs, n_pc, n_cc;
+  const BlockInfo* blocks;
+  const int* pc_obs;             // [n_pc + 1] first observation of each point copy
+  const int* pc_pt;              // [n_pc]
+  const int* cc_cam;             // [n_cc]
+  const unsigned char* obs_lc;   // [n_obs] local camera of each observation
+  const int* obs_pt;             // [n_obs] point id
+  const int* obs_cam;            // [n_obs] camera id
+  const void* z;                 // [n_obs] pixel pairs in T
+  const double* zt;              // [2 n_obs] reference pixels or null
+  const unsigned char* inlier;   // [n_obs] or null
+  void* pc_delta;                // [3][n_pc] T: copy minus the consensus it was solved against
+  double* pc_a;                  // [3][n_pc] scaled duals r / rho
+  void* cc_delta;                // [6][n_cc]
+  double* cc_a;                  // [6][n_cc]
+  double* X[2];                  // [3 n_pts] consensus, ping-pong
+  double* Y[2];                  // [6 n_cams]
+  const int* pt_cp_off;          // [n_pts + 1] CSR point -> its copies
+  const int* pt_cp;
+  const int* cam_cp_off;         // [n_cams + 1]
+  const int* cam_cp;
+  double* sums;                  // [8] metric accumulators
+  int* err;                      // bit 0: non-finite copy
+};
+
+template <typename T>
+__device__ __forceinline__ T wsum(T v) {
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
+  return v;
+}
+
+template <typename T>
+struct BlkSmem {
+  T lin[kBlkMaxCams][kLin][32];  // linearisation of each lane's observation slots
+  T S[kBlkMaxU][kBlkMaxU + 1];   // reduced camera system, then its Cholesky factor
+  T rhs[kBlkMaxU];
+  T g[kBlkMaxU];                 // camera part of the block gradient
+  T dy[kBlkMaxU];                // camera step
+  T vbar[kBlkMaxCams][6];        // camera consensus
+  T d[kBlkMaxCams][6];           // camera copy offsets
+  T dt[kBlkMaxCams][6];          // trial offsets
+  T a[kBlkMaxCams][6];           // camera scaled duals
+};
+
+// Eq. (14) at (point offsets dp of this lane, camera offsets dc): misfits of the
+// lane's observations + its point's dual and penalty terms, summed over the warp,
+// plus the cameras' terms.  +inf when an observation is behind its camera.
+template <typename T>
+__device__ __forceinline__ T block_objective(const Prm<T>& q, bool act, int nob, const int oc[kBlkMaxCams],
+                                             const T oz0[kBlkMaxCams], const T oz1[kBlkMaxCams], const T xbar[3],
+                                             const T dp[3], const T ax[3], const BlkSmem<T>& W, const T (*dc)[6],
+                                             int nc) {
+  T s = 0;
+  bool ok = true;
+  if (act) {
+#pragma unroll
+    for (int k = 0; k < kBlkMaxCams; ++k) {
+      if (k < nob) {
+        const int c = oc[k];
+        T v[9];
+#pragma unroll
+        for (int u = 0; u < 3; ++u) v[u] = xbar[u] + dp[u];
+#pragma unroll
+        for (int u = 0; u < 6; ++u) v[3 + u] = W.vbar[c][u] + dc[c][u];
+        Pose<T> P;
+        pose_at(v, q.eps, P);
+        if (!P.valid) {
+          ok = false;
+        } else {
+          const T iz = Num<T>::rcp(P.p[2]);
+          const T e0 = oz0[k] - (q.focal * P.p[0] * iz + q.cx);
+          const T e1 = oz1[k] - (q.focal * P.p[1] * iz + q.cy);
+          s += misfit<T>(q.loss, q.lp, e0 * e0 + e1 * e1);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 3; ++u) s += q.rho_x * dp[u] * (ax[u] + T(0.5) * dp[u]);
+  }
+  s = wsum(s);
+  ok = __all_sync(0xffffffffu, ok);
+  T sc = 0;
+  for (int c = 0; c < nc; ++c)
+#pragma unroll
+    for (int u = 0; u < 6; ++u) sc += q.rho(3 + u) * dc[c][u] * (W.a[c][u] + T(0.5) * dc[c][u]);
+  return ok ? s + sc : Num<T>::inf();
+}
+
+template <typename T>
+__device__ void solve_block(const BlockProblem& B, const Prm<T>& q, const BlockInfo& bi, BlkSmem<T>& W, int lane,
+                            int cur) {
+  using V2 = typename Num<T>::V2;
+  const int np = bi.np, nc = bi.nc, n_u = 6 * nc;
+  const bool act = lane < np;
+  const long long pc = (long long)bi.p0 + lane;
+  T* pdel = static_cast<T*>(B.pc_delta);
+  T* cdel = static_cast<T*>(B.cc_delta);
+  T xbar[3] = {0, 0, 0}, dp[3] = {0, 0, 0}, ax[3] = {0, 0, 0};
+  int nob = 0;
+  int oc[kBlkMaxCams] = {0, 0, 0, 0};
+  T oz0[kBlkMaxCams] = {0, 0, 0, 0}, oz1[kBlkMaxCams] = {0, 0, 0, 0};
+  if (act) {
+    const int i = B.pc_pt[pc];
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      xbar[u] = from_f64<T>(B.X[cur][3 * (long long)i + u]);
+      dp[u] = pdel[u * B.n_pc + pc];
+      ax[u] = from_f64<T>(B.pc_a[u * B.n_pc + pc]);
+    }
+    const int ob0 = B.pc_obs[pc];
+    nob = B.pc_obs[pc + 1] - ob0;
+    const V2* zz = static_cast<const V2*>(B.z);
+#pragma unroll
+    for (int k = 0; k < kBlkMaxCams; ++k)
+      if (k < nob) {
+        oc[k] = B.obs_lc[ob0 + k];
+        const V2 p = zz[ob0 + k];
+        oz0[k] = p.x;
+        oz1[k] = p.y;
+      }
+  }
+  // slot of this lane's observation on each camera of the block (-1: none)
+  int slot[kBlkMaxCams];
+#pragma unroll
+  for (int c = 0; c < kBlkMaxCams; ++c) {
+    slot[c] = -1;
+#pragma unroll
+    for (int k = 0; k < kBlkMaxCams; ++k)
+      if (k < nob && oc[k] == c) slot[c] = k;
+  }
+  if (lane < n_u) {
+    const int c = lane / 6, u = lane % 6;
+    const long long cc = (long long)bi.c0 + c;
+    const int j = B.cc_cam[cc];
+    W.vbar[c][u] = from_f64<T>(B.Y[cur][6 * (long long)j + u]);
+    W.d[c][u] = cdel[u * B.n_cc + cc];
+    W.a[c][u] = from_f64<T>(B.cc_a[u * B.n_cc + cc]);
+  }
+  __syncwarp();
+
+  T L = block_objective<T>(q, act, nob, oc, oz0, oz1, xbar, dp, ax, W, W.d, nc);
+  T lambda = T(-1);
+  for (int step = 0; step < q.steps; ++step) {
+    // linearise this lane's observations at the current copies
+    T Hpp[6] = {0, 0, 0, 0, 0, 0}, gp[3] = {0, 0, 0};
+    T noise = 0, trc = 0;
+#pragma unroll
+    for (int k = 0; k < kBlkMaxCams; ++k) {
+      if (k < nob) {
+        const int c = oc[k];
+        T v[9];
+#pragma unroll
+        for (int u = 0; u < 3; ++u) v[u] = xbar[u] + dp[u];
+#pragma unroll
+        for (int u = 0; u < 6; ++u) v[3 + u] = W.vbar[c][u] + W.d[c][u];
+        Pose<T> P;
+        pose_at(v, q.eps, P);
+        T J0[9], J1[9], e0 = 0, e1 = 0, w = 0;
+        if (P.valid) {
+          linearize(P, oz0[k], oz1[k], q, J0, J1, e0, e1, w);
+        } else {
+#pragma unroll
+          for (int u = 0; u < 9; ++u) J0[u] = J1[u] = 0;
+        }
+        const T tw = T(2) * w;
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+          W.lin[k][u][lane] = J0[u];
+          W.lin[k][3 + u][lane] = J1[u];
+        }
+#pragma unroll
+        for (int u = 0; u < 6; ++u) {
+          W.lin[k][6 + u][lane] = J0[3 + u];
+          W.lin[k][12 + u][lane] = J1[3 + u];
+        }
+        W.lin[k][18][lane] = tw;
+        W.lin[k][19][lane] = e0;
+        W.lin[k][20][lane] = e1;
+        Hpp[0] += tw * (J0[0] * J0[0] + J1[0] * J1[0]);
+        Hpp[1] += tw * (J0[0] * J0[1] + J1[0] * J1[1]);
+        Hpp[2] += tw * (J0[0] * J0[2] + J1[0] * J1[2]);
+        Hpp[3] += tw * (J0[1] * J0[1] + J1[1] * J1[1]);
+        Hpp[4] += tw * (J0[1] * J0[2] + J1[1] * J1[2]);
+        Hpp[5] += tw * (J0[2] * J0[2] + J1[2] * J1[2]);
+#pragma unroll
+        for (int u = 0; u < 3; ++u) gp[u] -= tw * (J0[u] * e0 + J1[u] * e1);
+#pragma unroll
+        for (int u = 3; u < 9; ++u) trc += tw * (J0[u] * J0[u] + J1[u] * J1[u]);
+        noise += tw * Num<T>::sqrt_(e0 * e0 + e1 * e1) * (fabs(oz0[k]) + fabs(oz1[k]));
+      }
+    }
+    if (act)
+#pragma unroll
+      for (int u = 0; u < 3; ++u) gp[u] += q.rho_x * (ax[u] + dp[u]);
+    __syncwarp();
+    if (lambda < T(0)) {
+      T tr = (act ? Hpp[0] + Hpp[3] + Hpp[5] + T(3) * q.rho_x : T(0)) + trc;
+      tr = wsum(tr);
+      for (int c = 0; c < nc; ++c)
+#pragma unroll
+        for (int u = 0; u < 6; ++u) tr += q.rho(3 + u);
+      lambda = q.lambda0 * tr / T(3 * np + n_u);
+    }
+    // W_p = (H_pp + (rho_x + lambda) I)^-1 by cofactors (symmetric positive definite)
+    T Wp[6] = {1, 0, 0, 1, 0, 1};
+    if (act) {
+      const T dg = q.rho_x + lambda;
+      const T h00 = Hpp[0] + dg, h01 = Hpp[1], h02 = Hpp[2], h11 = Hpp[3] + dg, h12 = Hpp[4], h22 = Hpp[5] + dg;
+      const T c00 = h11 * h22 - h12 * h12, c01 = h02 * h12 - h01 * h22, c02 = h01 * h12 - h02 * h11;
+      const T c11 = h00 * h22 - h02 * h02, c12 = h01 * h02 - h00 * h12, c22 = h00 * h11 - h01 * h01;
+      const T idet = Num<T>::rcp(h00 * c00 + h01 * c01 + h02 * c02);
+      Wp[0] = c00 * idet;
+      Wp[1] = c01 * idet;
+      Wp[2] = c02 * idet;
+      Wp[3] = c11 * idet;
+      Wp[4] = c12 * idet;
+      Wp[5] = c22 * idet;
+    }
+    const T Wg0 = Wp[0] * gp[0] + Wp[1] * gp[1] + Wp[2] * gp[2];
+    const T Wg1 = Wp[1] * gp[0] + Wp[3] * gp[1] + Wp[4] * gp[2];
+    const T Wg2 = Wp[2] * gp[0] + Wp[4] * gp[1] + Wp[5] * gp[2];
+    // camera gradient and reduced right-hand side: -g_c + H_cp W_p g_p summed over points
+    for (int c = 0; c < nc; ++c) {
+      const int k = act ? slot[c] : -1;
+      T tw = 0, e0 = 0, e1 = 0, u0 = 0, u1 = 0;
+      if (k >= 0) {
+        tw = W.lin[k][18][lane];
+        e0 = W.lin[k][19][lane];
+        e1 = W.lin[k][20][lane];
+        u0 = tw * (W.lin[k][0][lane] * Wg0 + W.lin[k][1][lane] * Wg1 + W.lin[k][2][lane] * Wg2);
+        u1 = tw * (W.lin[k][3][lane] * Wg0 + W.lin[k][4][lane] * Wg1 + W.lin[k][5][lane] * Wg2);
+      }
+#pragma unroll
+      for (int u = 0; u < 6; ++u) {
+        T b0 = 0, b1 = 0;
+        if (k >= 0) {
+          b0 = W.lin[k][6 + u][lane];
+          b1 = W.lin[k][12 + u][lane];
+        }
+        const T gsum = wsum(-tw * (b0 * e0 + b1 * e1));
+        const T hsum = wsum(b0 * u0 + b1 * u1);
+        if (lane == 0) {
+          const T gfull = gsum + q.rho(3 + u) * (W.a[c][u] + W.d[c][u]);
+          W.g[6 * c + u] = gfull;
+          W.rhs[6 * c + u] = hsum - gfull;
+        }
+      }
+    }
+    // reduced camera matrix S = H_cc - sum_p H_cp W_p H_pc, block (c1, c2) at a time
+    for (int c1 = 0; c1 < nc; ++c1) {
+      for (int c2 = c1; c2 < nc; ++c2) {
+        const int k1 = act ? slot[c1] : -1, k2 = act ? slot[c2] : -1;
+        const bool both = k1 >= 0 && k2 >= 0;
+        T tw1 = 0, m00 = 0, m01 = 0, m10 = 0, m11 = 0;
+        if (both) {
+          tw1 = W.lin[k1][18][lane];
+          const T tw2 = W.lin[k2][18][lane];
+          // M = (2 w1 A1) W_p (2 w2 A2)^T, 2x2
+          const T a10 = W.lin[k1][0][lane], a11 = W.lin[k1][1][lane], a12 = W.lin[k1][2][lane];
+          const T a13 = W.lin[k1][3][lane], a14 = W.lin[k1][4][lane], a15 = W.lin[k1][5][lane];
+          const T a20 = W.lin[k2][0][lane], a21 = W.lin[k2][1][lane], a22 = W.lin[k2][2][lane];
+          const T a23 = W.lin[k2][3][lane], a24 = W.lin[k2][4][lane], a25 = W.lin[k2][5][lane];
+          const T w20 = Wp[0] * a20 + Wp[1] * a21 + Wp[2] * a22, w21 = Wp[1] * a20 + Wp[3] * a21 + Wp[4] * a22,
+                  w22 = Wp[2] * a20 + Wp[4] * a21 + Wp[5] * a22;
+          const T w23 = Wp[0] * a23 + Wp[1] * a24 + Wp[2] * a25, w24 = Wp[1] * a23 + Wp[3] * a24 + Wp[4] * a25,
+                  w25 = Wp[2] * a23 + Wp[4] * a24 + Wp[5] * a25;
+          const T s = tw1 * tw2;
+          m00 = s * (a10 * w20 + a11 * w21 + a12 * w22);
+          m01 = s * (a10 * w23 + a11 * w24 + a12 * w25);
+          m10 = s * (a13 * w20 + a14 * w21 + a15 * w22);
+          m11 = s * (a13 * w23 + a14 * w24 + a15 * w25);
+        }
+        for (int r = 0; r < 6; ++r) {
+          T p0 = 0, p1 = 0;
+          if (both) {
+            p0 = W.lin[k1][6 + r][lane];
+            p1 = W.lin[k1][12 + r][lane];
+          }
+          // row r of B1^T M: (p0 m00 + p1 m10, p0 m01 + p1 m11)
+          const T q0 = p0 * m00 + p1 * m10, q1 = p0 * m01 + p1 * m11;
+          for (int s = (c1 == c2 ? r : 0); s < 6; ++s) {
+            T v = 0;
+            if (both) {
+              const T b0 = W.lin[k2][6 + s][lane], b1 = W.lin[k2][12 + s][lane];
+              v = -(q0 * b0 + q1 * b1);
+              if (c1 == c2) v += tw1 * (p0 * b0 + p1 * b1);
+            }
+            v = wsum(v);
+            if (lane == 0) {
+              W.S[6 * c1 + r][6 * c2 + s] = v;
+              W.S[6 * c2 + s][6 * c1 + r] = v;
+            }
+          }
+        }
+      }
+    }
+    __syncwarp();
+    if (lane < n_u) W.S[lane][lane] += q.rho(3 + lane % 6) + lambda;
+    __syncwarp();
+    // Cholesky S = L L^T, lane i owning row i
+    bool spd = true;
+    for (int k = 0; k < n_u; ++k) {
+      const T piv = __shfl_sync(0xffffffffu, W.S[k][k], 0);
+      if (!(piv > T(0))) {
+        spd = false;
+        break;
+      }
+      const T lkk = Num<T>::sqrt_(piv);
+      __syncwarp();
+      if (lane == 0) W.S[k][k] = lkk;
+      if (lane > k && lane < n_u) W.S[lane][k] = W.S[lane][k] / lkk;
+      __syncwarp();
+      if (lane > k && lane < n_u) {
+        const T lik = W.S[lane][k];
+        for (int jj = k + 1; jj <= lane; ++jj) W.S[lane][jj] -= lik * W.S[jj][k];
+      }
+      __syncwarp();
+    }
+    if (!spd) {
+      lambda *= T(10);
+      continue;
+    }
+    // L y = rhs, then L^T dy = y
+    if (lane < n_u) W.dy[lane] = W.rhs[lane];
+    __syncwarp();
+    for (int k = 0; k < n_u; ++k) {
+      if (lane == k) W.dy[k] = W.dy[k] / W.S[k][k];
+      __syncwarp();
+      if (lane > k && lane < n_u) W.dy[lane] -= W.S[lane][k] * W.dy[k];
+      __syncwarp();
+    }
+    for (int k = n_u - 1; k >= 0; --k) {
+      if (lane == k) W.dy[k] = W.dy[k] / W.S[k][k];
+      __syncwarp();
+      if (lane < k) W.dy[lane] -= W.S[k][lane] * W.dy[k];
+      __syncwarp();
+    }
+    // point step dx = -W_p (g_p + H_pc dy)
+    T dx[3] = {0, 0, 0};
+    if (act) {
+      T t0 = gp[0], t1 = gp[1], t2 = gp[2];
+#pragma unroll
+      for (int k = 0; k < kBlkMaxCams; ++k) {
+        if (k < nob) {
+          const int c = oc[k];
+          T r0 = 0, r1 = 0;
+#pragma unroll
+          for (int u = 0; u < 6; ++u) {
+            r0 += W.lin[k][6 + u][lane] * W.dy[6 * c + u];
+            r1 += W.lin[k][12 + u][lane] * W.dy[6 * c + u];
+          }
+          const T tw = W.lin[k][18][lane];
+          r0 *= tw;
+          r1 *= tw;
+          t0 += W.lin[k][0][lane] * r0 + W.lin[k][3][lane] * r1;
+          t1 += W.lin[k][1][lane] * r0 + W.lin[k][4][lane] * r1;
+          t2 += W.lin[k][2][lane] * r0 + W.lin[k][5][lane] * r1;
+        }
+      }
+      dx[0] = -(Wp[0] * t0 + Wp[1] * t1 + Wp[2] * t2);
+      dx[1] = -(Wp[1] * t0 + Wp[3] * t1 + Wp[4] * t2);
+      dx[2] = -(Wp[2] * t0 + Wp[4] * t1 + Wp[5] * t2);
+    }
+    // predicted decrease (lambda |d|^2 - g.d) / 2 and the rounding-noise bound
+    T gd = wsum(gp[0] * dx[0] + gp[1] * dx[1] + gp[2] * dx[2]);
+    T dd = wsum(dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2]);
+    for (int u = 0; u < n_u; ++u) {
+      gd += W.g[u] * W.dy[u];
+      dd += W.dy[u] * W.dy[u];
+    }
+    const T pred = T(0.5) * (lambda * dd - gd);
+    const T noise_sum = wsum(noise);
+    const bool trust = isfinite(L) && q.model_tol > T(0) &&
+                       pred <= q.model_tol * Num<T>::unit_roundoff * (fabs(L) + noise_sum);
+    T xt[3];
+#pragma unroll
+    for (int u = 0; u < 3; ++u) xt[u] = dp[u] + dx[u];
+    if (lane < n_u) W.dt[lane / 6][lane % 6] = W.d[lane / 6][lane % 6] + W.dy[lane];
+    __syncwarp();
+    const T Lt = block_objective<T>(q, act, nob, oc, oz0, oz1, xbar, xt, ax, W, W.dt, nc);
+    const bool valid = Lt < Num<T>::inf();
+    if (valid && (trust || Lt < L)) {
+#pragma unroll
+      for (int u = 0; u < 3; ++u) dp[u] = xt[u];
+      if (lane < n_u) W.d[lane / 6][lane % 6] = W.dt[lane / 6][lane % 6];
+      L = trust ? L - pred : Lt;
+      const T lr = Num<T>::tenth(lambda);
+      lambda = lr > q.lambda_min ? lr : q.lambda_min;
+    } else {
+      lambda *= T(10);
+    }
+    __syncwarp();
+  }
+  bool finite = true;
+  if (act)
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      pdel[u * B.n_pc + pc] = dp[u];
+      finite = finite && isfinite(dp[u]);
+    }
+  if (lane < n_u) {
+    const T v = W.d[lane / 6][lane % 6];
+    cdel[(lane % 6) * B.n_cc + bi.c0 + lane / 6] = v;
+    finite = finite && isfinite(v);
+  }
+  if (!finite) atomicOr(B.err, 1);
+  __syncwarp();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlkWarps * 32) block_solve_kernel(BlockProblem B, Prm<T> q, int cur) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  BlkSmem<T>& W = reinterpret_cast<BlkSmem<T>*>(smem_raw)[warp];
+  for (int b = blockIdx.x * kBlkWarps + warp; b < B.n_blocks; b += gridDim.x * kBlkWarps) {
+    const BlockInfo bi = B.blocks[b];
+    solve_block<T>(B, q, bi, W, lane, cur);
+  }
+}
+
+// Eqs. (10)-(11) over copies: consensus = old consensus + mean over its copies of
+// (offset + scaled dual), the old duals; a point or camera without copies keeps its value.
+template <typename T>
+__global__ void block_consensus_kernel(BlockProblem B, int cur) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int nxt = cur ^ 1;
+  if (t < B.n_pts) {
+    const int i = (int)t, k0 = B.pt_cp_off[i], k1 = B.pt_cp_off[i + 1];
+    const T* del = static_cast<const T*>(B.pc_delta);
+    for (int u = 0; u < 3; ++u) {
+      double s = 0.0;
+      for (int k = k0; k < k1; ++k) {
+        const int cp = B.pt_cp[k];
+        s += to_f64<T>(del[u * B.n_pc + cp]) + B.pc_a[u * B.n_pc + cp];
+      }
+      const double x = B.X[cur][3 * (long long)i + u];
+      B.X[nxt][3 * (long long)i + u] = k1 > k0 ? x + s / (double)(k1 - k0) : x;
+    }
+  } else if (t < (long long)B.n_pts + B.n_cams) {
+    const int j = (int)(t - B.n_pts), k0 = B.cam_cp_off[j], k1 = B.cam_cp_off[j + 1];
+    const T* del = static_cast<const T*>(B.cc_delta);
+    for (int u = 0; u < 6; ++u) {
+      double s = 0.0;
+      for (int k = k0; k < k1; ++k) {
+        const int cp = B.cam_cp[k];
+        s += to_f64<T>(del[u * B.n_cc + cp]) + B.cc_a[u * B.n_cc + cp];
+      }
+      const double y = B.Y[cur][6 * (long long)j + u];
+      B.Y[nxt][6 * (long long)j + u] = k1 > k0 ? y + s / (double)(k1 - k0) : y;
+    }
+  }
+}
+
+// Eqs. (12)-(13) per copy with the new consensus, in scaled form a += copy - consensus;
+// each offset is re-based on the new consensus.  With `sums`, adds the primal
+// (|copy - consensus|^2) and dual (rho^2 |change of consensus|^2) residual terms.
+template <typename T>
+__global__ void block_dual_kernel(BlockProblem B, Prm<double> q, int cur, int with_sums) {
+  __shared__ double red[2][256];
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int nxt = cur ^ 1;
+  double pr = 0.0, dr = 0.0;
+  if (t < B.n_pc) {
+    T* del = static_cast<T*>(B.pc_delta);
+    const int i = B.pc_pt[t];
+    for (int u = 0; u < 3; ++u) {
+      const double xo = B.X[cur][3 * (long long)i + u], xn = B.X[nxt][3 * (long long)i + u];
+      const double d = to_f64<T>(del[u * B.n_pc + t]) + (xo - xn);
+      B.pc_a[u * B.n_pc + t] += d;
+      del[u * B.n_pc + t] = from_f64<T>(d);
+      pr += d * d;
+      const double r = q.rho_x * (xn - xo);
+      dr += r * r;
+    }
+  } else if (t < B.n_pc + B.n_cc) {
+    const long long k = t - B.n_pc;
+    T* del = static_cast<T*>(B.cc_delta);
+    const int j = B.cc_cam[k];
+    for (int u = 0; u < 6; ++u) {
+      const double yo = B.Y[cur][6 * (long long)j + u], yn = B.Y[nxt][6 * (long long)j + u];
+      const double d = to_f64<T>(del[u * B.n_cc + k]) + (yo - yn);
+      B.cc_a[u * B.n_cc + k] += d;
+      del[u * B.n_cc + k] = from_f64<T>(d);
+      pr += d * d;
+      const double r = q.rho(3 + u) * (yn - yo);
+      dr += r * r;
+    }
+  }
+  if (!with_sums) return;
+  red[0][threadIdx.x] = pr;
+  red[1][threadIdx.x] = dr;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + w];
+      red[1][threadIdx.x] += red[1][threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    atomicAdd(&B.sums[6], red[0][0]);
+    atomicAdd(&B.sums[7], red[1][0]);
+  }
+}
+
+// Reprojection terms of Eq. (2) at consensus X[c], Y[c]: sums of |e|^2, phi_m, |f - z_ref|^2
+// (reference pixels, inliers), valid, invalid and reference counts.
+template <typename T>
+__global__ void block_metrics_kernel(BlockProblem B, Prm<T> q, int c) {
+  __shared__ double red[6][256];
+  using V2 = typename Num<T>::V2;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < B.n_obs;
+       o += (long long)gridDim.x * blockDim.x) {
+    const int i = B.obs_pt[o], j = B.obs_cam[o];
+    T v[9];
+    for (int u = 0; u < 3; ++u) v[u] = from_f64<T>(B.X[c][3 * (long long)i + u]);
+    for (int u = 0; u < 6; ++u) v[3 + u] = from_f64<T>(B.Y[c][6 * (long long)j + u]);
+    Pose<T> P;
+    pose_at(v, q.eps, P);
+    if (!P.valid) {
+      acc[4] += 1.0;
+      continue;
+    }
+    const V2 zz = static_cast<const V2*>(B.z)[o];
+    const T iz = T(1) / P.p[2];
+    const T zp0 = q.focal * P.p[0] * iz + q.cx, zp1 = q.focal * P.p[1] * iz + q.cy;
+    const T e0 = zz.x - zp0, e1 = zz.y - zp1;
+    const T s = e0 * e0 + e1 * e1;
+    acc[0] += (double)s;
+    acc[1] += (double)misfit<T>(q.loss, q.lp, s);
+    acc[3] += 1.0;
+    if (B.zt && (!B.inlier || B.inlier[o])) {
+      const double g0 = (double)zp0 - B.zt[2 * o], g1 = (double)zp1 - B.zt[2 * o + 1];
+      acc[2] += g0 * g0 + g1 * g1;
+      acc[5] += 1.0;
+    }
+  }
+  for (int k = 0; k < 6; ++k) red[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int k = 0; k < 6; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 6; ++k) atomicAdd(&B.sums[k], red[k][0]);
+}
+
+int blocks_of(long long n, int per) { return (int)((n + per - 1) / per); }
+
+}  // namespace
+}  // namespace dba
+
+// ------------------------------------------------------------ host side
+struct dba_block_ctx {
+  dba_config cfg{};
+  dba::Params prm{};
+  bool fp32 = true;
+  int pi = 1, kappa = 1;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  bool has_problem = false;
+  int cur = 0;
+  long long iters = 0;
+  int grid = 0;
+  std::string err = "no error";
+  // host copy of the layout (caller order <-> block order)
+  std::vector<long long> blk_obs;  // block order -> caller observation
+  std::vector<dba::BlockInfo> h_blocks;
+  dba::BlockProblem B{};
+  std::vector<void*> allocs;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+  dba_status fail(dba_status s, const std::string& msg) {
+    err = msg;
+    return s;
+  }
+  dba_status cuda_fail(cudaError_t e, const char* where) {
+    err = std::string(where) + ": " + cudaGetErrorString(e);
+    return DBA_ECUDA;
+  }
+  template <typename P>
+  cudaError_t alloc(P** p, size_t bytes) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes > 0 ? bytes : 16);
+    if (e == cudaSuccess) allocs.push_back(q);
+    *p = static_cast<P*>(q);
+    return e;
+  }
+  void free_all() {
+    for (void* p : allocs) cudaFree(p);
+    allocs.clear();
+    B = dba::BlockProblem{};
+    has_problem = false;
+  }
+};
+
+namespace {
+thread_local std::string g_block_error = "no error";
+
+#define BLK_CUDA(call, where)                           \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return ctx->cuda_fail(e_, where); \
+  } while (0)
+
+template <typename T>
+cudaError_t upload(dba_block_ctx* ctx, T** dst, const std::vector<T>& src) {
+  cudaError_t e = ctx->alloc(dst, sizeof(T) * src.size());
+  if (e != cudaSuccess || src.empty()) return e;
+  return cudaMemcpyAsync(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice, ctx->stream);
+}
+
+template <typename T>
+cudaError_t launch_block_solve(dba_block_ctx* ctx) {
+  const size_t smem = sizeof(dba::BlkSmem<T>) * dba::kBlkWarps;
+  static bool set = false;
+  if (!set) {
+    cudaError_t e = cudaFuncSetAttribute(dba::block_solve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    set = true;
+  }
+  if (!ctx->grid) {
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dba::block_solve_kernel<T>,
+                                                                  dba::kBlkWarps * 32, smem);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    ctx->grid = std::max(per_sm, 1) * sms;
+  }
+  const int need = dba::blocks_of(ctx->B.n_blocks, dba::kBlkWarps);
+  const int g = std::max(1, std::min(need, ctx->grid));
+  dba::block_solve_kernel<T><<<g, dba::kBlkWarps * 32, smem, ctx->stream>>>(ctx->B, dba::make_prm<T>(ctx->prm),
+                                                                              ctx->cur);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_iteration(dba_block_ctx* ctx, bool with_sums) {
+  cudaError_t e = ctx->fp32 ? launch_block_solve<float>(ctx) : launch_block_solve<double>(ctx);
+  if (e != cudaSuccess) return e;
+  const long long nc = (long long)ctx->B.n_pts + ctx->B.n_cams;
+  if (ctx->fp32)
+    dba::block_consensus_kernel<float><<<dba::blocks_of(nc, 256), 256, 0, ctx->stream>>>(ctx->B, ctx->cur);
+  else
+    dba::block_consensus_kernel<double><<<dba::blocks_of(nc, 256), 256, 0, ctx->stream>>>(ctx->B, ctx->cur);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (with_sums && (e = cudaMemsetAsync(ctx->B.sums, 0, 8 * sizeof(double), ctx->stream)) != cudaSuccess) return e;
+  const long long ncp = ctx->B.n_pc + ctx->B.n_cc;
+  const dba::Prm<double> q64 = dba::make_prm<double>(ctx->prm);
+  if (ctx->fp32)
+    dba::block_dual_kernel<float><<<dba::blocks_of(ncp, 256), 256, 0, ctx->stream>>>(ctx->B, q64, ctx->cur,
+                                                                                    with_sums ? 1 : 0);
+  else
+    dba::block_dual_kernel<double><<<dba::blocks_of(ncp, 256), 256, 0, ctx->stream>>>(ctx->B, q64, ctx->cur,
+                                                                                     with_sums ? 1 : 0);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  ctx->cur ^= 1;
+  return cudaSuccess;
+}
+
+dba_status read_stats(dba_block_ctx* ctx, bool have_residuals, dba_stats* st) {
+  if (!have_residuals) BLK_CUDA(cudaMemsetAsync(ctx->B.sums, 0, 8 * sizeof(double), ctx->stream), "metrics");
+  const int g = std::min(dba::blocks_of(ctx->B.n_obs, 256), 4096);
+  if (ctx->fp32)
+    dba::block_metrics_kernel<float><<<g, 256, 0, ctx->stream>>>(ctx->B, dba::make_prm<float>(ctx->prm), ctx->cur);
+  else
+    dba::block_metrics_kernel<double><<<g, 256, 0, ctx->stream>>>(ctx->B, dba::make_prm<double>(ctx->prm), ctx->cur);
+  BLK_CUDA(cudaGetLastError(), "metrics");
+  double h[8];
+  int herr = 0;
+  BLK_CUDA(cudaMemcpyAsync(h, ctx->B.sums, sizeof h, cudaMemcpyDeviceToHost, ctx->stream), "metrics");
+  BLK_CUDA(cudaMemcpyAsync(&herr, ctx->B.err, sizeof herr, cudaMemcpyDeviceToHost, ctx->stream), "metrics");
+  BLK_CUDA(cudaStreamSynchronize(ctx->stream), "metrics");
+  if (herr & 1) return ctx->fail(DBA_ENUMERIC, "a block solve produced a non-finite value");
+  st->iters_done = ctx->iters;
+  st->rmse_obs = h[3] > 0 ? std::sqrt(h[0] / h[3]) : 0.0;
+  st->objective = h[1];
+  st->rmse_gt = h[5] > 0 ? std::sqrt(h[2] / h[5]) : 0.0;
+  st->n_invalid = (long long)h[4];
+  st->primal_res = have_residuals ? std::sqrt(h[6]) : 0.0;
+  st->dual_res = have_residuals ? std::sqrt(h[7]) : 0.0;
+  return DBA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dba_status dba_block_create(const dba_config* cfg, int block_points, int block_cams, dba_block_ctx** out) {
+  if (!cfg || !out) {
+    g_block_error = "dba_block_create: null argument";
+    return DBA_EINVAL;
+  }
+  *out = nullptr;
+  const bool ok = std::isfinite(cfg->focal) && cfg->focal > 0 && std::isfinite(cfg->cx) && std::isfinite(cfg->cy) &&
+                  cfg->loss >= 0 && cfg->loss <= 2 &&
+                  (cfg->loss == DBA_LOSS_L2 || (std::isfinite(cfg->loss_param) && cfg->loss_param > 0)) &&
+                  std::isfinite(cfg->rho_x) && cfg->rho_x > 0 && std::isfinite(cfg->rho_y) && cfg->rho_y > 0 &&
+                  std::isfinite(cfg->rho_angle) && cfg->inner_steps >= 0 && cfg->inner_steps <= 1000 &&
+                  std::isfinite(cfg->lm_lambda0) && cfg->lm_lambda0 > 0 && std::isfinite(cfg->lm_lambda_min) &&
+                  cfg->lm_lambda_min >= 0 && std::isfinite(cfg->eps_depth) && std::isfinite(cfg->lm_model_tol) &&
+                  cfg->lm_model_tol >= 0 && (cfg->precision == 0 || cfg->precision == 1);
+  if (!ok) {
+    g_block_error = "dba_block_create: invalid configuration";
+    return DBA_EINVAL;
+  }
+  if (block_points < 1 || block_points > DBA_BLOCK_MAX_POINTS || block_cams < 1 ||
+      block_cams > DBA_BLOCK_MAX_CAMERAS) {
+    g_block_error = "dba_block_create: block_points must be in [1, 32] and block_cams in [1, 4]";
+    return DBA_EINVAL;
+  }
+  cudaError_t e = cudaFree(nullptr);
+  if (e != cudaSuccess) {
+    g_block_error = std::string("dba_block_create: CUDA unavailable: ") + cudaGetErrorString(e);
+    return DBA_ECUDA;
+  }
+  dba_block_ctx* ctx = new (std::nothrow) dba_block_ctx();
+  if (!ctx) {
+    g_block_error = "dba_block_create: out of host memory";
+    return DBA_ENOMEM;
+  }
+  ctx->cfg = *cfg;
+  ctx->fp32 = cfg->precision == DBA_PREC_F32_LOCAL;
+  ctx->pi = block_points;
+  ctx->kappa = block_cams;
+  ctx->prm = dba::Params{cfg->focal, cfg->cx, cfg->cy, cfg->loss, cfg->loss_param, cfg->rho_x, cfg->rho_y,
+                         cfg->rho_angle > 0 ? cfg->rho_angle : cfg->rho_y, cfg->inner_steps, cfg->lm_lambda0,
+                         cfg->lm_lambda_min, cfg->eps_depth, cfg->lm_model_tol};
+  if (cfg->cuda_stream) {
+    ctx->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
+  } else {
+    e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+    ctx->own_stream = e == cudaSuccess;
+  }
+  if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev0);
+  if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev1);
+  if (e != cudaSuccess) {
+    g_block_error = std::string("dba_block_create: ") + cudaGetErrorString(e);
+    dba_block_destroy(ctx);
+    return DBA_ECUDA;
+  }
+  *out = ctx;
+  return DBA_OK;
+}
+
+dba_status dba_block_set_observations(dba_block_ctx* ctx, int32_t n_cams, int32_t n_pts, int64_t n_obs,
+                                      const int32_t* pt_idx, const int32_t* cam_idx, const double* z,
+                                      const double* cams0, const double* pts0) {
+  if (!ctx) return DBA_EINVAL;
+  if (n_cams <= 0 || n_pts <= 0 || n_obs <= 0)
+    return ctx->fail(DBA_EINVAL, "dba_block_set_observations: n_cams, n_pts and n_obs must be positive");
+  if (n_obs > INT_MAX) return ctx->fail(DBA_EINVAL, "dba_block_set_observations: at most 2^31-1 observations");
+  if (!pt_idx || !cam_idx || !z || !cams0 || !pts0)
+    return ctx->fail(DBA_EINVAL, "dba_block_set_observations: null array");
+  for (int64_t o = 0; o < n_obs; ++o) {
+    if (pt_idx[o] < 0 || pt_idx[o] >= n_pts || cam_idx[o] < 0 || cam_idx[o] >= n_cams)
+      return ctx->fail(DBA_EINVAL, "dba_block_set_observations: observation " + std::to_string(o) +
+                                       " indexes outside the cameras or points");
+    if (!std::isfinite(z[2 * o]) || !std::isfinite(z[2 * o + 1]))
+      return ctx->fail(DBA_EINVAL, "dba_block_set_observations: non-finite pixel");
+  }
+  for (int64_t k = 0; k < 6LL * n_cams; ++k)
+    if (!std::isfinite(cams0[k])) return ctx->fail(DBA_EINVAL, "dba_block_set_observations: non-finite camera");
+  for (int64_t k = 0; k < 3LL * n_pts; ++k)
+    if (!std::isfinite(pts0[k])) return ctx->fail(DBA_EINVAL, "dba_block_set_observations: non-finite point");
+  ctx->free_all();
+  const long long l = n_obs;
+  const int n = n_pts, m = n_cams, pi = ctx->pi, kappa = ctx->kappa;
+  // point ranks by (smallest observing camera, point index)
+  std::vector<int> first(n, INT_MAX);
+  for (long long o = 0; o < l; ++o) first[pt_idx[o]] = std::min(first[pt_idx[o]], (int)cam_idx[o]);
+  std::vector<int> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return first[a] < first[b]; });
+  std::vector<int> rank(n);
+  for (int r = 0; r < n; ++r) rank[order[r]] = r;
+  const long long n_cg = (m + kappa - 1) / kappa;
+  auto key = [&](long long o) { return (long long)(rank[pt_idx[o]] / pi) * n_cg + cam_idx[o] / kappa; };
+  std::vector<long long>& idx = ctx->blk_obs;
+  idx.resize(l);
+  std::iota(idx.begin(), idx.end(), 0LL);
+  std::sort(idx.begin(), idx.end(), [&](long long a, long long b) {
+    const long long ka = key(a), kb = key(b);
+    if (ka != kb) return ka < kb;
+    if (rank[pt_idx[a]] != rank[pt_idx[b]]) return rank[pt_idx[a]] < rank[pt_idx[b]];
+    return cam_idx[a] < cam_idx[b];
+  });
+  for (long long t = 1; t < l; ++t)
+    if (pt_idx[idx[t]] == pt_idx[idx[t - 1]] && cam_idx[idx[t]] == cam_idx[idx[t - 1]])
+      return ctx->fail(DBA_EINVAL, "dba_block_set_observations: point " + std::to_string(pt_idx[idx[t]]) +
+                                       " is observed twice by camera " + std::to_string(cam_idx[idx[t]]));
+  // blocks, point copies (consecutive observations of one point), camera copies
+  std::vector<dba::BlockInfo>& blocks = ctx->h_blocks;
+  blocks.clear();
+  std::vector<int> pc_obs, pc_pt, cc_cam, obs_pt(l), obs_cam(l);
+  std::vector<unsigned char> obs_lc(l);
+  long long o = 0;
+  while (o < l) {
+    const long long k = key(idx[o]);
+    long long e = o;
+    while (e < l && key(idx[e]) == k) ++e;
+    dba::BlockInfo bi{};
+    bi.o0 = (int)o;
+    bi.no = (int)(e - o);
+    bi.p0 = (int)pc_pt.size();
+    bi.c0 = (int)cc_cam.size();
+    std::vector<int> cams;
+    for (long long t = o; t < e; ++t) cams.push_back(cam_idx[idx[t]]);
+    std::sort(cams.begin(), cams.end());
+    cams.erase(std::unique(cams.begin(), cams.end()), cams.end());
+    for (int c : cams) cc_cam.push_back(c);
+    bi.nc = (int)cams.size();
+    for (long long t = o; t < e; ++t) {
+      const int i = pt_idx[idx[t]];
+      if (t == o || pt_idx[idx[t - 1]] != i) {
+        pc_pt.push_back(i);
+        pc_obs.push_back((int)t);
+      }
+      obs_pt[t] = i;
+      obs_cam[t] = cam_idx[idx[t]];
+      obs_lc[t] = (unsigned char)(std::lower_bound(cams.begin(), cams.end(), (int)cam_idx[idx[t]]) - cams.begin());
+    }
+    bi.np = (int)pc_pt.size() - bi.p0;
+    blocks.push_back(bi);
+    o = e;
+  }
+  pc_obs.push_back((int)l);
+  const long long n_pc = (long long)pc_pt.size(), n_cc = (long long)cc_cam.size();
+  // copy lists per point and per camera (consensus)
+  std::vector<int> pt_off(n + 1, 0), cam_off(m + 1, 0), pt_cp(n_pc), cam_cp(n_cc);
+  for (long long k = 0; k < n_pc; ++k) ++pt_off[pc_pt[k] + 1];
+  for (long long k = 0; k < n_cc; ++k) ++cam_off[cc_cam[k] + 1];
+  for (int i = 0; i < n; ++i) pt_off[i + 1] += pt_off[i];
+  for (int j = 0; j < m; ++j) cam_off[j + 1] += cam_off[j];
+  {
+    std::vector<int> fill(pt_off.begin(), pt_off.end() - 1);
+    for (long long k = 0; k < n_pc; ++k) pt_cp[fill[pc_pt[k]]++] = (int)k;
+    std::vector<int> fc(cam_off.begin(), cam_off.end() - 1);
+    for (long long k = 0; k < n_cc; ++k) cam_cp[fc[cc_cam[k]]++] = (int)k;
+  }
+  // device problem
+  dba::BlockProblem& B = ctx->B;
+  B.n_cams = m;
+  B.n_pts = n;
+  B.n_obs = l;
+  B.n_blocks = (int)blocks.size();
+  B.n_pc = n_pc;
+  B.n_cc = n_cc;
+  const size_t tsz = ctx->fp32 ? sizeof(float) : sizeof(double);
+  dba::BlockInfo* d_blocks = nullptr;
+  int *d_pc_obs = nullptr, *d_pc_pt = nullptr, *d_cc_cam = nullptr, *d_obs_pt = nullptr, *d_obs_cam = nullptr;
+  int *d_pt_off = nullptr, *d_pt_cp = nullptr, *d_cam_off = nullptr, *d_cam_cp = nullptr;
+  unsigned char* d_lc = nullptr;
+  BLK_CUDA(upload(ctx, &d_blocks, blocks), "upload");
+  BLK_CUDA(upload(ctx, &d_pc_obs, pc_obs), "upload");
+  BLK_CUDA(upload(ctx, &d_pc_pt, pc_pt), "upload");
+  BLK_CUDA(upload(ctx, &d_cc_cam, cc_cam), "upload");
+  BLK_CUDA(upload(ctx, &d_obs_pt, obs_pt), "upload");
+  BLK_CUDA(upload(ctx, &d_obs_cam, obs_cam), "upload");
+  BLK_CUDA(upload(ctx, &d_lc, obs_lc), "upload");
+  BLK_CUDA(upload(ctx, &d_pt_off, pt_off), "upload");
+  BLK_CUDA(upload(ctx, &d_pt_cp, pt_cp), "upload");
+  BLK_CUDA(upload(ctx, &d_cam_off, cam_off), "upload");
+  BLK_CUDA(upload(ctx, &d_cam_cp, cam_cp), "upload");
+  B.blocks = d_blocks;
+  B.pc_obs = d_pc_obs;
+  B.pc_pt = d_pc_pt;
+  B.cc_cam = d_cc_cam;
+  B.obs_pt = d_obs_pt;
+  B.obs_cam = d_obs_cam;
+  B.obs_lc = d_lc;
+  B.pt_cp_off = d_pt_off;
+  B.pt_cp = d_pt_cp;
+  B.cam_cp_off = d_cam_off;
+  B.cam_cp = d_cam_cp;
+  // pixels in block order, in the working precision
+  {
+    std::vector<double> zb(2 * l);
+    for (long long t = 0; t < l; ++t) {
+      zb[2 * t] = z[2 * idx[t]];
+      zb[2 * t + 1] = z[2 * idx[t] + 1];
+    }
+    void* d_z = nullptr;
+    BLK_CUDA(ctx->alloc(&d_z, tsz * 2 * l), "alloc");
+    if (ctx->fp32) {
+      std::vector<float> zf(zb.begin(), zb.end());
+      BLK_CUDA(cudaMemcpyAsync(d_z, zf.data(), sizeof(float) * zf.size(), cudaMemcpyHostToDevice, ctx->stream),
+               "upload");
+      BLK_CUDA(cudaStreamSynchronize(ctx->stream), "upload");
+    } else {
+      BLK_CUDA(cudaMemcpyAsync(d_z, zb.data(), sizeof(double) * zb.size(), cudaMemcpyHostToDevice, ctx->stream),
+               "upload");
+      BLK_CUDA(cudaStreamSynchronize(ctx->stream), "upload");
+    }
+    B.z = d_z;
+  }
+  // state: copies at the consensus (offsets 0), duals 0
+  void *d_pdel = nullptr, *d_cdel = nullptr;
+  BLK_CUDA(ctx->alloc(&d_pdel, tsz * 3 * n_pc), "alloc");
+  BLK_CUDA(ctx->alloc(&d_cdel, tsz * 6 * n_cc), "alloc");
+  BLK_CUDA(ctx->alloc(&B.pc_a, sizeof(double) * 3 * n_pc), "alloc");
+  BLK_CUDA(ctx->alloc(&B.cc_a, sizeof(double) * 6 * n_cc), "alloc");
+  BLK_CUDA(cudaMemsetAsync(d_pdel, 0, tsz * 3 * n_pc, ctx->stream), "init");
+  BLK_CUDA(cudaMemsetAsync(d_cdel, 0, tsz * 6 * n_cc, ctx->stream), "init");
+  BLK_CUDA(cudaMemsetAsync(B.pc_a, 0, sizeof(double) * 3 * n_pc, ctx->stream), "init");
+  BLK_CUDA(cudaMemsetAsync(B.cc_a, 0, sizeof(double) * 6 * n_cc, ctx->stream), "init");
+  B.pc_delta = d_pdel;
+  B.cc_delta = d_cdel;
+  for (int k = 0; k < 2; ++k) {
+    BLK_CUDA(ctx->alloc(&B.X[k], sizeof(double) * 3 * n), "alloc");
+    BLK_CUDA(ctx->alloc(&B.Y[k], sizeof(double) * 6 * m), "alloc");
+  }
+  BLK_CUDA(cudaMemcpyAsync(B.X[0], pts0, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, ctx->stream), "upload");
+  BLK_CUDA(cudaMemcpyAsync(B.Y[0], cams0, sizeof(double) * 6 * m, cudaMemcpyHostToDevice, ctx->stream), "upload");
+  BLK_CUDA(ctx->alloc(&B.sums, sizeof(double) * 8), "alloc");
+  BLK_CUDA(ctx->alloc(&B.err, sizeof(int)), "alloc");
+  BLK_CUDA(cudaMemsetAsync(B.err, 0, sizeof(int), ctx->stream), "init");
+  BLK_CUDA(cudaStreamSynchronize(ctx->stream), "upload");
+  ctx->cur = 0;
+  ctx->iters = 0;
+  ctx->has_problem = true;
+  return DBA_OK;
+}
+
+dba_status dba_block_set_reference_pixels(dba_block_ctx* ctx, const double* z_ref, const uint8_t* inlier) {
+  if (!ctx) return DBA_EINVAL;
+  if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_block_set_reference_pixels before set_observations");
+  if (!z_ref) return ctx->fail(DBA_EINVAL, "dba_block_set_reference_pixels: null array");
+  const long long l = ctx->B.n_obs;
+  std::vector<double> zb(2 * l);
+  std::vector<unsigned char> mb(l, 1);
+  for (long long t = 0; t < l; ++t) {
+    const long long o = ctx->blk_obs[t];
+    zb[2 * t] = z_ref[2 * o];
+    zb[2 * t + 1] = z_ref[2 * o + 1];
+    if (!std::isfinite(zb[2 * t]) || !std::isfinite(zb[2 * t + 1]))
+      return ctx->fail(DBA_EINVAL, "dba_block_set_reference_pixels: non-finite pixel");
+    if (inlier) mb[t] = inlier[o] ? 1 : 0;
+  }
+  double* d_zt = nullptr;
+  unsigned char* d_in = nullptr;
+  BLK_CUDA(upload(ctx, &d_zt, zb), "upload");
+  BLK_CUDA(upload(ctx, &d_in, mb), "upload");
+  BLK_CUDA(cudaStreamSynchronize(ctx->stream), "upload");
+  ctx->B.zt = d_zt;
+  ctx->B.inlier = d_in;
+  return DBA_OK;
+}
+
+dba_status dba_block_iterate(dba_block_ctx* ctx, int n_iters, dba_stats* stats) {
+  if (!ctx) return DBA_EINVAL;
+  if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_block_iterate before dba_block_set_observations");
+  if (n_iters < 0) return ctx->fail(DBA_EINVAL, "dba_block_iterate: n_iters < 0");
+  BLK_CUDA(cudaEventRecord(ctx->ev0, ctx->stream), "iterate");
+  for (int it = 0; it < n_iters; ++it) BLK_CUDA(launch_iteration(ctx, stats && it == n_iters - 1), "iterate");
+  BLK_CUDA(cudaEventRecord(ctx->ev1, ctx->stream), "iterate");
+  ctx->iters += n_iters;
+  int herr = 0;
+  BLK_CUDA(cudaMemcpyAsync(&herr, ctx->B.err, sizeof herr, cudaMemcpyDeviceToHost, ctx->stream), "iterate");
+  BLK_CUDA(cudaStreamSynchronize(ctx->stream), "iterate");
+  if (herr & 1) return ctx->fail(DBA_ENUMERIC, "a block solve produced a non-finite value");
+  if (stats) {
+    float ms = 0.f;
+    BLK_CUDA(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1), "iterate");
+    const dba_status s = read_stats(ctx, n_iters > 0, stats);
+    stats->seconds = 1e-3 * ms;
+    return s;
+  }
+  return DBA_OK;
+}
+
+dba_status dba_block_iterate_until(dba_block_ctx* ctx, int max_iters, double target_rmse_gt, dba_stats* stats) {
+  if (!ctx || !stats) return DBA_EINVAL;
+  if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_block_iterate_until before set_observations");
+  if (!ctx->B.zt) return ctx->fail(DBA_ESTATE, "dba_block_iterate_until needs reference pixels");
+  if (max_iters < 0 || !(target_rmse_gt > 0)) return ctx->fail(DBA_EINVAL, "dba_block_iterate_until: bad arguments");
+  double secs = 0.0;
+  for (int it = 0; it < max_iters; ++it) {
+    BLK_CUDA(cudaEventRecord(ctx->ev0, ctx->stream), "iterate_until");
+    BLK_CUDA(launch_iteration(ctx, true), "iterate_until");
+    ctx->iters += 1;
+    const dba_status s = read_stats(ctx, true, stats);
+    BLK_CUDA(cudaEventRecord(ctx->ev1, ctx->stream), "iterate_until");
+    BLK_CUDA(cudaEventSynchronize(ctx->ev1), "iterate_until");
+    float ms = 0.f;
+    BLK_CUDA(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1), "iterate_until");
+    secs += 1e-3 * ms;
+    if (s != DBA_OK) return s;
+    if (stats->rmse_gt <= target_rmse_gt) break;
+  }
+  stats->seconds = secs;
+  return DBA_OK;
+}
+
+dba_status dba_block_get_params(dba_block_ctx* ctx, double* cams_out, double* pts_out) {
+  if (!ctx) return DBA_EINVAL;
+  if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_block_get_params before set_observations");
+  if (!cams_out || !pts_out) return ctx->fail(DBA_EINVAL, "dba_block_get_params: null array");
+  BLK_CUDA(cudaMemcpyAsync(cams_out, ctx->B.Y[ctx->cur], sizeof(double) * 6 * ctx->B.n_cams, cudaMemcpyDeviceToHost,
+                           ctx->stream),
+           "get_params");
+  BLK_CUDA(cudaMemcpyAsync(pts_out, ctx->B.X[ctx->cur], sizeof(double) * 3 * ctx->B.n_pts, cudaMemcpyDeviceToHost,
+                           ctx->stream),
+           "get_params");
+  BLK_CUDA(cudaStreamSynchronize(ctx->stream), "get_params");
+  return DBA_OK;
+}
+
+dba_status dba_block_layout(const dba_block_ctx* ctx, int64_t* n_blocks, int64_t* n_point_copies,
+                            int64_t* n_camera_copies) {
+  if (!ctx) return DBA_EINVAL;
+  if (!ctx->has_problem) return DBA_ESTATE;
+  if (n_blocks) *n_blocks = ctx->B.n_blocks;
+  if (n_point_copies) *n_point_copies = ctx->B.n_pc;
+  if (n_camera_copies) *n_camera_copies = ctx->B.n_cc;
+  return DBA_OK;
+}
+
+const char* dba_block_last_error(const dba_block_ctx* ctx) {
+  return ctx ? ctx->err.c_str() : g_block_error.c_str();
+}
+
+void dba_block_destroy(dba_block_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  ctx->free_all();
+  if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+  if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+}  // extern "C"

@@ -26,7 +26,11 @@ EXPORTED = [
     "dba_last_error", "dba_destroy", "dba_mlp_create", "dba_mlp_destroy", "dba_mlp_last_error",
     "dba_mlp_get_params", "dba_mlp_set_params", "dba_mlp_harvest", "dba_mlp_fit_normalizer",
     "dba_mlp_loss_grad", "dba_mlp_train", "dba_mlp_predict", "dba_set_warm_start",
+    "dba_block_create", "dba_block_set_observations", "dba_block_set_reference_pixels", "dba_block_iterate",
+    "dba_block_iterate_until", "dba_block_get_params", "dba_block_layout", "dba_block_last_error",
+    "dba_block_destroy",
 ]
+DBA_BLOCK_MAX_POINTS, DBA_BLOCK_MAX_CAMERAS = 32, 4
 DBA_MLP_N_PARAMS, DBA_MLP_N_FEATURES, DBA_MLP_N_TARGETS = 11552, 32, 16
 DBA_NOALLOC_MAX_OBS = 16777216
 
@@ -115,9 +119,21 @@ def load():
     L.dba_last_error.restype = ctypes.c_char_p
     L.dba_destroy.argtypes = [vp]
     L.dba_destroy.restype = None
+    L.dba_block_create.argtypes = [P(dba_config), ctypes.c_int, ctypes.c_int, P(vp)]
+    L.dba_block_set_observations.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ip, ip, dp, dp,
+                                             dp]
+    L.dba_block_set_reference_pixels.argtypes = [vp, dp, P(ctypes.c_uint8)]
+    L.dba_block_iterate.argtypes = [vp, ctypes.c_int, P(dba_stats)]
+    L.dba_block_iterate_until.argtypes = [vp, ctypes.c_int, ctypes.c_double, P(dba_stats)]
+    L.dba_block_get_params.argtypes = [vp, dp, dp]
+    L.dba_block_layout.argtypes = [vp, P(ctypes.c_int64), P(ctypes.c_int64), P(ctypes.c_int64)]
+    L.dba_block_last_error.argtypes = [vp]
+    L.dba_block_last_error.restype = ctypes.c_char_p
+    L.dba_block_destroy.argtypes = [vp]
+    L.dba_block_destroy.restype = None
     for name in EXPORTED:
         if name not in ("dba_config_default", "dba_last_error", "dba_destroy", "dba_mlp_destroy",
-                        "dba_mlp_last_error"):
+                        "dba_mlp_last_error", "dba_block_last_error", "dba_block_destroy"):
             getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -393,6 +409,88 @@ class Solver:
     def close(self):
         if self.ctx:
             dba_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BlockSolver:
+    """Block subproblems of pi points x kappa cameras (Sec. 3.1.4, Eq. 14) for one scene:
+    the context dba_block_ctx."""
+
+    def __init__(self, scene, block_points, block_cams, precision=None, inner_steps=5, rho_x=None, rho_y=None,
+                 rho_angle=None, stream=None, ground_truth=True, **cfg_overrides):
+        self.scene = scene
+        prec = scene.precision if precision is None else precision
+        self.cfg = dba_config_default(
+            focal=scene.focal, cx=scene.cx, cy=scene.cy, loss=scene.loss, loss_param=scene.loss_param,
+            rho_x=scene.rho_x if rho_x is None else rho_x, rho_y=scene.rho_y if rho_y is None else rho_y,
+            rho_angle=getattr(scene, "rho_angle", 0.0) if rho_angle is None else rho_angle,
+            inner_steps=inner_steps, precision=prec, cuda_stream=stream, **cfg_overrides)
+        L = load()
+        self.ctx = ctypes.c_void_p()
+        st = L.dba_block_create(ctypes.byref(self.cfg), int(block_points), int(block_cams), ctypes.byref(self.ctx))
+        if st != DBA_OK:
+            raise DbaError(st, L.dba_block_last_error(None).decode())
+        try:
+            pt_idx = np.ascontiguousarray(scene.pt_idx, dtype=np.int32)
+            cam_idx = np.ascontiguousarray(scene.cam_idx, dtype=np.int32)
+            l = pt_idx.shape[0]
+            z = _d(scene.z, (l, 2))
+            cams0 = _d(scene.cams0, (scene.n_cams, 6))
+            pts0 = _d(scene.pts0, (scene.n_pts, 3))
+            self._check(L.dba_block_set_observations(self.ctx, scene.n_cams, scene.n_pts, l, _ptr(pt_idx),
+                                                     _ptr(cam_idx), _ptr(z), _ptr(cams0), _ptr(pts0)))
+            if ground_truth:
+                zt = _d(scene.z_true, (l, 2))
+                mask = scene.clean_mask() if hasattr(scene, "clean_mask") else None
+                mp = None
+                if mask is not None:
+                    mask = np.ascontiguousarray(mask, dtype=np.uint8)
+                    mp = mask.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+                self._check(L.dba_block_set_reference_pixels(self.ctx, _ptr(zt), mp))
+        except Exception:
+            self.close()
+            raise
+
+    def _check(self, st):
+        if st != DBA_OK:
+            raise DbaError(st, load().dba_block_last_error(self.ctx).decode())
+
+    def iterate(self, n, stats=True):
+        st = dba_stats()
+        self._check(load().dba_block_iterate(self.ctx, int(n), ctypes.byref(st) if stats else None))
+        return st.as_dict() if stats else None
+
+    def iterate_until(self, max_iters, target):
+        st = dba_stats()
+        self._check(load().dba_block_iterate_until(self.ctx, int(max_iters), float(target), ctypes.byref(st)))
+        return st.as_dict()
+
+    def params(self):
+        cams = np.zeros((self.scene.n_cams, 6))
+        pts = np.zeros((self.scene.n_pts, 3))
+        self._check(load().dba_block_get_params(self.ctx, _ptr(cams), _ptr(pts)))
+        return cams, pts
+
+    def layout(self):
+        nb, npc, ncc = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        self._check(load().dba_block_layout(self.ctx, ctypes.byref(nb), ctypes.byref(npc), ctypes.byref(ncc)))
+        return {"n_blocks": nb.value, "n_point_copies": npc.value, "n_camera_copies": ncc.value}
+
+    def close(self):
+        if self.ctx:
+            load().dba_block_destroy(self.ctx)
             self.ctx = None
 
     def __enter__(self):

@@ -1,0 +1,139 @@
+"""Block subproblems (Sec. 3.1.4, Eq. 14) on the GPU against the block oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1708_07954_gb300 import build, dba
+from paper_1708_07954_gb300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-9
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    dba.load()
+
+
+def oracle_cfg(solver):
+    c = solver.cfg
+    return O.config(focal=c.focal, cx=c.cx, cy=c.cy, loss=c.loss, loss_param=c.loss_param, rho_x=c.rho_x,
+                    rho_y=c.rho_y, rho_angle=c.rho_angle, inner_steps=c.inner_steps, lm_lambda0=c.lm_lambda0,
+                    lm_lambda_min=c.lm_lambda_min, eps_depth=c.eps_depth, lm_model_tol=c.lm_model_tol)
+
+
+def relerr(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+@pytest.mark.parametrize("pi,kappa", [(1, 1), (8, 2), (32, 4), (5, 3), (32, 1)])
+def test_fp64_matches_block_oracle_per_iteration(pi, kappa):
+    sc = S.scene1(n_pts=400, n_cams=16, seed=17)
+    with dba.BlockSolver(sc, pi, kappa, precision=dba.DBA_PREC_F64) as s:
+        cfg = oracle_cfg(s)
+        st = O.BlockState(sc, pi, kappa)
+        lay = s.layout()
+        assert lay == {"n_blocks": st.layout.n_blocks, "n_point_copies": st.layout.n_pc,
+                       "n_camera_copies": st.layout.n_cc}
+        for it in range(6):
+            mg = s.iterate(1)
+            mo = st.iterate(cfg, 1)
+            cams, pts = s.params()
+            assert relerr(cams, st.cams) <= TOL64, it
+            assert relerr(pts, st.pts) <= TOL64, it
+            for k in ("rmse_obs", "objective", "primal_res", "dual_res"):
+                assert abs(mg[k] - mo[k]) <= 1e-8 * max(abs(mo[k]), 1e-12), (it, k)
+            assert abs(mg["rmse_gt"] - mo["rmse_gt"]) <= 1e-8 * max(mo["rmse_gt"], 1e-12)
+
+
+def test_fp64_ring_scene_many_iterations():
+    """Workload-0 geometry (every point in every view): blocks of 8 points x 2 cameras
+    for 30 iterations stay with the oracle."""
+    sc = S.scene0()
+    with dba.BlockSolver(sc, 8, 2, precision=dba.DBA_PREC_F64) as s:
+        cfg = oracle_cfg(s)
+        st = O.BlockState(sc, 8, 2)
+        for chunk in (1, 9, 20):
+            s.iterate(chunk, stats=False)
+            st.iterate(cfg, chunk)
+            cams, pts = s.params()
+            assert relerr(cams, st.cams) <= TOL64 and relerr(pts, st.pts) <= TOL64
+
+
+def test_one_point_one_camera_blocks_equal_the_per_observation_path():
+    sc = S.scene1(n_pts=500, n_cams=16, seed=23)
+    with dba.BlockSolver(sc, 1, 1, precision=dba.DBA_PREC_F64) as a, \
+            dba.Solver(sc, precision=dba.DBA_PREC_F64) as b:
+        a.iterate(10, stats=False)
+        b.iterate(10, stats=False)
+        ca, pa = a.params()
+        cb, pb = b.params()
+        assert relerr(ca, cb) <= TOL64 and relerr(pa, pb) <= TOL64
+
+
+@pytest.mark.parametrize("pi,kappa", [(8, 2), (32, 4)])
+def test_fp32_tracks_the_fp64_oracle(pi, kappa):
+    sc = S.scene1(n_pts=1500, n_cams=24, seed=29)
+    with dba.BlockSolver(sc, pi, kappa, precision=dba.DBA_PREC_F32_LOCAL) as s:
+        cfg = oracle_cfg(s)
+        st = O.BlockState(sc, pi, kappa)
+        mg = s.iterate(40)
+        mo = st.iterate(cfg, 40)
+        assert abs(mg["rmse_gt"] - mo["rmse_gt"]) <= 1e-3
+        assert abs(mg["rmse_obs"] - mo["rmse_obs"]) <= 1e-3
+        cams, _ = s.params()
+        assert relerr(cams, st.cams) <= 1e-4
+
+
+def test_edge_cases_single_observation_points_and_unobserved_points():
+    """Tracks of length one, a point with no observation (keeps its value), one camera
+    per block and one point per block in the same problem."""
+    sc = S.scene1(n_pts=200, n_cams=12, seed=31)
+    keep = np.ones(sc.n_obs, bool)
+    first = np.searchsorted(sc.pt_idx, np.arange(sc.n_pts))
+    # point 0: no observation; points 1..20: only their first observation
+    keep[sc.pt_idx == 0] = False
+    for i in range(1, 21):
+        idx = np.nonzero(sc.pt_idx == i)[0]
+        keep[idx[1:]] = False
+    del first
+    sub = S.Scene(n_cams=sc.n_cams, n_pts=sc.n_pts, pt_idx=sc.pt_idx[keep], cam_idx=sc.cam_idx[keep],
+                  z=sc.z[keep], z_true=sc.z_true[keep], outlier=sc.outlier[keep], cams_gt=sc.cams_gt,
+                  pts_gt=sc.pts_gt, cams0=sc.cams0, pts0=sc.pts0, focal=sc.focal, cx=sc.cx, cy=sc.cy,
+                  loss=sc.loss, loss_param=sc.loss_param, rho_x=sc.rho_x, rho_y=sc.rho_y,
+                  rho_angle=sc.rho_angle)
+    for pi, kappa in ((1, 1), (7, 3)):
+        with dba.BlockSolver(sub, pi, kappa, precision=dba.DBA_PREC_F64) as s:
+            cfg = oracle_cfg(s)
+            st = O.BlockState(sub, pi, kappa)
+            s.iterate(5, stats=False)
+            st.iterate(cfg, 5)
+            cams, pts = s.params()
+            assert relerr(cams, st.cams) <= TOL64 and relerr(pts, st.pts) <= TOL64
+            assert np.array_equal(pts[0], sub.pts0[0])
+
+
+def test_larger_blocks_reach_the_target_in_fewer_iterations():
+    """Sec. 4: more points and cameras per update lower the error faster per iteration."""
+    sc = S.scene2(n_pts=20000)
+    its = {}
+    for pi, kappa in ((1, 1), (8, 2), (32, 4)):
+        with dba.BlockSolver(sc, pi, kappa) as s:
+            its[(pi, kappa)] = s.iterate_until(400, 0.5)["iters_done"]
+    assert its[(32, 4)] < its[(8, 2)] < its[(1, 1)], its
+
+
+def test_errors():
+    sc = S.scene0(n_pts=10, n_cams=3)
+    with pytest.raises(dba.DbaError) as e:
+        dba.BlockSolver(sc, 33, 1)
+    assert e.value.status == dba.DBA_EINVAL
+    with pytest.raises(dba.DbaError) as e:
+        dba.BlockSolver(sc, 4, 5)
+    assert e.value.status == dba.DBA_EINVAL
+    with dba.BlockSolver(sc, 4, 2, ground_truth=False) as s:
+        with pytest.raises(dba.DbaError) as e:
+            s.iterate_until(5, 0.5)
+        assert e.value.status == dba.DBA_ESTATE
