@@ -297,6 +297,10 @@ dba_status dba_block_iterate(dba_block_ctx* ctx, int n_iters, dba_stats* stats);
 /* Iterates until rmse_gt <= target (metrics after every iteration, included in
  * stats->seconds) or max_iters; needs reference pixels (ESTATE). */
 dba_status dba_block_iterate_until(dba_block_ctx* ctx, int max_iters, double target_rmse_gt, dba_stats* stats);
+/* Runs n_iters iterations (no metrics) with CUDA events around each launch and
+ * writes the mean device milliseconds of block_solve, consensus and dual
+ * ascent (the consensus slot includes a residual-buffer clear) into ms_out[3]. */
+dba_status dba_block_profile(dba_block_ctx* ctx, int n_iters, double* ms_out);
 /* Consensus cameras [m][6] and points [n][3]. */
 dba_status dba_block_get_params(dba_block_ctx* ctx, double* cams_out, double* pts_out);
 /* Number of blocks, point copies and camera copies (any pointer may be NULL). */

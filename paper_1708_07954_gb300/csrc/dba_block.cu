@@ -467,34 +467,52 @@ __global__ void __launch_bounds__(kBlkWarps * 32) block_solve_kernel(BlockProble
 
 // Eqs. (10)-(11) over copies: consensus = old consensus + mean over its copies of
 // (offset + scaled dual), the old duals; a point or camera without copies keeps its value.
+// Points (a few copies each): one thread per point.
 template <typename T>
-__global__ void block_consensus_kernel(BlockProblem B, int cur) {
+__global__ void block_point_consensus_kernel(BlockProblem B, int cur) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= B.n_pts) return;
   const int nxt = cur ^ 1;
-  if (t < B.n_pts) {
-    const int i = (int)t, k0 = B.pt_cp_off[i], k1 = B.pt_cp_off[i + 1];
-    const T* del = static_cast<const T*>(B.pc_delta);
-    for (int u = 0; u < 3; ++u) {
-      double s = 0.0;
-      for (int k = k0; k < k1; ++k) {
-        const int cp = B.pt_cp[k];
-        s += to_f64<T>(del[u * B.n_pc + cp]) + B.pc_a[u * B.n_pc + cp];
-      }
-      const double x = B.X[cur][3 * (long long)i + u];
-      B.X[nxt][3 * (long long)i + u] = k1 > k0 ? x + s / (double)(k1 - k0) : x;
+  const int i = (int)t, k0 = B.pt_cp_off[i], k1 = B.pt_cp_off[i + 1];
+  const T* del = static_cast<const T*>(B.pc_delta);
+  for (int u = 0; u < 3; ++u) {
+    double s = 0.0;
+    for (int k = k0; k < k1; ++k) {
+      const int cp = B.pt_cp[k];
+      s += to_f64<T>(del[u * B.n_pc + cp]) + B.pc_a[u * B.n_pc + cp];
     }
-  } else if (t < (long long)B.n_pts + B.n_cams) {
-    const int j = (int)(t - B.n_pts), k0 = B.cam_cp_off[j], k1 = B.cam_cp_off[j + 1];
-    const T* del = static_cast<const T*>(B.cc_delta);
-    for (int u = 0; u < 6; ++u) {
-      double s = 0.0;
-      for (int k = k0; k < k1; ++k) {
-        const int cp = B.cam_cp[k];
-        s += to_f64<T>(del[u * B.n_cc + cp]) + B.cc_a[u * B.n_cc + cp];
-      }
-      const double y = B.Y[cur][6 * (long long)j + u];
-      B.Y[nxt][6 * (long long)j + u] = k1 > k0 ? y + s / (double)(k1 - k0) : y;
-    }
+    const double x = B.X[cur][3 * (long long)i + u];
+    B.X[nxt][3 * (long long)i + u] = k1 > k0 ? x + s / (double)(k1 - k0) : x;
+  }
+}
+
+// Cameras (thousands of copies each): one CTA of 256 threads per camera, strided
+// partial sums and a fixed reduction tree.
+template <typename T>
+__global__ void __launch_bounds__(256) block_camera_consensus_kernel(BlockProblem B, int cur) {
+  __shared__ double red[6][256];
+  const int j = blockIdx.x, nxt = cur ^ 1;
+  const int k0 = B.cam_cp_off[j], k1 = B.cam_cp_off[j + 1];
+  const T* del = static_cast<const T*>(B.cc_delta);
+  double s[6] = {0, 0, 0, 0, 0, 0};
+  for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+    const int cp = B.cam_cp[k];
+#pragma unroll
+    for (int u = 0; u < 6; ++u) s[u] += to_f64<T>(del[u * B.n_cc + cp]) + B.cc_a[u * B.n_cc + cp];
+  }
+#pragma unroll
+  for (int u = 0; u < 6; ++u) red[u][threadIdx.x] = s[u];
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+#pragma unroll
+      for (int u = 0; u < 6; ++u) red[u][threadIdx.x] += red[u][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < 6) {
+    const int u = threadIdx.x;
+    const double y = B.Y[cur][6 * (long long)j + u];
+    B.Y[nxt][6 * (long long)j + u] = k1 > k0 ? y + red[u][0] / (double)(k1 - k0) : y;
   }
 }
 
@@ -670,12 +688,20 @@ cudaError_t launch_block_solve(dba_block_ctx* ctx) {
     set = true;
   }
   if (!ctx->grid) {
-    int per_sm = 0, dev = 0, sms = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dba::block_solve_kernel<T>,
-                                                                  dba::kBlkWarps * 32, smem);
+    // resident CTAs per SM from the resources one CTA takes (registers, shared memory)
+    cudaFuncAttributes fa;
+    int dev = 0, sms = 0, smem_sm = 0, smem_rsv = 0, regs_sm = 0;
+    cudaError_t e = cudaFuncGetAttributes(&fa, dba::block_solve_kernel<T>);
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
     if (e != cudaSuccess) return e;
+    const int threads = dba::kBlkWarps * 32;
+    int per_sm = 2048 / threads;
+    per_sm = std::min(per_sm, regs_sm / std::max(1, (fa.numRegs + 7) / 8 * 8 * threads));
+    per_sm = std::min(per_sm, smem_sm / ((int)smem + smem_rsv + (int)fa.sharedSizeBytes));
     ctx->grid = std::max(per_sm, 1) * sms;
   }
   const int need = dba::blocks_of(ctx->B.n_blocks, dba::kBlkWarps);
@@ -685,16 +711,25 @@ cudaError_t launch_block_solve(dba_block_ctx* ctx) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_iteration(dba_block_ctx* ctx, bool with_sums) {
-  cudaError_t e = ctx->fp32 ? launch_block_solve<float>(ctx) : launch_block_solve<double>(ctx);
+// One iteration: block solves, consensus, dual ascent.  ev (nullable) receives an event
+// before each of the three launches and one after the last.
+cudaError_t launch_iteration(dba_block_ctx* ctx, bool with_sums, cudaEvent_t* ev = nullptr) {
+  cudaError_t e;
+  if (ev && (e = cudaEventRecord(ev[0], ctx->stream)) != cudaSuccess) return e;
+  e = ctx->fp32 ? launch_block_solve<float>(ctx) : launch_block_solve<double>(ctx);
   if (e != cudaSuccess) return e;
-  const long long nc = (long long)ctx->B.n_pts + ctx->B.n_cams;
-  if (ctx->fp32)
-    dba::block_consensus_kernel<float><<<dba::blocks_of(nc, 256), 256, 0, ctx->stream>>>(ctx->B, ctx->cur);
-  else
-    dba::block_consensus_kernel<double><<<dba::blocks_of(nc, 256), 256, 0, ctx->stream>>>(ctx->B, ctx->cur);
+  if (ev && (e = cudaEventRecord(ev[1], ctx->stream)) != cudaSuccess) return e;
+  const int gp = dba::blocks_of(ctx->B.n_pts, 256);
+  if (ctx->fp32) {
+    dba::block_point_consensus_kernel<float><<<gp, 256, 0, ctx->stream>>>(ctx->B, ctx->cur);
+    dba::block_camera_consensus_kernel<float><<<ctx->B.n_cams, 256, 0, ctx->stream>>>(ctx->B, ctx->cur);
+  } else {
+    dba::block_point_consensus_kernel<double><<<gp, 256, 0, ctx->stream>>>(ctx->B, ctx->cur);
+    dba::block_camera_consensus_kernel<double><<<ctx->B.n_cams, 256, 0, ctx->stream>>>(ctx->B, ctx->cur);
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (with_sums && (e = cudaMemsetAsync(ctx->B.sums, 0, 8 * sizeof(double), ctx->stream)) != cudaSuccess) return e;
+  if (ev && (e = cudaEventRecord(ev[2], ctx->stream)) != cudaSuccess) return e;
   const long long ncp = ctx->B.n_pc + ctx->B.n_cc;
   const dba::Prm<double> q64 = dba::make_prm<double>(ctx->prm);
   if (ctx->fp32)
@@ -704,6 +739,7 @@ cudaError_t launch_iteration(dba_block_ctx* ctx, bool with_sums) {
     dba::block_dual_kernel<double><<<dba::blocks_of(ncp, 256), 256, 0, ctx->stream>>>(ctx->B, q64, ctx->cur,
                                                                                      with_sums ? 1 : 0);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (ev && (e = cudaEventRecord(ev[3], ctx->stream)) != cudaSuccess) return e;
   ctx->cur ^= 1;
   return cudaSuccess;
 }
@@ -1039,6 +1075,31 @@ dba_status dba_block_iterate_until(dba_block_ctx* ctx, int max_iters, double tar
     if (stats->rmse_gt <= target_rmse_gt) break;
   }
   stats->seconds = secs;
+  return DBA_OK;
+}
+
+dba_status dba_block_profile(dba_block_ctx* ctx, int n_iters, double* ms_out) {
+  if (!ctx || !ms_out) return DBA_EINVAL;
+  if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_block_profile before set_observations");
+  if (n_iters <= 0) return ctx->fail(DBA_EINVAL, "dba_block_profile: n_iters must be positive");
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventCreate(&ev[k]);
+  double acc[3] = {0, 0, 0};
+  for (int it = 0; it < n_iters && e == cudaSuccess; ++it) {
+    e = launch_iteration(ctx, false, ev);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[3]);
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+      float ms = 0.f;
+      e = cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+      acc[k] += ms;
+    }
+    ctx->iters += 1;
+  }
+  for (int k = 0; k < 4; ++k)
+    if (ev[k]) cudaEventDestroy(ev[k]);
+  if (e != cudaSuccess) return ctx->cuda_fail(e, "dba_block_profile");
+  for (int k = 0; k < 3; ++k) ms_out[k] = acc[k] / n_iters;
   return DBA_OK;
 }
 

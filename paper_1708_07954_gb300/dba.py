@@ -27,7 +27,8 @@ EXPORTED = [
     "dba_mlp_get_params", "dba_mlp_set_params", "dba_mlp_harvest", "dba_mlp_fit_normalizer",
     "dba_mlp_loss_grad", "dba_mlp_train", "dba_mlp_predict", "dba_set_warm_start",
     "dba_block_create", "dba_block_set_observations", "dba_block_set_reference_pixels", "dba_block_iterate",
-    "dba_block_iterate_until", "dba_block_get_params", "dba_block_layout", "dba_block_last_error",
+    "dba_block_iterate_until", "dba_block_profile", "dba_block_get_params", "dba_block_layout",
+    "dba_block_last_error",
     "dba_block_destroy",
 ]
 DBA_BLOCK_MAX_POINTS, DBA_BLOCK_MAX_CAMERAS = 32, 4
@@ -125,6 +126,7 @@ def load():
     L.dba_block_set_reference_pixels.argtypes = [vp, dp, P(ctypes.c_uint8)]
     L.dba_block_iterate.argtypes = [vp, ctypes.c_int, P(dba_stats)]
     L.dba_block_iterate_until.argtypes = [vp, ctypes.c_int, ctypes.c_double, P(dba_stats)]
+    L.dba_block_profile.argtypes = [vp, ctypes.c_int, dp]
     L.dba_block_get_params.argtypes = [vp, dp, dp]
     L.dba_block_layout.argtypes = [vp, P(ctypes.c_int64), P(ctypes.c_int64), P(ctypes.c_int64)]
     L.dba_block_last_error.argtypes = [vp]
@@ -476,6 +478,11 @@ class BlockSolver:
         st = dba_stats()
         self._check(load().dba_block_iterate_until(self.ctx, int(max_iters), float(target), ctypes.byref(st)))
         return st.as_dict()
+
+    def profile(self, n):
+        ms = np.zeros(3)
+        self._check(load().dba_block_profile(self.ctx, int(n), _ptr(ms)))
+        return {"block_solve": ms[0], "block_consensus": ms[1], "block_dual": ms[2]}
 
     def params(self):
         cams = np.zeros((self.scene.n_cams, 6))

@@ -212,7 +212,8 @@ def scene1(seed: int = 1001, n_pts: int = 20000, n_cams: int = 64) -> Scene:
     return s
 
 
-def scene2(seed: int = 1002, n_pts: int = 500000, lanes: int = 25, stations: int = 40) -> Scene:
+def scene2(seed: int = 1002, n_pts: int = 500000, lanes: int = 25, stations: int = 40,
+           outlier_frac: float = 0.05) -> Scene:
     rng = np.random.default_rng(seed)
     alt, step = 150.0, 2.5
     m = lanes * stations
@@ -244,7 +245,7 @@ def scene2(seed: int = 1002, n_pts: int = 500000, lanes: int = 25, stations: int
     inside = np.abs(xy[:, None, :] - bc[None, :, :]).max(axis=2) < bs[None, :]
     roof = np.where(inside, bh[None, :], 0.0).max(axis=1)
     pts = np.concatenate([xy, (zg + roof)[:, None]], axis=1)
-    s = _finish(rng, rot, centers, pts, pt_idx, cam_idx, 0.5, 0.05, f"grid{m}-ground{n_pts}-pow")
+    s = _finish(rng, rot, centers, pts, pt_idx, cam_idx, 0.5, outlier_frac, f"grid{m}-ground{n_pts}-pow")
     s.loss, s.loss_param, s.iters, s.precision = LOSS_HUBER, 2.0, 300, PREC_F32
     s.rho_x, s.rho_y, s.rho_angle = default_rho(s)
     return s
