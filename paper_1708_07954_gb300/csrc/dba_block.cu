@@ -76,32 +76,42 @@ __device__ __forceinline__ T wsum(T v) {
   return v;
 }
 
-template <typename T>
+// Per-warp shared memory of one block solve; KC = the most cameras a block holds.
+template <typename T, int KC>
 struct BlkSmem {
-  T lin[kBlkMaxCams][kLin][32];  // linearisation of each lane's observation slots
-  T S[kBlkMaxU][kBlkMaxU + 1];   // reduced camera system, then its Cholesky factor
-  T rhs[kBlkMaxU];
-  T g[kBlkMaxU];                 // camera part of the block gradient
-  T dy[kBlkMaxU];                // camera step
-  T vbar[kBlkMaxCams][6];        // camera consensus
-  T d[kBlkMaxCams][6];           // camera copy offsets
-  T dt[kBlkMaxCams][6];          // trial offsets
-  T a[kBlkMaxCams][6];           // camera scaled duals
+  static constexpr int kU = 6 * KC;
+  static constexpr int kPairs = KC * (KC + 1) / 2;
+  T lin[KC][kLin][32];        // each lane's observation slots: A = dz/dx (2x3), B = dz/dy (2x6), 2w, e
+  T U[KC][2][32];             // 2w A W_p g_p per slot
+  T Q[kPairs][4][32];         // per camera pair c1 <= c2: 2x2 weight of the point's Schur term
+  signed char slot[KC][32];   // slot of each lane's observation on camera c (-1: none)
+  T S[kU][kU + 1];            // reduced camera system, then its Cholesky factor
+  T rhs[kU];
+  T g[kU];                    // camera part of the block gradient
+  T dy[kU];                   // camera step
+  T vbar[KC][6];              // camera consensus
+  T d[KC][6];                 // camera copy offsets
+  T dt[KC][6];                // trial offsets
+  T a[KC][6];                 // camera scaled duals
 };
+
+template <int KC>
+__device__ __forceinline__ int pair_index(int c1, int c2) {  // c1 <= c2
+  return c1 * KC - c1 * (c1 - 1) / 2 + (c2 - c1);
+}
 
 // Eq. (14) at (point offsets dp of this lane, camera offsets dc): misfits of the
 // lane's observations + its point's dual and penalty terms, summed over the warp,
 // plus the cameras' terms.  +inf when an observation is behind its camera.
-template <typename T>
-__device__ __forceinline__ T block_objective(const Prm<T>& q, bool act, int nob, const int oc[kBlkMaxCams],
-                                             const T oz0[kBlkMaxCams], const T oz1[kBlkMaxCams], const T xbar[3],
-                                             const T dp[3], const T ax[3], const BlkSmem<T>& W, const T (*dc)[6],
-                                             int nc) {
+template <typename T, int KC>
+__device__ __forceinline__ T block_objective(const Prm<T>& q, bool act, int nob, const int oc[KC], const T oz0[KC],
+                                             const T oz1[KC], const T xbar[3], const T dp[3], const T ax[3],
+                                             const BlkSmem<T, KC>& W, const T (*dc)[6], int nc) {
   T s = 0;
   bool ok = true;
   if (act) {
 #pragma unroll
-    for (int k = 0; k < kBlkMaxCams; ++k) {
+    for (int k = 0; k < KC; ++k) {
       if (k < nob) {
         const int c = oc[k];
         T v[9];
@@ -133,8 +143,8 @@ __device__ __forceinline__ T block_objective(const Prm<T>& q, bool act, int nob,
   return ok ? s + sc : Num<T>::inf();
 }
 
-template <typename T>
-__device__ void solve_block(const BlockProblem& B, const Prm<T>& q, const BlockInfo& bi, BlkSmem<T>& W, int lane,
+template <typename T, int KC>
+__device__ void solve_block(const BlockProblem& B, const Prm<T>& q, const BlockInfo& bi, BlkSmem<T, KC>& W, int lane,
                             int cur) {
   using V2 = typename Num<T>::V2;
   const int np = bi.np, nc = bi.nc, n_u = 6 * nc;
@@ -144,8 +154,13 @@ __device__ void solve_block(const BlockProblem& B, const Prm<T>& q, const BlockI
   T* cdel = static_cast<T*>(B.cc_delta);
   T xbar[3] = {0, 0, 0}, dp[3] = {0, 0, 0}, ax[3] = {0, 0, 0};
   int nob = 0;
-  int oc[kBlkMaxCams] = {0, 0, 0, 0};
-  T oz0[kBlkMaxCams] = {0, 0, 0, 0}, oz1[kBlkMaxCams] = {0, 0, 0, 0};
+  int oc[KC];
+  T oz0[KC], oz1[KC];
+#pragma unroll
+  for (int k = 0; k < KC; ++k) {
+    oc[k] = 0;
+    oz0[k] = oz1[k] = 0;
+  }
   if (act) {
     const int i = B.pc_pt[pc];
 #pragma unroll
@@ -158,7 +173,7 @@ __device__ void solve_block(const BlockProblem& B, const Prm<T>& q, const BlockI
     nob = B.pc_obs[pc + 1] - ob0;
     const V2* zz = static_cast<const V2*>(B.z);
 #pragma unroll
-    for (int k = 0; k < kBlkMaxCams; ++k)
+    for (int k = 0; k < KC; ++k)
       if (k < nob) {
         oc[k] = B.obs_lc[ob0 + k];
         const V2 p = zz[ob0 + k];
@@ -167,13 +182,14 @@ __device__ void solve_block(const BlockProblem& B, const Prm<T>& q, const BlockI
       }
   }
   // slot of this lane's observation on each camera of the block (-1: none)
-  int slot[kBlkMaxCams];
+  int slot[KC];
 #pragma unroll
-  for (int c = 0; c < kBlkMaxCams; ++c) {
+  for (int c = 0; c < KC; ++c) {
     slot[c] = -1;
 #pragma unroll
-    for (int k = 0; k < kBlkMaxCams; ++k)
+    for (int k = 0; k < KC; ++k)
       if (k < nob && oc[k] == c) slot[c] = k;
+    W.slot[c][lane] = (signed char)slot[c];
   }
   if (lane < n_u) {
     const int c = lane / 6, u = lane % 6;
@@ -185,14 +201,14 @@ __device__ void solve_block(const BlockProblem& B, const Prm<T>& q, const BlockI
   }
   __syncwarp();
 
-  T L = block_objective<T>(q, act, nob, oc, oz0, oz1, xbar, dp, ax, W, W.d, nc);
+  T L = block_objective<T, KC>(q, act, nob, oc, oz0, oz1, xbar, dp, ax, W, W.d, nc);
   T lambda = T(-1);
   for (int step = 0; step < q.steps; ++step) {
     // linearise this lane's observations at the current copies
     T Hpp[6] = {0, 0, 0, 0, 0, 0}, gp[3] = {0, 0, 0};
     T noise = 0, trc = 0;
 #pragma unroll
-    for (int k = 0; k < kBlkMaxCams; ++k) {
+    for (int k = 0; k < KC; ++k) {
       if (k < nob) {
         const int c = oc[k];
         T v[9];
@@ -239,7 +255,6 @@ __device__ void solve_block(const BlockProblem& B, const Prm<T>& q, const BlockI
     if (act)
 #pragma unroll
       for (int u = 0; u < 3; ++u) gp[u] += q.rho_x * (ax[u] + dp[u]);
-    __syncwarp();
     if (lambda < T(0)) {
       T tr = (act ? Hpp[0] + Hpp[3] + Hpp[5] + T(3) * q.rho_x : T(0)) + trc;
       tr = wsum(tr);
@@ -266,97 +281,121 @@ __device__ void solve_block(const BlockProblem& B, const Prm<T>& q, const BlockI
     const T Wg0 = Wp[0] * gp[0] + Wp[1] * gp[1] + Wp[2] * gp[2];
     const T Wg1 = Wp[1] * gp[0] + Wp[3] * gp[1] + Wp[4] * gp[2];
     const T Wg2 = Wp[2] * gp[0] + Wp[4] * gp[1] + Wp[5] * gp[2];
-    // camera gradient and reduced right-hand side: -g_c + H_cp W_p g_p summed over points
-    for (int c = 0; c < nc; ++c) {
-      const int k = act ? slot[c] : -1;
-      T tw = 0, e0 = 0, e1 = 0, u0 = 0, u1 = 0;
-      if (k >= 0) {
-        tw = W.lin[k][18][lane];
-        e0 = W.lin[k][19][lane];
-        e1 = W.lin[k][20][lane];
-        u0 = tw * (W.lin[k][0][lane] * Wg0 + W.lin[k][1][lane] * Wg1 + W.lin[k][2][lane] * Wg2);
-        u1 = tw * (W.lin[k][3][lane] * Wg0 + W.lin[k][4][lane] * Wg1 + W.lin[k][5][lane] * Wg2);
+    // this point's terms of the reduced system: U_k = 2w_k A_k W_p g_p and, per camera
+    // pair, Q = [c1 = c2] 2w_1 I - (2w_1 A_1) W_p (2w_2 A_2)^T
+#pragma unroll
+    for (int k = 0; k < KC; ++k)
+      if (k < nob) {
+        const T tw = W.lin[k][18][lane];
+        W.U[k][0][lane] = tw * (W.lin[k][0][lane] * Wg0 + W.lin[k][1][lane] * Wg1 + W.lin[k][2][lane] * Wg2);
+        W.U[k][1][lane] = tw * (W.lin[k][3][lane] * Wg0 + W.lin[k][4][lane] * Wg1 + W.lin[k][5][lane] * Wg2);
       }
 #pragma unroll
-      for (int u = 0; u < 6; ++u) {
-        T b0 = 0, b1 = 0;
-        if (k >= 0) {
-          b0 = W.lin[k][6 + u][lane];
-          b1 = W.lin[k][12 + u][lane];
-        }
-        const T gsum = wsum(-tw * (b0 * e0 + b1 * e1));
-        const T hsum = wsum(b0 * u0 + b1 * u1);
-        if (lane == 0) {
-          const T gfull = gsum + q.rho(3 + u) * (W.a[c][u] + W.d[c][u]);
-          W.g[6 * c + u] = gfull;
-          W.rhs[6 * c + u] = hsum - gfull;
-        }
-      }
-    }
-    // reduced camera matrix S = H_cc - sum_p H_cp W_p H_pc, block (c1, c2) at a time
-    for (int c1 = 0; c1 < nc; ++c1) {
-      for (int c2 = c1; c2 < nc; ++c2) {
-        const int k1 = act ? slot[c1] : -1, k2 = act ? slot[c2] : -1;
-        const bool both = k1 >= 0 && k2 >= 0;
-        T tw1 = 0, m00 = 0, m01 = 0, m10 = 0, m11 = 0;
-        if (both) {
-          tw1 = W.lin[k1][18][lane];
-          const T tw2 = W.lin[k2][18][lane];
-          // M = (2 w1 A1) W_p (2 w2 A2)^T, 2x2
-          const T a10 = W.lin[k1][0][lane], a11 = W.lin[k1][1][lane], a12 = W.lin[k1][2][lane];
-          const T a13 = W.lin[k1][3][lane], a14 = W.lin[k1][4][lane], a15 = W.lin[k1][5][lane];
+    for (int c1 = 0; c1 < KC; ++c1)
+#pragma unroll
+      for (int c2 = c1; c2 < KC; ++c2) {
+        const int k1 = slot[c1], k2 = slot[c2];
+        if (act && k1 >= 0 && k2 >= 0) {
+          const T tw1 = W.lin[k1][18][lane], tw2 = W.lin[k2][18][lane];
           const T a20 = W.lin[k2][0][lane], a21 = W.lin[k2][1][lane], a22 = W.lin[k2][2][lane];
           const T a23 = W.lin[k2][3][lane], a24 = W.lin[k2][4][lane], a25 = W.lin[k2][5][lane];
-          const T w20 = Wp[0] * a20 + Wp[1] * a21 + Wp[2] * a22, w21 = Wp[1] * a20 + Wp[3] * a21 + Wp[4] * a22,
-                  w22 = Wp[2] * a20 + Wp[4] * a21 + Wp[5] * a22;
-          const T w23 = Wp[0] * a23 + Wp[1] * a24 + Wp[2] * a25, w24 = Wp[1] * a23 + Wp[3] * a24 + Wp[4] * a25,
-                  w25 = Wp[2] * a23 + Wp[4] * a24 + Wp[5] * a25;
-          const T s = tw1 * tw2;
-          m00 = s * (a10 * w20 + a11 * w21 + a12 * w22);
-          m01 = s * (a10 * w23 + a11 * w24 + a12 * w25);
-          m10 = s * (a13 * w20 + a14 * w21 + a15 * w22);
-          m11 = s * (a13 * w23 + a14 * w24 + a15 * w25);
+          // columns of W_p A_2^T
+          const T w0 = Wp[0] * a20 + Wp[1] * a21 + Wp[2] * a22, w1 = Wp[1] * a20 + Wp[3] * a21 + Wp[4] * a22,
+                  w2 = Wp[2] * a20 + Wp[4] * a21 + Wp[5] * a22;
+          const T x0 = Wp[0] * a23 + Wp[1] * a24 + Wp[2] * a25, x1 = Wp[1] * a23 + Wp[3] * a24 + Wp[4] * a25,
+                  x2 = Wp[2] * a23 + Wp[4] * a24 + Wp[5] * a25;
+          const T a10 = W.lin[k1][0][lane], a11 = W.lin[k1][1][lane], a12 = W.lin[k1][2][lane];
+          const T a13 = W.lin[k1][3][lane], a14 = W.lin[k1][4][lane], a15 = W.lin[k1][5][lane];
+          const T sw = tw1 * tw2, dgw = c1 == c2 ? tw1 : T(0);
+          const int pr = pair_index<KC>(c1, c2);
+          W.Q[pr][0][lane] = dgw - sw * (a10 * w0 + a11 * w1 + a12 * w2);
+          W.Q[pr][1][lane] = -sw * (a10 * x0 + a11 * x1 + a12 * x2);
+          W.Q[pr][2][lane] = -sw * (a13 * w0 + a14 * w1 + a15 * w2);
+          W.Q[pr][3][lane] = dgw - sw * (a13 * x0 + a14 * x1 + a15 * x2);
         }
-        for (int r = 0; r < 6; ++r) {
-          T p0 = 0, p1 = 0;
-          if (both) {
-            p0 = W.lin[k1][6 + r][lane];
-            p1 = W.lin[k1][12 + r][lane];
+      }
+    __syncwarp();
+    // reduced camera system, one entry per lane at a time, summed over the block's points:
+    //   S(c1 r, c2 s) = sum_p B_1[:, r]^T Q B_2[:, s],  g_c = -sum 2w B^T e + rho (a + d),
+    //   rhs_c = sum_p B^T U - g_c
+    const int nS = 21 * nc + 18 * nc * (nc - 1);
+    const int nV = nS + 12 * nc;
+    for (int v = lane; v < nV; v += 32) {
+      T acc = 0;
+      if (v < nS) {
+        int c1 = 0, c2 = 0, e = v;
+        bool found = false;
+        for (c1 = 0; c1 < nc && !found; ++c1)
+          for (c2 = c1; c2 < nc; ++c2) {
+            const int size = c1 == c2 ? 21 : 36;
+            if (e < size) {
+              found = true;
+              break;
+            }
+            e -= size;
           }
-          // row r of B1^T M: (p0 m00 + p1 m10, p0 m01 + p1 m11)
-          const T q0 = p0 * m00 + p1 * m10, q1 = p0 * m01 + p1 * m11;
-          for (int s = (c1 == c2 ? r : 0); s < 6; ++s) {
-            T v = 0;
-            if (both) {
-              const T b0 = W.lin[k2][6 + s][lane], b1 = W.lin[k2][12 + s][lane];
-              v = -(q0 * b0 + q1 * b1);
-              if (c1 == c2) v += tw1 * (p0 * b0 + p1 * b1);
-            }
-            v = wsum(v);
-            if (lane == 0) {
-              W.S[6 * c1 + r][6 * c2 + s] = v;
-              W.S[6 * c2 + s][6 * c1 + r] = v;
-            }
+        --c1;  // the outer loop stepped past the pair it found
+        int r, s;
+        if (c1 == c2) {
+          r = 0;
+          while (e >= 6 - r) {
+            e -= 6 - r;
+            ++r;
+          }
+          s = r + e;
+        } else {
+          r = e / 6;
+          s = e % 6;
+        }
+        const int pr = pair_index<KC>(c1, c2);
+        for (int l = 0; l < np; ++l) {
+          const int k1 = W.slot[c1][l], k2 = W.slot[c2][l];
+          if (k1 >= 0 && k2 >= 0) {
+            const T b10 = W.lin[k1][6 + r][l], b11 = W.lin[k1][12 + r][l];
+            const T b20 = W.lin[k2][6 + s][l], b21 = W.lin[k2][12 + s][l];
+            acc += b10 * (W.Q[pr][0][l] * b20 + W.Q[pr][1][l] * b21) +
+                   b11 * (W.Q[pr][2][l] * b20 + W.Q[pr][3][l] * b21);
           }
         }
+        W.S[6 * c1 + r][6 * c2 + s] = acc;
+        W.S[6 * c2 + s][6 * c1 + r] = acc;
+      } else {
+        const int w = v - nS, c = w / 12, u = w % 6;
+        const bool isg = (w % 12) < 6;
+        for (int l = 0; l < np; ++l) {
+          const int k = W.slot[c][l];
+          if (k >= 0) {
+            const T b0 = W.lin[k][6 + u][l], b1 = W.lin[k][12 + u][l];
+            if (isg)
+              acc -= W.lin[k][18][l] * (b0 * W.lin[k][19][l] + b1 * W.lin[k][20][l]);
+            else
+              acc += b0 * W.U[k][0][l] + b1 * W.U[k][1][l];
+          }
+        }
+        if (isg)
+          W.g[6 * c + u] = acc + q.rho(3 + u) * (W.a[c][u] + W.d[c][u]);
+        else
+          W.rhs[6 * c + u] = acc;
       }
     }
     __syncwarp();
-    if (lane < n_u) W.S[lane][lane] += q.rho(3 + lane % 6) + lambda;
+    if (lane < n_u) {
+      W.rhs[lane] -= W.g[lane];
+      W.S[lane][lane] += q.rho(3 + lane % 6) + lambda;
+    }
     __syncwarp();
     // Cholesky S = L L^T, lane i owning row i
     bool spd = true;
     for (int k = 0; k < n_u; ++k) {
-      const T piv = __shfl_sync(0xffffffffu, W.S[k][k], 0);
+      const T piv = W.S[k][k];
       if (!(piv > T(0))) {
         spd = false;
         break;
       }
       const T lkk = Num<T>::sqrt_(piv);
+      if (lane > k && lane < n_u) W.S[lane][k] = Num<T>::div(W.S[lane][k], lkk);
       __syncwarp();
-      if (lane == 0) W.S[k][k] = lkk;
-      if (lane > k && lane < n_u) W.S[lane][k] = W.S[lane][k] / lkk;
-      __syncwarp();
+      if (lane == k) W.S[k][k] = lkk;
       if (lane > k && lane < n_u) {
         const T lik = W.S[lane][k];
         for (int jj = k + 1; jj <= lane; ++jj) W.S[lane][jj] -= lik * W.S[jj][k];
@@ -367,27 +406,26 @@ __device__ void solve_block(const BlockProblem& B, const Prm<T>& q, const BlockI
       lambda *= T(10);
       continue;
     }
-    // L y = rhs, then L^T dy = y
-    if (lane < n_u) W.dy[lane] = W.rhs[lane];
-    __syncwarp();
+    // L y = rhs, then L^T dy = y; lane i holds entry i
+    T y = lane < n_u ? W.rhs[lane] : T(0);
     for (int k = 0; k < n_u; ++k) {
-      if (lane == k) W.dy[k] = W.dy[k] / W.S[k][k];
-      __syncwarp();
-      if (lane > k && lane < n_u) W.dy[lane] -= W.S[lane][k] * W.dy[k];
-      __syncwarp();
+      const T yk = Num<T>::div(__shfl_sync(0xffffffffu, y, k), W.S[k][k]);
+      if (lane == k) y = yk;
+      else if (lane > k && lane < n_u) y -= W.S[lane][k] * yk;
     }
     for (int k = n_u - 1; k >= 0; --k) {
-      if (lane == k) W.dy[k] = W.dy[k] / W.S[k][k];
-      __syncwarp();
-      if (lane < k) W.dy[lane] -= W.S[k][lane] * W.dy[k];
-      __syncwarp();
+      const T xk = Num<T>::div(__shfl_sync(0xffffffffu, y, k), W.S[k][k]);
+      if (lane == k) y = xk;
+      else if (lane < k) y -= W.S[k][lane] * xk;
     }
+    if (lane < n_u) W.dy[lane] = y;
+    __syncwarp();
     // point step dx = -W_p (g_p + H_pc dy)
     T dx[3] = {0, 0, 0};
     if (act) {
       T t0 = gp[0], t1 = gp[1], t2 = gp[2];
 #pragma unroll
-      for (int k = 0; k < kBlkMaxCams; ++k) {
+      for (int k = 0; k < KC; ++k) {
         if (k < nob) {
           const int c = oc[k];
           T r0 = 0, r1 = 0;
@@ -424,7 +462,7 @@ __device__ void solve_block(const BlockProblem& B, const Prm<T>& q, const BlockI
     for (int u = 0; u < 3; ++u) xt[u] = dp[u] + dx[u];
     if (lane < n_u) W.dt[lane / 6][lane % 6] = W.d[lane / 6][lane % 6] + W.dy[lane];
     __syncwarp();
-    const T Lt = block_objective<T>(q, act, nob, oc, oz0, oz1, xbar, xt, ax, W, W.dt, nc);
+    const T Lt = block_objective<T, KC>(q, act, nob, oc, oz0, oz1, xbar, xt, ax, W, W.dt, nc);
     const bool valid = Lt < Num<T>::inf();
     if (valid && (trust || Lt < L)) {
 #pragma unroll
@@ -454,14 +492,14 @@ __device__ void solve_block(const BlockProblem& B, const Prm<T>& q, const BlockI
   __syncwarp();
 }
 
-template <typename T>
+template <typename T, int KC>
 __global__ void __launch_bounds__(kBlkWarps * 32) block_solve_kernel(BlockProblem B, Prm<T> q, int cur) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  BlkSmem<T>& W = reinterpret_cast<BlkSmem<T>*>(smem_raw)[warp];
+  BlkSmem<T, KC>& W = reinterpret_cast<BlkSmem<T, KC>*>(smem_raw)[warp];
   for (int b = blockIdx.x * kBlkWarps + warp; b < B.n_blocks; b += gridDim.x * kBlkWarps) {
     const BlockInfo bi = B.blocks[b];
-    solve_block<T>(B, q, bi, W, lane, cur);
+    solve_block<T, KC>(B, q, bi, W, lane, cur);
   }
 }
 
@@ -677,13 +715,13 @@ cudaError_t upload(dba_block_ctx* ctx, T** dst, const std::vector<T>& src) {
   return cudaMemcpyAsync(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice, ctx->stream);
 }
 
-template <typename T>
-cudaError_t launch_block_solve(dba_block_ctx* ctx) {
-  const size_t smem = sizeof(dba::BlkSmem<T>) * dba::kBlkWarps;
+template <typename T, int KC>
+cudaError_t launch_block_solve_kc(dba_block_ctx* ctx) {
+  const size_t smem = sizeof(dba::BlkSmem<T, KC>) * dba::kBlkWarps;
   static bool set = false;
   if (!set) {
-    cudaError_t e = cudaFuncSetAttribute(dba::block_solve_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(dba::block_solve_kernel<T, KC>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     set = true;
   }
@@ -691,7 +729,7 @@ cudaError_t launch_block_solve(dba_block_ctx* ctx) {
     // resident CTAs per SM from the resources one CTA takes (registers, shared memory)
     cudaFuncAttributes fa;
     int dev = 0, sms = 0, smem_sm = 0, smem_rsv = 0, regs_sm = 0;
-    cudaError_t e = cudaFuncGetAttributes(&fa, dba::block_solve_kernel<T>);
+    cudaError_t e = cudaFuncGetAttributes(&fa, dba::block_solve_kernel<T, KC>);
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
@@ -706,9 +744,16 @@ cudaError_t launch_block_solve(dba_block_ctx* ctx) {
   }
   const int need = dba::blocks_of(ctx->B.n_blocks, dba::kBlkWarps);
   const int g = std::max(1, std::min(need, ctx->grid));
-  dba::block_solve_kernel<T><<<g, dba::kBlkWarps * 32, smem, ctx->stream>>>(ctx->B, dba::make_prm<T>(ctx->prm),
-                                                                              ctx->cur);
+  dba::block_solve_kernel<T, KC><<<g, dba::kBlkWarps * 32, smem, ctx->stream>>>(
+      ctx->B, dba::make_prm<T>(ctx->prm), ctx->cur);
   return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_block_solve(dba_block_ctx* ctx) {
+  if (ctx->kappa == 1) return launch_block_solve_kc<T, 1>(ctx);
+  if (ctx->kappa == 2) return launch_block_solve_kc<T, 2>(ctx);
+  return launch_block_solve_kc<T, 4>(ctx);
 }
 
 // One iteration: block solves, consensus, dual ascent.  ev (nullable) receives an event
