@@ -30,7 +30,7 @@ class Config(ctypes.Structure):
         ("rho_x", ctypes.c_double), ("rho_y", ctypes.c_double), ("rho_angle", ctypes.c_double),
         ("inner_steps", ctypes.c_int), ("lm_lambda0", ctypes.c_double),
         ("lm_lambda_min", ctypes.c_double), ("eps_depth", ctypes.c_double),
-        ("lm_model_tol", ctypes.c_double),
+        ("lm_model_tol", ctypes.c_double), ("local_solver", ctypes.c_int),
     ]
 
 
@@ -83,6 +83,7 @@ def lib():
         L.ora_local_objective.argtypes = [cfgp, dp, dp, dp, dp, dp]
         L.ora_local_objective.restype = ctypes.c_double
         L.ora_local_solve.argtypes = [cfgp, dp, dp, dp, dp, dp]
+        L.ora_local_solve_lbfgs.argtypes = [cfgp, dp, dp, dp, dp, dp]
         L.ora_chol_solve.argtypes = [ctypes.c_int, dp, dp, dp]
         L.ora_chol_solve.restype = ctypes.c_int
         L.ora_admm_init.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_long, ip, ip, dp, dp, dp, dp]
@@ -130,11 +131,14 @@ def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
+SOLVER_GN, SOLVER_LBFGS = 0, 1
+
+
 def config(focal=500.0, cx=320.0, cy=240.0, loss=LOSS_HUBER, loss_param=2.0, rho_x=1.0, rho_y=1.0,
            rho_angle=0.0, inner_steps=5, lm_lambda0=1e-3, lm_lambda_min=1e-12, eps_depth=1e-6,
-           lm_model_tol=16.0) -> Config:
+           lm_model_tol=16.0, local_solver=SOLVER_GN) -> Config:
     return Config(focal, cx, cy, loss, loss_param, rho_x, rho_y, rho_angle, inner_steps, lm_lambda0,
-                  lm_lambda_min, eps_depth, lm_model_tol)
+                  lm_lambda_min, eps_depth, lm_model_tol, local_solver)
 
 
 def config_for(scene, **overrides) -> Config:
@@ -179,6 +183,13 @@ def local_solve(cfg, z, xbar, ybar, dual, v0):
     v = _f64(v0).copy()
     lib().ora_local_solve(ctypes.byref(cfg), _d(_f64(z)), _d(_f64(xbar)), _d(_f64(ybar)),
                           _d(_f64(dual)), _d(v))
+    return v
+
+
+def local_solve_lbfgs(cfg, z, xbar, ybar, dual, v0):
+    v = _f64(v0).copy()
+    lib().ora_local_solve_lbfgs(ctypes.byref(cfg), _d(_f64(z)), _d(_f64(xbar)), _d(_f64(ybar)),
+                                _d(_f64(dual)), _d(v))
     return v
 
 

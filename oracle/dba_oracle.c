@@ -298,6 +298,124 @@ void ora_local_solve(const ora_config* c, const double z[2], const double xbar[3
   }
 }
 
+/* Gradient of Eq. (9) at v: -2 w J^T e + dual + diag(rho) (v - vbar); a point behind the
+ * camera contributes no misfit term.  Also returns the noise scale 2 w |e| (|z1| + |z2|). */
+static void local_gradient(const ora_config* c, const double z[2], const double xbar[3],
+                           const double ybar[6], const double dual[9], const double v[9], double g[9],
+                           double* noise) {
+  double zp[2], J[18] = {0}, e[2] = {0.0, 0.0}, w = 0.0;
+  if (ora_project(c, v, v + 3, zp) > c->eps_depth) {
+    e[0] = z[0] - zp[0];
+    e[1] = z[1] - zp[1];
+    w = ora_weight(c->loss, c->loss_param, e[0] * e[0] + e[1] * e[1]);
+    ora_jacobian(c, v, v + 3, J);
+  }
+  for (int a = 0; a < 9; ++a) {
+    double vbar_a = a < 3 ? xbar[a] : ybar[a - 3];
+    g[a] = -2.0 * w * (J[a] * e[0] + J[9 + a] * e[1]) + dual[a] + rho_of(c, a) * (v[a] - vbar_a);
+  }
+  *noise = 2.0 * w * sqrt(e[0] * e[0] + e[1] * e[1]) * (fabs(z[0]) + fabs(z[1]));
+}
+
+/*
+ * L-BFGS (Nocedal and Wright, Numerical Optimization, Ch. 7) on Eq. (9) in the scaled
+ * coordinates u_a = sqrt(rho_a) (v_a - vbar_a), where the penalty has unit curvature:
+ *   p = -H g_u by the two-loop recursion over the last ORA_LBFGS_MEMORY pairs (s, y),
+ *       H0 = (s^T y / y^T y) I of the newest pair (I before the first);
+ *   step t = 1, 1/2, 1/4, ... until v + t p (unscaled) is in front of the camera and
+ *       L(trial) <= L + c1 t g_u.p, or the decrease -t g_u.p is below the objective's
+ *       rounding noise (the local solve's noise rule); no acceptable step ends the solve;
+ *   a pair is kept only when s^T y > 0.
+ */
+void ora_local_solve_lbfgs(const ora_config* c, const double z[2], const double xbar[3],
+                           const double ybar[6], const double dual[9], double v[9]) {
+  enum { M = ORA_LBFGS_MEMORY };
+  double r[9];
+  for (int a = 0; a < 9; ++a) r[a] = sqrt(rho_of(c, a));
+  double S[M][9], Y[M][9], rho_h[M];
+  int n_hist = 0, newest = -1;
+  double L = ora_local_objective(c, z, xbar, ybar, dual, v);
+  double g[9], gu[9], noise;
+  local_gradient(c, z, xbar, ybar, dual, v, g, &noise);
+  for (int a = 0; a < 9; ++a) gu[a] = g[a] / r[a];
+  for (int it = 0; it < c->inner_steps; ++it) {
+    /* two-loop recursion: q = g_u, newest to oldest, then H0, then oldest to newest */
+    double q[9], alpha[M];
+    for (int a = 0; a < 9; ++a) q[a] = gu[a];
+    for (int h = 0; h < n_hist; ++h) {
+      int k = (newest - h + M) % M;
+      double sq = 0.0;
+      for (int a = 0; a < 9; ++a) sq += S[k][a] * q[a];
+      alpha[k] = rho_h[k] * sq;
+      for (int a = 0; a < 9; ++a) q[a] -= alpha[k] * Y[k][a];
+    }
+    double gamma = 1.0;
+    if (n_hist > 0) {
+      double sy = 0.0, yy = 0.0;
+      for (int a = 0; a < 9; ++a) {
+        sy += S[newest][a] * Y[newest][a];
+        yy += Y[newest][a] * Y[newest][a];
+      }
+      gamma = sy / yy;
+    }
+    for (int a = 0; a < 9; ++a) q[a] *= gamma;
+    for (int h = n_hist - 1; h >= 0; --h) {
+      int k = (newest - h + M) % M;
+      double yq = 0.0;
+      for (int a = 0; a < 9; ++a) yq += Y[k][a] * q[a];
+      double beta = rho_h[k] * yq;
+      for (int a = 0; a < 9; ++a) q[a] += S[k][a] * (alpha[k] - beta);
+    }
+    double p[9], gp = 0.0;
+    for (int a = 0; a < 9; ++a) {
+      p[a] = -q[a];
+      gp += gu[a] * p[a];
+    }
+    if (!(gp < 0.0)) { /* not a descent direction: steepest descent */
+      gp = 0.0;
+      for (int a = 0; a < 9; ++a) {
+        p[a] = -gu[a];
+        gp -= gu[a] * gu[a];
+      }
+    }
+    /* backtracking line search */
+    double t = 1.0, vt[9], Lt = INFINITY;
+    int accepted = 0;
+    for (int hv = 0; hv <= ORA_LBFGS_HALVINGS; ++hv, t *= 0.5) {
+      for (int a = 0; a < 9; ++a) vt[a] = v[a] + t * p[a] / r[a];
+      Lt = ora_local_objective(c, z, xbar, ybar, dual, vt);
+      if (!isfinite(Lt)) continue;
+      int trust = isfinite(L) && c->lm_model_tol > 0.0 &&
+                  -t * gp <= c->lm_model_tol * 0x1p-53 * (fabs(L) + noise);
+      if (trust || Lt <= L + ORA_LBFGS_ARMIJO * t * gp) {
+        accepted = 1;
+        break;
+      }
+    }
+    if (!accepted) break;
+    double gt[9], gut[9], noise_t;
+    local_gradient(c, z, xbar, ybar, dual, vt, gt, &noise_t);
+    double sy = 0.0, sv[9], yv[9];
+    for (int a = 0; a < 9; ++a) {
+      gut[a] = gt[a] / r[a];
+      sv[a] = t * p[a];
+      yv[a] = gut[a] - gu[a];
+      sy += sv[a] * yv[a];
+    }
+    if (sy > 0.0) {
+      newest = (newest + 1) % M;
+      memcpy(S[newest], sv, sizeof sv);
+      memcpy(Y[newest], yv, sizeof yv);
+      rho_h[newest] = 1.0 / sy;
+      if (n_hist < M) n_hist += 1;
+    }
+    memcpy(v, vt, sizeof vt);
+    memcpy(gu, gut, sizeof gut);
+    L = Lt;
+    noise = noise_t;
+  }
+}
+
 /* ------------------------------------------- ADMM iteration, Eqs. (9)-(13) */
 
 void ora_admm_init(int n_cams, int n_pts, long n_obs, const int* pt_idx, const int* cam_idx,
@@ -345,8 +463,12 @@ int ora_admm_iterate(const ora_config* c, int n_cams, int n_pts, long n_obs, con
     /* Eq. (9): every observation's local subproblem, warm-started at its copy. */
 #pragma omp parallel for schedule(dynamic, 256)
     for (long o = 0; o < n_obs; ++o) {
-      ora_local_solve(c, z + 2 * o, pts + 3 * (long)pt_idx[o], cams + 6 * (long)cam_idx[o],
-                      duals + 9 * o, copies + 9 * o);
+      if (c->local_solver == ORA_SOLVER_LBFGS)
+        ora_local_solve_lbfgs(c, z + 2 * o, pts + 3 * (long)pt_idx[o], cams + 6 * (long)cam_idx[o],
+                              duals + 9 * o, copies + 9 * o);
+      else
+        ora_local_solve(c, z + 2 * o, pts + 3 * (long)pt_idx[o], cams + 6 * (long)cam_idx[o],
+                        duals + 9 * o, copies + 9 * o);
     }
 
     /* Eq. (10): x_i = mean over its copies of (x_i^j + r_i^j / rho_x), old duals. */

@@ -42,7 +42,12 @@ typedef struct {
   double lm_model_tol;  /* kappa: a step whose predicted decrease is <= kappa u (|L| + 2 w |e| (|z1|+|z2|)),
                            the rounding noise of the objective (u = 2^-53), is accepted without
                            the objective comparison; 0 disables */
+  int local_solver;     /* ORA_SOLVER_GN: damped Gauss-Newton; ORA_SOLVER_LBFGS: L-BFGS (Sec. 3.1) */
 } ora_config;
+
+enum { ORA_SOLVER_GN = 0, ORA_SOLVER_LBFGS = 1 };
+enum { ORA_LBFGS_MEMORY = 4, ORA_LBFGS_HALVINGS = 10 };
+#define ORA_LBFGS_ARMIJO 1e-4
 
 typedef struct {
   double rmse_obs;   /* sqrt(mean |z - f(x_i, y_j)|^2) at consensus */
@@ -69,6 +74,13 @@ double ora_local_objective(const ora_config* c, const double z[2], const double 
 /* Local solve of Eq. (9): inner_steps damped Gauss-Newton steps from v (in/out). */
 void ora_local_solve(const ora_config* c, const double z[2], const double xbar[3],
                      const double ybar[6], const double dual[9], double v[9]);
+
+/* Local solve of Eq. (9) by L-BFGS (Sec. 3.1 names it for the Huber loss): inner_steps
+ * iterations in the coordinates u = sqrt(rho) (v - vbar), memory ORA_LBFGS_MEMORY, two-loop
+ * recursion with H0 = (s^T y / y^T y) I (I before the first pair), backtracking Armijo line
+ * search from step 1 (constant ORA_LBFGS_ARMIJO, at most ORA_LBFGS_HALVINGS halvings).  v in/out. */
+void ora_local_solve_lbfgs(const ora_config* c, const double z[2], const double xbar[3],
+                           const double ybar[6], const double dual[9], double v[9]);
 
 /* Solves A x = b for symmetric positive definite A (n x n, row-major, copied). 0 on success. */
 int ora_chol_solve(int n, const double* A, const double* b, double* x);

@@ -361,3 +361,71 @@ def test_mlp_reference_relu_and_its_derivative():
     z = np.array([-3.0, -1e-300, 0.0, 1e-300, 0.7, 2.5])
     assert np.array_equal(OM.relu(z), [0.0, 0.0, 0.0, 1e-300, 0.7, 2.5])
     assert np.array_equal(OM.relu_grad(z), [0.0, 0.0, 0.0, 1.0, 1.0, 1.0])
+
+
+# --------------------------------------------- L-BFGS local solver (Sec. 3.1)
+@pytest.mark.parametrize("kind", [O.LOSS_HUBER, O.LOSS_L2])
+def test_lbfgs_local_solve_reaches_the_argmin(kind):
+    """Many L-BFGS iterations end at a stationary point of Eq. (9) (central differences of
+    the objective, no Jacobian code), the minimiser a long Gauss-Newton run and an
+    independent quasi-Newton routine also find."""
+    scipy_opt = pytest.importorskip("scipy.optimize")
+    s, cfg, z, xbar, ybar, dual, _ = _local_case(5, kind)
+    cfg.inner_steps = 300
+    v0 = np.r_[xbar, ybar]
+    v = O.local_solve_lbfgs(cfg, z, xbar, ybar, dual, v0)
+    f = lambda u: O.local_objective(cfg, z, xbar, ybar, dual, u)
+    g = np.zeros(9)
+    for k in range(9):
+        h = 1e-7 * max(1.0, abs(v[k]))
+        vp, vm = v.copy(), v.copy()
+        vp[k] += h
+        vm[k] -= h
+        g[k] = (f(vp) - f(vm)) / (2 * h)
+    g0 = np.zeros(9)
+    for k in range(9):
+        h = 1e-7 * max(1.0, abs(v0[k]))
+        vp, vm = v0.copy(), v0.copy()
+        vp[k] += h
+        vm[k] -= h
+        g0[k] = (f(vp) - f(vm)) / (2 * h)
+    assert np.linalg.norm(g) <= 1e-5 * np.linalg.norm(g0)
+    gn = O.local_solve(cfg, z, xbar, ybar, dual, v0)
+    assert np.abs(v - gn).max() <= 1e-6 * np.abs(gn).max()
+    res = scipy_opt.minimize(f, v0, method="BFGS", options={"gtol": 1e-10, "maxiter": 20000})
+    assert f(v) <= res.fun + 1e-9 * abs(res.fun)
+
+
+def test_lbfgs_never_increases_the_local_objective():
+    """Every accepted step satisfies the Armijo condition (or sits at rounding noise), so
+    the objective after k iterations is non-increasing in k."""
+    for seed in range(6):
+        s, cfg, z, xbar, ybar, dual, _ = _local_case(seed, O.LOSS_HUBER)
+        v0 = np.r_[xbar, ybar]
+        prev = O.local_objective(cfg, z, xbar, ybar, dual, v0)
+        for k in range(1, 12):
+            cfg.inner_steps = k
+            v = O.local_solve_lbfgs(cfg, z, xbar, ybar, dual, v0)
+            cur = O.local_objective(cfg, z, xbar, ybar, dual, v)
+            assert cur <= prev + 1e-12 * abs(prev)
+            prev = cur
+
+
+def test_lbfgs_and_gauss_newton_admm_share_the_fixed_point():
+    """Both local solvers stop moving only at a stationary point of Eq. (9), so the two ADMM
+    runs converge to the same limit (compared on gauge-free projections)."""
+    sc = S.scene0(n_pts=40, n_cams=6, seed=8)
+    runs = {}
+    for solver in (O.SOLVER_GN, O.SOLVER_LBFGS):
+        cfg = O.config_for(sc, local_solver=solver)
+        st = O.State(sc)
+        m = st.iterate(cfg, 1600)
+        runs[solver] = (st, m)
+    a, b = runs[O.SOLVER_GN][0], runs[O.SOLVER_LBFGS][0]
+    assert abs(runs[0][1]["objective"] - runs[1][1]["objective"]) <= 1e-8 * runs[0][1]["objective"]
+    cfg = O.config_for(sc)
+    for o in range(0, sc.n_obs, 7):
+        i, j = sc.pt_idx[o], sc.cam_idx[o]
+        za, _ = O.project(cfg, a.pts[i], a.cams[j])
+        zb, _ = O.project(cfg, b.pts[i], b.cams[j])
+        assert np.abs(za - zb).max() <= 1e-5
