@@ -83,7 +83,16 @@ typedef struct {
                              (cached per process by precision, size and mean track length) */
   int use_graph;          /* 1: replay each iteration as a CUDA graph; 0: plain launches */
   void* cuda_stream;      /* cudaStream_t to launch on; NULL = a stream owned by the context */
+  int local_solver;       /* dba_local_solver: how each local subproblem (Eq. 9) is solved */
 } dba_config;
+
+typedef enum {
+  DBA_SOLVER_GN = 0,      /* inner_steps damped Gauss-Newton steps (the paper's choice for l2) */
+  DBA_SOLVER_LBFGS = 1    /* inner_steps L-BFGS iterations (the paper's choice for Huber, Sec. 3.1):
+                             coordinates scaled by sqrt(rho), memory 4, two-loop recursion with
+                             H0 = (s.y / y.y) I, backtracking Armijo line search (c1 = 1e-4, at
+                             most 10 halvings) from step 1, the same rounding-noise acceptance */
+} dba_local_solver;
 
 typedef struct {
   long long iters_done;   /* ADMM iterations run on this context since the state was set */
@@ -99,7 +108,7 @@ typedef struct {
 /* Fills *cfg with defaults: focal 500, principal point (320, 240), Huber 2 px,
  * rho 1 (angles: rho_y), 5 inner steps, lambda0 1e-3, lambda_min 1e-12, eps_depth 1e-6,
  * lm_model_tol 16,
- * FP32 local solves, automatic tile size, graphs on, own stream. */
+ * FP32 local solves, automatic tile size, graphs on, own stream, Gauss-Newton local solver. */
 void dba_config_default(dba_config* cfg);
 
 /* Creates a context on the current CUDA device.  Validates *cfg (EINVAL).
@@ -280,8 +289,8 @@ typedef struct dba_block_ctx dba_block_ctx;
 #define DBA_BLOCK_MAX_POINTS 32
 #define DBA_BLOCK_MAX_CAMERAS 4
 
-/* Validates cfg as dba_create does (tile_obs, use_graph are ignored) and
- * 1 <= block_points <= 32, 1 <= block_cams <= 4 (EINVAL). */
+/* Validates cfg as dba_create does (tile_obs, use_graph are ignored; local_solver
+ * must be DBA_SOLVER_GN) and 1 <= block_points <= 32, 1 <= block_cams <= 4 (EINVAL). */
 dba_status dba_block_create(const dba_config* cfg, int block_points, int block_cams, dba_block_ctx** out);
 /* Same arrays and checks as dba_set_observations, and a (point, camera) pair
  * may appear once (EINVAL); builds the blocks and starts with copies at the

@@ -279,6 +279,7 @@ void dba_config_default(dba_config* cfg) {
   cfg->tile_obs = 0;
   cfg->use_graph = 1;
   cfg->cuda_stream = nullptr;
+  cfg->local_solver = DBA_SOLVER_GN;
 }
 
 dba_status dba_create(const dba_config* cfg, dba_ctx** out) {
@@ -297,9 +298,11 @@ dba_status dba_create(const dba_config* cfg, dba_ctx** out) {
                   std::isfinite(cfg->eps_depth) && std::isfinite(cfg->lm_model_tol) &&
                   cfg->lm_model_tol >= 0 && (cfg->precision == 0 || cfg->precision == 1) &&
                   (cfg->tile_obs == 0 || cfg->tile_obs == -1 || cfg->tile_obs == 64 ||
-                   cfg->tile_obs == 128 || cfg->tile_obs == 256);
+                   cfg->tile_obs == 128 || cfg->tile_obs == 256) &&
+                  (cfg->local_solver == DBA_SOLVER_GN || cfg->local_solver == DBA_SOLVER_LBFGS);
   if (!ok) {
-    g_create_error = "dba_create: invalid configuration (check focal, loss, rho, steps, precision, tile_obs)";
+    g_create_error =
+        "dba_create: invalid configuration (check focal, loss, rho, steps, precision, tile_obs, local_solver)";
     return DBA_EINVAL;
   }
   cudaError_t e = cudaFree(nullptr);  // initialise the runtime on the current device
@@ -318,7 +321,7 @@ dba_status dba_create(const dba_config* cfg, dba_ctx** out) {
   ctx->prm = Params{cfg->focal, cfg->cx, cfg->cy, cfg->loss, cfg->loss_param, cfg->rho_x, cfg->rho_y,
                     cfg->rho_angle > 0 ? cfg->rho_angle : cfg->rho_y,
                     cfg->inner_steps, cfg->lm_lambda0, cfg->lm_lambda_min, cfg->eps_depth,
-                    cfg->lm_model_tol};
+                    cfg->lm_model_tol, cfg->local_solver};
   if (cfg->cuda_stream) {
     ctx->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
   } else {

@@ -830,7 +830,8 @@ dba_status dba_block_create(const dba_config* cfg, int block_points, int block_c
                   std::isfinite(cfg->rho_angle) && cfg->inner_steps >= 0 && cfg->inner_steps <= 1000 &&
                   std::isfinite(cfg->lm_lambda0) && cfg->lm_lambda0 > 0 && std::isfinite(cfg->lm_lambda_min) &&
                   cfg->lm_lambda_min >= 0 && std::isfinite(cfg->eps_depth) && std::isfinite(cfg->lm_model_tol) &&
-                  cfg->lm_model_tol >= 0 && (cfg->precision == 0 || cfg->precision == 1);
+                  cfg->lm_model_tol >= 0 && (cfg->precision == 0 || cfg->precision == 1) &&
+                  cfg->local_solver == DBA_SOLVER_GN;
   if (!ok) {
     g_block_error = "dba_block_create: invalid configuration";
     return DBA_EINVAL;
@@ -856,7 +857,7 @@ dba_status dba_block_create(const dba_config* cfg, int block_points, int block_c
   ctx->kappa = block_cams;
   ctx->prm = dba::Params{cfg->focal, cfg->cx, cfg->cy, cfg->loss, cfg->loss_param, cfg->rho_x, cfg->rho_y,
                          cfg->rho_angle > 0 ? cfg->rho_angle : cfg->rho_y, cfg->inner_steps, cfg->lm_lambda0,
-                         cfg->lm_lambda_min, cfg->eps_depth, cfg->lm_model_tol};
+                         cfg->lm_lambda_min, cfg->eps_depth, cfg->lm_model_tol, DBA_SOLVER_GN};
   if (cfg->cuda_stream) {
     ctx->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
   } else {

@@ -94,7 +94,7 @@ template <> __device__ __forceinline__ double from_f64<double>(double v) { retur
 template <typename T>
 struct Prm {
   T focal, cx, cy, lp, rho_x, rho_y, rho_a, lambda0, lambda_min, eps, model_tol;
-  int loss, steps;
+  int loss, steps, solver;
   // penalty of coordinate c of (x, alpha, beta, gamma, t)
   __device__ __forceinline__ T rho(int c) const { return c < 3 ? rho_x : (c < 6 ? rho_a : rho_y); }
 };
@@ -105,7 +105,7 @@ __host__ __device__ Prm<T> make_prm(const Params& p) {
   q.focal = (T)p.focal; q.cx = (T)p.cx; q.cy = (T)p.cy; q.lp = (T)p.loss_param;
   q.rho_x = (T)p.rho_x; q.rho_y = (T)p.rho_y; q.rho_a = (T)p.rho_a; q.lambda0 = (T)p.lambda0;
   q.lambda_min = (T)p.lambda_min; q.eps = (T)p.eps_depth; q.model_tol = (T)p.model_tol;
-  q.loss = p.loss; q.steps = p.inner_steps;
+  q.loss = p.loss; q.steps = p.inner_steps; q.solver = p.solver;
   return q;
 }
 
@@ -343,6 +343,169 @@ __device__ __forceinline__ void local_solve(T z0, T z1, const T vbar[9], const T
     } else {
       lambda *= T(10);
     }
+  }
+}
+
+// Gradient of Eq. (9) in offset form at pose P (v = vbar + d): -2 w J^T e + rho (a + d), no
+// misfit term behind the camera; noise = 2 w |e| (|z1| + |z2|), the objective's rounding scale.
+template <typename T>
+__device__ __forceinline__ void local_gradient(const Pose<T>& P, T z0, T z1, const T a[9], const T d[9],
+                                               const Prm<T>& q, T g[9], T& noise) {
+  T J0[9], J1[9], e0 = 0, e1 = 0, w = 0;
+  if (P.valid) {
+    linearize(P, z0, z1, q, J0, J1, e0, e1, w);
+  } else {
+#pragma unroll
+    for (int c = 0; c < 9; ++c) J0[c] = J1[c] = 0;
+  }
+  const T tw = T(2) * w;
+#pragma unroll
+  for (int c = 0; c < 9; ++c) g[c] = -tw * (J0[c] * e0 + J1[c] * e1) + q.rho(c) * (a[c] + d[c]);
+  noise = tw * Num<T>::sqrt_(e0 * e0 + e1 * e1) * (fabs(z0) + fabs(z1));
+}
+
+constexpr int kLbfgsMemory = 4;
+constexpr int kLbfgsHalvings = 10;
+
+// Eq. (9) by L-BFGS (Sec. 3.1 names it for the Huber loss; Nocedal and Wright, Ch. 7):
+// inner_steps iterations in the coordinates u = r d, r_c = sqrt(rho_c), where the penalty has
+// unit curvature.  Direction -H g_u by the two-loop recursion over the last kLbfgsMemory
+// pairs, H0 = (s.y / y.y) I (I before the first pair); backtracking Armijo line search from
+// step 1 (c1 = 1e-4, at most kLbfgsHalvings halvings), accepting without the comparison a
+// decrease below the objective's rounding noise; a pair is kept when s.y > 0; a failed line
+// search ends the solve.  With kAlt, starts from the better of d and alt.  d in place.
+template <typename T, bool kAlt = false>
+__device__ __forceinline__ void local_solve_lbfgs(T z0, T z1, const T vbar[9], const T a[9], T d[9],
+                                                  const Prm<T>& q, const T* alt = nullptr) {
+  constexpr int M = kLbfgsMemory;
+  T r[9];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) r[c] = Num<T>::sqrt_(q.rho(c));
+  T v[9];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) v[c] = vbar[c] + d[c];
+  Pose<T> P;
+  pose_at(v, q.eps, P);
+  T L = local_objective(d, a, P, z0, z1, q);
+  if constexpr (kAlt) {
+    T da[9], va[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      da[c] = alt[c];
+      va[c] = vbar[c] + da[c];
+    }
+    Pose<T> Pa;
+    pose_at(va, q.eps, Pa);
+    const T La = local_objective(da, a, Pa, z0, z1, q);
+    if (La < L) {
+#pragma unroll
+      for (int c = 0; c < 9; ++c) d[c] = da[c];
+      P = Pa;
+      L = La;
+    }
+  }
+  T gu[9], noise;
+  {
+    T g[9];
+    local_gradient(P, z0, z1, a, d, q, g, noise);
+#pragma unroll
+    for (int c = 0; c < 9; ++c) gu[c] = Num<T>::div(g[c], r[c]);
+  }
+  T S[M][9], Y[M][9], rh[M];
+  int nh = 0, newest = -1;
+  for (int it = 0; it < q.steps; ++it) {
+    T qv[9], al[M];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) qv[c] = gu[c];
+    for (int h = 0; h < nh; ++h) {
+      const int k = (newest - h + M) % M;
+      T sq = 0;
+#pragma unroll
+      for (int c = 0; c < 9; ++c) sq += S[k][c] * qv[c];
+      al[k] = rh[k] * sq;
+#pragma unroll
+      for (int c = 0; c < 9; ++c) qv[c] -= al[k] * Y[k][c];
+    }
+    T gamma = 1;
+    if (nh > 0) {
+      T sy = 0, yy = 0;
+#pragma unroll
+      for (int c = 0; c < 9; ++c) {
+        sy += S[newest][c] * Y[newest][c];
+        yy += Y[newest][c] * Y[newest][c];
+      }
+      gamma = Num<T>::div(sy, yy);
+    }
+#pragma unroll
+    for (int c = 0; c < 9; ++c) qv[c] *= gamma;
+    for (int h = nh - 1; h >= 0; --h) {
+      const int k = (newest - h + M) % M;
+      T yq = 0;
+#pragma unroll
+      for (int c = 0; c < 9; ++c) yq += Y[k][c] * qv[c];
+      const T beta = rh[k] * yq;
+#pragma unroll
+      for (int c = 0; c < 9; ++c) qv[c] += S[k][c] * (al[k] - beta);
+    }
+    T p[9], gp = 0;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      p[c] = -qv[c];
+      gp += gu[c] * p[c];
+    }
+    if (!(gp < T(0))) {  // not a descent direction: steepest descent
+      gp = 0;
+#pragma unroll
+      for (int c = 0; c < 9; ++c) {
+        p[c] = -gu[c];
+        gp -= gu[c] * gu[c];
+      }
+    }
+    T t = 1, dt[9], Lt = Num<T>::inf();
+    Pose<T> Pt;
+    bool accepted = false;
+    for (int hv = 0; hv <= kLbfgsHalvings; ++hv, t *= T(0.5)) {
+      T vt[9];
+#pragma unroll
+      for (int c = 0; c < 9; ++c) {
+        dt[c] = d[c] + Num<T>::div(t * p[c], r[c]);
+        vt[c] = vbar[c] + dt[c];
+      }
+      pose_at(vt, q.eps, Pt);
+      Lt = local_objective(dt, a, Pt, z0, z1, q);
+      if (!(Lt < Num<T>::inf())) continue;
+      const bool trust = isfinite(L) && q.model_tol > T(0) &&
+                         -t * gp <= q.model_tol * Num<T>::unit_roundoff * (fabs(L) + noise);
+      if (trust || Lt <= L + T(1e-4) * t * gp) {
+        accepted = true;
+        break;
+      }
+    }
+    if (!accepted) break;
+    T gt[9], noise_t, sv[9], yv[9], sy = 0;
+    local_gradient(Pt, z0, z1, a, dt, q, gt, noise_t);
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      const T gut = Num<T>::div(gt[c], r[c]);
+      sv[c] = t * p[c];
+      yv[c] = gut - gu[c];
+      sy += sv[c] * yv[c];
+      gu[c] = gut;
+    }
+    if (sy > T(0)) {
+      newest = (newest + 1) % M;
+#pragma unroll
+      for (int c = 0; c < 9; ++c) {
+        S[newest][c] = sv[c];
+        Y[newest][c] = yv[c];
+      }
+      rh[newest] = Num<T>::rcp(sy);
+      if (nh < M) nh += 1;
+    }
+#pragma unroll
+    for (int c = 0; c < 9; ++c) d[c] = dt[c];
+    L = Lt;
+    noise = noise_t;
   }
 }
 

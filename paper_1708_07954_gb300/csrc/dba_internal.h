@@ -34,6 +34,7 @@ struct Params {
   double rho_x, rho_y, rho_a;  // points, camera translations, camera angles
   int inner_steps;
   double lambda0, lambda_min, eps_depth, model_tol;
+  int solver;  // dba_local_solver
 };
 
 // All device pointers of one problem.  Observation arrays are in internal

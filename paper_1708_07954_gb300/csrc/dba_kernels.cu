@@ -115,7 +115,7 @@ __device__ __forceinline__ void stage_tile(const DevProblem& P, TileStage<T, NT>
 }
 
 // One tile from its staged inputs: deferred dual ascent, local solves, run sums.
-template <typename T, int NT>
+template <typename T, int NT, int kS>
 __device__ __forceinline__ void process_tile(const DevProblem& P, const Prm<T>& q, const TileStage<T, NT>& S,
                                              double (*s_buf)[NT], const TileInfo& ti, int cur, int pending,
                                              int exact) {
@@ -164,9 +164,15 @@ __device__ __forceinline__ void process_tile(const DevProblem& P, const Prm<T>& 
       T alt[9];
 #pragma unroll
       for (int c = 0; c < 9; ++c) alt[c] = ms[c * l + o];
-      local_solve<T, true>(zz.x, zz.y, vbar, aT, d, q, alt);
+      if constexpr (kS == DBA_SOLVER_LBFGS)
+        local_solve_lbfgs<T, true>(zz.x, zz.y, vbar, aT, d, q, alt);
+      else
+        local_solve<T, true>(zz.x, zz.y, vbar, aT, d, q, alt);
     } else {
-      local_solve<T>(zz.x, zz.y, vbar, aT, d, q);
+      if constexpr (kS == DBA_SOLVER_LBFGS)
+        local_solve_lbfgs<T>(zz.x, zz.y, vbar, aT, d, q);
+      else
+        local_solve<T>(zz.x, zz.y, vbar, aT, d, q);
     }
     bool finite = true;
 #pragma unroll
@@ -234,7 +240,7 @@ __device__ __forceinline__ void process_tile(const DevProblem& P, const Prm<T>& 
   }
 }
 
-template <typename T, int NT>
+template <typename T, int NT, int kS>
 __global__ void __launch_bounds__(NT, 2) tile_iterate_kernel(DevProblem P, Prm<T> q) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   TileStage<T, NT>* stage = reinterpret_cast<TileStage<T, NT>*>(smem_raw);
@@ -260,7 +266,7 @@ __global__ void __launch_bounds__(NT, 2) tile_iterate_kernel(DevProblem P, Prm<T
     if (after < P.n_tiles) info_after = load_tile_info(P.tiles, after);  // used two tiles later
     cp_async_wait<1>();    // this thread's copies of the current tile have landed
     __syncthreads();       // ... and everyone else's
-    process_tile<T, NT>(P, q, stage[k & 1], s_buf, info, cur, pending, exact);
+    process_tile<T, NT, kS>(P, q, stage[k & 1], s_buf, info, cur, pending, exact);
     __syncthreads();       // stage and run buffers are free for reuse
     tile = next;
     next = after;
@@ -584,15 +590,16 @@ int grid_for(long long n, int threads, int cap) {
 namespace {
 // Persistent grid of the pipelined tile kernel: resident blocks per SM times SMs, set up
 // once per instantiation (dynamic shared memory opt-in, occupancy query).
-template <typename T, int NT>
+template <typename T, int NT, int kS>
 cudaError_t tile_grid(int* grid) {
   static int cached = 0;
   if (!cached) {
     const int smem = (int)tile_smem_bytes<T, NT>();
-    cudaError_t e = cudaFuncSetAttribute(tile_iterate_kernel<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(tile_iterate_kernel<T, NT, kS>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0, dev = 0, sms = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tile_iterate_kernel<T, NT>, NT, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tile_iterate_kernel<T, NT, kS>, NT, smem);
     if (e != cudaSuccess) return e;
     e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -604,44 +611,51 @@ cudaError_t tile_grid(int* grid) {
   return cudaSuccess;
 }
 
-template <typename T, int NT>
+template <typename T, int NT, int kS>
 cudaError_t launch_tile(const DevProblem& P, const Params& prm, cudaStream_t s) {
   int grid = 0;
-  const cudaError_t e = tile_grid<T, NT>(&grid);
+  const cudaError_t e = tile_grid<T, NT, kS>(&grid);
   if (e != cudaSuccess) return e;
   if (grid > P.n_tiles) grid = P.n_tiles;
-  tile_iterate_kernel<T, NT><<<grid, NT, tile_smem_bytes<T, NT>(), s>>>(P, make_prm<T>(prm));
+  tile_iterate_kernel<T, NT, kS><<<grid, NT, tile_smem_bytes<T, NT>(), s>>>(P, make_prm<T>(prm));
   return cudaGetLastError();
+}
+
+template <typename T, int kS>
+cudaError_t launch_tile_sized(const DevProblem& P, const Params& prm, cudaStream_t s) {
+  switch (P.tile_obs) {
+    case 256: return launch_tile<T, 256, kS>(P, prm, s);
+    case 128: return launch_tile<T, 128, kS>(P, prm, s);
+    case 64: return launch_tile<T, 64, kS>(P, prm, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 }  // namespace
 
 cudaError_t prepare_tile_kernels() {
   int g = 0;
   cudaError_t e;
-  if ((e = tile_grid<float, 256>(&g)) != cudaSuccess) return e;
-  if ((e = tile_grid<float, 128>(&g)) != cudaSuccess) return e;
-  if ((e = tile_grid<float, 64>(&g)) != cudaSuccess) return e;
-  if ((e = tile_grid<double, 256>(&g)) != cudaSuccess) return e;
-  if ((e = tile_grid<double, 128>(&g)) != cudaSuccess) return e;
-  return tile_grid<double, 64>(&g);
+  if ((e = tile_grid<float, 256, DBA_SOLVER_GN>(&g)) != cudaSuccess) return e;
+  if ((e = tile_grid<float, 128, DBA_SOLVER_GN>(&g)) != cudaSuccess) return e;
+  if ((e = tile_grid<float, 64, DBA_SOLVER_GN>(&g)) != cudaSuccess) return e;
+  if ((e = tile_grid<double, 256, DBA_SOLVER_GN>(&g)) != cudaSuccess) return e;
+  if ((e = tile_grid<double, 128, DBA_SOLVER_GN>(&g)) != cudaSuccess) return e;
+  if ((e = tile_grid<double, 64, DBA_SOLVER_GN>(&g)) != cudaSuccess) return e;
+  if ((e = tile_grid<float, 256, DBA_SOLVER_LBFGS>(&g)) != cudaSuccess) return e;
+  if ((e = tile_grid<float, 128, DBA_SOLVER_LBFGS>(&g)) != cudaSuccess) return e;
+  if ((e = tile_grid<float, 64, DBA_SOLVER_LBFGS>(&g)) != cudaSuccess) return e;
+  if ((e = tile_grid<double, 256, DBA_SOLVER_LBFGS>(&g)) != cudaSuccess) return e;
+  if ((e = tile_grid<double, 128, DBA_SOLVER_LBFGS>(&g)) != cudaSuccess) return e;
+  return tile_grid<double, 64, DBA_SOLVER_LBFGS>(&g);
 }
 
 cudaError_t launch_tile_iterate(const DevProblem& P, const Params& prm, bool fp32, cudaStream_t s) {
   if (P.n_tiles == 0) return cudaSuccess;
-  if (fp32) {
-    switch (P.tile_obs) {
-      case 256: return launch_tile<float, 256>(P, prm, s);
-      case 128: return launch_tile<float, 128>(P, prm, s);
-      case 64: return launch_tile<float, 64>(P, prm, s);
-      default: return cudaErrorInvalidValue;
-    }
-  }
-  switch (P.tile_obs) {
-    case 256: return launch_tile<double, 256>(P, prm, s);
-    case 128: return launch_tile<double, 128>(P, prm, s);
-    case 64: return launch_tile<double, 64>(P, prm, s);
-    default: return cudaErrorInvalidValue;
-  }
+  if (prm.solver == DBA_SOLVER_LBFGS)
+    return fp32 ? launch_tile_sized<float, DBA_SOLVER_LBFGS>(P, prm, s)
+                : launch_tile_sized<double, DBA_SOLVER_LBFGS>(P, prm, s);
+  return fp32 ? launch_tile_sized<float, DBA_SOLVER_GN>(P, prm, s)
+              : launch_tile_sized<double, DBA_SOLVER_GN>(P, prm, s);
 }
 
 cudaError_t launch_finalize(const DevProblem& P, bool fp32, cudaStream_t s) {

@@ -18,6 +18,7 @@ from . import build as _build
 DBA_OK, DBA_EINVAL, DBA_ENOMEM, DBA_ECUDA, DBA_ESTATE, DBA_ENUMERIC, DBA_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
 DBA_LOSS_L2, DBA_LOSS_HUBER, DBA_LOSS_STUDENT_T = 0, 1, 2
 DBA_PREC_F64, DBA_PREC_F32_LOCAL = 0, 1
+DBA_SOLVER_GN, DBA_SOLVER_LBFGS = 0, 1
 
 EXPORTED = [
     "dba_config_default", "dba_create", "dba_set_observations", "dba_set_ground_truth", "dba_iterate",
@@ -50,7 +51,7 @@ class dba_config(ctypes.Structure):
         ("inner_steps", ctypes.c_int), ("lm_lambda0", ctypes.c_double),
         ("lm_lambda_min", ctypes.c_double), ("eps_depth", ctypes.c_double),
         ("lm_model_tol", ctypes.c_double), ("precision", ctypes.c_int), ("tile_obs", ctypes.c_int), ("use_graph", ctypes.c_int),
-        ("cuda_stream", ctypes.c_void_p),
+        ("cuda_stream", ctypes.c_void_p), ("local_solver", ctypes.c_int),
     ]
 
 

@@ -3,6 +3,7 @@
     python -m paper_1708_07954_gb300.experiments blocks   # Sec. 4: points / cameras per update step
     python -m paper_1708_07954_gb300.experiments loss     # Sec. 4.1: squared vs Huber misfit
     python -m paper_1708_07954_gb300.experiments rho      # Sec. 4: the consensus penalty
+    python -m paper_1708_07954_gb300.experiments solver   # Sec. 3.1: Gauss-Newton vs L-BFGS local solves
 
 Each line printed is one JSON record.  Everything runs through the library's
 public API (dba.Solver, dba.BlockSolver); the datasets of the paper are not
@@ -93,15 +94,32 @@ def rho_sweep(n_pts=100000, factors=(0.25, 0.5, 1.0, 2.0, 4.0), iters=(10, 50, 2
                "iters_to_target": m["iters_done"] if m["rmse_gt"] <= target else None, "target_px": target})
 
 
+def solver_comparison(n_pts=500000, steps=(1, 2, 5, 10), target=0.5, max_iters=400, profile_iters=10):
+    """Local solver of Eq. (9) (Sec. 3.1: Gauss-Newton for l2, L-BFGS for Huber), Huber
+    workload 2: device time per iteration and iterations / device time to the target for
+    1-10 inner iterations of each."""
+    sc = S.scene2(n_pts=n_pts)
+    for name, solver in (("gauss-newton", dba.DBA_SOLVER_GN), ("l-bfgs", dba.DBA_SOLVER_LBFGS)):
+        for k in steps:
+            with dba.Solver(sc, inner_steps=k, local_solver=solver) as s:
+                prof = s.profile(profile_iters)
+            with dba.Solver(sc, inner_steps=k, local_solver=solver) as s:
+                m = s.iterate_until(max_iters, target)
+            _emit({"experiment": "solver", "workload": sc.name, "solver": name, "inner_steps": k,
+                   "ms_per_iter": sum(prof.values()), "kernels_ms": prof, "iters": m["iters_done"],
+                   "seconds": m["seconds"], "rmse_gt": m["rmse_gt"], "reached": m["rmse_gt"] <= target})
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    ap.add_argument("which", choices=["blocks", "loss", "rho"])
+    ap.add_argument("which", choices=["blocks", "loss", "rho", "solver"])
     ap.add_argument("--n-pts", type=int, default=None)
     args = ap.parse_args(argv)
     build.build()
     dba.load()
     kw = {} if args.n_pts is None else {"n_pts": args.n_pts}
-    {"blocks": block_sweep, "loss": loss_comparison, "rho": rho_sweep}[args.which](**kw)
+    {"blocks": block_sweep, "loss": loss_comparison, "rho": rho_sweep,
+     "solver": solver_comparison}[args.which](**kw)
     return 0
 
 

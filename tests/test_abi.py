@@ -47,7 +47,7 @@ def test_config_defaults(lib):
 
 @pytest.mark.parametrize("field,value", [("focal", -1.0), ("rho_x", 0.0), ("rho_y", float("nan")),
                                          ("loss", 7), ("inner_steps", -1), ("precision", 3),
-                                         ("tile_obs", 100), ("loss_param", 0.0)])
+                                         ("tile_obs", 100), ("loss_param", 0.0), ("local_solver", 2)])
 def test_invalid_config_is_rejected_before_any_device_work(lib, field, value):
     cfg = dba.dba_config_default(**{field: value})
     with pytest.raises(dba.DbaError) as ei:
@@ -77,3 +77,9 @@ def test_block_null_arguments(lib):
     assert lib.dba_block_iterate(None, 1, None) == dba.DBA_EINVAL
     assert lib.dba_block_get_params(None, None, None) == dba.DBA_EINVAL
     lib.dba_block_destroy(None)
+
+
+def test_block_path_takes_only_the_gauss_newton_solver(lib):
+    cfg = dba.dba_config_default(local_solver=dba.DBA_SOLVER_LBFGS)
+    ctx = ctypes.c_void_p()
+    assert lib.dba_block_create(ctypes.byref(cfg), 8, 2, ctypes.byref(ctx)) == dba.DBA_EINVAL

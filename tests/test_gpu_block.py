@@ -21,7 +21,8 @@ def oracle_cfg(solver):
     c = solver.cfg
     return O.config(focal=c.focal, cx=c.cx, cy=c.cy, loss=c.loss, loss_param=c.loss_param, rho_x=c.rho_x,
                     rho_y=c.rho_y, rho_angle=c.rho_angle, inner_steps=c.inner_steps, lm_lambda0=c.lm_lambda0,
-                    lm_lambda_min=c.lm_lambda_min, eps_depth=c.eps_depth, lm_model_tol=c.lm_model_tol)
+                    lm_lambda_min=c.lm_lambda_min, eps_depth=c.eps_depth, lm_model_tol=c.lm_model_tol,
+                    local_solver=c.local_solver)
 
 
 def relerr(a, b):
