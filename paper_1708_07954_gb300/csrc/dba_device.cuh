@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
+#include <type_traits>
+
 #include "dba_internal.h"
 
 namespace dba {
@@ -230,6 +232,80 @@ __device__ __forceinline__ void linearize(const Pose<T>& P, T z0, T z1, const Pr
   J1[8] = -fi * zy;
 }
 
+__device__ __forceinline__ float2 f2(float x, float y) { return make_float2(x, y); }
+
+// One Gauss-Newton step's linear algebra in FP32 on pairs of adjacent components
+// (packed FP32x2 multiply/add/FMA of the sm_100 family; component 8 alone): gradient
+// g = -2w J^T e + rho (a + d), the first damping from the trace of H, the step
+// s = -D^-1 g + 2w D^-1 J^T y with D = diag(rho) + lambda I and the 2x2 capacitance
+// solve for y, and the model decrease (lambda |s|^2 - g.s) / 2.  Same formulas as the
+// scalar path, summed in two lanes.
+__device__ __forceinline__ void gn_step_f32(const float J0[9], const float J1[9], float e0, float e1, float tw,
+                                            const float a[9], const float d[9], const Prm<float>& q,
+                                            float& lambda, float stp[9], float& pred, float& gs_out) {
+  const float2 rp[4] = {f2(q.rho_x, q.rho_x), f2(q.rho_x, q.rho_a), f2(q.rho_a, q.rho_a), f2(q.rho_y, q.rho_y)};
+  const float2 ntw = f2(-tw, -tw), E0 = f2(e0, e0), E1 = f2(e1, e1);
+  float2 g2[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float2 j0 = f2(J0[2 * k], J0[2 * k + 1]), j1 = f2(J1[2 * k], J1[2 * k + 1]);
+    const float2 m = __ffma2_rn(j1, E1, __fmul2_rn(j0, E0));
+    g2[k] = __ffma2_rn(rp[k], __fadd2_rn(f2(a[2 * k], a[2 * k + 1]), f2(d[2 * k], d[2 * k + 1])), __fmul2_rn(ntw, m));
+  }
+  const float g8 = -tw * (J0[8] * e0 + J1[8] * e1) + q.rho_y * (a[8] + d[8]);
+  if (lambda < 0.f) {
+    float2 tr2 = f2(0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float2 j0 = f2(J0[2 * k], J0[2 * k + 1]), j1 = f2(J1[2 * k], J1[2 * k + 1]);
+      tr2 = __ffma2_rn(j1, j1, __ffma2_rn(j0, j0, tr2));
+    }
+    const float tr = 3.f * (q.rho_x + q.rho_a + q.rho_y) + tw * (tr2.x + tr2.y + J0[8] * J0[8] + J1[8] * J1[8]);
+    lambda = q.lambda0 * tr / 9.f;
+  }
+  const float iDx = Num<float>::rcp(q.rho_x + lambda), iDa = Num<float>::rcp(q.rho_a + lambda),
+              iDy = Num<float>::rcp(q.rho_y + lambda);
+  const float2 niD[4] = {f2(-iDx, -iDx), f2(-iDx, -iDa), f2(-iDa, -iDa), f2(-iDy, -iDy)};
+  // nq = -D^-1 g; G = J D^-1 J^T; T = J nq = -J D^-1 g
+  float2 nq[4], G00 = f2(0.f, 0.f), G01 = f2(0.f, 0.f), G11 = f2(0.f, 0.f), T0 = f2(0.f, 0.f), T1 = f2(0.f, 0.f);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float2 j0 = f2(J0[2 * k], J0[2 * k + 1]), j1 = f2(J1[2 * k], J1[2 * k + 1]);
+    nq[k] = __fmul2_rn(g2[k], niD[k]);
+    const float2 a0 = __fmul2_rn(j0, niD[k]), a1 = __fmul2_rn(j1, niD[k]);  // -J D^-1
+    G00 = __ffma2_rn(a0, j0, G00);
+    G01 = __ffma2_rn(a0, j1, G01);
+    G11 = __ffma2_rn(a1, j1, G11);
+    T0 = __ffma2_rn(j0, nq[k], T0);
+    T1 = __ffma2_rn(j1, nq[k], T1);
+  }
+  const float nq8 = -g8 * iDy;
+  const float g00 = -(G00.x + G00.y) + J0[8] * J0[8] * iDy, g01 = -(G01.x + G01.y) + J0[8] * J1[8] * iDy,
+              g11 = -(G11.x + G11.y) + J1[8] * J1[8] * iDy;
+  const float t0 = -(T0.x + T0.y + J0[8] * nq8), t1 = -(T1.x + T1.y + J1[8] * nq8);
+  const float S00 = 1.f + tw * g00, S01 = tw * g01, S11 = 1.f + tw * g11;
+  const float idet = Num<float>::rcp(S00 * S11 - S01 * S01);
+  const float y0 = (S11 * t0 - S01 * t1) * idet;
+  const float y1 = (S00 * t1 - S01 * t0) * idet;
+  const float2 Y0 = f2(y0, y0), Y1 = f2(y1, y1);
+  float2 GS = f2(0.f, 0.f), SS = f2(0.f, 0.f);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float2 j0 = f2(J0[2 * k], J0[2 * k + 1]), j1 = f2(J1[2 * k], J1[2 * k + 1]);
+    const float2 u = __ffma2_rn(j1, Y1, __fmul2_rn(j0, Y0));
+    const float2 ntwiD = __fmul2_rn(ntw, niD[k]);  // 2w D^-1
+    const float2 s2 = __ffma2_rn(ntwiD, u, nq[k]);
+    GS = __ffma2_rn(g2[k], s2, GS);
+    SS = __ffma2_rn(s2, s2, SS);
+    stp[2 * k] = s2.x;
+    stp[2 * k + 1] = s2.y;
+  }
+  stp[8] = nq8 + tw * iDy * (J0[8] * y0 + J1[8] * y1);
+  const float gs = GS.x + GS.y + g8 * stp[8], ss = SS.x + SS.y + stp[8] * stp[8];
+  pred = 0.5f * (lambda * ss - gs);
+  gs_out = gs;
+}
+
 // Eq. (9): inner_steps damped Gauss-Newton steps with IRLS weights.  The
 // damped normal matrix 2w J^T J + diag(rho) + lambda I is diagonal plus rank
 // 2 (one observation has two residuals), so each step solves it exactly
@@ -278,44 +354,49 @@ __device__ __forceinline__ void local_solve(T z0, T z1, const T vbar[9], const T
       for (int k = 0; k < 9; ++k) J0[k] = J1[k] = 0;
     }
     const T tw = T(2) * w;
-    T g[9];
+    T stp[9], pred, gs;
+    if constexpr (std::is_same<T, float>::value) {
+      gn_step_f32(J0, J1, e0, e1, tw, a, d, q, lambda, stp, pred, gs);
+    } else {
+      T g[9];
 #pragma unroll
-    for (int c = 0; c < 9; ++c) g[c] = -tw * (J0[c] * e0 + J1[c] * e1) + q.rho(c) * (a[c] + d[c]);
-    if (lambda < T(0)) {
-      T tr = T(3) * (q.rho_x + q.rho_a + q.rho_y);
+      for (int c = 0; c < 9; ++c) g[c] = -tw * (J0[c] * e0 + J1[c] * e1) + q.rho(c) * (a[c] + d[c]);
+      if (lambda < T(0)) {
+        T tr = T(3) * (q.rho_x + q.rho_a + q.rho_y);
 #pragma unroll
-      for (int c = 0; c < 9; ++c) tr += tw * (J0[c] * J0[c] + J1[c] * J1[c]);
-      lambda = q.lambda0 * tr / T(9);
+        for (int c = 0; c < 9; ++c) tr += tw * (J0[c] * J0[c] + J1[c] * J1[c]);
+        lambda = q.lambda0 * tr / T(9);
+      }
+      const T iDx = Num<T>::rcp(q.rho_x + lambda), iDa = Num<T>::rcp(q.rho_a + lambda),
+              iDy = Num<T>::rcp(q.rho_y + lambda);
+      T G00 = 0, G01 = 0, G11 = 0, t0 = 0, t1 = 0;
+      T qv[9];
+#pragma unroll
+      for (int c = 0; c < 9; ++c) {
+        const T iD = c < 3 ? iDx : (c < 6 ? iDa : iDy);
+        qv[c] = g[c] * iD;
+        G00 += J0[c] * J0[c] * iD;
+        G01 += J0[c] * J1[c] * iD;
+        G11 += J1[c] * J1[c] * iD;
+        t0 += J0[c] * qv[c];
+        t1 += J1[c] * qv[c];
+      }
+      const T S00 = T(1) + tw * G00, S01 = tw * G01, S11 = T(1) + tw * G11;
+      const T idet = Num<T>::rcp(S00 * S11 - S01 * S01);
+      const T y0 = (S11 * t0 - S01 * t1) * idet;
+      const T y1 = (S00 * t1 - S01 * t0) * idet;
+      T ss = 0;
+      gs = 0;
+#pragma unroll
+      for (int c = 0; c < 9; ++c) {
+        const T iD = c < 3 ? iDx : (c < 6 ? iDa : iDy);
+        stp[c] = -qv[c] + tw * iD * (J0[c] * y0 + J1[c] * y1);
+        gs += g[c] * stp[c];
+        ss += stp[c] * stp[c];
+      }
+      // decrease of the Gauss-Newton model; with (H + lambda I) s = -g it is (lambda s.s - g.s) / 2
+      pred = T(0.5) * (lambda * ss - gs);
     }
-    const T iDx = Num<T>::rcp(q.rho_x + lambda), iDa = Num<T>::rcp(q.rho_a + lambda),
-            iDy = Num<T>::rcp(q.rho_y + lambda);
-    T G00 = 0, G01 = 0, G11 = 0, t0 = 0, t1 = 0;
-    T qv[9];
-#pragma unroll
-    for (int c = 0; c < 9; ++c) {
-      const T iD = c < 3 ? iDx : (c < 6 ? iDa : iDy);
-      qv[c] = g[c] * iD;
-      G00 += J0[c] * J0[c] * iD;
-      G01 += J0[c] * J1[c] * iD;
-      G11 += J1[c] * J1[c] * iD;
-      t0 += J0[c] * qv[c];
-      t1 += J1[c] * qv[c];
-    }
-    const T S00 = T(1) + tw * G00, S01 = tw * G01, S11 = T(1) + tw * G11;
-    const T idet = Num<T>::rcp(S00 * S11 - S01 * S01);
-    const T y0 = (S11 * t0 - S01 * t1) * idet;
-    const T y1 = (S00 * t1 - S01 * t0) * idet;
-    T stp[9];
-    T gs = 0, ss = 0;
-#pragma unroll
-    for (int c = 0; c < 9; ++c) {
-      const T iD = c < 3 ? iDx : (c < 6 ? iDa : iDy);
-      stp[c] = -qv[c] + tw * iD * (J0[c] * y0 + J1[c] * y1);
-      gs += g[c] * stp[c];
-      ss += stp[c] * stp[c];
-    }
-    // decrease of the Gauss-Newton model; with (H + lambda I) s = -g it is (lambda s.s - g.s) / 2
-    const T pred = T(0.5) * (lambda * ss - gs);
     bool trust = false;
     if (P.valid && q.model_tol > T(0)) {
       // below the rounding noise of L the objective comparison is arbitrary: trust the model
