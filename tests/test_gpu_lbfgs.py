@@ -80,3 +80,18 @@ def test_lbfgs_and_gauss_newton_reach_the_target_alike():
             assert m["rmse_gt"] <= 0.5
             its[solver] = m["iters_done"]
     assert abs(its[0] - its[1]) <= 0.25 * its[0] + 2, its
+
+
+def test_lbfgs_with_an_untrained_warm_start_keeps_the_limit():
+    """The L-BFGS solve also starts from the better of the plain and the learned start, so
+    a random network leaves the ADMM result within the FP32 tolerance."""
+    from paper_1708_07954_gb300 import dba as D
+
+    sc = S.scene1(n_pts=2000, n_cams=32, seed=79)
+    mlp = D.Mlp(11)
+    with D.Solver(sc, local_solver=D.DBA_SOLVER_LBFGS) as a, D.Solver(sc, local_solver=D.DBA_SOLVER_LBFGS) as b:
+        b.set_warm_start(mlp)
+        ma = a.iterate(120)
+        mb = b.iterate(120)
+        assert abs(ma["rmse_obs"] - mb["rmse_obs"]) <= 1e-3
+        assert abs(ma["rmse_gt"] - mb["rmse_gt"]) <= 1e-3
