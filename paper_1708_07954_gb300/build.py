@@ -63,7 +63,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             if verbose and log:
                 print(log)
     tmp = LIB + f".{os.getpid()}.tmp"
-    r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
+    r = subprocess.run([cc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)

@@ -14,6 +14,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/dba.h"
@@ -138,8 +139,28 @@ namespace {
 // in the finalize kernel.  Within a tile, observations of one camera form runs
 // in camera order; an observation's position in that order is packed above its
 // camera index.
+// Runs f(t, lo, hi) on T threads over contiguous chunks of [0, n).
+template <typename F>
+void parallel_chunks(long long n, int T, F f) {
+  if (T <= 1) {
+    f(0, 0LL, n);
+    return;
+  }
+  std::vector<std::thread> th;
+  th.reserve(T);
+  for (int t = 0; t < T; ++t) th.emplace_back(f, t, n * t / T, n * (t + 1) / T);
+  for (std::thread& x : th) x.join();
+}
+
+int host_threads(long long work) {
+  if (work < (1LL << 16)) return 1;
+  const unsigned hw = std::thread::hardware_concurrency();
+  return (int)std::max(1u, std::min(hw ? hw : 1u, 16u));
+}
+
 void build_layout(int n_cams, int n_pts, long long n_obs, const int32_t* pt_idx,
                   const int32_t* cam_idx, int NT, HostLayout& L) {
+  const int T = host_threads(n_obs);
   std::vector<int> count(n_pts, 0), min_cam(n_pts, n_cams);
   L.cam_count.assign(n_cams, 0);
   for (long long o = 0; o < n_obs; ++o) {
@@ -147,13 +168,31 @@ void build_layout(int n_cams, int n_pts, long long n_obs, const int32_t* pt_idx,
     L.cam_count[cam_idx[o]] += 1;
     min_cam[pt_idx[o]] = std::min(min_cam[pt_idx[o]], (int)cam_idx[o]);
   }
-  // counting sort of observations by caller point
+  // counting sort of observations by caller point, stable: per-thread histograms of
+  // contiguous observation chunks give each chunk its own slots within every point
   std::vector<long long> pstart(n_pts + 1, 0);
   for (int i = 0; i < n_pts; ++i) pstart[i + 1] = pstart[i] + count[i];
-  std::vector<long long> by_pt(n_obs);
+  std::vector<int> by_pt(n_obs);
   {
-    std::vector<long long> fill(pstart.begin(), pstart.end() - 1);
-    for (long long o = 0; o < n_obs; ++o) by_pt[fill[pt_idx[o]]++] = o;
+    std::vector<std::vector<int>> hist(T);
+    parallel_chunks(n_obs, T, [&](int t, long long lo, long long hi) {
+      hist[t].assign(n_pts, 0);
+      for (long long o = lo; o < hi; ++o) hist[t][pt_idx[o]] += 1;
+    });
+    parallel_chunks(n_pts, T, [&](int, long long lo, long long hi) {
+      for (long long i = lo; i < hi; ++i) {
+        long long off = pstart[i];
+        for (int t = 0; t < T; ++t) {
+          const int c = hist[t][i];
+          hist[t][i] = (int)off;  // first slot of chunk t in point i
+          off += c;
+        }
+      }
+    });
+    parallel_chunks(n_obs, T, [&](int t, long long lo, long long hi) {
+      std::vector<int>& h = hist[t];
+      for (long long o = lo; o < hi; ++o) by_pt[h[pt_idx[o]]++] = (int)o;
+    });
   }
   // internal point numbering: observed points by first camera, then unobserved ones
   std::vector<int> order;
@@ -166,11 +205,34 @@ void build_layout(int n_cams, int n_pts, long long n_obs, const int32_t* pt_idx,
   L.pt_perm = order;
   L.pt_count.resize(n_pts);
   for (int k = 0; k < n_pts; ++k) L.pt_count[k] = count[order[k]];
+  int n_obs_pts = 0;
+  while (n_obs_pts < n_pts && L.pt_count[n_obs_pts] > 0) ++n_obs_pts;
 
+  // each point's observations by camera (ties by caller index), written in internal order
+  std::vector<long long> kpos(n_obs_pts + 1, 0);
+  for (int k = 0; k < n_obs_pts; ++k) kpos[k + 1] = kpos[k] + L.pt_count[k];
   L.perm.resize(n_obs);
   L.obs_pt.resize(n_obs);
   L.obs_cam.resize(n_obs);
   L.obs_cam_rank.resize(n_obs);
+  parallel_chunks(n_obs_pts, T, [&](int, long long lo, long long hi) {
+    for (long long k = lo; k < hi; ++k) {
+      const int i = order[k];
+      const long long s = pstart[i];
+      const int c = count[i];
+      std::sort(by_pt.begin() + s, by_pt.begin() + s + c, [&](int a, int b) {
+        return cam_idx[a] != cam_idx[b] ? cam_idx[a] < cam_idx[b] : a < b;
+      });
+      for (int q = 0; q < c; ++q) {
+        const int o = by_pt[s + q];
+        L.perm[kpos[k] + q] = o;
+        L.obs_pt[kpos[k] + q] = (int)k;
+        L.obs_cam[kpos[k] + q] = cam_idx[o];
+      }
+    }
+  });
+
+  // tiles of whole tracks; a track longer than a tile is split over tiles of its own
   long long pos = 0;
   int fill_tile = 0;           // observations in the open tile
   long long tile_start = 0;    // first observation of the open tile
@@ -188,19 +250,8 @@ void build_layout(int n_cams, int n_pts, long long n_obs, const int32_t* pt_idx,
     tile_first_run = (int)L.pseg.size();
     fill_tile = 0;
   };
-  for (int k = 0; k < n_pts && L.pt_count[k] > 0; ++k) {
-    const int i = order[k];
-    const long long s = pstart[i];
-    const int c = count[i];
-    std::sort(by_pt.begin() + s, by_pt.begin() + s + c, [&](long long a, long long b) {
-      return cam_idx[a] != cam_idx[b] ? cam_idx[a] < cam_idx[b] : a < b;
-    });
-    for (int q = 0; q < c; ++q) {
-      const long long o = by_pt[s + q];
-      L.perm[pos + q] = o;
-      L.obs_pt[pos + q] = k;
-      L.obs_cam[pos + q] = cam_idx[o];
-    }
+  for (int k = 0; k < n_obs_pts; ++k) {
+    const int c = L.pt_count[k];
     if (c <= NT) {
       if (fill_tile + c > NT) close_tile();
       if (fill_tile == 0) tile_first_pt = k;
@@ -227,24 +278,42 @@ void build_layout(int n_cams, int n_pts, long long n_obs, const int32_t* pt_idx,
   }
   if (fill_tile > 0) close_tile();
 
-  // camera runs per tile, in camera order
-  std::vector<int> run_cam;
-  std::vector<int> idx;
-  for (dba::TileInfo& ti : L.tiles) {
-    idx.resize(ti.n);
-    for (int q = 0; q < ti.n; ++q) idx[q] = ti.o0 + q;
-    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return L.obs_cam[a] < L.obs_cam[b]; });
-    for (int r = 0; r < (int)idx.size(); ++r) L.obs_cam_rank[idx[r]] = L.obs_cam[idx[r]] | (r << 24);
-    ti.c0 = (int)L.cseg.size();
-    int r = 0;
-    while (r < (int)idx.size()) {
-      int e = r;
-      while (e < (int)idx.size() && L.obs_cam[idx[e]] == L.obs_cam[idx[r]]) ++e;
-      L.cseg.push_back(make_int2(r, e - r));
-      run_cam.push_back(L.obs_cam[idx[r]]);
-      r = e;
+  // camera runs per tile, in camera order: each thread handles a contiguous range of
+  // tiles into its own run lists, concatenated in tile order afterwards
+  const long long n_tiles = (long long)L.tiles.size();
+  const int Tt = std::max(1, std::min(T, (int)(n_tiles / 64)));
+  std::vector<std::vector<int2>> t_cseg(Tt);
+  std::vector<std::vector<int>> t_cam(Tt);
+  parallel_chunks(n_tiles, Tt, [&](int t, long long lo, long long hi) {
+    std::vector<int> idx;
+    for (long long q0 = lo; q0 < hi; ++q0) {
+      dba::TileInfo& ti = L.tiles[q0];
+      idx.resize(ti.n);
+      for (int q = 0; q < ti.n; ++q) idx[q] = ti.o0 + q;
+      std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return L.obs_cam[a] < L.obs_cam[b]; });
+      for (int r = 0; r < (int)idx.size(); ++r) L.obs_cam_rank[idx[r]] = L.obs_cam[idx[r]] | (r << 24);
+      ti.c0 = (int)t_cseg[t].size();  // local; shifted below
+      int r = 0;
+      while (r < (int)idx.size()) {
+        int e = r;
+        while (e < (int)idx.size() && L.obs_cam[idx[e]] == L.obs_cam[idx[r]]) ++e;
+        t_cseg[t].push_back(make_int2(r, e - r));
+        t_cam[t].push_back(L.obs_cam[idx[r]]);
+        r = e;
+      }
+      ti.nc = (int)t_cseg[t].size() - ti.c0;
     }
-    ti.nc = (int)L.cseg.size() - ti.c0;
+  });
+  std::vector<int> run_cam;
+  {
+    long long base = 0;
+    for (int t = 0; t < Tt; ++t) {
+      const long long lo = n_tiles * t / Tt, hi = n_tiles * (t + 1) / Tt;
+      for (long long q0 = lo; q0 < hi; ++q0) L.tiles[q0].c0 += (int)base;
+      L.cseg.insert(L.cseg.end(), t_cseg[t].begin(), t_cseg[t].end());
+      run_cam.insert(run_cam.end(), t_cam[t].begin(), t_cam[t].end());
+      base += (long long)t_cseg[t].size();
+    }
   }
   // camera partial slots grouped by camera
   L.cam_slot_off.assign(n_cams + 1, 0);
@@ -367,18 +436,26 @@ void to_T(const std::vector<double>& src, std::vector<T>& dst) {
   for (size_t k = 0; k < src.size(); ++k) dst[k] = (T)src[k];
 }
 
+// hdel / hdual empty: copies at the consensus (zero offsets) / zero duals, set on the device.
 template <typename T>
 dba_status upload_state_T(dba_ctx* ctx, const double* cams, const double* pts,
                           const std::vector<double>& hdel, const std::vector<double>& hdual, bool exact) {
   DevProblem& P = ctx->P;
   const int m = ctx->n_cams, n = ctx->n_pts;
+  const size_t nv = 9 * (size_t)ctx->n_obs;
   std::vector<T> tdel, tX, tY;
   to_T(hdel, tdel);
   to_T(std::vector<double>(pts, pts + 3 * (size_t)n), tX);
   to_T(std::vector<double>(cams, cams + 6 * (size_t)m), tY);
   cudaStream_t st = ctx->stream;
-  DBA_CUDA(cudaMemcpyAsync(P.delta, tdel.data(), tdel.size() * sizeof(T), cudaMemcpyHostToDevice, st), "upload copies");
-  DBA_CUDA(cudaMemcpyAsync(P.adual, hdual.data(), hdual.size() * sizeof(double), cudaMemcpyHostToDevice, st), "upload duals");
+  if (tdel.empty())
+    DBA_CUDA(cudaMemsetAsync(P.delta, 0, nv * sizeof(T), st), "clear copies");
+  else
+    DBA_CUDA(cudaMemcpyAsync(P.delta, tdel.data(), nv * sizeof(T), cudaMemcpyHostToDevice, st), "upload copies");
+  if (hdual.empty())
+    DBA_CUDA(cudaMemsetAsync(P.adual, 0, nv * sizeof(double), st), "clear duals");
+  else
+    DBA_CUDA(cudaMemcpyAsync(P.adual, hdual.data(), nv * sizeof(double), cudaMemcpyHostToDevice, st), "upload duals");
   for (int b = 0; b < 2; ++b) {
     DBA_CUDA(cudaMemcpyAsync(P.X[b], pts, 3 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice, st), "upload points");
     DBA_CUDA(cudaMemcpyAsync(P.Y[b], cams, 6 * (size_t)m * sizeof(double), cudaMemcpyHostToDevice, st), "upload cameras");
@@ -406,7 +483,9 @@ dba_status upload_state(dba_ctx* ctx, const double* cams, const double* pts_call
   for (int k = 0; k < ctx->n_pts; ++k)
     for (int c = 0; c < 3; ++c) pts_int[3 * (size_t)k + c] = pts_caller[3 * (size_t)ctx->pt_perm[k] + c];
   const double* pts = pts_int.data();
-  std::vector<double> hdel(9 * (size_t)l, 0.0), hdual(9 * (size_t)l, 0.0);
+  std::vector<double> hdel, hdual;
+  if (copies) hdel.assign(9 * (size_t)l, 0.0);
+  if (duals) hdual.assign(9 * (size_t)l, 0.0);
   if (copies || duals) {
     for (long long o = 0; o < l; ++o) {
       const long long src = ctx->perm[o];
@@ -546,16 +625,21 @@ dba_status load_problem(dba_ctx* ctx, int NT, int32_t n_cams, int32_t n_pts, int
   DBA_CUDA(ctx->upload(&P.split_slot_off, L.split_slot_off), "upload");
   DBA_CUDA(ctx->upload(&P.pt_count, L.pt_count), "upload");
   // observations in internal order
+  const int T = host_threads(n_obs);
   if (ctx->fp32) {
     std::vector<float2> hz(n_obs);
-    for (int64_t o = 0; o < n_obs; ++o)
-      hz[o] = make_float2((float)z[2 * ctx->perm[o]], (float)z[2 * ctx->perm[o] + 1]);
+    parallel_chunks(n_obs, T, [&](int, long long lo, long long hi) {
+      for (long long o = lo; o < hi; ++o)
+        hz[o] = make_float2((float)z[2 * ctx->perm[o]], (float)z[2 * ctx->perm[o] + 1]);
+    });
     const float2* dz = nullptr;
     DBA_CUDA(ctx->upload(&dz, hz), "upload observations");
     P.z = dz;
   } else {
     std::vector<double2> hz(n_obs);
-    for (int64_t o = 0; o < n_obs; ++o) hz[o] = make_double2(z[2 * ctx->perm[o]], z[2 * ctx->perm[o] + 1]);
+    parallel_chunks(n_obs, T, [&](int, long long lo, long long hi) {
+      for (long long o = lo; o < hi; ++o) hz[o] = make_double2(z[2 * ctx->perm[o]], z[2 * ctx->perm[o] + 1]);
+    });
     const double2* dz = nullptr;
     DBA_CUDA(ctx->upload(&dz, hz), "upload observations");
     P.z = dz;
