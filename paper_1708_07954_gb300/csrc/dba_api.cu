@@ -505,8 +505,11 @@ dba_status upload_state(dba_ctx* ctx, const double* cams, const double* pts_call
                    : upload_state_T<double>(ctx, cams, pts, hdel, hdual, exact);
 }
 
-dba_status read_metrics(dba_ctx* ctx, dba_stats* st, double seconds) {
-  DBA_CUDA(dba::launch_metrics(ctx->P, ctx->prm, ctx->fp32, ctx->cur, ctx->pending, ctx->stream), "metrics launch");
+// launch = false reads the sums of a metrics pass already queued on the stream.
+dba_status read_metrics(dba_ctx* ctx, dba_stats* st, double seconds, bool launch = true) {
+  if (launch)
+    DBA_CUDA(dba::launch_metrics(ctx->P, ctx->prm, ctx->fp32, ctx->cur, ctx->pending, ctx->stream),
+             "metrics launch");
   double h[8];
   DBA_CUDA(cudaMemcpyAsync(h, ctx->P.metric_out, sizeof h, cudaMemcpyDeviceToHost, ctx->stream), "metrics copy");
   DBA_CUDA(cudaStreamSynchronize(ctx->stream), "metrics");
@@ -847,7 +850,7 @@ dba_status dba_iterate_until(dba_ctx* ctx, int max_iters, double target_rmse_gt,
     float ms = 0.f;
     DBA_CUDA(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1), "event");
     seconds += ms * 1e-3;
-    s = read_metrics(ctx, &st, seconds);
+    s = read_metrics(ctx, &st, seconds, false);
     if (s != DBA_OK) return s;
     if (st.rmse_gt <= target_rmse_gt) break;
   }

@@ -346,7 +346,9 @@ __global__ void __launch_bounds__(kMetricThreads) metrics_kernel(DevProblem P, P
   const T* DX = static_cast<const T*>(P.DX);
   const T* DY = static_cast<const T*>(P.DY);
   const T* delta = static_cast<const T*>(P.delta);
-  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  // a thread's own observations (a few dozen) are summed in T; the FP64 pipe sees one
+  // conversion and add per sum and thread, then the FP64 block and grid reductions
+  T acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (long long o = blockIdx.x * (long long)kMetricThreads + threadIdx.x; o < l;
        o += (long long)gridDim.x * kMetricThreads) {
     const int i = P.obs_pt[o], j = P.obs_cam_rank[o] & kCamMask;
@@ -363,17 +365,17 @@ __global__ void __launch_bounds__(kMetricThreads) metrics_kernel(DevProblem P, P
       const T zp0 = q.focal * Q.p[0] * iz + q.cx, zp1 = q.focal * Q.p[1] * iz + q.cy;
       const T e0 = zz.x - zp0, e1 = zz.y - zp1;
       const T s = e0 * e0 + e1 * e1;
-      acc[0] += (double)s;
-      acc[1] += (double)misfit<T>(q.loss, q.lp, s);
+      acc[0] += s;
+      acc[1] += misfit<T>(q.loss, q.lp, s);
       if (P.zt && (!P.inlier || P.inlier[o])) {
         const V2 gt = static_cast<const V2*>(P.zt)[o];
         const T g0 = zp0 - gt.x, g1 = zp1 - gt.y;
-        acc[2] += (double)(g0 * g0 + g1 * g1);
-        acc[7] += 1.0;
+        acc[2] += g0 * g0 + g1 * g1;
+        acc[7] += T(1);
       }
-      acc[3] += 1.0;
+      acc[3] += T(1);
     } else {
-      acc[4] += 1.0;
+      acc[4] += T(1);
     }
     T pr = 0, dr = 0;
 #pragma unroll
@@ -384,10 +386,10 @@ __global__ void __launch_bounds__(kMetricThreads) metrics_kernel(DevProblem P, P
       pr += cp * cp;
       dr += (rho * dc) * (rho * dc);
     }
-    acc[5] += (double)pr;
-    acc[6] += (double)dr;
+    acc[5] += pr;
+    acc[6] += dr;
   }
-  for (int k = 0; k < 8; ++k) red[k][threadIdx.x] = acc[k];
+  for (int k = 0; k < 8; ++k) red[k][threadIdx.x] = to_f64<T>(acc[k]);
   __syncthreads();
   for (int w = kMetricThreads / 2; w > 0; w >>= 1) {
     if (threadIdx.x < w)
