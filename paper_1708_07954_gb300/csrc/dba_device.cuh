@@ -412,8 +412,13 @@ __device__ __forceinline__ void local_solve(T z0, T z1, const T vbar[9], const T
     }
     Pose<T> Pt;
     pose_at(vt, q.eps, Pt);
-    // a trusted step carries the objective as its model value L - pred
-    const T Lt = trust ? L - pred : local_objective(dt, a, Pt, z0, z1, q);
+    // a trusted step carries the objective as its model value L - pred; the trial objective
+    // is evaluated only when a lane of the warp needs the comparison
+    T Lt = L - pred;
+    if (__any_sync(__activemask(), !trust)) {
+      const T Lo = local_objective(dt, a, Pt, z0, z1, q);
+      if (!trust) Lt = Lo;
+    }
     if (Pt.valid && (trust || Lt < L)) {
 #pragma unroll
       for (int c = 0; c < 9; ++c) d[c] = dt[c];

@@ -138,3 +138,36 @@ def test_errors():
         with pytest.raises(dba.DbaError) as e:
             s.iterate_until(5, 0.5)
         assert e.value.status == dba.DBA_ESTATE
+
+
+def test_full_size_workload2_blocks_fp64_sampled():
+    """Blocks of 32 points x 2 cameras on the full workload 2 (~4M observations), FP64:
+    after one iteration from the initial state (zero duals) each point is the mean of its
+    block copies (Eqs. 10-11 over copies); for sampled points every block holding the point
+    is re-solved by the oracle (Eq. 14) and the mean compared, <= 1e-9."""
+    sc = S.scene2()
+    with dba.BlockSolver(sc, 32, 2, precision=dba.DBA_PREC_F64) as s:
+        s.iterate(1, stats=False)
+        _, pts = s.params()
+        cfg = oracle_cfg(s)
+    B = O.BlockLayout(sc, 32, 2)
+    blk_of_pc = np.repeat(np.arange(B.n_blocks), np.diff(B.pc_off))
+    order = np.argsort(B.pc_pt, kind="stable")
+    off = np.searchsorted(B.pc_pt[order], np.arange(sc.n_pts + 1))
+    rng = np.random.default_rng(5)
+    zero3 = lambda n: np.zeros(3 * n)
+    for i in rng.choice(sc.n_pts, 60, replace=False):
+        copies = []
+        for k in order[off[i]:off[i + 1]]:
+            b = blk_of_pc[k]
+            o0, o1 = B.obs_off[b], B.obs_off[b + 1]
+            obs = B.blk_obs[o0:o1]
+            pcs = B.pc_pt[B.pc_off[b]:B.pc_off[b + 1]]
+            ccs = B.cc_cam[B.cc_off[b]:B.cc_off[b + 1]]
+            xbar, ybar = sc.pts0[pcs].ravel(), sc.cams0[ccs].ravel()
+            X, _ = O.block_solve(cfg, B.obs_lp[o0:o1], B.obs_lc[o0:o1], sc.z[obs].ravel(), xbar, ybar,
+                                 zero3(len(pcs)), np.zeros(6 * len(ccs)), xbar, ybar)
+            copies.append(X.reshape(-1, 3)[int(k - B.pc_off[b])])
+        if copies:
+            ref = np.mean(copies, axis=0)
+            assert np.abs(pts[i] - ref).max() <= TOL64 * np.abs(ref).max(), i

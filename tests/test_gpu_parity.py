@@ -211,6 +211,22 @@ def test_full_size_workload2_fp64_sampled(scene_w2):
         assert np.abs(cams[j] - copies[sel, 3:].mean(axis=0)).max() <= TOL64 * np.abs(cams[j]).max()
 
 
+def test_full_size_workload2_lbfgs_fp64_sampled(scene_w2):
+    """The L-BFGS local solver at full size: one FP64 iteration from the initial state,
+    sampled observations re-solved by the oracle's L-BFGS, <= 1e-9."""
+    sc = scene_w2
+    with dba.Solver(sc, precision=dba.DBA_PREC_F64, local_solver=dba.DBA_SOLVER_LBFGS) as s:
+        s.iterate(1, stats=False)
+        copies, _ = s.state()
+        cfg = oracle_cfg(sc, s)
+    rng = np.random.default_rng(3)
+    zero = np.zeros(9)
+    for o in rng.choice(sc.n_obs, 300, replace=False):
+        i, j = sc.pt_idx[o], sc.cam_idx[o]
+        v = O.local_solve_lbfgs(cfg, sc.z[o], sc.pts0[i], sc.cams0[j], zero, np.r_[sc.pts0[i], sc.cams0[j]])
+        assert np.abs(copies[o] - v).max() <= TOL64 * np.abs(v).max()
+
+
 def test_full_size_workload2_fp32_sampled(scene_w2):
     """Workload 2 at full size in the benchmark's launch configuration (FP32 local solves,
     256-observation tiles, CUDA graph).  An FP32 local solve takes the same damped Gauss-Newton
