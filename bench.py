@@ -37,7 +37,7 @@ METRIC = "observations/s per ADMM iteration"
 UNIT = "obs/s"
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3000)
@@ -58,7 +58,7 @@ def parse():
     ap.add_argument("--profile-iters", type=int, default=200)
     ap.add_argument("--reference-seconds", type=float, default=90.0,
                     help="wall-clock budget of the whole --impl reference run")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def make_scene(args):
@@ -72,6 +72,23 @@ def make_scene(args):
 def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(
         os.environ.get("LOCAL_RANK", "0"))
+
+
+def max_over_ranks(ms, world, device):
+    """The slowest rank's time: a MAX all-reduce over the initialised process group."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, n_obs, steps, ms):
+    """Whole-job observations per second: every replica solves n_obs observations per step."""
+    return world * n_obs * steps / (ms * 1e-3)
 
 
 # ------------------------------------------------------------------ clocks
@@ -290,12 +307,8 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * sc.n_obs * args.steps / (ms * 1e-3)
+    ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
+    value = job_throughput(world, sc.n_obs, args.steps, ms)
     final = solver.evaluate()
 
     # per-kernel device time (CUDA events around each launch on the same stream)
