@@ -50,6 +50,11 @@ def parse(argv=None):
     ap.add_argument("--inner-steps", type=int, default=5, help="damped Gauss-Newton steps per local solve")
     ap.add_argument("--warm-start", action="store_true",
                     help="time the iteration with the learned warm start (shipped weights) in front of the local solves")
+    ap.add_argument("--local-solver", choices=["gn", "lbfgs"], default="gn",
+                    help="local solver of Eq. (9): damped Gauss-Newton or L-BFGS (Sec. 3.1)")
+    ap.add_argument("--block-points", type=int, default=0,
+                    help="> 0: time the block subproblems of Eq. (14) with this many points per block")
+    ap.add_argument("--block-cams", type=int, default=1, help="cameras per block (with --block-points)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-0.5-px measurement")
@@ -159,6 +164,12 @@ def algorithmic_bytes(scene, layout, fp32):
 #   capacitance terms 126, 2x2 solve 17, step + model decrease 96, noise bound 7,
 #   trial point 18, trial pose 44, trial objective 58, damping update 1  -> 501.
 FLOPS_START, FLOPS_PER_STEP = 179, 501
+# The same count for the L-BFGS local solve (memory 4, one line-search trial per iteration):
+#   start: copy + pose + objective 111, scaling 9, gradient 125, re-base 9, run sums 9;
+#   per iteration: two-loop recursion 2 x 83 (on average two stored pairs over five
+#   iterations), H0 scaling 37, direction and slope 27, trial point 36, trial pose 44,
+#   trial objective 58, gradient at the new point 125, pair update 37      -> 530.
+FLOPS_START_LBFGS, FLOPS_PER_STEP_LBFGS = 263, 530
 
 # 152 SMs x 128 FP32 lanes x 2 flops per FMA x 2.07 GHz (maximum SM clock)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -174,8 +185,25 @@ def mlp_bytes_per_obs(fp32):
     return 9 * t + 9 * 8 + 2 * t + 4 + 4 + 9 * t
 
 
-def algorithmic_flops(n_obs, inner_steps):
-    return n_obs * (FLOPS_START + FLOPS_PER_STEP * inner_steps)
+def flops_per_obs(inner_steps, lbfgs=False):
+    if lbfgs:
+        return FLOPS_START_LBFGS + FLOPS_PER_STEP_LBFGS * inner_steps
+    return FLOPS_START + FLOPS_PER_STEP * inner_steps
+
+
+def algorithmic_flops(n_obs, inner_steps, lbfgs=False):
+    return n_obs * flops_per_obs(inner_steps, lbfgs)
+
+
+def block_bytes(layout, n_obs, fp32):
+    """Algorithmic bytes of one block_solve launch: per observation its pixel pair and local
+    camera; per point copy its point id, observation offset, offset (read and write) and dual;
+    the point's consensus; per camera copy the same with 6 values; a 24-byte block record."""
+    t = 4 if fp32 else 8
+    per_pc = 4 + 4 + 2 * 3 * t + 3 * 8 + 3 * 8
+    per_cc = 4 + 2 * 6 * t + 6 * 8 + 6 * 8
+    return n_obs * (2 * t + 1) + layout["n_point_copies"] * per_pc + layout["n_camera_copies"] * per_cc + \
+        layout["n_blocks"] * 24
 
 
 # the sources tile_iterate_kernel is built from; their joint sha256 keys the ncu counters
@@ -283,7 +311,10 @@ def run_ours(args, rank, world, local_rank):
     prec = dba.DBA_PREC_F32_LOCAL if fp32 else dba.DBA_PREC_F64
     sc = make_scene(args)
     stream = torch.cuda.Stream()  # a real stream: the library launches on it, events are recorded on it
-    solver = dba.Solver(sc, precision=prec, inner_steps=args.inner_steps, stream=stream.cuda_stream)
+    lbfgs = args.local_solver == "lbfgs"
+    lsolver = dba.DBA_SOLVER_LBFGS if lbfgs else dba.DBA_SOLVER_GN
+    solver = dba.Solver(sc, precision=prec, inner_steps=args.inner_steps, stream=stream.cuda_stream,
+                        local_solver=lsolver)
     if args.warm_start:
         from paper_1708_07954_gb300 import warmstart
 
@@ -316,14 +347,14 @@ def run_ours(args, rank, world, local_rank):
     tile_ms = prof["tile_iterate"]
     bytes_launch, per_obs = algorithmic_bytes(sc, layout, fp32)
     peaks, src = measured_peaks()
-    flops = algorithmic_flops(sc.n_obs, args.inner_steps)
+    flops = algorithmic_flops(sc.n_obs, args.inner_steps, lbfgs)
     achieved_tf = flops / (tile_ms * 1e-3) / 1e12
     achieved_gbs = bytes_launch / (tile_ms * 1e-3) / 1e9
     roofline = {"bound": "alu", "achieved": achieved_tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved_tf / FP32_PEAK_TFLOPS, "traffic": ncu_traffic(sc.n_obs),
+                "frac": achieved_tf / FP32_PEAK_TFLOPS, "traffic": None if lbfgs else ncu_traffic(sc.n_obs),
                 "kernel": "tile_iterate", "kernel_ms": tile_ms, "kernel_share": tile_ms / sum(prof.values()),
                 "algorithmic_flops_per_launch": flops,
-                "algorithmic_flops_per_obs": FLOPS_START + FLOPS_PER_STEP * args.inner_steps,
+                "algorithmic_flops_per_obs": flops_per_obs(args.inner_steps, lbfgs),
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (unit counts and maximum clock)",
                 "hbm": {"achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                         "frac": achieved_gbs / peaks["hbm_gbs"], "algorithmic_bytes_per_launch": bytes_launch,
@@ -349,7 +380,7 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         with dba.Solver(sc, precision=prec, inner_steps=args.inner_steps, stream=stream.cuda_stream,
-                        ground_truth=False) as s2:
+                        ground_truth=False, local_solver=lsolver) as s2:
             s2.iterate(iters, stats=False)
             s2.params()
         dt = time.perf_counter() - t0
@@ -367,7 +398,8 @@ def run_ours(args, rank, world, local_rank):
         ttt = {"target_px": 0.5, "rmse": "vs noise-free projections over observations of outlier-free tracks",
                "max_iters": args.ttt_max_iters}
         for name, pr in (("fp32_plain", dba.DBA_PREC_F32_LOCAL), ("fp64_plain", dba.DBA_PREC_F64)):
-            with dba.Solver(sc, precision=pr, inner_steps=args.inner_steps, stream=stream.cuda_stream) as s3:
+            with dba.Solver(sc, precision=pr, inner_steps=args.inner_steps, stream=stream.cuda_stream,
+                            local_solver=lsolver) as s3:
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 m = s3.iterate_until(args.ttt_max_iters, 0.5)
@@ -403,7 +435,7 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle as O
 
-        cfg = O.config_for(sc)
+        cfg = O.config_for(sc, local_solver=O.SOLVER_LBFGS if lbfgs else O.SOLVER_GN)
         st = O.State(sc)
         t0 = time.perf_counter()
         st.iterate(cfg, args.cpu_iters)
@@ -419,7 +451,8 @@ def run_ours(args, rank, world, local_rank):
             "vs_baseline": None, "dtype": "f32+f64" if fp32 else "f64", "data": "synthetic",
             "config": {"workload": sc.name, "n_obs": sc.n_obs, "n_cams": sc.n_cams, "n_pts": sc.n_pts,
                        "n_scenes": 1 if sc.scene_off is None else len(sc.scene_off) - 1,
-                       "loss": "huber", "inner_steps": args.inner_steps, "warm_start": bool(args.warm_start),
+                       "loss": "huber", "inner_steps": args.inner_steps, "local_solver": args.local_solver,
+                       "warm_start": bool(args.warm_start),
                        "precision": "f32 local solves, f64 consensus/duals" if fp32 else "f64",
                        "l2": "inputs larger than L2 (~1 GB per iteration), no flush",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
@@ -433,11 +466,133 @@ def run_ours(args, rank, world, local_rank):
     return 0
 
 
+# ------------------------------------------------------------------ block subproblems
+def run_blocks(args, rank, world, local_rank):
+    """The same line for the block subproblems of Eq. (14): block_points x block_cams per
+    update, one iteration = block solves, consensus over copies, dual ascent."""
+    import torch
+
+    from paper_1708_07954_gb300 import build, dba
+
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    build.build()
+    dba.load()
+    fp32 = args.precision == "f32"
+    prec = dba.DBA_PREC_F32_LOCAL if fp32 else dba.DBA_PREC_F64
+    P, K = args.block_points, args.block_cams
+    sc = make_scene(args)
+    stream = torch.cuda.Stream()
+    solver = dba.BlockSolver(sc, P, K, precision=prec, inner_steps=args.inner_steps, stream=stream.cuda_stream)
+    layout = solver.layout()
+    solver.iterate(args.warmup, stats=False)
+    clocks = ClockSampler(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
+    clocks.start()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    solver.iterate(args.steps, stats=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
+    value = job_throughput(world, sc.n_obs, args.steps, ms)
+    final = solver.iterate(0)
+    prof = solver.profile(min(args.profile_iters, max(args.steps, 1)))
+    flops = solver.algorithmic_flops()
+    solve_ms = prof["block_solve"]
+    peaks, src = measured_peaks()
+    achieved_tf = flops / (solve_ms * 1e-3) / 1e12
+    bytes_launch = block_bytes(layout, sc.n_obs, fp32)
+    achieved_gbs = bytes_launch / (solve_ms * 1e-3) / 1e9
+    roofline = {"bound": "alu", "achieved": achieved_tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved_tf / FP32_PEAK_TFLOPS, "traffic": None, "kernel": "block_solve",
+                "kernel_ms": solve_ms, "kernel_share": solve_ms / sum(prof.values()),
+                "algorithmic_flops_per_launch": flops, "algorithmic_flops_per_obs": flops / sc.n_obs,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (unit counts and maximum clock)",
+                "hbm": {"achieved": achieved_gbs, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": achieved_gbs / peaks["hbm_gbs"], "algorithmic_bytes_per_launch": bytes_launch,
+                        "peak_source": f"{src} (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else "fallback"},
+                "kernels_ms": prof}
+    solver.close()
+    e2e = None
+    if not args.no_e2e:
+        iters = sc.iters
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with dba.BlockSolver(sc, P, K, precision=prec, inner_steps=args.inner_steps, stream=stream.cuda_stream,
+                             ground_truth=False) as s2:
+            s2.iterate(iters, stats=False)
+            s2.params()
+        dt = time.perf_counter() - t0
+        h2d = sc.n_obs * (4 + 4 + 16) + sc.n_cams * 48 + sc.n_pts * 24
+        d2h = sc.n_cams * 48 + sc.n_pts * 24
+        e2e = {"value": sc.n_obs * iters / dt, "unit": UNIT, "h2d_bytes_per_step": h2d / iters,
+               "d2h_bytes_per_step": d2h / iters, "iters_per_solve": iters, "seconds_per_solve": dt,
+               "what": f"dba_block_create + dba_block_set_observations + dba_block_iterate({iters}) + "
+                       "dba_block_get_params, wall clock"}
+    ttt = None
+    if not args.no_ttt:
+        with dba.BlockSolver(sc, P, K, precision=prec, inner_steps=args.inner_steps, stream=stream.cuda_stream) as s3:
+            m = s3.iterate_until(args.ttt_max_iters, 0.5)
+        ttt = {"target_px": 0.5, "seconds": m["seconds"], "iters": m["iters_done"], "rmse_gt": m["rmse_gt"],
+               "reached": m["rmse_gt"] <= 0.5}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle as O
+        from paper_1708_07954_gb300 import scenes as S
+
+        # the oracle's block iteration on whole tracks of the first points, all cameras
+        n_keep = min(sc.n_pts, 20000)
+        keep = sc.pt_idx < n_keep
+        sample = S.Scene(n_cams=sc.n_cams, n_pts=n_keep, pt_idx=sc.pt_idx[keep], cam_idx=sc.cam_idx[keep],
+                         z=sc.z[keep], z_true=sc.z_true[keep], outlier=sc.outlier[keep], cams_gt=sc.cams_gt,
+                         pts_gt=sc.pts_gt[:n_keep], cams0=sc.cams0, pts0=sc.pts0[:n_keep], name="sample")
+        cfg = O.config_for(sc)
+        cfg.inner_steps = args.inner_steps
+        st = O.BlockState(sample, P, K)
+        t0 = time.perf_counter()
+        st.iterate(cfg, args.cpu_iters)
+        dt = time.perf_counter() - t0
+        cpu = {"value": sample.n_obs * args.cpu_iters / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{args.cpu_iters} block ADMM iterations of {sample.n_obs} observations ({n_keep} whole "
+                         f"tracks, all cameras) of the workload (FP64, OpenMP over blocks)"}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64" if fp32 else "f64", "data": "synthetic",
+            "config": {"workload": sc.name, "n_obs": sc.n_obs, "n_cams": sc.n_cams, "n_pts": sc.n_pts,
+                       "path": "blocks", "block_points": P, "block_cams": K, **layout,
+                       "loss": "huber", "inner_steps": args.inner_steps,
+                       "precision": "f32 block solves, f64 consensus/duals" if fp32 else "f64",
+                       "l2": "inputs larger than L2, no flush",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "time_to_target": ttt,
+            "clocks": clk, "gpu_launches": 4 * args.steps,
+            "final": {k: final[k] for k in ("rmse_obs", "rmse_gt", "objective", "iters_done")},
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     rank, world, local_rank = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.block_points > 0:
+        return run_blocks(args, rank, world, local_rank)
     return run_ours(args, rank, world, local_rank)
 
 

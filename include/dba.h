@@ -315,6 +315,10 @@ dba_status dba_block_get_params(dba_block_ctx* ctx, double* cams_out, double* pt
 /* Number of blocks, point copies and camera copies (any pointer may be NULL). */
 dba_status dba_block_layout(const dba_block_ctx* ctx, int64_t* n_blocks, int64_t* n_point_copies,
                             int64_t* n_camera_copies);
+/* Algorithmic floating-point operations of one iteration's block solves (every
+ * Gauss-Newton step counted in full with its trial objective; add/mul 1, fma 2,
+ * reciprocal/square root/sine/cosine 1), counted from the loaded layout. */
+dba_status dba_block_algorithmic_flops(const dba_block_ctx* ctx, double* per_iteration);
 /* Message of the last failed call on ctx (ctx NULL: of the last failed create). */
 const char* dba_block_last_error(const dba_block_ctx* ctx);
 void dba_block_destroy(dba_block_ctx* ctx);

@@ -674,6 +674,7 @@ struct dba_block_ctx {
   dba::BlockProblem B{};
   std::vector<void*> allocs;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  double flops_start = 0.0, flops_step = 0.0;  // algorithmic FP work of the block solves
 
   dba_status fail(dba_status s, const std::string& msg) {
     err = msg;
@@ -958,6 +959,32 @@ dba_status dba_block_set_observations(dba_block_ctx* ctx, int32_t n_cams, int32_
   }
   pc_obs.push_back((int)l);
   const long long n_pc = (long long)pc_pt.size(), n_cc = (long long)cc_cam.size();
+  // algorithmic flops of the block solves (add/mul 1, fma 2, rcp/sqrt/sin/cos 1), counted
+  // from the kernel's arithmetic, each step a full step with its trial objective:
+  //   per observation: pose 44, Jacobian and residual 64, point block and gradient terms 43,
+  //     noise bound 7, its 2w A W g term 14, gradient and right-hand side entries 48,
+  //     back-substitution 30, trial pose and misfit 64                        -> 314
+  //   per camera pair of a point's observations (Schur weight 60 + 8 per entry of the
+  //     reduced system): 228 when both are one observation (21 entries), 348 otherwise
+  //   per point copy: penalty gradient 6, 3x3 inverse 35, W g 15, step 15, model terms 12,
+  //     trial penalty 9                                                      -> 92
+  //   per block: Cholesky n^3/3 + n^2/2, triangular solves 2 n^2, damping and camera
+  //     model/penalty terms 10 n (n = 6 cameras)
+  //   start of a solve: pose and misfit 64 per observation, penalty 9 per point copy and
+  //     per camera copy 24
+  {
+    double pairs_off = 0.0, per_block = 0.0;
+    for (long long k = 0; k < n_pc; ++k) {
+      const double c = (double)(pc_obs[k + 1] - pc_obs[k]);
+      pairs_off += c * (c - 1.0) / 2.0;
+    }
+    for (const dba::BlockInfo& bi : blocks) {
+      const double nu = 6.0 * bi.nc;
+      per_block += nu * nu * nu / 3.0 + nu * nu / 2.0 + 2.0 * nu * nu + 10.0 * nu;
+    }
+    ctx->flops_step = 314.0 * (double)l + 228.0 * (double)l + 348.0 * pairs_off + 92.0 * (double)n_pc + per_block;
+    ctx->flops_start = 64.0 * (double)l + 9.0 * (double)n_pc + 24.0 * (double)n_cc;
+  }
   // copy lists per point and per camera (consensus)
   std::vector<int> pt_off(n + 1, 0), cam_off(m + 1, 0), pt_cp(n_pc), cam_cp(n_cc);
   for (long long k = 0; k < n_pc; ++k) ++pt_off[pc_pt[k] + 1];
@@ -1160,6 +1187,13 @@ dba_status dba_block_get_params(dba_block_ctx* ctx, double* cams_out, double* pt
                            ctx->stream),
            "get_params");
   BLK_CUDA(cudaStreamSynchronize(ctx->stream), "get_params");
+  return DBA_OK;
+}
+
+dba_status dba_block_algorithmic_flops(const dba_block_ctx* ctx, double* per_iteration) {
+  if (!ctx || !per_iteration) return DBA_EINVAL;
+  if (!ctx->has_problem) return DBA_ESTATE;
+  *per_iteration = ctx->flops_start + ctx->cfg.inner_steps * ctx->flops_step;
   return DBA_OK;
 }
 
