@@ -81,9 +81,11 @@ template <typename T, int KC>
 struct BlkSmem {
   static constexpr int kU = 6 * KC;
   static constexpr int kPairs = KC * (KC + 1) / 2;
-  T lin[KC][kLin][32];        // each lane's observation slots: A = dz/dx (2x3), B = dz/dy (2x6), 2w, e
-  T U[KC][2][32];             // 2w A W_p g_p per slot
-  T Q[kPairs][4][32];         // per camera pair c1 <= c2: 2x2 weight of the point's Schur term
+  // rows padded to 33 words: the reduction reads one lane's column across rows, which a
+  // 32-word row would put in a single bank
+  T lin[KC][kLin][33];        // each lane's observation slots: A = dz/dx (2x3), B = dz/dy (2x6), 2w, e
+  T U[KC][2][33];             // 2w A W_p g_p per slot
+  T Q[kPairs][4][33];         // per camera pair c1 <= c2: 2x2 weight of the point's Schur term
   signed char slot[KC][32];   // slot of each lane's observation on camera c (-1: none)
   T S[kU][kU + 1];            // reduced camera system, then its Cholesky factor
   T rhs[kU];
