@@ -410,24 +410,30 @@ __device__ __forceinline__ void local_solve(T z0, T z1, const T vbar[9], const T
       dt[c] = d[c] + stp[c];
       vt[c] = vbar[c] + dt[c];
     }
-    Pose<T> Pt;
-    pose_at(vt, q.eps, Pt);
+    // the trial pose replaces the current one; a rejected step recomputes the kept copy's
+    // pose (the same arithmetic on the same input, so bit-identical to the pose it had)
+    pose_at(vt, q.eps, P);
     // a trusted step carries the objective as its model value L - pred; the trial objective
     // is evaluated only when a lane of the warp needs the comparison
     T Lt = L - pred;
     if (__any_sync(__activemask(), !trust)) {
-      const T Lo = local_objective(dt, a, Pt, z0, z1, q);
+      const T Lo = local_objective(dt, a, P, z0, z1, q);
       if (!trust) Lt = Lo;
     }
-    if (Pt.valid && (trust || Lt < L)) {
+    const bool accept = P.valid && (trust || Lt < L);
+    if (accept) {
 #pragma unroll
       for (int c = 0; c < 9; ++c) d[c] = dt[c];
-      P = Pt;
       L = Lt;
       const T lr = Num<T>::tenth(lambda);
       lambda = lr > q.lambda_min ? lr : q.lambda_min;
     } else {
       lambda *= T(10);
+    }
+    if (__any_sync(__activemask(), !accept) && !accept) {
+#pragma unroll
+      for (int c = 0; c < 9; ++c) v[c] = vbar[c] + d[c];
+      pose_at(v, q.eps, P);
     }
   }
 }
