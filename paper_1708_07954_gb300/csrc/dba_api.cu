@@ -40,10 +40,54 @@ struct HostLayout {
   int n_cam_slots = 0, n_pt_slots = 0;
 };
 
+// Runs f(t, lo, hi) on T threads over contiguous chunks of [0, n).
+template <typename F>
+void parallel_chunks(long long n, int T, F f) {
+  if (T <= 1) {
+    f(0, 0LL, n);
+    return;
+  }
+  std::vector<std::thread> th;
+  th.reserve(T);
+  for (int t = 0; t < T; ++t) th.emplace_back(f, t, n * t / T, n * (t + 1) / T);
+  for (std::thread& x : th) x.join();
+}
+
+int host_threads(long long work) {
+  if (work < (1LL << 16)) return 1;
+  const unsigned hw = std::thread::hardware_concurrency();
+  return (int)std::max(1u, std::min(hw ? hw : 1u, 16u));
+}
+
 bool finite_all(const double* p, long long n) {
-  for (long long k = 0; k < n; ++k)
-    if (!std::isfinite(p[k])) return false;
+  const int T = host_threads(n);
+  std::vector<char> ok(T, 1);
+  parallel_chunks(n, T, [&](int t, long long lo, long long hi) {
+    for (long long k = lo; k < hi; ++k)
+      if (!std::isfinite(p[k])) {
+        ok[t] = 0;
+        return;
+      }
+  });
+  for (char c : ok)
+    if (!c) return false;
   return true;
+}
+
+// First observation whose point or camera index is out of range, or -1.
+long long first_bad_index(const int32_t* pt_idx, const int32_t* cam_idx, long long n_obs, int n_pts, int n_cams) {
+  const int T = host_threads(n_obs);
+  std::vector<long long> bad(T, -1);
+  parallel_chunks(n_obs, T, [&](int t, long long lo, long long hi) {
+    for (long long o = lo; o < hi; ++o)
+      if (pt_idx[o] < 0 || pt_idx[o] >= n_pts || cam_idx[o] < 0 || cam_idx[o] >= n_cams) {
+        bad[t] = o;
+        return;
+      }
+  });
+  for (long long b : bad)
+    if (b >= 0) return b;  // chunks are in order: the first hit is the smallest index
+  return -1;
 }
 }  // namespace
 
@@ -139,46 +183,40 @@ namespace {
 // in the finalize kernel.  Within a tile, observations of one camera form runs
 // in camera order; an observation's position in that order is packed above its
 // camera index.
-// Runs f(t, lo, hi) on T threads over contiguous chunks of [0, n).
-template <typename F>
-void parallel_chunks(long long n, int T, F f) {
-  if (T <= 1) {
-    f(0, 0LL, n);
-    return;
-  }
-  std::vector<std::thread> th;
-  th.reserve(T);
-  for (int t = 0; t < T; ++t) th.emplace_back(f, t, n * t / T, n * (t + 1) / T);
-  for (std::thread& x : th) x.join();
-}
-
-int host_threads(long long work) {
-  if (work < (1LL << 16)) return 1;
-  const unsigned hw = std::thread::hardware_concurrency();
-  return (int)std::max(1u, std::min(hw ? hw : 1u, 16u));
-}
-
 void build_layout(int n_cams, int n_pts, long long n_obs, const int32_t* pt_idx,
                   const int32_t* cam_idx, int NT, HostLayout& L) {
   const int T = host_threads(n_obs);
+  // per-thread histograms of contiguous observation chunks: points (also giving each chunk
+  // its own slots within every point, a stable counting sort) and cameras; first camera of
+  // each point per chunk
+  std::vector<std::vector<int>> hist(T), camc(T), first(T);
+  parallel_chunks(n_obs, T, [&](int t, long long lo, long long hi) {
+    hist[t].assign(n_pts, 0);
+    camc[t].assign(n_cams, 0);
+    first[t].assign(n_pts, n_cams);
+    for (long long o = lo; o < hi; ++o) {
+      const int i = pt_idx[o], j = cam_idx[o];
+      hist[t][i] += 1;
+      camc[t][j] += 1;
+      if (j < first[t][i]) first[t][i] = j;
+    }
+  });
   std::vector<int> count(n_pts, 0), min_cam(n_pts, n_cams);
+  parallel_chunks(n_pts, T, [&](int, long long lo, long long hi) {
+    for (long long i = lo; i < hi; ++i)
+      for (int t = 0; t < T; ++t) {
+        count[i] += hist[t][i];
+        min_cam[i] = std::min(min_cam[i], first[t][i]);
+      }
+  });
+  first.clear();
   L.cam_count.assign(n_cams, 0);
-  for (long long o = 0; o < n_obs; ++o) {
-    count[pt_idx[o]] += 1;
-    L.cam_count[cam_idx[o]] += 1;
-    min_cam[pt_idx[o]] = std::min(min_cam[pt_idx[o]], (int)cam_idx[o]);
-  }
-  // counting sort of observations by caller point, stable: per-thread histograms of
-  // contiguous observation chunks give each chunk its own slots within every point
+  for (int t = 0; t < T; ++t)
+    for (int j = 0; j < n_cams; ++j) L.cam_count[j] += camc[t][j];
   std::vector<long long> pstart(n_pts + 1, 0);
   for (int i = 0; i < n_pts; ++i) pstart[i + 1] = pstart[i] + count[i];
   std::vector<int> by_pt(n_obs);
   {
-    std::vector<std::vector<int>> hist(T);
-    parallel_chunks(n_obs, T, [&](int t, long long lo, long long hi) {
-      hist[t].assign(n_pts, 0);
-      for (long long o = lo; o < hi; ++o) hist[t][pt_idx[o]] += 1;
-    });
     parallel_chunks(n_pts, T, [&](int, long long lo, long long hi) {
       for (long long i = lo; i < hi; ++i) {
         long long off = pstart[i];
@@ -194,14 +232,15 @@ void build_layout(int n_cams, int n_pts, long long n_obs, const int32_t* pt_idx,
       for (long long o = lo; o < hi; ++o) by_pt[h[pt_idx[o]]++] = (int)o;
     });
   }
-  // internal point numbering: observed points by first camera, then unobserved ones
-  std::vector<int> order;
-  order.reserve(n_pts);
-  for (int i = 0; i < n_pts; ++i)
-    if (count[i] > 0) order.push_back(i);
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return min_cam[a] < min_cam[b]; });
-  for (int i = 0; i < n_pts; ++i)
-    if (count[i] == 0) order.push_back(i);
+  // internal point numbering: observed points by first camera (ties by index: a counting
+  // sort over first cameras), then unobserved ones (first camera n_cams)
+  std::vector<int> order(n_pts);
+  {
+    std::vector<int> fc(n_cams + 2, 0);
+    for (int i = 0; i < n_pts; ++i) fc[min_cam[i] + 1] += 1;
+    for (int j = 0; j <= n_cams; ++j) fc[j + 1] += fc[j];
+    for (int i = 0; i < n_pts; ++i) order[fc[min_cam[i]]++] = i;
+  }
   L.pt_perm = order;
   L.pt_count.resize(n_pts);
   for (int k = 0; k < n_pts; ++k) L.pt_count[k] = count[order[k]];
@@ -750,10 +789,10 @@ dba_status dba_set_observations(dba_ctx* ctx, int32_t n_cams, int32_t n_pts, int
     return ctx->fail(DBA_EINVAL, "dba_set_observations: at most 16,777,215 cameras");
   if (!pt_idx || !cam_idx || !z || !cams0 || !pts0)
     return ctx->fail(DBA_EINVAL, "dba_set_observations: null array");
-  for (int64_t o = 0; o < n_obs; ++o)
-    if (pt_idx[o] < 0 || pt_idx[o] >= n_pts || cam_idx[o] < 0 || cam_idx[o] >= n_cams)
-      return ctx->fail(DBA_EINVAL, "dba_set_observations: observation " + std::to_string(o) +
-                                       " has an index out of range");
+  const long long bad = first_bad_index(pt_idx, cam_idx, n_obs, n_pts, n_cams);
+  if (bad >= 0)
+    return ctx->fail(DBA_EINVAL, "dba_set_observations: observation " + std::to_string(bad) +
+                                     " has an index out of range");
   if (!finite_all(z, 2 * n_obs) || !finite_all(cams0, 6 * (long long)n_cams) ||
       !finite_all(pts0, 3 * (long long)n_pts))
     return ctx->fail(DBA_EINVAL, "dba_set_observations: non-finite input value");
