@@ -18,6 +18,8 @@
 //                span several tiles.
 //  metrics       reprojection RMSE, objective and residuals at consensus.
 #include <cuda_runtime.h>
+
+#include <type_traits>
 #include <math_constants.h>
 
 #include <mutex>
@@ -203,11 +205,11 @@ __device__ __forceinline__ void process_tile(const DevProblem& P, const Prm<T>& 
     const int r = task / 3, c = task % 3;
     const int2 se = S.pseg[r];
     double sum;
+    T acc = 0;
     if (exact) {
       sum = 0.0;
       for (int e = se.x; e < se.x + se.y; ++e) sum += s_buf[c][e];
     } else {
-      T acc = 0;
       for (int e = se.x; e < se.x + se.y; ++e) acc += s_t[c][e];
       sum = to_f64<T>(acc);
     }
@@ -215,10 +217,20 @@ __device__ __forceinline__ void process_tile(const DevProblem& P, const Prm<T>& 
     if (slot < 0) {
       const long long k = 3 * ((long long)ti.pt_lo + r) + c;
       const double xo = S.X[task];
-      const double xn = xo + sum / (double)se.y;
-      P.X[nxt][k] = xn;
-      static_cast<T*>(P.Xm)[k] = (T)xn;
-      static_cast<T*>(P.DX)[k] = (T)(xo - xn);
+      if (std::is_same<T, float>::value && !exact) {
+        // FP32 offsets: their mean is formed in FP32 and added to the FP64 consensus, which
+        // keeps the divide and the conversions off the FP64 pipe
+        const T inc = acc * Num<T>::rcp((T)se.y);
+        const double xn = xo + to_f64<T>(inc);
+        P.X[nxt][k] = xn;
+        static_cast<T*>(P.Xm)[k] = from_f64<T>(xn);
+        static_cast<T*>(P.DX)[k] = -inc;
+      } else {
+        const double xn = xo + sum / (double)se.y;
+        P.X[nxt][k] = xn;
+        static_cast<T*>(P.Xm)[k] = from_f64<T>(xn);
+        static_cast<T*>(P.DX)[k] = from_f64<T>(xo - xn);
+      }
     } else {
       P.pt_part[3 * slot + c] = sum;
     }
