@@ -130,7 +130,11 @@ __device__ __forceinline__ void process_tile(const DevProblem& P, const Prm<T>& 
   const T* __restrict__ Ym = static_cast<const T*>(P.Ym);
   const T* __restrict__ DX = static_cast<const T*>(P.DX);
   const T* __restrict__ DY = static_cast<const T*>(P.DY);
-  T(*s_t)[NT] = reinterpret_cast<T(*)[NT]>(&s_buf[0][0]);  // T view: row c at s_t[c]
+  // T view of the run buffer, rows padded by one word so that the run sums, which read
+  // the same position of several rows at once, fall in different banks (9 (NT + 1) T
+  // words fit in the 9 NT doubles of s_buf for T = float; FP64 uses the unpadded rows)
+  constexpr int kRow = sizeof(T) == 4 ? NT + 1 : NT;
+  T(*s_t)[kRow] = reinterpret_cast<T(*)[kRow]>(&s_buf[0][0]);
 
   if (t < ti.n) {
     const int i = S.pt[t];
