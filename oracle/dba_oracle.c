@@ -442,7 +442,7 @@ int ora_admm_iterate(const ora_config* c, int n_cams, int n_pts, long n_obs, con
   if (n_cams < 0 || n_pts < 0 || n_obs < 0 || iters < 0) return -1;
   if (check_indices(n_cams, n_pts, n_obs, pt_idx, cam_idx) != 0) return -1;
 #ifdef _OPENMP
-  if (nthreads > 0) omp_set_num_threads(nthreads);
+  omp_set_num_threads(nthreads > 0 ? nthreads : omp_get_num_procs());
 #else
   (void)nthreads;
 #endif
@@ -797,7 +797,7 @@ int ora_block_iterate(const ora_config* c, int n_cams, int n_pts, long n_obs, co
     if (cc_cam[k] < 0 || cc_cam[k] >= n_cams) return -1;
   if (obs_off[n_blocks] != n_obs) return -1;
 #ifdef _OPENMP
-  if (nthreads > 0) omp_set_num_threads(nthreads);
+  omp_set_num_threads(nthreads > 0 ? nthreads : omp_get_num_procs());
 #else
   (void)nthreads;
 #endif

@@ -90,7 +90,7 @@ void ora_admm_init(int n_cams, int n_pts, long n_obs, const int* pt_idx, const i
                    const double* cams, const double* pts, double* copies, double* duals);
 /* Runs `iters` ADMM iterations, Eqs. (9)-(13), in place.  Observations in caller order.
  * z_true may be NULL.  metrics (nullable) receives the state after the last iteration.
- * nthreads <= 0 uses the OpenMP default.  Returns 0, or -1 on bad input. */
+ * nthreads <= 0 uses every processor.  Returns 0, or -1 on bad input. */
 int ora_admm_iterate(const ora_config* c, int n_cams, int n_pts, long n_obs, const int* pt_idx,
                      const int* cam_idx, const double* z, const double* z_true, double* copies,
                      double* duals, double* cams, double* pts, int iters, int nthreads,
