@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <cmath>
 #include <cstring>
@@ -721,7 +722,7 @@ cudaError_t upload(dba_block_ctx* ctx, T** dst, const std::vector<T>& src) {
 template <typename T, int KC>
 cudaError_t launch_block_solve_kc(dba_block_ctx* ctx) {
   const size_t smem = sizeof(dba::BlkSmem<T, KC>) * dba::kBlkWarps;
-  static bool set = false;
+  static std::atomic<bool> set{false};
   if (!set) {
     cudaError_t e = cudaFuncSetAttribute(dba::block_solve_kernel<T, KC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -19,6 +19,8 @@
 //  metrics       reprojection RMSE, objective and residuals at consensus.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include <type_traits>
 #include <math_constants.h>
 
@@ -610,7 +612,8 @@ namespace {
 // once per instantiation (dynamic shared memory opt-in, occupancy query).
 template <typename T, int NT, int kS>
 cudaError_t tile_grid(int* grid) {
-  static int cached = 0;
+  // per process and device-independent: first caller computes; racing callers compute the same
+  static std::atomic<int> cached{0};
   if (!cached) {
     const int smem = (int)tile_smem_bytes<T, NT>();
     cudaError_t e =

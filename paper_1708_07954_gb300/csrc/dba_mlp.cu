@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -579,7 +580,8 @@ __global__ void __launch_bounds__(kInferThreads, 4) mlp_infer_kernel(DevProblem 
 // memory, and 64 of an SM's 512 tensor-memory columns.
 template <typename T, bool kFromState>
 cudaError_t infer_grid(int* grid) {
-  static int cached = 0;
+  // per process and device-independent: first caller computes; racing callers compute the same
+  static std::atomic<int> cached{0};
   if (cached) {
     *grid = cached;
     return cudaSuccess;

@@ -171,3 +171,16 @@ def test_full_size_workload2_blocks_fp64_sampled():
         if copies:
             ref = np.mean(copies, axis=0)
             assert np.abs(pts[i] - ref).max() <= TOL64 * np.abs(ref).max(), i
+
+
+def test_a_repeated_point_camera_pair_is_rejected():
+    sc = S.scene0(n_pts=10, n_cams=3)
+    dup = S.Scene(n_cams=sc.n_cams, n_pts=sc.n_pts, pt_idx=np.r_[sc.pt_idx, sc.pt_idx[:1]].astype(np.int32),
+                  cam_idx=np.r_[sc.cam_idx, sc.cam_idx[:1]].astype(np.int32), z=np.r_[sc.z, sc.z[:1]],
+                  z_true=np.r_[sc.z_true, sc.z_true[:1]], outlier=np.r_[sc.outlier, sc.outlier[:1]],
+                  cams_gt=sc.cams_gt, pts_gt=sc.pts_gt, cams0=sc.cams0, pts0=sc.pts0, focal=sc.focal,
+                  cx=sc.cx, cy=sc.cy, loss=sc.loss, loss_param=sc.loss_param, rho_x=sc.rho_x, rho_y=sc.rho_y,
+                  rho_angle=sc.rho_angle)
+    with pytest.raises(dba.DbaError) as e:
+        dba.BlockSolver(dup, 4, 2)
+    assert e.value.status == dba.DBA_EINVAL and "observed twice" in str(e.value)
