@@ -707,6 +707,8 @@ dba_status load_problem(dba_ctx* ctx, int NT, int32_t n_cams, int32_t n_pts, int
   DBA_CUDA(ctx->alloc(&P.cam_part, 6 * (size_t)std::max(1, P.n_cam_slots)), "alloc partials");
   DBA_CUDA(ctx->alloc(&P.metric_part, 8 * (size_t)dba::kMetricBlocks), "alloc metrics");
   DBA_CUDA(ctx->alloc(&P.metric_out, 8), "alloc metrics");
+  DBA_CUDA(ctx->alloc(&p, 12 * (size_t)n_cams * esz), "alloc camera poses");
+  P.cam_pose = p;
   DBA_CUDA(ctx->alloc(&P.ctl, 1), "alloc control");
   ctx->has_problem = true;
   dba_status s = upload_state(ctx, cams0, pts0, nullptr, nullptr);
@@ -882,7 +884,9 @@ dba_status dba_iterate_until(dba_ctx* ctx, int max_iters, double target_rmse_gt,
     DBA_CUDA(cudaEventRecord(ctx->ev0, ctx->stream), "event");
     dba_status s = run_iterations(ctx, 1);
     if (s != DBA_OK) return s;
-    DBA_CUDA(dba::launch_metrics(ctx->P, ctx->prm, ctx->fp32, ctx->cur, ctx->pending, ctx->stream), "metrics");
+    // the stopping test needs rmse_gt only; the full statistics are evaluated once at the end
+    DBA_CUDA(dba::launch_metrics(ctx->P, ctx->prm, ctx->fp32, ctx->cur, ctx->pending, ctx->stream, true),
+             "metrics");
     DBA_CUDA(cudaEventRecord(ctx->ev1, ctx->stream), "event");
     s = check_device_flags(ctx);
     if (s != DBA_OK) return s;
@@ -893,8 +897,8 @@ dba_status dba_iterate_until(dba_ctx* ctx, int max_iters, double target_rmse_gt,
     if (s != DBA_OK) return s;
     if (st.rmse_gt <= target_rmse_gt) break;
   }
-  if (max_iters == 0) {
-    dba_status s = read_metrics(ctx, &st, 0.0);
+  {
+    dba_status s = read_metrics(ctx, &st, seconds);
     if (s != DBA_OK) return s;
   }
   if (stats) *stats = st;

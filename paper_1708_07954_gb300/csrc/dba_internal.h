@@ -75,6 +75,7 @@ struct DevProblem {
   const void* mlp_start;        // [9][l] T: learned candidate start (nullptr: none)
   double* metric_part;          // [metric blocks][8]
   double* metric_out;           // [8]
+  void* cam_pose;               // [n_cams][12] T: R (row-major) and t of each consensus camera
   DevCtl* ctl;
 };
 
@@ -89,8 +90,9 @@ cudaError_t prepare_tile_kernels();
 // Kernel launchers (return the launch error).  fp32 selects the FP32 local-solve path.
 cudaError_t launch_tile_iterate(const DevProblem& P, const Params& prm, bool fp32, cudaStream_t s);
 cudaError_t launch_finalize(const DevProblem& P, bool fp32, cudaStream_t s);
+// gt_only: only the reference-pixel sums (rmse_gt and its count) and the valid counts.
 cudaError_t launch_metrics(const DevProblem& P, const Params& prm, bool fp32, int cur, int pending,
-                           cudaStream_t s);
+                           cudaStream_t s, bool gt_only = false);
 cudaError_t launch_settle(const DevProblem& P, bool fp32, int cur, cudaStream_t s);
 cudaError_t launch_project_truth(const DevProblem& P, const Params& prm, bool fp32,
                                  const double* cams_gt, const double* pts_gt, void* zt_out,

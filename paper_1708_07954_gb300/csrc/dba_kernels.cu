@@ -354,37 +354,59 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(DevProblem P) {
 }
 
 // ------------------------------------------------------------ metrics
+// Rotation and translation of every consensus camera (R = Rz Ry Rx, Sec. 2.1), so that the
+// metrics pass projects each observation without re-evaluating its camera's angles.
 template <typename T>
+__global__ void camera_pose_kernel(DevProblem P) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= P.n_cams) return;
+  const T* Ym = static_cast<const T*>(P.Ym);
+  T v[9] = {0, 0, 0};
+#pragma unroll
+  for (int c = 0; c < 6; ++c) v[3 + c] = Ym[6 * j + c];
+  Pose<T> Q;
+  pose_at(v, T(0), Q);  // x = 0: u = 0, p = t
+  T* out = static_cast<T*>(P.cam_pose) + 12 * (long long)j;
+#pragma unroll
+  for (int c = 0; c < 9; ++c) out[c] = Q.R[c];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) out[9 + c] = v[6 + c];
+}
+
+// Metrics at consensus: sums of |e|^2, phi_m, |f - z_true|^2 (inliers), valid / invalid
+// counts, primal and dual residual terms, reference count.  kGtOnly: only the reference
+// sums and the counts (the stopping test of dba_iterate_until).
+template <typename T, bool kGtOnly>
 __global__ void __launch_bounds__(kMetricThreads) metrics_kernel(DevProblem P, Prm<T> q, int pending) {
   using V2 = typename Num<T>::V2;
   __shared__ double red[8][kMetricThreads];
   const long long l = P.n_obs;
   const T* Xm = static_cast<const T*>(P.Xm);
-  const T* Ym = static_cast<const T*>(P.Ym);
   const T* DX = static_cast<const T*>(P.DX);
   const T* DY = static_cast<const T*>(P.DY);
   const T* delta = static_cast<const T*>(P.delta);
+  const T* pose = static_cast<const T*>(P.cam_pose);
   // a thread's own observations (a few dozen) are summed in T; the FP64 pipe sees one
   // conversion and add per sum and thread, then the FP64 block and grid reductions
   T acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (long long o = blockIdx.x * (long long)kMetricThreads + threadIdx.x; o < l;
        o += (long long)gridDim.x * kMetricThreads) {
     const int i = P.obs_pt[o], j = P.obs_cam_rank[o] & kCamMask;
-    T v[9];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) v[c] = Xm[3 * i + c];
-#pragma unroll
-    for (int c = 0; c < 6; ++c) v[3 + c] = Ym[6 * j + c];
-    Pose<T> Q;
-    pose_at(v, q.eps, Q);
-    if (Q.valid) {
-      const V2 zz = static_cast<const V2*>(P.z)[o];
-      const T iz = T(1) / Q.p[2];
-      const T zp0 = q.focal * Q.p[0] * iz + q.cx, zp1 = q.focal * Q.p[1] * iz + q.cy;
-      const T e0 = zz.x - zp0, e1 = zz.y - zp1;
-      const T s = e0 * e0 + e1 * e1;
-      acc[0] += s;
-      acc[1] += misfit<T>(q.loss, q.lp, s);
+    const T x0 = Xm[3 * i], x1 = Xm[3 * i + 1], x2 = Xm[3 * i + 2];
+    const T* Rt = pose + 12 * (long long)j;
+    const T p0 = Rt[0] * x0 + Rt[1] * x1 + Rt[2] * x2 + Rt[9];
+    const T p1 = Rt[3] * x0 + Rt[4] * x1 + Rt[5] * x2 + Rt[10];
+    const T p2 = Rt[6] * x0 + Rt[7] * x1 + Rt[8] * x2 + Rt[11];
+    if (p2 > q.eps) {
+      const T iz = T(1) / p2;
+      const T zp0 = q.focal * p0 * iz + q.cx, zp1 = q.focal * p1 * iz + q.cy;
+      if (!kGtOnly) {
+        const V2 zz = static_cast<const V2*>(P.z)[o];
+        const T e0 = zz.x - zp0, e1 = zz.y - zp1;
+        const T s = e0 * e0 + e1 * e1;
+        acc[0] += s;
+        acc[1] += misfit<T>(q.loss, q.lp, s);
+      }
       if (P.zt && (!P.inlier || P.inlier[o])) {
         const V2 gt = static_cast<const V2*>(P.zt)[o];
         const T g0 = zp0 - gt.x, g1 = zp1 - gt.y;
@@ -395,17 +417,19 @@ __global__ void __launch_bounds__(kMetricThreads) metrics_kernel(DevProblem P, P
     } else {
       acc[4] += T(1);
     }
-    T pr = 0, dr = 0;
+    if (!kGtOnly) {
+      T pr = 0, dr = 0;
 #pragma unroll
-    for (int c = 0; c < 9; ++c) {
-      const T dc = c < 3 ? DX[3 * i + c] : DY[6 * j + c - 3];
-      const T cp = delta[c * l + o] + (pending ? dc : T(0));
-      const T rho = q.rho(c);
-      pr += cp * cp;
-      dr += (rho * dc) * (rho * dc);
+      for (int c = 0; c < 9; ++c) {
+        const T dc = c < 3 ? DX[3 * i + c] : DY[6 * j + c - 3];
+        const T cp = delta[c * l + o] + (pending ? dc : T(0));
+        const T rho = q.rho(c);
+        pr += cp * cp;
+        dr += (rho * dc) * (rho * dc);
+      }
+      acc[5] += pr;
+      acc[6] += dr;
     }
-    acc[5] += pr;
-    acc[6] += dr;
   }
   for (int k = 0; k < 8; ++k) red[k][threadIdx.x] = to_f64<T>(acc[k]);
   __syncthreads();
@@ -689,13 +713,23 @@ cudaError_t launch_finalize(const DevProblem& P, bool fp32, cudaStream_t s) {
 }
 
 cudaError_t launch_metrics(const DevProblem& P, const Params& prm, bool fp32, int cur, int pending,
-                           cudaStream_t s) {
+                           cudaStream_t s, bool gt_only) {
   (void)cur;
   const int g = grid_for(P.n_obs, kMetricThreads, kMetricBlocks);
-  if (fp32)
-    metrics_kernel<float><<<g, kMetricThreads, 0, s>>>(P, make_prm<float>(prm), pending);
-  else
-    metrics_kernel<double><<<g, kMetricThreads, 0, s>>>(P, make_prm<double>(prm), pending);
+  const int gc = (P.n_cams + 127) / 128;
+  if (fp32) {
+    camera_pose_kernel<float><<<gc, 128, 0, s>>>(P);
+    if (gt_only)
+      metrics_kernel<float, true><<<g, kMetricThreads, 0, s>>>(P, make_prm<float>(prm), pending);
+    else
+      metrics_kernel<float, false><<<g, kMetricThreads, 0, s>>>(P, make_prm<float>(prm), pending);
+  } else {
+    camera_pose_kernel<double><<<gc, 128, 0, s>>>(P);
+    if (gt_only)
+      metrics_kernel<double, true><<<g, kMetricThreads, 0, s>>>(P, make_prm<double>(prm), pending);
+    else
+      metrics_kernel<double, false><<<g, kMetricThreads, 0, s>>>(P, make_prm<double>(prm), pending);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   metrics_final_kernel<<<1, kMetricThreads, 0, s>>>(P, g);
