@@ -448,6 +448,7 @@ def run_ours(args, rank, world, local_rank):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "admm_iterations_per_s": 1e3 * args.steps / ms,
             "vs_baseline": None, "dtype": "f32+f64" if fp32 else "f64", "data": "synthetic",
             "config": {"workload": sc.name, "n_obs": sc.n_obs, "n_cams": sc.n_cams, "n_pts": sc.n_pts,
                        "n_scenes": 1 if sc.scene_off is None else len(sc.scene_off) - 1,
@@ -569,6 +570,7 @@ def run_blocks(args, rank, world, local_rank):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "admm_iterations_per_s": 1e3 * args.steps / ms,
             "vs_baseline": None, "dtype": "f32+f64" if fp32 else "f64", "data": "synthetic",
             "config": {"workload": sc.name, "n_obs": sc.n_obs, "n_cams": sc.n_cams, "n_pts": sc.n_pts,
                        "path": "blocks", "block_points": P, "block_cams": K, **layout,

@@ -117,7 +117,8 @@ struct dba_ctx {
   int cur = 0, pending = 0;
   long long iters = 0;
   // graph of one iteration
-  cudaGraphExec_t graph = nullptr;
+  cudaGraphExec_t graph = nullptr;        // one iteration
+  cudaGraphExec_t graph_until = nullptr;  // one iteration and the reference-pixel metrics pass
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 
   double rho_of(int c) const { return c < 3 ? prm.rho_x : (c < 6 ? prm.rho_a : prm.rho_y); }
@@ -129,9 +130,13 @@ struct dba_ctx {
     err = std::string(where) + ": " + cudaGetErrorString(e);
     return DBA_ECUDA;
   }
-  void free_problem() {
+  void drop_graphs() {  // after any change of the captured kernel arguments
     if (graph) cudaGraphExecDestroy(graph);
-    graph = nullptr;
+    if (graph_until) cudaGraphExecDestroy(graph_until);
+    graph = graph_until = nullptr;
+  }
+  void free_problem() {
+    drop_graphs();
     for (void* p : allocs) cudaFree(p);
     allocs.clear();
     P = DevProblem{};
@@ -573,8 +578,11 @@ dba_status launch_iteration(dba_ctx* ctx) {
   return DBA_OK;
 }
 
-dba_status ensure_graph(dba_ctx* ctx) {
-  if (ctx->graph) return DBA_OK;
+// with_metrics: the graph also runs the reference-pixel metrics pass after the iteration
+// (its kernel arguments hold pending = 1, the state after any iteration).
+dba_status ensure_graph(dba_ctx* ctx, bool with_metrics = false) {
+  cudaGraphExec_t& exec = with_metrics ? ctx->graph_until : ctx->graph;
+  if (exec) return DBA_OK;
   cudaGraph_t g = nullptr;
   DBA_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal), "graph capture");
   cudaError_t e0 = ctx->warm ? dba::launch_mlp_warmstart(ctx->P, ctx->prm, ctx->fp32, ctx->d_mlp_blob,
@@ -582,15 +590,18 @@ dba_status ensure_graph(dba_ctx* ctx) {
                              : cudaSuccess;
   cudaError_t e1 = dba::launch_tile_iterate(ctx->P, ctx->prm, ctx->fp32, ctx->stream);
   cudaError_t e2 = dba::launch_finalize(ctx->P, ctx->fp32, ctx->stream);
+  cudaError_t e4 = with_metrics ? dba::launch_metrics(ctx->P, ctx->prm, ctx->fp32, ctx->cur ^ 1, 1, ctx->stream, true)
+                                : cudaSuccess;
   cudaError_t e3 = cudaStreamEndCapture(ctx->stream, &g);
   if (e0 != cudaSuccess) return ctx->cuda_fail(e0, "graph capture (warm start)");
   if (e1 != cudaSuccess) return ctx->cuda_fail(e1, "graph capture (tile_iterate)");
   if (e2 != cudaSuccess) return ctx->cuda_fail(e2, "graph capture (finalize)");
+  if (e4 != cudaSuccess) return ctx->cuda_fail(e4, "graph capture (metrics)");
   if (e3 != cudaSuccess) return ctx->cuda_fail(e3, "graph capture");
-  cudaError_t e = cudaGraphInstantiate(&ctx->graph, g, 0);
+  cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) {
-    ctx->graph = nullptr;
+    exec = nullptr;
     return ctx->cuda_fail(e, "graph instantiate");
   }
   return DBA_OK;
@@ -850,10 +861,7 @@ dba_status dba_set_ground_truth(dba_ctx* ctx, const double* cams_gt, const doubl
   DBA_CUDA(cudaStreamSynchronize(st), "ground truth");
   ctx->P.zt = zt;
   ctx->has_gt = true;
-  if (ctx->graph) {  // kernel arguments changed
-    cudaGraphExecDestroy(ctx->graph);
-    ctx->graph = nullptr;
-  }
+  ctx->drop_graphs();  // kernel arguments changed
   return DBA_OK;
 }
 
@@ -881,20 +889,31 @@ dba_status dba_iterate_until(dba_ctx* ctx, int max_iters, double target_rmse_gt,
   dba_stats st{};
   double seconds = 0.0;
   for (int it = 0; it < max_iters; ++it) {
+    // one iteration and the stopping test's metrics pass (rmse_gt only; the full statistics
+    // are evaluated once at the end), one graph launch when graphs are on
     DBA_CUDA(cudaEventRecord(ctx->ev0, ctx->stream), "event");
-    dba_status s = run_iterations(ctx, 1);
-    if (s != DBA_OK) return s;
-    // the stopping test needs rmse_gt only; the full statistics are evaluated once at the end
-    DBA_CUDA(dba::launch_metrics(ctx->P, ctx->prm, ctx->fp32, ctx->cur, ctx->pending, ctx->stream, true),
-             "metrics");
+    if (ctx->cfg.use_graph) {
+      dba_status s = ensure_graph(ctx, true);
+      if (s != DBA_OK) return s;
+      DBA_CUDA(cudaGraphLaunch(ctx->graph_until, ctx->stream), "graph launch");
+      ctx->cur ^= 1;
+      ctx->pending = 1;
+      ctx->iters += 1;
+    } else {
+      dba_status s = run_iterations(ctx, 1);
+      if (s != DBA_OK) return s;
+      DBA_CUDA(dba::launch_metrics(ctx->P, ctx->prm, ctx->fp32, ctx->cur, ctx->pending, ctx->stream, true),
+               "metrics");
+    }
     DBA_CUDA(cudaEventRecord(ctx->ev1, ctx->stream), "event");
-    s = check_device_flags(ctx);
+    double h[8];
+    DBA_CUDA(cudaMemcpyAsync(h, ctx->P.metric_out, sizeof h, cudaMemcpyDeviceToHost, ctx->stream), "metrics copy");
+    dba_status s = check_device_flags(ctx);  // one synchronisation for both reads
     if (s != DBA_OK) return s;
     float ms = 0.f;
     DBA_CUDA(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1), "event");
     seconds += ms * 1e-3;
-    s = read_metrics(ctx, &st, seconds, false);
-    if (s != DBA_OK) return s;
+    st.rmse_gt = h[7] > 0 ? std::sqrt(h[2] / h[7]) : 0.0;
     if (st.rmse_gt <= target_rmse_gt) break;
   }
   {
@@ -1145,10 +1164,7 @@ dba_status dba_mlp_harvest(dba_ctx* ctx, int64_t stride, int target_steps, float
 dba_status dba_set_warm_start(dba_ctx* ctx, const dba_mlp* mlp) {
   if (!ctx) return DBA_EINVAL;
   if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_set_warm_start before dba_set_observations");
-  if (ctx->graph) {
-    cudaGraphExecDestroy(ctx->graph);
-    ctx->graph = nullptr;
-  }
+  ctx->drop_graphs();
   if (!mlp) {
     ctx->warm = false;
     ctx->P.mlp_start = nullptr;
