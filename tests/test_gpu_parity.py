@@ -366,3 +366,49 @@ def test_errors_are_status_codes_not_aborts():
         assert dba.dba_iterate(ctx, 2)["iters_done"] == 2
     finally:
         dba.dba_destroy(ctx)
+
+
+@pytest.mark.parametrize("solver", [dba.DBA_SOLVER_GN, dba.DBA_SOLVER_LBFGS])
+def test_points_starting_behind_a_camera(solver):
+    """Degenerate start (Sec. 3.1, Thm. 1's positive depths): a few points begin behind one
+    of the cameras that observe them.  Those observations have no misfit term until a step
+    brings the copy in front of the camera, which the oracle restates; FP64 parity holds."""
+    sc = S.scene0(n_pts=60, n_cams=8, seed=71)
+    pts0 = sc.pts0.copy()
+    for i in (0, 7, 13):
+        y = sc.cams0[0]
+        R = O.rotation(y)
+        centre = -R.T @ y[3:]
+        pts0[i] = centre - 0.5 * R[2]  # half a unit behind camera 0 along its optical axis
+    bad = S.Scene(**{**sc.__dict__, "pts0": pts0})
+    with dba.Solver(bad, precision=dba.DBA_PREC_F64, local_solver=solver) as s:
+        m0 = s.evaluate()
+        assert m0["n_invalid"] >= 3
+        cfg = oracle_cfg(bad, s)
+        st = O.State(bad)
+        for _ in range(4):
+            s.iterate(1, stats=False)
+            st.iterate(cfg, 1)
+            cams, pts = s.params()
+            assert relerr(cams, st.cams) <= TOL64 and relerr(pts, st.pts) <= TOL64
+
+
+def test_block_points_starting_behind_a_camera():
+    sc = S.scene0(n_pts=60, n_cams=8, seed=73)
+    pts0 = sc.pts0.copy()
+    for i in (2, 11):
+        y = sc.cams0[3]
+        R = O.rotation(y)
+        pts0[i] = -R.T @ y[3:] - 0.5 * R[2]
+    bad = S.Scene(**{**sc.__dict__, "pts0": pts0})
+    with dba.BlockSolver(bad, 8, 2, precision=dba.DBA_PREC_F64) as s:
+        c = s.cfg
+        cfg = O.config(focal=c.focal, cx=c.cx, cy=c.cy, loss=c.loss, loss_param=c.loss_param, rho_x=c.rho_x,
+                       rho_y=c.rho_y, rho_angle=c.rho_angle, inner_steps=c.inner_steps, lm_lambda0=c.lm_lambda0,
+                       lm_lambda_min=c.lm_lambda_min, eps_depth=c.eps_depth, lm_model_tol=c.lm_model_tol)
+        st = O.BlockState(bad, 8, 2)
+        for _ in range(4):
+            s.iterate(1, stats=False)
+            st.iterate(cfg, 1)
+            cams, pts = s.params()
+            assert relerr(cams, st.cams) <= TOL64 and relerr(pts, st.pts) <= TOL64
