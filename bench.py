@@ -320,6 +320,7 @@ def run_ours(args, rank, world, local_rank):
 
         solver.set_warm_start(warmstart.load())
     layout = solver.layout()
+    classes = solver.size_classes()
     solver.iterate(args.warmup, stats=False)
 
     def barrier():
@@ -489,6 +490,7 @@ def run_blocks(args, rank, world, local_rank):
     stream = torch.cuda.Stream()
     solver = dba.BlockSolver(sc, P, K, precision=prec, inner_steps=args.inner_steps, stream=stream.cuda_stream)
     layout = solver.layout()
+    classes = solver.size_classes()
     solver.iterate(args.warmup, stats=False)
     clocks = ClockSampler(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
     clocks.start()
@@ -574,12 +576,13 @@ def run_blocks(args, rank, world, local_rank):
             "vs_baseline": None, "dtype": "f32+f64" if fp32 else "f64", "data": "synthetic",
             "config": {"workload": sc.name, "n_obs": sc.n_obs, "n_cams": sc.n_cams, "n_pts": sc.n_pts,
                        "path": "blocks", "block_points": P, "block_cams": K, **layout,
+                       "blocks_per_size_class": classes,
                        "loss": "huber", "inner_steps": args.inner_steps,
                        "precision": "f32 block solves, f64 consensus/duals" if fp32 else "f64",
                        "l2": "inputs larger than L2, no flush",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "time_to_target": ttt,
-            "clocks": clk, "gpu_launches": 4 * args.steps,
+            "clocks": clk, "gpu_launches": (3 + sum(1 for c in classes if c)) * args.steps,
             "final": {k: final[k] for k in ("rmse_obs", "rmse_gt", "objective", "iters_done")},
         }
         print(json.dumps(line), flush=True)

@@ -315,6 +315,11 @@ dba_status dba_block_get_params(dba_block_ctx* ctx, double* cams_out, double* pt
 /* Number of blocks, point copies and camera copies (any pointer may be NULL). */
 dba_status dba_block_layout(const dba_block_ctx* ctx, int64_t* n_blocks, int64_t* n_point_copies,
                             int64_t* n_camera_copies);
+/* Blocks in each size class of the solve kernel, in launch order: one camera and at
+ * most 8 points (8-lane groups), at most 2 cameras and 16 points (16 lanes), the rest
+ * (32 lanes).  Each nonempty class is one kernel launch per iteration.  counts: 3
+ * entries, caller-owned. */
+dba_status dba_block_size_classes(const dba_block_ctx* ctx, int64_t* counts);
 /* Algorithmic floating-point operations of one iteration's block solves (every
  * Gauss-Newton step counted in full with its trial objective; add/mul 1, fma 2,
  * reciprocal/square root/sine/cosine 1), counted from the loaded layout. */

@@ -7,11 +7,12 @@
 // pi consecutive ranks, cameras cut into groups of kappa consecutive indices, one
 // block per (point group, camera group) pair holding observations.
 //
-// GPU mapping: one warp per block, one lane per point copy (pi <= 32), camera
-// copies (kappa <= 4) shared by the warp in shared memory.  Each damped
-// Gauss-Newton step eliminates the points (3x3 per lane) and solves the reduced
-// camera system (at most 24 x 24, a Schur complement accumulated with warp
-// reductions) by a lane-per-row Cholesky factorisation.  Consensus (Eqs. 10-11
+// GPU mapping: one group of G lanes per block (G = 8, 16 or 32 by the block's size,
+// several blocks per warp), one lane per point copy (pi <= 32), camera copies
+// (kappa <= 4) shared by the group in shared memory.  Each damped Gauss-Newton step
+// eliminates the points (3x3 per lane) and solves the reduced camera system (at most
+// 24 x 24, a Schur complement accumulated entry-parallel over the group's lanes) by a
+// lane-per-row Cholesky factorisation.  Consensus (Eqs. 10-11
 // over copies) and dual ascent (Eqs. 12-13) run in FP64 over copy lists.
 #include <cuda_runtime.h>
 
@@ -70,24 +71,33 @@ struct BlockProblem {
   int* err;                      // bit 0: non-finite copy
 };
 
-template <typename T>
-__device__ __forceinline__ T wsum(T v) {
+// A block's lane group: G consecutive lanes of a warp (G = 8, 16 or 32).  Every vote,
+// shuffle and barrier names the group's lanes only, so groups of one warp may diverge.
+template <int G>
+struct Grp {
+  int lane;       // lane in the warp: column of the per-lane shared arrays
+  int gl;         // lane in the group
+  int base;       // first warp lane of the group
+  unsigned mask;  // the group's lanes
+  __device__ explicit Grp(int warp_lane)
+      : lane(warp_lane), gl(warp_lane & (G - 1)), base(warp_lane & ~(G - 1)),
+        mask(G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (warp_lane & ~(G - 1)))) {}
+  __device__ void sync() const { __syncwarp(mask); }
+  template <typename T>
+  __device__ T sum(T v) const {
 #pragma unroll
-  for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
-  return v;
-}
+    for (int m = G / 2; m > 0; m >>= 1) v += __shfl_xor_sync(mask, v, m, G);
+    return v;
+  }
+  __device__ bool all(bool p) const { return __all_sync(mask, p); }
+  template <typename T>
+  __device__ T bcast(T v, int src) const { return __shfl_sync(mask, v, src, G); }
+};
 
-// Per-warp shared memory of one block solve; KC = the most cameras a block holds.
+// State of one block solve shared by its lane group; KC = the most cameras a block holds.
 template <typename T, int KC>
-struct BlkSmem {
+struct BlkShared {
   static constexpr int kU = 6 * KC;
-  static constexpr int kPairs = KC * (KC + 1) / 2;
-  // rows padded to 33 words: the reduction reads one lane's column across rows, which a
-  // 32-word row would put in a single bank
-  T lin[KC][kLin][33];        // each lane's observation slots: A = dz/dx (2x3), B = dz/dy (2x6), 2w, e
-  T U[KC][2][33];             // 2w A W_p g_p per slot
-  T Q[kPairs][4][33];         // per camera pair c1 <= c2: 2x2 weight of the point's Schur term
-  signed char slot[KC][32];   // slot of each lane's observation on camera c (-1: none)
   T S[kU][kU + 1];            // reduced camera system, then its Cholesky factor
   T rhs[kU];
   T g[kU];                    // camera part of the block gradient
@@ -98,6 +108,20 @@ struct BlkSmem {
   T a[KC][6];                 // camera scaled duals
 };
 
+// Per-warp shared memory: per-lane arrays (each lane one point copy of its group's block)
+// and the shared state of the warp's 32 / G blocks.
+template <typename T, int KC, int G>
+struct BlkSmem {
+  static constexpr int kPairs = KC * (KC + 1) / 2;
+  // rows padded to 33 words: the reduction reads one lane's column across rows, which a
+  // 32-word row would put in a single bank
+  T lin[KC][kLin][33];        // each lane's observation slots: A = dz/dx (2x3), B = dz/dy (2x6), 2w, e
+  T U[KC][2][33];             // 2w A W_p g_p per slot
+  T Q[kPairs][4][33];         // per camera pair c1 <= c2: 2x2 weight of the point's Schur term
+  signed char slot[KC][32];   // slot of each lane's observation on camera c (-1: none)
+  BlkShared<T, KC> grp[32 / G];
+};
+
 template <int KC>
 __device__ __forceinline__ int pair_index(int c1, int c2) {  // c1 <= c2
   return c1 * KC - c1 * (c1 - 1) / 2 + (c2 - c1);
@@ -106,10 +130,10 @@ __device__ __forceinline__ int pair_index(int c1, int c2) {  // c1 <= c2
 // Eq. (14) at (point offsets dp of this lane, camera offsets dc): misfits of the
 // lane's observations + its point's dual and penalty terms, summed over the warp,
 // plus the cameras' terms.  +inf when an observation is behind its camera.
-template <typename T, int KC>
-__device__ __forceinline__ T block_objective(const Prm<T>& q, bool act, int nob, const int oc[KC], const T oz0[KC],
-                                             const T oz1[KC], const T xbar[3], const T dp[3], const T ax[3],
-                                             const BlkSmem<T, KC>& W, const T (*dc)[6], int nc) {
+template <typename T, int KC, int G>
+__device__ __forceinline__ T block_objective(const Prm<T>& q, const Grp<G>& grp, bool act, int nob, const int oc[KC],
+                                             const T oz0[KC], const T oz1[KC], const T xbar[3], const T dp[3],
+                                             const T ax[3], const BlkShared<T, KC>& Z, const T (*dc)[6], int nc) {
   T s = 0;
   bool ok = true;
   if (act) {
@@ -121,7 +145,7 @@ __device__ __forceinline__ T block_objective(const Prm<T>& q, bool act, int nob,
 #pragma unroll
         for (int u = 0; u < 3; ++u) v[u] = xbar[u] + dp[u];
 #pragma unroll
-        for (int u = 0; u < 6; ++u) v[3 + u] = W.vbar[c][u] + dc[c][u];
+        for (int u = 0; u < 6; ++u) v[3 + u] = Z.vbar[c][u] + dc[c][u];
         Pose<T> P;
         pose_at(v, q.eps, P);
         if (!P.valid) {
@@ -137,22 +161,25 @@ __device__ __forceinline__ T block_objective(const Prm<T>& q, bool act, int nob,
 #pragma unroll
     for (int u = 0; u < 3; ++u) s += q.rho_x * dp[u] * (ax[u] + T(0.5) * dp[u]);
   }
-  s = wsum(s);
-  ok = __all_sync(0xffffffffu, ok);
+  s = grp.sum(s);
+  ok = grp.all(ok);
   T sc = 0;
   for (int c = 0; c < nc; ++c)
 #pragma unroll
-    for (int u = 0; u < 6; ++u) sc += q.rho(3 + u) * dc[c][u] * (W.a[c][u] + T(0.5) * dc[c][u]);
+    for (int u = 0; u < 6; ++u) sc += q.rho(3 + u) * dc[c][u] * (Z.a[c][u] + T(0.5) * dc[c][u]);
   return ok ? s + sc : Num<T>::inf();
 }
 
-template <typename T, int KC>
-__device__ void solve_block(const BlockProblem& B, const Prm<T>& q, const BlockInfo& bi, BlkSmem<T, KC>& W, int lane,
-                            int cur) {
+template <typename T, int KC, int G>
+__device__ void solve_block(const BlockProblem& B, const Prm<T>& q, const BlockInfo& bi, BlkSmem<T, KC, G>& W,
+                            const Grp<G>& grp, int cur) {
+  const int lane = grp.lane;  // column of the per-lane shared arrays
+  const int gl = grp.gl;      // lane in the group: point copy, row of the camera system
+  BlkShared<T, KC>& Z = W.grp[grp.base / G];
   using V2 = typename Num<T>::V2;
   const int np = bi.np, nc = bi.nc, n_u = 6 * nc;
-  const bool act = lane < np;
-  const long long pc = (long long)bi.p0 + lane;
+  const bool act = gl < np;
+  const long long pc = (long long)bi.p0 + gl;
   T* pdel = static_cast<T*>(B.pc_delta);
   T* cdel = static_cast<T*>(B.cc_delta);
   T xbar[3] = {0, 0, 0}, dp[3] = {0, 0, 0}, ax[3] = {0, 0, 0};
@@ -194,17 +221,17 @@ __device__ void solve_block(const BlockProblem& B, const Prm<T>& q, const BlockI
       if (k < nob && oc[k] == c) slot[c] = k;
     W.slot[c][lane] = (signed char)slot[c];
   }
-  if (lane < n_u) {
-    const int c = lane / 6, u = lane % 6;
+  if (gl < n_u) {
+    const int c = gl / 6, u = gl % 6;
     const long long cc = (long long)bi.c0 + c;
     const int j = B.cc_cam[cc];
-    W.vbar[c][u] = from_f64<T>(B.Y[cur][6 * (long long)j + u]);
-    W.d[c][u] = cdel[u * B.n_cc + cc];
-    W.a[c][u] = from_f64<T>(B.cc_a[u * B.n_cc + cc]);
+    Z.vbar[c][u] = from_f64<T>(B.Y[cur][6 * (long long)j + u]);
+    Z.d[c][u] = cdel[u * B.n_cc + cc];
+    Z.a[c][u] = from_f64<T>(B.cc_a[u * B.n_cc + cc]);
   }
-  __syncwarp();
+  grp.sync();
 
-  T L = block_objective<T, KC>(q, act, nob, oc, oz0, oz1, xbar, dp, ax, W, W.d, nc);
+  T L = block_objective<T, KC, G>(q, grp, act, nob, oc, oz0, oz1, xbar, dp, ax, Z, Z.d, nc);
   T lambda = T(-1);
   for (int step = 0; step < q.steps; ++step) {
     // linearise this lane's observations at the current copies
@@ -218,7 +245,7 @@ __device__ void solve_block(const BlockProblem& B, const Prm<T>& q, const BlockI
 #pragma unroll
         for (int u = 0; u < 3; ++u) v[u] = xbar[u] + dp[u];
 #pragma unroll
-        for (int u = 0; u < 6; ++u) v[3 + u] = W.vbar[c][u] + W.d[c][u];
+        for (int u = 0; u < 6; ++u) v[3 + u] = Z.vbar[c][u] + Z.d[c][u];
         Pose<T> P;
         pose_at(v, q.eps, P);
         T J0[9], J1[9], e0 = 0, e1 = 0, w = 0;
@@ -260,7 +287,7 @@ __device__ void solve_block(const BlockProblem& B, const Prm<T>& q, const BlockI
       for (int u = 0; u < 3; ++u) gp[u] += q.rho_x * (ax[u] + dp[u]);
     if (lambda < T(0)) {
       T tr = (act ? Hpp[0] + Hpp[3] + Hpp[5] + T(3) * q.rho_x : T(0)) + trc;
-      tr = wsum(tr);
+      tr = grp.sum(tr);
       for (int c = 0; c < nc; ++c)
 #pragma unroll
         for (int u = 0; u < 6; ++u) tr += q.rho(3 + u);
@@ -317,13 +344,13 @@ __device__ void solve_block(const BlockProblem& B, const Prm<T>& q, const BlockI
           W.Q[pr][3][lane] = dgw - sw * (a13 * x0 + a14 * x1 + a15 * x2);
         }
       }
-    __syncwarp();
+    grp.sync();
     // reduced camera system, one entry per lane at a time, summed over the block's points:
     //   S(c1 r, c2 s) = sum_p B_1[:, r]^T Q B_2[:, s],  g_c = -sum 2w B^T e + rho (a + d),
     //   rhs_c = sum_p B^T U - g_c
     const int nS = 21 * nc + 18 * nc * (nc - 1);
     const int nV = nS + 12 * nc;
-    for (int v = lane; v < nV; v += 32) {
+    for (int v = gl; v < nV; v += G) {
       T acc = 0;
       if (v < nS) {
         int c1 = 0, c2 = 0, e = v;
@@ -352,77 +379,79 @@ __device__ void solve_block(const BlockProblem& B, const Prm<T>& q, const BlockI
         }
         const int pr = pair_index<KC>(c1, c2);
         for (int l = 0; l < np; ++l) {
-          const int k1 = W.slot[c1][l], k2 = W.slot[c2][l];
+          const int lb = grp.base + l;
+          const int k1 = W.slot[c1][lb], k2 = W.slot[c2][lb];
           if (k1 >= 0 && k2 >= 0) {
-            const T b10 = W.lin[k1][6 + r][l], b11 = W.lin[k1][12 + r][l];
-            const T b20 = W.lin[k2][6 + s][l], b21 = W.lin[k2][12 + s][l];
-            acc += b10 * (W.Q[pr][0][l] * b20 + W.Q[pr][1][l] * b21) +
-                   b11 * (W.Q[pr][2][l] * b20 + W.Q[pr][3][l] * b21);
+            const T b10 = W.lin[k1][6 + r][lb], b11 = W.lin[k1][12 + r][lb];
+            const T b20 = W.lin[k2][6 + s][lb], b21 = W.lin[k2][12 + s][lb];
+            acc += b10 * (W.Q[pr][0][lb] * b20 + W.Q[pr][1][lb] * b21) +
+                   b11 * (W.Q[pr][2][lb] * b20 + W.Q[pr][3][lb] * b21);
           }
         }
-        W.S[6 * c1 + r][6 * c2 + s] = acc;
-        W.S[6 * c2 + s][6 * c1 + r] = acc;
+        Z.S[6 * c1 + r][6 * c2 + s] = acc;
+        Z.S[6 * c2 + s][6 * c1 + r] = acc;
       } else {
         const int w = v - nS, c = w / 12, u = w % 6;
         const bool isg = (w % 12) < 6;
         for (int l = 0; l < np; ++l) {
-          const int k = W.slot[c][l];
+          const int lb = grp.base + l;
+          const int k = W.slot[c][lb];
           if (k >= 0) {
-            const T b0 = W.lin[k][6 + u][l], b1 = W.lin[k][12 + u][l];
+            const T b0 = W.lin[k][6 + u][lb], b1 = W.lin[k][12 + u][lb];
             if (isg)
-              acc -= W.lin[k][18][l] * (b0 * W.lin[k][19][l] + b1 * W.lin[k][20][l]);
+              acc -= W.lin[k][18][lb] * (b0 * W.lin[k][19][lb] + b1 * W.lin[k][20][lb]);
             else
-              acc += b0 * W.U[k][0][l] + b1 * W.U[k][1][l];
+              acc += b0 * W.U[k][0][lb] + b1 * W.U[k][1][lb];
           }
         }
         if (isg)
-          W.g[6 * c + u] = acc + q.rho(3 + u) * (W.a[c][u] + W.d[c][u]);
+          Z.g[6 * c + u] = acc + q.rho(3 + u) * (Z.a[c][u] + Z.d[c][u]);
         else
-          W.rhs[6 * c + u] = acc;
+          Z.rhs[6 * c + u] = acc;
       }
     }
-    __syncwarp();
-    if (lane < n_u) {
-      W.rhs[lane] -= W.g[lane];
-      W.S[lane][lane] += q.rho(3 + lane % 6) + lambda;
+    grp.sync();
+    if (gl < n_u) {
+      Z.rhs[gl] -= Z.g[gl];
+      Z.S[gl][gl] += q.rho(3 + gl % 6) + lambda;
     }
-    __syncwarp();
+    grp.sync();
     // Cholesky S = L L^T, lane i owning row i
     bool spd = true;
     for (int k = 0; k < n_u; ++k) {
-      const T piv = W.S[k][k];
+      const T piv = Z.S[k][k];
       if (!(piv > T(0))) {
         spd = false;
         break;
       }
       const T lkk = Num<T>::sqrt_(piv);
-      if (lane > k && lane < n_u) W.S[lane][k] = Num<T>::div(W.S[lane][k], lkk);
-      __syncwarp();
-      if (lane == k) W.S[k][k] = lkk;
-      if (lane > k && lane < n_u) {
-        const T lik = W.S[lane][k];
-        for (int jj = k + 1; jj <= lane; ++jj) W.S[lane][jj] -= lik * W.S[jj][k];
+      if (gl > k && gl < n_u) Z.S[gl][k] = Num<T>::div(Z.S[gl][k], lkk);
+      grp.sync();
+      if (gl == k) Z.S[k][k] = lkk;
+      if (gl > k && gl < n_u) {
+        const T lik = Z.S[gl][k];
+        for (int jj = k + 1; jj <= gl; ++jj) Z.S[gl][jj] -= lik * Z.S[jj][k];
       }
-      __syncwarp();
+      grp.sync();
     }
     if (!spd) {
       lambda *= T(10);
       continue;
     }
     // L y = rhs, then L^T dy = y; lane i holds entry i
-    T y = lane < n_u ? W.rhs[lane] : T(0);
+    T y = gl < n_u ? Z.rhs[gl] : T(0);
     for (int k = 0; k < n_u; ++k) {
-      const T yk = Num<T>::div(__shfl_sync(0xffffffffu, y, k), W.S[k][k]);
-      if (lane == k) y = yk;
-      else if (lane > k && lane < n_u) y -= W.S[lane][k] * yk;
+      const T yk = Num<T>::div(grp.bcast(y, k), Z.S[k][k]);
+      if (gl == k) y = yk;
+      else if (gl > k && gl < n_u) y -= Z.S[gl][k] * yk;
     }
     for (int k = n_u - 1; k >= 0; --k) {
-      const T xk = Num<T>::div(__shfl_sync(0xffffffffu, y, k), W.S[k][k]);
-      if (lane == k) y = xk;
-      else if (lane < k) y -= W.S[k][lane] * xk;
+      const T xk = Num<T>::div(grp.bcast(y, k), Z.S[k][k]);
+      if (gl == k) y = xk;
+      else if (gl < k) y -= Z.S[k][gl] * xk;
     }
-    if (lane < n_u) W.dy[lane] = y;
-    __syncwarp();
+    if (gl < n_u) Z.dy[gl] = y;
+    grp.sync();
     // point step dx = -W_p (g_p + H_pc dy)
     T dx[3] = {0, 0, 0};
     if (act) {
@@ -434,8 +463,8 @@ __device__ void solve_block(const BlockProblem& B, const Prm<T>& q, const BlockI
           T r0 = 0, r1 = 0;
 #pragma unroll
           for (int u = 0; u < 6; ++u) {
-            r0 += W.lin[k][6 + u][lane] * W.dy[6 * c + u];
-            r1 += W.lin[k][12 + u][lane] * W.dy[6 * c + u];
+            r0 += W.lin[k][6 + u][lane] * Z.dy[6 * c + u];
+            r1 += W.lin[k][12 + u][lane] * Z.dy[6 * c + u];
           }
           const T tw = W.lin[k][18][lane];
           r0 *= tw;
@@ -450,34 +479,34 @@ __device__ void solve_block(const BlockProblem& B, const Prm<T>& q, const BlockI
       dx[2] = -(Wp[2] * t0 + Wp[4] * t1 + Wp[5] * t2);
     }
     // predicted decrease (lambda |d|^2 - g.d) / 2 and the rounding-noise bound
-    T gd = wsum(gp[0] * dx[0] + gp[1] * dx[1] + gp[2] * dx[2]);
-    T dd = wsum(dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2]);
+    T gd = grp.sum(gp[0] * dx[0] + gp[1] * dx[1] + gp[2] * dx[2]);
+    T dd = grp.sum(dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2]);
     for (int u = 0; u < n_u; ++u) {
-      gd += W.g[u] * W.dy[u];
-      dd += W.dy[u] * W.dy[u];
+      gd += Z.g[u] * Z.dy[u];
+      dd += Z.dy[u] * Z.dy[u];
     }
     const T pred = T(0.5) * (lambda * dd - gd);
-    const T noise_sum = wsum(noise);
+    const T noise_sum = grp.sum(noise);
     const bool trust = isfinite(L) && q.model_tol > T(0) &&
                        pred <= q.model_tol * Num<T>::unit_roundoff * (fabs(L) + noise_sum);
     T xt[3];
 #pragma unroll
     for (int u = 0; u < 3; ++u) xt[u] = dp[u] + dx[u];
-    if (lane < n_u) W.dt[lane / 6][lane % 6] = W.d[lane / 6][lane % 6] + W.dy[lane];
-    __syncwarp();
-    const T Lt = block_objective<T, KC>(q, act, nob, oc, oz0, oz1, xbar, xt, ax, W, W.dt, nc);
+    if (gl < n_u) Z.dt[gl / 6][gl % 6] = Z.d[gl / 6][gl % 6] + Z.dy[gl];
+    grp.sync();
+    const T Lt = block_objective<T, KC, G>(q, grp, act, nob, oc, oz0, oz1, xbar, xt, ax, Z, Z.dt, nc);
     const bool valid = Lt < Num<T>::inf();
     if (valid && (trust || Lt < L)) {
 #pragma unroll
       for (int u = 0; u < 3; ++u) dp[u] = xt[u];
-      if (lane < n_u) W.d[lane / 6][lane % 6] = W.dt[lane / 6][lane % 6];
+      if (gl < n_u) Z.d[gl / 6][gl % 6] = Z.dt[gl / 6][gl % 6];
       L = trust ? L - pred : Lt;
       const T lr = Num<T>::tenth(lambda);
       lambda = lr > q.lambda_min ? lr : q.lambda_min;
     } else {
       lambda *= T(10);
     }
-    __syncwarp();
+    grp.sync();
   }
   bool finite = true;
   if (act)
@@ -486,23 +515,29 @@ __device__ void solve_block(const BlockProblem& B, const Prm<T>& q, const BlockI
       pdel[u * B.n_pc + pc] = dp[u];
       finite = finite && isfinite(dp[u]);
     }
-  if (lane < n_u) {
-    const T v = W.d[lane / 6][lane % 6];
-    cdel[(lane % 6) * B.n_cc + bi.c0 + lane / 6] = v;
+  if (gl < n_u) {
+    const T v = Z.d[gl / 6][gl % 6];
+    cdel[(gl % 6) * B.n_cc + bi.c0 + gl / 6] = v;
     finite = finite && isfinite(v);
   }
   if (!finite) atomicOr(B.err, 1);
-  __syncwarp();
+  grp.sync();
 }
 
-template <typename T, int KC>
-__global__ void __launch_bounds__(kBlkWarps * 32) block_solve_kernel(BlockProblem B, Prm<T> q, int cur) {
+// Blocks [lo, hi) of one size class, each solved by a group of G lanes (32 / G groups
+// per warp, kBlkWarps warps per CTA); groups stride through the range independently.
+template <typename T, int KC, int G>
+__global__ void __launch_bounds__(kBlkWarps * 32)
+    block_solve_kernel(BlockProblem B, Prm<T> q, int cur, int lo, int hi) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  BlkSmem<T, KC>& W = reinterpret_cast<BlkSmem<T, KC>*>(smem_raw)[warp];
-  for (int b = blockIdx.x * kBlkWarps + warp; b < B.n_blocks; b += gridDim.x * kBlkWarps) {
+  constexpr int kPer = 32 / G;
+  const int warp = threadIdx.x >> 5;
+  const Grp<G> grp(threadIdx.x & 31);
+  BlkSmem<T, KC, G>& W = reinterpret_cast<BlkSmem<T, KC, G>*>(smem_raw)[warp];
+  const int stride = gridDim.x * kBlkWarps * kPer;
+  for (int b = lo + (blockIdx.x * kBlkWarps + warp) * kPer + grp.base / G; b < hi; b += stride) {
     const BlockInfo bi = B.blocks[b];
-    solve_block<T, KC>(B, q, bi, W, lane, cur);
+    solve_block<T, KC, G>(B, q, bi, W, grp, cur);
   }
 }
 
@@ -669,7 +704,7 @@ struct dba_block_ctx {
   bool has_problem = false;
   int cur = 0;
   long long iters = 0;
-  int grid = 0;
+  int cls[4] = {0, 0, 0, 0};  // block list cut into size classes: [cls[k], cls[k + 1])
   std::string err = "no error";
   // host copy of the layout (caller order <-> block order)
   std::vector<long long> blk_obs;  // block order -> caller observation
@@ -719,21 +754,20 @@ cudaError_t upload(dba_block_ctx* ctx, T** dst, const std::vector<T>& src) {
   return cudaMemcpyAsync(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice, ctx->stream);
 }
 
-template <typename T, int KC>
-cudaError_t launch_block_solve_kc(dba_block_ctx* ctx) {
-  const size_t smem = sizeof(dba::BlkSmem<T, KC>) * dba::kBlkWarps;
-  static std::atomic<bool> set{false};
-  if (!set) {
-    cudaError_t e = cudaFuncSetAttribute(dba::block_solve_kernel<T, KC>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    set = true;
-  }
-  if (!ctx->grid) {
+// Blocks [lo, hi) of one size class: lane groups of G, at most KC cameras per block.
+template <typename T, int KC, int G>
+cudaError_t launch_block_class(dba_block_ctx* ctx, int lo, int hi) {
+  if (hi <= lo) return cudaSuccess;
+  const size_t smem = sizeof(dba::BlkSmem<T, KC, G>) * dba::kBlkWarps;
+  static std::atomic<int> cached{0};  // CTAs of a full wave
+  int grid = cached.load();
+  if (!grid) {
     // resident CTAs per SM from the resources one CTA takes (registers, shared memory)
+    cudaError_t e = cudaFuncSetAttribute(dba::block_solve_kernel<T, KC, G>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncAttributes fa;
     int dev = 0, sms = 0, smem_sm = 0, smem_rsv = 0, regs_sm = 0;
-    cudaError_t e = cudaFuncGetAttributes(&fa, dba::block_solve_kernel<T, KC>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, dba::block_solve_kernel<T, KC, G>);
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
@@ -744,20 +778,28 @@ cudaError_t launch_block_solve_kc(dba_block_ctx* ctx) {
     int per_sm = 2048 / threads;
     per_sm = std::min(per_sm, regs_sm / std::max(1, (fa.numRegs + 7) / 8 * 8 * threads));
     per_sm = std::min(per_sm, smem_sm / ((int)smem + smem_rsv + (int)fa.sharedSizeBytes));
-    ctx->grid = std::max(per_sm, 1) * sms;
+    grid = std::max(per_sm, 1) * sms;
+    cached.store(grid);
   }
-  const int need = dba::blocks_of(ctx->B.n_blocks, dba::kBlkWarps);
-  const int g = std::max(1, std::min(need, ctx->grid));
-  dba::block_solve_kernel<T, KC><<<g, dba::kBlkWarps * 32, smem, ctx->stream>>>(
-      ctx->B, dba::make_prm<T>(ctx->prm), ctx->cur);
+  const int need = dba::blocks_of(hi - lo, dba::kBlkWarps * (32 / G));
+  const int g = std::max(1, std::min(need, grid));
+  dba::block_solve_kernel<T, KC, G><<<g, dba::kBlkWarps * 32, smem, ctx->stream>>>(
+      ctx->B, dba::make_prm<T>(ctx->prm), ctx->cur, lo, hi);
   return cudaGetLastError();
 }
 
+// The three size classes of the block list, in its order: one camera and at most 8
+// points (groups of 8 lanes), at most 2 cameras and 16 points (16 lanes), the rest (32).
 template <typename T>
 cudaError_t launch_block_solve(dba_block_ctx* ctx) {
-  if (ctx->kappa == 1) return launch_block_solve_kc<T, 1>(ctx);
-  if (ctx->kappa == 2) return launch_block_solve_kc<T, 2>(ctx);
-  return launch_block_solve_kc<T, 4>(ctx);
+  const int* c = ctx->cls;
+  cudaError_t e = launch_block_class<T, 1, 8>(ctx, c[0], c[1]);
+  if (e != cudaSuccess) return e;
+  e = ctx->kappa == 1 ? launch_block_class<T, 1, 16>(ctx, c[1], c[2]) : launch_block_class<T, 2, 16>(ctx, c[1], c[2]);
+  if (e != cudaSuccess) return e;
+  if (ctx->kappa == 1) return launch_block_class<T, 1, 32>(ctx, c[2], c[3]);
+  if (ctx->kappa == 2) return launch_block_class<T, 2, 32>(ctx, c[2], c[3]);
+  return launch_block_class<T, 4, 32>(ctx, c[2], c[3]);
 }
 
 // One iteration: block solves, consensus, dual ascent.  ev (nullable) receives an event
@@ -988,6 +1030,17 @@ dba_status dba_block_set_observations(dba_block_ctx* ctx, int32_t n_cams, int32_
     ctx->flops_step = 314.0 * (double)l + 228.0 * (double)l + 348.0 * pairs_off + 92.0 * (double)n_pc + per_block;
     ctx->flops_start = 64.0 * (double)l + 9.0 * (double)n_pc + 24.0 * (double)n_cc;
   }
+  // size classes of the solve kernel (lane groups of 8, 16, 32), each contiguous
+  {
+    auto cls_of = [](const dba::BlockInfo& b) { return b.nc == 1 && b.np <= 8 ? 0 : b.nc <= 2 && b.np <= 16 ? 1 : 2; };
+    std::stable_sort(blocks.begin(), blocks.end(),
+                     [&](const dba::BlockInfo& a, const dba::BlockInfo& b) { return cls_of(a) < cls_of(b); });
+    ctx->cls[0] = 0;
+    for (int k = 0; k < 3; ++k)
+      ctx->cls[k + 1] = (int)(std::partition_point(blocks.begin(), blocks.end(),
+                                                   [&](const dba::BlockInfo& b) { return cls_of(b) <= k; }) -
+                              blocks.begin());
+  }
   // copy lists per point and per camera (consensus)
   std::vector<int> pt_off(n + 1, 0), cam_off(m + 1, 0), pt_cp(n_pc), cam_cp(n_cc);
   for (long long k = 0; k < n_pc; ++k) ++pt_off[pc_pt[k] + 1];
@@ -1207,6 +1260,13 @@ dba_status dba_block_layout(const dba_block_ctx* ctx, int64_t* n_blocks, int64_t
   if (n_blocks) *n_blocks = ctx->B.n_blocks;
   if (n_point_copies) *n_point_copies = ctx->B.n_pc;
   if (n_camera_copies) *n_camera_copies = ctx->B.n_cc;
+  return DBA_OK;
+}
+
+dba_status dba_block_size_classes(const dba_block_ctx* ctx, int64_t* counts) {
+  if (!ctx || !counts) return DBA_EINVAL;
+  if (!ctx->has_problem) return DBA_ESTATE;
+  for (int k = 0; k < 3; ++k) counts[k] = ctx->cls[k + 1] - ctx->cls[k];
   return DBA_OK;
 }
 

@@ -29,7 +29,7 @@ EXPORTED = [
     "dba_mlp_loss_grad", "dba_mlp_train", "dba_mlp_predict", "dba_set_warm_start",
     "dba_block_create", "dba_block_set_observations", "dba_block_set_reference_pixels", "dba_block_iterate",
     "dba_block_iterate_until", "dba_block_profile", "dba_block_get_params", "dba_block_layout",
-    "dba_block_algorithmic_flops", "dba_block_last_error",
+    "dba_block_size_classes", "dba_block_algorithmic_flops", "dba_block_last_error",
     "dba_block_destroy",
 ]
 DBA_BLOCK_MAX_POINTS, DBA_BLOCK_MAX_CAMERAS = 32, 4
@@ -130,6 +130,7 @@ def load():
     L.dba_block_profile.argtypes = [vp, ctypes.c_int, dp]
     L.dba_block_get_params.argtypes = [vp, dp, dp]
     L.dba_block_layout.argtypes = [vp, P(ctypes.c_int64), P(ctypes.c_int64), P(ctypes.c_int64)]
+    L.dba_block_size_classes.argtypes = [vp, P(ctypes.c_int64)]
     L.dba_block_algorithmic_flops.argtypes = [vp, dp]
     L.dba_block_last_error.argtypes = [vp]
     L.dba_block_last_error.restype = ctypes.c_char_p
@@ -496,6 +497,13 @@ class BlockSolver:
         nb, npc, ncc = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
         self._check(load().dba_block_layout(self.ctx, ctypes.byref(nb), ctypes.byref(npc), ctypes.byref(ncc)))
         return {"n_blocks": nb.value, "n_point_copies": npc.value, "n_camera_copies": ncc.value}
+
+    def size_classes(self):
+        """Blocks per size class of the solve kernel (8-, 16-, 32-lane groups); each
+        nonempty class is one launch per iteration."""
+        c = (ctypes.c_int64 * 3)()
+        self._check(load().dba_block_size_classes(self.ctx, c))
+        return [c[0], c[1], c[2]]
 
     def algorithmic_flops(self):
         f = ctypes.c_double()

@@ -43,6 +43,7 @@ def block_sweep(n_pts=500000, pis=(1, 8, 32), kappas=(1, 2, 4), target=0.5, max_
         for kappa in kappas:
             with dba.BlockSolver(sc, pi, kappa, precision=prec) as s:
                 lay = s.layout()
+                lay["blocks_per_size_class"] = s.size_classes()
                 prof = s.profile(profile_iters)
             with dba.BlockSolver(sc, pi, kappa, precision=prec) as s:
                 m = s.iterate_until(max_iters, target)

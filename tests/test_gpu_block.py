@@ -29,7 +29,18 @@ def relerr(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
 
 
-@pytest.mark.parametrize("pi,kappa", [(1, 1), (8, 2), (32, 4), (5, 3), (32, 1)])
+def size_classes(layout):
+    """Blocks per size class of the solve kernel, recounted from the oracle's layout:
+    one camera and <= 8 points, <= 2 cameras and <= 16 points, the rest."""
+    npb, ncb = np.diff(layout.pc_off), np.diff(layout.cc_off)
+    c8 = (ncb == 1) & (npb <= 8)
+    c16 = ~c8 & (ncb <= 2) & (npb <= 16)
+    return [int(c8.sum()), int(c16.sum()), int((~c8 & ~c16).sum())]
+
+
+# together these put blocks in every (lane group, most cameras) kernel variant:
+# 8 lanes; 16 lanes with 1 and 2 cameras; 32 lanes with 1, 2 and 4 cameras
+@pytest.mark.parametrize("pi,kappa", [(1, 1), (8, 2), (32, 4), (5, 3), (32, 1), (32, 2)])
 def test_fp64_matches_block_oracle_per_iteration(pi, kappa):
     sc = S.scene1(n_pts=400, n_cams=16, seed=17)
     with dba.BlockSolver(sc, pi, kappa, precision=dba.DBA_PREC_F64) as s:
@@ -38,6 +49,7 @@ def test_fp64_matches_block_oracle_per_iteration(pi, kappa):
         lay = s.layout()
         assert lay == {"n_blocks": st.layout.n_blocks, "n_point_copies": st.layout.n_pc,
                        "n_camera_copies": st.layout.n_cc}
+        assert s.size_classes() == size_classes(st.layout)
         for it in range(6):
             mg = s.iterate(1)
             mo = st.iterate(cfg, 1)
