@@ -286,11 +286,11 @@ void dba_destroy(dba_ctx* ctx);
  * caller order, copied in.  Not thread-safe per context.
  * ------------------------------------------------------------------------- */
 typedef struct dba_block_ctx dba_block_ctx;
-#define DBA_BLOCK_MAX_POINTS 32
+#define DBA_BLOCK_MAX_POINTS 64
 #define DBA_BLOCK_MAX_CAMERAS 4
 
 /* Validates cfg as dba_create does (tile_obs, use_graph are ignored; local_solver
- * must be DBA_SOLVER_GN) and 1 <= block_points <= 32, 1 <= block_cams <= 4 (EINVAL). */
+ * must be DBA_SOLVER_GN) and 1 <= block_points <= 64, 1 <= block_cams <= 4 (EINVAL). */
 dba_status dba_block_create(const dba_config* cfg, int block_points, int block_cams, dba_block_ctx** out);
 /* Same arrays and checks as dba_set_observations, and a (point, camera) pair
  * may appear once (EINVAL); builds the blocks and starts with copies at the
@@ -316,9 +316,11 @@ dba_status dba_block_get_params(dba_block_ctx* ctx, double* cams_out, double* pt
 dba_status dba_block_layout(const dba_block_ctx* ctx, int64_t* n_blocks, int64_t* n_point_copies,
                             int64_t* n_camera_copies);
 /* Blocks in each size class of the solve kernel, in launch order: one camera and at
- * most 8 points (8-lane groups), at most 2 cameras and 16 points (16 lanes), the rest
- * (32 lanes).  Each nonempty class is one kernel launch per iteration.  counts: 3
- * entries, caller-owned. */
+ * most 8 points (8-lane groups), at most 2 cameras and 16 points (16 lanes), at most
+ * 32 points (32 lanes), the rest (32 lanes, two point copies each).  Each nonempty
+ * class is one kernel launch per iteration.  counts: DBA_BLOCK_SIZE_CLASSES entries,
+ * caller-owned. */
+#define DBA_BLOCK_SIZE_CLASSES 4
 dba_status dba_block_size_classes(const dba_block_ctx* ctx, int64_t* counts);
 /* Algorithmic floating-point operations of one iteration's block solves (every
  * Gauss-Newton step counted in full with its trial objective; add/mul 1, fma 2,

@@ -8,8 +8,8 @@
 // block per (point group, camera group) pair holding observations.
 //
 // GPU mapping: one group of G lanes per block (G = 8, 16 or 32 by the block's size,
-// several blocks per warp), one lane per point copy (pi <= 32), camera copies
-// (kappa <= 4) shared by the group in shared memory.  Each damped Gauss-Newton step
+// several blocks per warp), one lane per point copy (two per lane above 32 points;
+// pi <= 64), camera copies (kappa <= 4) shared by the group in shared memory.  Each damped Gauss-Newton step
 // eliminates the points (3x3 per lane) and solves the reduced camera system (at most
 // 24 x 24, a Schur complement accumulated entry-parallel over the group's lanes) by a
 // lane-per-row Cholesky factorisation.  Consensus (Eqs. 10-11
@@ -33,9 +33,8 @@
 namespace dba {
 namespace {
 
-constexpr int kBlkMaxCams = 4;
-constexpr int kBlkMaxU = 6 * kBlkMaxCams;
-constexpr int kBlkWarps = 4;  // blocks solved concurrently per CTA, one per warp
+constexpr int kBlkWarps = 4;  // most warps per CTA (fewer where shared memory would not hold them)
+constexpr int kBlkClasses = 4;
 constexpr int kLin = 21;      // per observation: A = dz/dx (2x3), B = dz/dy (2x6), 2w, e (2)
 
 struct BlockInfo {
@@ -108,17 +107,18 @@ struct BlkShared {
   T a[KC][6];                 // camera scaled duals
 };
 
-// Per-warp shared memory: per-lane arrays (each lane one point copy of its group's block)
-// and the shared state of the warp's 32 / G blocks.
-template <typename T, int KC, int G>
+// Per-warp shared memory: per-copy arrays (one column per point copy held by the warp:
+// 32 x PPL, padded) and the shared state of the warp's 32 / G blocks.
+template <typename T, int KC, int G, int PPL>
 struct BlkSmem {
   static constexpr int kPairs = KC * (KC + 1) / 2;
-  // rows padded to 33 words: the reduction reads one lane's column across rows, which a
-  // 32-word row would put in a single bank
-  T lin[KC][kLin][33];        // each lane's observation slots: A = dz/dx (2x3), B = dz/dy (2x6), 2w, e
-  T U[KC][2][33];             // 2w A W_p g_p per slot
-  T Q[kPairs][4][33];         // per camera pair c1 <= c2: 2x2 weight of the point's Schur term
-  signed char slot[KC][32];   // slot of each lane's observation on camera c (-1: none)
+  // rows padded by one word: the reduction reads one copy's column across rows, which an
+  // unpadded row of 32 words would put in a single bank
+  static constexpr int kCols = 32 * PPL + 1;
+  T lin[KC][kLin][kCols];     // each copy's observation slots: A = dz/dx (2x3), B = dz/dy (2x6), 2w, e
+  T U[KC][2][kCols];          // 2w A W_p g_p per slot
+  T Q[kPairs][4][kCols];      // per camera pair c1 <= c2: 2x2 weight of the point's Schur term
+  signed char slot[KC][32 * PPL];  // slot of each copy's observation on camera c (-1: none)
   BlkShared<T, KC> grp[32 / G];
 };
 
@@ -127,23 +127,37 @@ __device__ __forceinline__ int pair_index(int c1, int c2) {  // c1 <= c2
   return c1 * KC - c1 * (c1 - 1) / 2 + (c2 - c1);
 }
 
-// Eq. (14) at (point offsets dp of this lane, camera offsets dc): misfits of the
-// lane's observations + its point's dual and penalty terms, summed over the warp,
+// One point copy held by a lane: its consensus, offset and scaled dual, and its
+// observations in the block (at most one per camera).
+template <typename T, int KC>
+struct BlkPt {
+  bool act;          // the lane holds this copy
+  int nob;           // its observations
+  int oc[KC];        // local camera of observation k
+  int slot[KC];      // observation on local camera c (-1: none)
+  T oz0[KC], oz1[KC];
+  T xbar[3], ax[3];
+};
+
+// Eq. (14) at (point offsets dp of this lane's copies, camera offsets dc): misfits of
+// the lane's observations + its points' dual and penalty terms, summed over the group,
 // plus the cameras' terms.  +inf when an observation is behind its camera.
-template <typename T, int KC, int G>
-__device__ __forceinline__ T block_objective(const Prm<T>& q, const Grp<G>& grp, bool act, int nob, const int oc[KC],
-                                             const T oz0[KC], const T oz1[KC], const T xbar[3], const T dp[3],
-                                             const T ax[3], const BlkShared<T, KC>& Z, const T (*dc)[6], int nc) {
+template <typename T, int KC, int G, int PPL>
+__device__ __forceinline__ T block_objective(const Prm<T>& q, const Grp<G>& grp, const BlkPt<T, KC> (&pt)[PPL],
+                                             const T (&dp)[PPL][3], const BlkShared<T, KC>& Z, const T (*dc)[6],
+                                             int nc) {
   T s = 0;
   bool ok = true;
-  if (act) {
+#pragma unroll
+  for (int j = 0; j < PPL; ++j) {
+    if (!pt[j].act) continue;
 #pragma unroll
     for (int k = 0; k < KC; ++k) {
-      if (k < nob) {
-        const int c = oc[k];
+      if (k < pt[j].nob) {
+        const int c = pt[j].oc[k];
         T v[9];
 #pragma unroll
-        for (int u = 0; u < 3; ++u) v[u] = xbar[u] + dp[u];
+        for (int u = 0; u < 3; ++u) v[u] = pt[j].xbar[u] + dp[j][u];
 #pragma unroll
         for (int u = 0; u < 6; ++u) v[3 + u] = Z.vbar[c][u] + dc[c][u];
         Pose<T> P;
@@ -152,14 +166,14 @@ __device__ __forceinline__ T block_objective(const Prm<T>& q, const Grp<G>& grp,
           ok = false;
         } else {
           const T iz = Num<T>::rcp(P.p[2]);
-          const T e0 = oz0[k] - (q.focal * P.p[0] * iz + q.cx);
-          const T e1 = oz1[k] - (q.focal * P.p[1] * iz + q.cy);
+          const T e0 = pt[j].oz0[k] - (q.focal * P.p[0] * iz + q.cx);
+          const T e1 = pt[j].oz1[k] - (q.focal * P.p[1] * iz + q.cy);
           s += misfit<T>(q.loss, q.lp, e0 * e0 + e1 * e1);
         }
       }
     }
 #pragma unroll
-    for (int u = 0; u < 3; ++u) s += q.rho_x * dp[u] * (ax[u] + T(0.5) * dp[u]);
+    for (int u = 0; u < 3; ++u) s += q.rho_x * dp[j][u] * (pt[j].ax[u] + T(0.5) * dp[j][u]);
   }
   s = grp.sum(s);
   ok = grp.all(ok);
@@ -170,56 +184,65 @@ __device__ __forceinline__ T block_objective(const Prm<T>& q, const Grp<G>& grp,
   return ok ? s + sc : Num<T>::inf();
 }
 
-template <typename T, int KC, int G>
-__device__ void solve_block(const BlockProblem& B, const Prm<T>& q, const BlockInfo& bi, BlkSmem<T, KC, G>& W,
-                            const Grp<G>& grp, int cur) {
-  const int lane = grp.lane;  // column of the per-lane shared arrays
-  const int gl = grp.gl;      // lane in the group: point copy, row of the camera system
+// Point copy p of a block sits on group lane p % G, register slot p / G, shared-memory
+// column base + p (PPL = 2 only with G = 32, so a warp's columns never overlap).
+template <typename T, int KC, int G, int PPL>
+__device__ void solve_block(const BlockProblem& B, const Prm<T>& q, const BlockInfo& bi,
+                            BlkSmem<T, KC, G, PPL>& W, const Grp<G>& grp, int cur) {
+  static_assert(PPL == 1 || G == 32, "two point copies per lane need whole-warp groups");
+  static_assert(6 * KC <= G, "one lane per row of the reduced camera system");
+  const int gl = grp.gl;  // lane in the group: first point copy, row of the camera system
   BlkShared<T, KC>& Z = W.grp[grp.base / G];
   using V2 = typename Num<T>::V2;
   const int np = bi.np, nc = bi.nc, n_u = 6 * nc;
-  const bool act = gl < np;
-  const long long pc = (long long)bi.p0 + gl;
   T* pdel = static_cast<T*>(B.pc_delta);
   T* cdel = static_cast<T*>(B.cc_delta);
-  T xbar[3] = {0, 0, 0}, dp[3] = {0, 0, 0}, ax[3] = {0, 0, 0};
-  int nob = 0;
-  int oc[KC];
-  T oz0[KC], oz1[KC];
+  BlkPt<T, KC> pt[PPL];
+  T dp[PPL][3];
 #pragma unroll
-  for (int k = 0; k < KC; ++k) {
-    oc[k] = 0;
-    oz0[k] = oz1[k] = 0;
-  }
-  if (act) {
-    const int i = B.pc_pt[pc];
+  for (int j = 0; j < PPL; ++j) {
+    const int p = gl + G * j;
+    const int col = grp.base + p;
+    BlkPt<T, KC>& P = pt[j];
+    P.act = p < np;
+    P.nob = 0;
 #pragma unroll
-    for (int u = 0; u < 3; ++u) {
-      xbar[u] = from_f64<T>(B.X[cur][3 * (long long)i + u]);
-      dp[u] = pdel[u * B.n_pc + pc];
-      ax[u] = from_f64<T>(B.pc_a[u * B.n_pc + pc]);
+    for (int k = 0; k < KC; ++k) {
+      P.oc[k] = 0;
+      P.oz0[k] = P.oz1[k] = 0;
     }
-    const int ob0 = B.pc_obs[pc];
-    nob = B.pc_obs[pc + 1] - ob0;
-    const V2* zz = static_cast<const V2*>(B.z);
 #pragma unroll
-    for (int k = 0; k < KC; ++k)
-      if (k < nob) {
-        oc[k] = B.obs_lc[ob0 + k];
-        const V2 p = zz[ob0 + k];
-        oz0[k] = p.x;
-        oz1[k] = p.y;
+    for (int u = 0; u < 3; ++u) P.xbar[u] = dp[j][u] = P.ax[u] = 0;
+    if (P.act) {
+      const long long pc = (long long)bi.p0 + p;
+      const int i = B.pc_pt[pc];
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        P.xbar[u] = from_f64<T>(B.X[cur][3 * (long long)i + u]);
+        dp[j][u] = pdel[u * B.n_pc + pc];
+        P.ax[u] = from_f64<T>(B.pc_a[u * B.n_pc + pc]);
       }
-  }
-  // slot of this lane's observation on each camera of the block (-1: none)
-  int slot[KC];
+      const int ob0 = B.pc_obs[pc];
+      P.nob = B.pc_obs[pc + 1] - ob0;
+      const V2* zz = static_cast<const V2*>(B.z);
 #pragma unroll
-  for (int c = 0; c < KC; ++c) {
-    slot[c] = -1;
+      for (int k = 0; k < KC; ++k)
+        if (k < P.nob) {
+          P.oc[k] = B.obs_lc[ob0 + k];
+          const V2 z = zz[ob0 + k];
+          P.oz0[k] = z.x;
+          P.oz1[k] = z.y;
+        }
+    }
+    // slot of this copy's observation on each camera of the block (-1: none)
 #pragma unroll
-    for (int k = 0; k < KC; ++k)
-      if (k < nob && oc[k] == c) slot[c] = k;
-    W.slot[c][lane] = (signed char)slot[c];
+    for (int c = 0; c < KC; ++c) {
+      P.slot[c] = -1;
+#pragma unroll
+      for (int k = 0; k < KC; ++k)
+        if (k < P.nob && P.oc[k] == c) P.slot[c] = k;
+      W.slot[c][col] = (signed char)P.slot[c];
+    }
   }
   if (gl < n_u) {
     const int c = gl / 6, u = gl % 6;
@@ -231,62 +254,73 @@ __device__ void solve_block(const BlockProblem& B, const Prm<T>& q, const BlockI
   }
   grp.sync();
 
-  T L = block_objective<T, KC, G>(q, grp, act, nob, oc, oz0, oz1, xbar, dp, ax, Z, Z.d, nc);
+  T L = block_objective<T, KC, G, PPL>(q, grp, pt, dp, Z, Z.d, nc);
   T lambda = T(-1);
   for (int step = 0; step < q.steps; ++step) {
     // linearise this lane's observations at the current copies
-    T Hpp[6] = {0, 0, 0, 0, 0, 0}, gp[3] = {0, 0, 0};
+    T Hpp[PPL][6], gp[PPL][3];
     T noise = 0, trc = 0;
 #pragma unroll
-    for (int k = 0; k < KC; ++k) {
-      if (k < nob) {
-        const int c = oc[k];
-        T v[9];
+    for (int j = 0; j < PPL; ++j) {
+      const int col = grp.lane + 32 * j;
 #pragma unroll
-        for (int u = 0; u < 3; ++u) v[u] = xbar[u] + dp[u];
+      for (int u = 0; u < 6; ++u) Hpp[j][u] = 0;
 #pragma unroll
-        for (int u = 0; u < 6; ++u) v[3 + u] = Z.vbar[c][u] + Z.d[c][u];
-        Pose<T> P;
-        pose_at(v, q.eps, P);
-        T J0[9], J1[9], e0 = 0, e1 = 0, w = 0;
-        if (P.valid) {
-          linearize(P, oz0[k], oz1[k], q, J0, J1, e0, e1, w);
-        } else {
+      for (int u = 0; u < 3; ++u) gp[j][u] = 0;
 #pragma unroll
-          for (int u = 0; u < 9; ++u) J0[u] = J1[u] = 0;
+      for (int k = 0; k < KC; ++k) {
+        if (k < pt[j].nob) {
+          const int c = pt[j].oc[k];
+          T v[9];
+#pragma unroll
+          for (int u = 0; u < 3; ++u) v[u] = pt[j].xbar[u] + dp[j][u];
+#pragma unroll
+          for (int u = 0; u < 6; ++u) v[3 + u] = Z.vbar[c][u] + Z.d[c][u];
+          Pose<T> P;
+          pose_at(v, q.eps, P);
+          T J0[9], J1[9], e0 = 0, e1 = 0, w = 0;
+          if (P.valid) {
+            linearize(P, pt[j].oz0[k], pt[j].oz1[k], q, J0, J1, e0, e1, w);
+          } else {
+#pragma unroll
+            for (int u = 0; u < 9; ++u) J0[u] = J1[u] = 0;
+          }
+          const T tw = T(2) * w;
+#pragma unroll
+          for (int u = 0; u < 3; ++u) {
+            W.lin[k][u][col] = J0[u];
+            W.lin[k][3 + u][col] = J1[u];
+          }
+#pragma unroll
+          for (int u = 0; u < 6; ++u) {
+            W.lin[k][6 + u][col] = J0[3 + u];
+            W.lin[k][12 + u][col] = J1[3 + u];
+          }
+          W.lin[k][18][col] = tw;
+          W.lin[k][19][col] = e0;
+          W.lin[k][20][col] = e1;
+          Hpp[j][0] += tw * (J0[0] * J0[0] + J1[0] * J1[0]);
+          Hpp[j][1] += tw * (J0[0] * J0[1] + J1[0] * J1[1]);
+          Hpp[j][2] += tw * (J0[0] * J0[2] + J1[0] * J1[2]);
+          Hpp[j][3] += tw * (J0[1] * J0[1] + J1[1] * J1[1]);
+          Hpp[j][4] += tw * (J0[1] * J0[2] + J1[1] * J1[2]);
+          Hpp[j][5] += tw * (J0[2] * J0[2] + J1[2] * J1[2]);
+#pragma unroll
+          for (int u = 0; u < 3; ++u) gp[j][u] -= tw * (J0[u] * e0 + J1[u] * e1);
+#pragma unroll
+          for (int u = 3; u < 9; ++u) trc += tw * (J0[u] * J0[u] + J1[u] * J1[u]);
+          noise += tw * Num<T>::sqrt_(e0 * e0 + e1 * e1) * (fabs(pt[j].oz0[k]) + fabs(pt[j].oz1[k]));
         }
-        const T tw = T(2) * w;
-#pragma unroll
-        for (int u = 0; u < 3; ++u) {
-          W.lin[k][u][lane] = J0[u];
-          W.lin[k][3 + u][lane] = J1[u];
-        }
-#pragma unroll
-        for (int u = 0; u < 6; ++u) {
-          W.lin[k][6 + u][lane] = J0[3 + u];
-          W.lin[k][12 + u][lane] = J1[3 + u];
-        }
-        W.lin[k][18][lane] = tw;
-        W.lin[k][19][lane] = e0;
-        W.lin[k][20][lane] = e1;
-        Hpp[0] += tw * (J0[0] * J0[0] + J1[0] * J1[0]);
-        Hpp[1] += tw * (J0[0] * J0[1] + J1[0] * J1[1]);
-        Hpp[2] += tw * (J0[0] * J0[2] + J1[0] * J1[2]);
-        Hpp[3] += tw * (J0[1] * J0[1] + J1[1] * J1[1]);
-        Hpp[4] += tw * (J0[1] * J0[2] + J1[1] * J1[2]);
-        Hpp[5] += tw * (J0[2] * J0[2] + J1[2] * J1[2]);
-#pragma unroll
-        for (int u = 0; u < 3; ++u) gp[u] -= tw * (J0[u] * e0 + J1[u] * e1);
-#pragma unroll
-        for (int u = 3; u < 9; ++u) trc += tw * (J0[u] * J0[u] + J1[u] * J1[u]);
-        noise += tw * Num<T>::sqrt_(e0 * e0 + e1 * e1) * (fabs(oz0[k]) + fabs(oz1[k]));
       }
-    }
-    if (act)
+      if (pt[j].act)
 #pragma unroll
-      for (int u = 0; u < 3; ++u) gp[u] += q.rho_x * (ax[u] + dp[u]);
+        for (int u = 0; u < 3; ++u) gp[j][u] += q.rho_x * (pt[j].ax[u] + dp[j][u]);
+    }
     if (lambda < T(0)) {
-      T tr = (act ? Hpp[0] + Hpp[3] + Hpp[5] + T(3) * q.rho_x : T(0)) + trc;
+      T tr = trc;
+#pragma unroll
+      for (int j = 0; j < PPL; ++j)
+        if (pt[j].act) tr += Hpp[j][0] + Hpp[j][3] + Hpp[j][5] + T(3) * q.rho_x;
       tr = grp.sum(tr);
       for (int c = 0; c < nc; ++c)
 #pragma unroll
@@ -294,56 +328,64 @@ __device__ void solve_block(const BlockProblem& B, const Prm<T>& q, const BlockI
       lambda = q.lambda0 * tr / T(3 * np + n_u);
     }
     // W_p = (H_pp + (rho_x + lambda) I)^-1 by cofactors (symmetric positive definite)
-    T Wp[6] = {1, 0, 0, 1, 0, 1};
-    if (act) {
-      const T dg = q.rho_x + lambda;
-      const T h00 = Hpp[0] + dg, h01 = Hpp[1], h02 = Hpp[2], h11 = Hpp[3] + dg, h12 = Hpp[4], h22 = Hpp[5] + dg;
-      const T c00 = h11 * h22 - h12 * h12, c01 = h02 * h12 - h01 * h22, c02 = h01 * h12 - h02 * h11;
-      const T c11 = h00 * h22 - h02 * h02, c12 = h01 * h02 - h00 * h12, c22 = h00 * h11 - h01 * h01;
-      const T idet = Num<T>::rcp(h00 * c00 + h01 * c01 + h02 * c02);
-      Wp[0] = c00 * idet;
-      Wp[1] = c01 * idet;
-      Wp[2] = c02 * idet;
-      Wp[3] = c11 * idet;
-      Wp[4] = c12 * idet;
-      Wp[5] = c22 * idet;
-    }
-    const T Wg0 = Wp[0] * gp[0] + Wp[1] * gp[1] + Wp[2] * gp[2];
-    const T Wg1 = Wp[1] * gp[0] + Wp[3] * gp[1] + Wp[4] * gp[2];
-    const T Wg2 = Wp[2] * gp[0] + Wp[4] * gp[1] + Wp[5] * gp[2];
-    // this point's terms of the reduced system: U_k = 2w_k A_k W_p g_p and, per camera
-    // pair, Q = [c1 = c2] 2w_1 I - (2w_1 A_1) W_p (2w_2 A_2)^T
+    T Wp[PPL][6];
 #pragma unroll
-    for (int k = 0; k < KC; ++k)
-      if (k < nob) {
-        const T tw = W.lin[k][18][lane];
-        W.U[k][0][lane] = tw * (W.lin[k][0][lane] * Wg0 + W.lin[k][1][lane] * Wg1 + W.lin[k][2][lane] * Wg2);
-        W.U[k][1][lane] = tw * (W.lin[k][3][lane] * Wg0 + W.lin[k][4][lane] * Wg1 + W.lin[k][5][lane] * Wg2);
+    for (int j = 0; j < PPL; ++j) {
+      const int col = grp.lane + 32 * j;
+      Wp[j][0] = 1, Wp[j][1] = 0, Wp[j][2] = 0, Wp[j][3] = 1, Wp[j][4] = 0, Wp[j][5] = 1;
+      if (pt[j].act) {
+        const T dg = q.rho_x + lambda;
+        const T h00 = Hpp[j][0] + dg, h01 = Hpp[j][1], h02 = Hpp[j][2], h11 = Hpp[j][3] + dg, h12 = Hpp[j][4],
+                h22 = Hpp[j][5] + dg;
+        const T c00 = h11 * h22 - h12 * h12, c01 = h02 * h12 - h01 * h22, c02 = h01 * h12 - h02 * h11;
+        const T c11 = h00 * h22 - h02 * h02, c12 = h01 * h02 - h00 * h12, c22 = h00 * h11 - h01 * h01;
+        const T idet = Num<T>::rcp(h00 * c00 + h01 * c01 + h02 * c02);
+        Wp[j][0] = c00 * idet;
+        Wp[j][1] = c01 * idet;
+        Wp[j][2] = c02 * idet;
+        Wp[j][3] = c11 * idet;
+        Wp[j][4] = c12 * idet;
+        Wp[j][5] = c22 * idet;
       }
+      const T* w6 = Wp[j];
+      const T* g3 = gp[j];
+      const T Wg0 = w6[0] * g3[0] + w6[1] * g3[1] + w6[2] * g3[2];
+      const T Wg1 = w6[1] * g3[0] + w6[3] * g3[1] + w6[4] * g3[2];
+      const T Wg2 = w6[2] * g3[0] + w6[4] * g3[1] + w6[5] * g3[2];
+      // this point's terms of the reduced system: U_k = 2w_k A_k W_p g_p and, per camera
+      // pair, Q = [c1 = c2] 2w_1 I - (2w_1 A_1) W_p (2w_2 A_2)^T
 #pragma unroll
-    for (int c1 = 0; c1 < KC; ++c1)
-#pragma unroll
-      for (int c2 = c1; c2 < KC; ++c2) {
-        const int k1 = slot[c1], k2 = slot[c2];
-        if (act && k1 >= 0 && k2 >= 0) {
-          const T tw1 = W.lin[k1][18][lane], tw2 = W.lin[k2][18][lane];
-          const T a20 = W.lin[k2][0][lane], a21 = W.lin[k2][1][lane], a22 = W.lin[k2][2][lane];
-          const T a23 = W.lin[k2][3][lane], a24 = W.lin[k2][4][lane], a25 = W.lin[k2][5][lane];
-          // columns of W_p A_2^T
-          const T w0 = Wp[0] * a20 + Wp[1] * a21 + Wp[2] * a22, w1 = Wp[1] * a20 + Wp[3] * a21 + Wp[4] * a22,
-                  w2 = Wp[2] * a20 + Wp[4] * a21 + Wp[5] * a22;
-          const T x0 = Wp[0] * a23 + Wp[1] * a24 + Wp[2] * a25, x1 = Wp[1] * a23 + Wp[3] * a24 + Wp[4] * a25,
-                  x2 = Wp[2] * a23 + Wp[4] * a24 + Wp[5] * a25;
-          const T a10 = W.lin[k1][0][lane], a11 = W.lin[k1][1][lane], a12 = W.lin[k1][2][lane];
-          const T a13 = W.lin[k1][3][lane], a14 = W.lin[k1][4][lane], a15 = W.lin[k1][5][lane];
-          const T sw = tw1 * tw2, dgw = c1 == c2 ? tw1 : T(0);
-          const int pr = pair_index<KC>(c1, c2);
-          W.Q[pr][0][lane] = dgw - sw * (a10 * w0 + a11 * w1 + a12 * w2);
-          W.Q[pr][1][lane] = -sw * (a10 * x0 + a11 * x1 + a12 * x2);
-          W.Q[pr][2][lane] = -sw * (a13 * w0 + a14 * w1 + a15 * w2);
-          W.Q[pr][3][lane] = dgw - sw * (a13 * x0 + a14 * x1 + a15 * x2);
+      for (int k = 0; k < KC; ++k)
+        if (k < pt[j].nob) {
+          const T tw = W.lin[k][18][col];
+          W.U[k][0][col] = tw * (W.lin[k][0][col] * Wg0 + W.lin[k][1][col] * Wg1 + W.lin[k][2][col] * Wg2);
+          W.U[k][1][col] = tw * (W.lin[k][3][col] * Wg0 + W.lin[k][4][col] * Wg1 + W.lin[k][5][col] * Wg2);
         }
-      }
+#pragma unroll
+      for (int c1 = 0; c1 < KC; ++c1)
+#pragma unroll
+        for (int c2 = c1; c2 < KC; ++c2) {
+          const int k1 = pt[j].slot[c1], k2 = pt[j].slot[c2];
+          if (pt[j].act && k1 >= 0 && k2 >= 0) {
+            const T tw1 = W.lin[k1][18][col], tw2 = W.lin[k2][18][col];
+            const T a20 = W.lin[k2][0][col], a21 = W.lin[k2][1][col], a22 = W.lin[k2][2][col];
+            const T a23 = W.lin[k2][3][col], a24 = W.lin[k2][4][col], a25 = W.lin[k2][5][col];
+            // columns of W_p A_2^T
+            const T w0 = w6[0] * a20 + w6[1] * a21 + w6[2] * a22, w1 = w6[1] * a20 + w6[3] * a21 + w6[4] * a22,
+                    w2 = w6[2] * a20 + w6[4] * a21 + w6[5] * a22;
+            const T x0 = w6[0] * a23 + w6[1] * a24 + w6[2] * a25, x1 = w6[1] * a23 + w6[3] * a24 + w6[4] * a25,
+                    x2 = w6[2] * a23 + w6[4] * a24 + w6[5] * a25;
+            const T a10 = W.lin[k1][0][col], a11 = W.lin[k1][1][col], a12 = W.lin[k1][2][col];
+            const T a13 = W.lin[k1][3][col], a14 = W.lin[k1][4][col], a15 = W.lin[k1][5][col];
+            const T sw = tw1 * tw2, dgw = c1 == c2 ? tw1 : T(0);
+            const int pr = pair_index<KC>(c1, c2);
+            W.Q[pr][0][col] = dgw - sw * (a10 * w0 + a11 * w1 + a12 * w2);
+            W.Q[pr][1][col] = -sw * (a10 * x0 + a11 * x1 + a12 * x2);
+            W.Q[pr][2][col] = -sw * (a13 * w0 + a14 * w1 + a15 * w2);
+            W.Q[pr][3][col] = dgw - sw * (a13 * x0 + a14 * x1 + a15 * x2);
+          }
+        }
+    }
     grp.sync();
     // reduced camera system, one entry per lane at a time, summed over the block's points:
     //   S(c1 r, c2 s) = sum_p B_1[:, r]^T Q B_2[:, s],  g_c = -sum 2w B^T e + rho (a + d),
@@ -452,35 +494,44 @@ __device__ void solve_block(const BlockProblem& B, const Prm<T>& q, const BlockI
     }
     if (gl < n_u) Z.dy[gl] = y;
     grp.sync();
-    // point step dx = -W_p (g_p + H_pc dy)
-    T dx[3] = {0, 0, 0};
-    if (act) {
-      T t0 = gp[0], t1 = gp[1], t2 = gp[2];
+    // point steps dx = -W_p (g_p + H_pc dy); predicted decrease (lambda |d|^2 - g.d) / 2
+    T xt[PPL][3];
+    T gd = 0, dd = 0;
 #pragma unroll
-      for (int k = 0; k < KC; ++k) {
-        if (k < nob) {
-          const int c = oc[k];
-          T r0 = 0, r1 = 0;
+    for (int j = 0; j < PPL; ++j) {
+      const int col = grp.lane + 32 * j;
+      T dx[3] = {0, 0, 0};
+      if (pt[j].act) {
+        T t0 = gp[j][0], t1 = gp[j][1], t2 = gp[j][2];
 #pragma unroll
-          for (int u = 0; u < 6; ++u) {
-            r0 += W.lin[k][6 + u][lane] * Z.dy[6 * c + u];
-            r1 += W.lin[k][12 + u][lane] * Z.dy[6 * c + u];
+        for (int k = 0; k < KC; ++k) {
+          if (k < pt[j].nob) {
+            const int c = pt[j].oc[k];
+            T r0 = 0, r1 = 0;
+#pragma unroll
+            for (int u = 0; u < 6; ++u) {
+              r0 += W.lin[k][6 + u][col] * Z.dy[6 * c + u];
+              r1 += W.lin[k][12 + u][col] * Z.dy[6 * c + u];
+            }
+            const T tw = W.lin[k][18][col];
+            r0 *= tw;
+            r1 *= tw;
+            t0 += W.lin[k][0][col] * r0 + W.lin[k][3][col] * r1;
+            t1 += W.lin[k][1][col] * r0 + W.lin[k][4][col] * r1;
+            t2 += W.lin[k][2][col] * r0 + W.lin[k][5][col] * r1;
           }
-          const T tw = W.lin[k][18][lane];
-          r0 *= tw;
-          r1 *= tw;
-          t0 += W.lin[k][0][lane] * r0 + W.lin[k][3][lane] * r1;
-          t1 += W.lin[k][1][lane] * r0 + W.lin[k][4][lane] * r1;
-          t2 += W.lin[k][2][lane] * r0 + W.lin[k][5][lane] * r1;
         }
+        dx[0] = -(Wp[j][0] * t0 + Wp[j][1] * t1 + Wp[j][2] * t2);
+        dx[1] = -(Wp[j][1] * t0 + Wp[j][3] * t1 + Wp[j][4] * t2);
+        dx[2] = -(Wp[j][2] * t0 + Wp[j][4] * t1 + Wp[j][5] * t2);
       }
-      dx[0] = -(Wp[0] * t0 + Wp[1] * t1 + Wp[2] * t2);
-      dx[1] = -(Wp[1] * t0 + Wp[3] * t1 + Wp[4] * t2);
-      dx[2] = -(Wp[2] * t0 + Wp[4] * t1 + Wp[5] * t2);
+      gd += gp[j][0] * dx[0] + gp[j][1] * dx[1] + gp[j][2] * dx[2];
+      dd += dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2];
+#pragma unroll
+      for (int u = 0; u < 3; ++u) xt[j][u] = dp[j][u] + dx[u];
     }
-    // predicted decrease (lambda |d|^2 - g.d) / 2 and the rounding-noise bound
-    T gd = grp.sum(gp[0] * dx[0] + gp[1] * dx[1] + gp[2] * dx[2]);
-    T dd = grp.sum(dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2]);
+    gd = grp.sum(gd);
+    dd = grp.sum(dd);
     for (int u = 0; u < n_u; ++u) {
       gd += Z.g[u] * Z.dy[u];
       dd += Z.dy[u] * Z.dy[u];
@@ -489,16 +540,15 @@ __device__ void solve_block(const BlockProblem& B, const Prm<T>& q, const BlockI
     const T noise_sum = grp.sum(noise);
     const bool trust = isfinite(L) && q.model_tol > T(0) &&
                        pred <= q.model_tol * Num<T>::unit_roundoff * (fabs(L) + noise_sum);
-    T xt[3];
-#pragma unroll
-    for (int u = 0; u < 3; ++u) xt[u] = dp[u] + dx[u];
     if (gl < n_u) Z.dt[gl / 6][gl % 6] = Z.d[gl / 6][gl % 6] + Z.dy[gl];
     grp.sync();
-    const T Lt = block_objective<T, KC, G>(q, grp, act, nob, oc, oz0, oz1, xbar, xt, ax, Z, Z.dt, nc);
+    const T Lt = block_objective<T, KC, G, PPL>(q, grp, pt, xt, Z, Z.dt, nc);
     const bool valid = Lt < Num<T>::inf();
     if (valid && (trust || Lt < L)) {
 #pragma unroll
-      for (int u = 0; u < 3; ++u) dp[u] = xt[u];
+      for (int j = 0; j < PPL; ++j)
+#pragma unroll
+        for (int u = 0; u < 3; ++u) dp[j][u] = xt[j][u];
       if (gl < n_u) Z.d[gl / 6][gl % 6] = Z.dt[gl / 6][gl % 6];
       L = trust ? L - pred : Lt;
       const T lr = Num<T>::tenth(lambda);
@@ -509,11 +559,15 @@ __device__ void solve_block(const BlockProblem& B, const Prm<T>& q, const BlockI
     grp.sync();
   }
   bool finite = true;
-  if (act)
 #pragma unroll
-    for (int u = 0; u < 3; ++u) {
-      pdel[u * B.n_pc + pc] = dp[u];
-      finite = finite && isfinite(dp[u]);
+  for (int j = 0; j < PPL; ++j)
+    if (pt[j].act) {
+      const long long pc = (long long)bi.p0 + gl + G * j;
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        pdel[u * B.n_pc + pc] = dp[j][u];
+        finite = finite && isfinite(dp[j][u]);
+      }
     }
   if (gl < n_u) {
     const T v = Z.d[gl / 6][gl % 6];
@@ -524,20 +578,28 @@ __device__ void solve_block(const BlockProblem& B, const Prm<T>& q, const BlockI
   grp.sync();
 }
 
-// Blocks [lo, hi) of one size class, each solved by a group of G lanes (32 / G groups
-// per warp, kBlkWarps warps per CTA); groups stride through the range independently.
-template <typename T, int KC, int G>
-__global__ void __launch_bounds__(kBlkWarps * 32)
+// Blocks [lo, hi) of one size class, each solved by a group of G lanes holding PPL
+// point copies each (32 / G groups per warp, blockDim.x / 32 warps per CTA); groups
+// stride through the range independently.
+// Resident CTAs per SM the register allocation is held to (4 warps each): the FP32
+// one-camera variants fit in 72 registers a thread, the two-camera ones in 96.
+template <typename T, int KC, int PPL>
+constexpr int blk_min_ctas() {
+  return sizeof(T) > 4 || PPL > 1 ? 1 : KC == 1 ? 7 : KC == 2 ? 5 : 1;
+}
+
+template <typename T, int KC, int G, int PPL>
+__global__ void __launch_bounds__(kBlkWarps * 32, (blk_min_ctas<T, KC, PPL>()))
     block_solve_kernel(BlockProblem B, Prm<T> q, int cur, int lo, int hi) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int kPer = 32 / G;
-  const int warp = threadIdx.x >> 5;
+  const int warps = blockDim.x >> 5, warp = threadIdx.x >> 5;
   const Grp<G> grp(threadIdx.x & 31);
-  BlkSmem<T, KC, G>& W = reinterpret_cast<BlkSmem<T, KC, G>*>(smem_raw)[warp];
-  const int stride = gridDim.x * kBlkWarps * kPer;
-  for (int b = lo + (blockIdx.x * kBlkWarps + warp) * kPer + grp.base / G; b < hi; b += stride) {
+  BlkSmem<T, KC, G, PPL>& W = reinterpret_cast<BlkSmem<T, KC, G, PPL>*>(smem_raw)[warp];
+  const int stride = gridDim.x * warps * kPer;
+  for (int b = lo + (blockIdx.x * warps + warp) * kPer + grp.base / G; b < hi; b += stride) {
     const BlockInfo bi = B.blocks[b];
-    solve_block<T, KC, G>(B, q, bi, W, grp, cur);
+    solve_block<T, KC, G, PPL>(B, q, bi, W, grp, cur);
   }
 }
 
@@ -704,7 +766,7 @@ struct dba_block_ctx {
   bool has_problem = false;
   int cur = 0;
   long long iters = 0;
-  int cls[4] = {0, 0, 0, 0};  // block list cut into size classes: [cls[k], cls[k + 1])
+  int cls[dba::kBlkClasses + 1] = {};  // block list cut into size classes: [cls[k], cls[k + 1])
   std::string err = "no error";
   // host copy of the layout (caller order <-> block order)
   std::vector<long long> blk_obs;  // block order -> caller observation
@@ -754,52 +816,66 @@ cudaError_t upload(dba_block_ctx* ctx, T** dst, const std::vector<T>& src) {
   return cudaMemcpyAsync(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice, ctx->stream);
 }
 
-// Blocks [lo, hi) of one size class: lane groups of G, at most KC cameras per block.
-template <typename T, int KC, int G>
+// Blocks [lo, hi) of one size class: lane groups of G with PPL point copies per lane,
+// at most KC cameras per block.
+template <typename T, int KC, int G, int PPL>
 cudaError_t launch_block_class(dba_block_ctx* ctx, int lo, int hi) {
   if (hi <= lo) return cudaSuccess;
-  const size_t smem = sizeof(dba::BlkSmem<T, KC, G>) * dba::kBlkWarps;
+  using Smem = dba::BlkSmem<T, KC, G, PPL>;
+  constexpr int kWarps = sizeof(Smem) * dba::kBlkWarps <= 200 * 1024 ? dba::kBlkWarps : 2;
+  static_assert(sizeof(Smem) * kWarps <= 220 * 1024, "block solve shared memory");
+  const size_t smem = sizeof(Smem) * kWarps;
   static std::atomic<int> cached{0};  // CTAs of a full wave
   int grid = cached.load();
   if (!grid) {
     // resident CTAs per SM from the resources one CTA takes (registers, shared memory)
-    cudaError_t e = cudaFuncSetAttribute(dba::block_solve_kernel<T, KC, G>,
+    cudaError_t e = cudaFuncSetAttribute(dba::block_solve_kernel<T, KC, G, PPL>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaFuncAttributes fa;
     int dev = 0, sms = 0, smem_sm = 0, smem_rsv = 0, regs_sm = 0;
-    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, dba::block_solve_kernel<T, KC, G>);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, dba::block_solve_kernel<T, KC, G, PPL>);
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_rsv, cudaDevAttrReservedSharedMemoryPerBlock, dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
     if (e != cudaSuccess) return e;
-    const int threads = dba::kBlkWarps * 32;
+    const int threads = kWarps * 32;
     int per_sm = 2048 / threads;
     per_sm = std::min(per_sm, regs_sm / std::max(1, (fa.numRegs + 7) / 8 * 8 * threads));
     per_sm = std::min(per_sm, smem_sm / ((int)smem + smem_rsv + (int)fa.sharedSizeBytes));
     grid = std::max(per_sm, 1) * sms;
     cached.store(grid);
   }
-  const int need = dba::blocks_of(hi - lo, dba::kBlkWarps * (32 / G));
+  const int need = dba::blocks_of(hi - lo, kWarps * (32 / G));
   const int g = std::max(1, std::min(need, grid));
-  dba::block_solve_kernel<T, KC, G><<<g, dba::kBlkWarps * 32, smem, ctx->stream>>>(
+  dba::block_solve_kernel<T, KC, G, PPL><<<g, kWarps * 32, smem, ctx->stream>>>(
       ctx->B, dba::make_prm<T>(ctx->prm), ctx->cur, lo, hi);
   return cudaGetLastError();
 }
 
-// The three size classes of the block list, in its order: one camera and at most 8
-// points (groups of 8 lanes), at most 2 cameras and 16 points (16 lanes), the rest (32).
+template <typename T, int G, int PPL>
+cudaError_t launch_block_class_kc(dba_block_ctx* ctx, int k) {
+  const int lo = ctx->cls[k], hi = ctx->cls[k + 1];
+  if (ctx->kappa == 1) return launch_block_class<T, 1, G, PPL>(ctx, lo, hi);
+  if constexpr (G == 16) {  // the 16-lane class holds at most 2 cameras
+    return launch_block_class<T, 2, G, PPL>(ctx, lo, hi);
+  } else {
+    if (ctx->kappa == 2) return launch_block_class<T, 2, G, PPL>(ctx, lo, hi);
+    return launch_block_class<T, 4, G, PPL>(ctx, lo, hi);
+  }
+}
+
+// The size classes of the block list, in its order: one camera and at most 8 points
+// (groups of 8 lanes), at most 2 cameras and 16 points (16 lanes), at most 32 points
+// (32 lanes), the rest (32 lanes holding two point copies each).
 template <typename T>
 cudaError_t launch_block_solve(dba_block_ctx* ctx) {
-  const int* c = ctx->cls;
-  cudaError_t e = launch_block_class<T, 1, 8>(ctx, c[0], c[1]);
-  if (e != cudaSuccess) return e;
-  e = ctx->kappa == 1 ? launch_block_class<T, 1, 16>(ctx, c[1], c[2]) : launch_block_class<T, 2, 16>(ctx, c[1], c[2]);
-  if (e != cudaSuccess) return e;
-  if (ctx->kappa == 1) return launch_block_class<T, 1, 32>(ctx, c[2], c[3]);
-  if (ctx->kappa == 2) return launch_block_class<T, 2, 32>(ctx, c[2], c[3]);
-  return launch_block_class<T, 4, 32>(ctx, c[2], c[3]);
+  cudaError_t e = launch_block_class<T, 1, 8, 1>(ctx, ctx->cls[0], ctx->cls[1]);
+  if (e == cudaSuccess) e = launch_block_class_kc<T, 16, 1>(ctx, 1);
+  if (e == cudaSuccess) e = launch_block_class_kc<T, 32, 1>(ctx, 2);
+  if (e == cudaSuccess) e = launch_block_class_kc<T, 32, 2>(ctx, 3);
+  return e;
 }
 
 // One iteration: block solves, consensus, dual ascent.  ev (nullable) receives an event
@@ -884,7 +960,7 @@ dba_status dba_block_create(const dba_config* cfg, int block_points, int block_c
   }
   if (block_points < 1 || block_points > DBA_BLOCK_MAX_POINTS || block_cams < 1 ||
       block_cams > DBA_BLOCK_MAX_CAMERAS) {
-    g_block_error = "dba_block_create: block_points must be in [1, 32] and block_cams in [1, 4]";
+    g_block_error = "dba_block_create: block_points must be in [1, 64] and block_cams in [1, 4]";
     return DBA_EINVAL;
   }
   cudaError_t e = cudaFree(nullptr);
@@ -1030,13 +1106,16 @@ dba_status dba_block_set_observations(dba_block_ctx* ctx, int32_t n_cams, int32_
     ctx->flops_step = 314.0 * (double)l + 228.0 * (double)l + 348.0 * pairs_off + 92.0 * (double)n_pc + per_block;
     ctx->flops_start = 64.0 * (double)l + 9.0 * (double)n_pc + 24.0 * (double)n_cc;
   }
-  // size classes of the solve kernel (lane groups of 8, 16, 32), each contiguous
+  // size classes of the solve kernel (lane groups of 8, 16, 32, 32 with two copies per
+  // lane), each contiguous
   {
-    auto cls_of = [](const dba::BlockInfo& b) { return b.nc == 1 && b.np <= 8 ? 0 : b.nc <= 2 && b.np <= 16 ? 1 : 2; };
+    auto cls_of = [](const dba::BlockInfo& b) {
+      return b.nc == 1 && b.np <= 8 ? 0 : b.nc <= 2 && b.np <= 16 ? 1 : b.np <= 32 ? 2 : 3;
+    };
     std::stable_sort(blocks.begin(), blocks.end(),
                      [&](const dba::BlockInfo& a, const dba::BlockInfo& b) { return cls_of(a) < cls_of(b); });
     ctx->cls[0] = 0;
-    for (int k = 0; k < 3; ++k)
+    for (int k = 0; k < dba::kBlkClasses; ++k)
       ctx->cls[k + 1] = (int)(std::partition_point(blocks.begin(), blocks.end(),
                                                    [&](const dba::BlockInfo& b) { return cls_of(b) <= k; }) -
                               blocks.begin());
@@ -1266,7 +1345,7 @@ dba_status dba_block_layout(const dba_block_ctx* ctx, int64_t* n_blocks, int64_t
 dba_status dba_block_size_classes(const dba_block_ctx* ctx, int64_t* counts) {
   if (!ctx || !counts) return DBA_EINVAL;
   if (!ctx->has_problem) return DBA_ESTATE;
-  for (int k = 0; k < 3; ++k) counts[k] = ctx->cls[k + 1] - ctx->cls[k];
+  for (int k = 0; k < dba::kBlkClasses; ++k) counts[k] = ctx->cls[k + 1] - ctx->cls[k];
   return DBA_OK;
 }
 

@@ -32,7 +32,7 @@ EXPORTED = [
     "dba_block_size_classes", "dba_block_algorithmic_flops", "dba_block_last_error",
     "dba_block_destroy",
 ]
-DBA_BLOCK_MAX_POINTS, DBA_BLOCK_MAX_CAMERAS = 32, 4
+DBA_BLOCK_MAX_POINTS, DBA_BLOCK_MAX_CAMERAS, DBA_BLOCK_SIZE_CLASSES = 64, 4, 4
 DBA_MLP_N_PARAMS, DBA_MLP_N_FEATURES, DBA_MLP_N_TARGETS = 11552, 32, 16
 DBA_NOALLOC_MAX_OBS = 16777216
 
@@ -499,11 +499,11 @@ class BlockSolver:
         return {"n_blocks": nb.value, "n_point_copies": npc.value, "n_camera_copies": ncc.value}
 
     def size_classes(self):
-        """Blocks per size class of the solve kernel (8-, 16-, 32-lane groups); each
-        nonempty class is one launch per iteration."""
-        c = (ctypes.c_int64 * 3)()
+        """Blocks per size class of the solve kernel (8-, 16-, 32-lane groups, 32 lanes
+        with two point copies each); each nonempty class is one launch per iteration."""
+        c = (ctypes.c_int64 * DBA_BLOCK_SIZE_CLASSES)()
         self._check(load().dba_block_size_classes(self.ctx, c))
-        return [c[0], c[1], c[2]]
+        return list(c)
 
     def algorithmic_flops(self):
         f = ctypes.c_double()

@@ -24,7 +24,7 @@ def _emit(rec):
     print(json.dumps(rec), flush=True)
 
 
-def block_sweep(n_pts=500000, pis=(1, 8, 32), kappas=(1, 2, 4), target=0.5, max_iters=400, precision=None,
+def block_sweep(n_pts=500000, pis=(1, 8, 32, 64), kappas=(1, 2, 4), target=0.5, max_iters=400, precision=None,
                 profile_iters=10):
     """Points and cameras per update step (Sec. 3.1.4, Eq. 14; Sec. 4 sweeps both):
     blocks and copies, device time per iteration, iterations and device time until

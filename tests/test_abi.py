@@ -64,7 +64,7 @@ def test_null_arguments(lib):
     assert isinstance(lib.dba_last_error(None), bytes)
 
 
-@pytest.mark.parametrize("pi,kappa", [(0, 1), (33, 1), (4, 0), (4, 5)])
+@pytest.mark.parametrize("pi,kappa", [(0, 1), (65, 1), (4, 0), (4, 5)])
 def test_block_sizes_are_validated_before_any_device_work(lib, pi, kappa):
     cfg = dba.dba_config_default()
     ctx = ctypes.c_void_p()
@@ -76,7 +76,7 @@ def test_block_null_arguments(lib):
     assert lib.dba_block_create(None, 1, 1, None) == dba.DBA_EINVAL
     assert lib.dba_block_iterate(None, 1, None) == dba.DBA_EINVAL
     assert lib.dba_block_get_params(None, None, None) == dba.DBA_EINVAL
-    counts = (ctypes.c_int64 * 3)()
+    counts = (ctypes.c_int64 * dba.DBA_BLOCK_SIZE_CLASSES)()
     assert lib.dba_block_size_classes(None, counts) == dba.DBA_EINVAL
     lib.dba_block_destroy(None)
 

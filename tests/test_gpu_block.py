@@ -31,16 +31,19 @@ def relerr(a, b):
 
 def size_classes(layout):
     """Blocks per size class of the solve kernel, recounted from the oracle's layout:
-    one camera and <= 8 points, <= 2 cameras and <= 16 points, the rest."""
+    one camera and <= 8 points, <= 2 cameras and <= 16 points, <= 32 points, the rest."""
     npb, ncb = np.diff(layout.pc_off), np.diff(layout.cc_off)
     c8 = (ncb == 1) & (npb <= 8)
     c16 = ~c8 & (ncb <= 2) & (npb <= 16)
-    return [int(c8.sum()), int(c16.sum()), int((~c8 & ~c16).sum())]
+    c32 = ~c8 & ~c16 & (npb <= 32)
+    return [int(c8.sum()), int(c16.sum()), int(c32.sum()), int((~c8 & ~c16 & ~c32).sum())]
 
 
-# together these put blocks in every (lane group, most cameras) kernel variant:
-# 8 lanes; 16 lanes with 1 and 2 cameras; 32 lanes with 1, 2 and 4 cameras
-@pytest.mark.parametrize("pi,kappa", [(1, 1), (8, 2), (32, 4), (5, 3), (32, 1), (32, 2)])
+# together these put blocks in every (lane group, copies per lane, most cameras) kernel
+# variant: 8 lanes; 16 lanes with 1 and 2 cameras; 32 lanes with 1, 2 and 4 cameras, one
+# or two point copies per lane
+@pytest.mark.parametrize("pi,kappa", [(1, 1), (8, 2), (32, 4), (5, 3), (32, 1), (32, 2), (64, 1), (48, 2),
+                                      (64, 4)])
 def test_fp64_matches_block_oracle_per_iteration(pi, kappa):
     sc = S.scene1(n_pts=400, n_cams=16, seed=17)
     with dba.BlockSolver(sc, pi, kappa, precision=dba.DBA_PREC_F64) as s:
@@ -86,7 +89,7 @@ def test_one_point_one_camera_blocks_equal_the_per_observation_path():
         assert relerr(ca, cb) <= TOL64 and relerr(pa, pb) <= TOL64
 
 
-@pytest.mark.parametrize("pi,kappa", [(8, 2), (32, 4)])
+@pytest.mark.parametrize("pi,kappa", [(8, 2), (32, 4), (64, 2)])
 def test_fp32_tracks_the_fp64_oracle(pi, kappa):
     sc = S.scene1(n_pts=1500, n_cams=24, seed=29)
     with dba.BlockSolver(sc, pi, kappa, precision=dba.DBA_PREC_F32_LOCAL) as s:
@@ -117,7 +120,7 @@ def test_edge_cases_single_observation_points_and_unobserved_points():
                   pts_gt=sc.pts_gt, cams0=sc.cams0, pts0=sc.pts0, focal=sc.focal, cx=sc.cx, cy=sc.cy,
                   loss=sc.loss, loss_param=sc.loss_param, rho_x=sc.rho_x, rho_y=sc.rho_y,
                   rho_angle=sc.rho_angle)
-    for pi, kappa in ((1, 1), (7, 3)):
+    for pi, kappa in ((1, 1), (7, 3), (64, 2)):
         with dba.BlockSolver(sub, pi, kappa, precision=dba.DBA_PREC_F64) as s:
             cfg = oracle_cfg(s)
             st = O.BlockState(sub, pi, kappa)
@@ -141,7 +144,7 @@ def test_larger_blocks_reach_the_target_in_fewer_iterations():
 def test_errors():
     sc = S.scene0(n_pts=10, n_cams=3)
     with pytest.raises(dba.DbaError) as e:
-        dba.BlockSolver(sc, 33, 1)
+        dba.BlockSolver(sc, 65, 1)
     assert e.value.status == dba.DBA_EINVAL
     with pytest.raises(dba.DbaError) as e:
         dba.BlockSolver(sc, 4, 5)
