@@ -320,7 +320,6 @@ def run_ours(args, rank, world, local_rank):
 
         solver.set_warm_start(warmstart.load())
     layout = solver.layout()
-    classes = solver.size_classes()
     solver.iterate(args.warmup, stats=False)
 
     def barrier():
