@@ -114,6 +114,7 @@ struct dba_ctx {
   double* d_scene_sums = nullptr;  // [n_scenes][5]
   std::vector<void*> allocs;
   DevProblem P{};
+  dba::TileMaps tmaps{};  // tensor maps of P's observation arrays (tile kernel staging)
   int cur = 0, pending = 0;
   long long iters = 0;
   // graph of one iteration
@@ -486,20 +487,24 @@ dba_status upload_state_T(dba_ctx* ctx, const double* cams, const double* pts,
                           const std::vector<double>& hdel, const std::vector<double>& hdual, bool exact) {
   DevProblem& P = ctx->P;
   const int m = ctx->n_cams, n = ctx->n_pts;
-  const size_t nv = 9 * (size_t)ctx->n_obs;
+  const size_t l = (size_t)ctx->n_obs, lp = (size_t)P.pitch;  // host rows dense, device rows pitched
   std::vector<T> tdel, tX, tY;
   to_T(hdel, tdel);
   to_T(std::vector<double>(pts, pts + 3 * (size_t)n), tX);
   to_T(std::vector<double>(cams, cams + 6 * (size_t)m), tY);
   cudaStream_t st = ctx->stream;
   if (tdel.empty())
-    DBA_CUDA(cudaMemsetAsync(P.delta, 0, nv * sizeof(T), st), "clear copies");
+    DBA_CUDA(cudaMemsetAsync(P.delta, 0, 9 * lp * sizeof(T), st), "clear copies");
   else
-    DBA_CUDA(cudaMemcpyAsync(P.delta, tdel.data(), nv * sizeof(T), cudaMemcpyHostToDevice, st), "upload copies");
+    DBA_CUDA(cudaMemcpy2DAsync(P.delta, lp * sizeof(T), tdel.data(), l * sizeof(T), l * sizeof(T), 9,
+                               cudaMemcpyHostToDevice, st),
+             "upload copies");
   if (hdual.empty())
-    DBA_CUDA(cudaMemsetAsync(P.adual, 0, nv * sizeof(double), st), "clear duals");
+    DBA_CUDA(cudaMemsetAsync(P.adual, 0, 9 * lp * sizeof(double), st), "clear duals");
   else
-    DBA_CUDA(cudaMemcpyAsync(P.adual, hdual.data(), nv * sizeof(double), cudaMemcpyHostToDevice, st), "upload duals");
+    DBA_CUDA(cudaMemcpy2DAsync(P.adual, lp * sizeof(double), hdual.data(), l * sizeof(double), l * sizeof(double), 9,
+                               cudaMemcpyHostToDevice, st),
+             "upload duals");
   for (int b = 0; b < 2; ++b) {
     DBA_CUDA(cudaMemcpyAsync(P.X[b], pts, 3 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice, st), "upload points");
     DBA_CUDA(cudaMemcpyAsync(P.Y[b], cams, 6 * (size_t)m * sizeof(double), cudaMemcpyHostToDevice, st), "upload cameras");
@@ -573,7 +578,7 @@ dba_status launch_iteration(dba_ctx* ctx) {
   if (ctx->warm)
     DBA_CUDA(dba::launch_mlp_warmstart(ctx->P, ctx->prm, ctx->fp32, ctx->d_mlp_blob, ctx->d_mlp_params, ctx->stream),
              "warm start launch");
-  DBA_CUDA(dba::launch_tile_iterate(ctx->P, ctx->prm, ctx->fp32, ctx->stream), "tile_iterate launch");
+  DBA_CUDA(dba::launch_tile_iterate(ctx->P, ctx->tmaps, ctx->prm, ctx->fp32, ctx->stream), "tile_iterate launch");
   DBA_CUDA(dba::launch_finalize(ctx->P, ctx->fp32, ctx->stream), "finalize launch");
   return DBA_OK;
 }
@@ -588,7 +593,7 @@ dba_status ensure_graph(dba_ctx* ctx, bool with_metrics = false) {
   cudaError_t e0 = ctx->warm ? dba::launch_mlp_warmstart(ctx->P, ctx->prm, ctx->fp32, ctx->d_mlp_blob,
                                                           ctx->d_mlp_params, ctx->stream)
                              : cudaSuccess;
-  cudaError_t e1 = dba::launch_tile_iterate(ctx->P, ctx->prm, ctx->fp32, ctx->stream);
+  cudaError_t e1 = dba::launch_tile_iterate(ctx->P, ctx->tmaps, ctx->prm, ctx->fp32, ctx->stream);
   cudaError_t e2 = dba::launch_finalize(ctx->P, ctx->fp32, ctx->stream);
   cudaError_t e4 = with_metrics ? dba::launch_metrics(ctx->P, ctx->prm, ctx->fp32, ctx->cur ^ 1, 1, ctx->stream, true)
                                 : cudaSuccess;
@@ -632,6 +637,7 @@ dba_status check_device_flags(dba_ctx* ctx) {
   DBA_CUDA(cudaStreamSynchronize(ctx->stream), "iterate");
   if (h.err & 1) return ctx->fail(DBA_ENUMERIC, "a local solve produced a non-finite value");
   if (h.err & 2) return ctx->fail(DBA_ETIMEOUT, "a tensor-core wait of the warm-start network timed out");
+  if (h.err & 4) return ctx->fail(DBA_ETIMEOUT, "a wait for the tile kernel's tensor copies timed out");
   if (h.cur != ctx->cur) return ctx->fail(DBA_ECUDA, "device control word out of step with the host");
   return DBA_OK;
 }
@@ -699,9 +705,10 @@ dba_status load_problem(dba_ctx* ctx, int NT, int32_t n_cams, int32_t n_pts, int
   }
   const size_t esz = ctx->fp32 ? sizeof(float) : sizeof(double);
   char* p = nullptr;
-  DBA_CUDA(ctx->alloc(&p, 9 * (size_t)n_obs * esz), "alloc copies");
+  P.pitch = dba::obs_pitch(n_obs);
+  DBA_CUDA(ctx->alloc(&p, 9 * (size_t)P.pitch * esz), "alloc copies");
   P.delta = p;
-  DBA_CUDA(ctx->alloc(&P.adual, 9 * (size_t)n_obs), "alloc duals");
+  DBA_CUDA(ctx->alloc(&P.adual, 9 * (size_t)P.pitch), "alloc duals");
   for (int b = 0; b < 2; ++b) {
     DBA_CUDA(ctx->alloc(&P.X[b], 3 * (size_t)n_pts), "alloc points");
     DBA_CUDA(ctx->alloc(&P.Y[b], 6 * (size_t)n_cams), "alloc cameras");
@@ -721,6 +728,7 @@ dba_status load_problem(dba_ctx* ctx, int NT, int32_t n_cams, int32_t n_pts, int
   DBA_CUDA(ctx->alloc(&p, 12 * (size_t)n_cams * esz), "alloc camera poses");
   P.cam_pose = p;
   DBA_CUDA(ctx->alloc(&P.ctl, 1), "alloc control");
+  DBA_CUDA(dba::encode_tile_maps(P, ctx->fp32, &ctx->tmaps), "tensor maps");
   ctx->has_problem = true;
   dba_status s = upload_state(ctx, cams0, pts0, nullptr, nullptr);
   if (s != DBA_OK) {
@@ -964,14 +972,21 @@ dba_status dba_get_state(dba_ctx* ctx, double* copies, double* duals) {
   std::vector<double> X(3 * (size_t)n), Y(6 * (size_t)m), del(9 * (size_t)l), a(9 * (size_t)l);
   DBA_CUDA(cudaMemcpyAsync(X.data(), ctx->P.X[ctx->cur], X.size() * sizeof(double), cudaMemcpyDeviceToHost, st), "read");
   DBA_CUDA(cudaMemcpyAsync(Y.data(), ctx->P.Y[ctx->cur], Y.size() * sizeof(double), cudaMemcpyDeviceToHost, st), "read");
-  DBA_CUDA(cudaMemcpyAsync(a.data(), ctx->P.adual, a.size() * sizeof(double), cudaMemcpyDeviceToHost, st), "read");
+  const size_t lp = (size_t)ctx->P.pitch;  // device rows pitched, host rows dense
+  DBA_CUDA(cudaMemcpy2DAsync(a.data(), l * sizeof(double), ctx->P.adual, lp * sizeof(double), l * sizeof(double), 9,
+                             cudaMemcpyDeviceToHost, st),
+           "read");
   if (ctx->fp32) {
     std::vector<float> f(9 * (size_t)l);
-    DBA_CUDA(cudaMemcpyAsync(f.data(), ctx->P.delta, f.size() * sizeof(float), cudaMemcpyDeviceToHost, st), "read");
+    DBA_CUDA(cudaMemcpy2DAsync(f.data(), l * sizeof(float), ctx->P.delta, lp * sizeof(float), l * sizeof(float), 9,
+                               cudaMemcpyDeviceToHost, st),
+             "read");
     DBA_CUDA(cudaStreamSynchronize(st), "get_state");
     for (size_t k = 0; k < f.size(); ++k) del[k] = f[k];
   } else {
-    DBA_CUDA(cudaMemcpyAsync(del.data(), ctx->P.delta, del.size() * sizeof(double), cudaMemcpyDeviceToHost, st), "read");
+    DBA_CUDA(cudaMemcpy2DAsync(del.data(), l * sizeof(double), ctx->P.delta, lp * sizeof(double), l * sizeof(double),
+                               9, cudaMemcpyDeviceToHost, st),
+             "read");
     DBA_CUDA(cudaStreamSynchronize(st), "get_state");
   }
   for (long long o = 0; o < l; ++o) {
@@ -1013,7 +1028,7 @@ dba_status dba_profile(dba_ctx* ctx, int n_iters, const char** names, double* ms
                "warm start");
     }
     DBA_CUDA(cudaEventRecord(ev[3 * it], st), "event");
-    DBA_CUDA(dba::launch_tile_iterate(ctx->P, ctx->prm, ctx->fp32, st), "tile_iterate");
+    DBA_CUDA(dba::launch_tile_iterate(ctx->P, ctx->tmaps, ctx->prm, ctx->fp32, st), "tile_iterate");
     DBA_CUDA(cudaEventRecord(ev[3 * it + 1], st), "event");
     DBA_CUDA(dba::launch_finalize(ctx->P, ctx->fp32, st), "finalize");
     DBA_CUDA(cudaEventRecord(ev[3 * it + 2], st), "event");
@@ -1179,7 +1194,7 @@ dba_status dba_set_warm_start(dba_ctx* ctx, const dba_mlp* mlp) {
     DBA_CUDA(ctx->alloc(&ctx->d_mlp_blob, blob.size()), "warm start");
     DBA_CUDA(ctx->alloc(&ctx->d_mlp_params, params.size()), "warm start");
     char* p = nullptr;
-    DBA_CUDA(ctx->alloc(&p, 9 * (size_t)ctx->n_obs * (ctx->fp32 ? sizeof(float) : sizeof(double))), "warm start");
+    DBA_CUDA(ctx->alloc(&p, 9 * (size_t)ctx->P.pitch * (ctx->fp32 ? sizeof(float) : sizeof(double))), "warm start");
     ctx->P.mlp_start = p;
   }
   DBA_CUDA(cudaMemcpyAsync(ctx->d_mlp_blob, blob.data(), blob.size(), cudaMemcpyHostToDevice, ctx->stream),

@@ -2,6 +2,7 @@
 // (dba_kernels.cu).  Not installed; not part of the public ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -14,7 +15,8 @@ namespace dba {
 struct alignas(16) DevCtl {
   int cur;          // index (0/1) of the current consensus buffer
   int pending;      // 1: copies are offsets from the previous consensus, duals lag by one step
-  int err;          // bit 0: non-finite local solve
+  int err;          // bit 0: non-finite local solve; bit 1: warm-start network wait timed out;
+                    // bit 2: tile kernel tensor-copy wait timed out
   int exact;        // 1: duals may not sum to zero per point/camera (first iteration after set_state)
   unsigned long long k;   // iterations run
   unsigned int done;      // finalize-kernel block counter
@@ -38,10 +40,13 @@ struct Params {
 };
 
 // All device pointers of one problem.  Observation arrays are in internal
-// (tile) order; per-observation vectors are structure-of-arrays with stride n_obs.
+// (tile) order; per-observation vectors are structure-of-arrays with row stride
+// `pitch` (n_obs rounded up to kObsPitchAlign, so every row starts on a 128-byte
+// boundary as the tile kernel's tensor copies require).
 struct DevProblem {
   int n_cams, n_pts;
   long long n_obs;
+  long long pitch;              // row stride of delta, adual and mlp_start
   int n_tiles;
   int tile_obs;                 // block size of the tile kernel
   int n_cam_slots, n_pt_slots, n_split_pts;
@@ -62,8 +67,8 @@ struct DevProblem {
   const int* split_slot_off;    // [n_split_pts+1]
   const int* pt_count;          // [n] observations per point
   // state
-  void* delta;                  // [9][l] T: copy minus the consensus it was solved against
-  double* adual;                // [9][l] scaled duals (r/rho_x, s/rho_y)
+  void* delta;                  // [9][pitch] T: copy minus the consensus it was solved against
+  double* adual;                // [9][pitch] scaled duals (r/rho_x, s/rho_y)
   double* X[2];                 // [n][3] point consensus, ping-pong
   double* Y[2];                 // [m][6] camera consensus, ping-pong
   void* Xm;                     // [n][3] T copy of the current point consensus
@@ -72,14 +77,26 @@ struct DevProblem {
   void* DY;                     // [m][6]
   double* pt_part;              // [n_pt_slots][3]
   double* cam_part;             // [n_cam_slots][6]
-  const void* mlp_start;        // [9][l] T: learned candidate start (nullptr: none)
+  const void* mlp_start;        // [9][pitch] T: learned candidate start (nullptr: none)
   double* metric_part;          // [metric blocks][8]
   double* metric_out;           // [8]
   void* cam_pose;               // [n_cams][12] T: R (row-major) and t of each consensus camera
   DevCtl* ctl;
 };
 
+// Tensor maps of the observation arrays the tile kernel stages with TMA (built on the
+// host per problem; passed to the kernel as a grid constant).
+struct TileMaps {
+  CUtensorMap delta;  // [9][n_obs] T, row stride pitch
+  CUtensorMap adual;  // [9][n_obs] double
+  CUtensorMap z;      // [n_obs] float2 as 64-bit words, or [n_obs][2] double
+  CUtensorMap pt;     // [n_obs] int32
+  CUtensorMap cam;    // [n_obs] int32 (obs_cam_rank)
+};
+
 constexpr int kCamMask = 0xffffff;  // camera index bits of obs_cam_rank
+constexpr long long kObsPitchAlign = 32;  // elements: 128 bytes of float, 256 of double
+inline long long obs_pitch(long long n_obs) { return (n_obs + kObsPitchAlign - 1) / kObsPitchAlign * kObsPitchAlign; }
 constexpr int kMetricBlocks = 1024;
 constexpr int kMetricThreads = 256;
 
@@ -88,7 +105,10 @@ constexpr int kMetricThreads = 256;
 cudaError_t prepare_tile_kernels();
 
 // Kernel launchers (return the launch error).  fp32 selects the FP32 local-solve path.
-cudaError_t launch_tile_iterate(const DevProblem& P, const Params& prm, bool fp32, cudaStream_t s);
+// Encodes the tile kernel's tensor maps for P (its pointers, n_obs, pitch, tile_obs).
+cudaError_t encode_tile_maps(const DevProblem& P, bool fp32, TileMaps* M);
+cudaError_t launch_tile_iterate(const DevProblem& P, const TileMaps& M, const Params& prm, bool fp32,
+                                cudaStream_t s);
 cudaError_t launch_finalize(const DevProblem& P, bool fp32, cudaStream_t s);
 // gt_only: only the reference-pixel sums (rmse_gt and its count) and the valid counts.
 cudaError_t launch_metrics(const DevProblem& P, const Params& prm, bool fp32, int cur, int pending,

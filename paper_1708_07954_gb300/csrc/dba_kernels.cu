@@ -36,9 +36,10 @@ namespace {
 // ------------------------------------------------------------ tile kernel
 // Persistent, software-pipelined: each block walks tiles blockIdx.x,
 // blockIdx.x + gridDim.x, ... and while it computes one tile the copies, duals,
-// pixels and indices of its next tile stream into shared memory with cp.async
-// (no registers hold loads in flight), so DRAM latency hides behind the local
-// solves.  One thread per observation of a tile.
+// pixels and indices of its next tile stream into shared memory by tensor copies
+// (TMA, issued by one thread, completion on an mbarrier) and its run tables by
+// cp.async, so no registers hold loads in flight and DRAM latency hides behind
+// the local solves.  One thread per observation of a tile.
 //
 // Steady state: after any full iteration the scaled duals of every point and
 // camera sum to zero (sum of Eq. 12 over a track after Eq. 10; the oracle's
@@ -60,23 +61,51 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+constexpr int round128(int bytes) { return (bytes + 127) / 128 * 128; }
+
+// The observation rows of a tile reach shared memory by tensor copies (TMA).  A copy's
+// innermost coordinate must fall on a 16-byte boundary, so each row is fetched as a
+// window starting at the tile's first observation rounded down to 16 bytes, in two
+// boxes of kW elements (a box is at most 256 elements wide); box b lands in slab b.
+// Element t of the tile is at window position x = t + (o0 mod 16 / size), found by
+// win().  Double pixel pairs (16 bytes) are fetched as [n][2] rows, with no offset.
+template <int W, int kSlab>
+__device__ __forceinline__ int win(int x) {
+  return x < W ? x : kSlab + (x - W);
+}
+
 template <typename T, int NT>
 struct TileStage {
-  T delta[9][NT];
-  double adual[9][NT];
-  typename Num<T>::V2 z[NT];
-  int pt[NT];
-  int cam[NT];       // camera | rank << 24
-  double X[3 * NT];  // FP64 consensus of the tile's points (contiguous internal ids)
+  using V2 = typename Num<T>::V2;
+  static constexpr int kWT = NT / 2 + 16 / (int)sizeof(T);  // copies (T)
+  static constexpr int kWD = NT / 2 + 2;                     // duals (double)
+  static constexpr int kWI = NT / 2 + 4;                     // indices (int32)
+  static constexpr int kWZ = sizeof(T) == 4 ? NT / 2 + 2 : NT / 2;  // pixels (float2 / double2)
+  static constexpr int kSlabT = round128(9 * kWT * (int)sizeof(T)) / (int)sizeof(T);
+  static constexpr int kSlabD = round128(9 * kWD * 8) / 8;
+  static constexpr int kSlabI = round128(kWI * 4) / 4;
+  static constexpr int kSlabZ = round128(kWZ * (int)sizeof(V2)) / (int)sizeof(V2);
+  // bytes the tensor copies of one tile deliver (whole boxes, out-of-range parts filled)
+  static constexpr unsigned kTxBytes =
+      2u * (9u * kWT * sizeof(T) + 9u * kWD * 8u + kWZ * sizeof(V2) + 2u * kWI * 4u);
+  alignas(128) T delta[2 * kSlabT];      // [box][9][kWT]
+  alignas(128) double adual[2 * kSlabD]; // [box][9][kWD]
+  alignas(128) V2 z[2 * kSlabZ];
+  alignas(128) int pt[2 * kSlabI];
+  alignas(128) int cam[2 * kSlabI];      // camera | rank << 24
+  // run tables and the FP64 consensus of the tile's points (cp.async)
+  double X[3 * NT];  // contiguous internal ids
   int2 pseg[NT];
   int pslot[NT];
   int2 cseg[NT];
   int cslot[NT];
 };
 
+// dynamic shared memory: 128 bytes of alignment slack, two stages, the run buffer and
+// one mbarrier per stage
 template <typename T, int NT>
 constexpr size_t tile_smem_bytes() {
-  return 2 * sizeof(TileStage<T, NT>) + sizeof(double) * 9 * NT;
+  return 128 + 2 * sizeof(TileStage<T, NT>) + sizeof(double) * 9 * NT + 2 * sizeof(unsigned long long);
 }
 
 __device__ __forceinline__ TileInfo load_tile_info(const TileInfo* tiles, int tile) {
@@ -88,22 +117,68 @@ __device__ __forceinline__ TileInfo load_tile_info(const TileInfo* tiles, int ti
   return ti;
 }
 
-// Issues (and commits) the asynchronous copies of one tile into stage S.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void tma_1d(void* dst, const CUtensorMap* map, int x, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.1d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2}], [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_2d(void* dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// Bounded wait for completion `parity` of the mbarrier at bar; false after the limit.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  uint32_t done = 0;
+  for (int it = 0; it < (1 << 22) && !done; ++it)
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+  return done != 0;
+}
+
+// Issues the copies of one tile into stage S: the observation rows by tensor copies from
+// thread 0 (completion on bar), the run tables and consensus by cp.async from every
+// thread (one commit group).
 template <typename T, int NT>
-__device__ __forceinline__ void stage_tile(const DevProblem& P, TileStage<T, NT>& S, const TileInfo& ti,
-                                           int cur) {
-  using V2 = typename Num<T>::V2;
+__device__ __forceinline__ void stage_tile(const DevProblem& P, const TileMaps& M, TileStage<T, NT>& S,
+                                           const TileInfo& ti, int cur, uint32_t bar) {
+  using St = TileStage<T, NT>;
   const int t = threadIdx.x;
-  if (t < ti.n) {
-    const long long l = P.n_obs, o = (long long)ti.o0 + t;
-    const T* delta = static_cast<const T*>(P.delta);
-#pragma unroll
-    for (int c = 0; c < 9; ++c) cp_async<sizeof(T)>(&S.delta[c][t], delta + c * l + o);
-#pragma unroll
-    for (int c = 0; c < 9; ++c) cp_async<8>(&S.adual[c][t], P.adual + c * l + o);
-    cp_async<sizeof(V2)>(&S.z[t], static_cast<const V2*>(P.z) + o);
-    cp_async<4>(&S.pt[t], P.obs_pt + o);
-    cp_async<4>(&S.cam[t], P.obs_cam_rank + o);
+  if (t == 0) {
+    const int o0 = ti.o0;
+    const int xT = o0 & ~(16 / (int)sizeof(T) - 1), xD = o0 & ~1, xI = o0 & ~3;
+    // generic-proxy reads of this stage (the tile before last) precede the async writes
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(St::kTxBytes) : "memory");
+    tma_2d(S.delta, &M.delta, xT, 0, bar);
+    tma_2d(S.delta + St::kSlabT, &M.delta, xT + St::kWT, 0, bar);
+    tma_2d(S.adual, &M.adual, xD, 0, bar);
+    tma_2d(S.adual + St::kSlabD, &M.adual, xD + St::kWD, 0, bar);
+    if constexpr (sizeof(T) == 4) {
+      const int xZ = o0 & ~1;
+      tma_1d(S.z, &M.z, xZ, bar);
+      tma_1d(S.z + St::kSlabZ, &M.z, xZ + St::kWZ, bar);
+    } else {
+      tma_2d(S.z, &M.z, 0, o0, bar);
+      tma_2d(S.z + St::kSlabZ, &M.z, 0, o0 + St::kWZ, bar);
+    }
+    tma_1d(S.pt, &M.pt, xI, bar);
+    tma_1d(S.pt + St::kSlabI, &M.pt, xI + St::kWI, bar);
+    tma_1d(S.cam, &M.cam, xI, bar);
+    tma_1d(S.cam + St::kSlabI, &M.cam, xI + St::kWI, bar);
   }
   if (t < ti.nr) {
     cp_async<8>(&S.pseg[t], P.pseg + ti.r0 + t);
@@ -124,7 +199,7 @@ __device__ __forceinline__ void process_tile(const DevProblem& P, const Prm<T>& 
                                              double (*s_buf)[NT], const TileInfo& ti, int cur, int pending,
                                              int exact) {
   const int t = threadIdx.x;
-  const long long l = P.n_obs;
+  const long long l = P.pitch;  // row stride of delta, adual, mlp_start
   const long long o = (long long)ti.o0 + t;
   T* __restrict__ delta = static_cast<T*>(P.delta);
   double* __restrict__ adual = P.adual;
@@ -138,9 +213,15 @@ __device__ __forceinline__ void process_tile(const DevProblem& P, const Prm<T>& 
   constexpr int kRow = sizeof(T) == 4 ? NT + 1 : NT;
   T(*s_t)[kRow] = reinterpret_cast<T(*)[kRow]>(&s_buf[0][0]);
 
+  using St = TileStage<T, NT>;
   if (t < ti.n) {
-    const int i = S.pt[t];
-    const int cr = S.cam[t];
+    // this observation's positions in the staged windows
+    const int wT = win<St::kWT, St::kSlabT>(t + (ti.o0 & (16 / (int)sizeof(T) - 1)));
+    const int wD = win<St::kWD, St::kSlabD>(t + (ti.o0 & 1));
+    const int wI = win<St::kWI, St::kSlabI>(t + (ti.o0 & 3));
+    const int wZ = win<St::kWZ, St::kSlabZ>(t + (sizeof(T) == 4 ? (ti.o0 & 1) : 0));
+    const int i = S.pt[wI];
+    const int cr = S.cam[wI];
     const int j = cr & kCamMask, rk = (int)((unsigned int)cr >> 24);
     T d[9], vbar[9], aT[9];
 #pragma unroll
@@ -148,7 +229,7 @@ __device__ __forceinline__ void process_tile(const DevProblem& P, const Prm<T>& 
 #pragma unroll
     for (int c = 0; c < 6; ++c) vbar[3 + c] = Ym[6 * j + c];
 #pragma unroll
-    for (int c = 0; c < 9; ++c) d[c] = S.delta[c][t];
+    for (int c = 0; c < 9; ++c) d[c] = S.delta[wT + c * St::kWT];
     if (pending) {
       // Eqs. (12)-(13) of the previous iteration: the copy relative to the new
       // consensus is d0 = delta + (old - new consensus); a += d0 in FP64.
@@ -158,15 +239,15 @@ __device__ __forceinline__ void process_tile(const DevProblem& P, const Prm<T>& 
       for (int c = 0; c < 6; ++c) d[3 + c] += DY[6 * j + c];
 #pragma unroll
       for (int c = 0; c < 9; ++c) {
-        const double a = S.adual[c][t] + to_f64<T>(d[c]);
+        const double a = S.adual[wD + c * St::kWD] + to_f64<T>(d[c]);
         adual[c * l + o] = a;
         aT[c] = from_f64<T>(a);
       }
     } else {
 #pragma unroll
-      for (int c = 0; c < 9; ++c) aT[c] = from_f64<T>(S.adual[c][t]);
+      for (int c = 0; c < 9; ++c) aT[c] = from_f64<T>(S.adual[wD + c * St::kWD]);
     }
-    const typename Num<T>::V2 zz = S.z[t];
+    const typename Num<T>::V2 zz = S.z[wZ];
     if (P.mlp_start) {
       const T* ms = static_cast<const T*>(P.mlp_start);
       T alt[9];
@@ -193,7 +274,7 @@ __device__ __forceinline__ void process_tile(const DevProblem& P, const Prm<T>& 
       // first iteration after dba_set_state: full summands offset + dual (pending is 0 then)
 #pragma unroll
       for (int c = 0; c < 9; ++c) {
-        const double v = to_f64<T>(d[c]) + S.adual[c][t];
+        const double v = to_f64<T>(d[c]) + S.adual[wD + c * St::kWD];
         if (c < 3) s_buf[c][t] = v; else s_buf[c][rk] = v;
       }
     } else {
@@ -259,33 +340,55 @@ __device__ __forceinline__ void process_tile(const DevProblem& P, const Prm<T>& 
 }
 
 template <typename T, int NT, int kS>
-__global__ void __launch_bounds__(NT, 2) tile_iterate_kernel(DevProblem P, Prm<T> q) {
+__global__ void __launch_bounds__(NT, 2)
+    tile_iterate_kernel(DevProblem P, const __grid_constant__ TileMaps M, Prm<T> q) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  TileStage<T, NT>* stage = reinterpret_cast<TileStage<T, NT>*>(smem_raw);
-  double(*s_buf)[NT] = reinterpret_cast<double(*)[NT]>(smem_raw + 2 * sizeof(TileStage<T, NT>));
+  unsigned char* base = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
+  TileStage<T, NT>* stage = reinterpret_cast<TileStage<T, NT>*>(base);
+  double(*s_buf)[NT] = reinterpret_cast<double(*)[NT]>(base + 2 * sizeof(TileStage<T, NT>));
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(base + 2 * sizeof(TileStage<T, NT>) +
+                                                                    sizeof(double) * 9 * NT);
+  const uint32_t bar0 = smem_addr(&bars[0]), bar1 = smem_addr(&bars[1]);
   // The control word is written by the previous kernel and constant during this one: one
   // read-only-cache load per thread (cached per SM) instead of same-address L2 traffic.
   const int4 ctl = __ldg(reinterpret_cast<const int4*>(P.ctl));
   const int cur = ctl.x, pending = ctl.y, exact = ctl.w;
   int tile = blockIdx.x;
   if (tile >= P.n_tiles) return;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar0));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar1));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
   TileInfo info = load_tile_info(P.tiles, tile);
-  stage_tile<T, NT>(P, stage[0], info, cur);
+  stage_tile<T, NT>(P, M, stage[0], info, cur, bar0);
   int next = tile + gridDim.x;
   TileInfo info_next{};
   if (next < P.n_tiles) info_next = load_tile_info(P.tiles, next);
+  cp_async_wait<0>();
+  bool ok = mbar_wait(bar0, 0);
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0) atomicOr(&P.ctl->err, 4);
+    return;
+  }
   for (int k = 0; tile < P.n_tiles; ++k) {
-    if (next < P.n_tiles)
-      stage_tile<T, NT>(P, stage[(k + 1) & 1], info_next, cur);
-    else
-      cp_async_commit();  // empty group keeps the wait count uniform
+    // the next tile's copies go into the stage the previous tile used (free since the
+    // barrier that ended it) and land while this tile is solved; stage s serves tiles
+    // k = s, s + 2, ..., and its mbarrier completes once per use (parity (k >> 1) & 1)
+    const int sn = (k + 1) & 1;
+    if (next < P.n_tiles) stage_tile<T, NT>(P, M, stage[sn], info_next, cur, sn ? bar1 : bar0);
     const int after = next + gridDim.x;
     TileInfo info_after{};
     if (after < P.n_tiles) info_after = load_tile_info(P.tiles, after);  // used two tiles later
-    cp_async_wait<1>();    // this thread's copies of the current tile have landed
-    __syncthreads();       // ... and everyone else's
     process_tile<T, NT, kS>(P, q, stage[k & 1], s_buf, info, cur, pending, exact);
-    __syncthreads();       // stage and run buffers are free for reuse
+    cp_async_wait<0>();  // this thread's copies of the next tile have landed
+    ok = next >= P.n_tiles || mbar_wait(sn ? bar1 : bar0, ((k + 1) >> 1) & 1);
+    // ... and everyone else's, and the tensor copies; this stage and the run buffer are free
+    if (__syncthreads_or(!ok)) {
+      if (threadIdx.x == 0) atomicOr(&P.ctl->err, 4);
+      return;
+    }
     tile = next;
     next = after;
     info = info_next;
@@ -422,7 +525,7 @@ __global__ void __launch_bounds__(kMetricThreads) metrics_kernel(DevProblem P, P
 #pragma unroll
       for (int c = 0; c < 9; ++c) {
         const T dc = c < 3 ? DX[3 * i + c] : DY[6 * j + c - 3];
-        const T cp = delta[c * l + o] + (pending ? dc : T(0));
+        const T cp = delta[c * P.pitch + o] + (pending ? dc : T(0));
         const T rho = q.rho(c);
         pr += cp * cp;
         dr += (rho * dc) * (rho * dc);
@@ -523,9 +626,10 @@ __global__ void settle_kernel(DevProblem P) {
     const int i = P.obs_pt[o], j = P.obs_cam_rank[o] & kCamMask;
 #pragma unroll
     for (int c = 0; c < 9; ++c) {
-      const T d = delta[c * l + o] + (c < 3 ? DX[3 * i + c] : DY[6 * j + c - 3]);
-      delta[c * l + o] = d;
-      P.adual[c * l + o] += (double)d;
+      const long long k = c * P.pitch + o;
+      const T d = delta[k] + (c < 3 ? DX[3 * i + c] : DY[6 * j + c - 3]);
+      delta[k] = d;
+      P.adual[k] += (double)d;
     }
   }
 }
@@ -657,21 +761,21 @@ cudaError_t tile_grid(int* grid) {
 }
 
 template <typename T, int NT, int kS>
-cudaError_t launch_tile(const DevProblem& P, const Params& prm, cudaStream_t s) {
+cudaError_t launch_tile(const DevProblem& P, const TileMaps& M, const Params& prm, cudaStream_t s) {
   int grid = 0;
   const cudaError_t e = tile_grid<T, NT, kS>(&grid);
   if (e != cudaSuccess) return e;
   if (grid > P.n_tiles) grid = P.n_tiles;
-  tile_iterate_kernel<T, NT, kS><<<grid, NT, tile_smem_bytes<T, NT>(), s>>>(P, make_prm<T>(prm));
+  tile_iterate_kernel<T, NT, kS><<<grid, NT, tile_smem_bytes<T, NT>(), s>>>(P, M, make_prm<T>(prm));
   return cudaGetLastError();
 }
 
 template <typename T, int kS>
-cudaError_t launch_tile_sized(const DevProblem& P, const Params& prm, cudaStream_t s) {
+cudaError_t launch_tile_sized(const DevProblem& P, const TileMaps& M, const Params& prm, cudaStream_t s) {
   switch (P.tile_obs) {
-    case 256: return launch_tile<T, 256, kS>(P, prm, s);
-    case 128: return launch_tile<T, 128, kS>(P, prm, s);
-    case 64: return launch_tile<T, 64, kS>(P, prm, s);
+    case 256: return launch_tile<T, 256, kS>(P, M, prm, s);
+    case 128: return launch_tile<T, 128, kS>(P, M, prm, s);
+    case 64: return launch_tile<T, 64, kS>(P, M, prm, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -694,13 +798,86 @@ cudaError_t prepare_tile_kernels() {
   return tile_grid<double, 64, DBA_SOLVER_LBFGS>(&g);
 }
 
-cudaError_t launch_tile_iterate(const DevProblem& P, const Params& prm, bool fp32, cudaStream_t s) {
+namespace {
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encode_fn() {
+  static std::once_flag once;
+  static EncodeTiled fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiled>(p);
+  });
+  return fn;
+}
+
+// rank-1 or rank-2 map of a row-major array: dims[0] innermost (elements), stride1 the
+// byte stride of dimension 1, box the copied extent; out-of-range elements read as zero
+cudaError_t encode(CUtensorMap* map, CUtensorMapDataType type, int rank, const void* base, cuuint64_t dim0,
+                   cuuint64_t dim1, cuuint64_t stride1, cuuint32_t box0, cuuint32_t box1) {
+  EncodeTiled fn = encode_fn();
+  if (!fn) return cudaErrorNotSupported;
+  const cuuint64_t dims[2] = {dim0, dim1};
+  const cuuint64_t strides[1] = {stride1};
+  const cuuint32_t box[2] = {box0, box1};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = fn(map, type, (cuuint32_t)rank, const_cast<void*>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <typename T, int NT>
+cudaError_t encode_maps(const DevProblem& P, TileMaps* M) {
+  using St = TileStage<T, NT>;
+  const cuuint64_t l = (cuuint64_t)P.n_obs, rowT = (cuuint64_t)P.pitch * sizeof(T), rowD = (cuuint64_t)P.pitch * 8;
+  const CUtensorMapDataType tT = sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+  cudaError_t e = encode(&M->delta, tT, 2, P.delta, l, 9, rowT, St::kWT, 9);
+  if (e == cudaSuccess) e = encode(&M->adual, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, P.adual, l, 9, rowD, St::kWD, 9);
+  if (e == cudaSuccess) {
+    if constexpr (sizeof(T) == 4)
+      e = encode(&M->z, CU_TENSOR_MAP_DATA_TYPE_INT64, 1, P.z, l, 1, 16, St::kWZ, 1);
+    else
+      e = encode(&M->z, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, P.z, 2, l, 16, 2, St::kWZ);
+  }
+  if (e == cudaSuccess) e = encode(&M->pt, CU_TENSOR_MAP_DATA_TYPE_INT32, 1, P.obs_pt, l, 1, 16, St::kWI, 1);
+  if (e == cudaSuccess) e = encode(&M->cam, CU_TENSOR_MAP_DATA_TYPE_INT32, 1, P.obs_cam_rank, l, 1, 16, St::kWI, 1);
+  return e;
+}
+
+template <typename T>
+cudaError_t encode_maps_sized(const DevProblem& P, TileMaps* M) {
+  switch (P.tile_obs) {
+    case 256: return encode_maps<T, 256>(P, M);
+    case 128: return encode_maps<T, 128>(P, M);
+    case 64: return encode_maps<T, 64>(P, M);
+    default: return cudaErrorInvalidValue;
+  }
+}
+}  // namespace
+
+cudaError_t encode_tile_maps(const DevProblem& P, bool fp32, TileMaps* M) {
+  *M = TileMaps{};
+  if (P.n_obs <= 0) return cudaSuccess;
+  // the kernel's coordinates are 32-bit; the row pitch keeps every row 16-byte aligned
+  if (P.n_obs > 0x7fffffffLL || P.pitch % 4 != 0) return cudaErrorInvalidValue;
+  return fp32 ? encode_maps_sized<float>(P, M) : encode_maps_sized<double>(P, M);
+}
+
+cudaError_t launch_tile_iterate(const DevProblem& P, const TileMaps& M, const Params& prm, bool fp32,
+                                cudaStream_t s) {
   if (P.n_tiles == 0) return cudaSuccess;
   if (prm.solver == DBA_SOLVER_LBFGS)
-    return fp32 ? launch_tile_sized<float, DBA_SOLVER_LBFGS>(P, prm, s)
-                : launch_tile_sized<double, DBA_SOLVER_LBFGS>(P, prm, s);
-  return fp32 ? launch_tile_sized<float, DBA_SOLVER_GN>(P, prm, s)
-              : launch_tile_sized<double, DBA_SOLVER_GN>(P, prm, s);
+    return fp32 ? launch_tile_sized<float, DBA_SOLVER_LBFGS>(P, M, prm, s)
+                : launch_tile_sized<double, DBA_SOLVER_LBFGS>(P, M, prm, s);
+  return fp32 ? launch_tile_sized<float, DBA_SOLVER_GN>(P, M, prm, s)
+              : launch_tile_sized<double, DBA_SOLVER_GN>(P, M, prm, s);
 }
 
 cudaError_t launch_finalize(const DevProblem& P, bool fp32, cudaStream_t s) {

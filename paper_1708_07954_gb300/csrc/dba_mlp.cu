@@ -54,7 +54,7 @@ __global__ void harvest_kernel(DevProblem P, Prm<T> q, int pending, long long st
                                float* targs) {
   const long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (k >= cap) return;
-  const long long l = P.n_obs, o = k * stride;
+  const long long l = P.pitch, o = k * stride;  // l: row stride of delta and adual
   float* f = feats + k * kMlpIn;
   float* g = targs + k * kMlpOut;
   const int i = P.obs_pt[o], j = P.obs_cam_rank[o] & kCamMask;
@@ -467,8 +467,8 @@ __global__ void __launch_bounds__(kInferThreads, 4) mlp_infer_kernel(DevProblem 
   const uint32_t tmem = S.tmem;
   const uint32_t trow = tmem + ((uint32_t)(32 * (t / 32)) << 16);  // this warp's 32 lanes
   const uint32_t act = smem_u32(S.act), w = smem_u32(S.w);
-  const long long l = P.n_obs;
-  const long long rows = kFromState ? l : n;
+  const long long l = P.pitch;  // row stride of delta, adual and mlp_start
+  const long long rows = kFromState ? P.n_obs : n;
   int pending = 0;
   if (kFromState) pending = __ldg(&P.ctl->pending);
   uint32_t phase = 0;
