@@ -286,56 +286,60 @@ __device__ __forceinline__ void process_tile(const DevProblem& P, const Prm<T>& 
   }
   __syncthreads();
 
-  // Eq. (10): per point run, one thread per (run, coordinate); run r is point pt_lo + r.
+  // Eq. (10) per point run and the per-tile partial sums of Eq. (11) per camera run, one
+  // thread per (run, coordinate): point tasks first, camera tasks on the threads after
+  // them, so a thread takes a second task only when the two lists exceed the block.
+  // Point run r is point pt_lo + r.
   const int nxt = cur ^ 1;
-  for (int task = t; task < 3 * ti.nr; task += NT) {
-    const int r = task / 3, c = task % 3;
-    const int2 se = S.pseg[r];
-    double sum;
-    T acc = 0;
-    if (exact) {
-      sum = 0.0;
-      for (int e = se.x; e < se.x + se.y; ++e) sum += s_buf[c][e];
-    } else {
-      for (int e = se.x; e < se.x + se.y; ++e) acc += s_t[c][e];
-      sum = to_f64<T>(acc);
-    }
-    const int slot = S.pslot[r];
-    if (slot < 0) {
-      const long long k = 3 * ((long long)ti.pt_lo + r) + c;
-      const double xo = S.X[task];
-      if (std::is_same<T, float>::value && !exact) {
-        // FP32 offsets: their mean is formed in FP32 and added to the FP64 consensus, which
-        // keeps the divide and the conversions off the FP64 pipe
-        const T inc = acc * Num<T>::rcp((T)se.y);
-        const double xn = xo + to_f64<T>(inc);
-        P.X[nxt][k] = xn;
-        static_cast<T*>(P.Xm)[k] = from_f64<T>(xn);
-        static_cast<T*>(P.DX)[k] = -inc;
+  const int n_pt_tasks = 3 * ti.nr, n_tasks = n_pt_tasks + 6 * ti.nc;
+  for (int task = t; task < n_tasks; task += NT) {
+    if (task < n_pt_tasks) {
+      const int r = task / 3, c = task % 3;
+      const int2 se = S.pseg[r];
+      double sum;
+      T acc = 0;
+      if (exact) {
+        sum = 0.0;
+        for (int e = se.x; e < se.x + se.y; ++e) sum += s_buf[c][e];
       } else {
-        const double xn = xo + sum / (double)se.y;
-        P.X[nxt][k] = xn;
-        static_cast<T*>(P.Xm)[k] = from_f64<T>(xn);
-        static_cast<T*>(P.DX)[k] = from_f64<T>(xo - xn);
+        for (int e = se.x; e < se.x + se.y; ++e) acc += s_t[c][e];
+        sum = to_f64<T>(acc);
+      }
+      const int slot = S.pslot[r];
+      if (slot < 0) {
+        const long long k = 3 * ((long long)ti.pt_lo + r) + c;
+        const double xo = S.X[task];
+        if (std::is_same<T, float>::value && !exact) {
+          // FP32 offsets: their mean is formed in FP32 and added to the FP64 consensus, which
+          // keeps the divide and the conversions off the FP64 pipe
+          const T inc = acc * Num<T>::rcp((T)se.y);
+          const double xn = xo + to_f64<T>(inc);
+          P.X[nxt][k] = xn;
+          static_cast<T*>(P.Xm)[k] = from_f64<T>(xn);
+          static_cast<T*>(P.DX)[k] = -inc;
+        } else {
+          const double xn = xo + sum / (double)se.y;
+          P.X[nxt][k] = xn;
+          static_cast<T*>(P.Xm)[k] = from_f64<T>(xn);
+          static_cast<T*>(P.DX)[k] = from_f64<T>(xo - xn);
+        }
+      } else {
+        P.pt_part[3 * slot + c] = sum;
       }
     } else {
-      P.pt_part[3 * slot + c] = sum;
+      const int ct = task - n_pt_tasks, r = ct / 6, c = ct % 6;
+      const int2 se = S.cseg[r];
+      double sum;
+      if (exact) {
+        sum = 0.0;
+        for (int e = se.x; e < se.x + se.y; ++e) sum += s_buf[3 + c][e];
+      } else {
+        T acc = 0;
+        for (int e = se.x; e < se.x + se.y; ++e) acc += s_t[3 + c][e];
+        sum = to_f64<T>(acc);
+      }
+      P.cam_part[6 * S.cslot[r] + c] = sum;
     }
-  }
-  // Eq. (11): per camera run, partial sums for the finalize kernel.
-  for (int task = t; task < 6 * ti.nc; task += NT) {
-    const int r = task / 6, c = task % 6;
-    const int2 se = S.cseg[r];
-    double sum;
-    if (exact) {
-      sum = 0.0;
-      for (int e = se.x; e < se.x + se.y; ++e) sum += s_buf[3 + c][e];
-    } else {
-      T acc = 0;
-      for (int e = se.x; e < se.x + se.y; ++e) acc += s_t[3 + c][e];
-      sum = to_f64<T>(acc);
-    }
-    P.cam_part[6 * S.cslot[r] + c] = sum;
   }
 }
 
