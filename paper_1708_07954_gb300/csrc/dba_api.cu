@@ -219,28 +219,9 @@ void build_layout(int n_cams, int n_pts, long long n_obs, const int32_t* pt_idx,
   L.cam_count.assign(n_cams, 0);
   for (int t = 0; t < T; ++t)
     for (int j = 0; j < n_cams; ++j) L.cam_count[j] += camc[t][j];
-  std::vector<long long> pstart(n_pts + 1, 0);
-  for (int i = 0; i < n_pts; ++i) pstart[i + 1] = pstart[i] + count[i];
-  std::vector<int> by_pt(n_obs);
-  {
-    parallel_chunks(n_pts, T, [&](int, long long lo, long long hi) {
-      for (long long i = lo; i < hi; ++i) {
-        long long off = pstart[i];
-        for (int t = 0; t < T; ++t) {
-          const int c = hist[t][i];
-          hist[t][i] = (int)off;  // first slot of chunk t in point i
-          off += c;
-        }
-      }
-    });
-    parallel_chunks(n_obs, T, [&](int t, long long lo, long long hi) {
-      std::vector<int>& h = hist[t];
-      for (long long o = lo; o < hi; ++o) by_pt[h[pt_idx[o]]++] = (int)o;
-    });
-  }
   // internal point numbering: observed points by first camera (ties by index: a counting
   // sort over first cameras), then unobserved ones (first camera n_cams)
-  std::vector<int> order(n_pts);
+  std::vector<int> order(n_pts), inv(n_pts);
   {
     std::vector<int> fc(n_cams + 2, 0);
     for (int i = 0; i < n_pts; ++i) fc[min_cam[i] + 1] += 1;
@@ -249,31 +230,71 @@ void build_layout(int n_cams, int n_pts, long long n_obs, const int32_t* pt_idx,
   }
   L.pt_perm = order;
   L.pt_count.resize(n_pts);
-  for (int k = 0; k < n_pts; ++k) L.pt_count[k] = count[order[k]];
+  for (int k = 0; k < n_pts; ++k) {
+    L.pt_count[k] = count[order[k]];
+    inv[order[k]] = k;
+  }
   int n_obs_pts = 0;
   while (n_obs_pts < n_pts && L.pt_count[n_obs_pts] > 0) ++n_obs_pts;
+  std::vector<long long> kpos(n_pts + 1, 0);  // first internal position of each internal point
+  for (int k = 0; k < n_pts; ++k) kpos[k + 1] = kpos[k] + L.pt_count[k];
 
-  // each point's observations by camera (ties by caller index), written in internal order
-  std::vector<long long> kpos(n_obs_pts + 1, 0);
-  for (int k = 0; k < n_obs_pts; ++k) kpos[k + 1] = kpos[k] + L.pt_count[k];
+  // observations scattered straight into internal order (a stable counting sort by
+  // point: chunk t's observations of a point follow those of chunks before it), with
+  // their cameras alongside
   L.perm.resize(n_obs);
   L.obs_pt.resize(n_obs);
   L.obs_cam.resize(n_obs);
   L.obs_cam_rank.resize(n_obs);
-  parallel_chunks(n_obs_pts, T, [&](int, long long lo, long long hi) {
-    for (long long k = lo; k < hi; ++k) {
-      const int i = order[k];
-      const long long s = pstart[i];
-      const int c = count[i];
-      std::sort(by_pt.begin() + s, by_pt.begin() + s + c, [&](int a, int b) {
-        return cam_idx[a] != cam_idx[b] ? cam_idx[a] < cam_idx[b] : a < b;
-      });
-      for (int q = 0; q < c; ++q) {
-        const int o = by_pt[s + q];
-        L.perm[kpos[k] + q] = o;
-        L.obs_pt[kpos[k] + q] = (int)k;
-        L.obs_cam[kpos[k] + q] = cam_idx[o];
+  parallel_chunks(n_pts, T, [&](int, long long lo, long long hi) {
+    for (long long i = lo; i < hi; ++i) {
+      long long off = kpos[inv[i]];
+      for (int t = 0; t < T; ++t) {
+        const int c = hist[t][i];
+        hist[t][i] = (int)off;  // first position of chunk t's observations of point i
+        off += c;
       }
+    }
+  });
+  parallel_chunks(n_obs, T, [&](int t, long long lo, long long hi) {
+    std::vector<int>& h = hist[t];
+    for (long long o = lo; o < hi; ++o) {
+      const int q = h[pt_idx[o]]++;
+      L.perm[q] = o;
+      L.obs_cam[q] = cam_idx[o];
+    }
+  });
+  // each point's observations by camera, ties in caller order (the scatter left them in
+  // caller order, so a stable sort by camera)
+  parallel_chunks(n_obs_pts, T, [&](int, long long lo, long long hi) {
+    std::vector<std::pair<int, long long>> pr;
+    for (long long k = lo; k < hi; ++k) {
+      const long long s = kpos[k];
+      const int c = L.pt_count[k];
+      long long* bo = L.perm.data() + s;
+      int* bc = L.obs_cam.data() + s;
+      if (c <= 32) {
+        for (int a = 1; a < c; ++a) {
+          const int kc = bc[a];
+          const long long ko = bo[a];
+          int b = a - 1;
+          for (; b >= 0 && bc[b] > kc; --b) {
+            bc[b + 1] = bc[b];
+            bo[b + 1] = bo[b];
+          }
+          bc[b + 1] = kc;
+          bo[b + 1] = ko;
+        }
+      } else {
+        pr.resize(c);
+        for (int q = 0; q < c; ++q) pr[q] = {bc[q], bo[q]};
+        std::sort(pr.begin(), pr.end());
+        for (int q = 0; q < c; ++q) {
+          bc[q] = pr[q].first;
+          bo[q] = pr[q].second;
+        }
+      }
+      for (int q = 0; q < c; ++q) L.obs_pt[s + q] = (int)k;
     }
   });
 
