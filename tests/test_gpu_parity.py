@@ -150,12 +150,14 @@ def test_fp32_path_workload1_final_accuracy():
     assert ce.max() <= 1e-4, ce.max()
 
 
-def test_fp32_parity_per_iteration_small():
+@pytest.mark.parametrize("tile", [64, 128, 256])
+def test_fp32_parity_per_iteration_small(tile):
     """FP32 local solves track the FP64 oracle iteration by iteration: consensus projections
     within 1e-3 px RMS of the oracle's, parameters within 1e-4 relative (FP32 unit roundoff
-    6e-8 amplified by the conditioning of weakly triangulated points)."""
+    6e-8 amplified by the conditioning of weakly triangulated points).  Every tile size, so
+    every width of the staged observation windows."""
     sc = S.scene1(n_pts=2000, n_cams=32, seed=21)
-    with dba.Solver(sc, precision=dba.DBA_PREC_F32_LOCAL) as s:
+    with dba.Solver(sc, precision=dba.DBA_PREC_F32_LOCAL, tile_obs=tile) as s:
         cfg = oracle_cfg(sc, s)
         st = O.State(sc)
         for _ in range(10):
