@@ -340,6 +340,17 @@ def run_ours(args, rank, world, local_rank):
     clk = clocks.stop()
     ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
     value = job_throughput(world, sc.n_obs, args.steps, ms)
+    # the same steps again as five separately timed runs: their per-step times and median
+    runs = []
+    for _ in range(5):
+        r0 = torch.cuda.Event(enable_timing=True)
+        r1 = torch.cuda.Event(enable_timing=True)
+        n_run = max(1, args.steps // 5)
+        r0.record(stream)
+        solver.iterate(n_run, stats=False)
+        r1.record(stream)
+        torch.cuda.synchronize()
+        runs.append(max_over_ranks(r0.elapsed_time(r1), world, "cuda") / n_run)
     final = solver.evaluate()
 
     # per-kernel device time (CUDA events around each launch on the same stream)
@@ -449,6 +460,7 @@ def run_ours(args, rank, world, local_rank):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "admm_iterations_per_s": 1e3 * args.steps / ms,
+            "ms_per_step_runs": runs, "ms_per_step_median_of_runs": float(np.median(runs)),
             "vs_baseline": None, "dtype": "f32+f64" if fp32 else "f64", "data": "synthetic",
             "config": {"workload": sc.name, "n_obs": sc.n_obs, "n_cams": sc.n_cams, "n_pts": sc.n_pts,
                        "n_scenes": 1 if sc.scene_off is None else len(sc.scene_off) - 1,
