@@ -181,6 +181,16 @@ dba_status dba_set_state(dba_ctx* ctx, const double* copies, const double* duals
  * call: names[i] (static strings) and ms[i] for i < *count (in: capacity). */
 dba_status dba_profile(dba_ctx* ctx, int n_iters, const char** names, double* ms, int* count);
 
+/* Fault injection for tests of failure detection.  While `on` is nonzero, the
+ * tile kernel announces each tile's tensor copies on its mbarrier without
+ * issuing them, so the bounded wait for them (about two seconds) runs out:
+ * the kernel sets an error bit and returns, and dba_iterate reports
+ * DBA_ETIMEOUT.  The CUDA context stays usable; the iteration's state is not,
+ * so restore one with dba_set_state (which also clears the error bit) before
+ * iterating again.  EINVAL on a null context, ESTATE before
+ * dba_set_observations. */
+dba_status dba_inject_copy_stall(dba_ctx* ctx, int on);
+
 /* Sizes of the internal observation layout after dba_set_observations, for
  * traffic models: out[0] tiles, out[1] observations per tile (block size),
  * out[2] point runs, out[3] camera runs (= camera partial slots), out[4]

@@ -1032,6 +1032,15 @@ dba_status dba_set_state(dba_ctx* ctx, const double* copies, const double* duals
   return upload_state(ctx, cams, pts, copies, duals);
 }
 
+dba_status dba_inject_copy_stall(dba_ctx* ctx, int on) {
+  if (!ctx) return DBA_EINVAL;
+  if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_inject_copy_stall before dba_set_observations");
+  const unsigned int v = on ? 1u : 0u;
+  DBA_CUDA(cudaMemcpyAsync(&ctx->P.ctl->inject, &v, sizeof v, cudaMemcpyHostToDevice, ctx->stream), "inject");
+  DBA_CUDA(cudaStreamSynchronize(ctx->stream), "inject");
+  return DBA_OK;
+}
+
 dba_status dba_profile(dba_ctx* ctx, int n_iters, const char** names, double* ms, int* count) {
   if (!ctx || !count) return DBA_EINVAL;
   if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_profile before dba_set_observations");

@@ -20,7 +20,8 @@ struct alignas(16) DevCtl {
   int exact;        // 1: duals may not sum to zero per point/camera (first iteration after set_state)
   unsigned long long k;   // iterations run
   unsigned int done;      // finalize-kernel block counter
-  unsigned int pad2;
+  unsigned int inject;    // fault injection for tests: bit 0 = the tile kernel announces its
+                          // tensor copies but does not issue them (its bounded wait runs out)
 };
 
 // One tile of the observation layout: observations [o0, o0 + n), point runs

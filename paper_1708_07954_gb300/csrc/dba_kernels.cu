@@ -137,32 +137,60 @@ __device__ __forceinline__ void tma_2d(void* dst, const CUtensorMap* map, int x,
       : "memory");
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ uint32_t mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done;
+}
+
+// The polling loop of mbar_wait, out of line: false once about two seconds (global timer,
+// first read after 256 polls) or 2^22 polls have passed without completion.
+__device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity) {
+  constexpr unsigned long long kLimitNs = 2000000000ull;
+  unsigned long long t0 = 0;
+  for (int it = 0; it < (1 << 22); ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if ((it & 255) == 255) {
+      const unsigned long long now = global_ns();
+      if (t0 == 0) t0 = now;
+      else if (now - t0 > kLimitNs) return false;
+    }
+  }
+  return false;
+}
+
 // Bounded wait for completion `parity` of the mbarrier at bar; false after the limit.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  uint32_t done = 0;
-  for (int it = 0; it < (1 << 22) && !done; ++it)
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-  return done != 0;
+  return mbar_try(bar, parity) || mbar_wait_slow(bar, parity);
 }
 
 // Issues the copies of one tile into stage S: the observation rows by tensor copies from
 // thread 0 (completion on bar), the run tables and consensus by cp.async from every
-// thread (one commit group).
+// thread (one commit group).  stall (fault injection): the tensor copies are announced
+// on bar but not issued, so the wait for them runs out.
 template <typename T, int NT>
 __device__ __forceinline__ void stage_tile(const DevProblem& P, const TileMaps& M, TileStage<T, NT>& S,
-                                           const TileInfo& ti, int cur, uint32_t bar) {
+                                           const TileInfo& ti, int cur, uint32_t bar, bool stall) {
   using St = TileStage<T, NT>;
   const int t = threadIdx.x;
   if (t == 0) {
-    const int o0 = ti.o0;
-    const int xT = o0 & ~(16 / (int)sizeof(T) - 1), xD = o0 & ~1, xI = o0 & ~3;
     // generic-proxy reads of this stage (the tile before last) precede the async writes
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(St::kTxBytes) : "memory");
+  }
+  if (t == 0 && !stall) {
+    const int o0 = ti.o0;
+    const int xT = o0 & ~(16 / (int)sizeof(T) - 1), xD = o0 & ~1, xI = o0 & ~3;
     tma_2d(S.delta, &M.delta, xT, 0, bar);
     tma_2d(S.delta + St::kSlabT, &M.delta, xT + St::kWT, 0, bar);
     tma_2d(S.adual, &M.adual, xD, 0, bar);
@@ -357,6 +385,7 @@ __global__ void __launch_bounds__(NT, 2)
   // read-only-cache load per thread (cached per SM) instead of same-address L2 traffic.
   const int4 ctl = __ldg(reinterpret_cast<const int4*>(P.ctl));
   const int cur = ctl.x, pending = ctl.y, exact = ctl.w;
+  const bool stall = (__ldg(&P.ctl->inject) & 1u) != 0;
   int tile = blockIdx.x;
   if (tile >= P.n_tiles) return;
   if (threadIdx.x == 0) {
@@ -366,7 +395,7 @@ __global__ void __launch_bounds__(NT, 2)
   }
   __syncthreads();
   TileInfo info = load_tile_info(P.tiles, tile);
-  stage_tile<T, NT>(P, M, stage[0], info, cur, bar0);
+  stage_tile<T, NT>(P, M, stage[0], info, cur, bar0, stall);
   int next = tile + gridDim.x;
   TileInfo info_next{};
   if (next < P.n_tiles) info_next = load_tile_info(P.tiles, next);
@@ -381,7 +410,7 @@ __global__ void __launch_bounds__(NT, 2)
     // barrier that ended it) and land while this tile is solved; stage s serves tiles
     // k = s, s + 2, ..., and its mbarrier completes once per use (parity (k >> 1) & 1)
     const int sn = (k + 1) & 1;
-    if (next < P.n_tiles) stage_tile<T, NT>(P, M, stage[sn], info_next, cur, sn ? bar1 : bar0);
+    if (next < P.n_tiles) stage_tile<T, NT>(P, M, stage[sn], info_next, cur, sn ? bar1 : bar0, stall);
     const int after = next + gridDim.x;
     TileInfo info_after{};
     if (after < P.n_tiles) info_after = load_tile_info(P.tiles, after);  // used two tiles later

@@ -23,7 +23,7 @@ DBA_SOLVER_GN, DBA_SOLVER_LBFGS = 0, 1
 EXPORTED = [
     "dba_config_default", "dba_create", "dba_set_observations", "dba_set_ground_truth", "dba_iterate",
     "dba_iterate_until", "dba_evaluate", "dba_get_params", "dba_get_state", "dba_set_state",
-    "dba_profile", "dba_layout", "dba_evaluate_noalloc", "dba_set_scenes", "dba_scene_stats",
+    "dba_profile", "dba_inject_copy_stall", "dba_layout", "dba_evaluate_noalloc", "dba_set_scenes", "dba_scene_stats",
     "dba_last_error", "dba_destroy", "dba_mlp_create", "dba_mlp_destroy", "dba_mlp_last_error",
     "dba_mlp_get_params", "dba_mlp_set_params", "dba_mlp_harvest", "dba_mlp_fit_normalizer",
     "dba_mlp_loss_grad", "dba_mlp_train", "dba_mlp_predict", "dba_set_warm_start",
@@ -96,6 +96,7 @@ def load():
     L.dba_get_params.argtypes = [vp, dp, dp]
     L.dba_get_state.argtypes = [vp, dp, dp]
     L.dba_set_state.argtypes = [vp, dp, dp, dp, dp]
+    L.dba_inject_copy_stall.argtypes = [vp, ctypes.c_int]
     L.dba_profile.argtypes = [vp, ctypes.c_int, P(ctypes.c_char_p), dp, P(ctypes.c_int)]
     L.dba_layout.argtypes = [vp, P(ctypes.c_int64), P(ctypes.c_int)]
     L.dba_set_scenes.argtypes = [vp, ctypes.c_int32, P(ctypes.c_int64), ip, ip]
@@ -398,6 +399,10 @@ class Solver:
 
     def profile(self, n):
         return dba_profile(self.ctx, n)
+
+    def inject_copy_stall(self, on):
+        """Fault injection (tests): the tile kernel's wait for its tensor copies runs out."""
+        _check(load().dba_inject_copy_stall(self.ctx, 1 if on else 0), self.ctx)
 
     def layout(self):
         return dba_layout(self.ctx)

@@ -76,6 +76,7 @@ def test_block_null_arguments(lib):
     assert lib.dba_block_create(None, 1, 1, None) == dba.DBA_EINVAL
     assert lib.dba_block_iterate(None, 1, None) == dba.DBA_EINVAL
     assert lib.dba_block_get_params(None, None, None) == dba.DBA_EINVAL
+    assert lib.dba_inject_copy_stall(None, 1) == dba.DBA_EINVAL
     counts = (ctypes.c_int64 * dba.DBA_BLOCK_SIZE_CLASSES)()
     assert lib.dba_block_size_classes(None, counts) == dba.DBA_EINVAL
     lib.dba_block_destroy(None)

@@ -288,6 +288,35 @@ def test_resume_from_arbitrary_duals_matches_oracle():
 
 
 @pytest.mark.parametrize("prec", [dba.DBA_PREC_F64, dba.DBA_PREC_F32_LOCAL])
+def test_stalled_tensor_copies_time_out_and_the_context_recovers(prec):
+    """Failure detection without a GPU fault: with the copy stall injected, the tile
+    kernel's bounded mbarrier wait runs out (about two seconds), it sets its error bit
+    and returns, and dba_iterate reports DBA_ETIMEOUT.  After restoring a checkpoint the
+    same context iterates on and matches the oracle."""
+    sc = S.scene1(n_pts=800, n_cams=16, seed=53)
+    with dba.Solver(sc, precision=prec) as s:
+        cfg = oracle_cfg(sc, s)
+        s.iterate(2, stats=False)
+        copies, duals = s.state()
+        cams, pts = s.params()
+        s.inject_copy_stall(True)
+        with pytest.raises(dba.DbaError) as ei:
+            s.iterate(1, stats=False)
+        assert ei.value.status == dba.DBA_ETIMEOUT
+        assert "tensor copies" in str(ei.value)
+        s.inject_copy_stall(False)
+        s.set_state(copies, duals, cams, pts)
+        st = O.State(sc)
+        st.copies[:], st.duals[:], st.cams[:], st.pts[:] = copies, duals, cams, pts
+        for _ in range(3):
+            s.iterate(1, stats=False)
+            st.iterate(cfg, 1)
+        c2, p2 = s.params()
+        tol = TOL64 if prec == dba.DBA_PREC_F64 else 1e-4
+        assert relerr(c2, st.cams) <= tol and relerr(p2, st.pts) <= tol
+
+
+@pytest.mark.parametrize("prec", [dba.DBA_PREC_F64, dba.DBA_PREC_F32_LOCAL])
 def test_checkpoint_resume_matches_continuous_run(prec):
     sc = S.scene1(n_pts=1000, n_cams=16, seed=31)
     with dba.Solver(sc, precision=prec) as a, dba.Solver(sc, precision=prec) as b:
