@@ -233,8 +233,8 @@ dba_status dba_evaluate_noalloc(const dba_config* cfg, int32_t n_cams, int32_t n
  * local solve (Eq. 9) from the residual, Jacobian, offset and dual at the plain start, all in
  * coordinates scaled by sqrt(rho).  Inference runs on BF16 tensor cores (tcgen05, FP32
  * accumulation) before each iteration's local solves; each local solve starts from the
- * learned candidate only if that lowers Eq. (9) (the Levenberg-Marquardt solve is both the
- * judge and the fallback).  The network is trained on the GPU by this library's own FP32
+ * learned candidate only if that lowers Eq. (9), and the Levenberg-Marquardt solve
+ * refines whichever start it keeps.  The network is trained on the GPU by this library's own FP32
  * forward/backward/Adam kernels on targets harvested from long local solves.  The dba_mlp_*
  * calls run on a stream of the network that is ordered after work queued on the legacy
  * default stream and return when done; buffers filled on other streams must be complete. */

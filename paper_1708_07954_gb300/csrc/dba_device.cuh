@@ -336,7 +336,7 @@ __device__ __forceinline__ void local_solve(T z0, T z1, const T vbar[9], const T
     Pose<T> Pa;
     pose_at(va, q.eps, Pa);
     const T La = local_objective(da, a, Pa, z0, z1, q);
-    if (La < L) {  // the plain start stays unless the candidate is better (judge and fallback)
+    if (La < L) {  // the plain start stays unless the candidate lowers Eq. (9) (the fallback)
 #pragma unroll
       for (int c = 0; c < 9; ++c) d[c] = da[c];
       P = Pa;
