@@ -421,6 +421,48 @@ __device__ __forceinline__ void hidden_epilogue(uint32_t trow, const float* bias
   }
 }
 
+// Prefetches into L2 the state rows of the 128 observations from nb on (offsets and
+// duals, nine rows each, pixels, point and camera indices), one 128-byte line per
+// thread and pass, clipped to the arrays.
+template <typename T>
+__device__ __forceinline__ void prefetch_state_l2(const DevProblem& P, long long nb, int t) {
+  constexpr int kLT = 128 * (int)sizeof(T) / 128 + 1, kLD = 8 + 1;
+  constexpr int kLZ = 128 * 2 * (int)sizeof(T) / 128 + 1, kLI = 4 + 1;
+  constexpr int kLines = 9 * kLT + 9 * kLD + kLZ + 2 * kLI;
+  const long long n = P.n_obs, l = P.pitch;
+  if (nb >= n) return;
+  const long long m = (n - nb < 128 ? n - nb : 128);  // observations in the tile
+  for (int e = t; e < kLines; e += kInferThreads) {
+    const char* base;
+    long long bytes;
+    int line;
+    if (e < 9 * kLT) {
+      base = static_cast<const char*>(P.delta) + ((e / kLT) * l + nb) * (long long)sizeof(T);
+      bytes = m * (long long)sizeof(T);
+      line = e % kLT;
+    } else if (e < 9 * kLT + 9 * kLD) {
+      const int f = e - 9 * kLT;
+      base = reinterpret_cast<const char*>(P.adual + (f / kLD) * l + nb);
+      bytes = m * 8;
+      line = f % kLD;
+    } else if (e < 9 * kLT + 9 * kLD + kLZ) {
+      base = static_cast<const char*>(P.z) + nb * 2 * (long long)sizeof(T);
+      bytes = m * 2 * (long long)sizeof(T);
+      line = e - 9 * kLT - 9 * kLD;
+    } else {
+      const int f = e - 9 * kLT - 9 * kLD - kLZ;
+      base = reinterpret_cast<const char*>((f < kLI ? P.obs_pt : P.obs_cam_rank) + nb);
+      bytes = m * 4;
+      line = f % kLI;
+    }
+    // the line holding byte 128 * line of the range, counted from the range's aligned start
+    const uintptr_t a0 = reinterpret_cast<uintptr_t>(base) & ~(uintptr_t)127;
+    const uintptr_t a = a0 + 128 * (uintptr_t)line;
+    if (a < reinterpret_cast<uintptr_t>(base) + (uintptr_t)bytes)
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+  }
+}
+
 // Persistent inference.  kFromState: features from the ADMM state of every
 // observation, output = candidate start d0 + step / r written to P.mlp_start;
 // else features from `feats` (n rows), output = the network's 16 standardised
@@ -497,6 +539,8 @@ __global__ void __launch_bounds__(kInferThreads, 4) mlp_infer_kernel(DevProblem 
         const typename Num<T>::V2 zz = static_cast<const typename Num<T>::V2*>(P.z)[o];
         ok = warm_features<T>(zz.x, zz.y, vbar, aT, d0, q, f, r);
       }
+      // the next tile's state streams into L2 while this tile runs through the network
+      prefetch_state_l2<T>(P, base + (long long)gridDim.x * kInferThreads, t);
     } else if (o < rows) {
       const float4* src = reinterpret_cast<const float4*>(feats + o * kMlpIn);
 #pragma unroll
