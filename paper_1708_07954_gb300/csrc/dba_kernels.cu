@@ -219,6 +219,15 @@ __device__ __forceinline__ void stage_tile(const DevProblem& P, const TileMaps& 
   const double* X = P.X[cur] + 3 * (long long)ti.pt_lo;
   for (int e = t; e < 3 * ti.nr; e += NT) cp_async<8>(&S.X[e], X + e);
   cp_async_commit();
+  // the T mirror and last change of the tile's point consensus (read by its local solves
+  // and dual ascent; written an iteration ago, so mostly out of L2): prefetched into L2,
+  // one 128-byte line per thread
+  if (t < 64) {
+    const T* row = static_cast<const T*>(t < 32 ? P.Xm : P.DX) + 3 * (long long)ti.pt_lo;
+    const uintptr_t lo = reinterpret_cast<uintptr_t>(row);
+    const uintptr_t a = (lo & ~(uintptr_t)127) + 128 * (uintptr_t)(t & 31);
+    if (a < lo + 3 * (uintptr_t)ti.nr * sizeof(T)) asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+  }
 }
 
 // One tile from its staged inputs: deferred dual ascent, local solves, run sums.
