@@ -352,11 +352,16 @@ void build_layout(int n_cams, int n_pts, long long n_obs, const int32_t* pt_idx,
   std::vector<std::vector<int>> t_cam(Tt);
   parallel_chunks(n_tiles, Tt, [&](int t, long long lo, long long hi) {
     std::vector<int> idx;
+    std::vector<unsigned long long> key;
     for (long long q0 = lo; q0 < hi; ++q0) {
       dba::TileInfo& ti = L.tiles[q0];
+      // the tile's observations by camera, ties in tile order: sort (camera, position) keys
+      key.resize(ti.n);
+      for (int q = 0; q < ti.n; ++q)
+        key[q] = ((unsigned long long)(unsigned)L.obs_cam[ti.o0 + q] << 32) | (unsigned)q;
+      std::sort(key.begin(), key.end());
       idx.resize(ti.n);
-      for (int q = 0; q < ti.n; ++q) idx[q] = ti.o0 + q;
-      std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return L.obs_cam[a] < L.obs_cam[b]; });
+      for (int q = 0; q < ti.n; ++q) idx[q] = ti.o0 + (int)(key[q] & 0xffffffffu);
       for (int r = 0; r < (int)idx.size(); ++r) L.obs_cam_rank[idx[r]] = L.obs_cam[idx[r]] | (r << 24);
       ti.c0 = (int)t_cseg[t].size();  // local; shifted below
       int r = 0;
