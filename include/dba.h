@@ -181,6 +181,24 @@ dba_status dba_set_state(dba_ctx* ctx, const double* copies, const double* duals
  * call: names[i] (static strings) and ms[i] for i < *count (in: capacity). */
 dba_status dba_profile(dba_ctx* ctx, int n_iters, const char** names, double* ms, int* count);
 
+/* The internal observation order and tile table that dba_set_observations builds
+ * for these indices and tile size (64, 128 or 256), computed on the host only (no
+ * device), for inspection and tests.  Outputs, caller-allocated, any may be NULL:
+ *   perm[n_obs]        caller index of the observation at each internal position;
+ *   point[n_obs]       internal point id at each position (points ordered by their
+ *                      smallest observing camera, then caller index; each point's
+ *                      observations contiguous and ordered by camera, then caller index);
+ *   point_perm[n_pts]  caller id of each internal point (unobserved points last);
+ *   cam_rank[n_obs]    the position's rank in its tile's camera order;
+ *   tile_start[n_obs + 1]  first position of each tile, then n_obs after the last;
+ *   *n_tiles           number of tiles (a track longer than tile_obs is cut into
+ *                      tiles of its own; other tiles hold whole tracks).
+ * EINVAL as dba_set_observations or for another tile size; message in
+ * dba_last_error(NULL). */
+dba_status dba_build_layout(int32_t n_cams, int32_t n_pts, int64_t n_obs, const int32_t* pt_idx,
+                            const int32_t* cam_idx, int tile_obs, int64_t* perm, int32_t* point,
+                            int32_t* point_perm, int32_t* cam_rank, int64_t* tile_start, int64_t* n_tiles);
+
 /* Fault injection for tests of failure detection.  While `on` is nonzero, the
  * tile kernel announces each tile's tensor copies on its mbarrier without
  * issuing them, so the bounded wait for them (about two seconds) runs out:

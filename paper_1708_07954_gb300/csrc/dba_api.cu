@@ -1037,6 +1037,45 @@ dba_status dba_set_state(dba_ctx* ctx, const double* copies, const double* duals
   return upload_state(ctx, cams, pts, copies, duals);
 }
 
+dba_status dba_build_layout(int32_t n_cams, int32_t n_pts, int64_t n_obs, const int32_t* pt_idx,
+                            const int32_t* cam_idx, int tile_obs, int64_t* perm, int32_t* point,
+                            int32_t* point_perm, int32_t* cam_rank, int64_t* tile_start, int64_t* n_tiles) {
+  if (n_cams <= 0 || n_pts <= 0 || n_obs <= 0 || n_obs > (int64_t)0x7fffffff || n_cams > dba::kCamMask ||
+      !pt_idx || !cam_idx) {
+    g_create_error = "dba_build_layout: sizes out of range or null index array";
+    return DBA_EINVAL;
+  }
+  if (tile_obs != 64 && tile_obs != 128 && tile_obs != 256) {
+    g_create_error = "dba_build_layout: tile_obs must be 64, 128 or 256";
+    return DBA_EINVAL;
+  }
+  const long long bad = first_bad_index(pt_idx, cam_idx, n_obs, n_pts, n_cams);
+  if (bad >= 0) {
+    g_create_error = "dba_build_layout: observation " + std::to_string(bad) + " has an index out of range";
+    return DBA_EINVAL;
+  }
+  try {
+    HostLayout L;
+    build_layout(n_cams, n_pts, n_obs, pt_idx, cam_idx, tile_obs, L);
+    for (long long o = 0; o < n_obs; ++o) {
+      if (perm) perm[o] = L.perm[o];
+      if (point) point[o] = L.obs_pt[o];
+      if (cam_rank) cam_rank[o] = (int32_t)((unsigned int)L.obs_cam_rank[o] >> 24);
+    }
+    if (point_perm)
+      for (int k = 0; k < n_pts; ++k) point_perm[k] = L.pt_perm[k];
+    if (tile_start) {
+      for (size_t q = 0; q < L.tiles.size(); ++q) tile_start[q] = L.tiles[q].o0;
+      tile_start[L.tiles.size()] = n_obs;
+    }
+    if (n_tiles) *n_tiles = (int64_t)L.tiles.size();
+  } catch (const std::bad_alloc&) {
+    g_create_error = "dba_build_layout: out of host memory";
+    return DBA_ENOMEM;
+  }
+  return DBA_OK;
+}
+
 dba_status dba_inject_copy_stall(dba_ctx* ctx, int on) {
   if (!ctx) return DBA_EINVAL;
   if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_inject_copy_stall before dba_set_observations");

@@ -23,7 +23,7 @@ DBA_SOLVER_GN, DBA_SOLVER_LBFGS = 0, 1
 EXPORTED = [
     "dba_config_default", "dba_create", "dba_set_observations", "dba_set_ground_truth", "dba_iterate",
     "dba_iterate_until", "dba_evaluate", "dba_get_params", "dba_get_state", "dba_set_state",
-    "dba_profile", "dba_inject_copy_stall", "dba_layout", "dba_evaluate_noalloc", "dba_set_scenes", "dba_scene_stats",
+    "dba_profile", "dba_inject_copy_stall", "dba_build_layout", "dba_layout", "dba_evaluate_noalloc", "dba_set_scenes", "dba_scene_stats",
     "dba_last_error", "dba_destroy", "dba_mlp_create", "dba_mlp_destroy", "dba_mlp_last_error",
     "dba_mlp_get_params", "dba_mlp_set_params", "dba_mlp_harvest", "dba_mlp_fit_normalizer",
     "dba_mlp_loss_grad", "dba_mlp_train", "dba_mlp_predict", "dba_set_warm_start",
@@ -96,6 +96,8 @@ def load():
     L.dba_get_params.argtypes = [vp, dp, dp]
     L.dba_get_state.argtypes = [vp, dp, dp]
     L.dba_set_state.argtypes = [vp, dp, dp, dp, dp]
+    L.dba_build_layout.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ip, ip, ctypes.c_int,
+                                   P(ctypes.c_int64), ip, ip, ip, P(ctypes.c_int64), P(ctypes.c_int64)]
     L.dba_inject_copy_stall.argtypes = [vp, ctypes.c_int]
     L.dba_profile.argtypes = [vp, ctypes.c_int, P(ctypes.c_char_p), dp, P(ctypes.c_int)]
     L.dba_layout.argtypes = [vp, P(ctypes.c_int64), P(ctypes.c_int)]
@@ -189,6 +191,28 @@ def dba_set_observations(ctx, n_cams, n_pts, pt_idx, cam_idx, z, cams0, pts0):
     pts0 = _d(pts0, (n_pts, 3))
     _check(load().dba_set_observations(ctx, n_cams, n_pts, l, _ptr(pt_idx), _ptr(cam_idx), _ptr(z),
                                        _ptr(cams0), _ptr(pts0)), ctx)
+
+
+def dba_build_layout(n_cams, n_pts, pt_idx, cam_idx, tile_obs):
+    """The internal order and tile table of dba_set_observations, built on the host:
+    dict of perm, point, point_perm, cam_rank (numpy arrays) and tile_start."""
+    pt_idx = np.ascontiguousarray(pt_idx, dtype=np.int32)
+    cam_idx = np.ascontiguousarray(cam_idx, dtype=np.int32)
+    l = pt_idx.shape[0]
+    if cam_idx.shape[0] != l:
+        raise ValueError("pt_idx and cam_idx differ in length")
+    perm = np.zeros(l, np.int64)
+    point = np.zeros(l, np.int32)
+    point_perm = np.zeros(n_pts, np.int32)
+    cam_rank = np.zeros(l, np.int32)
+    tile_start = np.zeros(l + 1, np.int64)
+    nt = ctypes.c_int64()
+    i64 = ctypes.POINTER(ctypes.c_int64)
+    _check(load().dba_build_layout(n_cams, n_pts, l, _ptr(pt_idx), _ptr(cam_idx), tile_obs,
+                                   perm.ctypes.data_as(i64), _ptr(point), _ptr(point_perm), _ptr(cam_rank),
+                                   tile_start.ctypes.data_as(i64), ctypes.byref(nt)))
+    return {"perm": perm, "point": point, "point_perm": point_perm, "cam_rank": cam_rank,
+            "tile_start": tile_start[: nt.value + 1]}
 
 
 def dba_set_ground_truth(ctx, cams_gt, pts_gt, inlier=None):
