@@ -343,6 +343,24 @@ dba_status dba_block_get_params(dba_block_ctx* ctx, double* cams_out, double* pt
 /* Number of blocks, point copies and camera copies (any pointer may be NULL). */
 dba_status dba_block_layout(const dba_block_ctx* ctx, int64_t* n_blocks, int64_t* n_point_copies,
                             int64_t* n_camera_copies);
+/* The block layout dba_block_set_observations builds, computed on the host only (no
+ * device), for inspection and tests.  Same index checks as dba_block_set_observations
+ * and 1 <= block_points <= DBA_BLOCK_MAX_POINTS, 1 <= block_cams <= DBA_BLOCK_MAX_CAMERAS
+ * (EINVAL, message in dba_block_last_error(NULL)).  Outputs, caller-allocated, any may
+ * be NULL:
+ *   obs_order[n_obs]   caller index of each observation in block order (blocks by
+ *                      (point group, camera group); inside a block by point rank, then
+ *                      camera);
+ *   blocks[6 n_obs]    per block in launch (size-class) order: first observation, count;
+ *                      first point copy, count; first camera copy, count;
+ *   pc_point[n_obs]    point of each point copy (copies in block order);
+ *   cc_camera[n_obs]   camera of each camera copy;
+ *   counts[3]          blocks, point copies, camera copies;
+ *   size_classes[DBA_BLOCK_SIZE_CLASSES]  blocks per size class. */
+dba_status dba_block_build_layout(int32_t n_cams, int32_t n_pts, int64_t n_obs, const int32_t* pt_idx,
+                                  const int32_t* cam_idx, int block_points, int block_cams, int64_t* obs_order,
+                                  int32_t* blocks, int32_t* pc_point, int32_t* cc_camera, int64_t* counts,
+                                  int64_t* size_classes);
 /* Blocks in each size class of the solve kernel, in launch order: one camera and at
  * most 8 points (8-lane groups), at most 2 cameras and 16 points (16 lanes), at most
  * 32 points (32 lanes), the rest (32 lanes, two point copies each).  Each nonempty

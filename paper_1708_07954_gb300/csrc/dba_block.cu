@@ -937,6 +937,145 @@ dba_status read_stats(dba_block_ctx* ctx, bool have_residuals, dba_stats* st) {
 
 }  // namespace
 
+// The block layout of Sec. 3.1.4 (Eq. 14) under the reading in the header comment, built
+// on the host: observations in block order, blocks (in size-class order), point and
+// camera copies, their consensus lists and the algorithmic flop counts.  Returns an empty
+// string, or the message for a repeated (point, camera) pair.
+struct BlockHostLayout {
+  std::vector<long long> blk_obs;  // block order -> caller observation
+  std::vector<dba::BlockInfo> blocks;
+  int cls[dba::kBlkClasses + 1] = {};
+  std::vector<int> pc_obs, pc_pt, cc_cam, obs_pt, obs_cam;
+  std::vector<unsigned char> obs_lc;
+  std::vector<int> pt_off, cam_off, pt_cp, cam_cp;
+  double flops_step = 0.0, flops_start = 0.0;
+};
+
+std::string build_block_layout(int n_cams, int n_pts, long long l, const int32_t* pt_idx, const int32_t* cam_idx,
+                               int pi, int kappa, BlockHostLayout& H) {
+  const int n = n_pts, m = n_cams;
+  // point ranks by (smallest observing camera, point index)
+  std::vector<int> first(n, INT_MAX);
+  for (long long o = 0; o < l; ++o) first[pt_idx[o]] = std::min(first[pt_idx[o]], (int)cam_idx[o]);
+  std::vector<int> order(n);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return first[a] < first[b]; });
+  std::vector<int> rank(n);
+  for (int r = 0; r < n; ++r) rank[order[r]] = r;
+  const long long n_cg = (m + kappa - 1) / kappa;
+  auto key = [&](long long o) { return (long long)(rank[pt_idx[o]] / pi) * n_cg + cam_idx[o] / kappa; };
+  std::vector<long long>& idx = H.blk_obs;
+  idx.resize(l);
+  std::iota(idx.begin(), idx.end(), 0LL);
+  std::sort(idx.begin(), idx.end(), [&](long long a, long long b) {
+    const long long ka = key(a), kb = key(b);
+    if (ka != kb) return ka < kb;
+    if (rank[pt_idx[a]] != rank[pt_idx[b]]) return rank[pt_idx[a]] < rank[pt_idx[b]];
+    return cam_idx[a] < cam_idx[b];
+  });
+  for (long long t = 1; t < l; ++t)
+    if (pt_idx[idx[t]] == pt_idx[idx[t - 1]] && cam_idx[idx[t]] == cam_idx[idx[t - 1]])
+      return "point " + std::to_string(pt_idx[idx[t]]) + " is observed twice by camera " +
+             std::to_string(cam_idx[idx[t]]);
+  // blocks, point copies (consecutive observations of one point), camera copies
+  std::vector<dba::BlockInfo>& blocks = H.blocks;
+  blocks.clear();
+  std::vector<int>&pc_obs = H.pc_obs, &pc_pt = H.pc_pt, &cc_cam = H.cc_cam, &obs_pt = H.obs_pt, &obs_cam = H.obs_cam;
+  obs_pt.assign(l, 0);
+  obs_cam.assign(l, 0);
+  std::vector<unsigned char>& obs_lc = H.obs_lc;
+  obs_lc.assign(l, 0);
+  long long o = 0;
+  while (o < l) {
+    const long long k = key(idx[o]);
+    long long e = o;
+    while (e < l && key(idx[e]) == k) ++e;
+    dba::BlockInfo bi{};
+    bi.o0 = (int)o;
+    bi.no = (int)(e - o);
+    bi.p0 = (int)pc_pt.size();
+    bi.c0 = (int)cc_cam.size();
+    std::vector<int> cams;
+    for (long long t = o; t < e; ++t) cams.push_back(cam_idx[idx[t]]);
+    std::sort(cams.begin(), cams.end());
+    cams.erase(std::unique(cams.begin(), cams.end()), cams.end());
+    for (int c : cams) cc_cam.push_back(c);
+    bi.nc = (int)cams.size();
+    for (long long t = o; t < e; ++t) {
+      const int i = pt_idx[idx[t]];
+      if (t == o || pt_idx[idx[t - 1]] != i) {
+        pc_pt.push_back(i);
+        pc_obs.push_back((int)t);
+      }
+      obs_pt[t] = i;
+      obs_cam[t] = cam_idx[idx[t]];
+      obs_lc[t] = (unsigned char)(std::lower_bound(cams.begin(), cams.end(), (int)cam_idx[idx[t]]) - cams.begin());
+    }
+    bi.np = (int)pc_pt.size() - bi.p0;
+    blocks.push_back(bi);
+    o = e;
+  }
+  pc_obs.push_back((int)l);
+  const long long n_pc = (long long)pc_pt.size(), n_cc = (long long)cc_cam.size();
+  // algorithmic flops of the block solves (add/mul 1, fma 2, rcp/sqrt/sin/cos 1), counted
+  // from the kernel's arithmetic, each step a full step with its trial objective:
+  //   per observation: pose 44, Jacobian and residual 64, point block and gradient terms 43,
+  //     noise bound 7, its 2w A W g term 14, gradient and right-hand side entries 48,
+  //     back-substitution 30, trial pose and misfit 64                        -> 314
+  //   per camera pair of a point's observations (Schur weight 60 + 8 per entry of the
+  //     reduced system): 228 when both are one observation (21 entries), 348 otherwise
+  //   per point copy: penalty gradient 6, 3x3 inverse 35, W g 15, step 15, model terms 12,
+  //     trial penalty 9                                                      -> 92
+  //   per block: Cholesky n^3/3 + n^2/2, triangular solves 2 n^2, damping and camera
+  //     model/penalty terms 10 n (n = 6 cameras)
+  //   start of a solve: pose and misfit 64 per observation, penalty 9 per point copy and
+  //     per camera copy 24
+  {
+    double pairs_off = 0.0, per_block = 0.0;
+    for (long long k = 0; k < n_pc; ++k) {
+      const double c = (double)(pc_obs[k + 1] - pc_obs[k]);
+      pairs_off += c * (c - 1.0) / 2.0;
+    }
+    for (const dba::BlockInfo& bi : blocks) {
+      const double nu = 6.0 * bi.nc;
+      per_block += nu * nu * nu / 3.0 + nu * nu / 2.0 + 2.0 * nu * nu + 10.0 * nu;
+    }
+    H.flops_step = 314.0 * (double)l + 228.0 * (double)l + 348.0 * pairs_off + 92.0 * (double)n_pc + per_block;
+    H.flops_start = 64.0 * (double)l + 9.0 * (double)n_pc + 24.0 * (double)n_cc;
+  }
+  // size classes of the solve kernel (lane groups of 8, 16, 32, 32 with two copies per
+  // lane), each contiguous
+  {
+    auto cls_of = [](const dba::BlockInfo& b) {
+      return b.nc == 1 && b.np <= 8 ? 0 : b.nc <= 2 && b.np <= 16 ? 1 : b.np <= 32 ? 2 : 3;
+    };
+    std::stable_sort(blocks.begin(), blocks.end(),
+                     [&](const dba::BlockInfo& a, const dba::BlockInfo& b) { return cls_of(a) < cls_of(b); });
+    H.cls[0] = 0;
+    for (int k = 0; k < dba::kBlkClasses; ++k)
+      H.cls[k + 1] = (int)(std::partition_point(blocks.begin(), blocks.end(),
+                                                   [&](const dba::BlockInfo& b) { return cls_of(b) <= k; }) -
+                              blocks.begin());
+  }
+  // copy lists per point and per camera (consensus)
+  std::vector<int>&pt_off = H.pt_off, &cam_off = H.cam_off, &pt_cp = H.pt_cp, &cam_cp = H.cam_cp;
+  pt_off.assign(n + 1, 0);
+  cam_off.assign(m + 1, 0);
+  pt_cp.assign(n_pc, 0);
+  cam_cp.assign(n_cc, 0);
+  for (long long k = 0; k < n_pc; ++k) ++pt_off[pc_pt[k] + 1];
+  for (long long k = 0; k < n_cc; ++k) ++cam_off[cc_cam[k] + 1];
+  for (int i = 0; i < n; ++i) pt_off[i + 1] += pt_off[i];
+  for (int j = 0; j < m; ++j) cam_off[j + 1] += cam_off[j];
+  {
+    std::vector<int> fill(pt_off.begin(), pt_off.end() - 1);
+    for (long long k = 0; k < n_pc; ++k) pt_cp[fill[pc_pt[k]]++] = (int)k;
+    std::vector<int> fc(cam_off.begin(), cam_off.end() - 1);
+    for (long long k = 0; k < n_cc; ++k) cam_cp[fc[cc_cam[k]]++] = (int)k;
+  }
+  return std::string();
+}
+
 extern "C" {
 
 dba_status dba_block_create(const dba_config* cfg, int block_points, int block_cams, dba_block_ctx** out) {
@@ -1019,119 +1158,24 @@ dba_status dba_block_set_observations(dba_block_ctx* ctx, int32_t n_cams, int32_
     if (!std::isfinite(pts0[k])) return ctx->fail(DBA_EINVAL, "dba_block_set_observations: non-finite point");
   ctx->free_all();
   const long long l = n_obs;
-  const int n = n_pts, m = n_cams, pi = ctx->pi, kappa = ctx->kappa;
-  // point ranks by (smallest observing camera, point index)
-  std::vector<int> first(n, INT_MAX);
-  for (long long o = 0; o < l; ++o) first[pt_idx[o]] = std::min(first[pt_idx[o]], (int)cam_idx[o]);
-  std::vector<int> order(n);
-  std::iota(order.begin(), order.end(), 0);
-  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return first[a] < first[b]; });
-  std::vector<int> rank(n);
-  for (int r = 0; r < n; ++r) rank[order[r]] = r;
-  const long long n_cg = (m + kappa - 1) / kappa;
-  auto key = [&](long long o) { return (long long)(rank[pt_idx[o]] / pi) * n_cg + cam_idx[o] / kappa; };
-  std::vector<long long>& idx = ctx->blk_obs;
-  idx.resize(l);
-  std::iota(idx.begin(), idx.end(), 0LL);
-  std::sort(idx.begin(), idx.end(), [&](long long a, long long b) {
-    const long long ka = key(a), kb = key(b);
-    if (ka != kb) return ka < kb;
-    if (rank[pt_idx[a]] != rank[pt_idx[b]]) return rank[pt_idx[a]] < rank[pt_idx[b]];
-    return cam_idx[a] < cam_idx[b];
-  });
-  for (long long t = 1; t < l; ++t)
-    if (pt_idx[idx[t]] == pt_idx[idx[t - 1]] && cam_idx[idx[t]] == cam_idx[idx[t - 1]])
-      return ctx->fail(DBA_EINVAL, "dba_block_set_observations: point " + std::to_string(pt_idx[idx[t]]) +
-                                       " is observed twice by camera " + std::to_string(cam_idx[idx[t]]));
-  // blocks, point copies (consecutive observations of one point), camera copies
-  std::vector<dba::BlockInfo>& blocks = ctx->h_blocks;
-  blocks.clear();
-  std::vector<int> pc_obs, pc_pt, cc_cam, obs_pt(l), obs_cam(l);
-  std::vector<unsigned char> obs_lc(l);
-  long long o = 0;
-  while (o < l) {
-    const long long k = key(idx[o]);
-    long long e = o;
-    while (e < l && key(idx[e]) == k) ++e;
-    dba::BlockInfo bi{};
-    bi.o0 = (int)o;
-    bi.no = (int)(e - o);
-    bi.p0 = (int)pc_pt.size();
-    bi.c0 = (int)cc_cam.size();
-    std::vector<int> cams;
-    for (long long t = o; t < e; ++t) cams.push_back(cam_idx[idx[t]]);
-    std::sort(cams.begin(), cams.end());
-    cams.erase(std::unique(cams.begin(), cams.end()), cams.end());
-    for (int c : cams) cc_cam.push_back(c);
-    bi.nc = (int)cams.size();
-    for (long long t = o; t < e; ++t) {
-      const int i = pt_idx[idx[t]];
-      if (t == o || pt_idx[idx[t - 1]] != i) {
-        pc_pt.push_back(i);
-        pc_obs.push_back((int)t);
-      }
-      obs_pt[t] = i;
-      obs_cam[t] = cam_idx[idx[t]];
-      obs_lc[t] = (unsigned char)(std::lower_bound(cams.begin(), cams.end(), (int)cam_idx[idx[t]]) - cams.begin());
-    }
-    bi.np = (int)pc_pt.size() - bi.p0;
-    blocks.push_back(bi);
-    o = e;
+  const int n = n_pts, m = n_cams;
+  BlockHostLayout H;
+  {
+    const std::string msg = build_block_layout(n_cams, n_pts, l, pt_idx, cam_idx, ctx->pi, ctx->kappa, H);
+    if (!msg.empty()) return ctx->fail(DBA_EINVAL, "dba_block_set_observations: " + msg);
   }
-  pc_obs.push_back((int)l);
+  ctx->blk_obs = H.blk_obs;
+  ctx->h_blocks = H.blocks;
+  for (int k = 0; k <= dba::kBlkClasses; ++k) ctx->cls[k] = H.cls[k];
+  ctx->flops_step = H.flops_step;
+  ctx->flops_start = H.flops_start;
+  const std::vector<dba::BlockInfo>& blocks = H.blocks;
+  const std::vector<int>&pc_obs = H.pc_obs, &pc_pt = H.pc_pt, &cc_cam = H.cc_cam, &obs_pt = H.obs_pt,
+                    &obs_cam = H.obs_cam, &pt_off = H.pt_off, &cam_off = H.cam_off, &pt_cp = H.pt_cp,
+                    &cam_cp = H.cam_cp;
+  const std::vector<unsigned char>& obs_lc = H.obs_lc;
+  const std::vector<long long>& idx = H.blk_obs;
   const long long n_pc = (long long)pc_pt.size(), n_cc = (long long)cc_cam.size();
-  // algorithmic flops of the block solves (add/mul 1, fma 2, rcp/sqrt/sin/cos 1), counted
-  // from the kernel's arithmetic, each step a full step with its trial objective:
-  //   per observation: pose 44, Jacobian and residual 64, point block and gradient terms 43,
-  //     noise bound 7, its 2w A W g term 14, gradient and right-hand side entries 48,
-  //     back-substitution 30, trial pose and misfit 64                        -> 314
-  //   per camera pair of a point's observations (Schur weight 60 + 8 per entry of the
-  //     reduced system): 228 when both are one observation (21 entries), 348 otherwise
-  //   per point copy: penalty gradient 6, 3x3 inverse 35, W g 15, step 15, model terms 12,
-  //     trial penalty 9                                                      -> 92
-  //   per block: Cholesky n^3/3 + n^2/2, triangular solves 2 n^2, damping and camera
-  //     model/penalty terms 10 n (n = 6 cameras)
-  //   start of a solve: pose and misfit 64 per observation, penalty 9 per point copy and
-  //     per camera copy 24
-  {
-    double pairs_off = 0.0, per_block = 0.0;
-    for (long long k = 0; k < n_pc; ++k) {
-      const double c = (double)(pc_obs[k + 1] - pc_obs[k]);
-      pairs_off += c * (c - 1.0) / 2.0;
-    }
-    for (const dba::BlockInfo& bi : blocks) {
-      const double nu = 6.0 * bi.nc;
-      per_block += nu * nu * nu / 3.0 + nu * nu / 2.0 + 2.0 * nu * nu + 10.0 * nu;
-    }
-    ctx->flops_step = 314.0 * (double)l + 228.0 * (double)l + 348.0 * pairs_off + 92.0 * (double)n_pc + per_block;
-    ctx->flops_start = 64.0 * (double)l + 9.0 * (double)n_pc + 24.0 * (double)n_cc;
-  }
-  // size classes of the solve kernel (lane groups of 8, 16, 32, 32 with two copies per
-  // lane), each contiguous
-  {
-    auto cls_of = [](const dba::BlockInfo& b) {
-      return b.nc == 1 && b.np <= 8 ? 0 : b.nc <= 2 && b.np <= 16 ? 1 : b.np <= 32 ? 2 : 3;
-    };
-    std::stable_sort(blocks.begin(), blocks.end(),
-                     [&](const dba::BlockInfo& a, const dba::BlockInfo& b) { return cls_of(a) < cls_of(b); });
-    ctx->cls[0] = 0;
-    for (int k = 0; k < dba::kBlkClasses; ++k)
-      ctx->cls[k + 1] = (int)(std::partition_point(blocks.begin(), blocks.end(),
-                                                   [&](const dba::BlockInfo& b) { return cls_of(b) <= k; }) -
-                              blocks.begin());
-  }
-  // copy lists per point and per camera (consensus)
-  std::vector<int> pt_off(n + 1, 0), cam_off(m + 1, 0), pt_cp(n_pc), cam_cp(n_cc);
-  for (long long k = 0; k < n_pc; ++k) ++pt_off[pc_pt[k] + 1];
-  for (long long k = 0; k < n_cc; ++k) ++cam_off[cc_cam[k] + 1];
-  for (int i = 0; i < n; ++i) pt_off[i + 1] += pt_off[i];
-  for (int j = 0; j < m; ++j) cam_off[j + 1] += cam_off[j];
-  {
-    std::vector<int> fill(pt_off.begin(), pt_off.end() - 1);
-    for (long long k = 0; k < n_pc; ++k) pt_cp[fill[pc_pt[k]]++] = (int)k;
-    std::vector<int> fc(cam_off.begin(), cam_off.end() - 1);
-    for (long long k = 0; k < n_cc; ++k) cam_cp[fc[cc_cam[k]]++] = (int)k;
-  }
   // device problem
   dba::BlockProblem& B = ctx->B;
   B.n_cams = m;
@@ -1339,6 +1383,55 @@ dba_status dba_block_layout(const dba_block_ctx* ctx, int64_t* n_blocks, int64_t
   if (n_blocks) *n_blocks = ctx->B.n_blocks;
   if (n_point_copies) *n_point_copies = ctx->B.n_pc;
   if (n_camera_copies) *n_camera_copies = ctx->B.n_cc;
+  return DBA_OK;
+}
+
+dba_status dba_block_build_layout(int32_t n_cams, int32_t n_pts, int64_t n_obs, const int32_t* pt_idx,
+                                  const int32_t* cam_idx, int block_points, int block_cams, int64_t* obs_order,
+                                  int32_t* blocks, int32_t* pc_point, int32_t* cc_camera, int64_t* counts,
+                                  int64_t* size_classes) {
+  if (n_cams <= 0 || n_pts <= 0 || n_obs <= 0 || n_obs > INT_MAX || !pt_idx || !cam_idx ||
+      block_points < 1 || block_points > DBA_BLOCK_MAX_POINTS || block_cams < 1 ||
+      block_cams > DBA_BLOCK_MAX_CAMERAS) {
+    g_block_error = "dba_block_build_layout: sizes out of range or null index array";
+    return DBA_EINVAL;
+  }
+  for (int64_t o = 0; o < n_obs; ++o)
+    if (pt_idx[o] < 0 || pt_idx[o] >= n_pts || cam_idx[o] < 0 || cam_idx[o] >= n_cams) {
+      g_block_error = "dba_block_build_layout: observation " + std::to_string(o) +
+                      " indexes outside the cameras or points";
+      return DBA_EINVAL;
+    }
+  try {
+    BlockHostLayout H;
+    const std::string msg = build_block_layout(n_cams, n_pts, n_obs, pt_idx, cam_idx, block_points, block_cams, H);
+    if (!msg.empty()) {
+      g_block_error = "dba_block_build_layout: " + msg;
+      return DBA_EINVAL;
+    }
+    if (obs_order)
+      for (int64_t o = 0; o < n_obs; ++o) obs_order[o] = H.blk_obs[o];
+    if (blocks)
+      for (size_t b = 0; b < H.blocks.size(); ++b) {
+        const dba::BlockInfo& bi = H.blocks[b];
+        const int32_t v[6] = {bi.o0, bi.no, bi.p0, bi.np, bi.c0, bi.nc};
+        for (int k = 0; k < 6; ++k) blocks[6 * b + k] = v[k];
+      }
+    if (pc_point)
+      for (size_t k = 0; k < H.pc_pt.size(); ++k) pc_point[k] = H.pc_pt[k];
+    if (cc_camera)
+      for (size_t k = 0; k < H.cc_cam.size(); ++k) cc_camera[k] = H.cc_cam[k];
+    if (counts) {
+      counts[0] = (int64_t)H.blocks.size();
+      counts[1] = (int64_t)H.pc_pt.size();
+      counts[2] = (int64_t)H.cc_cam.size();
+    }
+    if (size_classes)
+      for (int k = 0; k < dba::kBlkClasses; ++k) size_classes[k] = H.cls[k + 1] - H.cls[k];
+  } catch (const std::bad_alloc&) {
+    g_block_error = "dba_block_build_layout: out of host memory";
+    return DBA_ENOMEM;
+  }
   return DBA_OK;
 }
 

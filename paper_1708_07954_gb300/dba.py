@@ -29,7 +29,7 @@ EXPORTED = [
     "dba_mlp_loss_grad", "dba_mlp_train", "dba_mlp_predict", "dba_set_warm_start",
     "dba_block_create", "dba_block_set_observations", "dba_block_set_reference_pixels", "dba_block_iterate",
     "dba_block_iterate_until", "dba_block_profile", "dba_block_get_params", "dba_block_layout",
-    "dba_block_size_classes", "dba_block_algorithmic_flops", "dba_block_last_error",
+    "dba_block_size_classes", "dba_block_build_layout", "dba_block_algorithmic_flops", "dba_block_last_error",
     "dba_block_destroy",
 ]
 DBA_BLOCK_MAX_POINTS, DBA_BLOCK_MAX_CAMERAS, DBA_BLOCK_SIZE_CLASSES = 64, 4, 4
@@ -134,6 +134,9 @@ def load():
     L.dba_block_get_params.argtypes = [vp, dp, dp]
     L.dba_block_layout.argtypes = [vp, P(ctypes.c_int64), P(ctypes.c_int64), P(ctypes.c_int64)]
     L.dba_block_size_classes.argtypes = [vp, P(ctypes.c_int64)]
+    L.dba_block_build_layout.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ip, ip, ctypes.c_int,
+                                         ctypes.c_int, P(ctypes.c_int64), ip, ip, ip, P(ctypes.c_int64),
+                                         P(ctypes.c_int64)]
     L.dba_block_algorithmic_flops.argtypes = [vp, dp]
     L.dba_block_last_error.argtypes = [vp]
     L.dba_block_last_error.restype = ctypes.c_char_p
@@ -374,6 +377,32 @@ def dba_mlp_harvest(ctx, stride, target_steps, feats_ptr, targs_ptr, cap):
 
 def dba_set_warm_start(ctx, mlp):
     _check(load().dba_set_warm_start(ctx, mlp.h if mlp is not None else None), ctx)
+
+
+def dba_block_build_layout(n_cams, n_pts, pt_idx, cam_idx, block_points, block_cams):
+    """The block layout of dba_block_set_observations, built on the host: dict of
+    obs_order, blocks (n_blocks x 6: first observation, count, first point copy, count,
+    first camera copy, count; launch order), pc_point, cc_camera, size_classes."""
+    pt_idx = np.ascontiguousarray(pt_idx, dtype=np.int32)
+    cam_idx = np.ascontiguousarray(cam_idx, dtype=np.int32)
+    l = pt_idx.shape[0]
+    if cam_idx.shape[0] != l:
+        raise ValueError("pt_idx and cam_idx differ in length")
+    order = np.zeros(l, np.int64)
+    blocks = np.zeros(6 * l, np.int32)
+    pc = np.zeros(l, np.int32)
+    cc = np.zeros(l, np.int32)
+    counts = np.zeros(3, np.int64)
+    cls = np.zeros(DBA_BLOCK_SIZE_CLASSES, np.int64)
+    i64 = ctypes.POINTER(ctypes.c_int64)
+    st = load().dba_block_build_layout(n_cams, n_pts, l, _ptr(pt_idx), _ptr(cam_idx), block_points, block_cams,
+                                       order.ctypes.data_as(i64), _ptr(blocks), _ptr(pc), _ptr(cc),
+                                       counts.ctypes.data_as(i64), cls.ctypes.data_as(i64))
+    if st != DBA_OK:
+        raise DbaError(st, load().dba_block_last_error(None).decode())
+    nb, npc, ncc = (int(x) for x in counts)
+    return {"obs_order": order, "blocks": blocks[: 6 * nb].reshape(nb, 6), "pc_point": pc[:npc],
+            "cc_camera": cc[:ncc], "size_classes": cls}
 
 
 class Solver:

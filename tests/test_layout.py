@@ -93,3 +93,35 @@ def test_layout_rejects_bad_input():
     assert e.value.status == dba.DBA_EINVAL and "observation 2" in str(e.value)
     with pytest.raises(dba.DbaError):
         dba.dba_build_layout(6, 3, pt, cam, 100)
+
+
+@pytest.mark.parametrize("pi,kappa", [(1, 1), (8, 2), (32, 4), (5, 3), (64, 2)])
+def test_block_layout_matches_the_oracle(pi, kappa):
+    """The library's block layout (Eq. 14 under the block reading) equals the oracle's,
+    which is built independently with numpy: observation order, block boundaries, point
+    and camera copies; blocks are launched grouped by size class."""
+    import oracle as O
+
+    sc = S.scene1(n_pts=1200, n_cams=24, seed=41)
+    ref = O.BlockLayout(sc, pi, kappa)
+    L = dba.dba_block_build_layout(sc.n_cams, sc.n_pts, sc.pt_idx, sc.cam_idx, pi, kappa)
+    assert np.array_equal(L["obs_order"], ref.blk_obs)
+    b = L["blocks"][np.argsort(L["blocks"][:, 0], kind="stable")]
+    assert len(b) == ref.n_blocks
+    assert np.array_equal(b[:, 0], ref.obs_off[:-1]) and np.array_equal(b[:, 1], np.diff(ref.obs_off))
+    assert np.array_equal(b[:, 2], ref.pc_off[:-1]) and np.array_equal(b[:, 3], np.diff(ref.pc_off))
+    assert np.array_equal(b[:, 4], ref.cc_off[:-1]) and np.array_equal(b[:, 5], np.diff(ref.cc_off))
+    assert np.array_equal(L["pc_point"], ref.pc_pt) and np.array_equal(L["cc_camera"], ref.cc_cam)
+    # launch order: size classes one after another (8, 16, 32 lanes; 32 lanes x 2 copies)
+    npb, ncb = L["blocks"][:, 3], L["blocks"][:, 5]
+    cls = np.where((ncb == 1) & (npb <= 8), 0, np.where((ncb <= 2) & (npb <= 16), 1, np.where(npb <= 32, 2, 3)))
+    assert np.all(np.diff(cls) >= 0)
+    assert np.array_equal(L["size_classes"], np.bincount(cls, minlength=4))
+
+
+def test_block_layout_rejects_a_repeated_pair():
+    pt = np.array([0, 1, 0], np.int32)
+    cam = np.array([2, 0, 2], np.int32)
+    with pytest.raises(dba.DbaError) as e:
+        dba.dba_block_build_layout(3, 2, pt, cam, 4, 2)
+    assert e.value.status == dba.DBA_EINVAL and "observed twice" in str(e.value)
