@@ -250,7 +250,6 @@ def run_reference(args, rank, world):
     cfg = O.config_for(sc)
     # bounded sample: a sub-problem of whole point tracks sized so that warmup + steps
     # iterations fit the time budget (calibrated on a small probe)
-    order = np.argsort(sc.pt_idx, kind="stable")
     budget = max(5.0, args.reference_seconds - (time.perf_counter() - t_gen) - 5.0)
     steps = args.steps + args.warmup
 
@@ -261,7 +260,6 @@ def run_reference(args, rank, world):
                      pts_gt=sc.pts_gt[:n_keep], cams0=sc.cams0, pts0=sc.pts0[:n_keep], name="sample")
         return s2
 
-    del order
     probe = sub(2000)
     st = O.State(probe)
     t0 = time.perf_counter()

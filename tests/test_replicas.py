@@ -57,3 +57,20 @@ def test_reference_arm_runs_on_rank_zero_only():
     import bench
 
     assert bench.run_reference(bench.parse([]), rank=1, world=2) == 0
+
+
+def test_reference_arm_prints_its_line(capsys):
+    """The reference arm (the oracle on the host cores, a bounded sample of the workload)
+    prints one JSON line with the contract's keys."""
+    import json
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    args = bench.parse(["--impl", "reference", "--steps", "1", "--warmup", "0", "--n-pts", "20000",
+                        "--reference-seconds", "6"])
+    assert bench.run_reference(args, rank=0, world=1) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
