@@ -125,3 +125,16 @@ def test_block_layout_rejects_a_repeated_pair():
     with pytest.raises(dba.DbaError) as e:
         dba.dba_block_build_layout(3, 2, pt, cam, 4, 2)
     assert e.value.status == dba.DBA_EINVAL and "observed twice" in str(e.value)
+
+
+def test_layout_size_limits():
+    """The camera word holds 24 bits of camera index; more cameras, or no observations,
+    are rejected before any work."""
+    pt = np.array([0, 1], np.int32)
+    cam = np.array([0, 1], np.int32)
+    with pytest.raises(dba.DbaError):
+        dba.dba_build_layout(1 << 24, 2, pt, cam, 256)
+    L = dba.dba_build_layout((1 << 24) - 1, 2, pt, cam, 256)
+    assert list(L["tile_start"]) == [0, 2]
+    with pytest.raises(dba.DbaError):
+        dba.dba_build_layout(2, 2, np.zeros(0, np.int32), np.zeros(0, np.int32), 256)
