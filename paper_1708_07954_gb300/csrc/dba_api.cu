@@ -827,6 +827,7 @@ extern "C" {
 dba_status dba_set_observations(dba_ctx* ctx, int32_t n_cams, int32_t n_pts, int64_t n_obs,
                                 const int32_t* pt_idx, const int32_t* cam_idx, const double* z,
                                 const double* cams0, const double* pts0) {
+  return dba::guarded(ctx ? &ctx->err : nullptr, [&]() -> dba_status {
   if (!ctx) return DBA_EINVAL;
   if (n_cams <= 0 || n_pts <= 0 || n_obs <= 0)
     return ctx->fail(DBA_EINVAL, "dba_set_observations: n_cams, n_pts and n_obs must be positive");
@@ -851,10 +852,12 @@ dba_status dba_set_observations(dba_ctx* ctx, int32_t n_cams, int32_t n_pts, int
     if (s != DBA_OK) return s;
   }
   return load_problem(ctx, NT, n_cams, n_pts, n_obs, pt_idx, cam_idx, z, cams0, pts0);
+  });
 }
 
 dba_status dba_set_ground_truth(dba_ctx* ctx, const double* cams_gt, const double* pts_gt,
                                 const uint8_t* inlier) {
+  return dba::guarded(ctx ? &ctx->err : nullptr, [&]() -> dba_status {
   if (!ctx) return DBA_EINVAL;
   if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_set_ground_truth before dba_set_observations");
   if (!cams_gt || !pts_gt) return ctx->fail(DBA_EINVAL, "dba_set_ground_truth: null array");
@@ -897,9 +900,11 @@ dba_status dba_set_ground_truth(dba_ctx* ctx, const double* cams_gt, const doubl
   ctx->has_gt = true;
   ctx->drop_graphs();  // kernel arguments changed
   return DBA_OK;
+  });
 }
 
 dba_status dba_iterate(dba_ctx* ctx, int n_iters, dba_stats* stats) {
+  return dba::guarded(ctx ? &ctx->err : nullptr, [&]() -> dba_status {
   if (!ctx) return DBA_EINVAL;
   if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_iterate before dba_set_observations");
   if (n_iters < 0) return ctx->fail(DBA_EINVAL, "dba_iterate: n_iters < 0");
@@ -913,9 +918,11 @@ dba_status dba_iterate(dba_ctx* ctx, int n_iters, dba_stats* stats) {
   DBA_CUDA(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1), "event");
   if (stats) return read_metrics(ctx, stats, ms * 1e-3);
   return DBA_OK;
+  });
 }
 
 dba_status dba_iterate_until(dba_ctx* ctx, int max_iters, double target_rmse_gt, dba_stats* stats) {
+  return dba::guarded(ctx ? &ctx->err : nullptr, [&]() -> dba_status {
   if (!ctx) return DBA_EINVAL;
   if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_iterate_until before dba_set_observations");
   if (!ctx->has_gt) return ctx->fail(DBA_ESTATE, "dba_iterate_until needs dba_set_ground_truth");
@@ -956,15 +963,19 @@ dba_status dba_iterate_until(dba_ctx* ctx, int max_iters, double target_rmse_gt,
   }
   if (stats) *stats = st;
   return DBA_OK;
+  });
 }
 
 dba_status dba_evaluate(dba_ctx* ctx, dba_stats* stats) {
+  return dba::guarded(ctx ? &ctx->err : nullptr, [&]() -> dba_status {
   if (!ctx || !stats) return DBA_EINVAL;
   if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_evaluate before dba_set_observations");
   return read_metrics(ctx, stats, 0.0);
+  });
 }
 
 dba_status dba_get_params(dba_ctx* ctx, double* cams, double* pts) {
+  return dba::guarded(ctx ? &ctx->err : nullptr, [&]() -> dba_status {
   if (!ctx) return DBA_EINVAL;
   if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_get_params before dba_set_observations");
   cudaStream_t st = ctx->stream;
@@ -980,9 +991,11 @@ dba_status dba_get_params(dba_ctx* ctx, double* cams, double* pts) {
     for (int k = 0; k < ctx->n_pts; ++k)
       for (int c = 0; c < 3; ++c) pts[3 * (size_t)ctx->pt_perm[k] + c] = X[3 * (size_t)k + c];
   return DBA_OK;
+  });
 }
 
 dba_status dba_get_state(dba_ctx* ctx, double* copies, double* duals) {
+  return dba::guarded(ctx ? &ctx->err : nullptr, [&]() -> dba_status {
   if (!ctx) return DBA_EINVAL;
   if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_get_state before dba_set_observations");
   cudaStream_t st = ctx->stream;
@@ -1024,10 +1037,12 @@ dba_status dba_get_state(dba_ctx* ctx, double* copies, double* duals) {
     }
   }
   return DBA_OK;
+  });
 }
 
 dba_status dba_set_state(dba_ctx* ctx, const double* copies, const double* duals, const double* cams,
                          const double* pts) {
+  return dba::guarded(ctx ? &ctx->err : nullptr, [&]() -> dba_status {
   if (!ctx) return DBA_EINVAL;
   if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_set_state before dba_set_observations");
   if (!copies || !duals || !cams || !pts) return ctx->fail(DBA_EINVAL, "dba_set_state: null array");
@@ -1035,6 +1050,7 @@ dba_status dba_set_state(dba_ctx* ctx, const double* copies, const double* duals
       !finite_all(cams, 6 * (long long)ctx->n_cams) || !finite_all(pts, 3 * (long long)ctx->n_pts))
     return ctx->fail(DBA_EINVAL, "dba_set_state: non-finite value");
   return upload_state(ctx, cams, pts, copies, duals);
+  });
 }
 
 dba_status dba_build_layout(int32_t n_cams, int32_t n_pts, int64_t n_obs, const int32_t* pt_idx,
@@ -1086,6 +1102,7 @@ dba_status dba_inject_copy_stall(dba_ctx* ctx, int on) {
 }
 
 dba_status dba_profile(dba_ctx* ctx, int n_iters, const char** names, double* ms, int* count) {
+  return dba::guarded(ctx ? &ctx->err : nullptr, [&]() -> dba_status {
   if (!ctx || !count) return DBA_EINVAL;
   if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_profile before dba_set_observations");
   if (n_iters <= 0 || *count < 2 || !names || !ms) return ctx->fail(DBA_EINVAL, "dba_profile: bad arguments");
@@ -1135,6 +1152,7 @@ dba_status dba_profile(dba_ctx* ctx, int n_iters, const char** names, double* ms
     *count = 3;
   }
   return DBA_OK;
+  });
 }
 
 dba_status dba_layout(dba_ctx* ctx, int64_t* out, int* count) {
@@ -1168,7 +1186,7 @@ dba_status dba_evaluate_noalloc(const dba_config* cfg, int32_t n_cams, int32_t n
     return DBA_EINVAL;
   }
   const Params prm{cfg->focal, cfg->cx, cfg->cy, cfg->loss, cfg->loss_param, 1.0, 1.0, 1.0,
-                   0, 1e-3, 0.0, cfg->eps_depth, 0.0};
+                   0, 1e-3, 0.0, cfg->eps_depth, 0.0, DBA_SOLVER_GN};
   const cudaError_t e = dba::launch_eval_noalloc(prm, n_obs, n_cams, n_pts, pt_idx, cam_idx, z, cams, pts, out,
                                                  static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) {
@@ -1180,6 +1198,7 @@ dba_status dba_evaluate_noalloc(const dba_config* cfg, int32_t n_cams, int32_t n
 
 dba_status dba_set_scenes(dba_ctx* ctx, int32_t n_scenes, const int64_t* obs_off, const int32_t* cam_off,
                           const int32_t* pt_off) {
+  return dba::guarded(ctx ? &ctx->err : nullptr, [&]() -> dba_status {
   if (!ctx) return DBA_EINVAL;
   if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_set_scenes before dba_set_observations");
   if (n_scenes <= 0 || !obs_off || !cam_off || !pt_off) return ctx->fail(DBA_EINVAL, "dba_set_scenes: bad arguments");
@@ -1212,9 +1231,11 @@ dba_status dba_set_scenes(dba_ctx* ctx, int32_t n_scenes, const int64_t* obs_off
   DBA_CUDA(cudaStreamSynchronize(ctx->stream), "set_scenes");
   ctx->n_scenes = n_scenes;
   return DBA_OK;
+  });
 }
 
 dba_status dba_scene_stats(dba_ctx* ctx, double* rmse_obs, double* rmse_gt, double* objective) {
+  return dba::guarded(ctx ? &ctx->err : nullptr, [&]() -> dba_status {
   if (!ctx) return DBA_EINVAL;
   if (!ctx->has_problem || ctx->n_scenes == 0)
     return ctx->fail(DBA_ESTATE, "dba_scene_stats needs dba_set_observations and dba_set_scenes");
@@ -1233,10 +1254,12 @@ dba_status dba_scene_stats(dba_ctx* ctx, double* rmse_obs, double* rmse_gt, doub
     if (rmse_gt) rmse_gt[sc] = (ctx->has_gt && v[4] > 0) ? std::sqrt(v[2] / v[4]) : 0.0;
   }
   return DBA_OK;
+  });
 }
 
 dba_status dba_mlp_harvest(dba_ctx* ctx, int64_t stride, int target_steps, float* feats, float* targets,
                            int64_t cap, int64_t* n_out) {
+  return dba::guarded(ctx ? &ctx->err : nullptr, [&]() -> dba_status {
   if (!ctx) return DBA_EINVAL;
   if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_mlp_harvest before dba_set_observations");
   if (stride <= 0 || cap < 0 || target_steps < 0 || target_steps > 1000 || !feats || !targets || !n_out)
@@ -1248,9 +1271,11 @@ dba_status dba_mlp_harvest(dba_ctx* ctx, int64_t stride, int target_steps, float
   DBA_CUDA(cudaStreamSynchronize(ctx->stream), "harvest");
   *n_out = n;
   return DBA_OK;
+  });
 }
 
 dba_status dba_set_warm_start(dba_ctx* ctx, const dba_mlp* mlp) {
+  return dba::guarded(ctx ? &ctx->err : nullptr, [&]() -> dba_status {
   if (!ctx) return DBA_EINVAL;
   if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_set_warm_start before dba_set_observations");
   ctx->drop_graphs();
@@ -1279,6 +1304,7 @@ dba_status dba_set_warm_start(dba_ctx* ctx, const dba_mlp* mlp) {
   DBA_CUDA(cudaStreamSynchronize(ctx->stream), "warm start");
   ctx->warm = true;
   return DBA_OK;
+  });
 }
 
 }  // extern "C"

@@ -1139,6 +1139,7 @@ dba_status dba_block_create(const dba_config* cfg, int block_points, int block_c
 dba_status dba_block_set_observations(dba_block_ctx* ctx, int32_t n_cams, int32_t n_pts, int64_t n_obs,
                                       const int32_t* pt_idx, const int32_t* cam_idx, const double* z,
                                       const double* cams0, const double* pts0) {
+  return dba::guarded(ctx ? &ctx->err : nullptr, [&]() -> dba_status {
   if (!ctx) return DBA_EINVAL;
   if (n_cams <= 0 || n_pts <= 0 || n_obs <= 0)
     return ctx->fail(DBA_EINVAL, "dba_block_set_observations: n_cams, n_pts and n_obs must be positive");
@@ -1258,9 +1259,11 @@ dba_status dba_block_set_observations(dba_block_ctx* ctx, int32_t n_cams, int32_
   ctx->iters = 0;
   ctx->has_problem = true;
   return DBA_OK;
+  });
 }
 
 dba_status dba_block_set_reference_pixels(dba_block_ctx* ctx, const double* z_ref, const uint8_t* inlier) {
+  return dba::guarded(ctx ? &ctx->err : nullptr, [&]() -> dba_status {
   if (!ctx) return DBA_EINVAL;
   if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_block_set_reference_pixels before set_observations");
   if (!z_ref) return ctx->fail(DBA_EINVAL, "dba_block_set_reference_pixels: null array");
@@ -1283,9 +1286,11 @@ dba_status dba_block_set_reference_pixels(dba_block_ctx* ctx, const double* z_re
   ctx->B.zt = d_zt;
   ctx->B.inlier = d_in;
   return DBA_OK;
+  });
 }
 
 dba_status dba_block_iterate(dba_block_ctx* ctx, int n_iters, dba_stats* stats) {
+  return dba::guarded(ctx ? &ctx->err : nullptr, [&]() -> dba_status {
   if (!ctx) return DBA_EINVAL;
   if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_block_iterate before dba_block_set_observations");
   if (n_iters < 0) return ctx->fail(DBA_EINVAL, "dba_block_iterate: n_iters < 0");
@@ -1305,9 +1310,11 @@ dba_status dba_block_iterate(dba_block_ctx* ctx, int n_iters, dba_stats* stats) 
     return s;
   }
   return DBA_OK;
+  });
 }
 
 dba_status dba_block_iterate_until(dba_block_ctx* ctx, int max_iters, double target_rmse_gt, dba_stats* stats) {
+  return dba::guarded(ctx ? &ctx->err : nullptr, [&]() -> dba_status {
   if (!ctx || !stats) return DBA_EINVAL;
   if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_block_iterate_until before set_observations");
   if (!ctx->B.zt) return ctx->fail(DBA_ESTATE, "dba_block_iterate_until needs reference pixels");
@@ -1328,9 +1335,11 @@ dba_status dba_block_iterate_until(dba_block_ctx* ctx, int max_iters, double tar
   }
   stats->seconds = secs;
   return DBA_OK;
+  });
 }
 
 dba_status dba_block_profile(dba_block_ctx* ctx, int n_iters, double* ms_out) {
+  return dba::guarded(ctx ? &ctx->err : nullptr, [&]() -> dba_status {
   if (!ctx || !ms_out) return DBA_EINVAL;
   if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_block_profile before set_observations");
   if (n_iters <= 0) return ctx->fail(DBA_EINVAL, "dba_block_profile: n_iters must be positive");
@@ -1353,9 +1362,11 @@ dba_status dba_block_profile(dba_block_ctx* ctx, int n_iters, double* ms_out) {
   if (e != cudaSuccess) return ctx->cuda_fail(e, "dba_block_profile");
   for (int k = 0; k < 3; ++k) ms_out[k] = acc[k] / n_iters;
   return DBA_OK;
+  });
 }
 
 dba_status dba_block_get_params(dba_block_ctx* ctx, double* cams_out, double* pts_out) {
+  return dba::guarded(ctx ? &ctx->err : nullptr, [&]() -> dba_status {
   if (!ctx) return DBA_EINVAL;
   if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_block_get_params before set_observations");
   if (!cams_out || !pts_out) return ctx->fail(DBA_EINVAL, "dba_block_get_params: null array");
@@ -1367,6 +1378,7 @@ dba_status dba_block_get_params(dba_block_ctx* ctx, double* cams_out, double* pt
            "get_params");
   BLK_CUDA(cudaStreamSynchronize(ctx->stream), "get_params");
   return DBA_OK;
+  });
 }
 
 dba_status dba_block_algorithmic_flops(const dba_block_ctx* ctx, double* per_iteration) {

@@ -793,6 +793,7 @@ dba_status dba_mlp_set_params(dba_mlp* m, const float* host) {
 }
 
 dba_status dba_mlp_fit_normalizer(dba_mlp* m, const float* feats, const float* targets, int64_t n) {
+  return dba::guarded(m ? &m->err : nullptr, [&]() -> dba_status {
   if (!m || !feats || !targets || n <= 1) return DBA_EINVAL;
   double* acc = nullptr;
   const int cols = dba::kMlpIn + dba::kMlpOut;
@@ -821,10 +822,12 @@ dba_status dba_mlp_fit_normalizer(dba_mlp* m, const float* feats, const float* t
   MLP_CUDA(cudaMemcpy(m->params + dba::kTrainable, stats.data(), sizeof(float) * stats.size(), cudaMemcpyHostToDevice),
            "normalizer");
   return DBA_OK;
+  });
 }
 
 dba_status dba_mlp_loss_grad(dba_mlp* m, const float* feats, const float* targets, int64_t n, double* loss,
                              float* grad) {
+  return dba::guarded(m ? &m->err : nullptr, [&]() -> dba_status {
   if (!m || !feats || !targets || n <= 0 || n > (1 << 26)) return DBA_EINVAL;
   MLP_CUDA(dba::mlp_reserve(m, (int)n), "loss_grad");
   const int b = dba::blocks_for(n * dba::kMlpIn, 256);
@@ -839,10 +842,12 @@ dba_status dba_mlp_loss_grad(dba_mlp* m, const float* feats, const float* target
   MLP_CUDA(cudaStreamSynchronize(m->stream), "loss_grad");
   if (loss) *loss = h;
   return DBA_OK;
+  });
 }
 
 dba_status dba_mlp_train(dba_mlp* m, const float* feats, const float* targets, int64_t n, int epochs, int batch,
                          float lr, uint64_t seed, double* last_loss) {
+  return dba::guarded(m ? &m->err : nullptr, [&]() -> dba_status {
   if (!m || !feats || !targets || n <= 0 || epochs < 0 || batch <= 0 || !(lr > 0)) return DBA_EINVAL;
   MLP_CUDA(dba::mlp_reserve(m, batch), "train");
   int* perm_dev = nullptr;
@@ -879,9 +884,11 @@ dba_status dba_mlp_train(dba_mlp* m, const float* feats, const float* targets, i
   if (e != cudaSuccess) return mlp_fail(m, e, "train");
   if (last_loss) *last_loss = epoch_loss;
   return DBA_OK;
+  });
 }
 
 dba_status dba_mlp_predict(dba_mlp* m, const float* feats, int64_t n, float* out) {
+  return dba::guarded(m ? &m->err : nullptr, [&]() -> dba_status {
   if (!m || !feats || !out || n <= 0) return DBA_EINVAL;
   std::vector<float> h(dba::kNParams);
   MLP_CUDA(cudaMemcpy(h.data(), m->params, sizeof(float) * h.size(), cudaMemcpyDeviceToHost), "predict");
@@ -907,6 +914,7 @@ dba_status dba_mlp_predict(dba_mlp* m, const float* feats, int64_t n, float* out
     return DBA_ETIMEOUT;
   }
   return DBA_OK;
+  });
 }
 
 }  // extern "C"
