@@ -828,228 +828,228 @@ dba_status dba_set_observations(dba_ctx* ctx, int32_t n_cams, int32_t n_pts, int
                                 const int32_t* pt_idx, const int32_t* cam_idx, const double* z,
                                 const double* cams0, const double* pts0) {
   return dba::guarded(ctx ? &ctx->err : nullptr, [&]() -> dba_status {
-  if (!ctx) return DBA_EINVAL;
-  if (n_cams <= 0 || n_pts <= 0 || n_obs <= 0)
-    return ctx->fail(DBA_EINVAL, "dba_set_observations: n_cams, n_pts and n_obs must be positive");
-  if (n_obs > (int64_t)0x7fffffff)
-    return ctx->fail(DBA_EINVAL, "dba_set_observations: at most 2^31-1 observations");
-  if (n_cams > dba::kCamMask)
-    return ctx->fail(DBA_EINVAL, "dba_set_observations: at most 16,777,215 cameras");
-  if (!pt_idx || !cam_idx || !z || !cams0 || !pts0)
-    return ctx->fail(DBA_EINVAL, "dba_set_observations: null array");
-  const long long bad = first_bad_index(pt_idx, cam_idx, n_obs, n_pts, n_cams);
-  if (bad >= 0)
-    return ctx->fail(DBA_EINVAL, "dba_set_observations: observation " + std::to_string(bad) +
-                                     " has an index out of range");
-  if (!finite_all(z, 2 * n_obs) || !finite_all(cams0, 6 * (long long)n_cams) ||
-      !finite_all(pts0, 3 * (long long)n_pts))
-    return ctx->fail(DBA_EINVAL, "dba_set_observations: non-finite input value");
-  cudaStreamSynchronize(ctx->stream);
-  ctx->free_problem();
-  int NT = ctx->cfg.tile_obs > 0 ? ctx->cfg.tile_obs : (ctx->fp32 ? 256 : 128);
-  if (ctx->cfg.tile_obs < 0) {
-    dba_status s = autotune_tile(ctx, n_cams, n_pts, n_obs, pt_idx, cam_idx, z, cams0, pts0, &NT);
-    if (s != DBA_OK) return s;
-  }
-  return load_problem(ctx, NT, n_cams, n_pts, n_obs, pt_idx, cam_idx, z, cams0, pts0);
+    if (!ctx) return DBA_EINVAL;
+    if (n_cams <= 0 || n_pts <= 0 || n_obs <= 0)
+      return ctx->fail(DBA_EINVAL, "dba_set_observations: n_cams, n_pts and n_obs must be positive");
+    if (n_obs > (int64_t)0x7fffffff)
+      return ctx->fail(DBA_EINVAL, "dba_set_observations: at most 2^31-1 observations");
+    if (n_cams > dba::kCamMask)
+      return ctx->fail(DBA_EINVAL, "dba_set_observations: at most 16,777,215 cameras");
+    if (!pt_idx || !cam_idx || !z || !cams0 || !pts0)
+      return ctx->fail(DBA_EINVAL, "dba_set_observations: null array");
+    const long long bad = first_bad_index(pt_idx, cam_idx, n_obs, n_pts, n_cams);
+    if (bad >= 0)
+      return ctx->fail(DBA_EINVAL, "dba_set_observations: observation " + std::to_string(bad) +
+                                       " has an index out of range");
+    if (!finite_all(z, 2 * n_obs) || !finite_all(cams0, 6 * (long long)n_cams) ||
+        !finite_all(pts0, 3 * (long long)n_pts))
+      return ctx->fail(DBA_EINVAL, "dba_set_observations: non-finite input value");
+    cudaStreamSynchronize(ctx->stream);
+    ctx->free_problem();
+    int NT = ctx->cfg.tile_obs > 0 ? ctx->cfg.tile_obs : (ctx->fp32 ? 256 : 128);
+    if (ctx->cfg.tile_obs < 0) {
+      dba_status s = autotune_tile(ctx, n_cams, n_pts, n_obs, pt_idx, cam_idx, z, cams0, pts0, &NT);
+      if (s != DBA_OK) return s;
+    }
+    return load_problem(ctx, NT, n_cams, n_pts, n_obs, pt_idx, cam_idx, z, cams0, pts0);
   });
 }
 
 dba_status dba_set_ground_truth(dba_ctx* ctx, const double* cams_gt, const double* pts_gt,
                                 const uint8_t* inlier) {
   return dba::guarded(ctx ? &ctx->err : nullptr, [&]() -> dba_status {
-  if (!ctx) return DBA_EINVAL;
-  if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_set_ground_truth before dba_set_observations");
-  if (!cams_gt || !pts_gt) return ctx->fail(DBA_EINVAL, "dba_set_ground_truth: null array");
-  if (!finite_all(cams_gt, 6 * (long long)ctx->n_cams) || !finite_all(pts_gt, 3 * (long long)ctx->n_pts))
-    return ctx->fail(DBA_EINVAL, "dba_set_ground_truth: non-finite value");
-  double *dc = nullptr, *dp = nullptr;
-  cudaStream_t st = ctx->stream;
-  DBA_CUDA(cudaMallocAsync(&dc, 6 * (size_t)ctx->n_cams * sizeof(double), st), "alloc");
-  DBA_CUDA(cudaMallocAsync(&dp, 3 * (size_t)ctx->n_pts * sizeof(double), st), "alloc");
-  DBA_CUDA(cudaMemcpyAsync(dc, cams_gt, 6 * (size_t)ctx->n_cams * sizeof(double), cudaMemcpyHostToDevice, st), "upload");
-  std::vector<double> pts_int(3 * (size_t)ctx->n_pts);
-  for (int k = 0; k < ctx->n_pts; ++k)
-    for (int c = 0; c < 3; ++c) pts_int[3 * (size_t)k + c] = pts_gt[3 * (size_t)ctx->pt_perm[k] + c];
-  DBA_CUDA(cudaMemcpyAsync(dp, pts_int.data(), pts_int.size() * sizeof(double), cudaMemcpyHostToDevice, st),
-           "upload");
-  void* zt = const_cast<void*>(ctx->P.zt);
-  if (!zt) {
-    char* p = nullptr;
-    DBA_CUDA(ctx->alloc(&p, (size_t)ctx->n_obs * (ctx->fp32 ? sizeof(float2) : sizeof(double2))), "alloc");
-    zt = p;
-  }
-  DBA_CUDA(dba::launch_project_truth(ctx->P, ctx->prm, ctx->fp32, dc, dp, zt, st), "project truth");
-  if (inlier) {
-    std::vector<unsigned char> h(ctx->n_obs);
-    for (long long o = 0; o < ctx->n_obs; ++o) h[o] = inlier[ctx->perm[o]] ? 1 : 0;
-    if (!ctx->P.inlier) {
-      DBA_CUDA(ctx->upload(&ctx->P.inlier, h), "upload inlier mask");
-    } else {
-      DBA_CUDA(cudaMemcpyAsync(const_cast<unsigned char*>(ctx->P.inlier), h.data(), h.size(),
-                               cudaMemcpyHostToDevice, st), "upload inlier mask");
+    if (!ctx) return DBA_EINVAL;
+    if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_set_ground_truth before dba_set_observations");
+    if (!cams_gt || !pts_gt) return ctx->fail(DBA_EINVAL, "dba_set_ground_truth: null array");
+    if (!finite_all(cams_gt, 6 * (long long)ctx->n_cams) || !finite_all(pts_gt, 3 * (long long)ctx->n_pts))
+      return ctx->fail(DBA_EINVAL, "dba_set_ground_truth: non-finite value");
+    double *dc = nullptr, *dp = nullptr;
+    cudaStream_t st = ctx->stream;
+    DBA_CUDA(cudaMallocAsync(&dc, 6 * (size_t)ctx->n_cams * sizeof(double), st), "alloc");
+    DBA_CUDA(cudaMallocAsync(&dp, 3 * (size_t)ctx->n_pts * sizeof(double), st), "alloc");
+    DBA_CUDA(cudaMemcpyAsync(dc, cams_gt, 6 * (size_t)ctx->n_cams * sizeof(double), cudaMemcpyHostToDevice, st), "upload");
+    std::vector<double> pts_int(3 * (size_t)ctx->n_pts);
+    for (int k = 0; k < ctx->n_pts; ++k)
+      for (int c = 0; c < 3; ++c) pts_int[3 * (size_t)k + c] = pts_gt[3 * (size_t)ctx->pt_perm[k] + c];
+    DBA_CUDA(cudaMemcpyAsync(dp, pts_int.data(), pts_int.size() * sizeof(double), cudaMemcpyHostToDevice, st),
+             "upload");
+    void* zt = const_cast<void*>(ctx->P.zt);
+    if (!zt) {
+      char* p = nullptr;
+      DBA_CUDA(ctx->alloc(&p, (size_t)ctx->n_obs * (ctx->fp32 ? sizeof(float2) : sizeof(double2))), "alloc");
+      zt = p;
     }
-    DBA_CUDA(cudaStreamSynchronize(st), "upload inlier mask");
-  } else {
-    ctx->P.inlier = nullptr;
-  }
-  DBA_CUDA(cudaFreeAsync(dc, st), "free");
-  DBA_CUDA(cudaFreeAsync(dp, st), "free");
-  DBA_CUDA(cudaStreamSynchronize(st), "ground truth");
-  ctx->P.zt = zt;
-  ctx->has_gt = true;
-  ctx->drop_graphs();  // kernel arguments changed
-  return DBA_OK;
+    DBA_CUDA(dba::launch_project_truth(ctx->P, ctx->prm, ctx->fp32, dc, dp, zt, st), "project truth");
+    if (inlier) {
+      std::vector<unsigned char> h(ctx->n_obs);
+      for (long long o = 0; o < ctx->n_obs; ++o) h[o] = inlier[ctx->perm[o]] ? 1 : 0;
+      if (!ctx->P.inlier) {
+        DBA_CUDA(ctx->upload(&ctx->P.inlier, h), "upload inlier mask");
+      } else {
+        DBA_CUDA(cudaMemcpyAsync(const_cast<unsigned char*>(ctx->P.inlier), h.data(), h.size(),
+                                 cudaMemcpyHostToDevice, st), "upload inlier mask");
+      }
+      DBA_CUDA(cudaStreamSynchronize(st), "upload inlier mask");
+    } else {
+      ctx->P.inlier = nullptr;
+    }
+    DBA_CUDA(cudaFreeAsync(dc, st), "free");
+    DBA_CUDA(cudaFreeAsync(dp, st), "free");
+    DBA_CUDA(cudaStreamSynchronize(st), "ground truth");
+    ctx->P.zt = zt;
+    ctx->has_gt = true;
+    ctx->drop_graphs();  // kernel arguments changed
+    return DBA_OK;
   });
 }
 
 dba_status dba_iterate(dba_ctx* ctx, int n_iters, dba_stats* stats) {
   return dba::guarded(ctx ? &ctx->err : nullptr, [&]() -> dba_status {
-  if (!ctx) return DBA_EINVAL;
-  if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_iterate before dba_set_observations");
-  if (n_iters < 0) return ctx->fail(DBA_EINVAL, "dba_iterate: n_iters < 0");
-  DBA_CUDA(cudaEventRecord(ctx->ev0, ctx->stream), "event");
-  dba_status s = run_iterations(ctx, n_iters);
-  if (s != DBA_OK) return s;
-  DBA_CUDA(cudaEventRecord(ctx->ev1, ctx->stream), "event");
-  s = check_device_flags(ctx);
-  if (s != DBA_OK) return s;
-  float ms = 0.f;
-  DBA_CUDA(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1), "event");
-  if (stats) return read_metrics(ctx, stats, ms * 1e-3);
-  return DBA_OK;
+    if (!ctx) return DBA_EINVAL;
+    if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_iterate before dba_set_observations");
+    if (n_iters < 0) return ctx->fail(DBA_EINVAL, "dba_iterate: n_iters < 0");
+    DBA_CUDA(cudaEventRecord(ctx->ev0, ctx->stream), "event");
+    dba_status s = run_iterations(ctx, n_iters);
+    if (s != DBA_OK) return s;
+    DBA_CUDA(cudaEventRecord(ctx->ev1, ctx->stream), "event");
+    s = check_device_flags(ctx);
+    if (s != DBA_OK) return s;
+    float ms = 0.f;
+    DBA_CUDA(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1), "event");
+    if (stats) return read_metrics(ctx, stats, ms * 1e-3);
+    return DBA_OK;
   });
 }
 
 dba_status dba_iterate_until(dba_ctx* ctx, int max_iters, double target_rmse_gt, dba_stats* stats) {
   return dba::guarded(ctx ? &ctx->err : nullptr, [&]() -> dba_status {
-  if (!ctx) return DBA_EINVAL;
-  if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_iterate_until before dba_set_observations");
-  if (!ctx->has_gt) return ctx->fail(DBA_ESTATE, "dba_iterate_until needs dba_set_ground_truth");
-  if (max_iters < 0) return ctx->fail(DBA_EINVAL, "dba_iterate_until: max_iters < 0");
-  dba_stats st{};
-  double seconds = 0.0;
-  for (int it = 0; it < max_iters; ++it) {
-    // one iteration and the stopping test's metrics pass (rmse_gt only; the full statistics
-    // are evaluated once at the end), one graph launch when graphs are on
-    DBA_CUDA(cudaEventRecord(ctx->ev0, ctx->stream), "event");
-    if (ctx->cfg.use_graph) {
-      dba_status s = ensure_graph(ctx, true);
+    if (!ctx) return DBA_EINVAL;
+    if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_iterate_until before dba_set_observations");
+    if (!ctx->has_gt) return ctx->fail(DBA_ESTATE, "dba_iterate_until needs dba_set_ground_truth");
+    if (max_iters < 0) return ctx->fail(DBA_EINVAL, "dba_iterate_until: max_iters < 0");
+    dba_stats st{};
+    double seconds = 0.0;
+    for (int it = 0; it < max_iters; ++it) {
+      // one iteration and the stopping test's metrics pass (rmse_gt only; the full statistics
+      // are evaluated once at the end), one graph launch when graphs are on
+      DBA_CUDA(cudaEventRecord(ctx->ev0, ctx->stream), "event");
+      if (ctx->cfg.use_graph) {
+        dba_status s = ensure_graph(ctx, true);
+        if (s != DBA_OK) return s;
+        DBA_CUDA(cudaGraphLaunch(ctx->graph_until, ctx->stream), "graph launch");
+        ctx->cur ^= 1;
+        ctx->pending = 1;
+        ctx->iters += 1;
+      } else {
+        dba_status s = run_iterations(ctx, 1);
+        if (s != DBA_OK) return s;
+        DBA_CUDA(dba::launch_metrics(ctx->P, ctx->prm, ctx->fp32, ctx->cur, ctx->pending, ctx->stream, true),
+                 "metrics");
+      }
+      DBA_CUDA(cudaEventRecord(ctx->ev1, ctx->stream), "event");
+      double h[8];
+      DBA_CUDA(cudaMemcpyAsync(h, ctx->P.metric_out, sizeof h, cudaMemcpyDeviceToHost, ctx->stream), "metrics copy");
+      dba_status s = check_device_flags(ctx);  // one synchronisation for both reads
       if (s != DBA_OK) return s;
-      DBA_CUDA(cudaGraphLaunch(ctx->graph_until, ctx->stream), "graph launch");
-      ctx->cur ^= 1;
-      ctx->pending = 1;
-      ctx->iters += 1;
-    } else {
-      dba_status s = run_iterations(ctx, 1);
-      if (s != DBA_OK) return s;
-      DBA_CUDA(dba::launch_metrics(ctx->P, ctx->prm, ctx->fp32, ctx->cur, ctx->pending, ctx->stream, true),
-               "metrics");
+      float ms = 0.f;
+      DBA_CUDA(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1), "event");
+      seconds += ms * 1e-3;
+      st.rmse_gt = h[7] > 0 ? std::sqrt(h[2] / h[7]) : 0.0;
+      if (st.rmse_gt <= target_rmse_gt) break;
     }
-    DBA_CUDA(cudaEventRecord(ctx->ev1, ctx->stream), "event");
-    double h[8];
-    DBA_CUDA(cudaMemcpyAsync(h, ctx->P.metric_out, sizeof h, cudaMemcpyDeviceToHost, ctx->stream), "metrics copy");
-    dba_status s = check_device_flags(ctx);  // one synchronisation for both reads
-    if (s != DBA_OK) return s;
-    float ms = 0.f;
-    DBA_CUDA(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1), "event");
-    seconds += ms * 1e-3;
-    st.rmse_gt = h[7] > 0 ? std::sqrt(h[2] / h[7]) : 0.0;
-    if (st.rmse_gt <= target_rmse_gt) break;
-  }
-  {
-    dba_status s = read_metrics(ctx, &st, seconds);
-    if (s != DBA_OK) return s;
-  }
-  if (stats) *stats = st;
-  return DBA_OK;
+    {
+      dba_status s = read_metrics(ctx, &st, seconds);
+      if (s != DBA_OK) return s;
+    }
+    if (stats) *stats = st;
+    return DBA_OK;
   });
 }
 
 dba_status dba_evaluate(dba_ctx* ctx, dba_stats* stats) {
   return dba::guarded(ctx ? &ctx->err : nullptr, [&]() -> dba_status {
-  if (!ctx || !stats) return DBA_EINVAL;
-  if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_evaluate before dba_set_observations");
-  return read_metrics(ctx, stats, 0.0);
+    if (!ctx || !stats) return DBA_EINVAL;
+    if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_evaluate before dba_set_observations");
+    return read_metrics(ctx, stats, 0.0);
   });
 }
 
 dba_status dba_get_params(dba_ctx* ctx, double* cams, double* pts) {
   return dba::guarded(ctx ? &ctx->err : nullptr, [&]() -> dba_status {
-  if (!ctx) return DBA_EINVAL;
-  if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_get_params before dba_set_observations");
-  cudaStream_t st = ctx->stream;
-  std::vector<double> X(3 * (size_t)ctx->n_pts);
-  if (cams)
-    DBA_CUDA(cudaMemcpyAsync(cams, ctx->P.Y[ctx->cur], 6 * (size_t)ctx->n_cams * sizeof(double),
-                             cudaMemcpyDeviceToHost, st), "read cameras");
-  if (pts)
-    DBA_CUDA(cudaMemcpyAsync(X.data(), ctx->P.X[ctx->cur], X.size() * sizeof(double), cudaMemcpyDeviceToHost, st),
-             "read points");
-  DBA_CUDA(cudaStreamSynchronize(st), "get_params");
-  if (pts)
-    for (int k = 0; k < ctx->n_pts; ++k)
-      for (int c = 0; c < 3; ++c) pts[3 * (size_t)ctx->pt_perm[k] + c] = X[3 * (size_t)k + c];
-  return DBA_OK;
+    if (!ctx) return DBA_EINVAL;
+    if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_get_params before dba_set_observations");
+    cudaStream_t st = ctx->stream;
+    std::vector<double> X(3 * (size_t)ctx->n_pts);
+    if (cams)
+      DBA_CUDA(cudaMemcpyAsync(cams, ctx->P.Y[ctx->cur], 6 * (size_t)ctx->n_cams * sizeof(double),
+                               cudaMemcpyDeviceToHost, st), "read cameras");
+    if (pts)
+      DBA_CUDA(cudaMemcpyAsync(X.data(), ctx->P.X[ctx->cur], X.size() * sizeof(double), cudaMemcpyDeviceToHost, st),
+               "read points");
+    DBA_CUDA(cudaStreamSynchronize(st), "get_params");
+    if (pts)
+      for (int k = 0; k < ctx->n_pts; ++k)
+        for (int c = 0; c < 3; ++c) pts[3 * (size_t)ctx->pt_perm[k] + c] = X[3 * (size_t)k + c];
+    return DBA_OK;
   });
 }
 
 dba_status dba_get_state(dba_ctx* ctx, double* copies, double* duals) {
   return dba::guarded(ctx ? &ctx->err : nullptr, [&]() -> dba_status {
-  if (!ctx) return DBA_EINVAL;
-  if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_get_state before dba_set_observations");
-  cudaStream_t st = ctx->stream;
-  if (ctx->pending) {
-    DBA_CUDA(dba::launch_settle(ctx->P, ctx->fp32, ctx->cur, st), "settle");
-    const int zero = 0;
-    DBA_CUDA(cudaMemcpyAsync(&ctx->P.ctl->pending, &zero, sizeof zero, cudaMemcpyHostToDevice, st), "settle");
-    DBA_CUDA(cudaStreamSynchronize(st), "settle");
-    ctx->pending = 0;
-  }
-  const long long l = ctx->n_obs;
-  const int m = ctx->n_cams, n = ctx->n_pts;
-  std::vector<double> X(3 * (size_t)n), Y(6 * (size_t)m), del(9 * (size_t)l), a(9 * (size_t)l);
-  DBA_CUDA(cudaMemcpyAsync(X.data(), ctx->P.X[ctx->cur], X.size() * sizeof(double), cudaMemcpyDeviceToHost, st), "read");
-  DBA_CUDA(cudaMemcpyAsync(Y.data(), ctx->P.Y[ctx->cur], Y.size() * sizeof(double), cudaMemcpyDeviceToHost, st), "read");
-  const size_t lp = (size_t)ctx->P.pitch;  // device rows pitched, host rows dense
-  DBA_CUDA(cudaMemcpy2DAsync(a.data(), l * sizeof(double), ctx->P.adual, lp * sizeof(double), l * sizeof(double), 9,
-                             cudaMemcpyDeviceToHost, st),
-           "read");
-  if (ctx->fp32) {
-    std::vector<float> f(9 * (size_t)l);
-    DBA_CUDA(cudaMemcpy2DAsync(f.data(), l * sizeof(float), ctx->P.delta, lp * sizeof(float), l * sizeof(float), 9,
+    if (!ctx) return DBA_EINVAL;
+    if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_get_state before dba_set_observations");
+    cudaStream_t st = ctx->stream;
+    if (ctx->pending) {
+      DBA_CUDA(dba::launch_settle(ctx->P, ctx->fp32, ctx->cur, st), "settle");
+      const int zero = 0;
+      DBA_CUDA(cudaMemcpyAsync(&ctx->P.ctl->pending, &zero, sizeof zero, cudaMemcpyHostToDevice, st), "settle");
+      DBA_CUDA(cudaStreamSynchronize(st), "settle");
+      ctx->pending = 0;
+    }
+    const long long l = ctx->n_obs;
+    const int m = ctx->n_cams, n = ctx->n_pts;
+    std::vector<double> X(3 * (size_t)n), Y(6 * (size_t)m), del(9 * (size_t)l), a(9 * (size_t)l);
+    DBA_CUDA(cudaMemcpyAsync(X.data(), ctx->P.X[ctx->cur], X.size() * sizeof(double), cudaMemcpyDeviceToHost, st), "read");
+    DBA_CUDA(cudaMemcpyAsync(Y.data(), ctx->P.Y[ctx->cur], Y.size() * sizeof(double), cudaMemcpyDeviceToHost, st), "read");
+    const size_t lp = (size_t)ctx->P.pitch;  // device rows pitched, host rows dense
+    DBA_CUDA(cudaMemcpy2DAsync(a.data(), l * sizeof(double), ctx->P.adual, lp * sizeof(double), l * sizeof(double), 9,
                                cudaMemcpyDeviceToHost, st),
              "read");
-    DBA_CUDA(cudaStreamSynchronize(st), "get_state");
-    for (size_t k = 0; k < f.size(); ++k) del[k] = f[k];
-  } else {
-    DBA_CUDA(cudaMemcpy2DAsync(del.data(), l * sizeof(double), ctx->P.delta, lp * sizeof(double), l * sizeof(double),
-                               9, cudaMemcpyDeviceToHost, st),
-             "read");
-    DBA_CUDA(cudaStreamSynchronize(st), "get_state");
-  }
-  for (long long o = 0; o < l; ++o) {
-    const long long dst = ctx->perm[o];
-    const size_t i = ctx->h_obs_pt[o], j = ctx->h_obs_cam[o];
-    for (int c = 0; c < 9; ++c) {
-      if (copies) copies[9 * dst + c] = (c < 3 ? X[3 * i + c] : Y[6 * j + c - 3]) + del[c * (size_t)l + o];
-      if (duals) duals[9 * dst + c] = ctx->rho_of(c) * a[c * (size_t)l + o];
+    if (ctx->fp32) {
+      std::vector<float> f(9 * (size_t)l);
+      DBA_CUDA(cudaMemcpy2DAsync(f.data(), l * sizeof(float), ctx->P.delta, lp * sizeof(float), l * sizeof(float), 9,
+                                 cudaMemcpyDeviceToHost, st),
+               "read");
+      DBA_CUDA(cudaStreamSynchronize(st), "get_state");
+      for (size_t k = 0; k < f.size(); ++k) del[k] = f[k];
+    } else {
+      DBA_CUDA(cudaMemcpy2DAsync(del.data(), l * sizeof(double), ctx->P.delta, lp * sizeof(double), l * sizeof(double),
+                                 9, cudaMemcpyDeviceToHost, st),
+               "read");
+      DBA_CUDA(cudaStreamSynchronize(st), "get_state");
     }
-  }
-  return DBA_OK;
+    for (long long o = 0; o < l; ++o) {
+      const long long dst = ctx->perm[o];
+      const size_t i = ctx->h_obs_pt[o], j = ctx->h_obs_cam[o];
+      for (int c = 0; c < 9; ++c) {
+        if (copies) copies[9 * dst + c] = (c < 3 ? X[3 * i + c] : Y[6 * j + c - 3]) + del[c * (size_t)l + o];
+        if (duals) duals[9 * dst + c] = ctx->rho_of(c) * a[c * (size_t)l + o];
+      }
+    }
+    return DBA_OK;
   });
 }
 
 dba_status dba_set_state(dba_ctx* ctx, const double* copies, const double* duals, const double* cams,
                          const double* pts) {
   return dba::guarded(ctx ? &ctx->err : nullptr, [&]() -> dba_status {
-  if (!ctx) return DBA_EINVAL;
-  if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_set_state before dba_set_observations");
-  if (!copies || !duals || !cams || !pts) return ctx->fail(DBA_EINVAL, "dba_set_state: null array");
-  if (!finite_all(copies, 9 * ctx->n_obs) || !finite_all(duals, 9 * ctx->n_obs) ||
-      !finite_all(cams, 6 * (long long)ctx->n_cams) || !finite_all(pts, 3 * (long long)ctx->n_pts))
-    return ctx->fail(DBA_EINVAL, "dba_set_state: non-finite value");
-  return upload_state(ctx, cams, pts, copies, duals);
+    if (!ctx) return DBA_EINVAL;
+    if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_set_state before dba_set_observations");
+    if (!copies || !duals || !cams || !pts) return ctx->fail(DBA_EINVAL, "dba_set_state: null array");
+    if (!finite_all(copies, 9 * ctx->n_obs) || !finite_all(duals, 9 * ctx->n_obs) ||
+        !finite_all(cams, 6 * (long long)ctx->n_cams) || !finite_all(pts, 3 * (long long)ctx->n_pts))
+      return ctx->fail(DBA_EINVAL, "dba_set_state: non-finite value");
+    return upload_state(ctx, cams, pts, copies, duals);
   });
 }
 
@@ -1103,55 +1103,55 @@ dba_status dba_inject_copy_stall(dba_ctx* ctx, int on) {
 
 dba_status dba_profile(dba_ctx* ctx, int n_iters, const char** names, double* ms, int* count) {
   return dba::guarded(ctx ? &ctx->err : nullptr, [&]() -> dba_status {
-  if (!ctx || !count) return DBA_EINVAL;
-  if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_profile before dba_set_observations");
-  if (n_iters <= 0 || *count < 2 || !names || !ms) return ctx->fail(DBA_EINVAL, "dba_profile: bad arguments");
-  const int capacity = *count;
-  std::vector<cudaEvent_t> ev(3 * (size_t)n_iters);
-  for (auto& e : ev) DBA_CUDA(cudaEventCreate(&e), "event");
-  cudaStream_t st = ctx->stream;
-  std::vector<cudaEvent_t> evw(ctx->warm ? (size_t)n_iters : 0);
-  for (auto& e : evw) DBA_CUDA(cudaEventCreate(&e), "event");
-  for (int it = 0; it < n_iters; ++it) {
-    if (ctx->warm) {
-      DBA_CUDA(cudaEventRecord(evw[it], st), "event");
-      DBA_CUDA(dba::launch_mlp_warmstart(ctx->P, ctx->prm, ctx->fp32, ctx->d_mlp_blob, ctx->d_mlp_params, st),
-               "warm start");
+    if (!ctx || !count) return DBA_EINVAL;
+    if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_profile before dba_set_observations");
+    if (n_iters <= 0 || *count < 2 || !names || !ms) return ctx->fail(DBA_EINVAL, "dba_profile: bad arguments");
+    const int capacity = *count;
+    std::vector<cudaEvent_t> ev(3 * (size_t)n_iters);
+    for (auto& e : ev) DBA_CUDA(cudaEventCreate(&e), "event");
+    cudaStream_t st = ctx->stream;
+    std::vector<cudaEvent_t> evw(ctx->warm ? (size_t)n_iters : 0);
+    for (auto& e : evw) DBA_CUDA(cudaEventCreate(&e), "event");
+    for (int it = 0; it < n_iters; ++it) {
+      if (ctx->warm) {
+        DBA_CUDA(cudaEventRecord(evw[it], st), "event");
+        DBA_CUDA(dba::launch_mlp_warmstart(ctx->P, ctx->prm, ctx->fp32, ctx->d_mlp_blob, ctx->d_mlp_params, st),
+                 "warm start");
+      }
+      DBA_CUDA(cudaEventRecord(ev[3 * it], st), "event");
+      DBA_CUDA(dba::launch_tile_iterate(ctx->P, ctx->tmaps, ctx->prm, ctx->fp32, st), "tile_iterate");
+      DBA_CUDA(cudaEventRecord(ev[3 * it + 1], st), "event");
+      DBA_CUDA(dba::launch_finalize(ctx->P, ctx->fp32, st), "finalize");
+      DBA_CUDA(cudaEventRecord(ev[3 * it + 2], st), "event");
     }
-    DBA_CUDA(cudaEventRecord(ev[3 * it], st), "event");
-    DBA_CUDA(dba::launch_tile_iterate(ctx->P, ctx->tmaps, ctx->prm, ctx->fp32, st), "tile_iterate");
-    DBA_CUDA(cudaEventRecord(ev[3 * it + 1], st), "event");
-    DBA_CUDA(dba::launch_finalize(ctx->P, ctx->fp32, st), "finalize");
-    DBA_CUDA(cudaEventRecord(ev[3 * it + 2], st), "event");
-  }
-  ctx->cur ^= (n_iters & 1);
-  ctx->pending = 1;
-  ctx->iters += n_iters;
-  dba_status s = check_device_flags(ctx);
-  double t0 = 0, t1 = 0, tw = 0;
-  for (int it = 0; it < n_iters && s == DBA_OK; ++it) {
-    float a = 0, b = 0, c = 0;
-    cudaEventElapsedTime(&a, ev[3 * it], ev[3 * it + 1]);
-    cudaEventElapsedTime(&b, ev[3 * it + 1], ev[3 * it + 2]);
-    if (ctx->warm) cudaEventElapsedTime(&c, evw[it], ev[3 * it]);
-    t0 += a;
-    t1 += b;
-    tw += c;
-  }
-  for (auto& e : ev) cudaEventDestroy(e);
-  for (auto& e : evw) cudaEventDestroy(e);
-  if (s != DBA_OK) return s;
-  names[0] = "tile_iterate";
-  ms[0] = t0 / n_iters;
-  names[1] = "finalize";
-  ms[1] = t1 / n_iters;
-  *count = 2;
-  if (ctx->warm && capacity >= 3) {
-    names[2] = "mlp_warm_start";
-    ms[2] = tw / n_iters;
-    *count = 3;
-  }
-  return DBA_OK;
+    ctx->cur ^= (n_iters & 1);
+    ctx->pending = 1;
+    ctx->iters += n_iters;
+    dba_status s = check_device_flags(ctx);
+    double t0 = 0, t1 = 0, tw = 0;
+    for (int it = 0; it < n_iters && s == DBA_OK; ++it) {
+      float a = 0, b = 0, c = 0;
+      cudaEventElapsedTime(&a, ev[3 * it], ev[3 * it + 1]);
+      cudaEventElapsedTime(&b, ev[3 * it + 1], ev[3 * it + 2]);
+      if (ctx->warm) cudaEventElapsedTime(&c, evw[it], ev[3 * it]);
+      t0 += a;
+      t1 += b;
+      tw += c;
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    for (auto& e : evw) cudaEventDestroy(e);
+    if (s != DBA_OK) return s;
+    names[0] = "tile_iterate";
+    ms[0] = t0 / n_iters;
+    names[1] = "finalize";
+    ms[1] = t1 / n_iters;
+    *count = 2;
+    if (ctx->warm && capacity >= 3) {
+      names[2] = "mlp_warm_start";
+      ms[2] = tw / n_iters;
+      *count = 3;
+    }
+    return DBA_OK;
   });
 }
 
@@ -1199,111 +1199,111 @@ dba_status dba_evaluate_noalloc(const dba_config* cfg, int32_t n_cams, int32_t n
 dba_status dba_set_scenes(dba_ctx* ctx, int32_t n_scenes, const int64_t* obs_off, const int32_t* cam_off,
                           const int32_t* pt_off) {
   return dba::guarded(ctx ? &ctx->err : nullptr, [&]() -> dba_status {
-  if (!ctx) return DBA_EINVAL;
-  if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_set_scenes before dba_set_observations");
-  if (n_scenes <= 0 || !obs_off || !cam_off || !pt_off) return ctx->fail(DBA_EINVAL, "dba_set_scenes: bad arguments");
-  if (obs_off[0] != 0 || cam_off[0] != 0 || pt_off[0] != 0 || obs_off[n_scenes] != ctx->n_obs ||
-      cam_off[n_scenes] != ctx->n_cams || pt_off[n_scenes] != ctx->n_pts)
-    return ctx->fail(DBA_EINVAL, "dba_set_scenes: offsets must start at 0 and end at n_obs, n_cams, n_pts");
-  for (int sc = 0; sc < n_scenes; ++sc)
-    if (obs_off[sc + 1] < obs_off[sc] || cam_off[sc + 1] < cam_off[sc] || pt_off[sc + 1] < pt_off[sc])
-      return ctx->fail(DBA_EINVAL, "dba_set_scenes: offsets must be nondecreasing");
-  // scene of every caller observation, checked against its camera and point
-  std::vector<int> scene_caller(ctx->n_obs);
-  std::vector<int> cam_scene(ctx->n_cams), pt_scene(ctx->n_pts);
-  for (int sc = 0; sc < n_scenes; ++sc) {
-    for (int64_t o = obs_off[sc]; o < obs_off[sc + 1]; ++o) scene_caller[o] = sc;
-    for (int32_t j = cam_off[sc]; j < cam_off[sc + 1]; ++j) cam_scene[j] = sc;
-    for (int32_t i = pt_off[sc]; i < pt_off[sc + 1]; ++i) pt_scene[i] = sc;
-  }
-  std::vector<int> scene_int(ctx->n_obs);
-  for (long long o = 0; o < ctx->n_obs; ++o) {
-    const long long src = ctx->perm[o];
-    const int sc = scene_caller[src];
-    if (cam_scene[ctx->h_obs_cam[o]] != sc || pt_scene[ctx->pt_perm[ctx->h_obs_pt[o]]] != sc)
-      return ctx->fail(DBA_EINVAL, "dba_set_scenes: observation " + std::to_string(src) + " leaves its scene");
-    scene_int[o] = sc;
-  }
-  const int* d = nullptr;
-  DBA_CUDA(ctx->upload(&d, scene_int), "upload scenes");
-  ctx->d_scene_of_obs = const_cast<int*>(d);
-  DBA_CUDA(ctx->alloc(&ctx->d_scene_sums, 5 * (size_t)n_scenes), "alloc scene sums");
-  DBA_CUDA(cudaStreamSynchronize(ctx->stream), "set_scenes");
-  ctx->n_scenes = n_scenes;
-  return DBA_OK;
+    if (!ctx) return DBA_EINVAL;
+    if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_set_scenes before dba_set_observations");
+    if (n_scenes <= 0 || !obs_off || !cam_off || !pt_off) return ctx->fail(DBA_EINVAL, "dba_set_scenes: bad arguments");
+    if (obs_off[0] != 0 || cam_off[0] != 0 || pt_off[0] != 0 || obs_off[n_scenes] != ctx->n_obs ||
+        cam_off[n_scenes] != ctx->n_cams || pt_off[n_scenes] != ctx->n_pts)
+      return ctx->fail(DBA_EINVAL, "dba_set_scenes: offsets must start at 0 and end at n_obs, n_cams, n_pts");
+    for (int sc = 0; sc < n_scenes; ++sc)
+      if (obs_off[sc + 1] < obs_off[sc] || cam_off[sc + 1] < cam_off[sc] || pt_off[sc + 1] < pt_off[sc])
+        return ctx->fail(DBA_EINVAL, "dba_set_scenes: offsets must be nondecreasing");
+    // scene of every caller observation, checked against its camera and point
+    std::vector<int> scene_caller(ctx->n_obs);
+    std::vector<int> cam_scene(ctx->n_cams), pt_scene(ctx->n_pts);
+    for (int sc = 0; sc < n_scenes; ++sc) {
+      for (int64_t o = obs_off[sc]; o < obs_off[sc + 1]; ++o) scene_caller[o] = sc;
+      for (int32_t j = cam_off[sc]; j < cam_off[sc + 1]; ++j) cam_scene[j] = sc;
+      for (int32_t i = pt_off[sc]; i < pt_off[sc + 1]; ++i) pt_scene[i] = sc;
+    }
+    std::vector<int> scene_int(ctx->n_obs);
+    for (long long o = 0; o < ctx->n_obs; ++o) {
+      const long long src = ctx->perm[o];
+      const int sc = scene_caller[src];
+      if (cam_scene[ctx->h_obs_cam[o]] != sc || pt_scene[ctx->pt_perm[ctx->h_obs_pt[o]]] != sc)
+        return ctx->fail(DBA_EINVAL, "dba_set_scenes: observation " + std::to_string(src) + " leaves its scene");
+      scene_int[o] = sc;
+    }
+    const int* d = nullptr;
+    DBA_CUDA(ctx->upload(&d, scene_int), "upload scenes");
+    ctx->d_scene_of_obs = const_cast<int*>(d);
+    DBA_CUDA(ctx->alloc(&ctx->d_scene_sums, 5 * (size_t)n_scenes), "alloc scene sums");
+    DBA_CUDA(cudaStreamSynchronize(ctx->stream), "set_scenes");
+    ctx->n_scenes = n_scenes;
+    return DBA_OK;
   });
 }
 
 dba_status dba_scene_stats(dba_ctx* ctx, double* rmse_obs, double* rmse_gt, double* objective) {
   return dba::guarded(ctx ? &ctx->err : nullptr, [&]() -> dba_status {
-  if (!ctx) return DBA_EINVAL;
-  if (!ctx->has_problem || ctx->n_scenes == 0)
-    return ctx->fail(DBA_ESTATE, "dba_scene_stats needs dba_set_observations and dba_set_scenes");
-  cudaStream_t st = ctx->stream;
-  std::vector<double> h(5 * (size_t)ctx->n_scenes);
-  DBA_CUDA(cudaMemsetAsync(ctx->d_scene_sums, 0, h.size() * sizeof(double), st), "scene stats");
-  DBA_CUDA(dba::launch_scene_metrics(ctx->P, ctx->prm, ctx->fp32, ctx->d_scene_of_obs, ctx->d_scene_sums, st),
-           "scene stats");
-  DBA_CUDA(cudaMemcpyAsync(h.data(), ctx->d_scene_sums, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st),
-           "scene stats");
-  DBA_CUDA(cudaStreamSynchronize(st), "scene stats");
-  for (int sc = 0; sc < ctx->n_scenes; ++sc) {
-    const double* v = &h[5 * (size_t)sc];
-    if (rmse_obs) rmse_obs[sc] = v[3] > 0 ? std::sqrt(v[0] / v[3]) : 0.0;
-    if (objective) objective[sc] = v[1];
-    if (rmse_gt) rmse_gt[sc] = (ctx->has_gt && v[4] > 0) ? std::sqrt(v[2] / v[4]) : 0.0;
-  }
-  return DBA_OK;
+    if (!ctx) return DBA_EINVAL;
+    if (!ctx->has_problem || ctx->n_scenes == 0)
+      return ctx->fail(DBA_ESTATE, "dba_scene_stats needs dba_set_observations and dba_set_scenes");
+    cudaStream_t st = ctx->stream;
+    std::vector<double> h(5 * (size_t)ctx->n_scenes);
+    DBA_CUDA(cudaMemsetAsync(ctx->d_scene_sums, 0, h.size() * sizeof(double), st), "scene stats");
+    DBA_CUDA(dba::launch_scene_metrics(ctx->P, ctx->prm, ctx->fp32, ctx->d_scene_of_obs, ctx->d_scene_sums, st),
+             "scene stats");
+    DBA_CUDA(cudaMemcpyAsync(h.data(), ctx->d_scene_sums, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st),
+             "scene stats");
+    DBA_CUDA(cudaStreamSynchronize(st), "scene stats");
+    for (int sc = 0; sc < ctx->n_scenes; ++sc) {
+      const double* v = &h[5 * (size_t)sc];
+      if (rmse_obs) rmse_obs[sc] = v[3] > 0 ? std::sqrt(v[0] / v[3]) : 0.0;
+      if (objective) objective[sc] = v[1];
+      if (rmse_gt) rmse_gt[sc] = (ctx->has_gt && v[4] > 0) ? std::sqrt(v[2] / v[4]) : 0.0;
+    }
+    return DBA_OK;
   });
 }
 
 dba_status dba_mlp_harvest(dba_ctx* ctx, int64_t stride, int target_steps, float* feats, float* targets,
                            int64_t cap, int64_t* n_out) {
   return dba::guarded(ctx ? &ctx->err : nullptr, [&]() -> dba_status {
-  if (!ctx) return DBA_EINVAL;
-  if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_mlp_harvest before dba_set_observations");
-  if (stride <= 0 || cap < 0 || target_steps < 0 || target_steps > 1000 || !feats || !targets || !n_out)
-    return ctx->fail(DBA_EINVAL, "dba_mlp_harvest: bad arguments");
-  const int64_t n = std::min<int64_t>(cap, (ctx->n_obs + stride - 1) / stride);
-  DBA_CUDA(dba::launch_mlp_harvest(ctx->P, ctx->prm, ctx->fp32, ctx->pending, stride, n, target_steps, feats,
-                                   targets, ctx->stream),
-           "harvest");
-  DBA_CUDA(cudaStreamSynchronize(ctx->stream), "harvest");
-  *n_out = n;
-  return DBA_OK;
+    if (!ctx) return DBA_EINVAL;
+    if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_mlp_harvest before dba_set_observations");
+    if (stride <= 0 || cap < 0 || target_steps < 0 || target_steps > 1000 || !feats || !targets || !n_out)
+      return ctx->fail(DBA_EINVAL, "dba_mlp_harvest: bad arguments");
+    const int64_t n = std::min<int64_t>(cap, (ctx->n_obs + stride - 1) / stride);
+    DBA_CUDA(dba::launch_mlp_harvest(ctx->P, ctx->prm, ctx->fp32, ctx->pending, stride, n, target_steps, feats,
+                                     targets, ctx->stream),
+             "harvest");
+    DBA_CUDA(cudaStreamSynchronize(ctx->stream), "harvest");
+    *n_out = n;
+    return DBA_OK;
   });
 }
 
 dba_status dba_set_warm_start(dba_ctx* ctx, const dba_mlp* mlp) {
   return dba::guarded(ctx ? &ctx->err : nullptr, [&]() -> dba_status {
-  if (!ctx) return DBA_EINVAL;
-  if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_set_warm_start before dba_set_observations");
-  ctx->drop_graphs();
-  if (!mlp) {
-    ctx->warm = false;
-    ctx->P.mlp_start = nullptr;
+    if (!ctx) return DBA_EINVAL;
+    if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_set_warm_start before dba_set_observations");
+    ctx->drop_graphs();
+    if (!mlp) {
+      ctx->warm = false;
+      ctx->P.mlp_start = nullptr;
+      return DBA_OK;
+    }
+    std::vector<float> params(DBA_MLP_N_PARAMS);
+    const dba_status ps = dba_mlp_get_params(mlp, params.data());
+    if (ps != DBA_OK) return ctx->fail(ps, "dba_set_warm_start: cannot read the network");
+    std::vector<unsigned char> blob;
+    dba::mlp_make_blob(params.data(), blob);
+    if (!ctx->d_mlp_blob) {
+      DBA_CUDA(ctx->alloc(&ctx->d_mlp_blob, blob.size()), "warm start");
+      DBA_CUDA(ctx->alloc(&ctx->d_mlp_params, params.size()), "warm start");
+      char* p = nullptr;
+      DBA_CUDA(ctx->alloc(&p, 9 * (size_t)ctx->P.pitch * (ctx->fp32 ? sizeof(float) : sizeof(double))), "warm start");
+      ctx->P.mlp_start = p;
+    }
+    DBA_CUDA(cudaMemcpyAsync(ctx->d_mlp_blob, blob.data(), blob.size(), cudaMemcpyHostToDevice, ctx->stream),
+             "warm start");
+    DBA_CUDA(cudaMemcpyAsync(ctx->d_mlp_params, params.data(), params.size() * sizeof(float), cudaMemcpyHostToDevice,
+                             ctx->stream),
+             "warm start");
+    DBA_CUDA(cudaStreamSynchronize(ctx->stream), "warm start");
+    ctx->warm = true;
     return DBA_OK;
-  }
-  std::vector<float> params(DBA_MLP_N_PARAMS);
-  const dba_status ps = dba_mlp_get_params(mlp, params.data());
-  if (ps != DBA_OK) return ctx->fail(ps, "dba_set_warm_start: cannot read the network");
-  std::vector<unsigned char> blob;
-  dba::mlp_make_blob(params.data(), blob);
-  if (!ctx->d_mlp_blob) {
-    DBA_CUDA(ctx->alloc(&ctx->d_mlp_blob, blob.size()), "warm start");
-    DBA_CUDA(ctx->alloc(&ctx->d_mlp_params, params.size()), "warm start");
-    char* p = nullptr;
-    DBA_CUDA(ctx->alloc(&p, 9 * (size_t)ctx->P.pitch * (ctx->fp32 ? sizeof(float) : sizeof(double))), "warm start");
-    ctx->P.mlp_start = p;
-  }
-  DBA_CUDA(cudaMemcpyAsync(ctx->d_mlp_blob, blob.data(), blob.size(), cudaMemcpyHostToDevice, ctx->stream),
-           "warm start");
-  DBA_CUDA(cudaMemcpyAsync(ctx->d_mlp_params, params.data(), params.size() * sizeof(float), cudaMemcpyHostToDevice,
-                           ctx->stream),
-           "warm start");
-  DBA_CUDA(cudaStreamSynchronize(ctx->stream), "warm start");
-  ctx->warm = true;
-  return DBA_OK;
   });
 }
 

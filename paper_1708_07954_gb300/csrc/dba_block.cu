@@ -1140,244 +1140,244 @@ dba_status dba_block_set_observations(dba_block_ctx* ctx, int32_t n_cams, int32_
                                       const int32_t* pt_idx, const int32_t* cam_idx, const double* z,
                                       const double* cams0, const double* pts0) {
   return dba::guarded(ctx ? &ctx->err : nullptr, [&]() -> dba_status {
-  if (!ctx) return DBA_EINVAL;
-  if (n_cams <= 0 || n_pts <= 0 || n_obs <= 0)
-    return ctx->fail(DBA_EINVAL, "dba_block_set_observations: n_cams, n_pts and n_obs must be positive");
-  if (n_obs > INT_MAX) return ctx->fail(DBA_EINVAL, "dba_block_set_observations: at most 2^31-1 observations");
-  if (!pt_idx || !cam_idx || !z || !cams0 || !pts0)
-    return ctx->fail(DBA_EINVAL, "dba_block_set_observations: null array");
-  for (int64_t o = 0; o < n_obs; ++o) {
-    if (pt_idx[o] < 0 || pt_idx[o] >= n_pts || cam_idx[o] < 0 || cam_idx[o] >= n_cams)
-      return ctx->fail(DBA_EINVAL, "dba_block_set_observations: observation " + std::to_string(o) +
-                                       " indexes outside the cameras or points");
-    if (!std::isfinite(z[2 * o]) || !std::isfinite(z[2 * o + 1]))
-      return ctx->fail(DBA_EINVAL, "dba_block_set_observations: non-finite pixel");
-  }
-  for (int64_t k = 0; k < 6LL * n_cams; ++k)
-    if (!std::isfinite(cams0[k])) return ctx->fail(DBA_EINVAL, "dba_block_set_observations: non-finite camera");
-  for (int64_t k = 0; k < 3LL * n_pts; ++k)
-    if (!std::isfinite(pts0[k])) return ctx->fail(DBA_EINVAL, "dba_block_set_observations: non-finite point");
-  ctx->free_all();
-  const long long l = n_obs;
-  const int n = n_pts, m = n_cams;
-  BlockHostLayout H;
-  {
-    const std::string msg = build_block_layout(n_cams, n_pts, l, pt_idx, cam_idx, ctx->pi, ctx->kappa, H);
-    if (!msg.empty()) return ctx->fail(DBA_EINVAL, "dba_block_set_observations: " + msg);
-  }
-  ctx->blk_obs = H.blk_obs;
-  ctx->h_blocks = H.blocks;
-  for (int k = 0; k <= dba::kBlkClasses; ++k) ctx->cls[k] = H.cls[k];
-  ctx->flops_step = H.flops_step;
-  ctx->flops_start = H.flops_start;
-  const std::vector<dba::BlockInfo>& blocks = H.blocks;
-  const std::vector<int>&pc_obs = H.pc_obs, &pc_pt = H.pc_pt, &cc_cam = H.cc_cam, &obs_pt = H.obs_pt,
-                    &obs_cam = H.obs_cam, &pt_off = H.pt_off, &cam_off = H.cam_off, &pt_cp = H.pt_cp,
-                    &cam_cp = H.cam_cp;
-  const std::vector<unsigned char>& obs_lc = H.obs_lc;
-  const std::vector<long long>& idx = H.blk_obs;
-  const long long n_pc = (long long)pc_pt.size(), n_cc = (long long)cc_cam.size();
-  // device problem
-  dba::BlockProblem& B = ctx->B;
-  B.n_cams = m;
-  B.n_pts = n;
-  B.n_obs = l;
-  B.n_blocks = (int)blocks.size();
-  B.n_pc = n_pc;
-  B.n_cc = n_cc;
-  const size_t tsz = ctx->fp32 ? sizeof(float) : sizeof(double);
-  dba::BlockInfo* d_blocks = nullptr;
-  int *d_pc_obs = nullptr, *d_pc_pt = nullptr, *d_cc_cam = nullptr, *d_obs_pt = nullptr, *d_obs_cam = nullptr;
-  int *d_pt_off = nullptr, *d_pt_cp = nullptr, *d_cam_off = nullptr, *d_cam_cp = nullptr;
-  unsigned char* d_lc = nullptr;
-  BLK_CUDA(upload(ctx, &d_blocks, blocks), "upload");
-  BLK_CUDA(upload(ctx, &d_pc_obs, pc_obs), "upload");
-  BLK_CUDA(upload(ctx, &d_pc_pt, pc_pt), "upload");
-  BLK_CUDA(upload(ctx, &d_cc_cam, cc_cam), "upload");
-  BLK_CUDA(upload(ctx, &d_obs_pt, obs_pt), "upload");
-  BLK_CUDA(upload(ctx, &d_obs_cam, obs_cam), "upload");
-  BLK_CUDA(upload(ctx, &d_lc, obs_lc), "upload");
-  BLK_CUDA(upload(ctx, &d_pt_off, pt_off), "upload");
-  BLK_CUDA(upload(ctx, &d_pt_cp, pt_cp), "upload");
-  BLK_CUDA(upload(ctx, &d_cam_off, cam_off), "upload");
-  BLK_CUDA(upload(ctx, &d_cam_cp, cam_cp), "upload");
-  B.blocks = d_blocks;
-  B.pc_obs = d_pc_obs;
-  B.pc_pt = d_pc_pt;
-  B.cc_cam = d_cc_cam;
-  B.obs_pt = d_obs_pt;
-  B.obs_cam = d_obs_cam;
-  B.obs_lc = d_lc;
-  B.pt_cp_off = d_pt_off;
-  B.pt_cp = d_pt_cp;
-  B.cam_cp_off = d_cam_off;
-  B.cam_cp = d_cam_cp;
-  // pixels in block order, in the working precision
-  {
-    std::vector<double> zb(2 * l);
-    for (long long t = 0; t < l; ++t) {
-      zb[2 * t] = z[2 * idx[t]];
-      zb[2 * t + 1] = z[2 * idx[t] + 1];
+    if (!ctx) return DBA_EINVAL;
+    if (n_cams <= 0 || n_pts <= 0 || n_obs <= 0)
+      return ctx->fail(DBA_EINVAL, "dba_block_set_observations: n_cams, n_pts and n_obs must be positive");
+    if (n_obs > INT_MAX) return ctx->fail(DBA_EINVAL, "dba_block_set_observations: at most 2^31-1 observations");
+    if (!pt_idx || !cam_idx || !z || !cams0 || !pts0)
+      return ctx->fail(DBA_EINVAL, "dba_block_set_observations: null array");
+    for (int64_t o = 0; o < n_obs; ++o) {
+      if (pt_idx[o] < 0 || pt_idx[o] >= n_pts || cam_idx[o] < 0 || cam_idx[o] >= n_cams)
+        return ctx->fail(DBA_EINVAL, "dba_block_set_observations: observation " + std::to_string(o) +
+                                         " indexes outside the cameras or points");
+      if (!std::isfinite(z[2 * o]) || !std::isfinite(z[2 * o + 1]))
+        return ctx->fail(DBA_EINVAL, "dba_block_set_observations: non-finite pixel");
     }
-    void* d_z = nullptr;
-    BLK_CUDA(ctx->alloc(&d_z, tsz * 2 * l), "alloc");
-    if (ctx->fp32) {
-      std::vector<float> zf(zb.begin(), zb.end());
-      BLK_CUDA(cudaMemcpyAsync(d_z, zf.data(), sizeof(float) * zf.size(), cudaMemcpyHostToDevice, ctx->stream),
-               "upload");
-      BLK_CUDA(cudaStreamSynchronize(ctx->stream), "upload");
-    } else {
-      BLK_CUDA(cudaMemcpyAsync(d_z, zb.data(), sizeof(double) * zb.size(), cudaMemcpyHostToDevice, ctx->stream),
-               "upload");
-      BLK_CUDA(cudaStreamSynchronize(ctx->stream), "upload");
+    for (int64_t k = 0; k < 6LL * n_cams; ++k)
+      if (!std::isfinite(cams0[k])) return ctx->fail(DBA_EINVAL, "dba_block_set_observations: non-finite camera");
+    for (int64_t k = 0; k < 3LL * n_pts; ++k)
+      if (!std::isfinite(pts0[k])) return ctx->fail(DBA_EINVAL, "dba_block_set_observations: non-finite point");
+    ctx->free_all();
+    const long long l = n_obs;
+    const int n = n_pts, m = n_cams;
+    BlockHostLayout H;
+    {
+      const std::string msg = build_block_layout(n_cams, n_pts, l, pt_idx, cam_idx, ctx->pi, ctx->kappa, H);
+      if (!msg.empty()) return ctx->fail(DBA_EINVAL, "dba_block_set_observations: " + msg);
     }
-    B.z = d_z;
-  }
-  // state: copies at the consensus (offsets 0), duals 0
-  void *d_pdel = nullptr, *d_cdel = nullptr;
-  BLK_CUDA(ctx->alloc(&d_pdel, tsz * 3 * n_pc), "alloc");
-  BLK_CUDA(ctx->alloc(&d_cdel, tsz * 6 * n_cc), "alloc");
-  BLK_CUDA(ctx->alloc(&B.pc_a, sizeof(double) * 3 * n_pc), "alloc");
-  BLK_CUDA(ctx->alloc(&B.cc_a, sizeof(double) * 6 * n_cc), "alloc");
-  BLK_CUDA(cudaMemsetAsync(d_pdel, 0, tsz * 3 * n_pc, ctx->stream), "init");
-  BLK_CUDA(cudaMemsetAsync(d_cdel, 0, tsz * 6 * n_cc, ctx->stream), "init");
-  BLK_CUDA(cudaMemsetAsync(B.pc_a, 0, sizeof(double) * 3 * n_pc, ctx->stream), "init");
-  BLK_CUDA(cudaMemsetAsync(B.cc_a, 0, sizeof(double) * 6 * n_cc, ctx->stream), "init");
-  B.pc_delta = d_pdel;
-  B.cc_delta = d_cdel;
-  for (int k = 0; k < 2; ++k) {
-    BLK_CUDA(ctx->alloc(&B.X[k], sizeof(double) * 3 * n), "alloc");
-    BLK_CUDA(ctx->alloc(&B.Y[k], sizeof(double) * 6 * m), "alloc");
-  }
-  BLK_CUDA(cudaMemcpyAsync(B.X[0], pts0, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, ctx->stream), "upload");
-  BLK_CUDA(cudaMemcpyAsync(B.Y[0], cams0, sizeof(double) * 6 * m, cudaMemcpyHostToDevice, ctx->stream), "upload");
-  BLK_CUDA(ctx->alloc(&B.sums, sizeof(double) * 8), "alloc");
-  BLK_CUDA(ctx->alloc(&B.err, sizeof(int)), "alloc");
-  BLK_CUDA(cudaMemsetAsync(B.err, 0, sizeof(int), ctx->stream), "init");
-  BLK_CUDA(cudaStreamSynchronize(ctx->stream), "upload");
-  ctx->cur = 0;
-  ctx->iters = 0;
-  ctx->has_problem = true;
-  return DBA_OK;
+    ctx->blk_obs = H.blk_obs;
+    ctx->h_blocks = H.blocks;
+    for (int k = 0; k <= dba::kBlkClasses; ++k) ctx->cls[k] = H.cls[k];
+    ctx->flops_step = H.flops_step;
+    ctx->flops_start = H.flops_start;
+    const std::vector<dba::BlockInfo>& blocks = H.blocks;
+    const std::vector<int>&pc_obs = H.pc_obs, &pc_pt = H.pc_pt, &cc_cam = H.cc_cam, &obs_pt = H.obs_pt,
+                      &obs_cam = H.obs_cam, &pt_off = H.pt_off, &cam_off = H.cam_off, &pt_cp = H.pt_cp,
+                      &cam_cp = H.cam_cp;
+    const std::vector<unsigned char>& obs_lc = H.obs_lc;
+    const std::vector<long long>& idx = H.blk_obs;
+    const long long n_pc = (long long)pc_pt.size(), n_cc = (long long)cc_cam.size();
+    // device problem
+    dba::BlockProblem& B = ctx->B;
+    B.n_cams = m;
+    B.n_pts = n;
+    B.n_obs = l;
+    B.n_blocks = (int)blocks.size();
+    B.n_pc = n_pc;
+    B.n_cc = n_cc;
+    const size_t tsz = ctx->fp32 ? sizeof(float) : sizeof(double);
+    dba::BlockInfo* d_blocks = nullptr;
+    int *d_pc_obs = nullptr, *d_pc_pt = nullptr, *d_cc_cam = nullptr, *d_obs_pt = nullptr, *d_obs_cam = nullptr;
+    int *d_pt_off = nullptr, *d_pt_cp = nullptr, *d_cam_off = nullptr, *d_cam_cp = nullptr;
+    unsigned char* d_lc = nullptr;
+    BLK_CUDA(upload(ctx, &d_blocks, blocks), "upload");
+    BLK_CUDA(upload(ctx, &d_pc_obs, pc_obs), "upload");
+    BLK_CUDA(upload(ctx, &d_pc_pt, pc_pt), "upload");
+    BLK_CUDA(upload(ctx, &d_cc_cam, cc_cam), "upload");
+    BLK_CUDA(upload(ctx, &d_obs_pt, obs_pt), "upload");
+    BLK_CUDA(upload(ctx, &d_obs_cam, obs_cam), "upload");
+    BLK_CUDA(upload(ctx, &d_lc, obs_lc), "upload");
+    BLK_CUDA(upload(ctx, &d_pt_off, pt_off), "upload");
+    BLK_CUDA(upload(ctx, &d_pt_cp, pt_cp), "upload");
+    BLK_CUDA(upload(ctx, &d_cam_off, cam_off), "upload");
+    BLK_CUDA(upload(ctx, &d_cam_cp, cam_cp), "upload");
+    B.blocks = d_blocks;
+    B.pc_obs = d_pc_obs;
+    B.pc_pt = d_pc_pt;
+    B.cc_cam = d_cc_cam;
+    B.obs_pt = d_obs_pt;
+    B.obs_cam = d_obs_cam;
+    B.obs_lc = d_lc;
+    B.pt_cp_off = d_pt_off;
+    B.pt_cp = d_pt_cp;
+    B.cam_cp_off = d_cam_off;
+    B.cam_cp = d_cam_cp;
+    // pixels in block order, in the working precision
+    {
+      std::vector<double> zb(2 * l);
+      for (long long t = 0; t < l; ++t) {
+        zb[2 * t] = z[2 * idx[t]];
+        zb[2 * t + 1] = z[2 * idx[t] + 1];
+      }
+      void* d_z = nullptr;
+      BLK_CUDA(ctx->alloc(&d_z, tsz * 2 * l), "alloc");
+      if (ctx->fp32) {
+        std::vector<float> zf(zb.begin(), zb.end());
+        BLK_CUDA(cudaMemcpyAsync(d_z, zf.data(), sizeof(float) * zf.size(), cudaMemcpyHostToDevice, ctx->stream),
+                 "upload");
+        BLK_CUDA(cudaStreamSynchronize(ctx->stream), "upload");
+      } else {
+        BLK_CUDA(cudaMemcpyAsync(d_z, zb.data(), sizeof(double) * zb.size(), cudaMemcpyHostToDevice, ctx->stream),
+                 "upload");
+        BLK_CUDA(cudaStreamSynchronize(ctx->stream), "upload");
+      }
+      B.z = d_z;
+    }
+    // state: copies at the consensus (offsets 0), duals 0
+    void *d_pdel = nullptr, *d_cdel = nullptr;
+    BLK_CUDA(ctx->alloc(&d_pdel, tsz * 3 * n_pc), "alloc");
+    BLK_CUDA(ctx->alloc(&d_cdel, tsz * 6 * n_cc), "alloc");
+    BLK_CUDA(ctx->alloc(&B.pc_a, sizeof(double) * 3 * n_pc), "alloc");
+    BLK_CUDA(ctx->alloc(&B.cc_a, sizeof(double) * 6 * n_cc), "alloc");
+    BLK_CUDA(cudaMemsetAsync(d_pdel, 0, tsz * 3 * n_pc, ctx->stream), "init");
+    BLK_CUDA(cudaMemsetAsync(d_cdel, 0, tsz * 6 * n_cc, ctx->stream), "init");
+    BLK_CUDA(cudaMemsetAsync(B.pc_a, 0, sizeof(double) * 3 * n_pc, ctx->stream), "init");
+    BLK_CUDA(cudaMemsetAsync(B.cc_a, 0, sizeof(double) * 6 * n_cc, ctx->stream), "init");
+    B.pc_delta = d_pdel;
+    B.cc_delta = d_cdel;
+    for (int k = 0; k < 2; ++k) {
+      BLK_CUDA(ctx->alloc(&B.X[k], sizeof(double) * 3 * n), "alloc");
+      BLK_CUDA(ctx->alloc(&B.Y[k], sizeof(double) * 6 * m), "alloc");
+    }
+    BLK_CUDA(cudaMemcpyAsync(B.X[0], pts0, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, ctx->stream), "upload");
+    BLK_CUDA(cudaMemcpyAsync(B.Y[0], cams0, sizeof(double) * 6 * m, cudaMemcpyHostToDevice, ctx->stream), "upload");
+    BLK_CUDA(ctx->alloc(&B.sums, sizeof(double) * 8), "alloc");
+    BLK_CUDA(ctx->alloc(&B.err, sizeof(int)), "alloc");
+    BLK_CUDA(cudaMemsetAsync(B.err, 0, sizeof(int), ctx->stream), "init");
+    BLK_CUDA(cudaStreamSynchronize(ctx->stream), "upload");
+    ctx->cur = 0;
+    ctx->iters = 0;
+    ctx->has_problem = true;
+    return DBA_OK;
   });
 }
 
 dba_status dba_block_set_reference_pixels(dba_block_ctx* ctx, const double* z_ref, const uint8_t* inlier) {
   return dba::guarded(ctx ? &ctx->err : nullptr, [&]() -> dba_status {
-  if (!ctx) return DBA_EINVAL;
-  if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_block_set_reference_pixels before set_observations");
-  if (!z_ref) return ctx->fail(DBA_EINVAL, "dba_block_set_reference_pixels: null array");
-  const long long l = ctx->B.n_obs;
-  std::vector<double> zb(2 * l);
-  std::vector<unsigned char> mb(l, 1);
-  for (long long t = 0; t < l; ++t) {
-    const long long o = ctx->blk_obs[t];
-    zb[2 * t] = z_ref[2 * o];
-    zb[2 * t + 1] = z_ref[2 * o + 1];
-    if (!std::isfinite(zb[2 * t]) || !std::isfinite(zb[2 * t + 1]))
-      return ctx->fail(DBA_EINVAL, "dba_block_set_reference_pixels: non-finite pixel");
-    if (inlier) mb[t] = inlier[o] ? 1 : 0;
-  }
-  double* d_zt = nullptr;
-  unsigned char* d_in = nullptr;
-  BLK_CUDA(upload(ctx, &d_zt, zb), "upload");
-  BLK_CUDA(upload(ctx, &d_in, mb), "upload");
-  BLK_CUDA(cudaStreamSynchronize(ctx->stream), "upload");
-  ctx->B.zt = d_zt;
-  ctx->B.inlier = d_in;
-  return DBA_OK;
+    if (!ctx) return DBA_EINVAL;
+    if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_block_set_reference_pixels before set_observations");
+    if (!z_ref) return ctx->fail(DBA_EINVAL, "dba_block_set_reference_pixels: null array");
+    const long long l = ctx->B.n_obs;
+    std::vector<double> zb(2 * l);
+    std::vector<unsigned char> mb(l, 1);
+    for (long long t = 0; t < l; ++t) {
+      const long long o = ctx->blk_obs[t];
+      zb[2 * t] = z_ref[2 * o];
+      zb[2 * t + 1] = z_ref[2 * o + 1];
+      if (!std::isfinite(zb[2 * t]) || !std::isfinite(zb[2 * t + 1]))
+        return ctx->fail(DBA_EINVAL, "dba_block_set_reference_pixels: non-finite pixel");
+      if (inlier) mb[t] = inlier[o] ? 1 : 0;
+    }
+    double* d_zt = nullptr;
+    unsigned char* d_in = nullptr;
+    BLK_CUDA(upload(ctx, &d_zt, zb), "upload");
+    BLK_CUDA(upload(ctx, &d_in, mb), "upload");
+    BLK_CUDA(cudaStreamSynchronize(ctx->stream), "upload");
+    ctx->B.zt = d_zt;
+    ctx->B.inlier = d_in;
+    return DBA_OK;
   });
 }
 
 dba_status dba_block_iterate(dba_block_ctx* ctx, int n_iters, dba_stats* stats) {
   return dba::guarded(ctx ? &ctx->err : nullptr, [&]() -> dba_status {
-  if (!ctx) return DBA_EINVAL;
-  if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_block_iterate before dba_block_set_observations");
-  if (n_iters < 0) return ctx->fail(DBA_EINVAL, "dba_block_iterate: n_iters < 0");
-  BLK_CUDA(cudaEventRecord(ctx->ev0, ctx->stream), "iterate");
-  for (int it = 0; it < n_iters; ++it) BLK_CUDA(launch_iteration(ctx, stats && it == n_iters - 1), "iterate");
-  BLK_CUDA(cudaEventRecord(ctx->ev1, ctx->stream), "iterate");
-  ctx->iters += n_iters;
-  int herr = 0;
-  BLK_CUDA(cudaMemcpyAsync(&herr, ctx->B.err, sizeof herr, cudaMemcpyDeviceToHost, ctx->stream), "iterate");
-  BLK_CUDA(cudaStreamSynchronize(ctx->stream), "iterate");
-  if (herr & 1) return ctx->fail(DBA_ENUMERIC, "a block solve produced a non-finite value");
-  if (stats) {
-    float ms = 0.f;
-    BLK_CUDA(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1), "iterate");
-    const dba_status s = read_stats(ctx, n_iters > 0, stats);
-    stats->seconds = 1e-3 * ms;
-    return s;
-  }
-  return DBA_OK;
+    if (!ctx) return DBA_EINVAL;
+    if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_block_iterate before dba_block_set_observations");
+    if (n_iters < 0) return ctx->fail(DBA_EINVAL, "dba_block_iterate: n_iters < 0");
+    BLK_CUDA(cudaEventRecord(ctx->ev0, ctx->stream), "iterate");
+    for (int it = 0; it < n_iters; ++it) BLK_CUDA(launch_iteration(ctx, stats && it == n_iters - 1), "iterate");
+    BLK_CUDA(cudaEventRecord(ctx->ev1, ctx->stream), "iterate");
+    ctx->iters += n_iters;
+    int herr = 0;
+    BLK_CUDA(cudaMemcpyAsync(&herr, ctx->B.err, sizeof herr, cudaMemcpyDeviceToHost, ctx->stream), "iterate");
+    BLK_CUDA(cudaStreamSynchronize(ctx->stream), "iterate");
+    if (herr & 1) return ctx->fail(DBA_ENUMERIC, "a block solve produced a non-finite value");
+    if (stats) {
+      float ms = 0.f;
+      BLK_CUDA(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1), "iterate");
+      const dba_status s = read_stats(ctx, n_iters > 0, stats);
+      stats->seconds = 1e-3 * ms;
+      return s;
+    }
+    return DBA_OK;
   });
 }
 
 dba_status dba_block_iterate_until(dba_block_ctx* ctx, int max_iters, double target_rmse_gt, dba_stats* stats) {
   return dba::guarded(ctx ? &ctx->err : nullptr, [&]() -> dba_status {
-  if (!ctx || !stats) return DBA_EINVAL;
-  if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_block_iterate_until before set_observations");
-  if (!ctx->B.zt) return ctx->fail(DBA_ESTATE, "dba_block_iterate_until needs reference pixels");
-  if (max_iters < 0 || !(target_rmse_gt > 0)) return ctx->fail(DBA_EINVAL, "dba_block_iterate_until: bad arguments");
-  double secs = 0.0;
-  for (int it = 0; it < max_iters; ++it) {
-    BLK_CUDA(cudaEventRecord(ctx->ev0, ctx->stream), "iterate_until");
-    BLK_CUDA(launch_iteration(ctx, true), "iterate_until");
-    ctx->iters += 1;
-    const dba_status s = read_stats(ctx, true, stats);
-    BLK_CUDA(cudaEventRecord(ctx->ev1, ctx->stream), "iterate_until");
-    BLK_CUDA(cudaEventSynchronize(ctx->ev1), "iterate_until");
-    float ms = 0.f;
-    BLK_CUDA(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1), "iterate_until");
-    secs += 1e-3 * ms;
-    if (s != DBA_OK) return s;
-    if (stats->rmse_gt <= target_rmse_gt) break;
-  }
-  stats->seconds = secs;
-  return DBA_OK;
+    if (!ctx || !stats) return DBA_EINVAL;
+    if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_block_iterate_until before set_observations");
+    if (!ctx->B.zt) return ctx->fail(DBA_ESTATE, "dba_block_iterate_until needs reference pixels");
+    if (max_iters < 0 || !(target_rmse_gt > 0)) return ctx->fail(DBA_EINVAL, "dba_block_iterate_until: bad arguments");
+    double secs = 0.0;
+    for (int it = 0; it < max_iters; ++it) {
+      BLK_CUDA(cudaEventRecord(ctx->ev0, ctx->stream), "iterate_until");
+      BLK_CUDA(launch_iteration(ctx, true), "iterate_until");
+      ctx->iters += 1;
+      const dba_status s = read_stats(ctx, true, stats);
+      BLK_CUDA(cudaEventRecord(ctx->ev1, ctx->stream), "iterate_until");
+      BLK_CUDA(cudaEventSynchronize(ctx->ev1), "iterate_until");
+      float ms = 0.f;
+      BLK_CUDA(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1), "iterate_until");
+      secs += 1e-3 * ms;
+      if (s != DBA_OK) return s;
+      if (stats->rmse_gt <= target_rmse_gt) break;
+    }
+    stats->seconds = secs;
+    return DBA_OK;
   });
 }
 
 dba_status dba_block_profile(dba_block_ctx* ctx, int n_iters, double* ms_out) {
   return dba::guarded(ctx ? &ctx->err : nullptr, [&]() -> dba_status {
-  if (!ctx || !ms_out) return DBA_EINVAL;
-  if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_block_profile before set_observations");
-  if (n_iters <= 0) return ctx->fail(DBA_EINVAL, "dba_block_profile: n_iters must be positive");
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-  cudaError_t e = cudaSuccess;
-  for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventCreate(&ev[k]);
-  double acc[3] = {0, 0, 0};
-  for (int it = 0; it < n_iters && e == cudaSuccess; ++it) {
-    e = launch_iteration(ctx, false, ev);
-    if (e == cudaSuccess) e = cudaEventSynchronize(ev[3]);
-    for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
-      float ms = 0.f;
-      e = cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
-      acc[k] += ms;
+    if (!ctx || !ms_out) return DBA_EINVAL;
+    if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_block_profile before set_observations");
+    if (n_iters <= 0) return ctx->fail(DBA_EINVAL, "dba_block_profile: n_iters must be positive");
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventCreate(&ev[k]);
+    double acc[3] = {0, 0, 0};
+    for (int it = 0; it < n_iters && e == cudaSuccess; ++it) {
+      e = launch_iteration(ctx, false, ev);
+      if (e == cudaSuccess) e = cudaEventSynchronize(ev[3]);
+      for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+        float ms = 0.f;
+        e = cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+        acc[k] += ms;
+      }
+      ctx->iters += 1;
     }
-    ctx->iters += 1;
-  }
-  for (int k = 0; k < 4; ++k)
-    if (ev[k]) cudaEventDestroy(ev[k]);
-  if (e != cudaSuccess) return ctx->cuda_fail(e, "dba_block_profile");
-  for (int k = 0; k < 3; ++k) ms_out[k] = acc[k] / n_iters;
-  return DBA_OK;
+    for (int k = 0; k < 4; ++k)
+      if (ev[k]) cudaEventDestroy(ev[k]);
+    if (e != cudaSuccess) return ctx->cuda_fail(e, "dba_block_profile");
+    for (int k = 0; k < 3; ++k) ms_out[k] = acc[k] / n_iters;
+    return DBA_OK;
   });
 }
 
 dba_status dba_block_get_params(dba_block_ctx* ctx, double* cams_out, double* pts_out) {
   return dba::guarded(ctx ? &ctx->err : nullptr, [&]() -> dba_status {
-  if (!ctx) return DBA_EINVAL;
-  if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_block_get_params before set_observations");
-  if (!cams_out || !pts_out) return ctx->fail(DBA_EINVAL, "dba_block_get_params: null array");
-  BLK_CUDA(cudaMemcpyAsync(cams_out, ctx->B.Y[ctx->cur], sizeof(double) * 6 * ctx->B.n_cams, cudaMemcpyDeviceToHost,
-                           ctx->stream),
-           "get_params");
-  BLK_CUDA(cudaMemcpyAsync(pts_out, ctx->B.X[ctx->cur], sizeof(double) * 3 * ctx->B.n_pts, cudaMemcpyDeviceToHost,
-                           ctx->stream),
-           "get_params");
-  BLK_CUDA(cudaStreamSynchronize(ctx->stream), "get_params");
-  return DBA_OK;
+    if (!ctx) return DBA_EINVAL;
+    if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_block_get_params before set_observations");
+    if (!cams_out || !pts_out) return ctx->fail(DBA_EINVAL, "dba_block_get_params: null array");
+    BLK_CUDA(cudaMemcpyAsync(cams_out, ctx->B.Y[ctx->cur], sizeof(double) * 6 * ctx->B.n_cams, cudaMemcpyDeviceToHost,
+                             ctx->stream),
+             "get_params");
+    BLK_CUDA(cudaMemcpyAsync(pts_out, ctx->B.X[ctx->cur], sizeof(double) * 3 * ctx->B.n_pts, cudaMemcpyDeviceToHost,
+                             ctx->stream),
+             "get_params");
+    BLK_CUDA(cudaStreamSynchronize(ctx->stream), "get_params");
+    return DBA_OK;
   });
 }
 

@@ -794,126 +794,126 @@ dba_status dba_mlp_set_params(dba_mlp* m, const float* host) {
 
 dba_status dba_mlp_fit_normalizer(dba_mlp* m, const float* feats, const float* targets, int64_t n) {
   return dba::guarded(m ? &m->err : nullptr, [&]() -> dba_status {
-  if (!m || !feats || !targets || n <= 1) return DBA_EINVAL;
-  double* acc = nullptr;
-  const int cols = dba::kMlpIn + dba::kMlpOut;
-  MLP_CUDA(cudaMalloc(&acc, sizeof(double) * 2 * cols), "normalizer");
-  dba::moments_kernel<<<cols, 256, 0, m->stream>>>(feats, targets, n, acc);
-  std::vector<double> h(2 * cols);
-  cudaError_t e = cudaMemcpyAsync(h.data(), acc, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, m->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
-  cudaFree(acc);
-  if (e != cudaSuccess) return mlp_fail(m, e, "normalizer");
-  std::vector<float> stats(dba::kNParams - dba::kTrainable);
-  for (int c = 0; c < cols; ++c) {
-    const double mean = h[2 * c] / (double)n;
-    const double var = std::max(h[2 * c + 1] / (double)n - mean * mean, 0.0);
-    double sd = std::sqrt(var);
-    if (!(sd > 1e-12)) sd = 1.0;
-    if (c < dba::kMlpIn) {
-      stats[c] = (float)mean;
-      stats[dba::kMlpIn + c] = (float)sd;
-    } else {
-      // targets: scaled by their root mean square (a zero-mean scale keeps "no step" at 0)
-      const double rms = std::sqrt(h[2 * c + 1] / (double)n);
-      stats[2 * dba::kMlpIn + (c - dba::kMlpIn)] = (float)(rms > 1e-12 ? rms : 1.0);
+    if (!m || !feats || !targets || n <= 1) return DBA_EINVAL;
+    double* acc = nullptr;
+    const int cols = dba::kMlpIn + dba::kMlpOut;
+    MLP_CUDA(cudaMalloc(&acc, sizeof(double) * 2 * cols), "normalizer");
+    dba::moments_kernel<<<cols, 256, 0, m->stream>>>(feats, targets, n, acc);
+    std::vector<double> h(2 * cols);
+    cudaError_t e = cudaMemcpyAsync(h.data(), acc, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, m->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    cudaFree(acc);
+    if (e != cudaSuccess) return mlp_fail(m, e, "normalizer");
+    std::vector<float> stats(dba::kNParams - dba::kTrainable);
+    for (int c = 0; c < cols; ++c) {
+      const double mean = h[2 * c] / (double)n;
+      const double var = std::max(h[2 * c + 1] / (double)n - mean * mean, 0.0);
+      double sd = std::sqrt(var);
+      if (!(sd > 1e-12)) sd = 1.0;
+      if (c < dba::kMlpIn) {
+        stats[c] = (float)mean;
+        stats[dba::kMlpIn + c] = (float)sd;
+      } else {
+        // targets: scaled by their root mean square (a zero-mean scale keeps "no step" at 0)
+        const double rms = std::sqrt(h[2 * c + 1] / (double)n);
+        stats[2 * dba::kMlpIn + (c - dba::kMlpIn)] = (float)(rms > 1e-12 ? rms : 1.0);
+      }
     }
-  }
-  MLP_CUDA(cudaMemcpy(m->params + dba::kTrainable, stats.data(), sizeof(float) * stats.size(), cudaMemcpyHostToDevice),
-           "normalizer");
-  return DBA_OK;
+    MLP_CUDA(cudaMemcpy(m->params + dba::kTrainable, stats.data(), sizeof(float) * stats.size(), cudaMemcpyHostToDevice),
+             "normalizer");
+    return DBA_OK;
   });
 }
 
 dba_status dba_mlp_loss_grad(dba_mlp* m, const float* feats, const float* targets, int64_t n, double* loss,
                              float* grad) {
   return dba::guarded(m ? &m->err : nullptr, [&]() -> dba_status {
-  if (!m || !feats || !targets || n <= 0 || n > (1 << 26)) return DBA_EINVAL;
-  MLP_CUDA(dba::mlp_reserve(m, (int)n), "loss_grad");
-  const int b = dba::blocks_for(n * dba::kMlpIn, 256);
-  dba::gather_standardize_kernel<<<b, 256, 0, m->stream>>>(feats, nullptr, (int)n, m->params, m->x);
-  dba::gather_targets_kernel<<<dba::blocks_for(n * dba::kMlpOut, 256), 256, 0, m->stream>>>(targets, nullptr, (int)n,
-                                                                                            m->params, m->t);
-  MLP_CUDA(dba::mlp_forward_backward(m, (int)n), "loss_grad");
-  double h = 0.0;
-  MLP_CUDA(cudaMemcpyAsync(&h, m->dloss, sizeof h, cudaMemcpyDeviceToHost, m->stream), "loss_grad");
-  if (grad) MLP_CUDA(cudaMemcpyAsync(grad, m->grad, sizeof(float) * dba::kNParams, cudaMemcpyDeviceToHost, m->stream),
-                     "loss_grad");
-  MLP_CUDA(cudaStreamSynchronize(m->stream), "loss_grad");
-  if (loss) *loss = h;
-  return DBA_OK;
+    if (!m || !feats || !targets || n <= 0 || n > (1 << 26)) return DBA_EINVAL;
+    MLP_CUDA(dba::mlp_reserve(m, (int)n), "loss_grad");
+    const int b = dba::blocks_for(n * dba::kMlpIn, 256);
+    dba::gather_standardize_kernel<<<b, 256, 0, m->stream>>>(feats, nullptr, (int)n, m->params, m->x);
+    dba::gather_targets_kernel<<<dba::blocks_for(n * dba::kMlpOut, 256), 256, 0, m->stream>>>(targets, nullptr, (int)n,
+                                                                                              m->params, m->t);
+    MLP_CUDA(dba::mlp_forward_backward(m, (int)n), "loss_grad");
+    double h = 0.0;
+    MLP_CUDA(cudaMemcpyAsync(&h, m->dloss, sizeof h, cudaMemcpyDeviceToHost, m->stream), "loss_grad");
+    if (grad) MLP_CUDA(cudaMemcpyAsync(grad, m->grad, sizeof(float) * dba::kNParams, cudaMemcpyDeviceToHost, m->stream),
+                       "loss_grad");
+    MLP_CUDA(cudaStreamSynchronize(m->stream), "loss_grad");
+    if (loss) *loss = h;
+    return DBA_OK;
   });
 }
 
 dba_status dba_mlp_train(dba_mlp* m, const float* feats, const float* targets, int64_t n, int epochs, int batch,
                          float lr, uint64_t seed, double* last_loss) {
   return dba::guarded(m ? &m->err : nullptr, [&]() -> dba_status {
-  if (!m || !feats || !targets || n <= 0 || epochs < 0 || batch <= 0 || !(lr > 0)) return DBA_EINVAL;
-  MLP_CUDA(dba::mlp_reserve(m, batch), "train");
-  int* perm_dev = nullptr;
-  MLP_CUDA(cudaMalloc(&perm_dev, sizeof(int) * (size_t)n), "train");
-  std::vector<int> perm(n);
-  for (int64_t k = 0; k < n; ++k) perm[k] = (int)k;
-  std::mt19937_64 rng(seed);
-  double epoch_loss = 0.0;
-  cudaError_t e = cudaSuccess;
-  for (int ep = 0; ep < epochs && e == cudaSuccess; ++ep) {
-    std::shuffle(perm.begin(), perm.end(), rng);
-    e = cudaMemcpyAsync(perm_dev, perm.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice, m->stream);
-    double sum = 0.0;
-    int nb = 0;
-    for (int64_t s0 = 0; s0 + batch <= n && e == cudaSuccess; s0 += batch, ++nb) {
-      dba::gather_standardize_kernel<<<dba::blocks_for((long long)batch * dba::kMlpIn, 256), 256, 0, m->stream>>>(
-          feats, perm_dev + s0, batch, m->params, m->x);
-      dba::gather_targets_kernel<<<dba::blocks_for((long long)batch * dba::kMlpOut, 256), 256, 0, m->stream>>>(
-          targets, perm_dev + s0, batch, m->params, m->t);
-      e = dba::mlp_forward_backward(m, batch);
-      if (e != cudaSuccess) break;
-      m->adam_t += 1;
-      const float c1 = 1.f - std::pow(0.9f, (float)m->adam_t), c2 = 1.f - std::pow(0.999f, (float)m->adam_t);
-      dba::adam_kernel<<<dba::blocks_for(dba::kTrainable, 256), 256, 0, m->stream>>>(
-          m->params, m->grad, m->adam_m, m->adam_v, dba::kTrainable, lr, 0.9f, 0.999f, c1, c2);
-      double h = 0.0;
-      e = cudaMemcpyAsync(&h, m->dloss, sizeof h, cudaMemcpyDeviceToHost, m->stream);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
-      sum += h;
+    if (!m || !feats || !targets || n <= 0 || epochs < 0 || batch <= 0 || !(lr > 0)) return DBA_EINVAL;
+    MLP_CUDA(dba::mlp_reserve(m, batch), "train");
+    int* perm_dev = nullptr;
+    MLP_CUDA(cudaMalloc(&perm_dev, sizeof(int) * (size_t)n), "train");
+    std::vector<int> perm(n);
+    for (int64_t k = 0; k < n; ++k) perm[k] = (int)k;
+    std::mt19937_64 rng(seed);
+    double epoch_loss = 0.0;
+    cudaError_t e = cudaSuccess;
+    for (int ep = 0; ep < epochs && e == cudaSuccess; ++ep) {
+      std::shuffle(perm.begin(), perm.end(), rng);
+      e = cudaMemcpyAsync(perm_dev, perm.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice, m->stream);
+      double sum = 0.0;
+      int nb = 0;
+      for (int64_t s0 = 0; s0 + batch <= n && e == cudaSuccess; s0 += batch, ++nb) {
+        dba::gather_standardize_kernel<<<dba::blocks_for((long long)batch * dba::kMlpIn, 256), 256, 0, m->stream>>>(
+            feats, perm_dev + s0, batch, m->params, m->x);
+        dba::gather_targets_kernel<<<dba::blocks_for((long long)batch * dba::kMlpOut, 256), 256, 0, m->stream>>>(
+            targets, perm_dev + s0, batch, m->params, m->t);
+        e = dba::mlp_forward_backward(m, batch);
+        if (e != cudaSuccess) break;
+        m->adam_t += 1;
+        const float c1 = 1.f - std::pow(0.9f, (float)m->adam_t), c2 = 1.f - std::pow(0.999f, (float)m->adam_t);
+        dba::adam_kernel<<<dba::blocks_for(dba::kTrainable, 256), 256, 0, m->stream>>>(
+            m->params, m->grad, m->adam_m, m->adam_v, dba::kTrainable, lr, 0.9f, 0.999f, c1, c2);
+        double h = 0.0;
+        e = cudaMemcpyAsync(&h, m->dloss, sizeof h, cudaMemcpyDeviceToHost, m->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+        sum += h;
+      }
+      epoch_loss = nb ? sum / nb : 0.0;
     }
-    epoch_loss = nb ? sum / nb : 0.0;
-  }
-  cudaFree(perm_dev);
-  if (e != cudaSuccess) return mlp_fail(m, e, "train");
-  if (last_loss) *last_loss = epoch_loss;
-  return DBA_OK;
+    cudaFree(perm_dev);
+    if (e != cudaSuccess) return mlp_fail(m, e, "train");
+    if (last_loss) *last_loss = epoch_loss;
+    return DBA_OK;
   });
 }
 
 dba_status dba_mlp_predict(dba_mlp* m, const float* feats, int64_t n, float* out) {
   return dba::guarded(m ? &m->err : nullptr, [&]() -> dba_status {
-  if (!m || !feats || !out || n <= 0) return DBA_EINVAL;
-  std::vector<float> h(dba::kNParams);
-  MLP_CUDA(cudaMemcpy(h.data(), m->params, sizeof(float) * h.size(), cudaMemcpyDeviceToHost), "predict");
-  std::vector<unsigned char> blob;
-  dba::mlp_make_blob(h.data(), blob);
-  unsigned char* dblob = nullptr;
-  int* derr = nullptr;
-  MLP_CUDA(cudaMalloc(&dblob, blob.size()), "predict");
-  MLP_CUDA(cudaMalloc(&derr, sizeof(int)), "predict");
-  cudaError_t e = cudaMemcpyAsync(dblob, blob.data(), blob.size(), cudaMemcpyHostToDevice, m->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(derr, 0, sizeof(int), m->stream);
-  dba::DevProblem none{};
-  if (e == cudaSuccess)
-    e = dba::launch_infer<float, false>(none, dba::Params{}, dblob, m->params, feats, n, out, derr, m->stream);
-  int herr = 0;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, m->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
-  cudaFree(dblob);
-  cudaFree(derr);
-  if (e != cudaSuccess) return mlp_fail(m, e, "predict");
-  if (herr) {
-    m->err = "dba_mlp_predict: a tensor-core wait timed out";
-    return DBA_ETIMEOUT;
-  }
-  return DBA_OK;
+    if (!m || !feats || !out || n <= 0) return DBA_EINVAL;
+    std::vector<float> h(dba::kNParams);
+    MLP_CUDA(cudaMemcpy(h.data(), m->params, sizeof(float) * h.size(), cudaMemcpyDeviceToHost), "predict");
+    std::vector<unsigned char> blob;
+    dba::mlp_make_blob(h.data(), blob);
+    unsigned char* dblob = nullptr;
+    int* derr = nullptr;
+    MLP_CUDA(cudaMalloc(&dblob, blob.size()), "predict");
+    MLP_CUDA(cudaMalloc(&derr, sizeof(int)), "predict");
+    cudaError_t e = cudaMemcpyAsync(dblob, blob.data(), blob.size(), cudaMemcpyHostToDevice, m->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(derr, 0, sizeof(int), m->stream);
+    dba::DevProblem none{};
+    if (e == cudaSuccess)
+      e = dba::launch_infer<float, false>(none, dba::Params{}, dblob, m->params, feats, n, out, derr, m->stream);
+    int herr = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, derr, sizeof(int), cudaMemcpyDeviceToHost, m->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(m->stream);
+    cudaFree(dblob);
+    cudaFree(derr);
+    if (e != cudaSuccess) return mlp_fail(m, e, "predict");
+    if (herr) {
+      m->err = "dba_mlp_predict: a tensor-core wait timed out";
+      return DBA_ETIMEOUT;
+    }
+    return DBA_OK;
   });
 }
 
