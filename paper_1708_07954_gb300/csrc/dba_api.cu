@@ -19,6 +19,7 @@
 
 #include "../../include/dba.h"
 #include "dba_internal.h"
+#include "dba_guard.h"
 
 using dba::DevCtl;
 using dba::DevProblem;

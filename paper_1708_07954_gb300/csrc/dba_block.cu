@@ -29,6 +29,7 @@
 #include "../../include/dba.h"
 #include "dba_device.cuh"
 #include "dba_internal.h"
+#include "dba_guard.h"
 
 namespace dba {
 namespace {

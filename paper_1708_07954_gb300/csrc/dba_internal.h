@@ -138,28 +138,7 @@ cudaError_t launch_eval_noalloc(const Params& prm, long long n_obs, int n_cams, 
 
 }  // namespace dba
 
-#include <exception>
-#include <new>
-#include <string>
 #include <vector>
-
-#include "../../include/dba.h"
-
 namespace dba {
 void mlp_make_blob(const float* params, std::vector<unsigned char>& blob);
-
-// Runs an entry point's body so that no C++ exception crosses the C ABI: a failed host
-// allocation (or another exhausted host resource, such as a thread that cannot start)
-// becomes DBA_ENOMEM with a message in *err (when err is not null).
-template <typename F>
-dba_status guarded(std::string* err, F&& body) {
-  try {
-    return body();
-  } catch (const std::bad_alloc&) {
-    if (err) try { *err = "out of host memory"; } catch (...) {}
-  } catch (const std::exception& e) {
-    if (err) try { *err = std::string("host resources exhausted: ") + e.what(); } catch (...) {}
-  }
-  return DBA_ENOMEM;
-}
 }  // namespace dba
