@@ -86,3 +86,17 @@ def test_block_path_takes_only_the_gauss_newton_solver(lib):
     cfg = dba.dba_config_default(local_solver=dba.DBA_SOLVER_LBFGS)
     ctx = ctypes.c_void_p()
     assert lib.dba_block_create(ctypes.byref(cfg), 8, 2, ctypes.byref(ctx)) == dba.DBA_EINVAL
+
+
+def test_binding_constants_match_the_header():
+    """The numeric #defines and enum values of include/dba.h and the binding's constants agree."""
+    text = open(os.path.join(ROOT, "include", "dba.h")).read()
+    defines = {k: int(v) for k, v in re.findall(r"#define\s+(DBA_[A-Z_0-9]+)\s+(\d+)", text)}
+    defines.update({k: int(v) for k, v in re.findall(r"\b(DBA_[A-Z_0-9]+)\s*=\s*(-?\d+)", text)})
+    assert defines, "no numeric defines found"
+    for name, value in defines.items():
+        if hasattr(dba, name):
+            assert getattr(dba, name) == value, name
+    for name in ("DBA_BLOCK_MAX_POINTS", "DBA_BLOCK_MAX_CAMERAS", "DBA_BLOCK_SIZE_CLASSES", "DBA_MLP_N_PARAMS",
+                 "DBA_ETIMEOUT", "DBA_SOLVER_LBFGS", "DBA_PREC_F32_LOCAL", "DBA_LOSS_STUDENT_T"):
+        assert name in defines and hasattr(dba, name), name
