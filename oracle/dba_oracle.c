@@ -8,6 +8,17 @@
  */
 #include "dba_oracle.h"
 
+/* Levenberg damping factors: lambda is divided by ORA_LM_DECREASE after an accepted step
+ * and multiplied by ORA_LM_INCREASE after a rejected one (the textbook factor 10).  They
+ * are macros only so that the tests can build deliberately wrong oracles and check that
+ * the step-wise pins reject them; the product path never builds this file. */
+#ifndef ORA_LM_DECREASE
+#define ORA_LM_DECREASE 10.0
+#endif
+#ifndef ORA_LM_INCREASE
+#define ORA_LM_INCREASE 10.0
+#endif
+
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -220,8 +231,8 @@ int ora_chol_solve(int n, const double* A, const double* b, double* x) {
  * lambda starts at lm_lambda0 * mean(diag H) at the first step.  A linearisation
  * point behind the camera contributes no misfit term (the proximal step).  A
  * step whose predicted decrease is below the objective's rounding noise is
- * accepted without the comparison (lm_model_tol) and the objective is then
- * carried as its model value.
+ * accepted without the comparison (lm_model_tol); like every accepted step it
+ * then re-evaluates Eq. (9) at the new point.
  */
 void ora_local_solve(const ora_config* c, const double z[2], const double xbar[3],
                      const double ybar[6], const double dual[9], double v[9]) {
@@ -254,7 +265,7 @@ void ora_local_solve(const ora_config* c, const double z[2], const double xbar[3
       neg_g[a] = -g[a];
     }
     if (ora_chol_solve(9, H, neg_g, d) != 0) {
-      lambda *= 10.0;
+      lambda *= ORA_LM_INCREASE;
       continue;
     }
     /* Decrease of the Gauss-Newton model -g.d - d^T H d / 2 (undamped H); since
@@ -267,8 +278,7 @@ void ora_local_solve(const ora_config* c, const double z[2], const double xbar[3
     double pred = 0.5 * (lambda * dd - gd);
     /* Below the rounding noise of the objective (residuals carry ~u |z| each), comparing
        objective values cannot tell a better point from a worse one, so the model's step
-       is trusted: accepted if the trial point is in front of the camera, and the objective
-       is carried as L - pred. */
+       is trusted: accepted if the trial point is in front of the camera. */
     int trust = 0;
     if (isfinite(L_old) && c->lm_model_tol > 0.0) {
       double noise = c->lm_model_tol * 0x1p-53 *
@@ -276,24 +286,13 @@ void ora_local_solve(const ora_config* c, const double z[2], const double xbar[3
       trust = pred <= noise;
     }
     for (int a = 0; a < 9; ++a) vt[a] = v[a] + d[a];
-    if (trust) {
-      double zp_t[2];
-      if (ora_project(c, vt, vt + 3, zp_t) > c->eps_depth) {
-        memcpy(v, vt, sizeof vt);
-        L_old -= pred;
-        lambda = fmax(lambda / 10.0, c->lm_lambda_min);
-      } else {
-        lambda *= 10.0;
-      }
-      continue;
-    }
-    double L_new = ora_local_objective(c, z, xbar, ybar, dual, vt);
-    if (L_new < L_old) {
+    double L_new = ora_local_objective(c, z, xbar, ybar, dual, vt); /* +inf behind the camera */
+    if (isfinite(L_new) && (trust || L_new < L_old)) {
       memcpy(v, vt, sizeof vt);
       L_old = L_new;
-      lambda = fmax(lambda / 10.0, c->lm_lambda_min);
+      lambda = fmax(lambda / ORA_LM_DECREASE, c->lm_lambda_min);
     } else {
-      lambda *= 10.0;
+      lambda *= ORA_LM_INCREASE;
     }
   }
 }
@@ -739,7 +738,7 @@ void ora_block_solve(const ora_config* c, int np, int nc, int no, const int* opl
       neg_g[u] = -g[u];
     }
     if (ora_chol_solve(n, H, neg_g, d) != 0) {
-      lambda *= 10.0;
+      lambda *= ORA_LM_INCREASE;
       continue;
     }
     double gd = 0.0, dd = 0.0;
@@ -753,30 +752,15 @@ void ora_block_solve(const ora_config* c, int np, int nc, int no, const int* opl
       trust = pred <= c->lm_model_tol * 0x1p-53 * (fabs(L_old) + noise_terms);
     for (int u = 0; u < 3 * np; ++u) Xt[u] = X[u] + d[u];
     for (int u = 0; u < 6 * nc; ++u) Yt[u] = Y[u] + d[3 * np + u];
-    if (trust) {
-      int valid = 1;
-      for (int k = 0; k < no && valid; ++k) {
-        double zp[2];
-        valid = ora_project(c, Xt + 3 * opl[k], Yt + 6 * ocl[k], zp) > c->eps_depth;
-      }
-      if (valid) {
-        memcpy(X, Xt, (size_t)3 * np * sizeof(double));
-        memcpy(Y, Yt, (size_t)6 * nc * sizeof(double));
-        L_old -= pred;
-        lambda = fmax(lambda / 10.0, c->lm_lambda_min);
-      } else {
-        lambda *= 10.0;
-      }
-      continue;
-    }
+    /* +inf when an observation of the block is behind its camera */
     double L_new = ora_block_objective(c, np, nc, no, opl, ocl, z, xbar, ybar, rx, sy, Xt, Yt);
-    if (L_new < L_old) {
+    if (isfinite(L_new) && (trust || L_new < L_old)) {
       memcpy(X, Xt, (size_t)3 * np * sizeof(double));
       memcpy(Y, Yt, (size_t)6 * nc * sizeof(double));
       L_old = L_new;
-      lambda = fmax(lambda / 10.0, c->lm_lambda_min);
+      lambda = fmax(lambda / ORA_LM_DECREASE, c->lm_lambda_min);
     } else {
-      lambda *= 10.0;
+      lambda *= ORA_LM_INCREASE;
     }
   }
   free(H); free(g); free(neg_g); free(d); free(Xt); free(Yt);

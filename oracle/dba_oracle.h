@@ -46,8 +46,17 @@ typedef struct {
 } ora_config;
 
 enum { ORA_SOLVER_GN = 0, ORA_SOLVER_LBFGS = 1 };
-enum { ORA_LBFGS_MEMORY = 4, ORA_LBFGS_HALVINGS = 10 };
+/* L-BFGS constants; macros only so that the tests can build deliberately wrong oracles
+ * and check that the step-wise pins reject them. */
+#ifndef ORA_LBFGS_MEMORY
+#define ORA_LBFGS_MEMORY 4
+#endif
+#ifndef ORA_LBFGS_HALVINGS
+#define ORA_LBFGS_HALVINGS 10
+#endif
+#ifndef ORA_LBFGS_ARMIJO
 #define ORA_LBFGS_ARMIJO 1e-4
+#endif
 
 typedef struct {
   double rmse_obs;   /* sqrt(mean |z - f(x_i, y_j)|^2) at consensus */

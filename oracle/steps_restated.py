@@ -1,0 +1,234 @@
+"""Second, independent statement of the two local solvers of Eq. (9), step by step.
+
+TEST INFRASTRUCTURE ONLY: used by ``tests/golden/make_local_steps.py`` to write the
+step-wise golden vectors that pin ``ora_local_solve`` and ``ora_local_solve_lbfgs``
+over a fixed number of steps.  It shares no code with ``dba_oracle.c`` and reaches
+each quantity by another route:
+
+- rotation (Sec. 2.1): built here as R3(gamma) R2(beta) R1(alpha) from the textbook
+  single-axis matrices and checked against scipy's extrinsic "xyz" Euler angles;
+- Jacobian of the pixel model (Eq. 1) and gradient of Eq. (9): complex-step
+  differentiation (Squire and Trapp, SIAM Review 40, 1998), exact to rounding, instead
+  of the oracle's chain rule;
+- the damped Gauss-Newton system: numpy's LU solve instead of a Cholesky factorisation;
+- L-BFGS (Nocedal and Wright, Numerical Optimization, Ch. 7): the inverse-Hessian
+  approximation formed as a dense matrix by the BFGS product update
+  H <- (I - rho s y^T) H (I - rho y s^T) + rho s s^T over the stored pairs, instead of
+  the two-loop recursion.
+
+The rules restated (the readings the oracle documents): Levenberg damping
+lambda_0 = lm_lambda0 * mean diag H at the first step, divided by 10 after an accepted
+step (clamped at lm_lambda_min) and multiplied by 10 after a rejected one; a step is
+accepted when the trial point is in front of the camera and lowers Eq. (9), or when its
+predicted decrease (lambda |d|^2 - g.d) / 2 is below kappa 2^-53 (|L| + 2 w |e| (|z1| + |z2|));
+a linearisation point behind the camera contributes no misfit term.  L-BFGS runs in
+u = sqrt(rho) (v - vbar), memory 4, H0 = (s.y / y.y) I (I before the first pair), steepest
+descent when -H g is not a descent direction, backtracking from t = 1 with at most 10
+halvings and Armijo constant 1e-4 (or the same rounding-noise rule on -t g.p), a pair kept
+only when s.y > 0, and a failed line search ends the solve.
+"""
+from __future__ import annotations
+
+import numpy as np
+from scipy.spatial.transform import Rotation
+
+L2, HUBER, STUDENT_T = 0, 1, 2
+U64 = 2.0 ** -53
+H_CS = 1e-30  # complex-step size
+
+
+def _rot(a, b, g):
+    ca, sa, cb, sb, cg, sg = np.cos(a), np.sin(a), np.cos(b), np.sin(b), np.cos(g), np.sin(g)
+    one, zero = ca ** 0, 0 * ca
+    R1 = np.array([[one, zero, zero], [zero, ca, -sa], [zero, sa, ca]])
+    R2 = np.array([[cb, zero, sb], [zero, one, zero], [-sb, zero, cb]])
+    R3 = np.array([[cg, -sg, zero], [sg, cg, zero], [zero, zero, one]])
+    return R3 @ R2 @ R1
+
+
+def check_rotation(y):
+    """The rotation above equals scipy's extrinsic x-y-z Euler angles (raises otherwise)."""
+    R = _rot(*np.asarray(y[:3], float))
+    Rs = Rotation.from_euler("xyz", np.asarray(y[:3], float)).as_matrix()
+    if np.abs(R - Rs).max() > 1e-14:
+        raise AssertionError("rotation convention mismatch")
+
+
+def pixel(cfg, v):
+    """z = f (R x + t)_{1,2} / (R x + t)_3 + (cx, cy) and the depth; v = (x, angles, t).
+    Works on complex v (for the complex step)."""
+    R = _rot(v[3], v[4], v[5])
+    q = R @ v[:3] + v[6:9]
+    return np.array([cfg["focal"] * q[0] / q[2] + cfg["cx"], cfg["focal"] * q[1] / q[2] + cfg["cy"]]), q[2]
+
+
+def rho_vec(cfg):
+    ra = cfg["rho_angle"] if cfg["rho_angle"] > 0 else cfg["rho_y"]
+    return np.array([cfg["rho_x"]] * 3 + [ra] * 3 + [cfg["rho_y"]] * 3)
+
+
+def misfit(cfg, s):
+    p = cfg["loss_param"]
+    if cfg["loss"] == HUBER:
+        return s if np.real(s) <= p * p else 2 * p * np.sqrt(s) - p * p
+    if cfg["loss"] == STUDENT_T:
+        return p * np.log(1 + s / p)
+    return s
+
+
+def weight(cfg, s):
+    """d misfit / d s, the IRLS weight."""
+    p = cfg["loss_param"]
+    if cfg["loss"] == HUBER:
+        return 1.0 if s <= p * p else p / np.sqrt(s)
+    if cfg["loss"] == STUDENT_T:
+        return p / (p + s)
+    return 1.0
+
+
+def objective(cfg, c, v):
+    """Eq. (9) at v: misfit + dual^T (v - vbar) + rho/2 |v - vbar|^2; +inf behind the camera."""
+    zp, depth = pixel(cfg, v)
+    if not np.real(depth) > cfg["eps_depth"]:
+        return np.inf
+    e = c["z"] - zp
+    dv = v - c["vbar"]
+    return misfit(cfg, e @ e) + c["dual"] @ dv + 0.5 * (rho_vec(cfg) * dv) @ dv
+
+
+def jacobian_cs(cfg, v):
+    J = np.zeros((2, 9))
+    for k in range(9):
+        vc = v.astype(complex)
+        vc[k] += 1j * H_CS
+        J[:, k] = np.imag(pixel(cfg, vc)[0]) / H_CS
+    return J
+
+
+def gradient_cs(cfg, c, v):
+    g = np.zeros(9)
+    for k in range(9):
+        vc = v.astype(complex)
+        vc[k] += 1j * H_CS
+        g[k] = np.imag(objective(cfg, c, vc)) / H_CS
+    return g
+
+
+def _linearise(cfg, c, v):
+    """Residual, weight, Jacobian at v; zero misfit terms behind the camera."""
+    zp, depth = pixel(cfg, v)
+    if not depth > cfg["eps_depth"]:
+        return np.zeros(2), 0.0, np.zeros((2, 9))
+    e = c["z"] - zp
+    return e, weight(cfg, e @ e), jacobian_cs(cfg, v)
+
+
+def gauss_newton(cfg, c, v0, steps):
+    """The damped Gauss-Newton (Levenberg) local solve; returns the iterates v_0..v_steps and
+    per step a code: 'A' accepted by comparison, 'T' accepted by the noise rule, 'R' rejected,
+    with the margins of every decision."""
+    rho = rho_vec(cfg)
+    v = np.array(v0, float)
+    L = objective(cfg, c, v)
+    lam = None
+    traj, codes, margins = [v.copy()], [], []
+    for _ in range(steps):
+        e, w, J = _linearise(cfg, c, v)
+        g = -2 * w * J.T @ e + c["dual"] + rho * (v - c["vbar"])
+        H = 2 * w * J.T @ J + np.diag(rho)
+        if lam is None:
+            lam = cfg["lm_lambda0"] * np.trace(H) / 9.0
+        d = np.linalg.solve(H + lam * np.eye(9), -g)
+        pred = 0.5 * (lam * d @ d - g @ d)
+        noise = cfg["lm_model_tol"] * U64 * (abs(L) + 2 * w * np.sqrt(e @ e) * (abs(c["z"][0]) + abs(c["z"][1])))
+        trust = np.isfinite(L) and cfg["lm_model_tol"] > 0 and pred <= noise
+        Lt = objective(cfg, c, v + d)
+        ok = np.isfinite(Lt) and (trust or Lt < L)
+        margins.append({"pred_over_noise": float(pred / noise) if noise > 0 else np.inf,
+                        "rel_change": float((Lt - L) / abs(L)) if np.isfinite(Lt) and np.isfinite(L) else np.inf})
+        if ok:
+            v = v + d
+            L = Lt
+            lam = max(lam / 10.0, cfg["lm_lambda_min"])
+            codes.append("T" if trust else "A")
+        else:
+            lam = lam * 10.0
+            codes.append("R")
+        traj.append(v.copy())
+    return traj, "".join(codes), margins
+
+
+def lbfgs(cfg, c, v0, iters, memory=4, halvings=10, armijo=1e-4):
+    """The L-BFGS local solve; returns the iterates, per iteration the number of line-search
+    trials ('-' once a line search failed and the solve ended), and per iteration the smallest
+    distance of its decisions from their thresholds (an Armijo comparison: relative to |L|; the
+    noise rule: 1e-9 times the decimal log of the ratio)."""
+    r = np.sqrt(rho_vec(cfg))
+    v = np.array(v0, float)
+    L = objective(cfg, c, v)
+
+    def grad_u(vv):
+        return gradient_cs(cfg, c, vv) / r
+
+    def noise_at(vv):
+        zp, depth = pixel(cfg, vv)
+        if not depth > cfg["eps_depth"]:
+            return 0.0
+        e = c["z"] - zp
+        return 2 * weight(cfg, e @ e) * np.sqrt(e @ e) * (abs(c["z"][0]) + abs(c["z"][1]))
+
+    gu, noise = grad_u(v), noise_at(v)
+    pairs = []
+    traj, trials = [v.copy()], []
+    margins = []  # per iteration: smallest relative distance of a line-search decision from its threshold
+    done = False
+    for _ in range(iters):
+        if done:
+            traj.append(v.copy())
+            trials.append("-")
+            continue
+        if pairs:
+            s_new, y_new = pairs[-1]
+            Hinv = (s_new @ y_new) / (y_new @ y_new) * np.eye(9)
+        else:
+            Hinv = np.eye(9)
+        for s, y in pairs:  # oldest to newest
+            p_ = 1.0 / (s @ y)
+            V = np.eye(9) - p_ * np.outer(y, s)
+            Hinv = V.T @ Hinv @ V + p_ * np.outer(s, s)
+        p = -Hinv @ gu
+        gp = gu @ p
+        if not gp < 0:
+            p = -gu
+            gp = -(gu @ gu)
+        t, accepted, n_trials, margin = 1.0, False, 0, np.inf
+        for _h in range(halvings + 1):
+            n_trials += 1
+            vt = v + t * p / r
+            Lt = objective(cfg, c, vt)
+            if np.isfinite(Lt):
+                tol = cfg["lm_model_tol"] * U64 * (abs(L) + noise)
+                trust = np.isfinite(L) and cfg["lm_model_tol"] > 0 and -t * gp <= tol
+                margin = min(margin, abs(Lt - (L + armijo * t * gp)) / abs(L))
+                if tol > 0:
+                    margin = min(margin, abs(np.log10(-t * gp / tol)) * 1e-9)
+                if trust or Lt <= L + armijo * t * gp:
+                    accepted = True
+                    break
+            t *= 0.5
+        margins.append(margin)
+        if not accepted:
+            done = True
+            traj.append(v.copy())
+            trials.append("-")
+            continue
+        gut = grad_u(vt)
+        s, y = t * p, gut - gu
+        if s @ y > 0:
+            pairs.append((s, y))
+            if len(pairs) > memory:
+                pairs.pop(0)
+        v, gu, L, noise = vt, gut, Lt, noise_at(vt)
+        traj.append(v.copy())
+        trials.append(str(n_trials))
+    return traj, trials, margins
