@@ -551,7 +551,7 @@ __device__ void solve_block(const BlockProblem& B, const Prm<T>& q, const BlockI
 #pragma unroll
         for (int u = 0; u < 3; ++u) dp[j][u] = xt[j][u];
       if (gl < n_u) Z.d[gl / 6][gl % 6] = Z.dt[gl / 6][gl % 6];
-      L = trust ? L - pred : Lt;
+      L = Lt;  // Eq. (14) at the accepted point, trusted step or not
       const T lr = Num<T>::tenth(lambda);
       lambda = lr > q.lambda_min ? lr : q.lambda_min;
     } else {

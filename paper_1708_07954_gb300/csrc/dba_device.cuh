@@ -186,8 +186,8 @@ __device__ __forceinline__ T local_objective(const T d[9], const T a[9], const P
 // 9x9 factorisation.  Accept/reject and the damping schedule follow the
 // Levenberg rule: accept iff the trial is in front of the camera and lowers
 // Eq. (9).  A step whose predicted decrease is below the objective's rounding
-// noise is accepted without the comparison (model_tol) and the objective is
-// carried as its model value.  d (offset from vbar) is updated in place.
+// noise is accepted without the comparison (model_tol).  d (offset from vbar)
+// is updated in place.
 // Linearisation of the pixel model at pose P: residual e = z - f(v), IRLS
 // weight w = phi'(|e|^2), and the 2x9 Jacobian rows J0, J1 (d p/d v columns:
 // x_k -> R[:,k]; alpha -> R[:,0] x u; beta -> (-sin g, cos g, 0) x u;
@@ -313,8 +313,8 @@ __device__ __forceinline__ void gn_step_f32(const float J0[9], const float J1[9]
 // 9x9 factorisation.  Accept/reject and the damping schedule follow the
 // Levenberg rule: accept iff the trial is in front of the camera and lowers
 // Eq. (9).  A step whose predicted decrease is below the objective's rounding
-// noise is accepted without the comparison (model_tol) and the objective is
-// carried as its model value.  d (offset from vbar) is updated in place.
+// noise is accepted without the comparison (model_tol); an accepted step keeps
+// Eq. (9) evaluated at its new point.  d (offset from vbar) is updated in place.
 // With kAlt, `alt` is a second candidate start (a learned warm start): the
 // solve starts from whichever of d and alt has the lower Eq. (9).
 template <typename T, bool kAlt = false>
@@ -413,13 +413,11 @@ __device__ __forceinline__ void local_solve(T z0, T z1, const T vbar[9], const T
     // the trial pose replaces the current one; a rejected step recomputes the kept copy's
     // pose (the same arithmetic on the same input, so bit-identical to the pose it had)
     pose_at(vt, q.eps, P);
-    // a trusted step carries the objective as its model value L - pred; the trial objective
-    // is evaluated only when a lane of the warp needs the comparison
-    T Lt = L - pred;
-    if (__any_sync(__activemask(), !trust)) {
-      const T Lo = local_objective(dt, a, P, z0, z1, q);
-      if (!trust) Lt = Lo;
-    }
+    // Eq. (9) at the trial point: compared with L, and kept as L once the step is accepted.
+    // Only a trusted last step needs neither (L is not read after the last step), so a warp
+    // whose lanes all trust their last step skips it.
+    T Lt = L;
+    if (__any_sync(__activemask(), !trust || step + 1 < q.steps)) Lt = local_objective(dt, a, P, z0, z1, q);
     const bool accept = P.valid && (trust || Lt < L);
     if (accept) {
 #pragma unroll
