@@ -111,8 +111,14 @@ typedef struct {
  * FP32 local solves, automatic tile size, graphs on, own stream, Gauss-Newton local solver. */
 void dba_config_default(dba_config* cfg);
 
-/* Creates a context on the current CUDA device.  Validates *cfg (EINVAL).
- * No device memory is allocated until dba_set_observations. */
+/* Creates a context on the current CUDA device for one problem of Sec. 2.2 solved by
+ * the consensus ADMM of Sec. 3.1: *cfg carries the known intrinsics of Eq. (1), the
+ * misfit phi_m of Eq. (2), the penalties rho of the augmented Lagrangian, Eq. (8), and
+ * how each local subproblem, Eq. (9), is solved.  *cfg is copied; *out receives the
+ * context (owned by the caller, freed by dba_destroy).  EINVAL for a null argument or an
+ * invalid configuration, ECUDA when no CUDA device is usable, ENOMEM when host memory
+ * runs out; the message is in dba_last_error(NULL).  No device memory is allocated
+ * until dba_set_observations. */
 dba_status dba_create(const dba_config* cfg, dba_ctx** out);
 
 /* Loads one problem (Sec. 2.2: unknowns 6m + 3n, one observation per listed
@@ -164,18 +170,28 @@ dba_status dba_iterate_until(dba_ctx* ctx, int max_iters, double target_rmse_gt,
 /* Metrics of the current state without iterating. */
 dba_status dba_evaluate(dba_ctx* ctx, dba_stats* stats);
 
-/* Copies the consensus estimate to cams [n_cams][6] and pts [n_pts][3]. */
+/* Copies the consensus estimate, the point and camera means of Eqs. (10)-(11) after
+ * the last iteration (Sec. 3.1), to cams [n_cams][6] and pts [n_pts][3] (caller-owned
+ * host arrays; a camera or point without observations keeps its input value).
+ * EINVAL for a null pointer, ESTATE before dba_set_observations. */
 dba_status dba_get_params(dba_ctx* ctx, double* cams, double* pts);
 
-/* Copies the per-observation copies [n_obs][9] and duals (r, s) [n_obs][9],
- * caller order.  Either pointer may be NULL. */
+/* Copies the ADMM state of Sec. 3.1 after the last iteration: every observation's
+ * private copy (x_o, y_o) of Eq. (9) to copies [n_obs][9] and its duals (r_o, s_o)
+ * after Eqs. (12)-(13) to duals [n_obs][9], caller order, caller-owned host arrays.
+ * Either pointer may be NULL.  ESTATE before dba_set_observations. */
 dba_status dba_get_state(dba_ctx* ctx, double* copies, double* duals);
 
-/* Replaces the whole ADMM state (checkpoint resume): copies, duals [n_obs][9]
- * in caller order, consensus cams [n_cams][6] and pts [n_pts][3].
- * iters_done restarts at 0. */
+/* Replaces the whole ADMM state of Sec. 3.1 (checkpoint resume): the copies of
+ * Eq. (9) and duals of Eqs. (12)-(13) [n_obs][9] in caller order, the consensus of
+ * Eqs. (10)-(11) cams [n_cams][6] and pts [n_pts][3] (host arrays, only read), and the
+ * iteration counter k >= 0 that dba_stats.iters_done continues from.  The next
+ * iteration forms the consensus sums in full, so any duals are accepted (after an
+ * iteration of the method they sum to zero per point and camera).  EINVAL for a null
+ * array, a non-finite value or k < 0; ESTATE before dba_set_observations.  Clears the
+ * device error flags. */
 dba_status dba_set_state(dba_ctx* ctx, const double* copies, const double* duals,
-                         const double* cams, const double* pts);
+                         const double* cams, const double* pts, int64_t k);
 
 /* Device time per kernel, averaged over the launches of the last dba_profile
  * call: names[i] (static strings) and ms[i] for i < *count (in: capacity). */
@@ -208,6 +224,14 @@ dba_status dba_build_layout(int32_t n_cams, int32_t n_pts, int64_t n_obs, const 
  * iterating again.  EINVAL on a null context, ESTATE before
  * dba_set_observations. */
 dba_status dba_inject_copy_stall(dba_ctx* ctx, int on);
+
+/* Fault injection for tests of the ABI's exception guard (no counterpart in the paper).
+ * The next n entry points called on this host thread fail as if their first host
+ * allocation had thrown: each returns DBA_ENOMEM with "out of host memory" as its
+ * message, touching none of its arguments.  n = 0 cancels; EINVAL for n < 0.  Every
+ * entry point that returns a dba_status runs its whole body under the guard, so no C++
+ * exception crosses this ABI. */
+dba_status dba_inject_host_alloc_failure(int n);
 
 /* Sizes of the internal observation layout after dba_set_observations, for
  * traffic models: out[0] tiles, out[1] observations per tile (block size),

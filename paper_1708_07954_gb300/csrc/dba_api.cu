@@ -424,64 +424,66 @@ void dba_config_default(dba_config* cfg) {
 }
 
 dba_status dba_create(const dba_config* cfg, dba_ctx** out) {
-  if (!cfg || !out) {
-    g_create_error = "dba_create: null argument";
-    return DBA_EINVAL;
-  }
-  *out = nullptr;
-  const bool ok = std::isfinite(cfg->focal) && cfg->focal > 0 && std::isfinite(cfg->cx) &&
-                  std::isfinite(cfg->cy) && cfg->loss >= 0 && cfg->loss <= 2 &&
-                  (cfg->loss == DBA_LOSS_L2 || (std::isfinite(cfg->loss_param) && cfg->loss_param > 0)) &&
-                  std::isfinite(cfg->rho_x) && cfg->rho_x > 0 && std::isfinite(cfg->rho_y) &&
-                  cfg->rho_y > 0 && std::isfinite(cfg->rho_angle) && cfg->inner_steps >= 0 && cfg->inner_steps <= 1000 &&
-                  std::isfinite(cfg->lm_lambda0) && cfg->lm_lambda0 > 0 &&
-                  std::isfinite(cfg->lm_lambda_min) && cfg->lm_lambda_min >= 0 &&
-                  std::isfinite(cfg->eps_depth) && std::isfinite(cfg->lm_model_tol) &&
-                  cfg->lm_model_tol >= 0 && (cfg->precision == 0 || cfg->precision == 1) &&
-                  (cfg->tile_obs == 0 || cfg->tile_obs == -1 || cfg->tile_obs == 64 ||
-                   cfg->tile_obs == 128 || cfg->tile_obs == 256) &&
-                  (cfg->local_solver == DBA_SOLVER_GN || cfg->local_solver == DBA_SOLVER_LBFGS);
-  if (!ok) {
-    g_create_error =
-        "dba_create: invalid configuration (check focal, loss, rho, steps, precision, tile_obs, local_solver)";
-    return DBA_EINVAL;
-  }
-  cudaError_t e = cudaFree(nullptr);  // initialise the runtime on the current device
-  if (e == cudaSuccess) e = dba::prepare_tile_kernels();
-  if (e != cudaSuccess) {
-    g_create_error = std::string("dba_create: CUDA unavailable: ") + cudaGetErrorString(e);
-    return DBA_ECUDA;
-  }
-  dba_ctx* ctx = new (std::nothrow) dba_ctx();
-  if (!ctx) {
-    g_create_error = "dba_create: out of host memory";
-    return DBA_ENOMEM;
-  }
-  ctx->cfg = *cfg;
-  ctx->fp32 = cfg->precision == DBA_PREC_F32_LOCAL;
-  ctx->prm = Params{cfg->focal, cfg->cx, cfg->cy, cfg->loss, cfg->loss_param, cfg->rho_x, cfg->rho_y,
-                    cfg->rho_angle > 0 ? cfg->rho_angle : cfg->rho_y,
-                    cfg->inner_steps, cfg->lm_lambda0, cfg->lm_lambda_min, cfg->eps_depth,
-                    cfg->lm_model_tol, cfg->local_solver};
-  if (cfg->cuda_stream) {
-    ctx->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
-  } else {
-    e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+  return dba::guarded(&g_create_error, [&]() -> dba_status {
+    if (!cfg || !out) {
+      g_create_error = "dba_create: null argument";
+      return DBA_EINVAL;
+    }
+    *out = nullptr;
+    const bool ok = std::isfinite(cfg->focal) && cfg->focal > 0 && std::isfinite(cfg->cx) &&
+                    std::isfinite(cfg->cy) && cfg->loss >= 0 && cfg->loss <= 2 &&
+                    (cfg->loss == DBA_LOSS_L2 || (std::isfinite(cfg->loss_param) && cfg->loss_param > 0)) &&
+                    std::isfinite(cfg->rho_x) && cfg->rho_x > 0 && std::isfinite(cfg->rho_y) &&
+                    cfg->rho_y > 0 && std::isfinite(cfg->rho_angle) && cfg->inner_steps >= 0 && cfg->inner_steps <= 1000 &&
+                    std::isfinite(cfg->lm_lambda0) && cfg->lm_lambda0 > 0 &&
+                    std::isfinite(cfg->lm_lambda_min) && cfg->lm_lambda_min >= 0 &&
+                    std::isfinite(cfg->eps_depth) && std::isfinite(cfg->lm_model_tol) &&
+                    cfg->lm_model_tol >= 0 && (cfg->precision == 0 || cfg->precision == 1) &&
+                    (cfg->tile_obs == 0 || cfg->tile_obs == -1 || cfg->tile_obs == 64 ||
+                     cfg->tile_obs == 128 || cfg->tile_obs == 256) &&
+                    (cfg->local_solver == DBA_SOLVER_GN || cfg->local_solver == DBA_SOLVER_LBFGS);
+    if (!ok) {
+      g_create_error =
+          "dba_create: invalid configuration (check focal, loss, rho, steps, precision, tile_obs, local_solver)";
+      return DBA_EINVAL;
+    }
+    cudaError_t e = cudaFree(nullptr);  // initialise the runtime on the current device
+    if (e == cudaSuccess) e = dba::prepare_tile_kernels();
     if (e != cudaSuccess) {
-      g_create_error = std::string("dba_create: ") + cudaGetErrorString(e);
+      g_create_error = std::string("dba_create: CUDA unavailable: ") + cudaGetErrorString(e);
+      return DBA_ECUDA;
+    }
+    dba_ctx* ctx = new (std::nothrow) dba_ctx();
+    if (!ctx) {
+      g_create_error = "dba_create: out of host memory";
+      return DBA_ENOMEM;
+    }
+    ctx->cfg = *cfg;
+    ctx->fp32 = cfg->precision == DBA_PREC_F32_LOCAL;
+    ctx->prm = Params{cfg->focal, cfg->cx, cfg->cy, cfg->loss, cfg->loss_param, cfg->rho_x, cfg->rho_y,
+                      cfg->rho_angle > 0 ? cfg->rho_angle : cfg->rho_y,
+                      cfg->inner_steps, cfg->lm_lambda0, cfg->lm_lambda_min, cfg->eps_depth,
+                      cfg->lm_model_tol, cfg->local_solver};
+    if (cfg->cuda_stream) {
+      ctx->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
+    } else {
+      e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+      if (e != cudaSuccess) {
+        g_create_error = std::string("dba_create: ") + cudaGetErrorString(e);
+        delete ctx;
+        return DBA_ECUDA;
+      }
+      ctx->own_stream = true;
+    }
+    if (cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess) {
+      g_create_error = "dba_create: cudaEventCreate failed";
+      if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
       delete ctx;
       return DBA_ECUDA;
     }
-    ctx->own_stream = true;
-  }
-  if (cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess) {
-    g_create_error = "dba_create: cudaEventCreate failed";
-    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
-    delete ctx;
-    return DBA_ECUDA;
-  }
-  *out = ctx;
-  return DBA_OK;
+    *out = ctx;
+    return DBA_OK;
+  });
 }
 
 void dba_destroy(dba_ctx* ctx) {
@@ -1042,36 +1044,45 @@ dba_status dba_get_state(dba_ctx* ctx, double* copies, double* duals) {
 }
 
 dba_status dba_set_state(dba_ctx* ctx, const double* copies, const double* duals, const double* cams,
-                         const double* pts) {
+                         const double* pts, int64_t k) {
   return dba::guarded(ctx ? &ctx->err : nullptr, [&]() -> dba_status {
     if (!ctx) return DBA_EINVAL;
     if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_set_state before dba_set_observations");
     if (!copies || !duals || !cams || !pts) return ctx->fail(DBA_EINVAL, "dba_set_state: null array");
+    if (k < 0) return ctx->fail(DBA_EINVAL, "dba_set_state: negative iteration count");
     if (!finite_all(copies, 9 * ctx->n_obs) || !finite_all(duals, 9 * ctx->n_obs) ||
         !finite_all(cams, 6 * (long long)ctx->n_cams) || !finite_all(pts, 3 * (long long)ctx->n_pts))
       return ctx->fail(DBA_EINVAL, "dba_set_state: non-finite value");
-    return upload_state(ctx, cams, pts, copies, duals);
+    const dba_status s = upload_state(ctx, cams, pts, copies, duals);
+    if (s == DBA_OK) ctx->iters = k;
+    return s;
   });
+}
+
+dba_status dba_inject_host_alloc_failure(int n) {
+  if (n < 0) return DBA_EINVAL;
+  dba::injected_host_alloc_failures() = n;
+  return DBA_OK;
 }
 
 dba_status dba_build_layout(int32_t n_cams, int32_t n_pts, int64_t n_obs, const int32_t* pt_idx,
                             const int32_t* cam_idx, int tile_obs, int64_t* perm, int32_t* point,
                             int32_t* point_perm, int32_t* cam_rank, int64_t* tile_start, int64_t* n_tiles) {
-  if (n_cams <= 0 || n_pts <= 0 || n_obs <= 0 || n_obs > (int64_t)0x7fffffff || n_cams > dba::kCamMask ||
-      !pt_idx || !cam_idx) {
-    g_create_error = "dba_build_layout: sizes out of range or null index array";
-    return DBA_EINVAL;
-  }
-  if (tile_obs != 64 && tile_obs != 128 && tile_obs != 256) {
-    g_create_error = "dba_build_layout: tile_obs must be 64, 128 or 256";
-    return DBA_EINVAL;
-  }
-  const long long bad = first_bad_index(pt_idx, cam_idx, n_obs, n_pts, n_cams);
-  if (bad >= 0) {
-    g_create_error = "dba_build_layout: observation " + std::to_string(bad) + " has an index out of range";
-    return DBA_EINVAL;
-  }
-  try {
+  return dba::guarded(&g_create_error, [&]() -> dba_status {
+    if (n_cams <= 0 || n_pts <= 0 || n_obs <= 0 || n_obs > (int64_t)0x7fffffff || n_cams > dba::kCamMask ||
+        !pt_idx || !cam_idx) {
+      g_create_error = "dba_build_layout: sizes out of range or null index array";
+      return DBA_EINVAL;
+    }
+    if (tile_obs != 64 && tile_obs != 128 && tile_obs != 256) {
+      g_create_error = "dba_build_layout: tile_obs must be 64, 128 or 256";
+      return DBA_EINVAL;
+    }
+    const long long bad = first_bad_index(pt_idx, cam_idx, n_obs, n_pts, n_cams);
+    if (bad >= 0) {
+      g_create_error = "dba_build_layout: observation " + std::to_string(bad) + " has an index out of range";
+      return DBA_EINVAL;
+    }
     HostLayout L;
     build_layout(n_cams, n_pts, n_obs, pt_idx, cam_idx, tile_obs, L);
     for (long long o = 0; o < n_obs; ++o) {
@@ -1086,20 +1097,19 @@ dba_status dba_build_layout(int32_t n_cams, int32_t n_pts, int64_t n_obs, const 
       tile_start[L.tiles.size()] = n_obs;
     }
     if (n_tiles) *n_tiles = (int64_t)L.tiles.size();
-  } catch (const std::bad_alloc&) {
-    g_create_error = "dba_build_layout: out of host memory";
-    return DBA_ENOMEM;
-  }
-  return DBA_OK;
+    return DBA_OK;
+  });
 }
 
 dba_status dba_inject_copy_stall(dba_ctx* ctx, int on) {
-  if (!ctx) return DBA_EINVAL;
-  if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_inject_copy_stall before dba_set_observations");
-  const unsigned int v = on ? 1u : 0u;
-  DBA_CUDA(cudaMemcpyAsync(&ctx->P.ctl->inject, &v, sizeof v, cudaMemcpyHostToDevice, ctx->stream), "inject");
-  DBA_CUDA(cudaStreamSynchronize(ctx->stream), "inject");
-  return DBA_OK;
+  return dba::guarded(ctx ? &ctx->err : nullptr, [&]() -> dba_status {
+    if (!ctx) return DBA_EINVAL;
+    if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_inject_copy_stall before dba_set_observations");
+    const unsigned int v = on ? 1u : 0u;
+    DBA_CUDA(cudaMemcpyAsync(&ctx->P.ctl->inject, &v, sizeof v, cudaMemcpyHostToDevice, ctx->stream), "inject");
+    DBA_CUDA(cudaStreamSynchronize(ctx->stream), "inject");
+    return DBA_OK;
+  });
 }
 
 dba_status dba_profile(dba_ctx* ctx, int n_iters, const char** names, double* ms, int* count) {
@@ -1157,44 +1167,48 @@ dba_status dba_profile(dba_ctx* ctx, int n_iters, const char** names, double* ms
 }
 
 dba_status dba_layout(dba_ctx* ctx, int64_t* out, int* count) {
-  if (!ctx || !out || !count) return DBA_EINVAL;
-  if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_layout before dba_set_observations");
-  const int64_t v[6] = {ctx->P.n_tiles, ctx->P.tile_obs, ctx->n_pseg, (int64_t)ctx->P.n_cam_slots,
-                        (int64_t)ctx->P.n_split_pts, (int64_t)ctx->P.n_pt_slots};
-  const int n = std::min(*count, 6);
-  for (int k = 0; k < n; ++k) out[k] = v[k];
-  *count = n;
-  return DBA_OK;
+  return dba::guarded(ctx ? &ctx->err : nullptr, [&]() -> dba_status {
+    if (!ctx || !out || !count) return DBA_EINVAL;
+    if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_layout before dba_set_observations");
+    const int64_t v[6] = {ctx->P.n_tiles, ctx->P.tile_obs, ctx->n_pseg, (int64_t)ctx->P.n_cam_slots,
+                          (int64_t)ctx->P.n_split_pts, (int64_t)ctx->P.n_pt_slots};
+    const int n = std::min(*count, 6);
+    for (int k = 0; k < n; ++k) out[k] = v[k];
+    *count = n;
+    return DBA_OK;
+  });
 }
 
 dba_status dba_evaluate_noalloc(const dba_config* cfg, int32_t n_cams, int32_t n_pts, int64_t n_obs,
                                 const int32_t* pt_idx, const int32_t* cam_idx, const double* z,
                                 const double* cams, const double* pts, double* out, void* stream) {
-  if (!cfg || !out || (n_obs > 0 && (!pt_idx || !cam_idx || !z || !cams || !pts))) {
-    g_create_error = "dba_evaluate_noalloc: null pointer";
-    return DBA_EINVAL;
-  }
-  if (n_obs < 0 || n_obs > (int64_t)DBA_NOALLOC_MAX_OBS || n_cams < 0 || n_pts < 0) {
-    g_create_error = "dba_evaluate_noalloc: n_obs must lie in [0, " + std::to_string(DBA_NOALLOC_MAX_OBS) +
-                     "] (the size of its fixed device scratch) and n_cams, n_pts must be >= 0";
-    return DBA_EINVAL;
-  }
-  if (!(std::isfinite(cfg->focal) && cfg->focal > 0 && std::isfinite(cfg->cx) && std::isfinite(cfg->cy) &&
-        cfg->loss >= 0 && cfg->loss <= 2 &&
-        (cfg->loss == DBA_LOSS_L2 || (std::isfinite(cfg->loss_param) && cfg->loss_param > 0)) &&
-        std::isfinite(cfg->eps_depth))) {
-    g_create_error = "dba_evaluate_noalloc: invalid configuration (focal, principal point, loss, eps_depth)";
-    return DBA_EINVAL;
-  }
-  const Params prm{cfg->focal, cfg->cx, cfg->cy, cfg->loss, cfg->loss_param, 1.0, 1.0, 1.0,
-                   0, 1e-3, 0.0, cfg->eps_depth, 0.0, DBA_SOLVER_GN};
-  const cudaError_t e = dba::launch_eval_noalloc(prm, n_obs, n_cams, n_pts, pt_idx, cam_idx, z, cams, pts, out,
-                                                 static_cast<cudaStream_t>(stream));
-  if (e != cudaSuccess) {
-    g_create_error = std::string("dba_evaluate_noalloc: ") + cudaGetErrorString(e);
-    return DBA_ECUDA;
-  }
-  return DBA_OK;
+  return dba::guarded(&g_create_error, [&]() -> dba_status {
+    if (!cfg || !out || (n_obs > 0 && (!pt_idx || !cam_idx || !z || !cams || !pts))) {
+      g_create_error = "dba_evaluate_noalloc: null pointer";
+      return DBA_EINVAL;
+    }
+    if (n_obs < 0 || n_obs > (int64_t)DBA_NOALLOC_MAX_OBS || n_cams < 0 || n_pts < 0) {
+      g_create_error = "dba_evaluate_noalloc: n_obs must lie in [0, " + std::to_string(DBA_NOALLOC_MAX_OBS) +
+                       "] (the size of its fixed device scratch) and n_cams, n_pts must be >= 0";
+      return DBA_EINVAL;
+    }
+    if (!(std::isfinite(cfg->focal) && cfg->focal > 0 && std::isfinite(cfg->cx) && std::isfinite(cfg->cy) &&
+          cfg->loss >= 0 && cfg->loss <= 2 &&
+          (cfg->loss == DBA_LOSS_L2 || (std::isfinite(cfg->loss_param) && cfg->loss_param > 0)) &&
+          std::isfinite(cfg->eps_depth))) {
+      g_create_error = "dba_evaluate_noalloc: invalid configuration (focal, principal point, loss, eps_depth)";
+      return DBA_EINVAL;
+    }
+    const Params prm{cfg->focal, cfg->cx, cfg->cy, cfg->loss, cfg->loss_param, 1.0, 1.0, 1.0,
+                     0, 1e-3, 0.0, cfg->eps_depth, 0.0, DBA_SOLVER_GN};
+    const cudaError_t e = dba::launch_eval_noalloc(prm, n_obs, n_cams, n_pts, pt_idx, cam_idx, z, cams, pts, out,
+                                                   static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) {
+      g_create_error = std::string("dba_evaluate_noalloc: ") + cudaGetErrorString(e);
+      return DBA_ECUDA;
+    }
+    return DBA_OK;
+  });
 }
 
 dba_status dba_set_scenes(dba_ctx* ctx, int32_t n_scenes, const int64_t* obs_off, const int32_t* cam_off,

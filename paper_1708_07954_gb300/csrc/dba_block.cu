@@ -1080,61 +1080,63 @@ std::string build_block_layout(int n_cams, int n_pts, long long l, const int32_t
 extern "C" {
 
 dba_status dba_block_create(const dba_config* cfg, int block_points, int block_cams, dba_block_ctx** out) {
-  if (!cfg || !out) {
-    g_block_error = "dba_block_create: null argument";
-    return DBA_EINVAL;
-  }
-  *out = nullptr;
-  const bool ok = std::isfinite(cfg->focal) && cfg->focal > 0 && std::isfinite(cfg->cx) && std::isfinite(cfg->cy) &&
-                  cfg->loss >= 0 && cfg->loss <= 2 &&
-                  (cfg->loss == DBA_LOSS_L2 || (std::isfinite(cfg->loss_param) && cfg->loss_param > 0)) &&
-                  std::isfinite(cfg->rho_x) && cfg->rho_x > 0 && std::isfinite(cfg->rho_y) && cfg->rho_y > 0 &&
-                  std::isfinite(cfg->rho_angle) && cfg->inner_steps >= 0 && cfg->inner_steps <= 1000 &&
-                  std::isfinite(cfg->lm_lambda0) && cfg->lm_lambda0 > 0 && std::isfinite(cfg->lm_lambda_min) &&
-                  cfg->lm_lambda_min >= 0 && std::isfinite(cfg->eps_depth) && std::isfinite(cfg->lm_model_tol) &&
-                  cfg->lm_model_tol >= 0 && (cfg->precision == 0 || cfg->precision == 1) &&
-                  cfg->local_solver == DBA_SOLVER_GN;
-  if (!ok) {
-    g_block_error = "dba_block_create: invalid configuration";
-    return DBA_EINVAL;
-  }
-  if (block_points < 1 || block_points > DBA_BLOCK_MAX_POINTS || block_cams < 1 ||
-      block_cams > DBA_BLOCK_MAX_CAMERAS) {
-    g_block_error = "dba_block_create: block_points must be in [1, 64] and block_cams in [1, 4]";
-    return DBA_EINVAL;
-  }
-  cudaError_t e = cudaFree(nullptr);
-  if (e != cudaSuccess) {
-    g_block_error = std::string("dba_block_create: CUDA unavailable: ") + cudaGetErrorString(e);
-    return DBA_ECUDA;
-  }
-  dba_block_ctx* ctx = new (std::nothrow) dba_block_ctx();
-  if (!ctx) {
-    g_block_error = "dba_block_create: out of host memory";
-    return DBA_ENOMEM;
-  }
-  ctx->cfg = *cfg;
-  ctx->fp32 = cfg->precision == DBA_PREC_F32_LOCAL;
-  ctx->pi = block_points;
-  ctx->kappa = block_cams;
-  ctx->prm = dba::Params{cfg->focal, cfg->cx, cfg->cy, cfg->loss, cfg->loss_param, cfg->rho_x, cfg->rho_y,
-                         cfg->rho_angle > 0 ? cfg->rho_angle : cfg->rho_y, cfg->inner_steps, cfg->lm_lambda0,
-                         cfg->lm_lambda_min, cfg->eps_depth, cfg->lm_model_tol, DBA_SOLVER_GN};
-  if (cfg->cuda_stream) {
-    ctx->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
-  } else {
-    e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
-    ctx->own_stream = e == cudaSuccess;
-  }
-  if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev0);
-  if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev1);
-  if (e != cudaSuccess) {
-    g_block_error = std::string("dba_block_create: ") + cudaGetErrorString(e);
-    dba_block_destroy(ctx);
-    return DBA_ECUDA;
-  }
-  *out = ctx;
-  return DBA_OK;
+  return dba::guarded(&g_block_error, [&]() -> dba_status {
+    if (!cfg || !out) {
+      g_block_error = "dba_block_create: null argument";
+      return DBA_EINVAL;
+    }
+    *out = nullptr;
+    const bool ok = std::isfinite(cfg->focal) && cfg->focal > 0 && std::isfinite(cfg->cx) && std::isfinite(cfg->cy) &&
+                    cfg->loss >= 0 && cfg->loss <= 2 &&
+                    (cfg->loss == DBA_LOSS_L2 || (std::isfinite(cfg->loss_param) && cfg->loss_param > 0)) &&
+                    std::isfinite(cfg->rho_x) && cfg->rho_x > 0 && std::isfinite(cfg->rho_y) && cfg->rho_y > 0 &&
+                    std::isfinite(cfg->rho_angle) && cfg->inner_steps >= 0 && cfg->inner_steps <= 1000 &&
+                    std::isfinite(cfg->lm_lambda0) && cfg->lm_lambda0 > 0 && std::isfinite(cfg->lm_lambda_min) &&
+                    cfg->lm_lambda_min >= 0 && std::isfinite(cfg->eps_depth) && std::isfinite(cfg->lm_model_tol) &&
+                    cfg->lm_model_tol >= 0 && (cfg->precision == 0 || cfg->precision == 1) &&
+                    cfg->local_solver == DBA_SOLVER_GN;
+    if (!ok) {
+      g_block_error = "dba_block_create: invalid configuration";
+      return DBA_EINVAL;
+    }
+    if (block_points < 1 || block_points > DBA_BLOCK_MAX_POINTS || block_cams < 1 ||
+        block_cams > DBA_BLOCK_MAX_CAMERAS) {
+      g_block_error = "dba_block_create: block_points must be in [1, 64] and block_cams in [1, 4]";
+      return DBA_EINVAL;
+    }
+    cudaError_t e = cudaFree(nullptr);
+    if (e != cudaSuccess) {
+      g_block_error = std::string("dba_block_create: CUDA unavailable: ") + cudaGetErrorString(e);
+      return DBA_ECUDA;
+    }
+    dba_block_ctx* ctx = new (std::nothrow) dba_block_ctx();
+    if (!ctx) {
+      g_block_error = "dba_block_create: out of host memory";
+      return DBA_ENOMEM;
+    }
+    ctx->cfg = *cfg;
+    ctx->fp32 = cfg->precision == DBA_PREC_F32_LOCAL;
+    ctx->pi = block_points;
+    ctx->kappa = block_cams;
+    ctx->prm = dba::Params{cfg->focal, cfg->cx, cfg->cy, cfg->loss, cfg->loss_param, cfg->rho_x, cfg->rho_y,
+                           cfg->rho_angle > 0 ? cfg->rho_angle : cfg->rho_y, cfg->inner_steps, cfg->lm_lambda0,
+                           cfg->lm_lambda_min, cfg->eps_depth, cfg->lm_model_tol, DBA_SOLVER_GN};
+    if (cfg->cuda_stream) {
+      ctx->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
+    } else {
+      e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
+      ctx->own_stream = e == cudaSuccess;
+    }
+    if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev1);
+    if (e != cudaSuccess) {
+      g_block_error = std::string("dba_block_create: ") + cudaGetErrorString(e);
+      dba_block_destroy(ctx);
+      return DBA_ECUDA;
+    }
+    *out = ctx;
+    return DBA_OK;
+  });
 }
 
 dba_status dba_block_set_observations(dba_block_ctx* ctx, int32_t n_cams, int32_t n_pts, int64_t n_obs,
@@ -1383,76 +1385,84 @@ dba_status dba_block_get_params(dba_block_ctx* ctx, double* cams_out, double* pt
 }
 
 dba_status dba_block_algorithmic_flops(const dba_block_ctx* ctx, double* per_iteration) {
-  if (!ctx || !per_iteration) return DBA_EINVAL;
-  if (!ctx->has_problem) return DBA_ESTATE;
-  *per_iteration = ctx->flops_start + ctx->cfg.inner_steps * ctx->flops_step;
-  return DBA_OK;
+  return dba::guarded(ctx ? &const_cast<dba_block_ctx*>(ctx)->err : nullptr, [&]() -> dba_status {
+    if (!ctx || !per_iteration) return DBA_EINVAL;
+    if (!ctx->has_problem) return DBA_ESTATE;
+    *per_iteration = ctx->flops_start + ctx->cfg.inner_steps * ctx->flops_step;
+    return DBA_OK;
+  });
 }
 
 dba_status dba_block_layout(const dba_block_ctx* ctx, int64_t* n_blocks, int64_t* n_point_copies,
                             int64_t* n_camera_copies) {
-  if (!ctx) return DBA_EINVAL;
-  if (!ctx->has_problem) return DBA_ESTATE;
-  if (n_blocks) *n_blocks = ctx->B.n_blocks;
-  if (n_point_copies) *n_point_copies = ctx->B.n_pc;
-  if (n_camera_copies) *n_camera_copies = ctx->B.n_cc;
-  return DBA_OK;
+  return dba::guarded(ctx ? &const_cast<dba_block_ctx*>(ctx)->err : nullptr, [&]() -> dba_status {
+    if (!ctx) return DBA_EINVAL;
+    if (!ctx->has_problem) return DBA_ESTATE;
+    if (n_blocks) *n_blocks = ctx->B.n_blocks;
+    if (n_point_copies) *n_point_copies = ctx->B.n_pc;
+    if (n_camera_copies) *n_camera_copies = ctx->B.n_cc;
+    return DBA_OK;
+  });
 }
 
 dba_status dba_block_build_layout(int32_t n_cams, int32_t n_pts, int64_t n_obs, const int32_t* pt_idx,
                                   const int32_t* cam_idx, int block_points, int block_cams, int64_t* obs_order,
                                   int32_t* blocks, int32_t* pc_point, int32_t* cc_camera, int64_t* counts,
                                   int64_t* size_classes) {
-  if (n_cams <= 0 || n_pts <= 0 || n_obs <= 0 || n_obs > INT_MAX || !pt_idx || !cam_idx ||
-      block_points < 1 || block_points > DBA_BLOCK_MAX_POINTS || block_cams < 1 ||
-      block_cams > DBA_BLOCK_MAX_CAMERAS) {
-    g_block_error = "dba_block_build_layout: sizes out of range or null index array";
-    return DBA_EINVAL;
-  }
-  for (int64_t o = 0; o < n_obs; ++o)
-    if (pt_idx[o] < 0 || pt_idx[o] >= n_pts || cam_idx[o] < 0 || cam_idx[o] >= n_cams) {
-      g_block_error = "dba_block_build_layout: observation " + std::to_string(o) +
-                      " indexes outside the cameras or points";
+  return dba::guarded(&g_block_error, [&]() -> dba_status {
+    if (n_cams <= 0 || n_pts <= 0 || n_obs <= 0 || n_obs > INT_MAX || !pt_idx || !cam_idx ||
+        block_points < 1 || block_points > DBA_BLOCK_MAX_POINTS || block_cams < 1 ||
+        block_cams > DBA_BLOCK_MAX_CAMERAS) {
+      g_block_error = "dba_block_build_layout: sizes out of range or null index array";
       return DBA_EINVAL;
     }
-  try {
-    BlockHostLayout H;
-    const std::string msg = build_block_layout(n_cams, n_pts, n_obs, pt_idx, cam_idx, block_points, block_cams, H);
-    if (!msg.empty()) {
-      g_block_error = "dba_block_build_layout: " + msg;
-      return DBA_EINVAL;
-    }
-    if (obs_order)
-      for (int64_t o = 0; o < n_obs; ++o) obs_order[o] = H.blk_obs[o];
-    if (blocks)
-      for (size_t b = 0; b < H.blocks.size(); ++b) {
-        const dba::BlockInfo& bi = H.blocks[b];
-        const int32_t v[6] = {bi.o0, bi.no, bi.p0, bi.np, bi.c0, bi.nc};
-        for (int k = 0; k < 6; ++k) blocks[6 * b + k] = v[k];
+    for (int64_t o = 0; o < n_obs; ++o)
+      if (pt_idx[o] < 0 || pt_idx[o] >= n_pts || cam_idx[o] < 0 || cam_idx[o] >= n_cams) {
+        g_block_error = "dba_block_build_layout: observation " + std::to_string(o) +
+                        " indexes outside the cameras or points";
+        return DBA_EINVAL;
       }
-    if (pc_point)
-      for (size_t k = 0; k < H.pc_pt.size(); ++k) pc_point[k] = H.pc_pt[k];
-    if (cc_camera)
-      for (size_t k = 0; k < H.cc_cam.size(); ++k) cc_camera[k] = H.cc_cam[k];
-    if (counts) {
-      counts[0] = (int64_t)H.blocks.size();
-      counts[1] = (int64_t)H.pc_pt.size();
-      counts[2] = (int64_t)H.cc_cam.size();
+    try {
+      BlockHostLayout H;
+      const std::string msg = build_block_layout(n_cams, n_pts, n_obs, pt_idx, cam_idx, block_points, block_cams, H);
+      if (!msg.empty()) {
+        g_block_error = "dba_block_build_layout: " + msg;
+        return DBA_EINVAL;
+      }
+      if (obs_order)
+        for (int64_t o = 0; o < n_obs; ++o) obs_order[o] = H.blk_obs[o];
+      if (blocks)
+        for (size_t b = 0; b < H.blocks.size(); ++b) {
+          const dba::BlockInfo& bi = H.blocks[b];
+          const int32_t v[6] = {bi.o0, bi.no, bi.p0, bi.np, bi.c0, bi.nc};
+          for (int k = 0; k < 6; ++k) blocks[6 * b + k] = v[k];
+        }
+      if (pc_point)
+        for (size_t k = 0; k < H.pc_pt.size(); ++k) pc_point[k] = H.pc_pt[k];
+      if (cc_camera)
+        for (size_t k = 0; k < H.cc_cam.size(); ++k) cc_camera[k] = H.cc_cam[k];
+      if (counts) {
+        counts[0] = (int64_t)H.blocks.size();
+        counts[1] = (int64_t)H.pc_pt.size();
+        counts[2] = (int64_t)H.cc_cam.size();
+      }
+      if (size_classes)
+        for (int k = 0; k < dba::kBlkClasses; ++k) size_classes[k] = H.cls[k + 1] - H.cls[k];
+    } catch (const std::bad_alloc&) {
+      g_block_error = "dba_block_build_layout: out of host memory";
+      return DBA_ENOMEM;
     }
-    if (size_classes)
-      for (int k = 0; k < dba::kBlkClasses; ++k) size_classes[k] = H.cls[k + 1] - H.cls[k];
-  } catch (const std::bad_alloc&) {
-    g_block_error = "dba_block_build_layout: out of host memory";
-    return DBA_ENOMEM;
-  }
-  return DBA_OK;
+    return DBA_OK;
+  });
 }
 
 dba_status dba_block_size_classes(const dba_block_ctx* ctx, int64_t* counts) {
-  if (!ctx || !counts) return DBA_EINVAL;
-  if (!ctx->has_problem) return DBA_ESTATE;
-  for (int k = 0; k < dba::kBlkClasses; ++k) counts[k] = ctx->cls[k + 1] - ctx->cls[k];
-  return DBA_OK;
+  return dba::guarded(ctx ? &const_cast<dba_block_ctx*>(ctx)->err : nullptr, [&]() -> dba_status {
+    if (!ctx || !counts) return DBA_EINVAL;
+    if (!ctx->has_problem) return DBA_ESTATE;
+    for (int k = 0; k < dba::kBlkClasses; ++k) counts[k] = ctx->cls[k + 1] - ctx->cls[k];
+    return DBA_OK;
+  });
 }
 
 const char* dba_block_last_error(const dba_block_ctx* ctx) {

@@ -726,39 +726,41 @@ dba_status mlp_fail(dba_mlp* m, cudaError_t e, const char* where) {
 extern "C" {
 
 dba_status dba_mlp_create(uint64_t seed, dba_mlp** out) {
-  if (!out) return DBA_EINVAL;
-  *out = nullptr;
-  dba_mlp* m = new (std::nothrow) dba_mlp();
-  if (!m) return DBA_ENOMEM;
-  std::vector<float> h(dba::kNParams, 0.f);
-  std::mt19937_64 rng(seed);
-  auto init = [&](int base, int nrow, int fan_in, float gain) {
-    std::normal_distribution<float> nd(0.f, gain * std::sqrt(2.f / (float)fan_in));
-    for (int e = 0; e < nrow * fan_in; ++e) h[base + e] = nd(rng);
-  };
-  init(dba::kW1, dba::kMlpHidden, dba::kMlpIn, 1.f);
-  init(dba::kW2, dba::kMlpHidden, dba::kMlpHidden, 1.f);
-  init(dba::kW3, dba::kMlpHidden, dba::kMlpHidden, 1.f);
-  init(dba::kW4, dba::kMlpOut, dba::kMlpHidden, 0.1f);
-  for (int c = 0; c < dba::kMlpIn; ++c) h[dba::kInStd + c] = 1.f;
-  for (int c = 0; c < dba::kMlpOut; ++c) h[dba::kOutStd + c] = 1.f;
-  // a blocking stream: orders after work the caller queued on the legacy default stream
-  cudaError_t e = cudaStreamCreate(&m->stream);
-  if (e == cudaSuccess) e = cudaMalloc(&m->params, sizeof(float) * dba::kNParams);
-  if (e == cudaSuccess) e = cudaMalloc(&m->grad, sizeof(float) * dba::kNParams);
-  if (e == cudaSuccess) e = cudaMalloc(&m->adam_m, sizeof(float) * dba::kNParams);
-  if (e == cudaSuccess) e = cudaMalloc(&m->adam_v, sizeof(float) * dba::kNParams);
-  if (e == cudaSuccess) e = cudaMalloc(&m->dloss, sizeof(double));
-  if (e == cudaSuccess) e = cudaMemcpy(m->params, h.data(), sizeof(float) * dba::kNParams, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemset(m->adam_m, 0, sizeof(float) * dba::kNParams);
-  if (e == cudaSuccess) e = cudaMemset(m->adam_v, 0, sizeof(float) * dba::kNParams);
-  if (e != cudaSuccess) {
-    g_mlp_error = std::string("dba_mlp_create: ") + cudaGetErrorString(e);
-    dba_mlp_destroy(m);
-    return DBA_ECUDA;
-  }
-  *out = m;
-  return DBA_OK;
+  return dba::guarded(&g_mlp_error, [&]() -> dba_status {
+    if (!out) return DBA_EINVAL;
+    *out = nullptr;
+    dba_mlp* m = new (std::nothrow) dba_mlp();
+    if (!m) return DBA_ENOMEM;
+    std::vector<float> h(dba::kNParams, 0.f);
+    std::mt19937_64 rng(seed);
+    auto init = [&](int base, int nrow, int fan_in, float gain) {
+      std::normal_distribution<float> nd(0.f, gain * std::sqrt(2.f / (float)fan_in));
+      for (int e = 0; e < nrow * fan_in; ++e) h[base + e] = nd(rng);
+    };
+    init(dba::kW1, dba::kMlpHidden, dba::kMlpIn, 1.f);
+    init(dba::kW2, dba::kMlpHidden, dba::kMlpHidden, 1.f);
+    init(dba::kW3, dba::kMlpHidden, dba::kMlpHidden, 1.f);
+    init(dba::kW4, dba::kMlpOut, dba::kMlpHidden, 0.1f);
+    for (int c = 0; c < dba::kMlpIn; ++c) h[dba::kInStd + c] = 1.f;
+    for (int c = 0; c < dba::kMlpOut; ++c) h[dba::kOutStd + c] = 1.f;
+    // a blocking stream: orders after work the caller queued on the legacy default stream
+    cudaError_t e = cudaStreamCreate(&m->stream);
+    if (e == cudaSuccess) e = cudaMalloc(&m->params, sizeof(float) * dba::kNParams);
+    if (e == cudaSuccess) e = cudaMalloc(&m->grad, sizeof(float) * dba::kNParams);
+    if (e == cudaSuccess) e = cudaMalloc(&m->adam_m, sizeof(float) * dba::kNParams);
+    if (e == cudaSuccess) e = cudaMalloc(&m->adam_v, sizeof(float) * dba::kNParams);
+    if (e == cudaSuccess) e = cudaMalloc(&m->dloss, sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpy(m->params, h.data(), sizeof(float) * dba::kNParams, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(m->adam_m, 0, sizeof(float) * dba::kNParams);
+    if (e == cudaSuccess) e = cudaMemset(m->adam_v, 0, sizeof(float) * dba::kNParams);
+    if (e != cudaSuccess) {
+      g_mlp_error = std::string("dba_mlp_create: ") + cudaGetErrorString(e);
+      dba_mlp_destroy(m);
+      return DBA_ECUDA;
+    }
+    *out = m;
+    return DBA_OK;
+  });
 }
 
 void dba_mlp_destroy(dba_mlp* m) {
@@ -776,21 +778,25 @@ void dba_mlp_destroy(dba_mlp* m) {
 const char* dba_mlp_last_error(const dba_mlp* m) { return m ? m->err.c_str() : g_mlp_error.c_str(); }
 
 dba_status dba_mlp_get_params(const dba_mlp* mc, float* host) {
-  dba_mlp* m = const_cast<dba_mlp*>(mc);
-  if (!m || !host) return DBA_EINVAL;
-  MLP_CUDA(cudaMemcpy(host, m->params, sizeof(float) * dba::kNParams, cudaMemcpyDeviceToHost), "get_params");
-  return DBA_OK;
+  return dba::guarded(mc ? &const_cast<dba_mlp*>(mc)->err : nullptr, [&]() -> dba_status {
+    dba_mlp* m = const_cast<dba_mlp*>(mc);
+    if (!m || !host) return DBA_EINVAL;
+    MLP_CUDA(cudaMemcpy(host, m->params, sizeof(float) * dba::kNParams, cudaMemcpyDeviceToHost), "get_params");
+    return DBA_OK;
+  });
 }
 
 dba_status dba_mlp_set_params(dba_mlp* m, const float* host) {
-  if (!m || !host) return DBA_EINVAL;
-  for (int k = 0; k < dba::kNParams; ++k)
-    if (!std::isfinite(host[k])) {
-      m->err = "dba_mlp_set_params: non-finite parameter";
-      return DBA_EINVAL;
-    }
-  MLP_CUDA(cudaMemcpy(m->params, host, sizeof(float) * dba::kNParams, cudaMemcpyHostToDevice), "set_params");
-  return DBA_OK;
+  return dba::guarded(m ? &m->err : nullptr, [&]() -> dba_status {
+    if (!m || !host) return DBA_EINVAL;
+    for (int k = 0; k < dba::kNParams; ++k)
+      if (!std::isfinite(host[k])) {
+        m->err = "dba_mlp_set_params: non-finite parameter";
+        return DBA_EINVAL;
+      }
+    MLP_CUDA(cudaMemcpy(m->params, host, sizeof(float) * dba::kNParams, cudaMemcpyHostToDevice), "set_params");
+    return DBA_OK;
+  });
 }
 
 dba_status dba_mlp_fit_normalizer(dba_mlp* m, const float* feats, const float* targets, int64_t n) {

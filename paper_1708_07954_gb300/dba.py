@@ -23,7 +23,7 @@ DBA_SOLVER_GN, DBA_SOLVER_LBFGS = 0, 1
 EXPORTED = [
     "dba_config_default", "dba_create", "dba_set_observations", "dba_set_ground_truth", "dba_iterate",
     "dba_iterate_until", "dba_evaluate", "dba_get_params", "dba_get_state", "dba_set_state",
-    "dba_profile", "dba_inject_copy_stall", "dba_build_layout", "dba_layout", "dba_evaluate_noalloc", "dba_set_scenes", "dba_scene_stats",
+    "dba_profile", "dba_inject_copy_stall", "dba_inject_host_alloc_failure", "dba_build_layout", "dba_layout", "dba_evaluate_noalloc", "dba_set_scenes", "dba_scene_stats",
     "dba_last_error", "dba_destroy", "dba_mlp_create", "dba_mlp_destroy", "dba_mlp_last_error",
     "dba_mlp_get_params", "dba_mlp_set_params", "dba_mlp_harvest", "dba_mlp_fit_normalizer",
     "dba_mlp_loss_grad", "dba_mlp_train", "dba_mlp_predict", "dba_set_warm_start",
@@ -95,7 +95,8 @@ def load():
     L.dba_evaluate.argtypes = [vp, P(dba_stats)]
     L.dba_get_params.argtypes = [vp, dp, dp]
     L.dba_get_state.argtypes = [vp, dp, dp]
-    L.dba_set_state.argtypes = [vp, dp, dp, dp, dp]
+    L.dba_set_state.argtypes = [vp, dp, dp, dp, dp, ctypes.c_int64]
+    L.dba_inject_host_alloc_failure.argtypes = [ctypes.c_int]
     L.dba_build_layout.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, ip, ip, ctypes.c_int,
                                    P(ctypes.c_int64), ip, ip, ip, P(ctypes.c_int64), P(ctypes.c_int64)]
     L.dba_inject_copy_stall.argtypes = [vp, ctypes.c_int]
@@ -260,9 +261,14 @@ def dba_get_state(ctx, n_obs):
     return copies, duals
 
 
-def dba_set_state(ctx, copies, duals, cams, pts):
+def dba_set_state(ctx, copies, duals, cams, pts, k=0):
     arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (copies, duals, cams, pts)]
-    _check(load().dba_set_state(ctx, *[_ptr(a) for a in arrs]), ctx)
+    _check(load().dba_set_state(ctx, *[_ptr(a) for a in arrs], int(k)), ctx)
+
+
+def dba_inject_host_alloc_failure(n):
+    """Fault injection (tests): the next n entry points on this thread fail with DBA_ENOMEM."""
+    _check(load().dba_inject_host_alloc_failure(int(n)), None)
 
 
 def dba_profile(ctx, n_iters):
@@ -447,8 +453,8 @@ class Solver:
     def state(self):
         return dba_get_state(self.ctx, self.scene.n_obs)
 
-    def set_state(self, copies, duals, cams, pts):
-        dba_set_state(self.ctx, copies, duals, cams, pts)
+    def set_state(self, copies, duals, cams, pts, k=0):
+        dba_set_state(self.ctx, copies, duals, cams, pts, k)
 
     def profile(self, n):
         return dba_profile(self.ctx, n)

@@ -100,3 +100,68 @@ def test_binding_constants_match_the_header():
     for name in ("DBA_BLOCK_MAX_POINTS", "DBA_BLOCK_MAX_CAMERAS", "DBA_BLOCK_SIZE_CLASSES", "DBA_MLP_N_PARAMS",
                  "DBA_ETIMEOUT", "DBA_SOLVER_LBFGS", "DBA_PREC_F32_LOCAL", "DBA_LOSS_STUDENT_T"):
         assert name in defines and hasattr(dba, name), name
+
+
+def _status_entry_points():
+    """(name, ctypes argument list of zeros/NULLs) of every dba_status function in dba.h."""
+    text = open(os.path.join(ROOT, "include", "dba.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    out = []
+    for name, params in re.findall(r"dba_status\s+(dba_[a-z_]+)\s*\(([^)]*)\)\s*;", text):
+        args = []
+        for p in [q.strip() for q in params.split(",") if q.strip()]:
+            if "*" in p:
+                args.append(ctypes.c_void_p(None))
+            elif p.startswith("double"):
+                args.append(ctypes.c_double(0.0))
+            elif p.startswith("float"):
+                args.append(ctypes.c_float(0.0))
+            elif p.startswith("int64_t"):
+                args.append(ctypes.c_int64(0))
+            elif p.startswith("uint64_t"):
+                args.append(ctypes.c_uint64(0))
+            else:
+                args.append(ctypes.c_int32(0))
+        out.append((name, args))
+    return out
+
+
+def test_every_entry_point_turns_a_host_allocation_failure_into_enomem(lib):
+    """An injected failed host allocation (std::bad_alloc) in each entry point comes back as
+    DBA_ENOMEM with no abort: every dba_status entry point runs its whole body under the
+    guard, before touching any argument (the calls pass NULL and zero for everything)."""
+    raw = ctypes.CDLL(build.LIB)  # a handle without the binding's argument types
+    raw.dba_last_error.restype = ctypes.c_char_p
+    raw.dba_block_last_error.restype = ctypes.c_char_p
+    raw.dba_mlp_last_error.restype = ctypes.c_char_p
+    entries = [e for e in _status_entry_points() if e[0] != "dba_inject_host_alloc_failure"]
+    assert len(entries) >= 30
+    for name, args in entries:
+        assert raw.dba_inject_host_alloc_failure(1) == dba.DBA_OK
+        assert getattr(raw, name)(*args) == dba.DBA_ENOMEM, name
+        # the injection is used up: the same call now fails on its NULL arguments instead
+        assert getattr(raw, name)(*args) != dba.DBA_ENOMEM, name
+    assert raw.dba_inject_host_alloc_failure(1) == dba.DBA_OK
+    assert raw.dba_create(None, None) == dba.DBA_ENOMEM
+    assert raw.dba_last_error(None) == b"out of host memory"
+    assert raw.dba_inject_host_alloc_failure(1) == dba.DBA_OK
+    assert raw.dba_block_create(None, 1, 1, None) == dba.DBA_ENOMEM
+    assert raw.dba_block_last_error(None) == b"out of host memory"
+    assert raw.dba_inject_host_alloc_failure(-1) == dba.DBA_EINVAL
+    assert raw.dba_inject_host_alloc_failure(0) == dba.DBA_OK
+
+
+def test_host_layout_reports_enomem_and_recovers(lib):
+    """A host-only entry point with real work: injected failure, then the same call succeeds."""
+    import numpy as np
+
+    pt = np.array([0, 0, 1, 1], np.int32)
+    cam = np.array([0, 1, 0, 1], np.int32)
+    n_tiles = ctypes.c_int64(0)
+    i32 = ctypes.POINTER(ctypes.c_int32)
+    raw = ctypes.CDLL(build.LIB)
+    raw.dba_inject_host_alloc_failure(1)
+    args = (2, 2, ctypes.c_int64(4), pt.ctypes.data_as(i32), cam.ctypes.data_as(i32), 64, None, None, None, None,
+            None, ctypes.byref(n_tiles))
+    assert raw.dba_build_layout(*args) == dba.DBA_ENOMEM
+    assert raw.dba_build_layout(*args) == dba.DBA_OK and n_tiles.value == 1
