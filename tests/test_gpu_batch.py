@@ -3,6 +3,7 @@ iteration) against the oracle run scene by scene; per-scene metrics; the
 tile-size autotuner."""
 import numpy as np
 import pytest
+from parity import colerr
 
 import oracle as O
 from paper_1708_07954_gb300 import build, dba
@@ -58,7 +59,7 @@ def test_batch_fp64_matches_oracle_scene_by_scene():
         m = st.iterate(cfg, 4)
         c0, c1 = batch.cam_off[k], batch.cam_off[k + 1]
         p0, p1 = batch.pt_off[k], batch.pt_off[k + 1]
-        assert relerr(cams[c0:c1], st.cams) <= TOL64 and relerr(pts[p0:p1], st.pts) <= TOL64, k
+        assert colerr(cams[c0:c1], st.cams) <= TOL64 and colerr(pts[p0:p1], st.pts) <= TOL64, k
         assert abs(stats["rmse_obs"][k] - m["rmse_obs"]) <= 1e-8 * m["rmse_obs"]
         assert abs(stats["objective"][k] - m["objective"]) <= 1e-8 * m["objective"]
         assert abs(stats["rmse_gt"][k] - m["rmse_gt"]) <= 1e-8 * max(m["rmse_gt"], 1e-12)
@@ -80,8 +81,8 @@ def test_autotuned_tile_matches_fixed_tile():
         assert a.layout()["tile_obs"] in (64, 128, 256)
         a.iterate(5, stats=False)
         b.iterate(5, stats=False)
-        assert relerr(a.params()[0], b.params()[0]) <= TOL64
-        assert relerr(a.params()[1], b.params()[1]) <= TOL64
+        assert colerr(a.params()[0], b.params()[0]) <= TOL64
+        assert colerr(a.params()[1], b.params()[1]) <= TOL64
 
 
 def test_set_scenes_rejects_an_observation_leaving_its_scene():

@@ -1,6 +1,7 @@
 """The L-BFGS local solver (Sec. 3.1) on the GPU against the oracle's L-BFGS."""
 import numpy as np
 import pytest
+from parity import colerr
 
 import oracle as O
 from paper_1708_07954_gb300 import build, dba
@@ -41,8 +42,8 @@ def test_fp64_lbfgs_matches_oracle_per_iteration(tile, loss):
             mg = s.iterate(1)
             mo = st.iterate(cfg, 1)
             cams, pts = s.params()
-            assert relerr(cams, st.cams) <= TOL64, it
-            assert relerr(pts, st.pts) <= TOL64, it
+            assert colerr(cams, st.cams) <= TOL64, it
+            assert colerr(pts, st.pts) <= TOL64, it
             assert abs(mg["objective"] - mo["objective"]) <= 1e-8 * mo["objective"]
 
 
@@ -55,7 +56,7 @@ def test_fp64_lbfgs_ring_scene_many_iterations():
             s.iterate(chunk, stats=False)
             st.iterate(cfg, chunk)
             cams, pts = s.params()
-            assert relerr(cams, st.cams) <= TOL64 and relerr(pts, st.pts) <= TOL64
+            assert colerr(cams, st.cams) <= TOL64 and colerr(pts, st.pts) <= TOL64
 
 
 def test_fp32_lbfgs_tracks_the_fp64_oracle():

@@ -6,13 +6,14 @@ up front), or they run inside graph-replayed or real-time loops where an
 allocation would stall or fail.  This entry point takes the caller's device
 buffers and keeps its partial sums in a fixed file-scope device array.  These
 tests call it through the C ABI on device buffers the test owns and compare
-it with the context-based dba_evaluate on the same parameters, twice in a row
-(the scratch array is shared by all calls and reused).  The file is named so
+it with the context-based dba_evaluate and with the FP64 CPU oracle on the same
+parameters, twice in a row (the scratch array is shared by all calls and reused).  The file is named so
 that pytest collects it last.
 """
 import numpy as np
 import pytest
 
+import oracle as O
 from paper_1708_07954_gb300 import build, dba
 from paper_1708_07954_gb300 import scenes as S
 
@@ -52,6 +53,11 @@ def test_evaluate_noalloc_matches_context_evaluation_twice():
         assert o[2] + o[3] == sc.n_obs and o[3] == ref["n_invalid"]
         assert abs(np.sqrt(o[0] / o[2]) - ref["rmse_obs"]) <= TOL * ref["rmse_obs"]
         assert abs(o[1] - ref["objective"]) <= TOL * ref["objective"]
+        # and, independently of the library, against the FP64 CPU oracle at the same parameters
+        ora = O.State(sc, cams=cams, pts=pts).metrics(O.config_for(sc), with_gt=False)
+        assert o[3] == ora["n_invalid"]
+        assert abs(np.sqrt(o[0] / o[2]) - ora["rmse_obs"]) <= TOL * ora["rmse_obs"]
+        assert abs(o[1] - ora["objective"]) <= TOL * ora["objective"]
 
 
 def test_evaluate_noalloc_rejects_sizes_beyond_its_scratch():
