@@ -474,7 +474,7 @@ def run_ours(args, rank, world, local_rank):
                     wall = time.perf_counter() - t0
                 ttt[name] = {"seconds": m["seconds"], "wall_seconds": wall, "iters": m["iters_done"],
                              "rmse_gt": m["rmse_gt"], "reached": m["rmse_gt"] <= 0.5, "inner_steps": 1}
-            ttt["fp32_learned"]["network"] = "32-64-64-64-16 ReLU MLP, BF16 tcgen05 inference, FP32 accumulation"
+            ttt["fp32_learned"]["network"] = "32-64-64-64-16 GELU MLP, BF16 tcgen05 inference, FP32 accumulation"
             mlp.close()
         for a, b in (("fp32_plain", "fp64_plain"), ("fp32_learned", "fp64_plain"), ("fp32_learned", "fp32_plain"),
                      ("fp32_learned", "fp32_plain_1step")):

@@ -271,7 +271,7 @@ dba_status dba_evaluate_noalloc(const dba_config* cfg, int32_t n_cams, int32_t n
                                 const double* cams, const double* pts, double* out, void* stream);
 
 /* ---- Learned warm start (no counterpart in the paper) ------------------------------------
- * A small network (32-64-64-64-16, ReLU) predicts, for every observation, a start for its
+ * A small network (32-64-64-64-16, GELU) predicts, for every observation, a start for its
  * local solve (Eq. 9) from the residual, Jacobian, offset and dual at the plain start, all in
  * coordinates scaled by sqrt(rho).  Inference runs on BF16 tensor cores (tcgen05, FP32
  * accumulation) before each iteration's local solves; each local solve starts from the

@@ -1,10 +1,10 @@
 // Learned warm start for the local solves (no counterpart in the paper).
 //
-// A 32-64-64-64-16 ReLU network maps the features of one local problem
+// A 32-64-64-64-16 GELU network maps the features of one local problem
 // (warm_features in dba_device.cuh) to the scaled step r (d* - d0) towards the
 // solution of a long local solve.  This unit holds
 //   - harvest_kernel: features and targets from the current ADMM state;
-//   - FP32 training kernels (tiled SGEMM, ReLU, loss, Adam);
+//   - FP32 training kernels (tiled SGEMM, GELU, loss, Adam);
 //   - mlp_infer_kernel: BF16 tensor-core inference with tcgen05.mma (operands
 //     in shared memory, FP32 accumulators in tensor memory), either on given
 //     features or fused with feature extraction from the ADMM state, writing a
@@ -81,8 +81,28 @@ __global__ void harvest_kernel(DevProblem P, Prm<T> q, int pending, long long st
   for (int c = 0; c < kMlpOut; ++c) g[c] = (ok && c < 9) ? (float)(r[c] * (d[c] - d0[c])) : 0.f;
 }
 
+// ------------------------------------------------------------ activation
+// GELU in its tanh form (Hendrycks and Gimpel): x/2 (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3))).
+constexpr float kGeluC = 0.7978845608028654f;  // sqrt(2/pi)
+constexpr float kGeluA = 0.044715f;
+// training: CUDA's tanhf
+__device__ __forceinline__ float gelu(float x) {
+  return 0.5f * x * (1.f + tanhf(kGeluC * fmaf(kGeluA * x * x, x, x)));
+}
+__device__ __forceinline__ float gelu_grad(float x) {
+  const float t = tanhf(kGeluC * fmaf(kGeluA * x * x, x, x));
+  return 0.5f * (1.f + t) + 0.5f * x * (1.f - t * t) * kGeluC * fmaf(3.f * kGeluA, x * x, 1.f);
+}
+// inference: the SFU tanh (PTX tanh.approx.f32, relative error about 2^-11, well below the
+// BF16 rounding of the activations that follows)
+__device__ __forceinline__ float gelu_fast(float x) {
+  float t;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(kGeluC * fmaf(kGeluA * x * x, x, x)));
+  const float h = 0.5f * x;
+  return fmaf(h, t, h);
+}
+
 // ------------------------------------------------------------ training (FP32)
-__device__ __forceinline__ float relu(float x) { return fmaxf(x, 0.f); }
 
 // C[M x N] = op(A) op(B) (+ C if accumulate), row-major; op(A) is M x K, op(B) K x N.
 constexpr int kGemmTile = 16;
@@ -130,13 +150,13 @@ __global__ void gather_targets_kernel(const float* Y, const int* idx, int n, con
   const long long src = idx ? idx[r] : r;
   out[e] = Y[src * kMlpOut + c] / params[kOutStd + c];
 }
-// Z += bias (per column); H = ReLU(Z) when H != nullptr
+// Z += bias (per column); H = GELU(Z) when H != nullptr
 __global__ void bias_act_kernel(float* Z, const float* bias, int n, int width, float* H) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n * width) return;
   const float z = Z[e] + bias[e % width];
   Z[e] = z;
-  if (H) H[e] = relu(z);
+  if (H) H[e] = gelu(z);
 }
 // dY = 2 (Y - T) / (n * 9) on the 9 used outputs; loss partial sums
 __global__ void loss_grad_kernel(const float* Y, const float* Tt, int n, float* dY, double* loss) {
@@ -151,10 +171,10 @@ __global__ void loss_grad_kernel(const float* Y, const float* Tt, int n, float* 
   for (int w = 16; w > 0; w >>= 1) l += __shfl_down_sync(0xffffffffu, l, w);
   if ((threadIdx.x & 31) == 0) atomicAdd(loss, l / (double)(n * kMlpUsedOut));
 }
-// dZ = dH * ReLU'(Z)
-__global__ void relu_back_kernel(const float* dH, const float* Z, int total, float* dZ) {
+// dZ = dH * GELU'(Z)
+__global__ void act_back_kernel(const float* dH, const float* Z, int total, float* dZ) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e < total) dZ[e] = Z[e] > 0.f ? dH[e] : 0.f;
+  if (e < total) dZ[e] = dH[e] * gelu_grad(Z[e]);
 }
 // column sums of dZ into grad (bias gradient)
 __global__ void colsum_kernel(const float* dZ, int n, int width, float* out) {
@@ -281,15 +301,15 @@ cudaError_t mlp_forward_backward(dba_mlp* m, int n) {
   sgemm(s, kMlpOut, H, n, m->dy, kMlpOut, true, m->h3, H, false, G + kW4, H);    // dW4 = dY^T H3
   colsum_kernel<<<kMlpOut, 256, 0, s>>>(m->dy, n, kMlpOut, G + kB4);
   sgemm(s, n, H, kMlpOut, m->dy, kMlpOut, false, P + kW4, H, false, m->d64a, H);  // dH3 = dY W4
-  relu_back_kernel<<<blocks_for((long long)n * H, 256), 256, 0, s>>>(m->d64a, m->z3, n * H, m->d64b);
+  act_back_kernel<<<blocks_for((long long)n * H, 256), 256, 0, s>>>(m->d64a, m->z3, n * H, m->d64b);
   sgemm(s, H, H, n, m->d64b, H, true, m->h2, H, false, G + kW3, H);              // dW3 = dZ3^T H2
   colsum_kernel<<<H, 256, 0, s>>>(m->d64b, n, H, G + kB3);
   sgemm(s, n, H, H, m->d64b, H, false, P + kW3, H, false, m->d64a, H);           // dH2 = dZ3 W3
-  relu_back_kernel<<<blocks_for((long long)n * H, 256), 256, 0, s>>>(m->d64a, m->z2, n * H, m->d64b);
+  act_back_kernel<<<blocks_for((long long)n * H, 256), 256, 0, s>>>(m->d64a, m->z2, n * H, m->d64b);
   sgemm(s, H, H, n, m->d64b, H, true, m->h1, H, false, G + kW2, H);              // dW2 = dZ2^T H1
   colsum_kernel<<<H, 256, 0, s>>>(m->d64b, n, H, G + kB2);
   sgemm(s, n, H, H, m->d64b, H, false, P + kW2, H, false, m->d64a, H);           // dH1 = dZ2 W2
-  relu_back_kernel<<<blocks_for((long long)n * H, 256), 256, 0, s>>>(m->d64a, m->z1, n * H, m->d64b);
+  act_back_kernel<<<blocks_for((long long)n * H, 256), 256, 0, s>>>(m->d64a, m->z1, n * H, m->d64b);
   sgemm(s, H, kMlpIn, n, m->d64b, H, true, m->x, kMlpIn, false, G + kW1, kMlpIn);  // dW1 = dZ1^T X
   colsum_kernel<<<H, 256, 0, s>>>(m->d64b, n, H, G + kB1);
   return cudaGetLastError();
@@ -401,7 +421,7 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   return *reinterpret_cast<const uint32_t*>(&p);
 }
 
-// Hidden layer epilogue: bias + ReLU of the accumulator row, BF16 into the
+// Hidden layer epilogue: bias + GELU of the accumulator row, BF16 into the
 // activation tile; 16 columns at a time, two 16-byte stores per 16 columns (the
 // 8 rows of a core matrix fill 128 contiguous bytes: no bank conflicts).
 __device__ __forceinline__ void hidden_epilogue(uint32_t trow, const float* bias, unsigned char* act, int row) {
@@ -413,10 +433,10 @@ __device__ __forceinline__ void hidden_epilogue(uint32_t trow, const float* bias
     for (int half = 0; half < 2; ++half) {
       const int c = c0 + 8 * half;
       uint4 v;
-      v.x = pack_bf16x2(relu(h[8 * half + 0] + bias[c + 0]), relu(h[8 * half + 1] + bias[c + 1]));
-      v.y = pack_bf16x2(relu(h[8 * half + 2] + bias[c + 2]), relu(h[8 * half + 3] + bias[c + 3]));
-      v.z = pack_bf16x2(relu(h[8 * half + 4] + bias[c + 4]), relu(h[8 * half + 5] + bias[c + 5]));
-      v.w = pack_bf16x2(relu(h[8 * half + 6] + bias[c + 6]), relu(h[8 * half + 7] + bias[c + 7]));
+      v.x = pack_bf16x2(gelu_fast(h[8 * half + 0] + bias[c + 0]), gelu_fast(h[8 * half + 1] + bias[c + 1]));
+      v.y = pack_bf16x2(gelu_fast(h[8 * half + 2] + bias[c + 2]), gelu_fast(h[8 * half + 3] + bias[c + 3]));
+      v.z = pack_bf16x2(gelu_fast(h[8 * half + 4] + bias[c + 4]), gelu_fast(h[8 * half + 5] + bias[c + 5]));
+      v.w = pack_bf16x2(gelu_fast(h[8 * half + 6] + bias[c + 6]), gelu_fast(h[8 * half + 7] + bias[c + 7]));
       *reinterpret_cast<uint4*>(act + kmajor_off(row, c, kMlpHidden)) = v;
     }
   }

@@ -355,12 +355,21 @@ def test_mlp_reference_gradient_matches_finite_differences():
     assert np.all(g[OM.N_TRAINABLE:] == 0)
 
 
-def test_mlp_reference_relu_and_its_derivative():
+def test_mlp_reference_gelu_and_its_derivative():
+    """The tanh form of GELU stays within 5e-4 of its definition x Phi(x) (Phi the standard
+    normal CDF, here through scipy's erf), has the limits 0 and x, and its derivative matches
+    central differences."""
     import oracle.mlp as OM
+    from scipy.special import erf
 
-    z = np.array([-3.0, -1e-300, 0.0, 1e-300, 0.7, 2.5])
-    assert np.array_equal(OM.relu(z), [0.0, 0.0, 0.0, 1e-300, 0.7, 2.5])
-    assert np.array_equal(OM.relu_grad(z), [0.0, 0.0, 0.0, 1.0, 1.0, 1.0])
+    z = np.linspace(-8.0, 8.0, 4001)
+    exact = 0.5 * z * (1.0 + erf(z / np.sqrt(2.0)))
+    assert np.abs(OM.gelu(z) - exact).max() < 5e-4
+    assert OM.gelu(np.array([0.0]))[0] == 0.0
+    assert abs(OM.gelu(np.array([30.0]))[0] - 30.0) < 1e-12 and abs(OM.gelu(np.array([-30.0]))[0]) < 1e-12
+    h = 1e-6
+    fd = (OM.gelu(z + h) - OM.gelu(z - h)) / (2 * h)
+    assert np.abs(OM.gelu_grad(z) - fd).max() < 1e-8
 
 
 # --------------------------------------------- L-BFGS local solver (Sec. 3.1)
