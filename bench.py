@@ -160,7 +160,9 @@ def algorithmic_bytes(scene, layout, fp32):
 
 # FP32 operations of the method per observation and ADMM iteration, counted from the
 # tile kernel's arithmetic (add/sub/mul 1, fma 2, rcp/sqrt/sin/cos 1), every Gauss-Newton
-# step counted as a full step with its trial objective:
+# step counted as a full step with its trial objective (the kernel skips only the trial
+# objective of a last step that every lane of a warp accepts by the noise rule, whose value
+# is never read: the count is at most 58 / 2684 = 2.2 % above the executed flops):
 #   start: copy + pose + objective 111, first damping 50, deferred dual re-base 9, run sums 9;
 #   per step: linearisation and Jacobian 64, gradient 64, damping reciprocals 6,
 #   capacitance terms 126, 2x2 solve 17, step + model decrease 96, noise bound 7,

@@ -521,60 +521,127 @@ __global__ void camera_pose_kernel(DevProblem P) {
 // Metrics at consensus: sums of |e|^2, phi_m, |f - z_true|^2 (inliers), valid / invalid
 // counts, primal and dual residual terms, reference count.  kGtOnly: only the reference
 // sums and the counts (the stopping test of dba_iterate_until).
+//
+// One observation's terms, added to acc (summed in T: a thread's own observations are a few
+// dozen; the FP64 pipe sees one conversion and add per sum and thread in the reduction).
+template <typename T, bool kGtOnly>
+__device__ __forceinline__ void metric_terms(const DevProblem& P, const Prm<T>& q, int i, int j,
+                                             typename Num<T>::V2 zz, typename Num<T>::V2 gt, bool counted,
+                                             T acc[8]) {
+  const T* Xm = static_cast<const T*>(P.Xm);
+  const T* pose = static_cast<const T*>(P.cam_pose);
+  const T x0 = Xm[3 * i], x1 = Xm[3 * i + 1], x2 = Xm[3 * i + 2];
+  const T* Rt = pose + 12 * (long long)j;
+  const T p0 = Rt[0] * x0 + Rt[1] * x1 + Rt[2] * x2 + Rt[9];
+  const T p1 = Rt[3] * x0 + Rt[4] * x1 + Rt[5] * x2 + Rt[10];
+  const T p2 = Rt[6] * x0 + Rt[7] * x1 + Rt[8] * x2 + Rt[11];
+  if (p2 > q.eps) {
+    const T iz = T(1) / p2;
+    const T zp0 = q.focal * p0 * iz + q.cx, zp1 = q.focal * p1 * iz + q.cy;
+    if (!kGtOnly) {
+      const T e0 = zz.x - zp0, e1 = zz.y - zp1;
+      const T s = e0 * e0 + e1 * e1;
+      acc[0] += s;
+      acc[1] += misfit<T>(q.loss, q.lp, s);
+    }
+    if (P.zt && counted) {
+      const T g0 = zp0 - gt.x, g1 = zp1 - gt.y;
+      acc[2] += g0 * g0 + g1 * g1;
+      acc[7] += T(1);
+    }
+    acc[3] += T(1);
+  } else {
+    acc[4] += T(1);
+  }
+}
+
+// Primal and dual residual terms of one copy coordinate c: the copy relative to the current
+// consensus (the stored offset plus the pending consensus change) and rho times that change.
+template <typename T>
+__device__ __forceinline__ void residual_terms(const DevProblem& P, const Prm<T>& q, int pending, int c, int i,
+                                               int j, T offset, T acc[8]) {
+  const T dc = c < 3 ? static_cast<const T*>(P.DX)[3 * i + c] : static_cast<const T*>(P.DY)[6 * j + c - 3];
+  const T cp = offset + (pending ? dc : T(0));
+  const T rd = q.rho(c) * dc;
+  acc[5] += cp * cp;
+  acc[6] += rd * rd;
+}
+
+// four consecutive pixel pairs from a 16-byte aligned address
+__device__ __forceinline__ void load4(const float2* p, float2 v[4]) {
+  const float4 a = reinterpret_cast<const float4*>(p)[0], b = reinterpret_cast<const float4*>(p)[1];
+  v[0] = make_float2(a.x, a.y);
+  v[1] = make_float2(a.z, a.w);
+  v[2] = make_float2(b.x, b.y);
+  v[3] = make_float2(b.z, b.w);
+}
+__device__ __forceinline__ void load4(const double2* p, double2 v[4]) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) v[k] = p[k];
+}
+// four consecutive elements of a copy row (16-byte aligned)
+__device__ __forceinline__ void load4(const float* p, float v[4]) {
+  const float4 a = *reinterpret_cast<const float4*>(p);
+  v[0] = a.x;
+  v[1] = a.y;
+  v[2] = a.z;
+  v[3] = a.w;
+}
+__device__ __forceinline__ void load4(const double* p, double v[4]) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+  v[0] = a.x;
+  v[1] = a.y;
+  v[2] = b.x;
+  v[3] = b.y;
+}
+
+// Each thread takes four consecutive observations per pass with vector loads of their
+// indices, pixels, reference pixels, inlier flags and copy rows (every array starts 256-byte
+// aligned and the copy rows' pitch is a multiple of 32 elements), so four independent
+// gathers of consensus points and camera poses are in flight per thread.
 template <typename T, bool kGtOnly>
 __global__ void __launch_bounds__(kMetricThreads) metrics_kernel(DevProblem P, Prm<T> q, int pending) {
   using V2 = typename Num<T>::V2;
   __shared__ double red[8][kMetricThreads];
   const long long l = P.n_obs;
-  const T* Xm = static_cast<const T*>(P.Xm);
-  const T* DX = static_cast<const T*>(P.DX);
-  const T* DY = static_cast<const T*>(P.DY);
   const T* delta = static_cast<const T*>(P.delta);
-  const T* pose = static_cast<const T*>(P.cam_pose);
-  // a thread's own observations (a few dozen) are summed in T; the FP64 pipe sees one
-  // conversion and add per sum and thread, then the FP64 block and grid reductions
+  const V2* z = static_cast<const V2*>(P.z);
+  const V2* zt = static_cast<const V2*>(P.zt);
   T acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (long long o = blockIdx.x * (long long)kMetricThreads + threadIdx.x; o < l;
-       o += (long long)gridDim.x * kMetricThreads) {
-    const int i = P.obs_pt[o], j = P.obs_cam_rank[o] & kCamMask;
-    const T x0 = Xm[3 * i], x1 = Xm[3 * i + 1], x2 = Xm[3 * i + 2];
-    const T* Rt = pose + 12 * (long long)j;
-    const T p0 = Rt[0] * x0 + Rt[1] * x1 + Rt[2] * x2 + Rt[9];
-    const T p1 = Rt[3] * x0 + Rt[4] * x1 + Rt[5] * x2 + Rt[10];
-    const T p2 = Rt[6] * x0 + Rt[7] * x1 + Rt[8] * x2 + Rt[11];
-    if (p2 > q.eps) {
-      const T iz = T(1) / p2;
-      const T zp0 = q.focal * p0 * iz + q.cx, zp1 = q.focal * p1 * iz + q.cy;
-      if (!kGtOnly) {
-        const V2 zz = static_cast<const V2*>(P.z)[o];
-        const T e0 = zz.x - zp0, e1 = zz.y - zp1;
-        const T s = e0 * e0 + e1 * e1;
-        acc[0] += s;
-        acc[1] += misfit<T>(q.loss, q.lp, s);
-      }
-      if (P.zt && (!P.inlier || P.inlier[o])) {
-        const V2 gt = static_cast<const V2*>(P.zt)[o];
-        const T g0 = zp0 - gt.x, g1 = zp1 - gt.y;
-        acc[2] += g0 * g0 + g1 * g1;
-        acc[7] += T(1);
-      }
-      acc[3] += T(1);
-    } else {
-      acc[4] += T(1);
-    }
+  const long long n4 = l / 4, stride = (long long)gridDim.x * kMetricThreads;
+  for (long long g = blockIdx.x * (long long)kMetricThreads + threadIdx.x; g < n4; g += stride) {
+    const long long o = 4 * g;
+    const int4 pi = *reinterpret_cast<const int4*>(P.obs_pt + o);
+    const int4 ci = *reinterpret_cast<const int4*>(P.obs_cam_rank + o);
+    const int ii[4] = {pi.x, pi.y, pi.z, pi.w};
+    const int jj[4] = {ci.x & kCamMask, ci.y & kCamMask, ci.z & kCamMask, ci.w & kCamMask};
+    V2 zz[4] = {}, gt[4] = {};
+    if (!kGtOnly) load4(z + o, zz);
+    if (zt) load4(zt + o, gt);
+    unsigned int inl = 0x01010101u;
+    if (P.inlier) inl = *reinterpret_cast<const unsigned int*>(P.inlier + o);
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      metric_terms<T, kGtOnly>(P, q, ii[k], jj[k], zz[k], gt[k], ((inl >> (8 * k)) & 0xffu) != 0, acc);
     if (!kGtOnly) {
-      T pr = 0, dr = 0;
 #pragma unroll
       for (int c = 0; c < 9; ++c) {
-        const T dc = c < 3 ? DX[3 * i + c] : DY[6 * j + c - 3];
-        const T cp = delta[c * P.pitch + o] + (pending ? dc : T(0));
-        const T rho = q.rho(c);
-        pr += cp * cp;
-        dr += (rho * dc) * (rho * dc);
+        T v[4];
+        load4(delta + c * P.pitch + o, v);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) residual_terms<T>(P, q, pending, c, ii[k], jj[k], v[k], acc);
       }
-      acc[5] += pr;
-      acc[6] += dr;
     }
+  }
+  // the last l mod 4 observations
+  for (long long o = 4 * n4 + blockIdx.x * (long long)kMetricThreads + threadIdx.x; o < l; o += stride) {
+    const int i = P.obs_pt[o], j = P.obs_cam_rank[o] & kCamMask;
+    const V2 zz = kGtOnly ? V2{} : z[o];
+    const V2 gt = zt ? zt[o] : V2{};
+    metric_terms<T, kGtOnly>(P, q, i, j, zz, gt, !P.inlier || P.inlier[o], acc);
+    if (!kGtOnly)
+#pragma unroll
+      for (int c = 0; c < 9; ++c) residual_terms<T>(P, q, pending, c, i, j, delta[c * P.pitch + o], acc);
   }
   for (int k = 0; k < 8; ++k) red[k][threadIdx.x] = to_f64<T>(acc[k]);
   __syncthreads();
