@@ -579,6 +579,310 @@ __device__ void solve_block(const BlockProblem& B, const Prm<T>& q, const BlockI
   grp.sync();
 }
 
+// ------------------------------------------------------------ one-camera blocks
+// A block with a single camera (every block when block_cams = 1; the 8-lane class always)
+// has a 6 x 6 reduced camera system.  It is solved without shared memory: each lane forms
+// the terms of its point copies (each holds the block's one observation of its point), a
+// butterfly over the group sums them, and every lane factors the system in registers.  A
+// butterfly stage adds the same two partial sums on both lanes of a pair (addition is
+// commutative), so all lanes end with the same bits and take the same step, acceptance
+// and damping.  Same arithmetic as solve_block: points eliminated by their 3x3 inverses,
+// Schur weights Q = 2w I - (2w)^2 A W_p A^T, right-hand side sum B^T U - g_c.
+template <typename T, int G, int PPL>
+struct OneCam {
+  const Grp<G>& grp;
+  const Prm<T>& q;
+  T cb[6], ca[6];                    // camera consensus and scaled dual
+  bool act[PPL];
+  T xb[PPL][3], ax[PPL][3], z0[PPL], z1[PPL];
+  __device__ OneCam(const Grp<G>& g, const Prm<T>& qq) : grp(g), q(qq) {}
+
+  // Eq. (14) at point offsets dp and camera offset dc, summed over the group; +inf when an
+  // observation is behind the camera
+  __device__ T objective(const T (&dp)[PPL][3], const T (&dc)[6]) const {
+    T s = 0;
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < PPL; ++j) {
+      if (!act[j]) continue;
+      T v[9];
+#pragma unroll
+      for (int u = 0; u < 3; ++u) v[u] = xb[j][u] + dp[j][u];
+#pragma unroll
+      for (int u = 0; u < 6; ++u) v[3 + u] = cb[u] + dc[u];
+      Pose<T> P;
+      pose_at(v, q.eps, P);
+      if (!P.valid) {
+        ok = false;
+      } else {
+        const T iz = Num<T>::rcp(P.p[2]);
+        const T e0 = z0[j] - (q.focal * P.p[0] * iz + q.cx);
+        const T e1 = z1[j] - (q.focal * P.p[1] * iz + q.cy);
+        s += misfit<T>(q.loss, q.lp, e0 * e0 + e1 * e1);
+      }
+#pragma unroll
+      for (int u = 0; u < 3; ++u) s += q.rho_x * dp[j][u] * (ax[j][u] + T(0.5) * dp[j][u]);
+    }
+    s = grp.sum(s);
+    ok = grp.all(ok);
+    T sc = 0;
+#pragma unroll
+    for (int u = 0; u < 6; ++u) sc += q.rho(3 + u) * dc[u] * (ca[u] + T(0.5) * dc[u]);
+    return ok ? s + sc : Num<T>::inf();
+  }
+};
+
+template <typename T, int G>
+__device__ void solve_block_1cam(const BlockProblem& B, const Prm<T>& q, const BlockInfo& bi, const Grp<G>& grp,
+                                 int cur) {
+  constexpr int PPL = 1;  // one point copy per lane (blocks of at most 32 points)
+  using V2 = typename Num<T>::V2;
+  const int gl = grp.gl, np = bi.np;
+  T* pdel = static_cast<T*>(B.pc_delta);
+  T* cdel = static_cast<T*>(B.cc_delta);
+  OneCam<T, G, PPL> K(grp, q);
+  T cd[6], dp[PPL][3];
+  const long long cc = bi.c0;
+  {
+    const int jc = B.cc_cam[cc];
+#pragma unroll
+    for (int u = 0; u < 6; ++u) {
+      K.cb[u] = from_f64<T>(B.Y[cur][6 * (long long)jc + u]);
+      cd[u] = cdel[u * B.n_cc + cc];
+      K.ca[u] = from_f64<T>(B.cc_a[u * B.n_cc + cc]);
+    }
+  }
+  const long long pc = (long long)bi.p0 + gl;
+  K.act[0] = gl < np;
+  K.z0[0] = K.z1[0] = 0;
+#pragma unroll
+  for (int u = 0; u < 3; ++u) K.xb[0][u] = K.ax[0][u] = dp[0][u] = 0;
+  if (K.act[0]) {
+    const int i = B.pc_pt[pc];
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      K.xb[0][u] = from_f64<T>(B.X[cur][3 * (long long)i + u]);
+      dp[0][u] = pdel[u * B.n_pc + pc];
+      K.ax[0][u] = from_f64<T>(B.pc_a[u * B.n_pc + pc]);
+    }
+    const V2 z = static_cast<const V2*>(B.z)[B.pc_obs[pc]];  // the copy's one observation
+    K.z0[0] = z.x;
+    K.z1[0] = z.y;
+  }
+  T L = K.objective(dp, cd);
+  T lambda = T(-1);
+  for (int step = 0; step < q.steps; ++step) {
+    // linearisation of this lane's observation at the current copies
+    T J0[9], J1[9], tw = 0, e0 = 0, e1 = 0;
+    {
+      T v[9], w = 0;
+#pragma unroll
+      for (int u = 0; u < 3; ++u) v[u] = K.xb[0][u] + dp[0][u];
+#pragma unroll
+      for (int u = 0; u < 6; ++u) v[3 + u] = K.cb[u] + cd[u];
+      Pose<T> P;
+      pose_at(v, q.eps, P);
+      if (K.act[0] && P.valid) {
+        linearize(P, K.z0[0], K.z1[0], q, J0, J1, e0, e1, w);
+      } else {
+#pragma unroll
+        for (int u = 0; u < 9; ++u) J0[u] = J1[u] = 0;
+      }
+      tw = T(2) * w;
+    }
+    // point block of H, point gradient, camera misfit gradient, noise scale
+    const T h00 = tw * (J0[0] * J0[0] + J1[0] * J1[0]), h01 = tw * (J0[0] * J0[1] + J1[0] * J1[1]),
+            h02 = tw * (J0[0] * J0[2] + J1[0] * J1[2]), h11 = tw * (J0[1] * J0[1] + J1[1] * J1[1]),
+            h12 = tw * (J0[1] * J0[2] + J1[1] * J1[2]), h22 = tw * (J0[2] * J0[2] + J1[2] * J1[2]);
+    T gp[3], gc[6];
+#pragma unroll
+    for (int u = 0; u < 3; ++u)
+      gp[u] = K.act[0] ? -tw * (J0[u] * e0 + J1[u] * e1) + q.rho_x * (K.ax[0][u] + dp[0][u]) : T(0);
+#pragma unroll
+    for (int u = 0; u < 6; ++u) gc[u] = -tw * (J0[3 + u] * e0 + J1[3 + u] * e1);
+    T noise = tw * Num<T>::sqrt_(e0 * e0 + e1 * e1) * (fabs(K.z0[0]) + fabs(K.z1[0]));
+    if (lambda < T(0)) {
+      T trc = K.act[0] ? h00 + h11 + h22 + T(3) * q.rho_x : T(0);
+#pragma unroll
+      for (int u = 3; u < 9; ++u) trc += tw * (J0[u] * J0[u] + J1[u] * J1[u]);
+      T tr = grp.sum(trc);
+#pragma unroll
+      for (int u = 0; u < 6; ++u) tr += q.rho(3 + u);
+      lambda = q.lambda0 * tr / T(3 * np + 6);
+    }
+    // W_p = (H_pp + (rho_x + lambda) I)^-1 by cofactors
+    T w6[6];
+    {
+      const T dg = q.rho_x + lambda;
+      const T a00 = h00 + dg, a11 = h11 + dg, a22 = h22 + dg;
+      const T c00 = a11 * a22 - h12 * h12, c01 = h02 * h12 - h01 * a22, c02 = h01 * h12 - h02 * a11;
+      const T c11 = a00 * a22 - h02 * h02, c12 = h01 * h02 - a00 * h12, c22 = a00 * a11 - h01 * h01;
+      const T idet = Num<T>::rcp(a00 * c00 + h01 * c01 + h02 * c02);
+      w6[0] = c00 * idet, w6[1] = c01 * idet, w6[2] = c02 * idet;
+      w6[3] = c11 * idet, w6[4] = c12 * idet, w6[5] = c22 * idet;
+    }
+    // this point's terms of the reduced camera system: S += B^T Q B, rhs += B^T U
+    T S[21], rhs[6];
+    {
+      const T Wg0 = w6[0] * gp[0] + w6[1] * gp[1] + w6[2] * gp[2];
+      const T Wg1 = w6[1] * gp[0] + w6[3] * gp[1] + w6[4] * gp[2];
+      const T Wg2 = w6[2] * gp[0] + w6[4] * gp[1] + w6[5] * gp[2];
+      const T w0 = w6[0] * J0[0] + w6[1] * J0[1] + w6[2] * J0[2], w1 = w6[1] * J0[0] + w6[3] * J0[1] + w6[4] * J0[2],
+              w2 = w6[2] * J0[0] + w6[4] * J0[1] + w6[5] * J0[2];
+      const T x0 = w6[0] * J1[0] + w6[1] * J1[1] + w6[2] * J1[2], x1 = w6[1] * J1[0] + w6[3] * J1[1] + w6[4] * J1[2],
+              x2 = w6[2] * J1[0] + w6[4] * J1[1] + w6[5] * J1[2];
+      const T sw = tw * tw;
+      const T q00 = tw - sw * (J0[0] * w0 + J0[1] * w1 + J0[2] * w2);
+      const T q01 = -sw * (J0[0] * x0 + J0[1] * x1 + J0[2] * x2);
+      const T q10 = -sw * (J1[0] * w0 + J1[1] * w1 + J1[2] * w2);
+      const T q11 = tw - sw * (J1[0] * x0 + J1[1] * x1 + J1[2] * x2);
+      const T U0 = tw * (J0[0] * Wg0 + J0[1] * Wg1 + J0[2] * Wg2);
+      const T U1 = tw * (J1[0] * Wg0 + J1[1] * Wg1 + J1[2] * Wg2);
+      int e = 0;
+#pragma unroll
+      for (int r = 0; r < 6; ++r) {
+        const T b0r = J0[3 + r], b1r = J1[3 + r];
+#pragma unroll
+        for (int c = r; c < 6; ++c, ++e) S[e] = b0r * (q00 * J0[3 + c] + q01 * J1[3 + c]) +
+                                                b1r * (q10 * J0[3 + c] + q11 * J1[3 + c]);
+        rhs[r] = b0r * U0 + b1r * U1;
+      }
+    }
+    // sums over the block's points (every lane receives the same bits)
+#pragma unroll
+    for (int e = 0; e < 21; ++e) S[e] = grp.sum(S[e]);
+#pragma unroll
+    for (int u = 0; u < 6; ++u) {
+      rhs[u] = grp.sum(rhs[u]);
+      gc[u] = grp.sum(gc[u]) + q.rho(3 + u) * (K.ca[u] + cd[u]);  // camera gradient with its penalty
+    }
+    noise = grp.sum(noise);
+    // (S + diag(rho_c) + lambda I) dy = rhs - g_c by a Cholesky factorisation in registers
+    T A[6][6];
+    {
+      int e = 0;
+#pragma unroll
+      for (int r = 0; r < 6; ++r)
+#pragma unroll
+        for (int c = r; c < 6; ++c, ++e) A[r][c] = A[c][r] = S[e];
+    }
+#pragma unroll
+    for (int u = 0; u < 6; ++u) A[u][u] += q.rho(3 + u) + lambda;
+    bool spd = true;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+#pragma unroll
+      for (int m = 0; m < k; ++m) A[k][k] -= A[k][m] * A[k][m];
+      spd = spd && A[k][k] > T(0);
+      const T lkk = Num<T>::sqrt_(A[k][k]);
+      A[k][k] = lkk;
+      const T ilkk = Num<T>::rcp(lkk);
+#pragma unroll
+      for (int i2 = k + 1; i2 < 6; ++i2) {
+#pragma unroll
+        for (int m = 0; m < k; ++m) A[i2][k] -= A[i2][m] * A[k][m];
+        A[i2][k] *= ilkk;
+      }
+    }
+    if (!spd) {
+      lambda *= T(10);
+      continue;
+    }
+    T dy[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      T y = rhs[k] - gc[k];
+#pragma unroll
+      for (int m = 0; m < k; ++m) y -= A[k][m] * dy[m];
+      dy[k] = Num<T>::div(y, A[k][k]);
+    }
+#pragma unroll
+    for (int k = 5; k >= 0; --k) {
+      T y = dy[k];
+#pragma unroll
+      for (int m = k + 1; m < 6; ++m) y -= A[m][k] * dy[m];
+      dy[k] = Num<T>::div(y, A[k][k]);
+    }
+    // point step dx = -W_p (g_p + 2w A^T B dy); predicted decrease (lambda |d|^2 - g.d) / 2
+    T xt[PPL][3], gd = 0, dd = 0;
+    {
+      T bd0 = 0, bd1 = 0;
+#pragma unroll
+      for (int u = 0; u < 6; ++u) {
+        bd0 += J0[3 + u] * dy[u];
+        bd1 += J1[3 + u] * dy[u];
+      }
+      T t3[3], dx[3] = {0, 0, 0};
+#pragma unroll
+      for (int u = 0; u < 3; ++u) t3[u] = gp[u] + tw * (J0[u] * bd0 + J1[u] * bd1);
+      if (K.act[0]) {
+        dx[0] = -(w6[0] * t3[0] + w6[1] * t3[1] + w6[2] * t3[2]);
+        dx[1] = -(w6[1] * t3[0] + w6[3] * t3[1] + w6[4] * t3[2]);
+        dx[2] = -(w6[2] * t3[0] + w6[4] * t3[1] + w6[5] * t3[2]);
+      }
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        gd += gp[u] * dx[u];
+        dd += dx[u] * dx[u];
+        xt[0][u] = dp[0][u] + dx[u];
+      }
+    }
+    gd = grp.sum(gd);
+    dd = grp.sum(dd);
+    T ct[6];
+#pragma unroll
+    for (int u = 0; u < 6; ++u) {
+      gd += gc[u] * dy[u];
+      dd += dy[u] * dy[u];
+      ct[u] = cd[u] + dy[u];
+    }
+    const T pred = T(0.5) * (lambda * dd - gd);
+    const bool trust = isfinite(L) && q.model_tol > T(0) &&
+                       pred <= q.model_tol * Num<T>::unit_roundoff * (fabs(L) + noise);
+    const T Lt = K.objective(xt, ct);
+    if (Lt < Num<T>::inf() && (trust || Lt < L)) {
+#pragma unroll
+      for (int u = 0; u < 3; ++u) dp[0][u] = xt[0][u];
+#pragma unroll
+      for (int u = 0; u < 6; ++u) cd[u] = ct[u];
+      L = Lt;  // Eq. (14) at the accepted point, trusted step or not
+      const T lr = Num<T>::tenth(lambda);
+      lambda = lr > q.lambda_min ? lr : q.lambda_min;
+    } else {
+      lambda *= T(10);
+    }
+  }
+  bool finite = true;
+  if (K.act[0]) {
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      pdel[u * B.n_pc + pc] = dp[0][u];
+      finite = finite && isfinite(dp[0][u]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 6; ++u)
+    if (gl == u) {
+      cdel[u * B.n_cc + cc] = cd[u];
+      finite = finite && isfinite(cd[u]);
+    }
+  if (!finite) atomicOr(B.err, 1);
+}
+
+// One-camera blocks [lo, hi) of one size class, one group of G lanes per block.
+template <typename T, int G>
+__global__ void __launch_bounds__(kBlkWarps * 32)
+    block_solve_1cam_kernel(BlockProblem B, Prm<T> q, int cur, int lo, int hi) {
+  constexpr int kPer = 32 / G;
+  const int warps = blockDim.x >> 5, warp = threadIdx.x >> 5;
+  const Grp<G> grp(threadIdx.x & 31);
+  const int stride = gridDim.x * warps * kPer;
+  for (int b = lo + (blockIdx.x * warps + warp) * kPer + grp.base / G; b < hi; b += stride) {
+    const BlockInfo bi = B.blocks[b];
+    solve_block_1cam<T, G>(B, q, bi, grp, cur);
+  }
+}
+
 // Blocks [lo, hi) of one size class, each solved by a group of G lanes holding PPL
 // point copies each (32 / G groups per warp, blockDim.x / 32 warps per CTA); groups
 // stride through the range independently.
@@ -855,10 +1159,37 @@ cudaError_t launch_block_class(dba_block_ctx* ctx, int lo, int hi) {
   return cudaGetLastError();
 }
 
+// One-camera blocks [lo, hi): the register-resident solve, groups of G lanes.
+template <typename T, int G>
+cudaError_t launch_block_class_1cam(dba_block_ctx* ctx, int lo, int hi) {
+  if (hi <= lo) return cudaSuccess;
+  constexpr int kThreads = dba::kBlkWarps * 32;
+  static std::atomic<int> cached{0};  // CTAs of a full wave
+  int grid = cached.load();
+  if (!grid) {
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dba::block_solve_1cam_kernel<T, G>,
+                                                                  kThreads, 0);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    grid = std::max(per_sm, 1) * sms;
+    cached.store(grid);
+  }
+  const int need = dba::blocks_of(hi - lo, dba::kBlkWarps * (32 / G));
+  const int g = std::max(1, std::min(need, grid));
+  dba::block_solve_1cam_kernel<T, G><<<g, kThreads, 0, ctx->stream>>>(ctx->B, dba::make_prm<T>(ctx->prm), ctx->cur,
+                                                                       lo, hi);
+  return cudaGetLastError();
+}
+
 template <typename T, int G, int PPL>
 cudaError_t launch_block_class_kc(dba_block_ctx* ctx, int k) {
   const int lo = ctx->cls[k], hi = ctx->cls[k + 1];
-  if (ctx->kappa == 1) return launch_block_class<T, 1, G, PPL>(ctx, lo, hi);
+  if (ctx->kappa == 1) {
+    if constexpr (PPL == 1) return launch_block_class_1cam<T, G>(ctx, lo, hi);
+    return launch_block_class<T, 1, G, PPL>(ctx, lo, hi);
+  }
   if constexpr (G == 16) {  // the 16-lane class holds at most 2 cameras
     return launch_block_class<T, 2, G, PPL>(ctx, lo, hi);
   } else {
@@ -869,10 +1200,11 @@ cudaError_t launch_block_class_kc(dba_block_ctx* ctx, int k) {
 
 // The size classes of the block list, in its order: one camera and at most 8 points
 // (groups of 8 lanes), at most 2 cameras and 16 points (16 lanes), at most 32 points
-// (32 lanes), the rest (32 lanes holding two point copies each).
+// (32 lanes), the rest (32 lanes holding two point copies each).  Blocks with one camera
+// (the first class; the next two when block_cams = 1) take the register-resident solve.
 template <typename T>
 cudaError_t launch_block_solve(dba_block_ctx* ctx) {
-  cudaError_t e = launch_block_class<T, 1, 8, 1>(ctx, ctx->cls[0], ctx->cls[1]);
+  cudaError_t e = launch_block_class_1cam<T, 8>(ctx, ctx->cls[0], ctx->cls[1]);
   if (e == cudaSuccess) e = launch_block_class_kc<T, 16, 1>(ctx, 1);
   if (e == cudaSuccess) e = launch_block_class_kc<T, 32, 1>(ctx, 2);
   if (e == cudaSuccess) e = launch_block_class_kc<T, 32, 2>(ctx, 3);
