@@ -68,6 +68,7 @@ struct BlockProblem {
   const int* cam_cp_off;         // [n_cams + 1]
   const int* cam_cp;
   double* sums;                  // [8] metric accumulators
+  void* cam_pose;                // [n_cams][12] T: R (row-major) and t of each consensus camera
   int* err;                      // bit 0: non-finite copy
 };
 
@@ -1011,40 +1012,61 @@ __global__ void block_dual_kernel(BlockProblem B, Prm<double> q, int cur, int wi
   }
 }
 
+// Rotation and translation of every consensus camera Y[c] (R = Rz Ry Rx, Sec. 2.1), so that
+// the metrics project each observation without evaluating its camera's angles again.
+template <typename T>
+__global__ void block_camera_pose_kernel(BlockProblem B, int c) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= B.n_cams) return;
+  T v[9] = {0, 0, 0};
+#pragma unroll
+  for (int u = 0; u < 6; ++u) v[3 + u] = from_f64<T>(B.Y[c][6 * (long long)j + u]);
+  Pose<T> P;
+  pose_at(v, T(0), P);  // x = 0: p = t
+  T* out = static_cast<T*>(B.cam_pose) + 12 * (long long)j;
+#pragma unroll
+  for (int u = 0; u < 9; ++u) out[u] = P.R[u];
+#pragma unroll
+  for (int u = 0; u < 3; ++u) out[9 + u] = v[6 + u];
+}
+
 // Reprojection terms of Eq. (2) at consensus X[c], Y[c]: sums of |e|^2, phi_m, |f - z_ref|^2
-// (reference pixels, inliers), valid, invalid and reference counts.
+// (reference pixels, inliers), valid, invalid and reference counts.  A thread's own
+// observations (a few) are summed in T, the block and grid reductions in FP64.
 template <typename T>
 __global__ void block_metrics_kernel(BlockProblem B, Prm<T> q, int c) {
   __shared__ double red[6][256];
   using V2 = typename Num<T>::V2;
-  double acc[6] = {0, 0, 0, 0, 0, 0};
+  const T* pose = static_cast<const T*>(B.cam_pose);
+  T acc[6] = {0, 0, 0, 0, 0, 0};
   for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < B.n_obs;
        o += (long long)gridDim.x * blockDim.x) {
     const int i = B.obs_pt[o], j = B.obs_cam[o];
-    T v[9];
-    for (int u = 0; u < 3; ++u) v[u] = from_f64<T>(B.X[c][3 * (long long)i + u]);
-    for (int u = 0; u < 6; ++u) v[3 + u] = from_f64<T>(B.Y[c][6 * (long long)j + u]);
-    Pose<T> P;
-    pose_at(v, q.eps, P);
-    if (!P.valid) {
-      acc[4] += 1.0;
+    const T x0 = from_f64<T>(B.X[c][3 * (long long)i]), x1 = from_f64<T>(B.X[c][3 * (long long)i + 1]),
+            x2 = from_f64<T>(B.X[c][3 * (long long)i + 2]);
+    const T* Rt = pose + 12 * (long long)j;
+    const T p0 = Rt[0] * x0 + Rt[1] * x1 + Rt[2] * x2 + Rt[9];
+    const T p1 = Rt[3] * x0 + Rt[4] * x1 + Rt[5] * x2 + Rt[10];
+    const T p2 = Rt[6] * x0 + Rt[7] * x1 + Rt[8] * x2 + Rt[11];
+    if (!(p2 > q.eps)) {
+      acc[4] += T(1);
       continue;
     }
     const V2 zz = static_cast<const V2*>(B.z)[o];
-    const T iz = T(1) / P.p[2];
-    const T zp0 = q.focal * P.p[0] * iz + q.cx, zp1 = q.focal * P.p[1] * iz + q.cy;
+    const T iz = T(1) / p2;
+    const T zp0 = q.focal * p0 * iz + q.cx, zp1 = q.focal * p1 * iz + q.cy;
     const T e0 = zz.x - zp0, e1 = zz.y - zp1;
     const T s = e0 * e0 + e1 * e1;
-    acc[0] += (double)s;
-    acc[1] += (double)misfit<T>(q.loss, q.lp, s);
-    acc[3] += 1.0;
+    acc[0] += s;
+    acc[1] += misfit<T>(q.loss, q.lp, s);
+    acc[3] += T(1);
     if (B.zt && (!B.inlier || B.inlier[o])) {
-      const double g0 = (double)zp0 - B.zt[2 * o], g1 = (double)zp1 - B.zt[2 * o + 1];
-      acc[2] += g0 * g0 + g1 * g1;
-      acc[5] += 1.0;
+      const double g0 = to_f64<T>(zp0) - B.zt[2 * o], g1 = to_f64<T>(zp1) - B.zt[2 * o + 1];
+      acc[2] += from_f64<T>(g0 * g0 + g1 * g1);
+      acc[5] += T(1);
     }
   }
-  for (int k = 0; k < 6; ++k) red[k][threadIdx.x] = acc[k];
+  for (int k = 0; k < 6; ++k) red[k][threadIdx.x] = to_f64<T>(acc[k]);
   __syncthreads();
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
     if (threadIdx.x < w)
@@ -1246,11 +1268,14 @@ cudaError_t launch_iteration(dba_block_ctx* ctx, bool with_sums, cudaEvent_t* ev
 
 dba_status read_stats(dba_block_ctx* ctx, bool have_residuals, dba_stats* st) {
   if (!have_residuals) BLK_CUDA(cudaMemsetAsync(ctx->B.sums, 0, 8 * sizeof(double), ctx->stream), "metrics");
-  const int g = std::min(dba::blocks_of(ctx->B.n_obs, 256), 4096);
-  if (ctx->fp32)
+  const int g = std::min(dba::blocks_of(ctx->B.n_obs, 256), 4096), gc = dba::blocks_of(ctx->B.n_cams, 128);
+  if (ctx->fp32) {
+    dba::block_camera_pose_kernel<float><<<gc, 128, 0, ctx->stream>>>(ctx->B, ctx->cur);
     dba::block_metrics_kernel<float><<<g, 256, 0, ctx->stream>>>(ctx->B, dba::make_prm<float>(ctx->prm), ctx->cur);
-  else
+  } else {
+    dba::block_camera_pose_kernel<double><<<gc, 128, 0, ctx->stream>>>(ctx->B, ctx->cur);
     dba::block_metrics_kernel<double><<<g, 256, 0, ctx->stream>>>(ctx->B, dba::make_prm<double>(ctx->prm), ctx->cur);
+  }
   BLK_CUDA(cudaGetLastError(), "metrics");
   double h[8];
   int herr = 0;
@@ -1587,6 +1612,7 @@ dba_status dba_block_set_observations(dba_block_ctx* ctx, int32_t n_cams, int32_
     BLK_CUDA(cudaMemcpyAsync(B.X[0], pts0, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, ctx->stream), "upload");
     BLK_CUDA(cudaMemcpyAsync(B.Y[0], cams0, sizeof(double) * 6 * m, cudaMemcpyHostToDevice, ctx->stream), "upload");
     BLK_CUDA(ctx->alloc(&B.sums, sizeof(double) * 8), "alloc");
+    BLK_CUDA(ctx->alloc(&B.cam_pose, tsz * 12 * (size_t)m), "alloc");
     BLK_CUDA(ctx->alloc(&B.err, sizeof(int)), "alloc");
     BLK_CUDA(cudaMemsetAsync(B.err, 0, sizeof(int), ctx->stream), "init");
     BLK_CUDA(cudaStreamSynchronize(ctx->stream), "upload");
