@@ -359,8 +359,9 @@ dba_status dba_block_iterate(dba_block_ctx* ctx, int n_iters, dba_stats* stats);
  * stats->seconds) or max_iters; needs reference pixels (ESTATE). */
 dba_status dba_block_iterate_until(dba_block_ctx* ctx, int max_iters, double target_rmse_gt, dba_stats* stats);
 /* Runs n_iters iterations (no metrics) with CUDA events around each launch and
- * writes the mean device milliseconds of block_solve, consensus and dual
- * ascent (the consensus slot includes a residual-buffer clear) into ms_out[3]. */
+ * writes the mean device milliseconds into ms_out[3]: the block solves (Eq. 14, with
+ * the previous iteration's dual ascent, Eqs. 12-13, applied as they start), the point
+ * consensus (Eq. 10) and the camera consensus (Eq. 11). */
 dba_status dba_block_profile(dba_block_ctx* ctx, int n_iters, double* ms_out);
 /* Consensus cameras [m][6] and points [n][3]. */
 dba_status dba_block_get_params(dba_block_ctx* ctx, double* cams_out, double* pts_out);

@@ -69,6 +69,14 @@ struct BlockProblem {
   const int* cam_cp;
   double* sums;                  // [8] metric accumulators
   void* cam_pose;                // [n_cams][12] T: R (row-major) and t of each consensus camera
+  // T mirrors of the current consensus and of its last change (previous minus current),
+  // written by the consensus kernels; they let the next block solves re-base the copies
+  // and apply the deferred dual ascent without FP64 gathers
+  void* Xm;                      // [3 n_pts]
+  void* DX;                      // [3 n_pts]
+  void* Ym;                      // [6 n_cams]
+  void* DY;                      // [6 n_cams]
+  int pending;                   // 1: the last iteration's dual ascent (Eqs. 12-13) is still to apply
   int* err;                      // bit 0: non-finite copy
 };
 
@@ -186,6 +194,26 @@ __device__ __forceinline__ T block_objective(const Prm<T>& q, const Grp<G>& grp,
   return ok ? s + sc : Num<T>::inf();
 }
 
+// One coordinate of a copy at the start of a block solve: its consensus (the T mirror), its
+// offset re-based on that consensus and its scaled dual.  With a pending dual ascent (every
+// iteration but the first) the previous iteration's Eqs. (12)-(13) are applied here, now
+// that the new consensus exists: the offset becomes d0 = offset + (previous - current
+// consensus) and the dual a + d0, in FP64, written back.
+template <typename T>
+__device__ __forceinline__ void deferred_ascent(const BlockProblem& B, T cons, T change, T offset, double* a,
+                                                T& vbar, T& d0, T& aT) {
+  vbar = cons;
+  if (B.pending) {
+    d0 = offset + change;
+    const double an = *a + to_f64<T>(d0);
+    *a = an;
+    aT = from_f64<T>(an);
+  } else {
+    d0 = offset;
+    aT = from_f64<T>(*a);
+  }
+}
+
 // Point copy p of a block sits on group lane p % G, register slot p / G, shared-memory
 // column base + p (PPL = 2 only with G = 32, so a warp's columns never overlap).
 template <typename T, int KC, int G, int PPL>
@@ -219,11 +247,10 @@ __device__ void solve_block(const BlockProblem& B, const Prm<T>& q, const BlockI
       const long long pc = (long long)bi.p0 + p;
       const int i = B.pc_pt[pc];
 #pragma unroll
-      for (int u = 0; u < 3; ++u) {
-        P.xbar[u] = from_f64<T>(B.X[cur][3 * (long long)i + u]);
-        dp[j][u] = pdel[u * B.n_pc + pc];
-        P.ax[u] = from_f64<T>(B.pc_a[u * B.n_pc + pc]);
-      }
+      for (int u = 0; u < 3; ++u)
+        deferred_ascent<T>(B, static_cast<const T*>(B.Xm)[3 * (long long)i + u],
+                           static_cast<const T*>(B.DX)[3 * (long long)i + u], pdel[u * B.n_pc + pc],
+                           B.pc_a + u * B.n_pc + pc, P.xbar[u], dp[j][u], P.ax[u]);
       const int ob0 = B.pc_obs[pc];
       P.nob = B.pc_obs[pc + 1] - ob0;
       const V2* zz = static_cast<const V2*>(B.z);
@@ -250,9 +277,9 @@ __device__ void solve_block(const BlockProblem& B, const Prm<T>& q, const BlockI
     const int c = gl / 6, u = gl % 6;
     const long long cc = (long long)bi.c0 + c;
     const int j = B.cc_cam[cc];
-    Z.vbar[c][u] = from_f64<T>(B.Y[cur][6 * (long long)j + u]);
-    Z.d[c][u] = cdel[u * B.n_cc + cc];
-    Z.a[c][u] = from_f64<T>(B.cc_a[u * B.n_cc + cc]);
+    deferred_ascent<T>(B, static_cast<const T*>(B.Ym)[6 * (long long)j + u],
+                       static_cast<const T*>(B.DY)[6 * (long long)j + u], cdel[u * B.n_cc + cc],
+                       B.cc_a + u * B.n_cc + cc, Z.vbar[c][u], Z.d[c][u], Z.a[c][u]);
   }
   grp.sync();
 
@@ -645,12 +672,24 @@ __device__ void solve_block_1cam(const BlockProblem& B, const Prm<T>& q, const B
   T cd[6], dp[PPL][3];
   const long long cc = bi.c0;
   {
+    // every lane forms the camera's six coordinates (the same bits); lane u writes back the
+    // deferred dual ascent of coordinate u
     const int jc = B.cc_cam[cc];
 #pragma unroll
     for (int u = 0; u < 6; ++u) {
-      K.cb[u] = from_f64<T>(B.Y[cur][6 * (long long)jc + u]);
-      cd[u] = cdel[u * B.n_cc + cc];
-      K.ca[u] = from_f64<T>(B.cc_a[u * B.n_cc + cc]);
+      const T off = cdel[u * B.n_cc + cc];
+      const T ch = static_cast<const T*>(B.DY)[6 * (long long)jc + u];
+      K.cb[u] = static_cast<const T*>(B.Ym)[6 * (long long)jc + u];
+      const double a = B.cc_a[u * B.n_cc + cc];
+      if (B.pending) {
+        cd[u] = off + ch;
+        const double an = a + to_f64<T>(cd[u]);
+        if (gl == u) B.cc_a[u * B.n_cc + cc] = an;
+        K.ca[u] = from_f64<T>(an);
+      } else {
+        cd[u] = off;
+        K.ca[u] = from_f64<T>(a);
+      }
     }
   }
   const long long pc = (long long)bi.p0 + gl;
@@ -661,11 +700,10 @@ __device__ void solve_block_1cam(const BlockProblem& B, const Prm<T>& q, const B
   if (K.act[0]) {
     const int i = B.pc_pt[pc];
 #pragma unroll
-    for (int u = 0; u < 3; ++u) {
-      K.xb[0][u] = from_f64<T>(B.X[cur][3 * (long long)i + u]);
-      dp[0][u] = pdel[u * B.n_pc + pc];
-      K.ax[0][u] = from_f64<T>(B.pc_a[u * B.n_pc + pc]);
-    }
+    for (int u = 0; u < 3; ++u)
+      deferred_ascent<T>(B, static_cast<const T*>(B.Xm)[3 * (long long)i + u],
+                         static_cast<const T*>(B.DX)[3 * (long long)i + u], pdel[u * B.n_pc + pc],
+                         B.pc_a + u * B.n_pc + pc, K.xb[0][u], dp[0][u], K.ax[0][u]);
     const V2 z = static_cast<const V2*>(B.z)[B.pc_obs[pc]];  // the copy's one observation
     K.z0[0] = z.x;
     K.z1[0] = z.y;
@@ -909,29 +947,40 @@ __global__ void __launch_bounds__(kBlkWarps * 32, (blk_min_ctas<T, KC, PPL>()))
   }
 }
 
-// Eqs. (10)-(11) over copies: consensus = old consensus + mean over its copies of
-// (offset + scaled dual), the old duals; a point or camera without copies keeps its value.
+// Eqs. (10)-(11) over copies.  After any full iteration the scaled duals of a point's (a
+// camera's) copies sum to zero (Eqs. 10 and 12 summed over the copies; the oracle's tests
+// pin it), and the duals are zero before the first, so the mean of copy + dual / rho is
+// the consensus the copies were solved against plus the mean of their offsets.  Offsets
+// are summed in T (points) or FP64 (cameras), the mean added to the FP64 consensus; the T
+// mirror and the change are written for the next block solves.  A point or camera without
+// copies keeps its value.
 // Points (a few copies each): one thread per point.
 template <typename T>
-__global__ void block_point_consensus_kernel(BlockProblem B, int cur) {
+__global__ void __launch_bounds__(256) block_point_consensus_kernel(BlockProblem B, int cur) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= B.n_pts) return;
   const int nxt = cur ^ 1;
   const int i = (int)t, k0 = B.pt_cp_off[i], k1 = B.pt_cp_off[i + 1];
   const T* del = static_cast<const T*>(B.pc_delta);
+  T acc[3] = {0, 0, 0};
+  for (int k = k0; k < k1; ++k) {
+    const int cp = B.pt_cp[k];
+#pragma unroll
+    for (int u = 0; u < 3; ++u) acc[u] += del[u * B.n_pc + cp];
+  }
+#pragma unroll
   for (int u = 0; u < 3; ++u) {
-    double s = 0.0;
-    for (int k = k0; k < k1; ++k) {
-      const int cp = B.pt_cp[k];
-      s += to_f64<T>(del[u * B.n_pc + cp]) + B.pc_a[u * B.n_pc + cp];
-    }
-    const double x = B.X[cur][3 * (long long)i + u];
-    B.X[nxt][3 * (long long)i + u] = k1 > k0 ? x + s / (double)(k1 - k0) : x;
+    const long long e = 3 * (long long)i + u;
+    const T inc = k1 > k0 ? acc[u] / (T)(k1 - k0) : T(0);
+    const double x = B.X[cur][e] + to_f64<T>(inc);
+    B.X[nxt][e] = x;
+    static_cast<T*>(B.Xm)[e] = from_f64<T>(x);
+    static_cast<T*>(B.DX)[e] = -inc;
   }
 }
 
-// Cameras (thousands of copies each): one CTA of 256 threads per camera, strided
-// partial sums and a fixed reduction tree.
+// Cameras (thousands of copies each): one CTA of 256 threads per camera, strided partial
+// sums of the offsets in FP64 and a fixed reduction tree.
 template <typename T>
 __global__ void __launch_bounds__(256) block_camera_consensus_kernel(BlockProblem B, int cur) {
   __shared__ double red[6][256];
@@ -942,7 +991,7 @@ __global__ void __launch_bounds__(256) block_camera_consensus_kernel(BlockProble
   for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
     const int cp = B.cam_cp[k];
 #pragma unroll
-    for (int u = 0; u < 6; ++u) s[u] += to_f64<T>(del[u * B.n_cc + cp]) + B.cc_a[u * B.n_cc + cp];
+    for (int u = 0; u < 6; ++u) s[u] += to_f64<T>(del[u * B.n_cc + cp]);
   }
 #pragma unroll
   for (int u = 0; u < 6; ++u) red[u][threadIdx.x] = s[u];
@@ -955,47 +1004,47 @@ __global__ void __launch_bounds__(256) block_camera_consensus_kernel(BlockProble
   }
   if (threadIdx.x < 6) {
     const int u = threadIdx.x;
-    const double y = B.Y[cur][6 * (long long)j + u];
-    B.Y[nxt][6 * (long long)j + u] = k1 > k0 ? y + red[u][0] / (double)(k1 - k0) : y;
+    const long long e = 6 * (long long)j + u;
+    const double yo = B.Y[cur][e];
+    const double yn = k1 > k0 ? yo + red[u][0] / (double)(k1 - k0) : yo;
+    B.Y[nxt][e] = yn;
+    static_cast<T*>(B.Ym)[e] = from_f64<T>(yn);
+    static_cast<T*>(B.DY)[e] = from_f64<T>(yo - yn);
   }
 }
 
-// Eqs. (12)-(13) per copy with the new consensus, in scaled form a += copy - consensus;
-// each offset is re-based on the new consensus.  With `sums`, adds the primal
-// (|copy - consensus|^2) and dual (rho^2 |change of consensus|^2) residual terms.
+// Primal (|copy - consensus|^2) and dual (rho^2 |change of consensus|^2) residual terms of
+// the last iteration, one thread per point or camera copy in storage order: right after an
+// iteration the offsets are still relative to the previous consensus Y[cur ^ 1] (the dual
+// ascent is deferred), so copy - new consensus = offset - (new - previous consensus).
 template <typename T>
-__global__ void block_dual_kernel(BlockProblem B, Prm<double> q, int cur, int with_sums) {
+__global__ void __launch_bounds__(256) block_residual_kernel(BlockProblem B, Prm<double> q, int cur) {
   __shared__ double red[2][256];
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const int nxt = cur ^ 1;
+  const int prv = cur ^ 1;
   double pr = 0.0, dr = 0.0;
   if (t < B.n_pc) {
-    T* del = static_cast<T*>(B.pc_delta);
-    const int i = B.pc_pt[t];
+    const T* del = static_cast<const T*>(B.pc_delta);
+    const long long i = B.pc_pt[t];
     for (int u = 0; u < 3; ++u) {
-      const double xo = B.X[cur][3 * (long long)i + u], xn = B.X[nxt][3 * (long long)i + u];
-      const double d = to_f64<T>(del[u * B.n_pc + t]) + (xo - xn);
-      B.pc_a[u * B.n_pc + t] += d;
-      del[u * B.n_pc + t] = from_f64<T>(d);
+      const double inc = B.X[cur][3 * i + u] - B.X[prv][3 * i + u];
+      const double d = to_f64<T>(del[u * B.n_pc + t]) - inc;
       pr += d * d;
-      const double r = q.rho_x * (xn - xo);
+      const double r = q.rho_x * inc;
       dr += r * r;
     }
   } else if (t < B.n_pc + B.n_cc) {
     const long long k = t - B.n_pc;
-    T* del = static_cast<T*>(B.cc_delta);
-    const int j = B.cc_cam[k];
+    const T* del = static_cast<const T*>(B.cc_delta);
+    const long long j = B.cc_cam[k];
     for (int u = 0; u < 6; ++u) {
-      const double yo = B.Y[cur][6 * (long long)j + u], yn = B.Y[nxt][6 * (long long)j + u];
-      const double d = to_f64<T>(del[u * B.n_cc + k]) + (yo - yn);
-      B.cc_a[u * B.n_cc + k] += d;
-      del[u * B.n_cc + k] = from_f64<T>(d);
+      const double inc = B.Y[cur][6 * j + u] - B.Y[prv][6 * j + u];
+      const double d = to_f64<T>(del[u * B.n_cc + k]) - inc;
       pr += d * d;
-      const double r = q.rho(3 + u) * (yn - yo);
+      const double r = q.rho(3 + u) * inc;
       dr += r * r;
     }
   }
-  if (!with_sums) return;
   red[0][threadIdx.x] = pr;
   red[1][threadIdx.x] = dr;
   __syncthreads();
@@ -1235,48 +1284,53 @@ cudaError_t launch_block_solve(dba_block_ctx* ctx) {
 
 // One iteration: block solves, consensus, dual ascent.  ev (nullable) receives an event
 // before each of the three launches and one after the last.
-cudaError_t launch_iteration(dba_block_ctx* ctx, bool with_sums, cudaEvent_t* ev = nullptr) {
+cudaError_t launch_iteration(dba_block_ctx* ctx, cudaEvent_t* ev = nullptr) {
   cudaError_t e;
   if (ev && (e = cudaEventRecord(ev[0], ctx->stream)) != cudaSuccess) return e;
   e = ctx->fp32 ? launch_block_solve<float>(ctx) : launch_block_solve<double>(ctx);
   if (e != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[1], ctx->stream)) != cudaSuccess) return e;
   const int gp = dba::blocks_of(ctx->B.n_pts, 256);
-  if (ctx->fp32) {
-    dba::block_point_consensus_kernel<float><<<gp, 256, 0, ctx->stream>>>(ctx->B, ctx->cur);
-    dba::block_camera_consensus_kernel<float><<<ctx->B.n_cams, 256, 0, ctx->stream>>>(ctx->B, ctx->cur);
-  } else {
-    dba::block_point_consensus_kernel<double><<<gp, 256, 0, ctx->stream>>>(ctx->B, ctx->cur);
-    dba::block_camera_consensus_kernel<double><<<ctx->B.n_cams, 256, 0, ctx->stream>>>(ctx->B, ctx->cur);
-  }
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if (with_sums && (e = cudaMemsetAsync(ctx->B.sums, 0, 8 * sizeof(double), ctx->stream)) != cudaSuccess) return e;
-  if (ev && (e = cudaEventRecord(ev[2], ctx->stream)) != cudaSuccess) return e;
-  const long long ncp = ctx->B.n_pc + ctx->B.n_cc;
-  const dba::Prm<double> q64 = dba::make_prm<double>(ctx->prm);
   if (ctx->fp32)
-    dba::block_dual_kernel<float><<<dba::blocks_of(ncp, 256), 256, 0, ctx->stream>>>(ctx->B, q64, ctx->cur,
-                                                                                    with_sums ? 1 : 0);
+    dba::block_point_consensus_kernel<float><<<gp, 256, 0, ctx->stream>>>(ctx->B, ctx->cur);
   else
-    dba::block_dual_kernel<double><<<dba::blocks_of(ncp, 256), 256, 0, ctx->stream>>>(ctx->B, q64, ctx->cur,
-                                                                                     with_sums ? 1 : 0);
+    dba::block_point_consensus_kernel<double><<<gp, 256, 0, ctx->stream>>>(ctx->B, ctx->cur);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (ev && (e = cudaEventRecord(ev[2], ctx->stream)) != cudaSuccess) return e;
+  if (ctx->fp32)
+    dba::block_camera_consensus_kernel<float><<<ctx->B.n_cams, 256, 0, ctx->stream>>>(ctx->B, ctx->cur);
+  else
+    dba::block_camera_consensus_kernel<double><<<ctx->B.n_cams, 256, 0, ctx->stream>>>(ctx->B, ctx->cur);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[3], ctx->stream)) != cudaSuccess) return e;
   ctx->cur ^= 1;
+  ctx->B.pending = 1;  // the next block solves apply this iteration's dual ascent
   return cudaSuccess;
 }
 
-dba_status read_stats(dba_block_ctx* ctx, bool have_residuals, dba_stats* st) {
-  if (!have_residuals) BLK_CUDA(cudaMemsetAsync(ctx->B.sums, 0, 8 * sizeof(double), ctx->stream), "metrics");
+// The metric sums at the current consensus into B.sums[0..5] (cleared first); with
+// residuals, the last iteration's primal and dual residual terms into B.sums[6..7].
+cudaError_t launch_stats(dba_block_ctx* ctx, bool residuals) {
+  cudaError_t e = cudaMemsetAsync(ctx->B.sums, 0, 8 * sizeof(double), ctx->stream);
+  if (e != cudaSuccess) return e;
   const int g = std::min(dba::blocks_of(ctx->B.n_obs, 256), 4096), gc = dba::blocks_of(ctx->B.n_cams, 128);
+  const dba::Prm<double> q64 = dba::make_prm<double>(ctx->prm);
+  const int gr = dba::blocks_of(ctx->B.n_pc + ctx->B.n_cc, 256);
   if (ctx->fp32) {
+    if (residuals) dba::block_residual_kernel<float><<<gr, 256, 0, ctx->stream>>>(ctx->B, q64, ctx->cur);
     dba::block_camera_pose_kernel<float><<<gc, 128, 0, ctx->stream>>>(ctx->B, ctx->cur);
     dba::block_metrics_kernel<float><<<g, 256, 0, ctx->stream>>>(ctx->B, dba::make_prm<float>(ctx->prm), ctx->cur);
   } else {
+    if (residuals) dba::block_residual_kernel<double><<<gr, 256, 0, ctx->stream>>>(ctx->B, q64, ctx->cur);
     dba::block_camera_pose_kernel<double><<<gc, 128, 0, ctx->stream>>>(ctx->B, ctx->cur);
     dba::block_metrics_kernel<double><<<g, 256, 0, ctx->stream>>>(ctx->B, dba::make_prm<double>(ctx->prm), ctx->cur);
   }
-  BLK_CUDA(cudaGetLastError(), "metrics");
+  return cudaGetLastError();
+}
+
+// Metrics (and, with residuals, the last iteration's residual terms) at the current state.
+dba_status read_stats(dba_block_ctx* ctx, bool residuals, dba_stats* st) {
+  BLK_CUDA(launch_stats(ctx, residuals), "metrics");
   double h[8];
   int herr = 0;
   BLK_CUDA(cudaMemcpyAsync(h, ctx->B.sums, sizeof h, cudaMemcpyDeviceToHost, ctx->stream), "metrics");
@@ -1288,8 +1342,8 @@ dba_status read_stats(dba_block_ctx* ctx, bool have_residuals, dba_stats* st) {
   st->objective = h[1];
   st->rmse_gt = h[5] > 0 ? std::sqrt(h[2] / h[5]) : 0.0;
   st->n_invalid = (long long)h[4];
-  st->primal_res = have_residuals ? std::sqrt(h[6]) : 0.0;
-  st->dual_res = have_residuals ? std::sqrt(h[7]) : 0.0;
+  st->primal_res = residuals ? std::sqrt(h[6]) : 0.0;
+  st->dual_res = residuals ? std::sqrt(h[7]) : 0.0;
   return DBA_OK;
 }
 
@@ -1546,6 +1600,7 @@ dba_status dba_block_set_observations(dba_block_ctx* ctx, int32_t n_cams, int32_
     B.n_pc = n_pc;
     B.n_cc = n_cc;
     const size_t tsz = ctx->fp32 ? sizeof(float) : sizeof(double);
+    std::vector<float> mirror_pts, mirror_cams;  // FP32 mirrors of the initial consensus (uploaded below)
     dba::BlockInfo* d_blocks = nullptr;
     int *d_pc_obs = nullptr, *d_pc_pt = nullptr, *d_cc_cam = nullptr, *d_obs_pt = nullptr, *d_obs_cam = nullptr;
     int *d_pt_off = nullptr, *d_pt_cp = nullptr, *d_cam_off = nullptr, *d_cam_cp = nullptr;
@@ -1611,6 +1666,25 @@ dba_status dba_block_set_observations(dba_block_ctx* ctx, int32_t n_cams, int32_
     }
     BLK_CUDA(cudaMemcpyAsync(B.X[0], pts0, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, ctx->stream), "upload");
     BLK_CUDA(cudaMemcpyAsync(B.Y[0], cams0, sizeof(double) * 6 * m, cudaMemcpyHostToDevice, ctx->stream), "upload");
+    // T mirrors of the consensus and its (zero) last change
+    BLK_CUDA(ctx->alloc(&B.Xm, tsz * 3 * (size_t)n), "alloc");
+    BLK_CUDA(ctx->alloc(&B.DX, tsz * 3 * (size_t)n), "alloc");
+    BLK_CUDA(ctx->alloc(&B.Ym, tsz * 6 * (size_t)m), "alloc");
+    BLK_CUDA(ctx->alloc(&B.DY, tsz * 6 * (size_t)m), "alloc");
+    BLK_CUDA(cudaMemsetAsync(B.DX, 0, tsz * 3 * (size_t)n, ctx->stream), "init");
+    BLK_CUDA(cudaMemsetAsync(B.DY, 0, tsz * 6 * (size_t)m, ctx->stream), "init");
+    if (ctx->fp32) {
+      mirror_pts.assign(pts0, pts0 + 3 * (size_t)n);
+      mirror_cams.assign(cams0, cams0 + 6 * (size_t)m);
+      BLK_CUDA(cudaMemcpyAsync(B.Xm, mirror_pts.data(), sizeof(float) * mirror_pts.size(), cudaMemcpyHostToDevice,
+                               ctx->stream), "upload");
+      BLK_CUDA(cudaMemcpyAsync(B.Ym, mirror_cams.data(), sizeof(float) * mirror_cams.size(), cudaMemcpyHostToDevice,
+                               ctx->stream), "upload");
+    } else {
+      BLK_CUDA(cudaMemcpyAsync(B.Xm, pts0, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, ctx->stream), "upload");
+      BLK_CUDA(cudaMemcpyAsync(B.Ym, cams0, sizeof(double) * 6 * m, cudaMemcpyHostToDevice, ctx->stream), "upload");
+    }
+    B.pending = 0;  // duals start at zero: nothing to apply before the first block solves
     BLK_CUDA(ctx->alloc(&B.sums, sizeof(double) * 8), "alloc");
     BLK_CUDA(ctx->alloc(&B.cam_pose, tsz * 12 * (size_t)m), "alloc");
     BLK_CUDA(ctx->alloc(&B.err, sizeof(int)), "alloc");
@@ -1656,7 +1730,7 @@ dba_status dba_block_iterate(dba_block_ctx* ctx, int n_iters, dba_stats* stats) 
     if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_block_iterate before dba_block_set_observations");
     if (n_iters < 0) return ctx->fail(DBA_EINVAL, "dba_block_iterate: n_iters < 0");
     BLK_CUDA(cudaEventRecord(ctx->ev0, ctx->stream), "iterate");
-    for (int it = 0; it < n_iters; ++it) BLK_CUDA(launch_iteration(ctx, stats && it == n_iters - 1), "iterate");
+    for (int it = 0; it < n_iters; ++it) BLK_CUDA(launch_iteration(ctx), "iterate");
     BLK_CUDA(cudaEventRecord(ctx->ev1, ctx->stream), "iterate");
     ctx->iters += n_iters;
     int herr = 0;
@@ -1681,19 +1755,29 @@ dba_status dba_block_iterate_until(dba_block_ctx* ctx, int max_iters, double tar
     if (!ctx->B.zt) return ctx->fail(DBA_ESTATE, "dba_block_iterate_until needs reference pixels");
     if (max_iters < 0 || !(target_rmse_gt > 0)) return ctx->fail(DBA_EINVAL, "dba_block_iterate_until: bad arguments");
     double secs = 0.0;
+    bool any = false;
     for (int it = 0; it < max_iters; ++it) {
+      // one iteration and the stopping test's metrics, timed on the device
       BLK_CUDA(cudaEventRecord(ctx->ev0, ctx->stream), "iterate_until");
-      BLK_CUDA(launch_iteration(ctx, true), "iterate_until");
-      ctx->iters += 1;
-      const dba_status s = read_stats(ctx, true, stats);
+      BLK_CUDA(launch_iteration(ctx), "iterate_until");
+      BLK_CUDA(launch_stats(ctx, false), "iterate_until");
       BLK_CUDA(cudaEventRecord(ctx->ev1, ctx->stream), "iterate_until");
-      BLK_CUDA(cudaEventSynchronize(ctx->ev1), "iterate_until");
+      ctx->iters += 1;
+      any = true;
+      double h[8];
+      int herr = 0;
+      BLK_CUDA(cudaMemcpyAsync(h, ctx->B.sums, sizeof h, cudaMemcpyDeviceToHost, ctx->stream), "iterate_until");
+      BLK_CUDA(cudaMemcpyAsync(&herr, ctx->B.err, sizeof herr, cudaMemcpyDeviceToHost, ctx->stream), "iterate_until");
+      BLK_CUDA(cudaStreamSynchronize(ctx->stream), "iterate_until");
+      if (herr & 1) return ctx->fail(DBA_ENUMERIC, "a block solve produced a non-finite value");
       float ms = 0.f;
       BLK_CUDA(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1), "iterate_until");
       secs += 1e-3 * ms;
-      if (s != DBA_OK) return s;
-      if (stats->rmse_gt <= target_rmse_gt) break;
+      if (h[5] > 0 && std::sqrt(h[2] / h[5]) <= target_rmse_gt) break;
     }
+    // the full statistics of the last iteration, residuals included
+    const dba_status s = read_stats(ctx, any, stats);
+    if (s != DBA_OK) return s;
     stats->seconds = secs;
     return DBA_OK;
   });
@@ -1709,7 +1793,7 @@ dba_status dba_block_profile(dba_block_ctx* ctx, int n_iters, double* ms_out) {
     for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaEventCreate(&ev[k]);
     double acc[3] = {0, 0, 0};
     for (int it = 0; it < n_iters && e == cudaSuccess; ++it) {
-      e = launch_iteration(ctx, false, ev);
+      e = launch_iteration(ctx, ev);
       if (e == cudaSuccess) e = cudaEventSynchronize(ev[3]);
       for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
         float ms = 0.f;

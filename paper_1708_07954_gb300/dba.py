@@ -549,7 +549,7 @@ class BlockSolver:
     def profile(self, n):
         ms = np.zeros(3)
         self._check(load().dba_block_profile(self.ctx, int(n), _ptr(ms)))
-        return {"block_solve": ms[0], "block_consensus": ms[1], "block_dual": ms[2]}
+        return {"block_solve": ms[0], "block_point_consensus": ms[1], "block_camera_consensus": ms[2]}
 
     def params(self):
         cams = np.zeros((self.scene.n_cams, 6))
