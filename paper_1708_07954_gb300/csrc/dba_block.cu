@@ -660,9 +660,34 @@ struct OneCam {
   }
 };
 
+// L1 prefetch of the copy rows of block nb (the group's next block), so that its start
+// does not wait on them: offsets and duals of its point copies (one per lane), their point
+// and observation indices, and its camera copy's rows.
+template <typename T, int G>
+__device__ __forceinline__ void prefetch_block(const BlockProblem& B, const BlockInfo& nb, int gl) {
+  const T* pdel = static_cast<const T*>(B.pc_delta);
+  const T* cdel = static_cast<const T*>(B.cc_delta);
+  if (gl < nb.np) {
+    const long long pc = (long long)nb.p0 + gl;
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(pdel + u * B.n_pc + pc));
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(B.pc_a + u * B.n_pc + pc));
+    }
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(B.pc_pt + pc));
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(B.pc_obs + pc));
+  }
+  if (gl < 6) {
+    const long long cc = nb.c0;
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(cdel + gl * B.n_cc + cc));
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(B.cc_a + gl * B.n_cc + cc));
+    if (gl == 0) asm volatile("prefetch.global.L1 [%0];" ::"l"(B.cc_cam + cc));
+  }
+}
+
 template <typename T, int G>
 __device__ void solve_block_1cam(const BlockProblem& B, const Prm<T>& q, const BlockInfo& bi, const Grp<G>& grp,
-                                 int cur) {
+                                 int cur, const BlockInfo* next) {
   constexpr int PPL = 1;  // one point copy per lane (blocks of at most 32 points)
   using V2 = typename Num<T>::V2;
   const int gl = grp.gl, np = bi.np;
@@ -708,6 +733,7 @@ __device__ void solve_block_1cam(const BlockProblem& B, const Prm<T>& q, const B
     K.z0[0] = z.x;
     K.z1[0] = z.y;
   }
+  if (next) prefetch_block<T, G>(B, *next, gl);
   T L = K.objective(dp, cd);
   T lambda = T(-1);
   for (int step = 0; step < q.steps; ++step) {
@@ -916,9 +942,17 @@ __global__ void __launch_bounds__(kBlkWarps * 32)
   const int warps = blockDim.x >> 5, warp = threadIdx.x >> 5;
   const Grp<G> grp(threadIdx.x & 31);
   const int stride = gridDim.x * warps * kPer;
-  for (int b = lo + (blockIdx.x * warps + warp) * kPer + grp.base / G; b < hi; b += stride) {
-    const BlockInfo bi = B.blocks[b];
-    solve_block_1cam<T, G>(B, q, bi, grp, cur);
+  int b = lo + (blockIdx.x * warps + warp) * kPer + grp.base / G;
+  BlockInfo bi{};
+  if (b < hi) bi = B.blocks[b];
+  for (; b < hi; b += stride) {
+    // the next block's record is loaded now and its rows prefetched once this block's own
+    // loads are in, so that both arrive while this block is solved
+    const bool more = b + stride < hi;
+    BlockInfo nb{};
+    if (more) nb = B.blocks[b + stride];
+    solve_block_1cam<T, G>(B, q, bi, grp, cur, more ? &nb : nullptr);
+    bi = nb;
   }
 }
 
