@@ -48,6 +48,8 @@ def parse(argv=None):
                     help="2: the 4M-observation scene; 3: a batch of 256 uneven scenes")
     ap.add_argument("--n-pts", type=int, default=500000, help="points of the scene (default: full size)")
     ap.add_argument("--inner-steps", type=int, default=5, help="damped Gauss-Newton steps per local solve")
+    ap.add_argument("--tile-obs", type=int, default=0,
+                    help="observations per tile (64, 128, 256; 0: the library's choice, -1: autotune)")
     ap.add_argument("--warm-start", action="store_true",
                     help="time the iteration with the learned warm start (shipped weights) in front of the local solves")
     ap.add_argument("--local-solver", choices=["gn", "lbfgs"], default="gn",
@@ -322,7 +324,7 @@ def run_ours(args, rank, world, local_rank):
     lbfgs = args.local_solver == "lbfgs"
     lsolver = dba.DBA_SOLVER_LBFGS if lbfgs else dba.DBA_SOLVER_GN
     solver = dba.Solver(sc, precision=prec, inner_steps=args.inner_steps, stream=stream.cuda_stream,
-                        local_solver=lsolver)
+                        local_solver=lsolver, tile_obs=args.tile_obs)
     if args.warm_start:
         from paper_1708_07954_gb300 import warmstart
 

@@ -380,8 +380,16 @@ __device__ __forceinline__ void process_tile(const DevProblem& P, const Prm<T>& 
   }
 }
 
+// Resident blocks per SM the register allocation is held to: 16 warps for the FP32 kernels at
+// every tile size (4 blocks of 128 threads run four tiles' latency chains side by side where
+// 2 blocks at 129 registers fit only 3); the FP64 kernels, bound by the FP64 pipe, keep 2.
+template <typename T, int NT>
+constexpr int tile_min_blocks() {
+  return sizeof(T) == 4 ? 512 / NT : 2;
+}
+
 template <typename T, int NT, int kS>
-__global__ void __launch_bounds__(NT, 2)
+__global__ void __launch_bounds__(NT, (tile_min_blocks<T, NT>()))
     tile_iterate_kernel(DevProblem P, const __grid_constant__ TileMaps M, Prm<T> q) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* base = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
