@@ -9,11 +9,15 @@
 //
 // GPU mapping: one group of G lanes per block (G = 8, 16 or 32 by the block's size,
 // several blocks per warp), one lane per point copy (two per lane above 32 points;
-// pi <= 64), camera copies (kappa <= 4) shared by the group in shared memory.  Each damped Gauss-Newton step
-// eliminates the points (3x3 per lane) and solves the reduced camera system (at most
-// 24 x 24, a Schur complement accumulated entry-parallel over the group's lanes) by a
-// lane-per-row Cholesky factorisation.  Consensus (Eqs. 10-11
-// over copies) and dual ascent (Eqs. 12-13) run in FP64 over copy lists.
+// pi <= 64), camera copies (kappa <= 4) shared by the group in shared memory.  Each damped
+// Gauss-Newton step eliminates the points (3x3 per lane) and solves the reduced camera
+// system (at most 24 x 24).  Three solve kernels:
+//   one camera (6 x 6): terms summed by butterflies, factored in every lane's registers;
+//   two cameras, at most 32 points (12 x 12): terms formed in registers, summed by a
+//     reduce-scatter over the group, factored lane-per-row in shared memory;
+//   otherwise: terms staged in shared memory, summed entry-parallel, factored lane-per-row.
+// Consensus (Eqs. 10-11 over copies) and dual ascent (Eqs. 12-13) run in FP64 over copy
+// lists.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -24,6 +28,7 @@
 #include <new>
 #include <numeric>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/dba.h"
@@ -956,6 +961,524 @@ __global__ void __launch_bounds__(kBlkWarps * 32)
   }
 }
 
+// ------------------------------------------------------------ two-camera blocks
+// A block with at most two cameras and at most G <= 32 points has a reduced camera system of
+// at most 12 x 12.  Each lane keeps its point copy's linearisation in registers (at most one
+// observation per camera) and forms its terms of the whole system: the three 6 x 6 blocks of
+// B^T Q B, the right-hand side B^T U and the camera misfit gradient.  A reduce-scatter over
+// the group (recursive halving) sums them, G values at a time, so that each value passes
+// through one shuffle instead of log2(G); lane i receives the sum of value i and writes it
+// into the group's system in shared memory, which then is factored lane-per-row as in
+// solve_block.  Same arithmetic as solve_block; the sums run in another order.
+template <typename T>
+struct TwoCamShared {
+  // the reduced camera system's upper triangle S(row <= col) at 13 row + col, then the
+  // right-hand side sums B^T U, the camera misfit gradients and the rounding-noise scale
+  static constexpr int kRhs = 12 * 13, kG = kRhs + 12, kNoise = kG + 12, kSys = kNoise + 1;
+  T sys[kSys];
+  T vbar[2][6];
+  T d[2][6];
+  T dt[2][6];
+  T a[2][6];
+};
+
+// The values one lane contributes to the reduced system, in this order: the upper triangles
+// of the two diagonal 6 x 6 blocks (21 each), the off-diagonal block (36, row-major), the
+// right-hand sides B^T U (6 per camera), the camera misfit gradients (6 per camera) and the
+// rounding-noise scale; the rest of the last group of G is zero.
+constexpr int kSysValues = 21 + 21 + 36 + 12 + 12 + 1;
+
+struct SysEntry {
+  int kind;  // 0: S(row, col), 1: rhs(row), 2: g(row), 3: noise, 4: none
+  int row, col;
+};
+
+__host__ __device__ constexpr SysEntry sys_entry(int e) {
+  if (e < 42) {
+    const int c = e < 21 ? 0 : 1;
+    int t = e - 21 * c, r = 0;
+    while (t >= 6 - r) {
+      t -= 6 - r;
+      ++r;
+    }
+    return SysEntry{0, 6 * c + r, 6 * c + r + t};
+  }
+  if (e < 78) return SysEntry{0, (e - 42) / 6, 6 + (e - 42) % 6};
+  if (e < 90) return SysEntry{1, e - 78, 0};
+  if (e < 102) return SysEntry{2, e - 90, 0};
+  if (e == 102) return SysEntry{3, 0, 0};
+  return SysEntry{4, 0, 0};
+}
+
+// where value e lands in TwoCamShared::sys, or -1
+__host__ __device__ constexpr int sys_dst(int e) {
+  const SysEntry se = sys_entry(e);
+  return se.kind == 0 ? 13 * se.row + se.col
+                      : se.kind == 1 ? 12 * 13 + se.row : se.kind == 2 ? 12 * 13 + 12 + se.row
+                                                                         : se.kind == 3 ? 12 * 13 + 24 : -1;
+}
+
+// Lane gl of a group of G receives the sum over the group of v[gl] (v is overwritten).
+// Stage h: the lane keeps the half of its values whose index has bit h equal to its own lane
+// bit h, adds the partner's partial sums of that half and hands over the other half.
+template <typename T, int G>
+__device__ __forceinline__ T reduce_scatter(T (&v)[G], const Grp<G>& grp) {
+#pragma unroll
+  for (int h = G / 2; h >= 1; h >>= 1) {
+    const bool up = (grp.gl & h) != 0;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const T send = up ? v[i] : v[i + h];
+      const T keep = up ? v[i + h] : v[i];
+      v[i] = keep + __shfl_xor_sync(grp.mask, send, h, G);
+    }
+  }
+  return v[0];
+}
+
+// One lane's terms of the reduced system: the camera rows B_c of its observations' Jacobians,
+// U_c, the Schur weights Q of the camera pairs 00, 01, 11, the IRLS weights 2w_c, the
+// residuals and the rounding-noise scale (camera slots without an observation: zero).
+template <typename T>
+struct SysTerms {
+  T Bc[2][2][6], U[2][2], Q[3][4], tw[2], ez[2][2], noise;
+};
+
+// value E of the list above, E a compile-time index
+template <int E, typename T>
+__device__ __forceinline__ T sys_value(const SysTerms<T>& m) {
+  constexpr SysEntry se = sys_entry(E);
+  if constexpr (se.kind == 0) {
+    constexpr int c1 = se.row / 6, r = se.row % 6, c2 = se.col / 6, s = se.col % 6, pr = c1 + c2;
+    const T b10 = m.Bc[c1][0][r], b11 = m.Bc[c1][1][r], b20 = m.Bc[c2][0][s], b21 = m.Bc[c2][1][s];
+    return b10 * (m.Q[pr][0] * b20 + m.Q[pr][1] * b21) + b11 * (m.Q[pr][2] * b20 + m.Q[pr][3] * b21);
+  } else if constexpr (se.kind == 1) {
+    constexpr int c = se.row / 6, r = se.row % 6;
+    return m.Bc[c][0][r] * m.U[c][0] + m.Bc[c][1][r] * m.U[c][1];
+  } else if constexpr (se.kind == 2) {
+    constexpr int c = se.row / 6, r = se.row % 6;
+    return -m.tw[c] * (m.Bc[c][0][r] * m.ez[c][0] + m.Bc[c][1][r] * m.ez[c][1]);
+  } else if constexpr (se.kind == 3) {
+    return m.noise;
+  } else {
+    return T(0);
+  }
+}
+
+// values K G ... K G + G - 1: summed over the group, value K G + gl landing on lane gl, which
+// writes it to its place in the system (dst: sys_dst of every value, a per-CTA table)
+template <typename T, int G, int K, int... I>
+__device__ __forceinline__ void sys_chunk(const SysTerms<T>& m, const Grp<G>& grp, TwoCamShared<T>& Z,
+                                          const short* dst, std::integer_sequence<int, I...>) {
+  T v[G] = {sys_value<K * G + I>(m)...};
+  const T sum = reduce_scatter<T, G>(v, grp);
+  const int o = dst[K * G + grp.gl];
+  if (o >= 0) Z.sys[o] = sum;
+}
+
+template <typename T, int G, int... K>
+__device__ __forceinline__ void sys_reduce(const SysTerms<T>& m, const Grp<G>& grp, TwoCamShared<T>& Z,
+                                           const short* dst, std::integer_sequence<int, K...>) {
+  (sys_chunk<T, G, K>(m, grp, Z, dst, std::make_integer_sequence<int, G>{}), ...);
+}
+
+constexpr int kSysSlots = 128;  // values padded to whole groups of 16 or 32 lanes
+
+// One lane's point copy in a two-camera block: consensus, scaled dual, its observation on
+// each camera slot (has[c]) and the pixels.
+template <typename T>
+struct TwoCamPt {
+  bool act, has[2];
+  T xb[3], ax[3], z0[2], z1[2];
+
+  // Eq. (14) at point offsets dp and camera offsets dc (nc cameras), summed over the group;
+  // +inf when an observation is behind its camera
+  template <int G>
+  __device__ T objective(const Prm<T>& q, const Grp<G>& grp, const T (&dp)[3], const TwoCamShared<T>& Z,
+                         const T (*dc)[6], int nc) const {
+    T s = 0;
+    bool ok = true;
+    if (act) {
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        if (!has[c]) continue;
+        T v[9];
+#pragma unroll
+        for (int u = 0; u < 3; ++u) v[u] = xb[u] + dp[u];
+#pragma unroll
+        for (int u = 0; u < 6; ++u) v[3 + u] = Z.vbar[c][u] + dc[c][u];
+        Pose<T> P;
+        pose_at(v, q.eps, P);
+        if (!P.valid) {
+          ok = false;
+        } else {
+          const T iz = Num<T>::rcp(P.p[2]);
+          const T e0 = z0[c] - (q.focal * P.p[0] * iz + q.cx);
+          const T e1 = z1[c] - (q.focal * P.p[1] * iz + q.cy);
+          s += misfit<T>(q.loss, q.lp, e0 * e0 + e1 * e1);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 3; ++u) s += q.rho_x * dp[u] * (ax[u] + T(0.5) * dp[u]);
+    }
+    s = grp.sum(s);
+    ok = grp.all(ok);
+    T sc = 0;
+    for (int c = 0; c < nc; ++c)
+#pragma unroll
+      for (int u = 0; u < 6; ++u) sc += q.rho(3 + u) * dc[c][u] * (Z.a[c][u] + T(0.5) * dc[c][u]);
+    return ok ? s + sc : Num<T>::inf();
+  }
+};
+
+// L1 prefetch of the copy rows of block nb (the group's next block): its point copies' offsets,
+// duals and indices (one per lane) and its camera copies' rows (one coordinate per lane).
+template <typename T, int G>
+__device__ __forceinline__ void prefetch_block_2cam(const BlockProblem& B, const BlockInfo& nb, int gl) {
+  const T* pdel = static_cast<const T*>(B.pc_delta);
+  const T* cdel = static_cast<const T*>(B.cc_delta);
+  if (gl < nb.np) {
+    const long long pc = (long long)nb.p0 + gl;
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(pdel + u * B.n_pc + pc));
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(B.pc_a + u * B.n_pc + pc));
+    }
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(B.pc_pt + pc));
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(B.pc_obs + pc));
+  }
+  if (gl < 6 * nb.nc) {
+    const long long cc = (long long)nb.c0 + gl / 6;
+    const int u = gl % 6;
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(cdel + u * B.n_cc + cc));
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(B.cc_a + u * B.n_cc + cc));
+    if (u == 0) asm volatile("prefetch.global.L1 [%0];" ::"l"(B.cc_cam + cc));
+  }
+}
+
+template <typename T, int G>
+__device__ void solve_block_2cam(const BlockProblem& B, const Prm<T>& q, const BlockInfo& bi, const Grp<G>& grp,
+                                 TwoCamShared<T>& Z, const short* dst, const BlockInfo* next) {
+  static_assert(G >= 12, "one lane per camera coordinate");
+  using V2 = typename Num<T>::V2;
+  const int gl = grp.gl, np = bi.np, nc = bi.nc, n_u = 6 * nc;
+  T* pdel = static_cast<T*>(B.pc_delta);
+  T* cdel = static_cast<T*>(B.cc_delta);
+  // camera copies: lane 6 c + u takes coordinate u of camera c; an absent second camera is
+  // zero, so that the sums over both camera slots below need no test
+  if (gl < n_u) {
+    const int c = gl / 6, u = gl % 6;
+    const long long cc = (long long)bi.c0 + c;
+    const int j = B.cc_cam[cc];
+    deferred_ascent<T>(B, static_cast<const T*>(B.Ym)[6 * (long long)j + u],
+                       static_cast<const T*>(B.DY)[6 * (long long)j + u], cdel[u * B.n_cc + cc],
+                       B.cc_a + u * B.n_cc + cc, Z.vbar[c][u], Z.d[c][u], Z.a[c][u]);
+  } else if (gl < 12) {
+    Z.vbar[gl / 6][gl % 6] = Z.d[gl / 6][gl % 6] = Z.a[gl / 6][gl % 6] = 0;
+  }
+  const long long pc = (long long)bi.p0 + gl;
+  TwoCamPt<T> K;
+  T dp[3];
+  K.act = gl < np;
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    K.has[c] = false;
+    K.z0[c] = K.z1[c] = 0;
+  }
+#pragma unroll
+  for (int u = 0; u < 3; ++u) K.xb[u] = K.ax[u] = dp[u] = 0;
+  if (K.act) {
+    const int i = B.pc_pt[pc];
+#pragma unroll
+    for (int u = 0; u < 3; ++u)
+      deferred_ascent<T>(B, static_cast<const T*>(B.Xm)[3 * (long long)i + u],
+                         static_cast<const T*>(B.DX)[3 * (long long)i + u], pdel[u * B.n_pc + pc],
+                         B.pc_a + u * B.n_pc + pc, K.xb[u], dp[u], K.ax[u]);
+    // at most one observation per camera of the block
+    const int ob0 = B.pc_obs[pc], nob = B.pc_obs[pc + 1] - ob0;
+    const V2* zz = static_cast<const V2*>(B.z);
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+      if (k < nob) {
+        const int c = B.obs_lc[ob0 + k];
+        const V2 z = zz[ob0 + k];
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+          if (c == s) {
+            K.has[s] = true;
+            K.z0[s] = z.x;
+            K.z1[s] = z.y;
+          }
+      }
+  }
+  if (next) prefetch_block_2cam<T, G>(B, *next, gl);
+  grp.sync();
+
+  T L = K.objective(q, grp, dp, Z, Z.d, nc);
+  T lambda = T(-1);
+  for (int step = 0; step < q.steps; ++step) {
+    // linearisation of this lane's observations (camera slots without one: zero)
+    SysTerms<T> m;
+    T Ap[2][2][3];
+    T h[6] = {0, 0, 0, 0, 0, 0}, gp[3] = {0, 0, 0}, trc = 0;
+    m.noise = 0;
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      T J0[9], J1[9], e0 = 0, e1 = 0, w = 0;
+      bool lin = false;
+      if (K.act && K.has[c]) {
+        T v[9];
+#pragma unroll
+        for (int u = 0; u < 3; ++u) v[u] = K.xb[u] + dp[u];
+#pragma unroll
+        for (int u = 0; u < 6; ++u) v[3 + u] = Z.vbar[c][u] + Z.d[c][u];
+        Pose<T> P;
+        pose_at(v, q.eps, P);
+        if (P.valid) {
+          linearize(P, K.z0[c], K.z1[c], q, J0, J1, e0, e1, w);
+          lin = true;
+        }
+      }
+      if (!lin) {
+#pragma unroll
+        for (int u = 0; u < 9; ++u) J0[u] = J1[u] = 0;
+        e0 = e1 = w = 0;
+      }
+      const T t = T(2) * w;
+      m.tw[c] = t;
+      m.ez[c][0] = e0;
+      m.ez[c][1] = e1;
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        Ap[c][0][u] = J0[u];
+        Ap[c][1][u] = J1[u];
+      }
+#pragma unroll
+      for (int u = 0; u < 6; ++u) {
+        m.Bc[c][0][u] = J0[3 + u];
+        m.Bc[c][1][u] = J1[3 + u];
+      }
+      h[0] += t * (J0[0] * J0[0] + J1[0] * J1[0]);
+      h[1] += t * (J0[0] * J0[1] + J1[0] * J1[1]);
+      h[2] += t * (J0[0] * J0[2] + J1[0] * J1[2]);
+      h[3] += t * (J0[1] * J0[1] + J1[1] * J1[1]);
+      h[4] += t * (J0[1] * J0[2] + J1[1] * J1[2]);
+      h[5] += t * (J0[2] * J0[2] + J1[2] * J1[2]);
+#pragma unroll
+      for (int u = 0; u < 3; ++u) gp[u] -= t * (J0[u] * e0 + J1[u] * e1);
+#pragma unroll
+      for (int u = 3; u < 9; ++u) trc += t * (J0[u] * J0[u] + J1[u] * J1[u]);
+      m.noise += t * Num<T>::sqrt_(e0 * e0 + e1 * e1) * (fabs(K.z0[c]) + fabs(K.z1[c]));
+    }
+    if (K.act)
+#pragma unroll
+      for (int u = 0; u < 3; ++u) gp[u] += q.rho_x * (K.ax[u] + dp[u]);
+    if (lambda < T(0)) {
+      T tr = trc;
+      if (K.act) tr += h[0] + h[3] + h[5] + T(3) * q.rho_x;
+      tr = grp.sum(tr);
+      for (int c = 0; c < nc; ++c)
+#pragma unroll
+        for (int u = 0; u < 6; ++u) tr += q.rho(3 + u);
+      lambda = q.lambda0 * tr / T(3 * np + n_u);
+    }
+    // W_p = (H_pp + (rho_x + lambda) I)^-1 by cofactors (identity on lanes without a copy)
+    T w6[6] = {1, 0, 0, 1, 0, 1};
+    if (K.act) {
+      const T dg = q.rho_x + lambda;
+      const T a00 = h[0] + dg, a01 = h[1], a02 = h[2], a11 = h[3] + dg, a12 = h[4], a22 = h[5] + dg;
+      const T c00 = a11 * a22 - a12 * a12, c01 = a02 * a12 - a01 * a22, c02 = a01 * a12 - a02 * a11;
+      const T c11 = a00 * a22 - a02 * a02, c12 = a01 * a02 - a00 * a12, c22 = a00 * a11 - a01 * a01;
+      const T idet = Num<T>::rcp(a00 * c00 + a01 * c01 + a02 * c02);
+      w6[0] = c00 * idet, w6[1] = c01 * idet, w6[2] = c02 * idet;
+      w6[3] = c11 * idet, w6[4] = c12 * idet, w6[5] = c22 * idet;
+    }
+    // U_c = 2w_c A_c W_p g_p and, per camera pair c1 <= c2 (00, 01, 11), the Schur weight
+    // Q = [c1 = c2] 2w_1 I - (2w_1 A_1) W_p (2w_2 A_2)^T
+    {
+      const T Wg0 = w6[0] * gp[0] + w6[1] * gp[1] + w6[2] * gp[2];
+      const T Wg1 = w6[1] * gp[0] + w6[3] * gp[1] + w6[4] * gp[2];
+      const T Wg2 = w6[2] * gp[0] + w6[4] * gp[1] + w6[5] * gp[2];
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        m.U[c][0] = m.tw[c] * (Ap[c][0][0] * Wg0 + Ap[c][0][1] * Wg1 + Ap[c][0][2] * Wg2);
+        m.U[c][1] = m.tw[c] * (Ap[c][1][0] * Wg0 + Ap[c][1][1] * Wg1 + Ap[c][1][2] * Wg2);
+      }
+#pragma unroll
+      for (int pr = 0; pr < 3; ++pr) {
+        const int c1 = pr == 2 ? 1 : 0, c2 = pr == 0 ? 0 : 1;
+        const T* a2r0 = Ap[c2][0];
+        const T* a2r1 = Ap[c2][1];
+        const T w0 = w6[0] * a2r0[0] + w6[1] * a2r0[1] + w6[2] * a2r0[2];
+        const T w1 = w6[1] * a2r0[0] + w6[3] * a2r0[1] + w6[4] * a2r0[2];
+        const T w2 = w6[2] * a2r0[0] + w6[4] * a2r0[1] + w6[5] * a2r0[2];
+        const T x0 = w6[0] * a2r1[0] + w6[1] * a2r1[1] + w6[2] * a2r1[2];
+        const T x1 = w6[1] * a2r1[0] + w6[3] * a2r1[1] + w6[4] * a2r1[2];
+        const T x2 = w6[2] * a2r1[0] + w6[4] * a2r1[1] + w6[5] * a2r1[2];
+        const T* a1r0 = Ap[c1][0];
+        const T* a1r1 = Ap[c1][1];
+        const T sw = m.tw[c1] * m.tw[c2], dgw = c1 == c2 ? m.tw[c1] : T(0);
+        m.Q[pr][0] = dgw - sw * (a1r0[0] * w0 + a1r0[1] * w1 + a1r0[2] * w2);
+        m.Q[pr][1] = -sw * (a1r0[0] * x0 + a1r0[1] * x1 + a1r0[2] * x2);
+        m.Q[pr][2] = -sw * (a1r1[0] * w0 + a1r1[1] * w1 + a1r1[2] * w2);
+        m.Q[pr][3] = dgw - sw * (a1r1[0] * x0 + a1r1[1] * x1 + a1r1[2] * x2);
+      }
+    }
+    // sums over the block's points, G values at a time
+    sys_reduce<T, G>(m, grp, Z, dst, std::make_integer_sequence<int, (kSysValues + G - 1) / G>{});
+    grp.sync();
+    // lane i < n_u takes row i of S + diag(rho_c) + lambda I (entries j <= i), g_i (the camera
+    // gradient with its penalty) and its right-hand side rhs_i - g_i; a block with one camera
+    // is padded to 12 x 12 by identity rows with a zero right-hand side, which leave its
+    // factor and solution as they are
+    T a[12], lc[12], y = 0, gi = 0;
+    {
+      const bool row = gl < n_u;
+      const int c = row ? gl / 6 : 0, u = row ? gl % 6 : 0;
+      const T shift = q.rho(3 + u) + lambda;
+#pragma unroll
+      for (int j = 0; j < 12; ++j) {
+        a[j] = row && j <= gl ? Z.sys[13 * j + gl] + (j == gl ? shift : T(0)) : T(j == gl ? 1 : 0);
+        lc[j] = 0;
+      }
+      if (row) {
+        gi = Z.sys[TwoCamShared<T>::kG + gl] + q.rho(3 + u) * (Z.a[c][u] + Z.d[c][u]);
+        y = Z.sys[TwoCamShared<T>::kRhs + gl] - gi;
+      }
+    }
+    // Cholesky factor in registers: lane i holds row i of L (a) and, below the diagonal,
+    // column i (lc[j] = L_ji); pivots and columns pass by shuffles
+    bool spd = true;
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      const T piv = grp.bcast(a[k], k);
+      spd = spd && piv > T(0);
+      const T lkk = Num<T>::sqrt_(piv);
+      if (gl == k) a[k] = lkk;
+      else if (gl > k) a[k] = Num<T>::div(a[k], lkk);
+#pragma unroll 11
+      for (int j = k + 1; j < 12; ++j) {
+        const T ljk = grp.bcast(a[k], j);
+        if (gl == k) lc[j] = ljk;
+        if (gl >= j) a[j] -= a[k] * ljk;
+      }
+    }
+    if (!spd) {
+      lambda *= T(10);
+      continue;
+    }
+    // L y = rhs - g, then L^T dy = y; lane i holds entry i (zero beyond n_u)
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      if (gl == k) y = Num<T>::div(y, a[k]);
+      const T yk = grp.bcast(y, k);
+      if (gl > k) y -= a[k] * yk;
+    }
+#pragma unroll
+    for (int k = 11; k >= 0; --k) {
+      if (gl == k) y = Num<T>::div(y, a[k]);
+      const T xk = grp.bcast(y, k);
+      if (gl < k) y -= lc[k] * xk;
+    }
+    // point step dx = -W_p (g_p + sum_c 2w_c A_c^T B_c dy_c); predicted decrease
+    // (lambda |d|^2 - g.d) / 2
+    T xt[3], gd = 0, dd = 0;
+    {
+      T t3[3] = {gp[0], gp[1], gp[2]};
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        T r0 = 0, r1 = 0;
+#pragma unroll
+        for (int u = 0; u < 6; ++u) {
+          const T dyu = grp.bcast(y, 6 * c + u);
+          r0 += m.Bc[c][0][u] * dyu;
+          r1 += m.Bc[c][1][u] * dyu;
+        }
+        r0 *= m.tw[c];
+        r1 *= m.tw[c];
+#pragma unroll
+        for (int u = 0; u < 3; ++u) t3[u] += Ap[c][0][u] * r0 + Ap[c][1][u] * r1;
+      }
+      T dx[3] = {0, 0, 0};
+      if (K.act) {
+        dx[0] = -(w6[0] * t3[0] + w6[1] * t3[1] + w6[2] * t3[2]);
+        dx[1] = -(w6[1] * t3[0] + w6[3] * t3[1] + w6[4] * t3[2]);
+        dx[2] = -(w6[2] * t3[0] + w6[4] * t3[1] + w6[5] * t3[2]);
+      }
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        gd += gp[u] * dx[u];
+        dd += dx[u] * dx[u];
+        xt[u] = dp[u] + dx[u];
+      }
+    }
+    if (gl < n_u) {  // the camera terms, one per lane
+      gd += gi * y;
+      dd += y * y;
+    }
+    gd = grp.sum(gd);
+    dd = grp.sum(dd);
+    const T pred = T(0.5) * (lambda * dd - gd);
+    const bool trust = isfinite(L) && q.model_tol > T(0) &&
+                       pred <= q.model_tol * Num<T>::unit_roundoff * (fabs(L) + Z.sys[TwoCamShared<T>::kNoise]);
+    if (gl < n_u) Z.dt[gl / 6][gl % 6] = Z.d[gl / 6][gl % 6] + y;
+    grp.sync();
+    const T Lt = K.objective(q, grp, xt, Z, Z.dt, nc);
+    if (Lt < Num<T>::inf() && (trust || Lt < L)) {
+#pragma unroll
+      for (int u = 0; u < 3; ++u) dp[u] = xt[u];
+      if (gl < n_u) Z.d[gl / 6][gl % 6] = Z.dt[gl / 6][gl % 6];
+      L = Lt;  // Eq. (14) at the accepted point, trusted step or not
+      const T lr = Num<T>::tenth(lambda);
+      lambda = lr > q.lambda_min ? lr : q.lambda_min;
+    } else {
+      lambda *= T(10);
+    }
+    grp.sync();
+  }
+  bool finite = true;
+  if (K.act) {
+#pragma unroll
+    for (int u = 0; u < 3; ++u) {
+      pdel[u * B.n_pc + pc] = dp[u];
+      finite = finite && isfinite(dp[u]);
+    }
+  }
+  if (gl < n_u) {
+    const T v = Z.d[gl / 6][gl % 6];
+    cdel[(gl % 6) * B.n_cc + bi.c0 + gl / 6] = v;
+    finite = finite && isfinite(v);
+  }
+  if (!finite) atomicOr(B.err, 1);
+  grp.sync();
+}
+
+// Blocks [lo, hi) of one size class with at most two cameras and G points, one group of G
+// lanes per block, the groups' systems in static shared memory.
+template <typename T, int G>
+__global__ void __launch_bounds__(kBlkWarps * 32, (sizeof(T) == 4 ? 4 : 1))
+    block_solve_2cam_kernel(BlockProblem B, Prm<T> q, int cur, int lo, int hi) {
+  constexpr int kPer = 32 / G;
+  __shared__ TwoCamShared<T> sh[kBlkWarps * kPer];
+  __shared__ short dst[kSysSlots];
+  for (int e = threadIdx.x; e < kSysSlots; e += blockDim.x) dst[e] = (short)sys_dst(e);
+  __syncthreads();
+  const int warps = blockDim.x >> 5, warp = threadIdx.x >> 5;
+  const Grp<G> grp(threadIdx.x & 31);
+  TwoCamShared<T>& Z = sh[warp * kPer + grp.base / G];
+  const int stride = gridDim.x * warps * kPer;
+  int b = lo + (blockIdx.x * warps + warp) * kPer + grp.base / G;
+  BlockInfo bi{};
+  if (b < hi) bi = B.blocks[b];
+  for (; b < hi; b += stride) {
+    const bool more = b + stride < hi;
+    BlockInfo nb{};
+    if (more) nb = B.blocks[b + stride];
+    solve_block_2cam<T, G>(B, q, bi, grp, Z, dst, more ? &nb : nullptr);
+    bi = nb;
+  }
+}
+
 // Blocks [lo, hi) of one size class, each solved by a group of G lanes holding PPL
 // point copies each (32 / G groups per warp, blockDim.x / 32 warps per CTA); groups
 // stride through the range independently.
@@ -1288,6 +1811,30 @@ cudaError_t launch_block_class_1cam(dba_block_ctx* ctx, int lo, int hi) {
   return cudaGetLastError();
 }
 
+// Blocks [lo, hi) with at most two cameras and G points: the register solve, groups of G lanes.
+template <typename T, int G>
+cudaError_t launch_block_class_2cam(dba_block_ctx* ctx, int lo, int hi) {
+  if (hi <= lo) return cudaSuccess;
+  constexpr int kThreads = dba::kBlkWarps * 32;
+  static std::atomic<int> cached{0};  // CTAs of a full wave
+  int grid = cached.load();
+  if (!grid) {
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dba::block_solve_2cam_kernel<T, G>,
+                                                                  kThreads, 0);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    grid = std::max(per_sm, 1) * sms;
+    cached.store(grid);
+  }
+  const int need = dba::blocks_of(hi - lo, dba::kBlkWarps * (32 / G));
+  const int g = std::max(1, std::min(need, grid));
+  dba::block_solve_2cam_kernel<T, G><<<g, kThreads, 0, ctx->stream>>>(ctx->B, dba::make_prm<T>(ctx->prm), ctx->cur,
+                                                                       lo, hi);
+  return cudaGetLastError();
+}
+
 template <typename T, int G, int PPL>
 cudaError_t launch_block_class_kc(dba_block_ctx* ctx, int k) {
   const int lo = ctx->cls[k], hi = ctx->cls[k + 1];
@@ -1295,8 +1842,14 @@ cudaError_t launch_block_class_kc(dba_block_ctx* ctx, int k) {
     if constexpr (PPL == 1) return launch_block_class_1cam<T, G>(ctx, lo, hi);
     return launch_block_class<T, 1, G, PPL>(ctx, lo, hi);
   }
-  if constexpr (G == 16) {  // the 16-lane class holds at most 2 cameras
-    return launch_block_class<T, 2, G, PPL>(ctx, lo, hi);
+  if constexpr (PPL == 1) {
+    // the 16-lane class holds at most 2 cameras, the 32-lane one at most block_cams
+    if constexpr (G == 16) {
+      return launch_block_class_2cam<T, G>(ctx, lo, hi);
+    } else {
+      if (ctx->kappa == 2) return launch_block_class_2cam<T, G>(ctx, lo, hi);
+      return launch_block_class<T, 4, G, PPL>(ctx, lo, hi);
+    }
   } else {
     if (ctx->kappa == 2) return launch_block_class<T, 2, G, PPL>(ctx, lo, hi);
     return launch_block_class<T, 4, G, PPL>(ctx, lo, hi);
@@ -1306,7 +1859,8 @@ cudaError_t launch_block_class_kc(dba_block_ctx* ctx, int k) {
 // The size classes of the block list, in its order: one camera and at most 8 points
 // (groups of 8 lanes), at most 2 cameras and 16 points (16 lanes), at most 32 points
 // (32 lanes), the rest (32 lanes holding two point copies each).  Blocks with one camera
-// (the first class; the next two when block_cams = 1) take the register-resident solve.
+// (the first class; the next two when block_cams = 1) take the register-resident solve,
+// blocks of the next two classes with at most two cameras the reduce-scatter solve.
 template <typename T>
 cudaError_t launch_block_solve(dba_block_ctx* ctx) {
   cudaError_t e = launch_block_class_1cam<T, 8>(ctx, ctx->cls[0], ctx->cls[1]);
