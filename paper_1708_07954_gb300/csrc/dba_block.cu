@@ -682,11 +682,11 @@ __device__ __forceinline__ void prefetch_block(const BlockProblem& B, const Bloc
     asm volatile("prefetch.global.L1 [%0];" ::"l"(B.pc_pt + pc));
     asm volatile("prefetch.global.L1 [%0];" ::"l"(B.pc_obs + pc));
   }
-  if (gl < 6) {
+  for (int u = gl; u < 6; u += G) {
     const long long cc = nb.c0;
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(cdel + gl * B.n_cc + cc));
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(B.cc_a + gl * B.n_cc + cc));
-    if (gl == 0) asm volatile("prefetch.global.L1 [%0];" ::"l"(B.cc_cam + cc));
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(cdel + u * B.n_cc + cc));
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(B.cc_a + u * B.n_cc + cc));
+    if (u == 0) asm volatile("prefetch.global.L1 [%0];" ::"l"(B.cc_cam + cc));
   }
 }
 
@@ -702,8 +702,8 @@ __device__ void solve_block_1cam(const BlockProblem& B, const Prm<T>& q, const B
   T cd[6], dp[PPL][3];
   const long long cc = bi.c0;
   {
-    // every lane forms the camera's six coordinates (the same bits); lane u writes back the
-    // deferred dual ascent of coordinate u
+    // every lane forms the camera's six coordinates (the same bits); lane u mod G writes back
+    // the deferred dual ascent of coordinate u
     const int jc = B.cc_cam[cc];
 #pragma unroll
     for (int u = 0; u < 6; ++u) {
@@ -714,7 +714,7 @@ __device__ void solve_block_1cam(const BlockProblem& B, const Prm<T>& q, const B
       if (B.pending) {
         cd[u] = off + ch;
         const double an = a + to_f64<T>(cd[u]);
-        if (gl == u) B.cc_a[u * B.n_cc + cc] = an;
+        if (gl == u % G) B.cc_a[u * B.n_cc + cc] = an;
         K.ca[u] = from_f64<T>(an);
       } else {
         cd[u] = off;
@@ -932,7 +932,7 @@ __device__ void solve_block_1cam(const BlockProblem& B, const Prm<T>& q, const B
   }
 #pragma unroll
   for (int u = 0; u < 6; ++u)
-    if (gl == u) {
+    if (gl == u % G) {
       cdel[u * B.n_cc + cc] = cd[u];
       finite = finite && isfinite(cd[u]);
     }
@@ -1147,9 +1147,9 @@ __device__ __forceinline__ void prefetch_block_2cam(const BlockProblem& B, const
     asm volatile("prefetch.global.L1 [%0];" ::"l"(B.pc_pt + pc));
     asm volatile("prefetch.global.L1 [%0];" ::"l"(B.pc_obs + pc));
   }
-  if (gl < 6 * nb.nc) {
-    const long long cc = (long long)nb.c0 + gl / 6;
-    const int u = gl % 6;
+  for (int r = gl; r < 6 * nb.nc; r += G) {
+    const long long cc = (long long)nb.c0 + r / 6;
+    const int u = r % 6;
     asm volatile("prefetch.global.L1 [%0];" ::"l"(cdel + u * B.n_cc + cc));
     asm volatile("prefetch.global.L1 [%0];" ::"l"(B.cc_a + u * B.n_cc + cc));
     if (u == 0) asm volatile("prefetch.global.L1 [%0];" ::"l"(B.cc_cam + cc));
@@ -1159,22 +1159,27 @@ __device__ __forceinline__ void prefetch_block_2cam(const BlockProblem& B, const
 template <typename T, int G>
 __device__ void solve_block_2cam(const BlockProblem& B, const Prm<T>& q, const BlockInfo& bi, const Grp<G>& grp,
                                  TwoCamShared<T>& Z, const short* dst, const BlockInfo* next) {
-  static_assert(G >= 12, "one lane per camera coordinate");
+  // rows of the camera system held by a lane: gl + G t, t < R
+  constexpr int R = (12 + G - 1) / G;
   using V2 = typename Num<T>::V2;
   const int gl = grp.gl, np = bi.np, nc = bi.nc, n_u = 6 * nc;
   T* pdel = static_cast<T*>(B.pc_delta);
   T* cdel = static_cast<T*>(B.cc_delta);
-  // camera copies: lane 6 c + u takes coordinate u of camera c; an absent second camera is
+  // camera copies: row r = 6 c + u is coordinate u of camera c; an absent second camera is
   // zero, so that the sums over both camera slots below need no test
-  if (gl < n_u) {
-    const int c = gl / 6, u = gl % 6;
-    const long long cc = (long long)bi.c0 + c;
-    const int j = B.cc_cam[cc];
-    deferred_ascent<T>(B, static_cast<const T*>(B.Ym)[6 * (long long)j + u],
-                       static_cast<const T*>(B.DY)[6 * (long long)j + u], cdel[u * B.n_cc + cc],
-                       B.cc_a + u * B.n_cc + cc, Z.vbar[c][u], Z.d[c][u], Z.a[c][u]);
-  } else if (gl < 12) {
-    Z.vbar[gl / 6][gl % 6] = Z.d[gl / 6][gl % 6] = Z.a[gl / 6][gl % 6] = 0;
+#pragma unroll
+  for (int t = 0; t < R; ++t) {
+    const int r = gl + G * t;
+    if (r < n_u) {
+      const int c = r / 6, u = r % 6;
+      const long long cc = (long long)bi.c0 + c;
+      const int j = B.cc_cam[cc];
+      deferred_ascent<T>(B, static_cast<const T*>(B.Ym)[6 * (long long)j + u],
+                         static_cast<const T*>(B.DY)[6 * (long long)j + u], cdel[u * B.n_cc + cc],
+                         B.cc_a + u * B.n_cc + cc, Z.vbar[c][u], Z.d[c][u], Z.a[c][u]);
+    } else if (r < 12) {
+      Z.vbar[r / 6][r % 6] = Z.d[r / 6][r % 6] = Z.a[r / 6][r % 6] = 0;
+    }
   }
   const long long pc = (long long)bi.p0 + gl;
   TwoCamPt<T> K;
@@ -1327,58 +1332,79 @@ __device__ void solve_block_2cam(const BlockProblem& B, const Prm<T>& q, const B
     // sums over the block's points, G values at a time
     sys_reduce<T, G>(m, grp, Z, dst, std::make_integer_sequence<int, (kSysValues + G - 1) / G>{});
     grp.sync();
-    // lane i < n_u takes row i of S + diag(rho_c) + lambda I (entries j <= i), g_i (the camera
-    // gradient with its penalty) and its right-hand side rhs_i - g_i; a block with one camera
-    // is padded to 12 x 12 by identity rows with a zero right-hand side, which leave its
-    // factor and solution as they are
-    T a[12], lc[12], y = 0, gi = 0;
-    {
-      const bool row = gl < n_u;
-      const int c = row ? gl / 6 : 0, u = row ? gl % 6 : 0;
+    // row r < n_u of S + diag(rho_c) + lambda I (entries j <= r), g_r (the camera gradient
+    // with its penalty) and the right-hand side rhs_r - g_r, on lane r mod G; a block with one
+    // camera is padded to 12 x 12 by identity rows with a zero right-hand side, which leave
+    // its factor and solution as they are
+    T a[R][12], lc[R][12], y[R], gi[R];
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      const int r = gl + G * t;
+      const bool row = r < n_u;
+      const int c = row ? r / 6 : 0, u = row ? r % 6 : 0;
       const T shift = q.rho(3 + u) + lambda;
 #pragma unroll
       for (int j = 0; j < 12; ++j) {
-        a[j] = row && j <= gl ? Z.sys[13 * j + gl] + (j == gl ? shift : T(0)) : T(j == gl ? 1 : 0);
-        lc[j] = 0;
+        a[t][j] = row && j <= r ? Z.sys[13 * j + r] + (j == r ? shift : T(0)) : T(j == r ? 1 : 0);
+        lc[t][j] = 0;
       }
+      gi[t] = y[t] = 0;
       if (row) {
-        gi = Z.sys[TwoCamShared<T>::kG + gl] + q.rho(3 + u) * (Z.a[c][u] + Z.d[c][u]);
-        y = Z.sys[TwoCamShared<T>::kRhs + gl] - gi;
+        gi[t] = Z.sys[TwoCamShared<T>::kG + r] + q.rho(3 + u) * (Z.a[c][u] + Z.d[c][u]);
+        y[t] = Z.sys[TwoCamShared<T>::kRhs + r] - gi[t];
       }
     }
-    // Cholesky factor in registers: lane i holds row i of L (a) and, below the diagonal,
-    // column i (lc[j] = L_ji); pivots and columns pass by shuffles
+    // Cholesky factor in registers: each held row r of L (a) and, below the diagonal,
+    // column r (lc[j] = L_jr); pivots and columns pass by shuffles.  Row k sits on lane
+    // k mod G in slot k / G; the tests on G t skip rows a slot cannot hold.
     bool spd = true;
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-      const T piv = grp.bcast(a[k], k);
+      const T piv = grp.bcast(a[k / G][k], k % G);
       spd = spd && piv > T(0);
       const T lkk = Num<T>::sqrt_(piv);
-      if (gl == k) a[k] = lkk;
-      else if (gl > k) a[k] = Num<T>::div(a[k], lkk);
+#pragma unroll
+      for (int t = 0; t < R; ++t) {
+        if (G * t + G - 1 < k) continue;
+        const int r = gl + G * t;
+        if (r == k) a[t][k] = lkk;
+        else if (r > k) a[t][k] = Num<T>::div(a[t][k], lkk);
+      }
 #pragma unroll 11
       for (int j = k + 1; j < 12; ++j) {
-        const T ljk = grp.bcast(a[k], j);
-        if (gl == k) lc[j] = ljk;
-        if (gl >= j) a[j] -= a[k] * ljk;
+        const T ljk = grp.bcast(a[j / G][k], j % G);
+        if (gl == k % G) lc[k / G][j] = ljk;
+#pragma unroll
+        for (int t = 0; t < R; ++t) {
+          if (G * t + G - 1 < j) continue;
+          if (gl + G * t >= j) a[t][j] -= a[t][k] * ljk;
+        }
       }
     }
     if (!spd) {
       lambda *= T(10);
       continue;
     }
-    // L y = rhs - g, then L^T dy = y; lane i holds entry i (zero beyond n_u)
+    // L y = rhs - g, then L^T dy = y; row r's entry on lane r mod G (zero beyond n_u)
 #pragma unroll
     for (int k = 0; k < 12; ++k) {
-      if (gl == k) y = Num<T>::div(y, a[k]);
-      const T yk = grp.bcast(y, k);
-      if (gl > k) y -= a[k] * yk;
+      if (gl == k % G) y[k / G] = Num<T>::div(y[k / G], a[k / G][k]);
+      const T yk = grp.bcast(y[k / G], k % G);
+#pragma unroll
+      for (int t = 0; t < R; ++t) {
+        if (G * t + G - 1 <= k) continue;
+        if (gl + G * t > k) y[t] -= a[t][k] * yk;
+      }
     }
 #pragma unroll
     for (int k = 11; k >= 0; --k) {
-      if (gl == k) y = Num<T>::div(y, a[k]);
-      const T xk = grp.bcast(y, k);
-      if (gl < k) y -= lc[k] * xk;
+      if (gl == k % G) y[k / G] = Num<T>::div(y[k / G], a[k / G][k]);
+      const T xk = grp.bcast(y[k / G], k % G);
+#pragma unroll
+      for (int t = 0; t < R; ++t) {
+        if (G * t >= k) continue;
+        if (gl + G * t < k) y[t] -= lc[t][k] * xk;
+      }
     }
     // point step dx = -W_p (g_p + sum_c 2w_c A_c^T B_c dy_c); predicted decrease
     // (lambda |d|^2 - g.d) / 2
@@ -1390,7 +1416,7 @@ __device__ void solve_block_2cam(const BlockProblem& B, const Prm<T>& q, const B
         T r0 = 0, r1 = 0;
 #pragma unroll
         for (int u = 0; u < 6; ++u) {
-          const T dyu = grp.bcast(y, 6 * c + u);
+          const T dyu = grp.bcast(y[(6 * c + u) / G], (6 * c + u) % G);
           r0 += m.Bc[c][0][u] * dyu;
           r1 += m.Bc[c][1][u] * dyu;
         }
@@ -1412,22 +1438,32 @@ __device__ void solve_block_2cam(const BlockProblem& B, const Prm<T>& q, const B
         xt[u] = dp[u] + dx[u];
       }
     }
-    if (gl < n_u) {  // the camera terms, one per lane
-      gd += gi * y;
-      dd += y * y;
-    }
+#pragma unroll
+    for (int t = 0; t < R; ++t)
+      if (gl + G * t < n_u) {  // the camera terms of the rows this lane holds
+        gd += gi[t] * y[t];
+        dd += y[t] * y[t];
+      }
     gd = grp.sum(gd);
     dd = grp.sum(dd);
     const T pred = T(0.5) * (lambda * dd - gd);
     const bool trust = isfinite(L) && q.model_tol > T(0) &&
                        pred <= q.model_tol * Num<T>::unit_roundoff * (fabs(L) + Z.sys[TwoCamShared<T>::kNoise]);
-    if (gl < n_u) Z.dt[gl / 6][gl % 6] = Z.d[gl / 6][gl % 6] + y;
+#pragma unroll
+    for (int t = 0; t < R; ++t) {
+      const int r = gl + G * t;
+      if (r < n_u) Z.dt[r / 6][r % 6] = Z.d[r / 6][r % 6] + y[t];
+    }
     grp.sync();
     const T Lt = K.objective(q, grp, xt, Z, Z.dt, nc);
     if (Lt < Num<T>::inf() && (trust || Lt < L)) {
 #pragma unroll
       for (int u = 0; u < 3; ++u) dp[u] = xt[u];
-      if (gl < n_u) Z.d[gl / 6][gl % 6] = Z.dt[gl / 6][gl % 6];
+#pragma unroll
+      for (int t = 0; t < R; ++t) {
+        const int r = gl + G * t;
+        if (r < n_u) Z.d[r / 6][r % 6] = Z.dt[r / 6][r % 6];
+      }
       L = Lt;  // Eq. (14) at the accepted point, trusted step or not
       const T lr = Num<T>::tenth(lambda);
       lambda = lr > q.lambda_min ? lr : q.lambda_min;
@@ -1444,10 +1480,14 @@ __device__ void solve_block_2cam(const BlockProblem& B, const Prm<T>& q, const B
       finite = finite && isfinite(dp[u]);
     }
   }
-  if (gl < n_u) {
-    const T v = Z.d[gl / 6][gl % 6];
-    cdel[(gl % 6) * B.n_cc + bi.c0 + gl / 6] = v;
-    finite = finite && isfinite(v);
+#pragma unroll
+  for (int t = 0; t < R; ++t) {
+    const int r = gl + G * t;
+    if (r < n_u) {
+      const T v = Z.d[r / 6][r % 6];
+      cdel[(r % 6) * B.n_cc + bi.c0 + r / 6] = v;
+      finite = finite && isfinite(v);
+    }
   }
   if (!finite) atomicOr(B.err, 1);
   grp.sync();
@@ -1700,6 +1740,7 @@ struct dba_block_ctx {
   int cur = 0;
   long long iters = 0;
   int cls[dba::kBlkClasses + 1] = {};  // block list cut into size classes: [cls[k], cls[k + 1])
+  int small[dba::kBlkClasses][4] = {};  // in class k: first block of more than 1, 2, 4, 8 points
   std::string err = "no error";
   // host copy of the layout (caller order <-> block order)
   std::vector<long long> blk_obs;  // block order -> caller observation
@@ -1843,9 +1884,12 @@ cudaError_t launch_block_class_kc(dba_block_ctx* ctx, int k) {
     return launch_block_class<T, 1, G, PPL>(ctx, lo, hi);
   }
   if constexpr (PPL == 1) {
-    // the 16-lane class holds at most 2 cameras, the 32-lane one at most block_cams
+    // the 16-lane class holds at most 2 cameras (its blocks of at most 8 points in groups of
+    // 8 lanes), the 32-lane one at most block_cams
     if constexpr (G == 16) {
-      return launch_block_class_2cam<T, G>(ctx, lo, hi);
+      const int mid = ctx->small[k][3];
+      cudaError_t e = launch_block_class_2cam<T, 8>(ctx, lo, mid);
+      return e == cudaSuccess ? launch_block_class_2cam<T, 16>(ctx, mid, hi) : e;
     } else {
       if (ctx->kappa == 2) return launch_block_class_2cam<T, G>(ctx, lo, hi);
       return launch_block_class<T, 4, G, PPL>(ctx, lo, hi);
@@ -1857,13 +1901,18 @@ cudaError_t launch_block_class_kc(dba_block_ctx* ctx, int k) {
 }
 
 // The size classes of the block list, in its order: one camera and at most 8 points
-// (groups of 8 lanes), at most 2 cameras and 16 points (16 lanes), at most 32 points
-// (32 lanes), the rest (32 lanes holding two point copies each).  Blocks with one camera
-// (the first class; the next two when block_cams = 1) take the register-resident solve,
-// blocks of the next two classes with at most two cameras the reduce-scatter solve.
+// (groups of 1, 2, 4 or 8 lanes by the block's points), at most 2 cameras and 16 points
+// (16 lanes; 8 for two cameras and at most 8 points), at most 32 points (32 lanes), the rest
+// (32 lanes holding two point copies each).  Blocks with one camera (the first class; the
+// next two when block_cams = 1) take the register-resident solve, blocks of the next two
+// classes with at most two cameras the reduce-scatter solve.
 template <typename T>
 cudaError_t launch_block_solve(dba_block_ctx* ctx) {
-  cudaError_t e = launch_block_class_1cam<T, 8>(ctx, ctx->cls[0], ctx->cls[1]);
+  const int* c0 = ctx->small[0];
+  cudaError_t e = launch_block_class_1cam<T, 1>(ctx, ctx->cls[0], c0[0]);
+  if (e == cudaSuccess) e = launch_block_class_1cam<T, 2>(ctx, c0[0], c0[1]);
+  if (e == cudaSuccess) e = launch_block_class_1cam<T, 4>(ctx, c0[1], c0[2]);
+  if (e == cudaSuccess) e = launch_block_class_1cam<T, 8>(ctx, c0[2], ctx->cls[1]);
   if (e == cudaSuccess) e = launch_block_class_kc<T, 16, 1>(ctx, 1);
   if (e == cudaSuccess) e = launch_block_class_kc<T, 32, 1>(ctx, 2);
   if (e == cudaSuccess) e = launch_block_class_kc<T, 32, 2>(ctx, 3);
@@ -1945,6 +1994,7 @@ struct BlockHostLayout {
   std::vector<long long> blk_obs;  // block order -> caller observation
   std::vector<dba::BlockInfo> blocks;
   int cls[dba::kBlkClasses + 1] = {};
+  int small[dba::kBlkClasses][4] = {};
   std::vector<int> pc_obs, pc_pt, cc_cam, obs_pt, obs_cam;
   std::vector<unsigned char> obs_lc;
   std::vector<int> pt_off, cam_off, pt_cp, cam_cp;
@@ -2044,18 +2094,25 @@ std::string build_block_layout(int n_cams, int n_pts, long long l, const int32_t
     H.flops_start = 64.0 * (double)l + 9.0 * (double)n_pc + 24.0 * (double)n_cc;
   }
   // size classes of the solve kernel (lane groups of 8, 16, 32, 32 with two copies per
-  // lane), each contiguous
+  // lane), each contiguous and ordered by points, so that its small blocks can take
+  // narrower lane groups
   {
     auto cls_of = [](const dba::BlockInfo& b) {
       return b.nc == 1 && b.np <= 8 ? 0 : b.nc <= 2 && b.np <= 16 ? 1 : b.np <= 32 ? 2 : 3;
     };
-    std::stable_sort(blocks.begin(), blocks.end(),
-                     [&](const dba::BlockInfo& a, const dba::BlockInfo& b) { return cls_of(a) < cls_of(b); });
+    std::stable_sort(blocks.begin(), blocks.end(), [&](const dba::BlockInfo& a, const dba::BlockInfo& b) {
+      const int ca = cls_of(a), cb = cls_of(b);
+      return ca != cb ? ca < cb : a.np < b.np;
+    });
     H.cls[0] = 0;
-    for (int k = 0; k < dba::kBlkClasses; ++k)
-      H.cls[k + 1] = (int)(std::partition_point(blocks.begin(), blocks.end(),
-                                                   [&](const dba::BlockInfo& b) { return cls_of(b) <= k; }) -
+    for (int k = 0; k < dba::kBlkClasses; ++k) {
+      const auto lo = blocks.begin() + H.cls[k];
+      const auto hi = std::partition_point(lo, blocks.end(), [&](const dba::BlockInfo& b) { return cls_of(b) <= k; });
+      H.cls[k + 1] = (int)(hi - blocks.begin());
+      for (int t = 0; t < 4; ++t)
+        H.small[k][t] = (int)(std::partition_point(lo, hi, [&](const dba::BlockInfo& b) { return b.np <= (1 << t); }) -
                               blocks.begin());
+    }
   }
   // copy lists per point and per camera (consensus)
   std::vector<int>&pt_off = H.pt_off, &cam_off = H.cam_off, &pt_cp = H.pt_cp, &cam_cp = H.cam_cp;
@@ -2170,6 +2227,8 @@ dba_status dba_block_set_observations(dba_block_ctx* ctx, int32_t n_cams, int32_
     ctx->blk_obs = H.blk_obs;
     ctx->h_blocks = H.blocks;
     for (int k = 0; k <= dba::kBlkClasses; ++k) ctx->cls[k] = H.cls[k];
+    for (int k = 0; k < dba::kBlkClasses; ++k)
+      for (int t = 0; t < 4; ++t) ctx->small[k][t] = H.small[k][t];
     ctx->flops_step = H.flops_step;
     ctx->flops_start = H.flops_start;
     const std::vector<dba::BlockInfo>& blocks = H.blocks;
