@@ -1887,9 +1887,10 @@ cudaError_t launch_block_class_kc(dba_block_ctx* ctx, int k) {
     // the 16-lane class holds at most 2 cameras (its blocks of at most 8 points in groups of
     // 8 lanes), the 32-lane one at most block_cams
     if constexpr (G == 16) {
-      const int mid = ctx->small[k][3];
-      cudaError_t e = launch_block_class_2cam<T, 8>(ctx, lo, mid);
-      return e == cudaSuccess ? launch_block_class_2cam<T, 16>(ctx, mid, hi) : e;
+      const int m4 = ctx->small[k][2], m8 = ctx->small[k][3];
+      cudaError_t e = launch_block_class_2cam<T, 4>(ctx, lo, m4);
+      if (e == cudaSuccess) e = launch_block_class_2cam<T, 8>(ctx, m4, m8);
+      return e == cudaSuccess ? launch_block_class_2cam<T, 16>(ctx, m8, hi) : e;
     } else {
       if (ctx->kappa == 2) return launch_block_class_2cam<T, G>(ctx, lo, hi);
       return launch_block_class<T, 4, G, PPL>(ctx, lo, hi);
