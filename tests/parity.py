@@ -1,4 +1,4 @@
-"""Error measures shared by the GPU parity tests."""
+"""Error measures and block settings shared by the GPU parity tests."""
 import numpy as np
 
 
@@ -13,3 +13,10 @@ def colerr(a, b):
         a, b = a[:, None], b[:, None]
     scale = np.maximum(np.abs(b).max(axis=0), 1e-300)
     return float((np.abs(a - b).max(axis=0) / scale).max())
+
+
+# Block sizes (points, cameras) of the block parity test.  Together they put blocks in every
+# kernel variant of the block solve: one-camera blocks in groups of 1, 2, 4, 8, 16 and 32
+# lanes; two-camera blocks in groups of 4, 8, 16 and 32 lanes; blocks of up to 4 cameras and
+# up to 64 points (two point copies a lane) in the shared-memory kernel.
+BLOCK_SETTINGS = [(1, 1), (8, 2), (32, 4), (5, 3), (32, 1), (32, 2), (64, 1), (48, 2), (64, 4)]

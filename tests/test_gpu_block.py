@@ -1,7 +1,7 @@
 """Block subproblems (Sec. 3.1.4, Eq. 14) on the GPU against the block oracle."""
 import numpy as np
 import pytest
-from parity import colerr
+from parity import BLOCK_SETTINGS, colerr
 
 import oracle as O
 from paper_1708_07954_gb300 import build, dba
@@ -40,11 +40,8 @@ def size_classes(layout):
     return [int(c8.sum()), int(c16.sum()), int(c32.sum()), int((~c8 & ~c16 & ~c32).sum())]
 
 
-# together these put blocks in every (lane group, copies per lane, most cameras) kernel
-# variant: 8 lanes; 16 lanes with 1 and 2 cameras; 32 lanes with 1, 2 and 4 cameras, one
-# or two point copies per lane
-@pytest.mark.parametrize("pi,kappa", [(1, 1), (8, 2), (32, 4), (5, 3), (32, 1), (32, 2), (64, 1), (48, 2),
-                                      (64, 4)])
+# BLOCK_SETTINGS put blocks in every kernel variant (tests/test_block_variants.py checks it)
+@pytest.mark.parametrize("pi,kappa", BLOCK_SETTINGS)
 def test_fp64_matches_block_oracle_per_iteration(pi, kappa):
     sc = S.scene1(n_pts=400, n_cams=16, seed=17)
     with dba.BlockSolver(sc, pi, kappa, precision=dba.DBA_PREC_F64) as s:
