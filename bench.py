@@ -61,6 +61,9 @@ def parse(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-ttt", action="store_true", help="skip the time-to-0.5-px measurement")
     ap.add_argument("--no-workload3", action="store_true", help="skip the batch-of-256-scenes sub-record")
+    ap.add_argument("--no-blocks", action="store_true",
+                    help="skip the sub-record of the block subproblems (32 points x 2 cameras)")
+    ap.add_argument("--blocks-steps", type=int, default=20)
     ap.add_argument("--workload3-steps", type=int, default=100)
     ap.add_argument("--ttt-max-iters", type=int, default=400)
     ap.add_argument("--cpu-iters", type=int, default=2)
@@ -451,6 +454,10 @@ def run_ours(args, rank, world, local_rank):
               "what": "all scenes in one tile_iterate launch + one finalize per ADMM iteration (CUDA graph), "
                       "tile size by the autotuner (tile_obs = -1)"}
 
+    blocks = None
+    if args.workload == 2 and fp32 and not args.no_blocks and world == 1 and not args.warm_start:
+        blocks = block_subrecord(args, sc, stream)
+
     ttt = None
     if not args.no_ttt and args.workload == 2:
         # time to rmse_gt <= 0.5 px (noise-free projections, observations of outlier-free tracks),
@@ -524,6 +531,7 @@ def run_ours(args, rank, world, local_rank):
                              "what": "K5: consensus camera poses, per-observation reprojection and residual "
                                      "sums, final reduction (one dba_evaluate, CUDA events)"},
             "workload3": w3,
+            "blocks": blocks,
             "clocks": clk, "gpu_launches": (3 if args.warm_start else 2) * args.steps,
             "final": {k: final[k] for k in ("rmse_obs", "rmse_gt", "objective", "iters_done")},
         }
@@ -534,6 +542,47 @@ def run_ours(args, rank, world, local_rank):
 
 
 # ------------------------------------------------------------------ block subproblems
+def block_subrecord(args, sc, stream, pi=32, kappa=2):
+    """The same scene solved with block subproblems of Eq. (14), pi points x kappa cameras
+    per update (Sec. 4 finds about 32 points per update fastest): ms per iteration by CUDA
+    events, the block solve's share and roofline, and the time to 0.5 px."""
+    import torch
+
+    from paper_1708_07954_gb300 import dba
+
+    with dba.BlockSolver(sc, pi, kappa, precision=dba.DBA_PREC_F32_LOCAL, inner_steps=args.inner_steps,
+                         stream=stream.cuda_stream) as s:
+        layout = s.layout()
+        launches = s.launches_per_iteration()
+        s.iterate(args.warmup, stats=False)
+        torch.cuda.synchronize()
+        b0 = torch.cuda.Event(enable_timing=True)
+        b1 = torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        s.iterate(args.blocks_steps, stats=False)
+        b1.record(stream)
+        torch.cuda.synchronize()
+        ms = b0.elapsed_time(b1) / args.blocks_steps
+        prof = s.profile(args.blocks_steps)
+        flops = s.algorithmic_flops()
+    achieved_tf = flops / (prof["block_solve"] * 1e-3) / 1e12
+    rec = {"block_points": pi, "block_cams": kappa, **layout, "steps": args.blocks_steps, "ms_per_step": ms,
+           "value": sc.n_obs / (ms * 1e-3), "unit": UNIT, "kernels_ms": prof,
+           "block_solve_roofline": {"bound": "alu", "achieved": achieved_tf, "peak": FP32_PEAK_TFLOPS,
+                                    "unit": "TFLOP/s", "frac": achieved_tf / FP32_PEAK_TFLOPS,
+                                    "algorithmic_flops_per_launch": flops},
+           "gpu_launches_per_step": launches, "time_to_target": None,
+           "what": "block solves + point and camera consensus per ADMM iteration, FP32 block solves, "
+                   "FP64 consensus and duals"}
+    if not args.no_ttt:
+        with dba.BlockSolver(sc, pi, kappa, precision=dba.DBA_PREC_F32_LOCAL, inner_steps=args.inner_steps,
+                             stream=stream.cuda_stream) as s:
+            m = s.iterate_until(args.ttt_max_iters, 0.5)
+        rec["time_to_target"] = {"target_px": 0.5, "seconds": m["seconds"], "iters": m["iters_done"],
+                                 "rmse_gt": m["rmse_gt"], "reached": m["rmse_gt"] <= 0.5}
+    return rec
+
+
 def run_blocks(args, rank, world, local_rank):
     """The same line for the block subproblems of Eq. (14): block_points x block_cams per
     update, one iteration = block solves, consensus over copies, dual ascent."""
@@ -556,6 +605,7 @@ def run_blocks(args, rank, world, local_rank):
     solver = dba.BlockSolver(sc, P, K, precision=prec, inner_steps=args.inner_steps, stream=stream.cuda_stream)
     layout = solver.layout()
     classes = solver.size_classes()
+    launches = solver.launches_per_iteration()
     solver.iterate(args.warmup, stats=False)
     clocks = ClockSampler(local_rank if "CUDA_VISIBLE_DEVICES" not in os.environ else 0)
     clocks.start()
@@ -647,7 +697,7 @@ def run_blocks(args, rank, world, local_rank):
                        "l2": "inputs larger than L2, no flush",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "time_to_target": ttt,
-            "clocks": clk, "gpu_launches": (3 + sum(1 for c in classes if c)) * args.steps,
+            "clocks": clk, "gpu_launches": launches * args.steps,
             "final": {k: final[k] for k in ("rmse_obs", "rmse_gt", "objective", "iters_done")},
         }
         print(json.dumps(line), flush=True)

@@ -387,12 +387,17 @@ dba_status dba_block_build_layout(int32_t n_cams, int32_t n_pts, int64_t n_obs, 
                                   int32_t* blocks, int32_t* pc_point, int32_t* cc_camera, int64_t* counts,
                                   int64_t* size_classes);
 /* Blocks in each size class of the solve kernel, in launch order: one camera and at
- * most 8 points (8-lane groups), at most 2 cameras and 16 points (16 lanes), at most
- * 32 points (32 lanes), the rest (32 lanes, two point copies each).  Each nonempty
- * class is one kernel launch per iteration.  counts: DBA_BLOCK_SIZE_CLASSES entries,
- * caller-owned. */
+ * most 8 points (lane groups of 1, 2, 4 or 8 by the block's points), at most 2
+ * cameras and 16 points (16 lanes; two-camera blocks of at most 4 or 8 points in 4 or
+ * 8), at most 32 points (32 lanes), the rest (32 lanes, two point copies each).
+ * counts: DBA_BLOCK_SIZE_CLASSES entries, caller-owned. */
 #define DBA_BLOCK_SIZE_CLASSES 4
 dba_status dba_block_size_classes(const dba_block_ctx* ctx, int64_t* counts);
+/* Kernel launches one iteration of dba_block_iterate makes with the loaded layout: one
+ * block-solve launch per nonempty range of blocks that share a kernel and lane-group
+ * width, then the point and the camera consensus.  Launch bookkeeping of this library;
+ * the paper has no counterpart.  launches: caller-owned. */
+dba_status dba_block_launches_per_iteration(const dba_block_ctx* ctx, int32_t* launches);
 /* Algorithmic floating-point operations of one iteration's block solves (every
  * Gauss-Newton step counted in full with its trial objective; add/mul 1, fma 2,
  * reciprocal/square root/sine/cosine 1), counted from the loaded layout. */

@@ -1909,6 +1909,7 @@ cudaError_t launch_block_class_kc(dba_block_ctx* ctx, int k) {
 // classes with at most two cameras the reduce-scatter solve.
 template <typename T>
 cudaError_t launch_block_solve(dba_block_ctx* ctx) {
+  // block_solve_launches counts the nonempty ranges launched here; keep the two in step
   const int* c0 = ctx->small[0];
   cudaError_t e = launch_block_class_1cam<T, 1>(ctx, ctx->cls[0], c0[0]);
   if (e == cudaSuccess) e = launch_block_class_1cam<T, 2>(ctx, c0[0], c0[1]);
@@ -1918,6 +1919,28 @@ cudaError_t launch_block_solve(dba_block_ctx* ctx) {
   if (e == cudaSuccess) e = launch_block_class_kc<T, 32, 1>(ctx, 2);
   if (e == cudaSuccess) e = launch_block_class_kc<T, 32, 2>(ctx, 3);
   return e;
+}
+
+// Block-solve launches of one iteration: the nonempty ranges launch_block_solve launches.
+int block_solve_launches(const dba_block_ctx* ctx) {
+  std::vector<std::pair<int, int>> r;
+  const int* c0 = ctx->small[0];
+  r.push_back({ctx->cls[0], c0[0]});
+  r.push_back({c0[0], c0[1]});
+  r.push_back({c0[1], c0[2]});
+  r.push_back({c0[2], ctx->cls[1]});
+  if (ctx->kappa == 1) {
+    r.push_back({ctx->cls[1], ctx->cls[2]});
+  } else {
+    r.push_back({ctx->cls[1], ctx->small[1][2]});
+    r.push_back({ctx->small[1][2], ctx->small[1][3]});
+    r.push_back({ctx->small[1][3], ctx->cls[2]});
+  }
+  r.push_back({ctx->cls[2], ctx->cls[3]});
+  r.push_back({ctx->cls[3], ctx->cls[4]});
+  int n = 0;
+  for (const auto& x : r) n += x.second > x.first;
+  return n;
 }
 
 // One iteration: block solves, consensus, dual ascent.  ev (nullable) receives an event
@@ -2551,6 +2574,15 @@ dba_status dba_block_size_classes(const dba_block_ctx* ctx, int64_t* counts) {
     if (!ctx || !counts) return DBA_EINVAL;
     if (!ctx->has_problem) return DBA_ESTATE;
     for (int k = 0; k < dba::kBlkClasses; ++k) counts[k] = ctx->cls[k + 1] - ctx->cls[k];
+    return DBA_OK;
+  });
+}
+
+dba_status dba_block_launches_per_iteration(const dba_block_ctx* ctx, int32_t* launches) {
+  return dba::guarded(ctx ? &const_cast<dba_block_ctx*>(ctx)->err : nullptr, [&]() -> dba_status {
+    if (!ctx || !launches) return DBA_EINVAL;
+    if (!ctx->has_problem) return DBA_ESTATE;
+    *launches = block_solve_launches(ctx) + 2;  // and the point and camera consensus
     return DBA_OK;
   });
 }

@@ -29,7 +29,8 @@ EXPORTED = [
     "dba_mlp_loss_grad", "dba_mlp_train", "dba_mlp_predict", "dba_set_warm_start",
     "dba_block_create", "dba_block_set_observations", "dba_block_set_reference_pixels", "dba_block_iterate",
     "dba_block_iterate_until", "dba_block_profile", "dba_block_get_params", "dba_block_layout",
-    "dba_block_size_classes", "dba_block_build_layout", "dba_block_algorithmic_flops", "dba_block_last_error",
+    "dba_block_size_classes", "dba_block_launches_per_iteration", "dba_block_build_layout",
+    "dba_block_algorithmic_flops", "dba_block_last_error",
     "dba_block_destroy",
 ]
 DBA_BLOCK_MAX_POINTS, DBA_BLOCK_MAX_CAMERAS, DBA_BLOCK_SIZE_CLASSES = 64, 4, 4
@@ -139,6 +140,7 @@ def load():
                                          ctypes.c_int, P(ctypes.c_int64), ip, ip, ip, P(ctypes.c_int64),
                                          P(ctypes.c_int64)]
     L.dba_block_algorithmic_flops.argtypes = [vp, dp]
+    L.dba_block_launches_per_iteration.argtypes = [vp, P(ctypes.c_int32)]
     L.dba_block_last_error.argtypes = [vp]
     L.dba_block_last_error.restype = ctypes.c_char_p
     L.dba_block_destroy.argtypes = [vp]
@@ -573,6 +575,12 @@ class BlockSolver:
         f = ctypes.c_double()
         self._check(load().dba_block_algorithmic_flops(self.ctx, ctypes.byref(f)))
         return f.value
+
+    def launches_per_iteration(self):
+        """Kernel launches of one block iteration (block solves by range, consensus)."""
+        n = ctypes.c_int32()
+        self._check(load().dba_block_launches_per_iteration(self.ctx, ctypes.byref(n)))
+        return n.value
 
     def close(self):
         if self.ctx:

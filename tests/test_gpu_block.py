@@ -199,3 +199,28 @@ def test_a_repeated_point_camera_pair_is_rejected():
     with pytest.raises(dba.DbaError) as e:
         dba.BlockSolver(dup, 4, 2)
     assert e.value.status == dba.DBA_EINVAL and "observed twice" in str(e.value)
+
+
+def expected_launches(layout, kappa):
+    """Kernel launches of one block iteration, recounted from the oracle's layout by the
+    library's documented dispatch: one block-solve launch per nonempty range of blocks
+    sharing a kernel and lane-group width, then the point and camera consensus."""
+    npb, ncb = np.diff(layout.pc_off), np.diff(layout.cc_off)
+    c0 = (ncb == 1) & (npb <= 8)
+    c1 = ~c0 & (ncb <= 2) & (npb <= 16)
+    c2 = ~c0 & ~c1 & (npb <= 32)
+    c3 = ~c0 & ~c1 & ~c2
+    ranges = [c0 & (npb == 1), c0 & (npb == 2), c0 & (npb > 2) & (npb <= 4), c0 & (npb > 4)]
+    if kappa == 1:
+        ranges.append(c1)
+    else:
+        ranges += [c1 & (npb <= 4), c1 & (npb > 4) & (npb <= 8), c1 & (npb > 8)]
+    ranges += [c2, c3]
+    return sum(1 for r in ranges if r.any()) + 2
+
+
+@pytest.mark.parametrize("pi,kappa", BLOCK_SETTINGS)
+def test_launches_per_iteration_match_the_layout(pi, kappa):
+    sc = S.scene1(n_pts=400, n_cams=16, seed=17)
+    with dba.BlockSolver(sc, pi, kappa, precision=dba.DBA_PREC_F32_LOCAL) as s:
+        assert s.launches_per_iteration() == expected_launches(O.BlockLayout(sc, pi, kappa), kappa)
