@@ -448,11 +448,12 @@ def run_ours(args, rank, world, local_rank):
         w3 = {"workload": "batch256-uneven", "n_scenes": len(sc3.scene_off) - 1, "n_obs": sc3.n_obs,
               "n_cams": sc3.n_cams, "n_pts": sc3.n_pts, "steps": args.workload3_steps,
               "value": sc3.n_obs * args.workload3_steps / (ms3 * 1e-3), "unit": UNIT,
-              "ms_per_step": ms3 / args.workload3_steps, "tile_obs": lay3["tile_obs"], "kernels_ms": prof3,
+              "ms_per_step": ms3 / args.workload3_steps, "tile_obs": lay3["tile_obs"],
+              "finalize_threads": lay3.get("finalize_threads"), "kernels_ms": prof3,
               "tile_iterate_frac_of_fp32_peak": sc3.n_obs * flops_per_obs(args.inner_steps, lbfgs) /
               (prof3["tile_iterate"] * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
               "what": "all scenes in one tile_iterate launch + one finalize per ADMM iteration (CUDA graph), "
-                      "tile size by the autotuner (tile_obs = -1)"}
+                      "tile size and finalize block size by the autotuner (tile_obs = -1)"}
 
     blocks = None
     if args.workload == 2 and fp32 and not args.no_blocks and world == 1 and not args.warm_start:

@@ -84,6 +84,11 @@ typedef struct {
   int use_graph;          /* 1: replay each iteration as a CUDA graph; 0: plain launches */
   void* cuda_stream;      /* cudaStream_t to launch on; NULL = a stream owned by the context */
   int local_solver;       /* dba_local_solver: how each local subproblem (Eq. 9) is solved */
+  int finalize_threads;   /* threads per block of the segmented reduction that completes
+                             Eqs. (10)-(11) over the per-tile partial sums (one block per
+                             camera and per track spanning several tiles): 32, 64, 128 or
+                             256; 0 = 128, or with tile_obs = -1 timed together with the
+                             tile size and the fastest pair kept */
 } dba_config;
 
 typedef enum {
@@ -108,7 +113,8 @@ typedef struct {
 /* Fills *cfg with defaults: focal 500, principal point (320, 240), Huber 2 px,
  * rho 1 (angles: rho_y), 5 inner steps, lambda0 1e-3, lambda_min 1e-12, eps_depth 1e-6,
  * lm_model_tol 16,
- * FP32 local solves, automatic tile size, graphs on, own stream, Gauss-Newton local solver. */
+ * FP32 local solves, automatic tile size, graphs on, own stream, Gauss-Newton local solver,
+ * finalize_threads 0. */
 void dba_config_default(dba_config* cfg);
 
 /* Creates a context on the current CUDA device for one problem of Sec. 2.2 solved by
@@ -236,7 +242,8 @@ dba_status dba_inject_host_alloc_failure(int n);
 /* Sizes of the internal observation layout after dba_set_observations, for
  * traffic models: out[0] tiles, out[1] observations per tile (block size),
  * out[2] point runs, out[3] camera runs (= camera partial slots), out[4]
- * points whose track spans several tiles, out[5] their partial slots.
+ * points whose track spans several tiles, out[5] their partial slots, out[6]
+ * threads per block of the partial-sum reduction (finalize_threads in use).
  * *count: in capacity, out entries written. */
 dba_status dba_layout(dba_ctx* ctx, int64_t* out, int* count);
 

@@ -99,6 +99,7 @@ struct dba_ctx {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   bool fp32 = true;
+  int fin_threads = 128;  // block size of finalize for the loaded problem
   // problem
   bool has_problem = false, has_gt = false;
   int n_cams = 0, n_pts = 0;
@@ -421,6 +422,7 @@ void dba_config_default(dba_config* cfg) {
   cfg->use_graph = 1;
   cfg->cuda_stream = nullptr;
   cfg->local_solver = DBA_SOLVER_GN;
+  cfg->finalize_threads = 0;
 }
 
 dba_status dba_create(const dba_config* cfg, dba_ctx** out) {
@@ -441,10 +443,13 @@ dba_status dba_create(const dba_config* cfg, dba_ctx** out) {
                     cfg->lm_model_tol >= 0 && (cfg->precision == 0 || cfg->precision == 1) &&
                     (cfg->tile_obs == 0 || cfg->tile_obs == -1 || cfg->tile_obs == 64 ||
                      cfg->tile_obs == 128 || cfg->tile_obs == 256) &&
-                    (cfg->local_solver == DBA_SOLVER_GN || cfg->local_solver == DBA_SOLVER_LBFGS);
+                    (cfg->local_solver == DBA_SOLVER_GN || cfg->local_solver == DBA_SOLVER_LBFGS) &&
+                    (cfg->finalize_threads == 0 || cfg->finalize_threads == 32 || cfg->finalize_threads == 64 ||
+                     cfg->finalize_threads == 128 || cfg->finalize_threads == 256);
     if (!ok) {
       g_create_error =
-          "dba_create: invalid configuration (check focal, loss, rho, steps, precision, tile_obs, local_solver)";
+          "dba_create: invalid configuration (check focal, loss, rho, steps, precision, tile_obs, local_solver, "
+          "finalize_threads)";
       return DBA_EINVAL;
     }
     cudaError_t e = cudaFree(nullptr);  // initialise the runtime on the current device
@@ -697,6 +702,7 @@ dba_status load_problem(dba_ctx* ctx, int NT, int32_t n_cams, int32_t n_pts, int
   P.n_obs = n_obs;
   P.n_tiles = (int)L.tiles.size();
   P.tile_obs = NT;
+  P.fin_threads = ctx->fin_threads;
   P.n_cam_slots = L.n_cam_slots;
   P.n_pt_slots = L.n_pt_slots;
   P.n_split_pts = (int)L.split_pt.size();
@@ -767,15 +773,19 @@ dba_status load_problem(dba_ctx* ctx, int NT, int32_t n_cams, int32_t n_pts, int
   return DBA_OK;
 }
 
-// Tile-size autotuner: times a few iterations per candidate size and keeps the fastest,
-// then reloads the problem with it (so the state is the initial one).  Results are cached
-// per process by precision, problem size (power of two) and mean track length.
+// Autotuner of the two launch sizes of an iteration: the tile size (observations per tile
+// and threads per block of tile_iterate, 64 / 128 / 256) and the block size of finalize's
+// segmented reduction (32 / 64 / 128 / 256, unless the configuration fixes it).  For each
+// tile size it loads the problem, and for each finalize size it times a few iterations; it
+// keeps the fastest pair, and the caller reloads the problem with it (so the state is the
+// initial one).  Results are cached per process by precision, problem size (power of two),
+// mean track length and the fixed finalize size.
 std::mutex g_tune_mutex;
-std::map<std::tuple<int, int, int>, int> g_tune_cache;
+std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tune_cache;
 
 dba_status autotune_tile(dba_ctx* ctx, int32_t n_cams, int32_t n_pts, int64_t n_obs, const int32_t* pt_idx,
                          const int32_t* cam_idx, const double* z, const double* cams0, const double* pts0,
-                         int* best) {
+                         int* best, int* best_fin) {
   int used = 0;
   {
     std::vector<char> seen(n_pts, 0);
@@ -785,41 +795,51 @@ dba_status autotune_tile(dba_ctx* ctx, int32_t n_cams, int32_t n_pts, int64_t n_
   int lg = 0;
   while ((1ll << (lg + 1)) <= n_obs) ++lg;
   const int mean_track = (int)std::lround((double)n_obs / std::max(1, used));
-  const auto key = std::make_tuple(ctx->fp32 ? 1 : 0, lg, std::min(mean_track, 64));
+  const int fixed_fin = ctx->cfg.finalize_threads;
+  const auto key = std::make_tuple(ctx->fp32 ? 1 : 0, lg, std::min(mean_track, 64), fixed_fin);
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) {
-      *best = it->second;
+      *best = it->second.first;
+      *best_fin = it->second.second;
       return DBA_OK;
     }
   }
   const int candidates[3] = {64, 128, 256};
+  const int fin_all[4] = {32, 64, 128, 256};
+  const int n_fin = fixed_fin > 0 ? 1 : 4;
+  const int* fin_candidates = fixed_fin > 0 ? &fixed_fin : fin_all;
   float best_ms = 0.f;
   *best = ctx->fp32 ? 256 : 128;
+  *best_fin = fixed_fin > 0 ? fixed_fin : 128;
   const int reps = 3;
   for (int nt : candidates) {
     dba_status s = load_problem(ctx, nt, n_cams, n_pts, n_obs, pt_idx, cam_idx, z, cams0, pts0);
     if (s != DBA_OK) return s;
-    s = launch_iteration(ctx);  // warm-up
-    if (s != DBA_OK) return s;
-    DBA_CUDA(cudaEventRecord(ctx->ev0, ctx->stream), "autotune");
-    for (int r = 0; r < reps; ++r) {
-      s = launch_iteration(ctx);
+    for (int f = 0; f < n_fin; ++f) {
+      ctx->P.fin_threads = fin_candidates[f];  // launched directly below, not from a graph
+      s = launch_iteration(ctx);               // warm-up
       if (s != DBA_OK) return s;
-    }
-    DBA_CUDA(cudaEventRecord(ctx->ev1, ctx->stream), "autotune");
-    DBA_CUDA(cudaEventSynchronize(ctx->ev1), "autotune");
-    float ms = 0.f;
-    DBA_CUDA(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1), "autotune");
-    if (best_ms == 0.f || ms < best_ms) {
-      best_ms = ms;
-      *best = nt;
+      DBA_CUDA(cudaEventRecord(ctx->ev0, ctx->stream), "autotune");
+      for (int r = 0; r < reps; ++r) {
+        s = launch_iteration(ctx);
+        if (s != DBA_OK) return s;
+      }
+      DBA_CUDA(cudaEventRecord(ctx->ev1, ctx->stream), "autotune");
+      DBA_CUDA(cudaEventSynchronize(ctx->ev1), "autotune");
+      float ms = 0.f;
+      DBA_CUDA(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1), "autotune");
+      if (best_ms == 0.f || ms < best_ms) {
+        best_ms = ms;
+        *best = nt;
+        *best_fin = fin_candidates[f];
+      }
     }
     ctx->free_problem();
   }
   std::lock_guard<std::mutex> lock(g_tune_mutex);
-  g_tune_cache[key] = *best;
+  g_tune_cache[key] = {*best, *best_fin};
   return DBA_OK;
 }
 
@@ -850,9 +870,12 @@ dba_status dba_set_observations(dba_ctx* ctx, int32_t n_cams, int32_t n_pts, int
     cudaStreamSynchronize(ctx->stream);
     ctx->free_problem();
     int NT = ctx->cfg.tile_obs > 0 ? ctx->cfg.tile_obs : (ctx->fp32 ? 256 : 128);
+    ctx->fin_threads = ctx->cfg.finalize_threads > 0 ? ctx->cfg.finalize_threads : 128;
     if (ctx->cfg.tile_obs < 0) {
-      dba_status s = autotune_tile(ctx, n_cams, n_pts, n_obs, pt_idx, cam_idx, z, cams0, pts0, &NT);
+      int NF = ctx->fin_threads;
+      dba_status s = autotune_tile(ctx, n_cams, n_pts, n_obs, pt_idx, cam_idx, z, cams0, pts0, &NT, &NF);
       if (s != DBA_OK) return s;
+      ctx->fin_threads = NF;
     }
     return load_problem(ctx, NT, n_cams, n_pts, n_obs, pt_idx, cam_idx, z, cams0, pts0);
   });
@@ -1170,9 +1193,9 @@ dba_status dba_layout(dba_ctx* ctx, int64_t* out, int* count) {
   return dba::guarded(ctx ? &ctx->err : nullptr, [&]() -> dba_status {
     if (!ctx || !out || !count) return DBA_EINVAL;
     if (!ctx->has_problem) return ctx->fail(DBA_ESTATE, "dba_layout before dba_set_observations");
-    const int64_t v[6] = {ctx->P.n_tiles, ctx->P.tile_obs, ctx->n_pseg, (int64_t)ctx->P.n_cam_slots,
-                          (int64_t)ctx->P.n_split_pts, (int64_t)ctx->P.n_pt_slots};
-    const int n = std::min(*count, 6);
+    const int64_t v[7] = {ctx->P.n_tiles, ctx->P.tile_obs, ctx->n_pseg, (int64_t)ctx->P.n_cam_slots,
+                          (int64_t)ctx->P.n_split_pts, (int64_t)ctx->P.n_pt_slots, (int64_t)ctx->P.fin_threads};
+    const int n = std::min(*count, 7);
     for (int k = 0; k < n; ++k) out[k] = v[k];
     *count = n;
     return DBA_OK;

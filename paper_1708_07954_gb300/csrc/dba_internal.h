@@ -50,6 +50,7 @@ struct DevProblem {
   long long pitch;              // row stride of delta, adual and mlp_start
   int n_tiles;
   int tile_obs;                 // block size of the tile kernel
+  int fin_threads;              // block size of finalize: 32, 64, 128 or 256
   int n_cam_slots, n_pt_slots, n_split_pts;
   // static structure
   const int* obs_pt;            // [l] internal point id

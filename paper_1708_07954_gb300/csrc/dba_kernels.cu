@@ -447,11 +447,11 @@ __global__ void __launch_bounds__(NT, (tile_min_blocks<T, NT>()))
 }
 
 // ------------------------------------------------------------ finalize
-constexpr int kFinThreads = 128;
-
-template <typename T>
-__global__ void __launch_bounds__(kFinThreads) finalize_kernel(DevProblem P) {
-  __shared__ double red[6][kFinThreads];
+// One block of NF threads per segment of partial sums (a camera's, or a point's whose track
+// spans several tiles): strided FP64 sums, then a fixed tree over the block.
+template <typename T, int NF>
+__global__ void __launch_bounds__(NF) finalize_kernel(DevProblem P) {
+  __shared__ double red[6][NF];
   const int cur = __ldg(&P.ctl->cur), nxt = cur ^ 1;
   const int b = blockIdx.x, t = threadIdx.x;
   const bool is_cam = b < P.n_cams;
@@ -471,11 +471,11 @@ __global__ void __launch_bounds__(kFinThreads) finalize_kernel(DevProblem P) {
   }
   const double* part = is_cam ? P.cam_part : P.pt_part;
   double acc[6] = {0, 0, 0, 0, 0, 0};
-  for (int s = s0 + t; s < s1; s += kFinThreads)
+  for (int s = s0 + t; s < s1; s += NF)
     for (int c = 0; c < nc; ++c) acc[c] += part[nc * s + c];
   for (int c = 0; c < 6; ++c) red[c][t] = acc[c];
   __syncthreads();
-  for (int w = kFinThreads / 2; w > 0; w >>= 1) {
+  for (int w = NF / 2; w > 0; w >>= 1) {
     if (t < w)
       for (int c = 0; c < 6; ++c) red[c][t] += red[c][t + w];
     __syncthreads();
@@ -997,12 +997,22 @@ cudaError_t launch_tile_iterate(const DevProblem& P, const TileMaps& M, const Pa
               : launch_tile_sized<double, DBA_SOLVER_GN>(P, M, prm, s);
 }
 
+template <typename T>
+void launch_finalize_sized(const DevProblem& P, int blocks, cudaStream_t s) {
+  switch (P.fin_threads) {
+    case 32: finalize_kernel<T, 32><<<blocks, 32, 0, s>>>(P); break;
+    case 64: finalize_kernel<T, 64><<<blocks, 64, 0, s>>>(P); break;
+    case 256: finalize_kernel<T, 256><<<blocks, 256, 0, s>>>(P); break;
+    default: finalize_kernel<T, 128><<<blocks, 128, 0, s>>>(P); break;
+  }
+}
+
 cudaError_t launch_finalize(const DevProblem& P, bool fp32, cudaStream_t s) {
   const int blocks = P.n_cams + P.n_split_pts;
   if (fp32)
-    finalize_kernel<float><<<blocks, kFinThreads, 0, s>>>(P);
+    launch_finalize_sized<float>(P, blocks, s);
   else
-    finalize_kernel<double><<<blocks, kFinThreads, 0, s>>>(P);
+    launch_finalize_sized<double>(P, blocks, s);
   return cudaGetLastError();
 }
 

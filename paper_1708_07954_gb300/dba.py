@@ -52,7 +52,7 @@ class dba_config(ctypes.Structure):
         ("inner_steps", ctypes.c_int), ("lm_lambda0", ctypes.c_double),
         ("lm_lambda_min", ctypes.c_double), ("eps_depth", ctypes.c_double),
         ("lm_model_tol", ctypes.c_double), ("precision", ctypes.c_int), ("tile_obs", ctypes.c_int), ("use_graph", ctypes.c_int),
-        ("cuda_stream", ctypes.c_void_p), ("local_solver", ctypes.c_int),
+        ("cuda_stream", ctypes.c_void_p), ("local_solver", ctypes.c_int), ("finalize_threads", ctypes.c_int),
     ]
 
 
@@ -283,10 +283,10 @@ def dba_profile(ctx, n_iters):
 
 
 def dba_layout(ctx):
-    out = (ctypes.c_int64 * 6)()
-    count = ctypes.c_int(6)
+    out = (ctypes.c_int64 * 7)()
+    count = ctypes.c_int(7)
     _check(load().dba_layout(ctx, out, ctypes.byref(count)), ctx)
-    keys = ["tiles", "tile_obs", "point_runs", "camera_runs", "split_points", "point_slots"]
+    keys = ["tiles", "tile_obs", "point_runs", "camera_runs", "split_points", "point_slots", "finalize_threads"]
     return {keys[k]: int(out[k]) for k in range(count.value)}
 
 

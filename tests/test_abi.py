@@ -43,11 +43,13 @@ def test_config_defaults(lib):
     assert cfg.focal == 500.0 and cfg.cx == 320.0 and cfg.cy == 240.0
     assert cfg.loss == dba.DBA_LOSS_HUBER and cfg.loss_param == 2.0
     assert cfg.inner_steps == 5 and cfg.precision == dba.DBA_PREC_F32_LOCAL and cfg.use_graph == 1
+    assert cfg.tile_obs == 0 and cfg.finalize_threads == 0
 
 
 @pytest.mark.parametrize("field,value", [("focal", -1.0), ("rho_x", 0.0), ("rho_y", float("nan")),
                                          ("loss", 7), ("inner_steps", -1), ("precision", 3),
-                                         ("tile_obs", 100), ("loss_param", 0.0), ("local_solver", 2)])
+                                         ("tile_obs", 100), ("loss_param", 0.0), ("local_solver", 2),
+                                         ("finalize_threads", 48)])
 def test_invalid_config_is_rejected_before_any_device_work(lib, field, value):
     cfg = dba.dba_config_default(**{field: value})
     with pytest.raises(dba.DbaError) as ei:

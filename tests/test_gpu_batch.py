@@ -79,6 +79,8 @@ def test_autotuned_tile_matches_fixed_tile():
     with dba.Solver(sc, precision=dba.DBA_PREC_F64, tile_obs=-1) as a, \
             dba.Solver(sc, precision=dba.DBA_PREC_F64, tile_obs=128) as b:
         assert a.layout()["tile_obs"] in (64, 128, 256)
+        assert a.layout()["finalize_threads"] in (32, 64, 128, 256)
+        assert b.layout()["finalize_threads"] == 128
         a.iterate(5, stats=False)
         b.iterate(5, stats=False)
         assert colerr(a.params()[0], b.params()[0]) <= TOL64

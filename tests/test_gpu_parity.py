@@ -97,10 +97,12 @@ def test_fp64_parity_multi_tile_ragged(tile, loss):
     run_pair(sc, 8, tile_obs=tile, state_at=(8,))
 
 
-def test_fp64_parity_tracks_longer_than_a_tile():
-    """150-camera tracks are cut into 64-observation pieces reduced by the finalize kernel."""
+@pytest.mark.parametrize("fin", [0, 32, 64, 256])
+def test_fp64_parity_tracks_longer_than_a_tile(fin):
+    """150-camera tracks are cut into 64-observation pieces reduced by the finalize kernel,
+    at every block size of its segmented reduction (0: the default, 128)."""
     sc = S.scene0(n_cams=150, n_pts=9, seed=5)
-    run_pair(sc, 6, tile_obs=64, state_at=(6,))
+    run_pair(sc, 6, tile_obs=64, state_at=(6,), finalize_threads=fin)
 
 
 def test_fp64_parity_run_lengths_around_warp_size():
