@@ -565,8 +565,9 @@ class BlockSolver:
         return {"n_blocks": nb.value, "n_point_copies": npc.value, "n_camera_copies": ncc.value}
 
     def size_classes(self):
-        """Blocks per size class of the solve kernel (8-, 16-, 32-lane groups, 32 lanes
-        with two point copies each); each nonempty class is one launch per iteration."""
+        """Blocks per size class of the solve kernels: one camera and at most 8 points, at most
+        2 cameras and 16 points, at most 32 points, the rest (see dba_block_size_classes in
+        include/dba.h for the lane groups of each)."""
         c = (ctypes.c_int64 * DBA_BLOCK_SIZE_CLASSES)()
         self._check(load().dba_block_size_classes(self.ctx, c))
         return list(c)
