@@ -38,3 +38,18 @@ def test_block_parity_settings_reach_every_kernel_variant():
     want |= {("two cameras", w) for w in (4, 8, 16, 32)}
     want |= {("shared memory", 32), ("shared memory, two copies a lane", 32)}
     assert want <= seen, sorted(want - seen)
+
+
+def test_block_parity_settings_reach_one_camera_blocks_in_the_two_camera_solve():
+    """With block_cams >= 2, a block of one camera and more than 8 points takes the
+    two-camera solve, its 12 x 12 system padded by identity rows: the parity settings
+    put such blocks in both the 16- and the 32-lane groups."""
+    sc = S.scene1(n_pts=400, n_cams=16, seed=17)
+    seen = set()
+    for pi, kappa in BLOCK_SETTINGS:
+        L = O.BlockLayout(sc, pi, kappa)
+        for n_p, n_c in zip(np.diff(L.pc_off), np.diff(L.cc_off)):
+            v = variant(int(n_p), int(n_c), kappa)
+            if v[0] == "two cameras" and n_c == 1:
+                seen.add(v[1])
+    assert {16, 32} <= seen, sorted(seen)
