@@ -66,25 +66,30 @@ template <> struct Num<double> {
 
 // float <-> double by integer bit manipulation (IEEE-754 binary32/binary64 layouts), so the
 // FP32 path spends none of GB300's scarce FP64 issue slots on conversions.  Exact for normal
-// numbers; magnitudes below 2^-126 become signed zero; non-finite values and float overflow
-// take the hardware conversion.
+// numbers; magnitudes below 2^-126 become signed zero; infinities stay infinite, NaNs stay
+// NaN and float overflow becomes infinity.  The special cases are selected, not branched
+// to, so the conversions compile to straight-line integer code.
 __device__ __forceinline__ double widen(float f) {
   const unsigned int b = __float_as_uint(f);
-  const unsigned int mag = b & 0x7fffffffu;
-  if (mag >= 0x7f800000u) return (double)f;
-  if (mag < 0x00800000u) return __hiloint2double((int)(b & 0x80000000u), 0);
-  const unsigned int hi = (b & 0x80000000u) | ((mag >> 3) + (896u << 20));
-  return __hiloint2double((int)hi, (int)(mag << 29));
+  const unsigned int sign = b & 0x80000000u, mag = b & 0x7fffffffu;
+  const bool special = mag >= 0x7f800000u, tiny = mag < 0x00800000u;
+  unsigned int hi = sign | ((mag >> 3) + (896u << 20));
+  hi = special ? (sign | 0x7ff00000u | ((mag >> 3) & 0xfffffu)) : hi;
+  hi = tiny ? sign : hi;
+  const unsigned int lo = tiny ? 0u : (mag << 29);
+  return __hiloint2double((int)hi, (int)lo);
 }
 __device__ __forceinline__ float narrow(double d) {
   const unsigned int hi = (unsigned int)__double2hiint(d);
   const unsigned int lo = (unsigned int)__double2loint(d);
+  const unsigned int sign = hi & 0x80000000u;
   const unsigned int e = (hi >> 20) & 0x7ffu;
-  if (e >= 1151u) return (float)d;
-  if (e <= 896u) return __uint_as_float(hi & 0x80000000u);
   unsigned int f = ((e - 896u) << 23) + (((hi & 0xfffffu) << 3) | (lo >> 29));
   f += (lo >> 28) & 1u;  // round to nearest (halfway cases away from zero)
-  return __uint_as_float(f | (hi & 0x80000000u));
+  const bool nan = e == 0x7ffu && ((hi & 0xfffffu) | lo) != 0u;
+  f = e >= 1151u ? (nan ? 0x7fc00000u : 0x7f800000u) : f;
+  f = e <= 896u ? 0u : f;
+  return __uint_as_float(f | sign);
 }
 template <typename T> __device__ __forceinline__ double to_f64(T v);
 template <> __device__ __forceinline__ double to_f64<float>(float v) { return widen(v); }
