@@ -230,11 +230,14 @@ __device__ __forceinline__ void stage_tile(const DevProblem& P, const TileMaps& 
   }
 }
 
-// One tile from its staged inputs: deferred dual ascent, local solves, run sums.
-template <typename T, int NT, int kS>
-__device__ __forceinline__ void process_tile(const DevProblem& P, const Prm<T>& q, const TileStage<T, NT>& S,
-                                             double (*s_buf)[NT], const TileInfo& ti, int cur, int pending,
-                                             int exact) {
+// One tile from its staged inputs: deferred dual ascent, local solves, run sums.  kLoss >= 0
+// fixes the misfit at compile time (the loss tests of every local-solve step fold away).
+template <typename T, int NT, int kS, int kLoss>
+__device__ __forceinline__ void process_tile_body(const DevProblem& P, const Prm<T>& qr, const TileStage<T, NT>& S,
+                                                  double (*s_buf)[NT], const TileInfo& ti, int cur, int pending,
+                                                  int exact) {
+  Prm<T> q = qr;
+  if constexpr (kLoss >= 0) q.loss = kLoss;
   const int t = threadIdx.x;
   const long long l = P.pitch;  // row stride of delta, adual, mlp_start
   const long long o = (long long)ti.o0 + t;
@@ -377,6 +380,24 @@ __device__ __forceinline__ void process_tile(const DevProblem& P, const Prm<T>& 
       }
       P.cam_part[6 * S.cslot[r] + c] = sum;
     }
+  }
+}
+
+// The FP32 Gauss-Newton kernel (the benchmarked path) has one body per loss; the other
+// kernels read the loss at run time.
+template <typename T, int NT, int kS>
+__device__ __forceinline__ void process_tile(const DevProblem& P, const Prm<T>& q, const TileStage<T, NT>& S,
+                                             double (*s_buf)[NT], const TileInfo& ti, int cur, int pending,
+                                             int exact) {
+  if constexpr (sizeof(T) == 4 && kS == DBA_SOLVER_GN) {
+    if (q.loss == DBA_LOSS_HUBER)
+      process_tile_body<T, NT, kS, DBA_LOSS_HUBER>(P, q, S, s_buf, ti, cur, pending, exact);
+    else if (q.loss == DBA_LOSS_STUDENT_T)
+      process_tile_body<T, NT, kS, DBA_LOSS_STUDENT_T>(P, q, S, s_buf, ti, cur, pending, exact);
+    else
+      process_tile_body<T, NT, kS, DBA_LOSS_L2>(P, q, S, s_buf, ti, cur, pending, exact);
+  } else {
+    process_tile_body<T, NT, kS, -1>(P, q, S, s_buf, ti, cur, pending, exact);
   }
 }
 

@@ -188,13 +188,17 @@ def test_fp32_path_workload2_geometry_final_accuracy():
     assert ce.max() <= 1e-4, ce.max()
 
 
-@pytest.mark.parametrize("tile", [64, 128, 256])
-def test_fp32_parity_per_iteration_small(tile):
+@pytest.mark.parametrize("tile,loss", [(64, None), (128, None), (256, None), (256, S.LOSS_L2),
+                                       (256, S.LOSS_HUBER)])
+def test_fp32_parity_per_iteration_small(tile, loss):
     """FP32 local solves track the FP64 oracle iteration by iteration: consensus projections
     within 1e-3 px RMS of the oracle's, parameters within 1e-4 relative (FP32 unit roundoff
     6e-8 amplified by the conditioning of weakly triangulated points).  Every tile size, so
-    every width of the staged observation windows."""
+    every width of the staged observation windows, and every misfit (the FP32 kernel has a
+    body per loss; None: the scene's Student's t)."""
     sc = S.scene1(n_pts=2000, n_cams=32, seed=21)
+    if loss is not None:
+        sc.loss, sc.loss_param = loss, {S.LOSS_L2: 0.0, S.LOSS_HUBER: 2.0}[loss]
     with dba.Solver(sc, precision=dba.DBA_PREC_F32_LOCAL, tile_obs=tile) as s:
         cfg = oracle_cfg(sc, s)
         st = O.State(sc)
