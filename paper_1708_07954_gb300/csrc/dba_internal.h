@@ -22,6 +22,7 @@ struct alignas(16) DevCtl {
   unsigned int done;      // finalize-kernel block counter
   unsigned int inject;    // fault injection for tests: bit 0 = the tile kernel announces its
                           // tensor copies but does not issue them (its bounded wait runs out)
+  unsigned int metric_done;  // metrics-kernel block counter (the last block reduces)
 };
 
 // One tile of the observation layout: observations [o0, o0 + n), point runs

@@ -19,6 +19,7 @@
 //  metrics       reprojection RMSE, objective and residuals at consensus.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 
 #include <type_traits>
@@ -547,6 +548,28 @@ __global__ void camera_pose_kernel(DevProblem P) {
   for (int c = 0; c < 3; ++c) out[9 + c] = v[6 + c];
 }
 
+// A camera pose row (R row-major, then t; 16-byte aligned) by vector loads.
+__device__ __forceinline__ void load_pose(const float* p, float v[12]) {
+  const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float4 a = q[k];
+    v[4 * k] = a.x;
+    v[4 * k + 1] = a.y;
+    v[4 * k + 2] = a.z;
+    v[4 * k + 3] = a.w;
+  }
+}
+__device__ __forceinline__ void load_pose(const double* p, double v[12]) {
+  const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    const double2 a = q[k];
+    v[2 * k] = a.x;
+    v[2 * k + 1] = a.y;
+  }
+}
+
 // Metrics at consensus: sums of |e|^2, phi_m, |f - z_true|^2 (inliers), valid / invalid
 // counts, primal and dual residual terms, reference count.  kGtOnly: only the reference
 // sums and the counts (the stopping test of dba_iterate_until).
@@ -558,9 +581,9 @@ __device__ __forceinline__ void metric_terms(const DevProblem& P, const Prm<T>& 
                                              typename Num<T>::V2 zz, typename Num<T>::V2 gt, bool counted,
                                              T acc[8]) {
   const T* Xm = static_cast<const T*>(P.Xm);
-  const T* pose = static_cast<const T*>(P.cam_pose);
   const T x0 = Xm[3 * i], x1 = Xm[3 * i + 1], x2 = Xm[3 * i + 2];
-  const T* Rt = pose + 12 * (long long)j;
+  T Rt[12];
+  load_pose(static_cast<const T*>(P.cam_pose) + 12 * (long long)j, Rt);
   const T p0 = Rt[0] * x0 + Rt[1] * x1 + Rt[2] * x2 + Rt[9];
   const T p1 = Rt[3] * x0 + Rt[4] * x1 + Rt[5] * x2 + Rt[10];
   const T p2 = Rt[6] * x0 + Rt[7] * x1 + Rt[8] * x2 + Rt[11];
@@ -680,6 +703,26 @@ __global__ void __launch_bounds__(kMetricThreads) metrics_kernel(DevProblem P, P
     __syncthreads();
   }
   if (threadIdx.x < 8) P.metric_part[8 * blockIdx.x + threadIdx.x] = red[threadIdx.x][0];
+  // the last block to finish sums every block's partials (strided, then the same tree) into
+  // metric_out and rearms the counter for the next launch
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(&P.ctl->metric_done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  double tot[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += kMetricThreads)
+    for (int k = 0; k < 8; ++k) tot[k] += __ldcg(&P.metric_part[8 * b + k]);
+  for (int k = 0; k < 8; ++k) red[k][threadIdx.x] = tot[k];
+  __syncthreads();
+  for (int w = kMetricThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int k = 0; k < 8; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < 8) P.metric_out[threadIdx.x] = red[threadIdx.x][0];
+  if (threadIdx.x == 0) P.ctl->metric_done = 0u;
 }
 
 // Per-scene metrics of a batch: each block walks a contiguous chunk of
@@ -735,20 +778,6 @@ scene_metrics_kernel(DevProblem P, Prm<T> q, const int* scene_of_obs, double* ou
     for (int k = 0; k < 5; ++k) atomicAdd(&out[5 * scene + k], acc[k]);
 }
 
-__global__ void __launch_bounds__(kMetricThreads) metrics_final_kernel(DevProblem P, int nblocks) {
-  __shared__ double red[8][kMetricThreads];
-  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  for (int b = threadIdx.x; b < nblocks; b += kMetricThreads)
-    for (int k = 0; k < 8; ++k) acc[k] += P.metric_part[8 * b + k];
-  for (int k = 0; k < 8; ++k) red[k][threadIdx.x] = acc[k];
-  __syncthreads();
-  for (int w = kMetricThreads / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w)
-      for (int k = 0; k < 8; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x < 8) P.metric_out[threadIdx.x] = red[threadIdx.x][0];
-}
 
 // ------------------------------------------------------------ settle
 // Applies a deferred dual ascent and rebases the copies onto the current
@@ -1040,7 +1069,23 @@ cudaError_t launch_finalize(const DevProblem& P, bool fp32, cudaStream_t s) {
 cudaError_t launch_metrics(const DevProblem& P, const Params& prm, bool fp32, int cur, int pending,
                            cudaStream_t s, bool gt_only) {
   (void)cur;
-  const int g = grid_for(P.n_obs, kMetricThreads, kMetricBlocks);
+  // one wave of resident blocks (at most kMetricBlocks, the partial-sum slots)
+  static std::atomic<int> resident[4] = {};
+  const int key = (fp32 ? 0 : 2) + (gt_only ? 1 : 0);
+  int cap = resident[key].load();
+  if (!cap) {
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaError_t e0 = fp32 ? (gt_only ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, metrics_kernel<float, true>, kMetricThreads, 0)
+                                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, metrics_kernel<float, false>, kMetricThreads, 0))
+                          : (gt_only ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, metrics_kernel<double, true>, kMetricThreads, 0)
+                                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, metrics_kernel<double, false>, kMetricThreads, 0));
+    if (e0 == cudaSuccess) e0 = cudaGetDevice(&dev);
+    if (e0 == cudaSuccess) e0 = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e0 != cudaSuccess) return e0;
+    cap = std::max(1, std::min(kMetricBlocks, per_sm * sms));
+    resident[key].store(cap);
+  }
+  const int g = grid_for(P.n_obs, kMetricThreads, cap);
   const int gc = (P.n_cams + 127) / 128;
   if (fp32) {
     camera_pose_kernel<float><<<gc, 128, 0, s>>>(P);
@@ -1055,9 +1100,6 @@ cudaError_t launch_metrics(const DevProblem& P, const Params& prm, bool fp32, in
     else
       metrics_kernel<double, false><<<g, kMetricThreads, 0, s>>>(P, make_prm<double>(prm), pending);
   }
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  metrics_final_kernel<<<1, kMetricThreads, 0, s>>>(P, g);
   return cudaGetLastError();
 }
 
