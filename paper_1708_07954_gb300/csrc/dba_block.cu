@@ -961,41 +961,47 @@ __global__ void __launch_bounds__(kBlkWarps * 32)
   }
 }
 
-// ------------------------------------------------------------ two-camera blocks
-// A block with at most two cameras and at most G <= 32 points has a reduced camera system of
-// at most 12 x 12.  Each lane keeps its point copy's linearisation in registers (at most one
-// observation per camera) and forms its terms of the whole system: the three 6 x 6 blocks of
-// B^T Q B, the right-hand side B^T U and the camera misfit gradient.  A reduce-scatter over
-// the group (recursive halving) sums them, G values at a time, so that each value passes
-// through one shuffle instead of log2(G); lane i receives the sum of value i and writes it
-// into the group's system in shared memory, which then is factored lane-per-row as in
-// solve_block.  Same arithmetic as solve_block; the sums run in another order.
-template <typename T>
-struct TwoCamShared {
-  // the reduced camera system's upper triangle S(row <= col) at 13 row + col, then the
+// ------------------------------------------------------------ blocks of two or four cameras
+// A block with at most KC cameras (KC = 2 or 4) and at most G <= 32 points has a reduced camera
+// system of at most 6 KC x 6 KC.  Each lane keeps its point copy's linearisation in registers
+// (at most one observation per camera) and forms its terms of the whole system: the 6 x 6
+// blocks of B^T Q B, the right-hand side B^T U and the camera misfit gradient.  A
+// reduce-scatter over the group (recursive halving) sums them, G values at a time, so that each
+// value passes through one shuffle instead of log2(G); lane i receives the sum of value i and
+// writes it into the group's system in shared memory.  The system is then factored in
+// registers, a row per lane (6 KC / G rows a lane below 6 KC lanes), pivots and columns by
+// shuffles.  Same arithmetic as solve_block; the sums run in another order.
+template <typename T, int KC>
+struct CamShared {
+  // the reduced camera system's upper triangle S(row <= col) at kLd row + col, then the
   // right-hand side sums B^T U, the camera misfit gradients and the rounding-noise scale
-  static constexpr int kRhs = 12 * 13, kG = kRhs + 12, kNoise = kG + 12, kSys = kNoise + 1;
+  static constexpr int kN = 6 * KC, kLd = kN + 1;
+  static constexpr int kRhs = kN * kLd, kG = kRhs + kN, kNoise = kG + kN, kSys = kNoise + 1;
   T sys[kSys];
-  T vbar[2][6];
-  T d[2][6];
-  T dt[2][6];
-  T a[2][6];
+  T vbar[KC][6];
+  T d[KC][6];
+  T dt[KC][6];
+  T a[KC][6];
 };
 
 // The values one lane contributes to the reduced system, in this order: the upper triangles
-// of the two diagonal 6 x 6 blocks (21 each), the off-diagonal block (36, row-major), the
-// right-hand sides B^T U (6 per camera), the camera misfit gradients (6 per camera) and the
-// rounding-noise scale; the rest of the last group of G is zero.
-constexpr int kSysValues = 21 + 21 + 36 + 12 + 12 + 1;
+// of the KC diagonal 6 x 6 blocks (21 each), the off-diagonal blocks of the camera pairs
+// c1 < c2 (36 each, row-major), the right-hand sides B^T U (6 per camera), the camera misfit
+// gradients (6 per camera) and the rounding-noise scale; the rest of the last group of G is zero.
+template <int KC>
+__host__ __device__ constexpr int sys_values() {
+  return 21 * KC + 36 * (KC * (KC - 1) / 2) + 12 * KC + 1;
+}
 
 struct SysEntry {
   int kind;  // 0: S(row, col), 1: rhs(row), 2: g(row), 3: noise, 4: none
   int row, col;
 };
 
+template <int KC>
 __host__ __device__ constexpr SysEntry sys_entry(int e) {
-  if (e < 42) {
-    const int c = e < 21 ? 0 : 1;
+  if (e < 21 * KC) {
+    const int c = e / 21;
     int t = e - 21 * c, r = 0;
     while (t >= 6 - r) {
       t -= 6 - r;
@@ -1003,19 +1009,34 @@ __host__ __device__ constexpr SysEntry sys_entry(int e) {
     }
     return SysEntry{0, 6 * c + r, 6 * c + r + t};
   }
-  if (e < 78) return SysEntry{0, (e - 42) / 6, 6 + (e - 42) % 6};
-  if (e < 90) return SysEntry{1, e - 78, 0};
-  if (e < 102) return SysEntry{2, e - 90, 0};
-  if (e == 102) return SysEntry{3, 0, 0};
-  return SysEntry{4, 0, 0};
+  e -= 21 * KC;
+  for (int c1 = 0; c1 < KC; ++c1)
+    for (int c2 = c1 + 1; c2 < KC; ++c2) {
+      if (e < 36) return SysEntry{0, 6 * c1 + e / 6, 6 * c2 + e % 6};
+      e -= 36;
+    }
+  if (e < 6 * KC) return SysEntry{1, e, 0};
+  e -= 6 * KC;
+  if (e < 6 * KC) return SysEntry{2, e, 0};
+  e -= 6 * KC;
+  return e == 0 ? SysEntry{3, 0, 0} : SysEntry{4, 0, 0};
 }
 
-// where value e lands in TwoCamShared::sys, or -1
+// where value e lands in CamShared::sys, or -1
+template <int KC>
 __host__ __device__ constexpr int sys_dst(int e) {
-  const SysEntry se = sys_entry(e);
-  return se.kind == 0 ? 13 * se.row + se.col
-                      : se.kind == 1 ? 12 * 13 + se.row : se.kind == 2 ? 12 * 13 + 12 + se.row
-                                                                         : se.kind == 3 ? 12 * 13 + 24 : -1;
+  using Sh = CamShared<float, KC>;
+  const SysEntry se = sys_entry<KC>(e);
+  return se.kind == 0   ? Sh::kLd * se.row + se.col
+         : se.kind == 1 ? Sh::kRhs + se.row
+         : se.kind == 2 ? Sh::kG + se.row
+         : se.kind == 3 ? Sh::kNoise
+                        : -1;
+}
+
+// index of the camera pair c1 <= c2 among the KC (KC + 1) / 2 pairs
+__host__ __device__ constexpr int cam_pair(int KC, int c1, int c2) {
+  return c1 * KC - c1 * (c1 - 1) / 2 + (c2 - c1);
 }
 
 // Lane gl of a group of G receives the sum over the group of v[gl] (v is overwritten).
@@ -1037,19 +1058,19 @@ __device__ __forceinline__ T reduce_scatter(T (&v)[G], const Grp<G>& grp) {
 }
 
 // One lane's terms of the reduced system: the camera rows B_c of its observations' Jacobians,
-// U_c, the Schur weights Q of the camera pairs 00, 01, 11, the IRLS weights 2w_c, the
-// residuals and the rounding-noise scale (camera slots without an observation: zero).
-template <typename T>
+// U_c, the Schur weights Q of the camera pairs, the IRLS weights 2w_c, the residuals and the
+// rounding-noise scale (camera slots without an observation: zero).
+template <typename T, int KC>
 struct SysTerms {
-  T Bc[2][2][6], U[2][2], Q[3][4], tw[2], ez[2][2], noise;
+  T Bc[KC][2][6], U[KC][2], Q[KC * (KC + 1) / 2][4], tw[KC], ez[KC][2], noise;
 };
 
 // value E of the list above, E a compile-time index
-template <int E, typename T>
-__device__ __forceinline__ T sys_value(const SysTerms<T>& m) {
-  constexpr SysEntry se = sys_entry(E);
+template <int E, typename T, int KC>
+__device__ __forceinline__ T sys_value(const SysTerms<T, KC>& m) {
+  constexpr SysEntry se = sys_entry<KC>(E);
   if constexpr (se.kind == 0) {
-    constexpr int c1 = se.row / 6, r = se.row % 6, c2 = se.col / 6, s = se.col % 6, pr = c1 + c2;
+    constexpr int c1 = se.row / 6, r = se.row % 6, c2 = se.col / 6, s = se.col % 6, pr = cam_pair(KC, c1, c2);
     const T b10 = m.Bc[c1][0][r], b11 = m.Bc[c1][1][r], b20 = m.Bc[c2][0][s], b21 = m.Bc[c2][1][s];
     return b10 * (m.Q[pr][0] * b20 + m.Q[pr][1] * b21) + b11 * (m.Q[pr][2] * b20 + m.Q[pr][3] * b21);
   } else if constexpr (se.kind == 1) {
@@ -1067,40 +1088,44 @@ __device__ __forceinline__ T sys_value(const SysTerms<T>& m) {
 
 // values K G ... K G + G - 1: summed over the group, value K G + gl landing on lane gl, which
 // writes it to its place in the system (dst: sys_dst of every value, a per-CTA table)
-template <typename T, int G, int K, int... I>
-__device__ __forceinline__ void sys_chunk(const SysTerms<T>& m, const Grp<G>& grp, TwoCamShared<T>& Z,
+template <typename T, int G, int KC, int K, int... I>
+__device__ __forceinline__ void sys_chunk(const SysTerms<T, KC>& m, const Grp<G>& grp, CamShared<T, KC>& Z,
                                           const short* dst, std::integer_sequence<int, I...>) {
-  T v[G] = {sys_value<K * G + I>(m)...};
+  T v[G] = {sys_value<K * G + I, T, KC>(m)...};
   const T sum = reduce_scatter<T, G>(v, grp);
   const int o = dst[K * G + grp.gl];
   if (o >= 0) Z.sys[o] = sum;
 }
 
-template <typename T, int G, int... K>
-__device__ __forceinline__ void sys_reduce(const SysTerms<T>& m, const Grp<G>& grp, TwoCamShared<T>& Z,
+template <typename T, int G, int KC, int... K>
+__device__ __forceinline__ void sys_reduce(const SysTerms<T, KC>& m, const Grp<G>& grp, CamShared<T, KC>& Z,
                                            const short* dst, std::integer_sequence<int, K...>) {
-  (sys_chunk<T, G, K>(m, grp, Z, dst, std::make_integer_sequence<int, G>{}), ...);
+  (sys_chunk<T, G, KC, K>(m, grp, Z, dst, std::make_integer_sequence<int, G>{}), ...);
 }
 
-constexpr int kSysSlots = 128;  // values padded to whole groups of 16 or 32 lanes
+// values padded to whole groups of G lanes (the size of the per-CTA destination table)
+template <int KC, int G>
+__host__ __device__ constexpr int sys_slots() {
+  return (sys_values<KC>() + G - 1) / G * G;
+}
 
-// One lane's point copy in a two-camera block: consensus, scaled dual, its observation on
-// each camera slot (has[c]) and the pixels.
-template <typename T>
-struct TwoCamPt {
-  bool act, has[2];
-  T xb[3], ax[3], z0[2], z1[2];
+// One lane's point copy in a block of at most KC cameras: consensus, scaled dual, its
+// observation on each camera slot (has[c]) and the pixels.
+template <typename T, int KC>
+struct CamPt {
+  bool act, has[KC];
+  T xb[3], ax[3], z0[KC], z1[KC];
 
   // Eq. (14) at point offsets dp and camera offsets dc (nc cameras), summed over the group;
   // +inf when an observation is behind its camera
   template <int G>
-  __device__ T objective(const Prm<T>& q, const Grp<G>& grp, const T (&dp)[3], const TwoCamShared<T>& Z,
+  __device__ T objective(const Prm<T>& q, const Grp<G>& grp, const T (&dp)[3], const CamShared<T, KC>& Z,
                          const T (*dc)[6], int nc) const {
     T s = 0;
     bool ok = true;
     if (act) {
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
+      for (int c = 0; c < KC; ++c) {
         if (!has[c]) continue;
         T v[9];
 #pragma unroll
@@ -1134,7 +1159,7 @@ struct TwoCamPt {
 // L1 prefetch of the copy rows of block nb (the group's next block): its point copies' offsets,
 // duals and indices (one per lane) and its camera copies' rows (one coordinate per lane).
 template <typename T, int G>
-__device__ __forceinline__ void prefetch_block_2cam(const BlockProblem& B, const BlockInfo& nb, int gl) {
+__device__ __forceinline__ void prefetch_block_cams(const BlockProblem& B, const BlockInfo& nb, int gl) {
   const T* pdel = static_cast<const T*>(B.pc_delta);
   const T* cdel = static_cast<const T*>(B.cc_delta);
   if (gl < nb.np) {
@@ -1156,17 +1181,18 @@ __device__ __forceinline__ void prefetch_block_2cam(const BlockProblem& B, const
   }
 }
 
-template <typename T, int G>
-__device__ void solve_block_2cam(const BlockProblem& B, const Prm<T>& q, const BlockInfo& bi, const Grp<G>& grp,
-                                 TwoCamShared<T>& Z, const short* dst, const BlockInfo* next) {
+template <typename T, int G, int KC>
+__device__ void solve_block_cams(const BlockProblem& B, const Prm<T>& q, const BlockInfo& bi, const Grp<G>& grp,
+                                 CamShared<T, KC>& Z, const short* dst, const BlockInfo* next) {
   // rows of the camera system held by a lane: gl + G t, t < R
-  constexpr int R = (12 + G - 1) / G;
+  constexpr int N = 6 * KC, R = (N + G - 1) / G, kPairs = KC * (KC + 1) / 2;
+  using Sh = CamShared<T, KC>;
   using V2 = typename Num<T>::V2;
   const int gl = grp.gl, np = bi.np, nc = bi.nc, n_u = 6 * nc;
   T* pdel = static_cast<T*>(B.pc_delta);
   T* cdel = static_cast<T*>(B.cc_delta);
-  // camera copies: row r = 6 c + u is coordinate u of camera c; an absent second camera is
-  // zero, so that the sums over both camera slots below need no test
+  // camera copies: row r = 6 c + u is coordinate u of camera c; absent camera slots are
+  // zero, so that the sums over all KC slots below need no test
 #pragma unroll
   for (int t = 0; t < R; ++t) {
     const int r = gl + G * t;
@@ -1177,16 +1203,16 @@ __device__ void solve_block_2cam(const BlockProblem& B, const Prm<T>& q, const B
       deferred_ascent<T>(B, static_cast<const T*>(B.Ym)[6 * (long long)j + u],
                          static_cast<const T*>(B.DY)[6 * (long long)j + u], cdel[u * B.n_cc + cc],
                          B.cc_a + u * B.n_cc + cc, Z.vbar[c][u], Z.d[c][u], Z.a[c][u]);
-    } else if (r < 12) {
+    } else if (r < N) {
       Z.vbar[r / 6][r % 6] = Z.d[r / 6][r % 6] = Z.a[r / 6][r % 6] = 0;
     }
   }
   const long long pc = (long long)bi.p0 + gl;
-  TwoCamPt<T> K;
+  CamPt<T, KC> K;
   T dp[3];
   K.act = gl < np;
 #pragma unroll
-  for (int c = 0; c < 2; ++c) {
+  for (int c = 0; c < KC; ++c) {
     K.has[c] = false;
     K.z0[c] = K.z1[c] = 0;
   }
@@ -1203,12 +1229,12 @@ __device__ void solve_block_2cam(const BlockProblem& B, const Prm<T>& q, const B
     const int ob0 = B.pc_obs[pc], nob = B.pc_obs[pc + 1] - ob0;
     const V2* zz = static_cast<const V2*>(B.z);
 #pragma unroll
-    for (int k = 0; k < 2; ++k)
+    for (int k = 0; k < KC; ++k)
       if (k < nob) {
         const int c = B.obs_lc[ob0 + k];
         const V2 z = zz[ob0 + k];
 #pragma unroll
-        for (int s = 0; s < 2; ++s)
+        for (int s = 0; s < KC; ++s)
           if (c == s) {
             K.has[s] = true;
             K.z0[s] = z.x;
@@ -1216,19 +1242,19 @@ __device__ void solve_block_2cam(const BlockProblem& B, const Prm<T>& q, const B
           }
       }
   }
-  if (next) prefetch_block_2cam<T, G>(B, *next, gl);
+  if (next) prefetch_block_cams<T, G>(B, *next, gl);
   grp.sync();
 
   T L = K.objective(q, grp, dp, Z, Z.d, nc);
   T lambda = T(-1);
   for (int step = 0; step < q.steps; ++step) {
     // linearisation of this lane's observations (camera slots without one: zero)
-    SysTerms<T> m;
-    T Ap[2][2][3];
+    SysTerms<T, KC> m;
+    T Ap[KC][2][3];
     T h[6] = {0, 0, 0, 0, 0, 0}, gp[3] = {0, 0, 0}, trc = 0;
     m.noise = 0;
 #pragma unroll
-    for (int c = 0; c < 2; ++c) {
+    for (int c = 0; c < KC; ++c) {
       T J0[9], J1[9], e0 = 0, e1 = 0, w = 0;
       bool lin = false;
       if (K.act && K.has[c]) {
@@ -1298,20 +1324,19 @@ __device__ void solve_block_2cam(const BlockProblem& B, const Prm<T>& q, const B
       w6[0] = c00 * idet, w6[1] = c01 * idet, w6[2] = c02 * idet;
       w6[3] = c11 * idet, w6[4] = c12 * idet, w6[5] = c22 * idet;
     }
-    // U_c = 2w_c A_c W_p g_p and, per camera pair c1 <= c2 (00, 01, 11), the Schur weight
+    // U_c = 2w_c A_c W_p g_p and, per camera pair c1 <= c2, the Schur weight
     // Q = [c1 = c2] 2w_1 I - (2w_1 A_1) W_p (2w_2 A_2)^T
     {
       const T Wg0 = w6[0] * gp[0] + w6[1] * gp[1] + w6[2] * gp[2];
       const T Wg1 = w6[1] * gp[0] + w6[3] * gp[1] + w6[4] * gp[2];
       const T Wg2 = w6[2] * gp[0] + w6[4] * gp[1] + w6[5] * gp[2];
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
+      for (int c = 0; c < KC; ++c) {
         m.U[c][0] = m.tw[c] * (Ap[c][0][0] * Wg0 + Ap[c][0][1] * Wg1 + Ap[c][0][2] * Wg2);
         m.U[c][1] = m.tw[c] * (Ap[c][1][0] * Wg0 + Ap[c][1][1] * Wg1 + Ap[c][1][2] * Wg2);
       }
 #pragma unroll
-      for (int pr = 0; pr < 3; ++pr) {
-        const int c1 = pr == 2 ? 1 : 0, c2 = pr == 0 ? 0 : 1;
+      for (int c2 = 0; c2 < KC; ++c2) {
         const T* a2r0 = Ap[c2][0];
         const T* a2r1 = Ap[c2][1];
         const T w0 = w6[0] * a2r0[0] + w6[1] * a2r0[1] + w6[2] * a2r0[2];
@@ -1320,23 +1345,28 @@ __device__ void solve_block_2cam(const BlockProblem& B, const Prm<T>& q, const B
         const T x0 = w6[0] * a2r1[0] + w6[1] * a2r1[1] + w6[2] * a2r1[2];
         const T x1 = w6[1] * a2r1[0] + w6[3] * a2r1[1] + w6[4] * a2r1[2];
         const T x2 = w6[2] * a2r1[0] + w6[4] * a2r1[1] + w6[5] * a2r1[2];
-        const T* a1r0 = Ap[c1][0];
-        const T* a1r1 = Ap[c1][1];
-        const T sw = m.tw[c1] * m.tw[c2], dgw = c1 == c2 ? m.tw[c1] : T(0);
-        m.Q[pr][0] = dgw - sw * (a1r0[0] * w0 + a1r0[1] * w1 + a1r0[2] * w2);
-        m.Q[pr][1] = -sw * (a1r0[0] * x0 + a1r0[1] * x1 + a1r0[2] * x2);
-        m.Q[pr][2] = -sw * (a1r1[0] * w0 + a1r1[1] * w1 + a1r1[2] * w2);
-        m.Q[pr][3] = dgw - sw * (a1r1[0] * x0 + a1r1[1] * x1 + a1r1[2] * x2);
+#pragma unroll
+        for (int c1 = 0; c1 <= c2; ++c1) {
+          const int pr = cam_pair(KC, c1, c2);
+          const T* a1r0 = Ap[c1][0];
+          const T* a1r1 = Ap[c1][1];
+          const T sw = m.tw[c1] * m.tw[c2], dgw = c1 == c2 ? m.tw[c1] : T(0);
+          m.Q[pr][0] = dgw - sw * (a1r0[0] * w0 + a1r0[1] * w1 + a1r0[2] * w2);
+          m.Q[pr][1] = -sw * (a1r0[0] * x0 + a1r0[1] * x1 + a1r0[2] * x2);
+          m.Q[pr][2] = -sw * (a1r1[0] * w0 + a1r1[1] * w1 + a1r1[2] * w2);
+          m.Q[pr][3] = dgw - sw * (a1r1[0] * x0 + a1r1[1] * x1 + a1r1[2] * x2);
+        }
       }
+      static_assert(kPairs == KC * (KC + 1) / 2, "camera pairs");
     }
     // sums over the block's points, G values at a time
-    sys_reduce<T, G>(m, grp, Z, dst, std::make_integer_sequence<int, (kSysValues + G - 1) / G>{});
+    sys_reduce<T, G, KC>(m, grp, Z, dst, std::make_integer_sequence<int, sys_slots<KC, G>() / G>{});
     grp.sync();
     // row r < n_u of S + diag(rho_c) + lambda I (entries j <= r), g_r (the camera gradient
-    // with its penalty) and the right-hand side rhs_r - g_r, on lane r mod G; a block with one
-    // camera is padded to 12 x 12 by identity rows with a zero right-hand side, which leave
-    // its factor and solution as they are
-    T a[R][12], lc[R][12], y[R], gi[R];
+    // with its penalty) and the right-hand side rhs_r - g_r, on lane r mod G; a block with
+    // fewer than KC cameras is padded to N x N by identity rows with a zero right-hand side,
+    // which leave its factor and solution as they are
+    T a[R][N], lc[R][N], y[R], gi[R];
 #pragma unroll
     for (int t = 0; t < R; ++t) {
       const int r = gl + G * t;
@@ -1344,14 +1374,14 @@ __device__ void solve_block_2cam(const BlockProblem& B, const Prm<T>& q, const B
       const int c = row ? r / 6 : 0, u = row ? r % 6 : 0;
       const T shift = q.rho(3 + u) + lambda;
 #pragma unroll
-      for (int j = 0; j < 12; ++j) {
-        a[t][j] = row && j <= r ? Z.sys[13 * j + r] + (j == r ? shift : T(0)) : T(j == r ? 1 : 0);
+      for (int j = 0; j < N; ++j) {
+        a[t][j] = row && j <= r ? Z.sys[Sh::kLd * j + r] + (j == r ? shift : T(0)) : T(j == r ? 1 : 0);
         lc[t][j] = 0;
       }
       gi[t] = y[t] = 0;
       if (row) {
-        gi[t] = Z.sys[TwoCamShared<T>::kG + r] + q.rho(3 + u) * (Z.a[c][u] + Z.d[c][u]);
-        y[t] = Z.sys[TwoCamShared<T>::kRhs + r] - gi[t];
+        gi[t] = Z.sys[Sh::kG + r] + q.rho(3 + u) * (Z.a[c][u] + Z.d[c][u]);
+        y[t] = Z.sys[Sh::kRhs + r] - gi[t];
       }
     }
     // Cholesky factor in registers: each held row r of L (a) and, below the diagonal,
@@ -1359,7 +1389,7 @@ __device__ void solve_block_2cam(const BlockProblem& B, const Prm<T>& q, const B
     // k mod G in slot k / G; the tests on G t skip rows a slot cannot hold.
     bool spd = true;
 #pragma unroll
-    for (int k = 0; k < 12; ++k) {
+    for (int k = 0; k < N; ++k) {
       const T piv = grp.bcast(a[k / G][k], k % G);
       spd = spd && piv > T(0);
       const T lkk = Num<T>::sqrt_(piv);
@@ -1370,8 +1400,8 @@ __device__ void solve_block_2cam(const BlockProblem& B, const Prm<T>& q, const B
         if (r == k) a[t][k] = lkk;
         else if (r > k) a[t][k] = Num<T>::div(a[t][k], lkk);
       }
-#pragma unroll 11
-      for (int j = k + 1; j < 12; ++j) {
+#pragma unroll N
+      for (int j = k + 1; j < N; ++j) {
         const T ljk = grp.bcast(a[j / G][k], j % G);
         if (gl == k % G) lc[k / G][j] = ljk;
 #pragma unroll
@@ -1387,7 +1417,7 @@ __device__ void solve_block_2cam(const BlockProblem& B, const Prm<T>& q, const B
     }
     // L y = rhs - g, then L^T dy = y; row r's entry on lane r mod G (zero beyond n_u)
 #pragma unroll
-    for (int k = 0; k < 12; ++k) {
+    for (int k = 0; k < N; ++k) {
       if (gl == k % G) y[k / G] = Num<T>::div(y[k / G], a[k / G][k]);
       const T yk = grp.bcast(y[k / G], k % G);
 #pragma unroll
@@ -1397,7 +1427,7 @@ __device__ void solve_block_2cam(const BlockProblem& B, const Prm<T>& q, const B
       }
     }
 #pragma unroll
-    for (int k = 11; k >= 0; --k) {
+    for (int k = N - 1; k >= 0; --k) {
       if (gl == k % G) y[k / G] = Num<T>::div(y[k / G], a[k / G][k]);
       const T xk = grp.bcast(y[k / G], k % G);
 #pragma unroll
@@ -1412,7 +1442,7 @@ __device__ void solve_block_2cam(const BlockProblem& B, const Prm<T>& q, const B
     {
       T t3[3] = {gp[0], gp[1], gp[2]};
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
+      for (int c = 0; c < KC; ++c) {
         T r0 = 0, r1 = 0;
 #pragma unroll
         for (int u = 0; u < 6; ++u) {
@@ -1448,7 +1478,7 @@ __device__ void solve_block_2cam(const BlockProblem& B, const Prm<T>& q, const B
     dd = grp.sum(dd);
     const T pred = T(0.5) * (lambda * dd - gd);
     const bool trust = isfinite(L) && q.model_tol > T(0) &&
-                       pred <= q.model_tol * Num<T>::unit_roundoff * (fabs(L) + Z.sys[TwoCamShared<T>::kNoise]);
+                       pred <= q.model_tol * Num<T>::unit_roundoff * (fabs(L) + Z.sys[Sh::kNoise]);
 #pragma unroll
     for (int t = 0; t < R; ++t) {
       const int r = gl + G * t;
@@ -1493,19 +1523,18 @@ __device__ void solve_block_2cam(const BlockProblem& B, const Prm<T>& q, const B
   grp.sync();
 }
 
-// Blocks [lo, hi) of one size class with at most two cameras and G points, one group of G
+// Blocks [lo, hi) of one size class with at most KC cameras and G points, one group of G
 // lanes per block, the groups' systems in static shared memory.
-template <typename T, int G>
-__global__ void __launch_bounds__(kBlkWarps * 32, (sizeof(T) == 4 ? 4 : 1))
-    block_solve_2cam_kernel(BlockProblem B, Prm<T> q, int cur, int lo, int hi) {
-  constexpr int kPer = 32 / G;
-  __shared__ TwoCamShared<T> sh[kBlkWarps * kPer];
-  __shared__ short dst[kSysSlots];
-  for (int e = threadIdx.x; e < kSysSlots; e += blockDim.x) dst[e] = (short)sys_dst(e);
+template <typename T, int G, int KC>
+__device__ __forceinline__ void block_solve_cams(const BlockProblem& B, const Prm<T>& q, int lo, int hi) {
+  constexpr int kPer = 32 / G, kSlots = sys_slots<KC, G>();
+  __shared__ CamShared<T, KC> sh[kBlkWarps * kPer];
+  __shared__ short dst[kSlots];
+  for (int e = threadIdx.x; e < kSlots; e += blockDim.x) dst[e] = (short)sys_dst<KC>(e);
   __syncthreads();
   const int warps = blockDim.x >> 5, warp = threadIdx.x >> 5;
   const Grp<G> grp(threadIdx.x & 31);
-  TwoCamShared<T>& Z = sh[warp * kPer + grp.base / G];
+  CamShared<T, KC>& Z = sh[warp * kPer + grp.base / G];
   const int stride = gridDim.x * warps * kPer;
   int b = lo + (blockIdx.x * warps + warp) * kPer + grp.base / G;
   BlockInfo bi{};
@@ -1514,9 +1543,23 @@ __global__ void __launch_bounds__(kBlkWarps * 32, (sizeof(T) == 4 ? 4 : 1))
     const bool more = b + stride < hi;
     BlockInfo nb{};
     if (more) nb = B.blocks[b + stride];
-    solve_block_2cam<T, G>(B, q, bi, grp, Z, dst, more ? &nb : nullptr);
+    solve_block_cams<T, G, KC>(B, q, bi, grp, Z, dst, more ? &nb : nullptr);
     bi = nb;
   }
+}
+
+// at most two cameras: 4 CTAs of 4 warps per SM in FP32 (128 registers)
+template <typename T, int G>
+__global__ void __launch_bounds__(kBlkWarps * 32, (sizeof(T) == 4 ? 4 : 1))
+    block_solve_2cam_kernel(BlockProblem B, Prm<T> q, int cur, int lo, int hi) {
+  block_solve_cams<T, G, 2>(B, q, lo, hi);
+}
+
+// at most four cameras (a 24 x 24 system, a row per lane): 2 CTAs of 4 warps per SM
+template <typename T, int G>
+__global__ void __launch_bounds__(kBlkWarps * 32, (sizeof(T) == 4 ? 2 : 1))
+    block_solve_4cam_kernel(BlockProblem B, Prm<T> q, int cur, int lo, int hi) {
+  block_solve_cams<T, G, 4>(B, q, lo, hi);
 }
 
 // Blocks [lo, hi) of one size class, each solved by a group of G lanes holding PPL
@@ -1852,17 +1895,21 @@ cudaError_t launch_block_class_1cam(dba_block_ctx* ctx, int lo, int hi) {
   return cudaGetLastError();
 }
 
-// Blocks [lo, hi) with at most two cameras and G points: the register solve, groups of G lanes.
-template <typename T, int G>
+// Blocks [lo, hi) with at most KC = 2 or 4 cameras and G points: the register solve, groups of
+// G lanes.
+template <typename T, int G, int KC = 2>
 cudaError_t launch_block_class_2cam(dba_block_ctx* ctx, int lo, int hi) {
   if (hi <= lo) return cudaSuccess;
   constexpr int kThreads = dba::kBlkWarps * 32;
+  auto kernel = [] {
+    if constexpr (KC == 2) return dba::block_solve_2cam_kernel<T, G>;
+    else return dba::block_solve_4cam_kernel<T, G>;
+  }();
   static std::atomic<int> cached{0};  // CTAs of a full wave
   int grid = cached.load();
   if (!grid) {
     int per_sm = 0, dev = 0, sms = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dba::block_solve_2cam_kernel<T, G>,
-                                                                  kThreads, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0);
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
@@ -1871,8 +1918,7 @@ cudaError_t launch_block_class_2cam(dba_block_ctx* ctx, int lo, int hi) {
   }
   const int need = dba::blocks_of(hi - lo, dba::kBlkWarps * (32 / G));
   const int g = std::max(1, std::min(need, grid));
-  dba::block_solve_2cam_kernel<T, G><<<g, kThreads, 0, ctx->stream>>>(ctx->B, dba::make_prm<T>(ctx->prm), ctx->cur,
-                                                                       lo, hi);
+  kernel<<<g, kThreads, 0, ctx->stream>>>(ctx->B, dba::make_prm<T>(ctx->prm), ctx->cur, lo, hi);
   return cudaGetLastError();
 }
 
@@ -1893,7 +1939,7 @@ cudaError_t launch_block_class_kc(dba_block_ctx* ctx, int k) {
       return e == cudaSuccess ? launch_block_class_2cam<T, 16>(ctx, m8, hi) : e;
     } else {
       if (ctx->kappa == 2) return launch_block_class_2cam<T, G>(ctx, lo, hi);
-      return launch_block_class<T, 4, G, PPL>(ctx, lo, hi);
+      return launch_block_class_2cam<T, G, 4>(ctx, lo, hi);
     }
   } else {
     if (ctx->kappa == 2) return launch_block_class<T, 2, G, PPL>(ctx, lo, hi);
