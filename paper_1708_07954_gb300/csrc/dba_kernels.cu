@@ -343,6 +343,8 @@ __device__ __forceinline__ void process_tile_body(const DevProblem& P, const Prm
         sum = 0.0;
         for (int e = se.x; e < se.x + se.y; ++e) sum += s_buf[c][e];
       } else {
+        // one accumulator, so unrolling keeps the summation order
+#pragma unroll 4
         for (int e = se.x; e < se.x + se.y; ++e) acc += s_t[c][e];
         sum = to_f64<T>(acc);
       }
@@ -376,6 +378,7 @@ __device__ __forceinline__ void process_tile_body(const DevProblem& P, const Prm
         for (int e = se.x; e < se.x + se.y; ++e) sum += s_buf[3 + c][e];
       } else {
         T acc = 0;
+#pragma unroll 4
         for (int e = se.x; e < se.x + se.y; ++e) acc += s_t[3 + c][e];
         sum = to_f64<T>(acc);
       }
