@@ -108,6 +108,24 @@ struct Grp {
   __device__ T bcast(T v, int src) const { return __shfl_sync(mask, v, src, G); }
 };
 
+// Lane gl of a group of G receives the sum over the group of v[gl] (v is overwritten).
+// Stage h: the lane keeps the half of its values whose index has bit h equal to its own lane
+// bit h, adds the partner's partial sums of that half and hands over the other half.
+template <typename T, int G>
+__device__ __forceinline__ T reduce_scatter(T (&v)[G], const Grp<G>& grp) {
+#pragma unroll
+  for (int h = G / 2; h >= 1; h >>= 1) {
+    const bool up = (grp.gl & h) != 0;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const T send = up ? v[i] : v[i + h];
+      const T keep = up ? v[i + h] : v[i];
+      v[i] = keep + __shfl_xor_sync(grp.mask, send, h, G);
+    }
+  }
+  return v[0];
+}
+
 // State of one block solve shared by its lane group; KC = the most cameras a block holds.
 template <typename T, int KC>
 struct BlkShared {
@@ -614,12 +632,12 @@ __device__ void solve_block(const BlockProblem& B, const Prm<T>& q, const BlockI
 
 // ------------------------------------------------------------ one-camera blocks
 // A block with a single camera (every block when block_cams = 1; the 8-lane class always)
-// has a 6 x 6 reduced camera system.  It is solved without shared memory: each lane forms
-// the terms of its point copies (each holds the block's one observation of its point), a
-// butterfly over the group sums them, and every lane factors the system in registers.  A
-// butterfly stage adds the same two partial sums on both lanes of a pair (addition is
-// commutative), so all lanes end with the same bits and take the same step, acceptance
-// and damping.  Same arithmetic as solve_block: points eliminated by their 3x3 inverses,
+// has a 6 x 6 reduced camera system.  Each lane forms the terms of its point copies (each
+// holds the block's one observation of its point); a reduce-scatter over the group sums
+// them into a small per-group buffer that every lane reads back (butterflies in groups of
+// one or two lanes, where a butterfly stage adds the same two partial sums on both lanes
+// of a pair), so all lanes hold the same bits, factor the system in registers and take the
+// same step, acceptance and damping.  Same arithmetic as solve_block: points eliminated by their 3x3 inverses,
 // Schur weights Q = 2w I - (2w)^2 A W_p A^T, right-hand side sum B^T U - g_c.
 template <typename T, int G, int PPL>
 struct OneCam {
@@ -692,7 +710,7 @@ __device__ __forceinline__ void prefetch_block(const BlockProblem& B, const Bloc
 
 template <typename T, int G>
 __device__ void solve_block_1cam(const BlockProblem& B, const Prm<T>& q, const BlockInfo& bi, const Grp<G>& grp,
-                                 int cur, const BlockInfo* next) {
+                                 int cur, const BlockInfo* next, T* red) {
   constexpr int PPL = 1;  // one point copy per lane (blocks of at most 32 points)
   using V2 = typename Num<T>::V2;
   const int gl = grp.gl, np = bi.np;
@@ -818,15 +836,50 @@ __device__ void solve_block_1cam(const BlockProblem& B, const Prm<T>& q, const B
         rhs[r] = b0r * U0 + b1r * U1;
       }
     }
-    // sums over the block's points (every lane receives the same bits)
+    // sums over the block's points (every lane receives the same bits): in groups of 4 or
+    // more lanes a reduce-scatter of the 34 values, G at a time, into the group's buffer,
+    // read back by every lane; below that butterflies
+    if constexpr (G >= 4) {
+      constexpr int kV = 34, kC = (kV + G - 1) / G;
+      T vals[kC * G];
 #pragma unroll
-    for (int e = 0; e < 21; ++e) S[e] = grp.sum(S[e]);
+      for (int e = 0; e < 21; ++e) vals[e] = S[e];
 #pragma unroll
-    for (int u = 0; u < 6; ++u) {
-      rhs[u] = grp.sum(rhs[u]);
-      gc[u] = grp.sum(gc[u]) + q.rho(3 + u) * (K.ca[u] + cd[u]);  // camera gradient with its penalty
+      for (int u = 0; u < 6; ++u) {
+        vals[21 + u] = rhs[u];
+        vals[27 + u] = gc[u];
+      }
+      vals[33] = noise;
+#pragma unroll
+      for (int e = kV; e < kC * G; ++e) vals[e] = 0;
+#pragma unroll
+      for (int k = 0; k < kC; ++k) {
+        T v[G];
+#pragma unroll
+        for (int i = 0; i < G; ++i) v[i] = vals[k * G + i];
+        const T sum = reduce_scatter<T, G>(v, grp);
+        if (k * G + grp.gl < kV) red[k * G + grp.gl] = sum;
+      }
+      grp.sync();
+#pragma unroll
+      for (int e = 0; e < 21; ++e) S[e] = red[e];
+#pragma unroll
+      for (int u = 0; u < 6; ++u) {
+        rhs[u] = red[21 + u];
+        gc[u] = red[27 + u] + q.rho(3 + u) * (K.ca[u] + cd[u]);  // camera gradient with its penalty
+      }
+      noise = red[33];
+      grp.sync();  // the buffer is free for the next step
+    } else {
+#pragma unroll
+      for (int e = 0; e < 21; ++e) S[e] = grp.sum(S[e]);
+#pragma unroll
+      for (int u = 0; u < 6; ++u) {
+        rhs[u] = grp.sum(rhs[u]);
+        gc[u] = grp.sum(gc[u]) + q.rho(3 + u) * (K.ca[u] + cd[u]);  // camera gradient with its penalty
+      }
+      noise = grp.sum(noise);
     }
-    noise = grp.sum(noise);
     // (S + diag(rho_c) + lambda I) dy = rhs - g_c by a Cholesky factorisation in registers
     T A[6][6];
     {
@@ -944,6 +997,7 @@ template <typename T, int G>
 __global__ void __launch_bounds__(kBlkWarps * 32)
     block_solve_1cam_kernel(BlockProblem B, Prm<T> q, int cur, int lo, int hi) {
   constexpr int kPer = 32 / G;
+  __shared__ T red[kBlkWarps * kPer][G >= 4 ? 36 : 1];  // each group's sums (groups of >= 4 lanes)
   const int warps = blockDim.x >> 5, warp = threadIdx.x >> 5;
   const Grp<G> grp(threadIdx.x & 31);
   const int stride = gridDim.x * warps * kPer;
@@ -956,7 +1010,7 @@ __global__ void __launch_bounds__(kBlkWarps * 32)
     const bool more = b + stride < hi;
     BlockInfo nb{};
     if (more) nb = B.blocks[b + stride];
-    solve_block_1cam<T, G>(B, q, bi, grp, cur, more ? &nb : nullptr);
+    solve_block_1cam<T, G>(B, q, bi, grp, cur, more ? &nb : nullptr, red[warp * kPer + grp.base / G]);
     bi = nb;
   }
 }
@@ -1039,23 +1093,6 @@ __host__ __device__ constexpr int cam_pair(int KC, int c1, int c2) {
   return c1 * KC - c1 * (c1 - 1) / 2 + (c2 - c1);
 }
 
-// Lane gl of a group of G receives the sum over the group of v[gl] (v is overwritten).
-// Stage h: the lane keeps the half of its values whose index has bit h equal to its own lane
-// bit h, adds the partner's partial sums of that half and hands over the other half.
-template <typename T, int G>
-__device__ __forceinline__ T reduce_scatter(T (&v)[G], const Grp<G>& grp) {
-#pragma unroll
-  for (int h = G / 2; h >= 1; h >>= 1) {
-    const bool up = (grp.gl & h) != 0;
-#pragma unroll
-    for (int i = 0; i < h; ++i) {
-      const T send = up ? v[i] : v[i + h];
-      const T keep = up ? v[i + h] : v[i];
-      v[i] = keep + __shfl_xor_sync(grp.mask, send, h, G);
-    }
-  }
-  return v[0];
-}
 
 // One lane's terms of the reduced system: the camera rows B_c of its observations' Jacobians,
 // U_c, the Schur weights Q of the camera pairs, the IRLS weights 2w_c, the residuals and the
