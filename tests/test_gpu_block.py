@@ -87,7 +87,9 @@ def test_one_point_one_camera_blocks_equal_the_per_observation_path():
         assert colerr(ca, cb) <= TOL64 and colerr(pa, pb) <= TOL64
 
 
-@pytest.mark.parametrize("pi,kappa", [(8, 2), (32, 4), (64, 2)])
+# every FP32 solve kernel: one camera in groups of 1 to 32 lanes (32 x 1), two and four
+# camera slots, and two point copies a lane
+@pytest.mark.parametrize("pi,kappa", [(8, 2), (32, 1), (32, 4), (64, 2)])
 def test_fp32_tracks_the_fp64_oracle(pi, kappa):
     sc = S.scene1(n_pts=1500, n_cams=24, seed=29)
     with dba.BlockSolver(sc, pi, kappa, precision=dba.DBA_PREC_F32_LOCAL) as s:
