@@ -1222,7 +1222,7 @@ template <typename T, int G, int KC>
 __device__ void solve_block_cams(const BlockProblem& B, const Prm<T>& q, const BlockInfo& bi, const Grp<G>& grp,
                                  CamShared<T, KC>& Z, const short* dst, const BlockInfo* next) {
   // rows of the camera system held by a lane: gl + G t, t < R
-  constexpr int N = 6 * KC, R = (N + G - 1) / G, kPairs = KC * (KC + 1) / 2;
+  constexpr int N = 6 * KC, R = (N + G - 1) / G;
   using Sh = CamShared<T, KC>;
   using V2 = typename Num<T>::V2;
   const int gl = grp.gl, np = bi.np, nc = bi.nc, n_u = 6 * nc;
@@ -1394,7 +1394,6 @@ __device__ void solve_block_cams(const BlockProblem& B, const Prm<T>& q, const B
           m.Q[pr][3] = dgw - sw * (a1r1[0] * x0 + a1r1[1] * x1 + a1r1[2] * x2);
         }
       }
-      static_assert(kPairs == KC * (KC + 1) / 2, "camera pairs");
     }
     // sums over the block's points, G values at a time
     sys_reduce<T, G, KC>(m, grp, Z, dst, std::make_integer_sequence<int, sys_slots<KC, G>() / G>{});
