@@ -12,10 +12,12 @@
 // pi <= 64), camera copies (kappa <= 4) shared by the group in shared memory.  Each damped
 // Gauss-Newton step eliminates the points (3x3 per lane) and solves the reduced camera
 // system (at most 24 x 24).  Three solve kernels:
-//   one camera (6 x 6): terms summed by butterflies, factored in every lane's registers;
-//   two cameras, at most 32 points (12 x 12): terms formed in registers, summed by a
-//     reduce-scatter over the group, factored lane-per-row in shared memory;
-//   otherwise: terms staged in shared memory, summed entry-parallel, factored lane-per-row.
+//   one camera (6 x 6): terms summed by a reduce-scatter over the group (butterflies in
+//     groups of one or two lanes), factored in every lane's registers;
+//   two or four camera slots, at most 32 points (12 x 12 or 24 x 24): terms formed in
+//     registers, summed by the reduce-scatter, factored in registers a row per lane;
+//   above 32 points (two copies a lane): terms staged in shared memory, summed
+//     entry-parallel, factored lane-per-row in shared memory.
 // Consensus (Eqs. 10-11 over copies) and dual ascent (Eqs. 12-13) run in FP64 over copy
 // lists.
 #include <cuda_runtime.h>
@@ -1987,8 +1989,9 @@ cudaError_t launch_block_class_kc(dba_block_ctx* ctx, int k) {
 // (groups of 1, 2, 4 or 8 lanes by the block's points), at most 2 cameras and 16 points
 // (16 lanes; 8 for two cameras and at most 8 points), at most 32 points (32 lanes), the rest
 // (32 lanes holding two point copies each).  Blocks with one camera (the first class; the
-// next two when block_cams = 1) take the register-resident solve, blocks of the next two
-// classes with at most two cameras the reduce-scatter solve.
+// next two when block_cams = 1) take the one-camera solve, blocks of the next two classes
+// the two-camera solve (the 32-lane class: the four-slot solve when block_cams >= 3), the
+// rest the shared-memory solve.
 template <typename T>
 cudaError_t launch_block_solve(dba_block_ctx* ctx) {
   // block_solve_launches counts the nonempty ranges launched here; keep the two in step
