@@ -1017,6 +1017,304 @@ __global__ void __launch_bounds__(kBlkWarps * 32)
   }
 }
 
+// ------------------------------------------------------------ one-point blocks
+// A block of one point and nc <= 4 cameras (one observation per camera) has 3 + 6 nc unknowns.
+// One thread solves it by eliminating the cameras instead of the point: each camera's block
+// of the damped normal matrix is diagonal plus rank 2 (its one observation), so it is
+// inverted through its 2 x 2 capacitance matrix (Sherman-Morrison-Woodbury, as the
+// per-observation solve does), which leaves a 3 x 3 system for the point.  Same damped
+// normal equations, damping start, acceptance and noise rules as the other block solves.
+template <typename T>
+struct PointCam {
+  T vbar[6], a[6], z0, z1;
+};
+
+// y = (D + tw B^T B)^-1 v with D = diag(iD)^-1 (iD: the inverse diagonal) and B the 2 x 6
+// camera rows: D^-1 v - tw D^-1 B^T S^-1 B D^-1 v, S = I + tw B D^-1 B^T (det >= 1)
+template <typename T>
+__device__ __forceinline__ void cam_block_solve(const T (&iD)[6], const T (&Bc)[2][6], T tw, const T (&v)[6],
+                                                T (&y)[6]) {
+  T s00 = 0, s01 = 0, s11 = 0, t0 = 0, t1 = 0;
+#pragma unroll
+  for (int u = 0; u < 6; ++u) {
+    const T q = iD[u] * v[u];
+    y[u] = q;
+    s00 += Bc[0][u] * iD[u] * Bc[0][u];
+    s01 += Bc[0][u] * iD[u] * Bc[1][u];
+    s11 += Bc[1][u] * iD[u] * Bc[1][u];
+    t0 += Bc[0][u] * q;
+    t1 += Bc[1][u] * q;
+  }
+  const T S00 = T(1) + tw * s00, S01 = tw * s01, S11 = T(1) + tw * s11;
+  const T idet = Num<T>::rcp(S00 * S11 - S01 * S01);
+  const T w0 = (S11 * t0 - S01 * t1) * idet, w1 = (S00 * t1 - S01 * t0) * idet;
+#pragma unroll
+  for (int u = 0; u < 6; ++u) y[u] -= tw * iD[u] * (Bc[0][u] * w0 + Bc[1][u] * w1);
+}
+
+template <typename T>
+__device__ void solve_block_point(const BlockProblem& B, const Prm<T>& q, const BlockInfo& bi) {
+  constexpr int KC = 4;  // most cameras of a block
+  using V2 = typename Num<T>::V2;
+  const int nc = bi.nc, n_u = 6 * nc;
+  T* pdel = static_cast<T*>(B.pc_delta);
+  T* cdel = static_cast<T*>(B.cc_delta);
+  PointCam<T> C[KC];
+  T cd[KC][6];  // camera offsets
+  bool has[KC];
+#pragma unroll
+  for (int c = 0; c < KC; ++c) {
+    has[c] = c < nc;
+#pragma unroll
+    for (int u = 0; u < 6; ++u) C[c].vbar[u] = cd[c][u] = C[c].a[u] = 0;
+    C[c].z0 = C[c].z1 = 0;
+    if (has[c]) {
+      const long long cc = (long long)bi.c0 + c;
+      const int j = B.cc_cam[cc];
+#pragma unroll
+      for (int u = 0; u < 6; ++u)
+        deferred_ascent<T>(B, static_cast<const T*>(B.Ym)[6 * (long long)j + u],
+                           static_cast<const T*>(B.DY)[6 * (long long)j + u], cdel[u * B.n_cc + cc],
+                           B.cc_a + u * B.n_cc + cc, C[c].vbar[u], cd[c][u], C[c].a[u]);
+    }
+  }
+  const long long pc = bi.p0;
+  T xb[3], ax[3], dp[3];
+  {
+    const int i = B.pc_pt[pc];
+#pragma unroll
+    for (int u = 0; u < 3; ++u)
+      deferred_ascent<T>(B, static_cast<const T*>(B.Xm)[3 * (long long)i + u],
+                         static_cast<const T*>(B.DX)[3 * (long long)i + u], pdel[u * B.n_pc + pc],
+                         B.pc_a + u * B.n_pc + pc, xb[u], dp[u], ax[u]);
+    // one observation per camera of the block
+    const int ob0 = B.pc_obs[pc], nob = B.pc_obs[pc + 1] - ob0;
+    const V2* zz = static_cast<const V2*>(B.z);
+#pragma unroll
+    for (int k = 0; k < KC; ++k)
+      if (k < nob) {
+        const int c = B.obs_lc[ob0 + k];
+        const V2 z = zz[ob0 + k];
+#pragma unroll
+        for (int s = 0; s < KC; ++s)
+          if (c == s) {
+            C[s].z0 = z.x;
+            C[s].z1 = z.y;
+          }
+      }
+  }
+  // Eq. (14) at point offset p and camera offsets dc; +inf when an observation is behind its camera
+  auto objective = [&](const T (&p)[3], const T (&dc)[KC][6]) -> T {
+    T s = 0;
+    bool ok = true;
+#pragma unroll
+    for (int c = 0; c < KC; ++c) {
+      if (!has[c]) continue;
+      T v[9];
+#pragma unroll
+      for (int u = 0; u < 3; ++u) v[u] = xb[u] + p[u];
+#pragma unroll
+      for (int u = 0; u < 6; ++u) v[3 + u] = C[c].vbar[u] + dc[c][u];
+      Pose<T> P;
+      pose_at(v, q.eps, P);
+      if (!P.valid) {
+        ok = false;
+      } else {
+        const T iz = Num<T>::rcp(P.p[2]);
+        const T e0 = C[c].z0 - (q.focal * P.p[0] * iz + q.cx);
+        const T e1 = C[c].z1 - (q.focal * P.p[1] * iz + q.cy);
+        s += misfit<T>(q.loss, q.lp, e0 * e0 + e1 * e1);
+      }
+#pragma unroll
+      for (int u = 0; u < 6; ++u) s += q.rho(3 + u) * dc[c][u] * (C[c].a[u] + T(0.5) * dc[c][u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 3; ++u) s += q.rho_x * p[u] * (ax[u] + T(0.5) * p[u]);
+    return ok ? s : Num<T>::inf();
+  };
+  T L = objective(dp, cd);
+  T lambda = T(-1);
+  for (int step = 0; step < q.steps; ++step) {
+    // linearisation of each observation (camera slots without one, or behind the camera: zero)
+    T Ap[KC][2][3], Bc[KC][2][6], tw[KC], gc[KC][6];
+    T h[6] = {0, 0, 0, 0, 0, 0}, gx[3] = {0, 0, 0}, trc = 0, noise = 0;
+#pragma unroll
+    for (int c = 0; c < KC; ++c) {
+      T J0[9], J1[9], e0 = 0, e1 = 0, w = 0;
+      bool lin = false;
+      if (has[c]) {
+        T v[9];
+#pragma unroll
+        for (int u = 0; u < 3; ++u) v[u] = xb[u] + dp[u];
+#pragma unroll
+        for (int u = 0; u < 6; ++u) v[3 + u] = C[c].vbar[u] + cd[c][u];
+        Pose<T> P;
+        pose_at(v, q.eps, P);
+        if (P.valid) {
+          linearize(P, C[c].z0, C[c].z1, q, J0, J1, e0, e1, w);
+          lin = true;
+        }
+      }
+      if (!lin) {
+#pragma unroll
+        for (int u = 0; u < 9; ++u) J0[u] = J1[u] = 0;
+        e0 = e1 = w = 0;
+      }
+      const T t = T(2) * w;
+      tw[c] = t;
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        Ap[c][0][u] = J0[u];
+        Ap[c][1][u] = J1[u];
+      }
+#pragma unroll
+      for (int u = 0; u < 6; ++u) {
+        Bc[c][0][u] = J0[3 + u];
+        Bc[c][1][u] = J1[3 + u];
+        gc[c][u] = -t * (J0[3 + u] * e0 + J1[3 + u] * e1) + (has[c] ? q.rho(3 + u) * (C[c].a[u] + cd[c][u]) : T(0));
+      }
+      h[0] += t * (J0[0] * J0[0] + J1[0] * J1[0]);
+      h[1] += t * (J0[0] * J0[1] + J1[0] * J1[1]);
+      h[2] += t * (J0[0] * J0[2] + J1[0] * J1[2]);
+      h[3] += t * (J0[1] * J0[1] + J1[1] * J1[1]);
+      h[4] += t * (J0[1] * J0[2] + J1[1] * J1[2]);
+      h[5] += t * (J0[2] * J0[2] + J1[2] * J1[2]);
+#pragma unroll
+      for (int u = 0; u < 3; ++u) gx[u] -= t * (J0[u] * e0 + J1[u] * e1);
+#pragma unroll
+      for (int u = 3; u < 9; ++u) trc += t * (J0[u] * J0[u] + J1[u] * J1[u]);
+      noise += t * Num<T>::sqrt_(e0 * e0 + e1 * e1) * (fabs(C[c].z0) + fabs(C[c].z1));
+    }
+#pragma unroll
+    for (int u = 0; u < 3; ++u) gx[u] += q.rho_x * (ax[u] + dp[u]);
+    if (lambda < T(0)) {
+      T tr = trc + h[0] + h[3] + h[5] + T(3) * q.rho_x;
+      for (int c = 0; c < nc; ++c)
+#pragma unroll
+        for (int u = 0; u < 6; ++u) tr += q.rho(3 + u);
+      lambda = q.lambda0 * tr / T(3 + n_u);
+    }
+    // cameras eliminated: S = H_xx - sum_c H_xc H_cc^-1 H_cx, r = -g_x + sum_c H_xc H_cc^-1 g_c,
+    // with H_cx = 2w B^T A (6 x 3) and H_cc = diag(rho_c) + lambda I + 2w B^T B
+    T iD[6];
+#pragma unroll
+    for (int u = 0; u < 6; ++u) iD[u] = Num<T>::rcp(q.rho(3 + u) + lambda);
+    T S[6], r[3];
+    {
+      const T dg = q.rho_x + lambda;
+      S[0] = h[0] + dg, S[1] = h[1], S[2] = h[2], S[3] = h[3] + dg, S[4] = h[4], S[5] = h[5] + dg;
+    }
+#pragma unroll
+    for (int u = 0; u < 3; ++u) r[u] = -gx[u];
+#pragma unroll
+    for (int c = 0; c < KC; ++c) {
+      if (!has[c]) continue;
+      // H_xc = 2w A^T B (its rows hx[k] = columns of H_cx); M_k = H_cc^-1 H_cx[:, k],
+      // m = H_cc^-1 g_c; S -= H_xc M, r += H_xc m
+      T hx[3][6], Mk[3][6], m[6];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+#pragma unroll
+        for (int u = 0; u < 6; ++u) hx[k][u] = tw[c] * (Ap[c][0][k] * Bc[c][0][u] + Ap[c][1][k] * Bc[c][1][u]);
+        cam_block_solve<T>(iD, Bc[c], tw[c], hx[k], Mk[k]);
+      }
+      cam_block_solve<T>(iD, Bc[c], tw[c], gc[c], m);
+      T p00 = 0, p01 = 0, p02 = 0, p11 = 0, p12 = 0, p22 = 0, q0 = 0, q1 = 0, q2 = 0;
+#pragma unroll
+      for (int u = 0; u < 6; ++u) {
+        p00 += hx[0][u] * Mk[0][u];
+        p01 += hx[0][u] * Mk[1][u];
+        p02 += hx[0][u] * Mk[2][u];
+        p11 += hx[1][u] * Mk[1][u];
+        p12 += hx[1][u] * Mk[2][u];
+        p22 += hx[2][u] * Mk[2][u];
+        q0 += hx[0][u] * m[u];
+        q1 += hx[1][u] * m[u];
+        q2 += hx[2][u] * m[u];
+      }
+      S[0] -= p00, S[1] -= p01, S[2] -= p02, S[3] -= p11, S[4] -= p12, S[5] -= p22;
+      r[0] += q0, r[1] += q1, r[2] += q2;
+    }
+    // the point step by cofactors (S symmetric positive definite when H is)
+    const T c00 = S[3] * S[5] - S[4] * S[4], c01 = S[2] * S[4] - S[1] * S[5], c02 = S[1] * S[4] - S[2] * S[3];
+    const T c11 = S[0] * S[5] - S[2] * S[2], c12 = S[1] * S[2] - S[0] * S[4], c22 = S[0] * S[3] - S[1] * S[1];
+    const T det = S[0] * c00 + S[1] * c01 + S[2] * c02;
+    if (!(det > T(0)) || !(S[0] > T(0)) || !(c22 > T(0))) {
+      lambda *= T(10);
+      continue;
+    }
+    const T idet = Num<T>::rcp(det);
+    T dx[3];
+    dx[0] = (c00 * r[0] + c01 * r[1] + c02 * r[2]) * idet;
+    dx[1] = (c01 * r[0] + c11 * r[1] + c12 * r[2]) * idet;
+    dx[2] = (c02 * r[0] + c12 * r[1] + c22 * r[2]) * idet;
+    // camera steps dy_c = -H_cc^-1 (g_c + H_cx dx); predicted decrease (lambda |d|^2 - g.d) / 2
+    T gd = gx[0] * dx[0] + gx[1] * dx[1] + gx[2] * dx[2], dd = dx[0] * dx[0] + dx[1] * dx[1] + dx[2] * dx[2];
+    T xt[3], ct[KC][6];
+#pragma unroll
+    for (int u = 0; u < 3; ++u) xt[u] = dp[u] + dx[u];
+#pragma unroll
+    for (int c = 0; c < KC; ++c) {
+      T v[6], y[6];
+#pragma unroll
+      for (int u = 0; u < 6; ++u) {
+        const T a0 = Ap[c][0][0] * dx[0] + Ap[c][0][1] * dx[1] + Ap[c][0][2] * dx[2];
+        const T a1 = Ap[c][1][0] * dx[0] + Ap[c][1][1] * dx[1] + Ap[c][1][2] * dx[2];
+        v[u] = gc[c][u] + tw[c] * (Bc[c][0][u] * a0 + Bc[c][1][u] * a1);
+      }
+      cam_block_solve<T>(iD, Bc[c], tw[c], v, y);
+#pragma unroll
+      for (int u = 0; u < 6; ++u) {
+        const T dy = has[c] ? -y[u] : T(0);
+        gd += gc[c][u] * dy;
+        dd += dy * dy;
+        ct[c][u] = cd[c][u] + dy;
+      }
+    }
+    const T pred = T(0.5) * (lambda * dd - gd);
+    const bool trust = isfinite(L) && q.model_tol > T(0) &&
+                       pred <= q.model_tol * Num<T>::unit_roundoff * (fabs(L) + noise);
+    const T Lt = objective(xt, ct);
+    if (Lt < Num<T>::inf() && (trust || Lt < L)) {
+#pragma unroll
+      for (int u = 0; u < 3; ++u) dp[u] = xt[u];
+#pragma unroll
+      for (int c = 0; c < KC; ++c)
+#pragma unroll
+        for (int u = 0; u < 6; ++u) cd[c][u] = ct[c][u];
+      L = Lt;  // Eq. (14) at the accepted point, trusted step or not
+      const T lr = Num<T>::tenth(lambda);
+      lambda = lr > q.lambda_min ? lr : q.lambda_min;
+    } else {
+      lambda *= T(10);
+    }
+  }
+  bool finite = true;
+#pragma unroll
+  for (int u = 0; u < 3; ++u) {
+    pdel[u * B.n_pc + pc] = dp[u];
+    finite = finite && isfinite(dp[u]);
+  }
+#pragma unroll
+  for (int c = 0; c < KC; ++c)
+    if (has[c])
+#pragma unroll
+      for (int u = 0; u < 6; ++u) {
+        cdel[u * B.n_cc + bi.c0 + c] = cd[c][u];
+        finite = finite && isfinite(cd[c][u]);
+      }
+  if (!finite) atomicOr(B.err, 1);
+}
+
+// One-point blocks [lo, hi), one thread per block.
+template <typename T>
+__global__ void __launch_bounds__(kBlkWarps * 32, (sizeof(T) == 4 ? 2 : 1))
+    block_solve_point_kernel(BlockProblem B, Prm<T> q, int cur, int lo, int hi) {
+  for (long long b = lo + blockIdx.x * (long long)blockDim.x + threadIdx.x; b < hi;
+       b += (long long)gridDim.x * blockDim.x)
+    solve_block_point<T>(B, q, B.blocks[b]);
+}
+
 // ------------------------------------------------------------ blocks of two or four cameras
 // A block with at most KC cameras (KC = 2 or 4) and at most G <= 32 points has a reduced camera
 // system of at most 6 KC x 6 KC.  Each lane keeps its point copy's linearisation in registers
@@ -1960,6 +2258,30 @@ cudaError_t launch_block_class_2cam(dba_block_ctx* ctx, int lo, int hi) {
   return cudaGetLastError();
 }
 
+// One-point blocks [lo, hi): one thread per block, cameras eliminated.
+template <typename T>
+cudaError_t launch_block_class_point(dba_block_ctx* ctx, int lo, int hi) {
+  if (hi <= lo) return cudaSuccess;
+  constexpr int kThreads = dba::kBlkWarps * 32;
+  static std::atomic<int> cached{0};  // CTAs of a full wave
+  int grid = cached.load();
+  if (!grid) {
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dba::block_solve_point_kernel<T>,
+                                                                  kThreads, 0);
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    grid = std::max(per_sm, 1) * sms;
+    cached.store(grid);
+  }
+  const int need = dba::blocks_of(hi - lo, kThreads);
+  const int g = std::max(1, std::min(need, grid));
+  dba::block_solve_point_kernel<T><<<g, kThreads, 0, ctx->stream>>>(ctx->B, dba::make_prm<T>(ctx->prm), ctx->cur,
+                                                                     lo, hi);
+  return cudaGetLastError();
+}
+
 template <typename T, int G, int PPL>
 cudaError_t launch_block_class_kc(dba_block_ctx* ctx, int k) {
   const int lo = ctx->cls[k], hi = ctx->cls[k + 1];
@@ -1970,14 +2292,18 @@ cudaError_t launch_block_class_kc(dba_block_ctx* ctx, int k) {
   if constexpr (PPL == 1) {
     // the 16-lane class holds at most 2 cameras (its blocks of at most 8 points in groups of
     // 8 lanes), the 32-lane one at most block_cams
+    // blocks of one point (the first of each class) eliminate their cameras instead
+    const int m1 = ctx->small[k][0];
+    cudaError_t e = launch_block_class_point<T>(ctx, lo, m1);
+    if (e != cudaSuccess) return e;
     if constexpr (G == 16) {
       const int m4 = ctx->small[k][2], m8 = ctx->small[k][3];
-      cudaError_t e = launch_block_class_2cam<T, 4>(ctx, lo, m4);
+      e = launch_block_class_2cam<T, 4>(ctx, m1, m4);
       if (e == cudaSuccess) e = launch_block_class_2cam<T, 8>(ctx, m4, m8);
       return e == cudaSuccess ? launch_block_class_2cam<T, 16>(ctx, m8, hi) : e;
     } else {
-      if (ctx->kappa == 2) return launch_block_class_2cam<T, G>(ctx, lo, hi);
-      return launch_block_class_2cam<T, G, 4>(ctx, lo, hi);
+      if (ctx->kappa == 2) return launch_block_class_2cam<T, G>(ctx, m1, hi);
+      return launch_block_class_2cam<T, G, 4>(ctx, m1, hi);
     }
   } else {
     if (ctx->kappa == 2) return launch_block_class<T, 2, G, PPL>(ctx, lo, hi);
@@ -2016,12 +2342,15 @@ int block_solve_launches(const dba_block_ctx* ctx) {
   r.push_back({c0[2], ctx->cls[1]});
   if (ctx->kappa == 1) {
     r.push_back({ctx->cls[1], ctx->cls[2]});
+    r.push_back({ctx->cls[2], ctx->cls[3]});
   } else {
-    r.push_back({ctx->cls[1], ctx->small[1][2]});
+    r.push_back({ctx->cls[1], ctx->small[1][0]});  // one point
+    r.push_back({ctx->small[1][0], ctx->small[1][2]});
     r.push_back({ctx->small[1][2], ctx->small[1][3]});
     r.push_back({ctx->small[1][3], ctx->cls[2]});
+    r.push_back({ctx->cls[2], ctx->small[2][0]});  // one point
+    r.push_back({ctx->small[2][0], ctx->cls[3]});
   }
-  r.push_back({ctx->cls[2], ctx->cls[3]});
   r.push_back({ctx->cls[3], ctx->cls[4]});
   int n = 0;
   for (const auto& x : r) n += x.second > x.first;
@@ -2181,25 +2510,33 @@ std::string build_block_layout(int n_cams, int n_pts, long long l, const int32_t
   //   per observation: pose 44, Jacobian and residual 64, point block and gradient terms 43,
   //     noise bound 7, its 2w A W g term 14, gradient and right-hand side entries 48,
   //     back-substitution 30, trial pose and misfit 64                        -> 314
-  //   per camera pair of a point's observations (Schur weight 60 + 8 per entry of the
-  //     reduced system): 228 when both are one observation (21 entries), 348 otherwise
   //   per point copy: penalty gradient 6, 3x3 inverse 35, W g 15, step 15, model terms 12,
   //     trial penalty 9                                                      -> 92
-  //   per block: Cholesky n^3/3 + n^2/2, triangular solves 2 n^2, damping and camera
-  //     model/penalty terms 10 n (n = 6 cameras)
+  //   blocks whose points are eliminated:
+  //     per camera pair of a point's observations (Schur weight 60 + 8 per entry of the
+  //       reduced system): 228 when both are one observation (21 entries), 348 otherwise;
+  //     per block: Cholesky n^3/3 + n^2/2, triangular solves 2 n^2, damping and camera
+  //       model/penalty terms 10 n (n = 6 cameras)
+  //   blocks of one point and several cameras (cameras eliminated): per camera five
+  //     capacitance solves of 140, its H_xc rows 72, the 3 x 3 Schur update 108, the
+  //     back-substitution terms 66 -> 946; per block the 3 x 3 solve and damping 60
   //   start of a solve: pose and misfit 64 per observation, penalty 9 per point copy and
   //     per camera copy 24
   {
-    double pairs_off = 0.0, per_block = 0.0;
-    for (long long k = 0; k < n_pc; ++k) {
-      const double c = (double)(pc_obs[k + 1] - pc_obs[k]);
-      pairs_off += c * (c - 1.0) / 2.0;
-    }
+    double schur = 0.0, per_block = 0.0;
     for (const dba::BlockInfo& bi : blocks) {
+      if (bi.np == 1 && bi.nc >= 2) {
+        per_block += 946.0 * bi.nc + 60.0;
+        continue;
+      }
+      for (int k = bi.p0; k < bi.p0 + bi.np; ++k) {
+        const double c = (double)(pc_obs[k + 1] - pc_obs[k]);
+        schur += 228.0 * c + 348.0 * c * (c - 1.0) / 2.0;
+      }
       const double nu = 6.0 * bi.nc;
       per_block += nu * nu * nu / 3.0 + nu * nu / 2.0 + 2.0 * nu * nu + 10.0 * nu;
     }
-    H.flops_step = 314.0 * (double)l + 228.0 * (double)l + 348.0 * pairs_off + 92.0 * (double)n_pc + per_block;
+    H.flops_step = 314.0 * (double)l + 92.0 * (double)n_pc + schur + per_block;
     H.flops_start = 64.0 * (double)l + 9.0 * (double)n_pc + 24.0 * (double)n_cc;
   }
   // size classes of the solve kernel (lane groups of 8, 16, 32, 32 with two copies per

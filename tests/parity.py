@@ -18,6 +18,7 @@ def colerr(a, b):
 # Block sizes (points, cameras) of the block parity test.  Together they put blocks in every
 # kernel variant of the block solve: one-camera blocks in groups of 1, 2, 4, 8, 16 and 32
 # lanes; two-camera blocks in groups of 4, 8, 16 and 32 lanes; blocks of up to 4 cameras in
-# 32 lanes (the register solve with four camera slots) and above 32 points (two point copies
-# a lane, the shared-memory kernel).
-BLOCK_SETTINGS = [(1, 1), (8, 2), (32, 4), (5, 3), (32, 1), (32, 2), (64, 1), (48, 2), (64, 4)]
+# 32 lanes (the register solve with four camera slots); one-point blocks of two to four
+# cameras (cameras eliminated, a thread per block); above 32 points (two point copies a lane,
+# the shared-memory kernel).
+BLOCK_SETTINGS = [(1, 1), (8, 2), (32, 4), (5, 3), (32, 1), (32, 2), (64, 1), (48, 2), (64, 4), (1, 4)]

@@ -7,7 +7,8 @@ cameras and 16 points in a group of 4, 8 or 16 lanes (two cameras: the register
 reduce-scatter solve; one camera when every block has one: the one-camera solve); at most
 32 points in 32 lanes (the two-camera solve when block_cams = 2, the same register solve
 with four camera slots when block_cams >= 3); above that two point copies a lane, in the
-shared-memory solve.  This recounts, from the
+shared-memory solve.  Blocks of one point and two to four cameras eliminate their cameras
+instead, a thread per block.  This recounts, from the
 oracle's block layout of the parity test's scene, which variants its settings reach."""
 import numpy as np
 
@@ -22,6 +23,8 @@ def variant(n_pts, n_cams, kappa):
         width *= 2
     if n_cams == 1 and n_pts <= 8:
         return ("one camera", width)
+    if n_pts == 1:
+        return ("one point", 1)
     if n_cams <= 2 and n_pts <= 16:
         return ("one camera" if kappa == 1 else "two cameras", max(width, 4 if kappa > 1 else 16))
     if n_pts <= 32:
@@ -38,7 +41,7 @@ def test_block_parity_settings_reach_every_kernel_variant():
             seen.add(variant(int(n_p), int(n_c), kappa))
     want = {("one camera", w) for w in (1, 2, 4, 8, 16, 32)}
     want |= {("two cameras", w) for w in (4, 8, 16, 32)}
-    want |= {("four cameras", 32), ("shared memory, two copies a lane", 32)}
+    want |= {("four cameras", 32), ("shared memory, two copies a lane", 32), ("one point", 1)}
     assert want <= seen, sorted(want - seen)
 
 

@@ -214,10 +214,11 @@ def expected_launches(layout, kappa):
     c3 = ~c0 & ~c1 & ~c2
     ranges = [c0 & (npb == 1), c0 & (npb == 2), c0 & (npb > 2) & (npb <= 4), c0 & (npb > 4)]
     if kappa == 1:
-        ranges.append(c1)
+        ranges += [c1, c2]
     else:
-        ranges += [c1 & (npb <= 4), c1 & (npb > 4) & (npb <= 8), c1 & (npb > 8)]
-    ranges += [c2, c3]
+        ranges += [c1 & (npb == 1), c1 & (npb > 1) & (npb <= 4), c1 & (npb > 4) & (npb <= 8), c1 & (npb > 8),
+                   c2 & (npb == 1), c2 & (npb > 1)]
+    ranges += [c3]
     return sum(1 for r in ranges if r.any()) + 2
 
 
