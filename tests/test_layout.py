@@ -112,11 +112,17 @@ def test_block_layout_matches_the_oracle(pi, kappa):
     assert np.array_equal(b[:, 2], ref.pc_off[:-1]) and np.array_equal(b[:, 3], np.diff(ref.pc_off))
     assert np.array_equal(b[:, 4], ref.cc_off[:-1]) and np.array_equal(b[:, 5], np.diff(ref.cc_off))
     assert np.array_equal(L["pc_point"], ref.pc_pt) and np.array_equal(L["cc_camera"], ref.cc_cam)
-    # launch order: size classes one after another (8, 16, 32 lanes; 32 lanes x 2 copies)
+    # launch order: size classes one after another (8, 16, 32 lanes; 32 lanes x 2 copies),
+    # each ordered by point count (the kernels take its small blocks in narrower lane
+    # groups), equal counts in layout order
     npb, ncb = L["blocks"][:, 3], L["blocks"][:, 5]
     cls = np.where((ncb == 1) & (npb <= 8), 0, np.where((ncb <= 2) & (npb <= 16), 1, np.where(npb <= 32, 2, 3)))
     assert np.all(np.diff(cls) >= 0)
     assert np.array_equal(L["size_classes"], np.bincount(cls, minlength=4))
+    key = cls.astype(np.int64) * 1000 + npb
+    assert np.all(np.diff(key) >= 0)
+    same = np.diff(key) == 0
+    assert np.all(np.diff(L["blocks"][:, 0])[same] > 0)
 
 
 def test_block_layout_rejects_a_repeated_pair():
