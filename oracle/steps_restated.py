@@ -1,8 +1,10 @@
-"""Second, independent statement of the two local solvers of Eq. (9), step by step.
+"""Second, independent statement of the two local solvers of Eq. (9) and of the block
+solve of Eq. (14), step by step.
 
-TEST INFRASTRUCTURE ONLY: used by ``tests/golden/make_local_steps.py`` to write the
-step-wise golden vectors that pin ``ora_local_solve`` and ``ora_local_solve_lbfgs``
-over a fixed number of steps.  It shares no code with ``dba_oracle.c`` and reaches
+TEST INFRASTRUCTURE ONLY: used by ``tests/golden/make_local_steps.py`` and
+``tests/golden/make_block_steps.py`` to write the step-wise golden vectors that pin
+``ora_local_solve``, ``ora_local_solve_lbfgs`` and ``ora_block_solve`` over a fixed
+number of steps.  It shares no code with ``dba_oracle.c`` and reaches
 each quantity by another route:
 
 - rotation (Sec. 2.1): built here as R3(gamma) R2(beta) R1(alpha) from the textbook
@@ -14,7 +16,10 @@ each quantity by another route:
 - L-BFGS (Nocedal and Wright, Numerical Optimization, Ch. 7): the inverse-Hessian
   approximation formed as a dense matrix by the BFGS product update
   H <- (I - rho s y^T) H (I - rho y s^T) + rho s s^T over the stored pairs, instead of
-  the two-loop recursion.
+  the two-loop recursion;
+- the block system of Eq. (14): the stacked Jacobian of all the block's pixels by complex
+  steps of the whole block vector and dense products with the weights, instead of the
+  oracle's per-observation 9 x 9 scatter into the block system.
 
 The rules restated (the readings the oracle documents): Levenberg damping
 lambda_0 = lm_lambda0 * mean diag H at the first step, divided by 10 after an accepted
@@ -232,3 +237,111 @@ def lbfgs(cfg, c, v0, iters, memory=4, halvings=10, armijo=1e-4):
         traj.append(v.copy())
         trials.append(str(n_trials))
     return traj, trials, margins
+
+
+# ---------------------------------------------------------------------------------------
+# The block subproblem of Eq. (14) (Sec. 3.1.4), step by step.
+#
+# A block holds np point copies X and nc camera copies Y; its parameter vector is
+# v = (X_1 .. X_np, Y_1 .. Y_nc) of length n = 3 np + 6 nc.  The second statement reaches
+# the damped Gauss-Newton system by another route than the oracle's per-observation
+# scatter: the stacked pixel residual of all the block's observations is differentiated
+# column by column with complex steps of the WHOLE vector v (an observation that does not
+# depend on a column gets an exactly zero derivative), H and g are dense products of that
+# stacked Jacobian with the IRLS weights, and (H + lambda I) d = -g is solved by numpy LU.
+# The rules are those of the local solve above, over the block: lambda_0 = lm_lambda0 *
+# mean diag H over all n unknowns, the noise bound summed over the observations in front
+# of their cameras, and Eq. (14) +inf when any observation of a trial is behind its camera.
+# ---------------------------------------------------------------------------------------
+
+
+def _block_unpack(blk, v):
+    np_ = len(blk["xbar"]) // 3
+    return v[:3 * np_].reshape(np_, 3), v[3 * np_:].reshape(-1, 6)
+
+
+def block_pixels(cfg, blk, v):
+    """Predicted pixels [no, 2] and depths [no] of the block's observations at v."""
+    X, Y = _block_unpack(blk, v)
+    zs, ds = [], []
+    for lp, lc in zip(blk["opl"], blk["ocl"]):
+        zp, depth = pixel(cfg, np.concatenate([X[lp], Y[lc]]))
+        zs.append(zp)
+        ds.append(depth)
+    return np.array(zs), np.array(ds)
+
+
+def block_rho(cfg, blk):
+    """The penalty of every unknown of v: rho_x for point coordinates, the camera penalty
+    (angles, translation) for camera components."""
+    np_, nc = len(blk["xbar"]) // 3, len(blk["ybar"]) // 6
+    r = rho_vec(cfg)
+    return np.concatenate([np.tile(r[:3], np_), np.tile(r[3:], nc)])
+
+
+def block_objective(cfg, blk, v):
+    """Eq. (14) at v: the misfits of the block's observations plus, per copy, dual^T (copy -
+    consensus) + rho/2 |copy - consensus|^2; +inf when any observation is behind its camera."""
+    zp, depth = block_pixels(cfg, blk, v)
+    if not np.all(np.real(depth) > cfg["eps_depth"]):
+        return np.inf
+    e = np.asarray(blk["z"]).reshape(-1, 2) - zp
+    vbar = np.concatenate([blk["xbar"], blk["ybar"]])
+    dual = np.concatenate([blk["rx"], blk["sy"]])
+    dv = v - vbar
+    return sum(misfit(cfg, ek @ ek) for ek in e) + dual @ dv + 0.5 * (block_rho(cfg, blk) * dv) @ dv
+
+
+def block_jacobian_cs(cfg, blk, v):
+    """d (stacked predicted pixels) / d v, [2 no, n], by complex steps of the whole vector."""
+    n = len(v)
+    J = np.zeros((2 * len(blk["opl"]), n))
+    for k in range(n):
+        vc = v.astype(complex)
+        vc[k] += 1j * H_CS
+        J[:, k] = np.imag(block_pixels(cfg, blk, vc)[0]).ravel() / H_CS
+    return J
+
+
+def block_gauss_newton(cfg, blk, v0, steps):
+    """The damped Gauss-Newton (Levenberg) solve of Eq. (14); returns the iterates, the step
+    codes ('A', 'T', 'R' as in gauss_newton) and the margins of every decision."""
+    rho = block_rho(cfg, blk)
+    vbar = np.concatenate([blk["xbar"], blk["ybar"]])
+    dual = np.concatenate([blk["rx"], blk["sy"]])
+    z = np.asarray(blk["z"], float).reshape(-1, 2)
+    n = len(vbar)
+    v = np.array(v0, float)
+    L = block_objective(cfg, blk, v)
+    lam = None
+    traj, codes, margins = [v.copy()], [], []
+    for _ in range(steps):
+        zp, depth = block_pixels(cfg, blk, v)
+        front = depth > cfg["eps_depth"]  # a linearisation point behind its camera adds no misfit term
+        e = np.where(front[:, None], z - zp, 0.0)
+        s = np.sum(e * e, axis=1)
+        w = np.array([weight(cfg, sk) if f else 0.0 for sk, f in zip(s, front)])
+        J = block_jacobian_cs(cfg, blk, v)
+        w2 = np.repeat(2.0 * w, 2)
+        g = -J.T @ (w2 * e.ravel()) + dual + rho * (v - vbar)
+        H = J.T @ (w2[:, None] * J) + np.diag(rho)
+        if lam is None:
+            lam = cfg["lm_lambda0"] * np.trace(H) / n
+        d = np.linalg.solve(H + lam * np.eye(n), -g)
+        pred = 0.5 * (lam * d @ d - g @ d)
+        noise = cfg["lm_model_tol"] * U64 * (abs(L) + np.sum(2 * w * np.sqrt(s) * np.abs(z).sum(axis=1)))
+        trust = np.isfinite(L) and cfg["lm_model_tol"] > 0 and pred <= noise
+        Lt = block_objective(cfg, blk, v + d)
+        ok = np.isfinite(Lt) and (trust or Lt < L)
+        margins.append({"pred_over_noise": float(pred / noise) if noise > 0 else np.inf,
+                        "rel_change": float((Lt - L) / abs(L)) if np.isfinite(Lt) and np.isfinite(L) else np.inf})
+        if ok:
+            v = v + d
+            L = Lt
+            lam = max(lam / 10.0, cfg["lm_lambda_min"])
+            codes.append("T" if trust else "A")
+        else:
+            lam = lam * 10.0
+            codes.append("R")
+        traj.append(v.copy())
+    return traj, "".join(codes), margins
