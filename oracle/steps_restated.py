@@ -345,3 +345,49 @@ def block_gauss_newton(cfg, blk, v0, steps):
             codes.append("R")
         traj.append(v.copy())
     return traj, "".join(codes), margins
+
+
+# ---------------------------------------------------------------------------------------
+# One consensus ADMM iteration (Sec. 3.1, Eqs. 9-13) over all observations.
+#
+# The local solves are gauss_newton above, one per observation, each warm-started at its
+# copy with the consensus and dual of the previous iteration.  The consensus of a point
+# (likewise a camera) is reached as the minimiser of its part of the augmented Lagrangian,
+#   sum_j  r_ij^T (x_ij - x) + rho/2 |x_ij - x|^2,
+# by a least-squares solve over the stacked rows sqrt(rho) (x - (x_ij + r_ij / rho)) of all
+# its copies, not by averaging; an unobserved point or camera keeps its value.  The duals
+# then ascend by rho (copy - new consensus).
+# ---------------------------------------------------------------------------------------
+
+
+def _consensus(idx, count, values, weights, old):
+    out = np.array(old, float)
+    for i in range(count):
+        rows = np.flatnonzero(idx == i)
+        if len(rows) == 0:
+            continue
+        k = values.shape[1]
+        A = np.kron(np.ones((len(rows), 1)), np.diag(np.sqrt(weights)))
+        b = (values[rows] * np.sqrt(weights)).ravel()
+        out[i] = np.linalg.lstsq(A, b, rcond=None)[0].reshape(k)
+    return out
+
+
+def admm_iteration(cfg, pt_idx, cam_idx, z, copies, duals, cams, pts, steps):
+    """One iteration; returns the new (copies, duals, cams, pts) and the codes of every local
+    solve with their margins (for the golden writer's cleanliness check)."""
+    rho = rho_vec(cfg)
+    copies, duals = np.array(copies, float), np.array(duals, float)
+    codes, margins = [], []
+    for o in range(len(pt_idx)):
+        c = {"z": np.asarray(z[o], float), "vbar": np.r_[pts[pt_idx[o]], cams[cam_idx[o]]], "dual": duals[o]}
+        traj, code, marg = gauss_newton(cfg, c, copies[o], steps)
+        copies[o] = traj[-1]
+        codes.append(code)
+        margins.append(marg)
+    target = copies + duals / rho
+    pts_new = _consensus(np.asarray(pt_idx), len(pts), target[:, :3], rho[:3], pts)
+    cams_new = _consensus(np.asarray(cam_idx), len(cams), target[:, 3:], rho[3:], cams)
+    consensus = np.concatenate([pts_new[pt_idx], cams_new[cam_idx]], axis=1)
+    duals = duals + rho * (copies - consensus)
+    return copies, duals, cams_new, pts_new, codes, margins
