@@ -391,3 +391,37 @@ def admm_iteration(cfg, pt_idx, cam_idx, z, copies, duals, cams, pts, steps):
     consensus = np.concatenate([pts_new[pt_idx], cams_new[cam_idx]], axis=1)
     duals = duals + rho * (copies - consensus)
     return copies, duals, cams_new, pts_new, codes, margins
+
+
+def block_admm_iteration(cfg, layout, z, pcopies, pduals, ccopies, cduals, cams, pts, steps):
+    """One consensus ADMM iteration with block subproblems (Sec. 3.1.4, Eq. 14): every block
+    solved by block_gauss_newton from its copies, each point's (camera's) consensus the
+    least-squares minimiser over its copies, one per block that holds it, then the duals of
+    every copy ascend by rho (copy - new consensus).  layout carries the block arrays
+    (obs_off, blk_obs, obs_lp, obs_lc, pc_off, pc_pt, cc_off, cc_cam); returns the new
+    (pcopies, pduals, ccopies, cduals, cams, pts) and every block's step codes."""
+    rho = rho_vec(cfg)
+    pcopies, pduals = np.array(pcopies, float), np.array(pduals, float)
+    ccopies, cduals = np.array(ccopies, float), np.array(cduals, float)
+    z = np.asarray(z, float)
+    codes = []
+    for b in range(len(layout["obs_off"]) - 1):
+        o0, o1 = layout["obs_off"][b], layout["obs_off"][b + 1]
+        p0, p1 = layout["pc_off"][b], layout["pc_off"][b + 1]
+        c0, c1 = layout["cc_off"][b], layout["cc_off"][b + 1]
+        blk = {"opl": list(layout["obs_lp"][o0:o1]), "ocl": list(layout["obs_lc"][o0:o1]),
+               "z": z[np.asarray(layout["blk_obs"][o0:o1])].ravel(),
+               "xbar": pts[np.asarray(layout["pc_pt"][p0:p1])].ravel(),
+               "ybar": cams[np.asarray(layout["cc_cam"][c0:c1])].ravel(),
+               "rx": pduals[p0:p1].ravel(), "sy": cduals[c0:c1].ravel()}
+        v0 = np.concatenate([pcopies[p0:p1].ravel(), ccopies[c0:c1].ravel()])
+        traj, code, _ = block_gauss_newton(cfg, blk, v0, steps)
+        pcopies[p0:p1] = traj[-1][:3 * (p1 - p0)].reshape(-1, 3)
+        ccopies[c0:c1] = traj[-1][3 * (p1 - p0):].reshape(-1, 6)
+        codes.append(code)
+    pc_pt, cc_cam = np.asarray(layout["pc_pt"]), np.asarray(layout["cc_cam"])
+    pts_new = _consensus(pc_pt, len(pts), pcopies + pduals / rho[:3], rho[:3], pts)
+    cams_new = _consensus(cc_cam, len(cams), ccopies + cduals / rho[3:], rho[3:], cams)
+    pduals = pduals + rho[:3] * (pcopies - pts_new[pc_pt])
+    cduals = cduals + rho[3:] * (ccopies - cams_new[cc_cam])
+    return pcopies, pduals, ccopies, cduals, cams_new, pts_new, codes

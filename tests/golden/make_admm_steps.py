@@ -1,15 +1,18 @@
 """Writes tests/golden/admm_steps.json: golden iterates of the consensus ADMM iteration
-(Sec. 3.1, Eqs. 9-13) over whole small scenes, for the tests that pin the oracle's
-ora_admm_iterate iteration by iteration.
+(Sec. 3.1, Eqs. 9-13) over whole small scenes, per observation and with block subproblems
+(Sec. 3.1.4, Eq. 14), for the tests that pin the oracle's ora_admm_iterate and
+ora_block_iterate iteration by iteration.
 
-The values come from oracle/steps_restated.py (admm_iteration): the restated local
-Gauss-Newton solve per observation, the consensus as the least-squares minimiser of each
+The values come from oracle/steps_restated.py (admm_iteration, block_admm_iteration): the
+restated local Gauss-Newton solve per observation or block, the consensus as the least-squares minimiser of each
 point's and camera's part of the augmented Lagrangian, and the dual ascent; it shares no
 code with the C oracle.  The scenes are small versions of the synthetic geometries of
 paper_1708_07954_gb300.scenes with their own penalties, one of them with a point penalty
 different from the camera penalty, the paper's single camera penalty (rho_angle 0), and an
 unobserved point and camera appended.  Every case stores the consensus after each iteration
-and the copies and duals after the first and the last.
+and the copies and duals after the last.  Block cases take the oracle's block
+layout (oracle.BlockLayout, pinned against brute-force grouping) and cover one-point,
+one-camera and two-camera blocks.
 
     python tests/golden/make_admm_steps.py      # rewrites admm_steps.json
 """
@@ -26,6 +29,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(os.path.dirname(HERE))
 sys.path.insert(0, ROOT)
 
+import oracle as O  # noqa: E402
 from oracle import steps_restated as R  # noqa: E402
 from paper_1708_07954_gb300 import scenes as S  # noqa: E402
 
@@ -56,9 +60,39 @@ def case(name, sc, loss, loss_param, rho_x, rho_y, rho_angle, steps, iters):
                                                               cams, pts, steps)
         out["cams"].append(cams.tolist())
         out["pts"].append(pts.tolist())
-        if it in (1, iters):
+        if it == iters:
             out["copies"][str(it)] = copies.tolist()
             out["duals"][str(it)] = duals.tolist()
+        out.setdefault("codes", []).append("".join(codes))
+    return out
+
+
+def block_case(name, sc, pi, kappa, loss, loss_param, rho_x, rho_y, rho_angle, steps, iters):
+    """The same with block subproblems of pi points and kappa cameras (Sec. 3.1.4, Eq. 14);
+    the block layout is the oracle's (pinned against brute-force grouping)."""
+    cfg = {"focal": sc.focal, "cx": sc.cx, "cy": sc.cy, "loss": loss, "loss_param": loss_param,
+           "rho_x": rho_x, "rho_y": rho_y, "rho_angle": rho_angle, "lm_lambda0": 1e-3,
+           "lm_lambda_min": 1e-12, "eps_depth": 1e-6, "lm_model_tol": 16.0}
+    B = O.BlockLayout(sc, pi, kappa)
+    layout = {k: getattr(B, k).tolist() for k in ("obs_off", "blk_obs", "obs_lp", "obs_lc", "pc_off", "pc_pt",
+                                                   "cc_off", "cc_cam")}
+    cams, pts = sc.cams0.astype(float).copy(), sc.pts0.astype(float).copy()
+    pcopies, ccopies = pts[B.pc_pt].copy(), cams[B.cc_cam].copy()
+    pduals, cduals = np.zeros_like(pcopies), np.zeros_like(ccopies)
+    out = {"name": name, "cfg": cfg, "steps": steps, "pi": pi, "kappa": kappa, "n_pts": sc.n_pts,
+           "n_cams": sc.n_cams, "pt_idx": sc.pt_idx.tolist(), "cam_idx": sc.cam_idx.tolist(), "z": sc.z.tolist(),
+           "cams0": cams.tolist(), "pts0": pts.tolist(), "cams": [], "pts": [], "copies": {}, "duals": {}}
+    shapes = sorted({(int(B.pc_off[b + 1] - B.pc_off[b]), int(B.cc_off[b + 1] - B.cc_off[b]))
+                     for b in range(B.n_blocks)})
+    out["block_shapes"] = [list(t) for t in shapes]
+    for it in range(1, iters + 1):
+        pcopies, pduals, ccopies, cduals, cams, pts, codes = R.block_admm_iteration(
+            cfg, layout, sc.z, pcopies, pduals, ccopies, cduals, cams, pts, steps)
+        out["cams"].append(cams.tolist())
+        out["pts"].append(pts.tolist())
+        if it == iters:
+            out["copies"][str(it)] = {"points": pcopies.tolist(), "cameras": ccopies.tolist()}
+            out["duals"][str(it)] = {"points": pduals.tolist(), "cameras": cduals.tolist()}
         out.setdefault("codes", []).append("".join(codes))
     return out
 
@@ -77,9 +111,22 @@ def main():
              ring64.rho_x, 2.0 * ring64.rho_y, ring64.rho_angle, 5, 3),
         case("grid-huber-single_rho_y", grid, S.LOSS_HUBER, 2.0, grid.rho_x, grid.rho_y, 0.0, 3, 3),
     ]
+    block_cases = [
+        block_case("ring8-4x2-huber-rho_angle", ring, 4, 2, S.LOSS_HUBER, 2.0, ring.rho_x, ring.rho_y,
+                   ring.rho_angle, 5, 3),
+        block_case("ring64-1x3-student-single_rho_y-rho_x_half", ring64, 1, 3, S.LOSS_STUDENT_T, 4.0,
+                   0.5 * ring64.rho_x, ring64.rho_y, 0.0, 5, 3),
+        block_case("grid-5x1-l2-rho_angle-unobserved", with_unobserved(grid), 5, 1, S.LOSS_L2, 0.0, grid.rho_x,
+                   grid.rho_y, grid.rho_angle, 5, 3),
+        block_case("grid-3x2-huber-single_rho_y", grid, 3, 2, S.LOSS_HUBER, 2.0, grid.rho_x, 2.0 * grid.rho_y,
+                   0.0, 4, 3),
+    ]
     with open(OUT, "w") as fh:
-        json.dump({"about": "consensus ADMM iterates (Eqs. 9-13); written by make_admm_steps.py from "
-                            "oracle/steps_restated.py", "cases": cases}, fh, indent=0)
+        json.dump({"about": "consensus ADMM iterates (Eqs. 9-13, Eq. 14 for blocks); written by "
+                            "make_admm_steps.py from oracle/steps_restated.py",
+                   "cases": cases, "block_cases": block_cases}, fh, separators=(",", ":"))
+    for k in block_cases:
+        print(f"{k['name']:40s} shapes={k['block_shapes']} codes={k['codes'][-1][:30]}")
     for k in cases:
         print(f"{k['name']:40s} obs={len(k['pt_idx']):3d} iters={len(k['cams'])} codes={k['codes'][-1][:30]}")
 

@@ -1,11 +1,15 @@
-"""Iteration-wise pins of the oracle's consensus ADMM iteration (Sec. 3.1, Eqs. 9-13).
+"""Iteration-wise pins of the oracle's consensus ADMM iteration (Sec. 3.1, Eqs. 9-13), per
+observation (ora_admm_iterate) and with block subproblems (Sec. 3.1.4, Eq. 14;
+ora_block_iterate).
 
 tests/golden/admm_steps.json holds iterates written by tests/golden/make_admm_steps.py from
 oracle/steps_restated.py, a second statement of the iteration that shares no code with
 oracle/dba_oracle.c: its local solves are the restated Gauss-Newton solve, its consensus is
 the least-squares minimiser of each point's and camera's part of the augmented Lagrangian,
-and its duals ascend by rho (copy - new consensus).  ora_admm_iterate is replayed over every
-case and compared after each iteration.
+and its duals ascend by rho (copy - new consensus).  The block cases solve each block by the
+restated block solve over the oracle's block layout (pinned against brute-force grouping)
+and take each consensus over the copies, one per block that holds the point or camera.
+Both oracle iterations are replayed over every case and compared after each iteration.
 
 The invariants pinned elsewhere (duals summing to zero per point and camera, the noise-free
 fixed point, the centralized optimum at convergence) hold for any positive dual step, so a
@@ -88,7 +92,7 @@ def test_golden_cases_cover_the_readings():
     for need in ("rho_angle", "single_rho_y", "rho_x_half", "unobserved", "huber", "l2", "student"):
         assert need in names, need
     for c in cases:
-        assert len(c["cams"]) >= 3 and "1" in c["copies"]
+        assert len(c["cams"]) >= 3 and str(len(c["cams"])) in c["copies"]
     # the unobserved point and camera are the last ones and keep their starting values
     c = next(c for c in cases if "unobserved" in c["name"])
     assert c["n_pts"] - 1 not in c["pt_idx"] and c["n_cams"] - 1 not in c["cam_idx"]
@@ -169,6 +173,129 @@ def test_pins_reject_a_planted_mistake_in_the_iteration(tmp_path, mutation):
 def test_unmutated_copy_passes_the_pins(tmp_path):
     lib = _mutant(tmp_path, "none", "int ora_admm_iterate(", "int ora_admm_iterate(")
     assert all(_worst(_iterate_with(lib, c), c) <= 1.0 for c in _cases())
+
+
+# ------------------------------------------------------------ block subproblems (Eq. 14)
+def _block_cases():
+    with open(GOLDEN) as fh:
+        return json.load(fh)["block_cases"]
+
+
+def _block_worst(iterate, case):
+    """As _worst, over an oracle.BlockState of the case's (pi, kappa)."""
+    st = O.BlockState(_scene(case), case["pi"], case["kappa"])
+    rho = _rho(case)
+    worst = 0.0
+    for it in range(1, len(case["cams"]) + 1):
+        iterate(st)
+        cams, pts = np.array(case["cams"][it - 1]), np.array(case["pts"][it - 1])
+        worst = max(worst, _excess(st.cams, cams, np.abs(cams).max(axis=0)),
+                    _excess(st.pts, pts, np.abs(pts).max(axis=0)))
+        if str(it) in case["copies"]:
+            cp, du = case["copies"][str(it)], case["duals"][str(it)]
+            for got_c, got_d, key, r in ((st.pcopies, st.pduals, "points", rho[:3]),
+                                         (st.ccopies, st.cduals, "cameras", rho[3:])):
+                want_c, want_d = np.array(cp[key]), np.array(du[key])
+                scale = np.abs(want_c).max(axis=0)
+                worst = max(worst, _excess(got_c, want_c, scale), _excess(got_d, want_d, r * scale))
+    return worst
+
+
+def test_golden_block_cases_cover_every_block_kind():
+    cases = _block_cases()
+    shapes = {tuple(s) for c in cases for s in c["block_shapes"]}
+    assert {(1, 1), (1, 3), (5, 1), (4, 2), (3, 2)} <= shapes
+    names = " ".join(c["name"] for c in cases)
+    for need in ("rho_angle", "single_rho_y", "rho_x_half", "unobserved", "huber", "l2", "student"):
+        assert need in names, need
+    assert any("R" in "".join(c["codes"]) for c in cases)
+
+
+@pytest.mark.parametrize("case", _block_cases(), ids=lambda c: c["name"])
+def test_oracle_block_iteration_follows_golden_iterates(case):
+    cfg = _cfg(case)
+    assert _block_worst(lambda st: st.iterate(cfg, 1, with_gt=False), case) <= 1.0
+
+
+_BLOCK_WARM_FROM_CONSENSUS = (
+    "      for (int u = 0; u < 3 * np; ++u) pcopies[3 * pc_off[b] + u] = xbar[u];\n"
+    "      for (int u = 0; u < 6 * nc; ++u) ccopies[6 * cc_off[b] + u] = ybar[u];\n"
+    "      ora_block_solve(c, np, nc, no,")
+
+_CONSENSUS_PER_OBSERVATION = (
+    "    for (long b = 0; b < n_blocks; ++b)\n"
+    "      for (long q = obs_off[b]; q < obs_off[b + 1]; ++q) {\n"
+    "        long k = pc_off[b] + obs_lp[q], i = pc_pt[k];\n"
+    "        for (int a = 0; a < 3; ++a) sum_x[3 * i + a] += pcopies[3 * k + a] + pduals[3 * k + a] / rho_of(c, a);\n"
+    "        cnt_x[i] += 1;\n"
+    "      }\n")
+
+# Planted mistakes in ora_block_iterate (each text occurs once in it).
+BLOCK_MUTATIONS = [
+    ("point-copy duals ascend against the old consensus",
+     "pduals[3 * k + a] += rho_of(c, a) * (pcopies[3 * k + a] - pts[3 * (long)pc_pt[k] + a]);",
+     "pduals[3 * k + a] += rho_of(c, a) * (pcopies[3 * k + a] - pts_prev[3 * (long)pc_pt[k] + a]);"),
+    ("camera-copy duals ascend by rho_y for every component",
+     "cduals[6 * k + a] += rho_of(c, 3 + a) *", "cduals[6 * k + a] += c->rho_y *"),
+    ("camera-copy dual ascent reversed", "cduals[6 * k + a] += rho_of(c, 3 + a) *",
+     "cduals[6 * k + a] -= rho_of(c, 3 + a) *"),
+    ("point consensus weights each copy by its observations",
+     "    for (long k = 0; k < n_pc; ++k) {\n"
+     "      long i = pc_pt[k];\n"
+     "      for (int a = 0; a < 3; ++a) sum_x[3 * i + a] += pcopies[3 * k + a] + pduals[3 * k + a] / rho_of(c, a);\n"
+     "      cnt_x[i] += 1;\n"
+     "    }\n", _CONSENSUS_PER_OBSERVATION),
+    ("block solves warm-started at the consensus", "      ora_block_solve(c, np, nc, no,",
+     _BLOCK_WARM_FROM_CONSENSUS),
+]
+
+
+def _block_mutant(tmp_path, name, old, new):
+    src = open(ORACLE_SRC).read()
+    start = src.index("int ora_block_iterate(")
+    body = src[start:]
+    assert body.count(old) == 1, name
+    path = tmp_path / ("mutb_" + "".join(ch if ch.isalnum() else "_" for ch in name))
+    path.with_suffix(".c").write_text(src[:start] + body.replace(old, new))
+    so = path.with_suffix(".so")
+    cmd = ["gcc", "-O2", "-fPIC", "-shared", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+           "-I", os.path.dirname(ORACLE_SRC), "-o", str(so), str(path.with_suffix(".c")), "-lm"]
+    subprocess.run(cmd, check=True, capture_output=True)
+    L = ctypes.CDLL(str(so))
+    L.ora_block_iterate.argtypes = O.lib().ora_block_iterate.argtypes
+    L.ora_block_iterate.restype = ctypes.c_int
+    return L
+
+
+def _block_iterate_with(lib, case):
+    cfg = _cfg(case)
+
+    def step(st):
+        s, B = st.scene, st.layout
+        ip, lp = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_long)
+        dp = ctypes.POINTER(ctypes.c_double)
+        I = lambda a: a.ctypes.data_as(ip)  # noqa: E731
+        L = lambda a: a.ctypes.data_as(lp)  # noqa: E731
+        D = lambda a: a.ctypes.data_as(dp)  # noqa: E731
+        rc = lib.ora_block_iterate(ctypes.byref(cfg), s.n_cams, s.n_pts, s.n_obs, I(s.pt_idx), I(s.cam_idx),
+                                   D(np.ascontiguousarray(s.z)), None, B.n_blocks, L(B.obs_off), L(B.blk_obs),
+                                   I(B.obs_lp), I(B.obs_lc), L(B.pc_off), I(B.pc_pt), L(B.cc_off), I(B.cc_cam),
+                                   D(st.pcopies), D(st.pduals), D(st.ccopies), D(st.cduals), D(st.cams), D(st.pts),
+                                   1, 1, None)
+        assert rc == 0
+
+    return step
+
+
+@pytest.mark.parametrize("mutation", BLOCK_MUTATIONS, ids=lambda m: m[0])
+def test_pins_reject_a_planted_mistake_in_the_block_iteration(tmp_path, mutation):
+    lib = _block_mutant(tmp_path, *mutation)
+    assert any(_block_worst(_block_iterate_with(lib, c), c) > 1.0 for c in _block_cases()), mutation[0]
+
+
+def test_unmutated_block_copy_passes_the_pins(tmp_path):
+    lib = _block_mutant(tmp_path, "none", "int ora_block_iterate(", "int ora_block_iterate(")
+    assert all(_block_worst(_block_iterate_with(lib, c), c) <= 1.0 for c in _block_cases())
 
 
 def test_golden_file_is_what_the_restatement_writes():
