@@ -373,15 +373,20 @@ def _consensus(idx, count, values, weights, old):
     return out
 
 
-def admm_iteration(cfg, pt_idx, cam_idx, z, copies, duals, cams, pts, steps):
-    """One iteration; returns the new (copies, duals, cams, pts) and the codes of every local
-    solve with their margins (for the golden writer's cleanliness check)."""
+def admm_iteration(cfg, pt_idx, cam_idx, z, copies, duals, cams, pts, steps, solver="gn"):
+    """One iteration with the Gauss-Newton ("gn") or L-BFGS ("lbfgs") local solve of `steps`
+    steps / iterations; returns the new (copies, duals, cams, pts) and the codes of every
+    local solve with their margins (for the golden writer's cleanliness check)."""
     rho = rho_vec(cfg)
     copies, duals = np.array(copies, float), np.array(duals, float)
     codes, margins = [], []
     for o in range(len(pt_idx)):
         c = {"z": np.asarray(z[o], float), "vbar": np.r_[pts[pt_idx[o]], cams[cam_idx[o]]], "dual": duals[o]}
-        traj, code, marg = gauss_newton(cfg, c, copies[o], steps)
+        if solver == "lbfgs":
+            traj, trials, marg = lbfgs(cfg, c, copies[o], steps)
+            code = ",".join(trials)
+        else:
+            traj, code, marg = gauss_newton(cfg, c, copies[o], steps)
         copies[o] = traj[-1]
         codes.append(code)
         margins.append(marg)

@@ -9,7 +9,7 @@ point's and camera's part of the augmented Lagrangian, and the dual ascent; it s
 code with the C oracle.  The scenes are small versions of the synthetic geometries of
 paper_1708_07954_gb300.scenes with their own penalties, one of them with a point penalty
 different from the camera penalty, the paper's single camera penalty (rho_angle 0), and an
-unobserved point and camera appended.  Every case stores the consensus after each iteration
+unobserved point and camera appended; one case takes the L-BFGS local solve.  Every case stores the consensus after each iteration
 and the copies and duals after the last.  Block cases take the oracle's block
 layout (oracle.BlockLayout, pinned against brute-force grouping) and cover one-point,
 one-camera and two-camera blocks.
@@ -45,19 +45,19 @@ def with_unobserved(sc):
                                cams_gt=np.vstack([sc.cams_gt, sc.cams_gt[:1]]))
 
 
-def case(name, sc, loss, loss_param, rho_x, rho_y, rho_angle, steps, iters):
+def case(name, sc, loss, loss_param, rho_x, rho_y, rho_angle, steps, iters, solver="gn"):
     cfg = {"focal": sc.focal, "cx": sc.cx, "cy": sc.cy, "loss": loss, "loss_param": loss_param,
            "rho_x": rho_x, "rho_y": rho_y, "rho_angle": rho_angle, "lm_lambda0": 1e-3,
            "lm_lambda_min": 1e-12, "eps_depth": 1e-6, "lm_model_tol": 16.0}
     cams, pts = sc.cams0.astype(float).copy(), sc.pts0.astype(float).copy()
     copies = np.concatenate([pts[sc.pt_idx], cams[sc.cam_idx]], axis=1)
     duals = np.zeros_like(copies)
-    out = {"name": name, "cfg": cfg, "steps": steps, "n_pts": sc.n_pts, "n_cams": sc.n_cams,
+    out = {"name": name, "cfg": cfg, "steps": steps, "solver": solver, "n_pts": sc.n_pts, "n_cams": sc.n_cams,
            "pt_idx": sc.pt_idx.tolist(), "cam_idx": sc.cam_idx.tolist(), "z": sc.z.tolist(),
            "cams0": cams.tolist(), "pts0": pts.tolist(), "cams": [], "pts": [], "copies": {}, "duals": {}}
     for it in range(1, iters + 1):
         copies, duals, cams, pts, codes, _ = R.admm_iteration(cfg, sc.pt_idx, sc.cam_idx, sc.z, copies, duals,
-                                                              cams, pts, steps)
+                                                              cams, pts, steps, solver)
         out["cams"].append(cams.tolist())
         out["pts"].append(pts.tolist())
         if it == iters:
@@ -110,6 +110,8 @@ def main():
         case("ring64-student-rho_angle-unobserved", with_unobserved(ring64), S.LOSS_STUDENT_T, 4.0,
              ring64.rho_x, 2.0 * ring64.rho_y, ring64.rho_angle, 5, 3),
         case("grid-huber-single_rho_y", grid, S.LOSS_HUBER, 2.0, grid.rho_x, grid.rho_y, 0.0, 3, 3),
+        case("ring8-huber-rho_angle-lbfgs", ring, S.LOSS_HUBER, 2.0, ring.rho_x, ring.rho_y, ring.rho_angle, 2, 4,
+             solver="lbfgs"),
     ]
     block_cases = [
         block_case("ring8-4x2-huber-rho_angle", ring, 4, 2, S.LOSS_HUBER, 2.0, ring.rho_x, ring.rho_y,

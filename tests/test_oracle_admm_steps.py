@@ -6,7 +6,8 @@ tests/golden/admm_steps.json holds iterates written by tests/golden/make_admm_st
 oracle/steps_restated.py, a second statement of the iteration that shares no code with
 oracle/dba_oracle.c: its local solves are the restated Gauss-Newton solve, its consensus is
 the least-squares minimiser of each point's and camera's part of the augmented Lagrangian,
-and its duals ascend by rho (copy - new consensus).  The block cases solve each block by the
+and its duals ascend by rho (copy - new consensus); one case takes the L-BFGS local solve,
+whose dispatch the invariants cannot see either.  The block cases solve each block by the
 restated block solve over the oracle's block layout (pinned against brute-force grouping)
 and take each consensus over the copies, one per block that holds the point or camera.
 Both oracle iterations are replayed over every case and compared after each iteration.
@@ -55,7 +56,8 @@ def _cfg(case):
     return O.config(focal=c["focal"], cx=c["cx"], cy=c["cy"], loss=c["loss"], loss_param=c["loss_param"],
                     rho_x=c["rho_x"], rho_y=c["rho_y"], rho_angle=c["rho_angle"], inner_steps=case["steps"],
                     lm_lambda0=c["lm_lambda0"], lm_lambda_min=c["lm_lambda_min"], eps_depth=c["eps_depth"],
-                    lm_model_tol=c["lm_model_tol"])
+                    lm_model_tol=c["lm_model_tol"],
+                    local_solver=O.SOLVER_LBFGS if case.get("solver") == "lbfgs" else O.SOLVER_GN)
 
 
 def _rho(case):
@@ -89,8 +91,9 @@ def _worst(iterate, case):
 def test_golden_cases_cover_the_readings():
     cases = _cases()
     names = " ".join(c["name"] for c in cases)
-    for need in ("rho_angle", "single_rho_y", "rho_x_half", "unobserved", "huber", "l2", "student"):
+    for need in ("rho_angle", "single_rho_y", "rho_x_half", "unobserved", "huber", "l2", "student", "lbfgs"):
         assert need in names, need
+    assert any(c.get("solver") == "lbfgs" for c in cases)
     for c in cases:
         assert len(c["cams"]) >= 3 and str(len(c["cams"])) in c["copies"]
     # the unobserved point and camera are the last ones and keep their starting values
@@ -122,6 +125,7 @@ MUTATIONS = [
     ("dual ascent reversed", "duals[9 * o + k] += c->rho_x *", "duals[9 * o + k] -= c->rho_x *"),
     ("camera consensus not a mean", "cams[6 * j + k] = sum_y[6 * j + k] / (double)cnt_y[j];",
      "cams[6 * j + k] = sum_y[6 * j + k] / (double)(cnt_y[j] + 1);"),
+    ("the L-BFGS local solve ignored", "if (c->local_solver == ORA_SOLVER_LBFGS)", "if (0)"),
     ("local solves warm-started at the consensus",
      "    /* Eq. (9): every observation's local subproblem, warm-started at its copy. */\n",
      _WARM_FROM_CONSENSUS),
