@@ -334,7 +334,8 @@ def block_gauss_newton(cfg, blk, v0, steps):
         Lt = block_objective(cfg, blk, v + d)
         ok = np.isfinite(Lt) and (trust or Lt < L)
         margins.append({"pred_over_noise": float(pred / noise) if noise > 0 else np.inf,
-                        "rel_change": float((Lt - L) / abs(L)) if np.isfinite(Lt) and np.isfinite(L) else np.inf})
+                        "rel_change": float((Lt - L) / abs(L)) if np.isfinite(Lt) and np.isfinite(L) else np.inf,
+                        "pred": float(pred)})
         if ok:
             v = v + d
             L = Lt

@@ -13,7 +13,8 @@ plausible size, and a start displaced from the consensus.  As in make_local_step
 case keeps the leading steps whose every decision is far from its threshold.  The case set
 covers one-point, one-camera and wider blocks, all three misfits, both camera-penalty
 readings, rejected steps, steps accepted by the rounding-noise rule, a binding damping
-clamp, a trial behind a camera and a start with an observation behind its camera.
+clamp, a trial behind a camera, a start with an observation behind its camera, and rejected
+steps with a small predicted decrease (below 0.5 px^2, far above the rounding noise).
 
     python tests/golden/make_block_steps.py      # rewrites block_steps.json
 """
@@ -177,6 +178,26 @@ def main():
     start = case_of("behind-camera-start", dict(cfg, lm_lambda0=1e-5), blk, v0, min_clean=2)
     assert start is not None and not np.isfinite(R.block_objective(cfg, blk, v0))
     cases.append(start)
+
+    # a rejected step whose predicted decrease is small (below 0.5 px^2) but far above the
+    # rounding noise: plain comparison must reject it, the noise rule must not trust it
+    rng2 = np.random.default_rng(20262)
+    sc = scenes["grid"]
+    for layout, shape, loss, lname in (((1, 3), (1, 2), S.LOSS_STUDENT_T, "student"),
+                                       ((5, 1), (2, 1), S.LOSS_HUBER, "huber")):
+        B, cand = blocks_of(sc, *layout, shape)
+
+        def make_small(r, B=B, cand=cand, loss=loss, lname=lname, shape=shape):
+            cfg = base_cfg(sc, loss, False)
+            blk, v0 = draw(sc, cfg, r, B, int(r.choice(cand)), 2.0, float(r.choice([0.0, 10.0, 60.0])),
+                           float(r.choice([3.0, 10.0, 30.0])), 3.0)
+            traj, codes, margins = R.block_gauss_newton(cfg, blk, v0, STEPS)
+            k = n_clean(margins)
+            if not any(c == "R" and m["pred"] < 0.5 for c, m in zip(codes[:k], margins[:k])):
+                return None
+            return case_of(f"grid-{shape[0]}x{shape[1]}-{lname}-single_rho_y-small-prediction-reject", cfg, blk, v0)
+
+        cases.append(search(make_small, lambda k: True, rng2, 2000))
 
     with open(OUT, "w") as fh:
         json.dump({"about": "step-wise trajectories of the block solve of Eq. (14); written by "

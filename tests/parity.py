@@ -12,7 +12,9 @@ def colerr(a, b):
     if b.ndim == 1:
         a, b = a[:, None], b[:, None]
     scale = np.maximum(np.abs(b).max(axis=0), 1e-300)
-    return float((np.abs(a - b).max(axis=0) / scale).max())
+    err = float((np.abs(a - b).max(axis=0) / scale).max())
+    # a NaN anywhere is an infinite error, so that a running max over checks cannot drop it
+    return err if np.isfinite(err) else float("inf")
 
 
 # Block sizes (points, cameras) of the block parity test.  Together they put blocks in every

@@ -121,6 +121,14 @@ def test_cholesky_matches_numpy():
         np.testing.assert_allclose(O.chol_solve(A, b), np.linalg.solve(A, b), rtol=1e-12, atol=1e-12)
     with pytest.raises(np.linalg.LinAlgError):
         O.chol_solve(-np.eye(3), np.ones(3))
+    # every pivot below 1 (a well-posed system at a small scale) still solves ...
+    A = rng.normal(size=(9, 9))
+    A = 1e-6 * (A @ A.T + 9 * np.eye(9))
+    b = rng.normal(size=9)
+    np.testing.assert_allclose(O.chol_solve(A, b), np.linalg.solve(A, b), rtol=1e-10)
+    # ... and an exactly zero pivot is refused, not divided by
+    with pytest.raises(np.linalg.LinAlgError):
+        O.chol_solve(np.diag([1.0, 0.0, 1.0]), np.ones(3))
 
 
 # ------------------------------------------------- local subproblem, Eq. (9)
@@ -221,7 +229,7 @@ def test_admm_is_insensitive_to_last_bit_perturbations():
     for _ in range(6):
         a.iterate(c, 1)
         b.iterate(c, 1)
-    err = max(np.abs(a.pts - b.pts).max() / np.abs(a.pts).max(), np.abs(a.cams - b.cams).max() / np.abs(a.cams).max())
+    err = np.max([np.abs(a.pts - b.pts).max() / np.abs(a.pts).max(), np.abs(a.cams - b.cams).max() / np.abs(a.cams).max()])
     assert err < 1e-13
 
 

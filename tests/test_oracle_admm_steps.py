@@ -67,7 +67,9 @@ def _rho(case):
 
 
 def _excess(got, want, scale):
-    return float((np.abs(got - want) / (REL * np.maximum(scale, 1e-300))).max())
+    """Largest error in units of the tolerance; +inf for a NaN (which a running max would drop)."""
+    err = float((np.abs(got - want) / (REL * np.maximum(scale, 1e-300))).max())
+    return err if np.isfinite(err) else np.inf
 
 
 def _worst(iterate, case):

@@ -8,8 +8,9 @@ whole block vector, dense products with the weights, numpy LU).  Every GPU parit
 the block path compares a few-step trajectory of every block, so ora_block_solve must be
 right step by step: each golden case is replayed with 1, 2, ... steps.  The cases cover
 one-point, one-camera and wider blocks, a single-observation block, rejected steps, steps
-taken by the rounding-noise rule, a binding damping clamp, a trial behind a camera and a
-start with an observation behind its camera.
+taken by the rounding-noise rule, a binding damping clamp, a trial behind a camera, a
+start with an observation behind its camera, and rejected steps whose predicted decrease is
+small but far above the rounding noise (the noise rule must not trust them).
 
 The mutation tests plant mistakes in a copy of the C oracle's block solve (a dropped dual,
 a transposed camera index, a wrong penalty, the damping start over 9 unknowns instead of
@@ -70,7 +71,8 @@ def _worst(lib, case, **over):
         want = np.array(case["v"][k])
         got = _solve(lib, case, k, **over)
         tol = REL_TRAVEL * np.abs(want - v0).max() + REL_COORD * np.abs(want).max()
-        worst = max(worst, np.abs(got - want).max() / tol)
+        err = np.abs(got - want).max() / tol
+        worst = max(worst, err if np.isfinite(err) else np.inf)  # a NaN result fails
     return worst
 
 
@@ -80,7 +82,8 @@ def test_golden_cases_cover_every_rule_and_block_shape():
     assert {"A", "R", "T"} <= set(codes)
     names = [c["name"] for c in cases]
     for need in ("1x3", "5x1", "4x2", "8x2", "4x4", "1x1", "clamp", "at-minimum", "behind-camera-trial",
-                 "behind-camera-start", "reject", "single_rho_y", "rho_angle", "l2", "huber", "student"):
+                 "behind-camera-start", "reject", "small-prediction-reject", "single_rho_y", "rho_angle", "l2",
+                 "huber", "student"):
         assert any(need in n for n in names), need
     shapes = {(len(c["xbar"]) // 3, len(c["ybar"]) // 6) for c in cases}
     assert {(1, 3), (5, 1), (4, 2), (8, 2), (4, 4), (1, 1)} <= shapes
@@ -113,6 +116,8 @@ MUTATIONS = [
      "H[(size_t)col[a] * n + col[b]] += 2.0 * (J[a] * J[b] + J[9 + a] * J[9 + b]);"),
     ("point-camera coupling dropped", "for (int b = 0; b < 9; ++b)\n",
      "for (int b = (a < 3 ? 0 : 3); b < (a < 3 ? 3 : 9); ++b)\n"),
+    ("predicted decrease shifted by 0.5 (steps that increase Eq. (14) trusted)", "double gd = 0.0, dd = 0.0;",
+     "double gd = 1.0, dd = 0.0;"),
     ("misfit kept behind the camera at the linearisation point",
      "if (!(depth > c->eps_depth)) continue; /* no misfit term at this linearisation point */", ""),
 ]
@@ -174,6 +179,30 @@ def test_golden_file_is_what_the_restatement_writes():
         blk["opl"], blk["ocl"] = case["opl"], case["ocl"]
         traj = R.block_gauss_newton(case["cfg"], blk, np.array(case["v"][0]), len(case["v"]) - 1)[0]
         np.testing.assert_array_equal(np.array(traj), np.array(case["v"]))
+
+
+def test_block_objective_matches_the_restatement():
+    """The value of Eq. (14), not only its differences (which are all a solve compares), against
+    the restated objective at every golden point, +inf where an observation is behind its camera."""
+    from oracle import steps_restated as R
+
+    n_inf = 0
+    for case in _cases():
+        cfg = _cfg(case, 1)
+        blk = {k: np.array(case[k]) for k in ("z", "xbar", "ybar", "rx", "sy")}
+        blk["opl"], blk["ocl"] = case["opl"], case["ocl"]
+        np_ = len(case["xbar"]) // 3
+        for v in case["v"]:
+            v = np.array(v)
+            want = R.block_objective(case["cfg"], blk, v)
+            got = O.block_objective(cfg, case["opl"], case["ocl"], blk["z"], blk["xbar"], blk["ybar"], blk["rx"],
+                                    blk["sy"], v[:3 * np_], v[3 * np_:])
+            if np.isinf(want):
+                n_inf += 1
+                assert got == np.inf, case["name"]
+            else:
+                assert abs(got - want) <= 1e-12 * max(abs(want), 1.0), case["name"]
+    assert n_inf >= 1
 
 
 def test_one_observation_block_restates_the_local_solve():

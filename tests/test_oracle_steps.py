@@ -70,7 +70,8 @@ def _worst(lib, case, **over):
         want = np.array(case["v"][k])
         got = _solve(lib, case, k, **over)
         tol = REL_TRAVEL * np.abs(want - v0).max() + REL_COORD * np.abs(want).max()
-        worst = max(worst, np.abs(got - want).max() / tol)
+        err = np.abs(got - want).max() / tol
+        worst = max(worst, err if np.isfinite(err) else np.inf)  # a NaN result fails
     return worst
 
 
