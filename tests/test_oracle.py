@@ -363,6 +363,44 @@ def test_mlp_reference_gradient_matches_finite_differences():
     assert np.all(g[OM.N_TRAINABLE:] == 0)
 
 
+def test_mlp_reference_forward_loss_and_gradient_match_torch():
+    """The network as the layout documents it, stated with torch's own modules in float64 (the
+    tanh-form GELU, linear layers, standardised inputs, the mean squared error over the first 9
+    outputs against scaled targets), and its gradient by torch's autograd: every output, the
+    loss and every trainable parameter's derivative agree with the numpy reference."""
+    import torch
+    import torch.nn.functional as F
+
+    import oracle.mlp as OM
+
+    rng = np.random.default_rng(22)
+    p = rng.normal(0, 0.3, OM.N_PARAMS)
+    p[OM.N_TRAINABLE:OM.N_TRAINABLE + OM.N_IN] = rng.normal(0, 1, OM.N_IN)
+    p[OM.N_TRAINABLE + OM.N_IN:OM.N_TRAINABLE + 2 * OM.N_IN] = rng.uniform(0.5, 2, OM.N_IN)
+    p[OM.N_TRAINABLE + 2 * OM.N_IN:] = rng.uniform(0.5, 2, OM.N_OUT)
+    f = rng.normal(0, 1, (11, OM.N_IN))
+    t = rng.normal(0, 1, (11, OM.N_OUT))
+
+    q = {k: torch.tensor(v, dtype=torch.float64, requires_grad=True) for k, v in OM.unpack(p).items()}
+    x = (torch.tensor(f) - q["in_mean"]) / q["in_std"]
+    h = F.gelu(F.linear(x, q["W1"], q["b1"]), approximate="tanh")
+    h = F.gelu(F.linear(h, q["W2"], q["b2"]), approximate="tanh")
+    h = F.gelu(F.linear(h, q["W3"], q["b3"]), approximate="tanh")
+    y = F.linear(h, q["W4"], q["b4"])
+    target = torch.tensor(t) / q["out_scale"]
+    loss = F.mse_loss(y[:, :OM.N_USED], target[:, :OM.N_USED])
+    loss.backward()
+
+    y_ref, _ = OM.forward(p, f)
+    np.testing.assert_allclose(y_ref, y.detach().numpy(), rtol=1e-12, atol=1e-12)
+    loss_ref, g_ref = OM.loss_and_grad(p, f, t)
+    assert abs(loss_ref - loss.item()) <= 1e-12 * loss.item()
+    trainable = [name for name, _ in OM.SHAPES][:8]
+    g_torch = np.concatenate([q[name].grad.numpy().ravel() for name in trainable])
+    assert len(g_torch) == OM.N_TRAINABLE
+    np.testing.assert_allclose(g_ref[:OM.N_TRAINABLE], g_torch, rtol=1e-10, atol=1e-13)
+
+
 def test_mlp_reference_gelu_and_its_derivative():
     """The tanh form of GELU stays within 5e-4 of its definition x Phi(x) (Phi the standard
     normal CDF, here through scipy's erf), has the limits 0 and x, and its derivative matches
