@@ -11,8 +11,9 @@ from paper_1708_07954_gb300 import scenes as S
 
 
 def test_layout_matches_brute_force_grouping():
-    """Every observation lands in the block of (its point's group, its camera's group);
-    copies are the distinct points/cameras of each block, in rank / index order."""
+    """Every observation lands in the block of (its point's group, its camera's group), in
+    (point rank, camera) order inside it; copies are the distinct points/cameras of each
+    block, in rank / index order."""
     sc = S.scene1(n_pts=300, n_cams=24, seed=5)
     for pi, kappa in ((1, 1), (8, 2), (32, 4), (7, 3)):
         B = O.BlockLayout(sc, pi, kappa)
@@ -30,7 +31,8 @@ def test_layout_matches_brute_force_grouping():
         assert B.n_blocks == len(keys)
         for b, key in enumerate(keys):
             obs = B.blk_obs[B.obs_off[b]:B.obs_off[b + 1]]
-            assert sorted(obs.tolist()) == sorted(blocks[key])
+            # inside a block: by point rank, then camera
+            assert obs.tolist() == sorted(blocks[key], key=lambda o: (rank[int(sc.pt_idx[o])], int(sc.cam_idx[o])))
             pts = sorted({int(sc.pt_idx[o]) for o in blocks[key]}, key=lambda i: rank[i])
             cams = sorted({int(sc.cam_idx[o]) for o in blocks[key]})
             assert B.pc_pt[B.pc_off[b]:B.pc_off[b + 1]].tolist() == pts
